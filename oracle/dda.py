@@ -1,0 +1,329 @@
+"""FP64 numpy statement of the discrete dipole approximation (DDA).
+
+Test infrastructure (see the package docstring).  Units: lattice units,
+dipole spacing d = 1, incident amplitude |E0| = 1, Gaussian units, so
+"kd" below is the dimensionless k*d.
+
+The guide states the linear system A P = E ("Choice of Iterative
+Algorithm", eq. AP=E) and names the formulae it uses (Draine 1988 for the
+DDA equations and cross sections; Draine & Goodman 1993 for the LATTDR
+polarizability; Goodman, Draine & Flatau 1990 for the FFT method) without
+printing them.  The forms below are the published ones; each docstring says
+which reading is taken and what pins it.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# LATTDR coefficients of the lattice dispersion relation (Draine & Goodman
+# 1993), cited by the guide in "Dipole Polarizabilities".  The guide does not
+# print them: parity unpinned for these three numbers (they are pinned only
+# indirectly, through convergence to the Mie series as N grows).
+LDR_B1 = -1.8915316
+LDR_B2 = 0.1648469
+LDR_B3 = -1.7700004
+
+
+# ---------------------------------------------------------------- geometry --
+def site_positions(grid: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Occupied sites of a composition grid [nz, ny, nx] (x fastest).
+
+    Returns (r, comp): r (N, 3) float64 dipole positions in lattice units,
+    r = (ix-(nx-1)/2, iy-(ny-1)/2, iz-(nz-1)/2), ordered with x fastest, then
+    y, then z (the order of a row-major scan of the grid); comp (N,) the
+    composition code (1..ncomp) of each site.  Target Frame origin at the
+    centre of the computational volume (ELLIPSOID section: origin at the
+    centroid).
+    """
+    nz, ny, nx = grid.shape
+    iz, iy, ix = np.nonzero(grid)           # row-major order == x fastest
+    r = np.stack([ix - (nx - 1) / 2.0, iy - (ny - 1) / 2.0, iz - (nz - 1) / 2.0], axis=1)
+    return r.astype(np.float64), grid[iz, iy, ix].astype(np.int64)
+
+
+def aeff_lattice(ndipoles: int) -> float:
+    """a_eff = (3V/4pi)^(1/3) with V = N d^3 (eq. for a_eff, "Applicability
+    of the DDA"), in units of d."""
+    return (3.0 * ndipoles / (4.0 * math.pi)) ** (1.0 / 3.0)
+
+
+def kd_from_size_parameter(x: float, ndipoles: int) -> float:
+    """k d from x = k a_eff (size-parameter equation)."""
+    return x / aeff_lattice(ndipoles)
+
+
+# ---------------------------------------------------------- polarizability --
+def ldr_inverse_polarizability(eps, kd: float, khat, ehat) -> np.ndarray:
+    """1/alpha for the LATTDR prescription (Draine & Goodman 1993).
+
+    alpha_CM = (3/4pi) (eps-1)/(eps+2)          (Clausius-Mossotti, d = 1)
+    1/alpha  = 1/alpha_CM + (b1 + b2 eps + b3 eps S) (kd)^2 - (2/3) i (kd)^3
+    S        = sum_a (khat_a ehat_a)^2            (ehat as given, unconjugated)
+
+    eps may be an array (one value per composition or per dipole).  The
+    -(2/3) i k^3 term is the radiative-reaction correction; pinned by the
+    N = 1 closed forms and the lossless invariant (C_abs = 0 for real eps).
+    The b_i are parity unpinned (see module constants).
+    """
+    eps = np.asarray(eps, dtype=np.complex128)
+    khat = np.asarray(khat, dtype=np.float64)
+    ehat = np.asarray(ehat, dtype=np.complex128)
+    S = np.sum((khat * ehat) ** 2)
+    inv_acm = (4.0 * math.pi / 3.0) * (eps + 2.0) / (eps - 1.0)
+    return inv_acm + (LDR_B1 + LDR_B2 * eps + LDR_B3 * eps * S) * kd ** 2 - (2.0 / 3.0) * 1j * kd ** 3
+
+
+def ldr_inverse_polarizability_derivative(eps, kd: float, khat, ehat) -> np.ndarray:
+    """d(1/alpha)/d(eps) of the LATTDR form above: -4pi/(eps-1)^2 + (b2 + b3 S) k^2."""
+    eps = np.asarray(eps, dtype=np.complex128)
+    S = np.sum((np.asarray(khat, float) * np.asarray(ehat, complex)) ** 2)
+    return -4.0 * math.pi / (eps - 1.0) ** 2 + (LDR_B2 + LDR_B3 * S) * kd ** 2
+
+
+# ------------------------------------------------------ interaction matrix --
+def interaction_tensor(rvec, kd: float) -> np.ndarray:
+    """Off-diagonal 3x3 block A_jl for displacement r = r_j - r_l != 0.
+
+    A_jl = exp(ik rho)/rho [ k^2 (rr - I) + (ik rho - 1)/rho^2 (3 rr - I) ],
+    rr = rhat rhat^T, rho = |r|, so that the field at j from dipole l is
+    -A_jl P_l and the DDA equations read A P = E with A_jj = (1/alpha_j) I
+    (Draine 1988, the form the guide cites under eq. AP=E).  Pinned by the
+    two-dipole test against the textbook dipole field.  Vectorised over
+    leading axes of rvec (..., 3).
+    """
+    rvec = np.asarray(rvec, dtype=np.float64)
+    rho = np.linalg.norm(rvec, axis=-1)
+    rh = rvec / rho[..., None]
+    rr = rh[..., :, None] * rh[..., None, :]
+    eye = np.eye(3)
+    ph = np.exp(1j * kd * rho) / rho
+    t1 = (kd * kd)[..., None, None] if np.ndim(kd) else kd * kd
+    c2 = (1j * kd * rho - 1.0) / rho ** 2
+    return ph[..., None, None] * (t1 * (rr - eye) + c2[..., None, None] * (3.0 * rr - eye))
+
+
+def dense_matrix(r: np.ndarray, kd: float, beta: np.ndarray) -> np.ndarray:
+    """The full 3N x 3N matrix A, row/column index 3*j + a.
+
+    beta (N,) holds 1/alpha_j for each dipole (isotropic diagonal blocks).
+    """
+    n = r.shape[0]
+    A = np.zeros((n, 3, n, 3), dtype=np.complex128)
+    for j in range(n):
+        d = r[j] - r
+        d[j] = (1.0, 0.0, 0.0)                # placeholder, overwritten below
+        blk = interaction_tensor(d, kd)       # (n, 3, 3)
+        blk[j] = beta[j] * np.eye(3)
+        A[j] = np.transpose(blk, (1, 0, 2))
+    return A.reshape(3 * n, 3 * n)
+
+
+def pairwise_matvec(r: np.ndarray, kd: float, beta: np.ndarray, P: np.ndarray,
+                    rows: np.ndarray | None = None, chunk: int = 256) -> np.ndarray:
+    """(A P)_j = beta_j P_j + sum_{l != j} A(r_j - r_l) P_l, the plain O(N^2) sum.
+
+    P (N, 3) complex.  If ``rows`` is given only those output rows are formed
+    (row sampling for large targets).  Returns (len(rows) or N, 3).
+    """
+    P = np.asarray(P, dtype=np.complex128)
+    rows = np.arange(r.shape[0]) if rows is None else np.asarray(rows)
+    out = np.empty((rows.size, 3), dtype=np.complex128)
+    for s in range(0, rows.size, chunk):
+        jj = rows[s:s + chunk]
+        d = r[jj][:, None, :] - r[None, :, :]            # (c, N, 3)
+        self_mask = np.zeros(d.shape[:2], dtype=bool)
+        self_mask[np.arange(jj.size), jj] = True
+        d[self_mask] = (1.0, 0.0, 0.0)
+        blk = interaction_tensor(d, kd)                   # (c, N, 3, 3)
+        blk[self_mask] = 0.0
+        out[s:s + chunk] = np.einsum("clab,lb->ca", blk, P) + beta[jj][:, None] * P[jj]
+    return out
+
+
+# ----------------------------------------------------------- incident field --
+def incident_field(r: np.ndarray, kd: float, khat, ehat) -> np.ndarray:
+    """E_inc,j = ehat exp(i kd khat . r_j)  (N, 3); phase origin at the lattice centre."""
+    ph = np.exp(1j * kd * (r @ np.asarray(khat, dtype=np.float64)))
+    return ph[:, None] * np.asarray(ehat, dtype=np.complex128)[None, :]
+
+
+# ------------------------------------------------------------------ solvers --
+def solve_dense(A: np.ndarray, E: np.ndarray) -> np.ndarray:
+    """Direct solve of A P = E (LAPACK LU via numpy); E, P as (N, 3)."""
+    return np.linalg.solve(A, E.reshape(-1)).reshape(-1, 3)
+
+
+def bicgstab(matvec, b: np.ndarray, tol: float, maxit: int, x0=None):
+    """Unpreconditioned BiCGstab (van der Vorst 1992) for complex A x = b.
+
+    The guide's recommended solvers are BiCGstab variants (PBCGS2, PBCGST,
+    "Choice of Iterative Algorithm").  Stops when ||b - A x|| <= tol ||b||
+    (recurrence residual; the caller re-checks the true residual).  Vectors
+    are flat complex arrays.  Returns (x, iterations, matvecs, relres).
+    """
+    b = np.asarray(b, dtype=np.complex128).ravel()
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.complex128).ravel()
+    r = b - matvec(x) if x0 is not None else b.copy()
+    nmv = 1 if x0 is not None else 0
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return x, 0, nmv, 0.0
+    rhat = r.copy()
+    rho_old = alpha = omega = 1.0 + 0j
+    v = np.zeros_like(b)
+    p = np.zeros_like(b)
+    relres = np.linalg.norm(r) / bnorm
+    it = 0
+    while relres > tol and it < maxit:
+        rho = np.vdot(rhat, r)
+        beta = (rho / rho_old) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        v = matvec(p)
+        alpha = rho / np.vdot(rhat, v)
+        s = r - alpha * v
+        t = matvec(s)
+        nmv += 2
+        omega = np.vdot(t, s) / np.vdot(t, t)
+        x = x + alpha * p + omega * s
+        r = s - omega * t
+        rho_old = rho
+        it += 1
+        relres = np.linalg.norm(r) / bnorm
+    return x, it, nmv, relres
+
+
+def normal_equation_error(matvec, P: np.ndarray, E: np.ndarray) -> float:
+    """|A^H A P - A^H E| / |A^H E| (eq. err_tol).  Uses A^H x = conj(A conj(x)),
+    valid because A = A^T."""
+    P = np.asarray(P).ravel()
+    E = np.asarray(E).ravel()
+    ah = lambda v: np.conj(matvec(np.conj(v)))  # noqa: E731
+    num = np.linalg.norm(ah(matvec(P)) - ah(E))
+    return float(num / np.linalg.norm(ah(E)))
+
+
+# ---------------------------------------------------------- cross sections --
+def cross_sections(kd: float, E_inc: np.ndarray, P: np.ndarray, beta: np.ndarray):
+    """(C_ext, C_abs, C_sca) in units of d^2 (Draine 1988 forms).
+
+    C_ext = 4 pi k sum_j Im(E_inc,j^* . P_j)
+    C_abs = 4 pi k sum_j [ Im(P_j . (1/alpha_j)^* P_j^*) - (2/3) k^3 |P_j|^2 ]
+    C_sca = C_ext - C_abs  (the guide's printed output obeys Q_ext = Q_abs +
+    Q_sca to all digits, App. "Sample output", and defines Q_ext that way in
+    "What Does DDSCAT Calculate?").
+    Pinned by the single-dipole closed forms and by the independent far-field
+    C_sca of a converged solve.
+    """
+    k = kd
+    cext = 4.0 * math.pi * k * float(np.sum(np.imag(np.conj(E_inc) * P)))
+    p2 = np.sum(np.abs(P) ** 2, axis=1)
+    cabs = 4.0 * math.pi * k * float(np.sum(np.imag(np.conj(beta)) * p2 - (2.0 / 3.0) * k ** 3 * p2))
+    return cext, cabs, cext - cabs
+
+
+def efficiencies(C, aeff: float):
+    """Q = C / (pi a_eff^2) ("What Does DDSCAT Calculate?")."""
+    return tuple(c / (math.pi * aeff ** 2) for c in C)
+
+
+def _sph_j012(u: np.ndarray):
+    """Spherical Bessel j0, j1, j2.  For u < 1 the power series
+    j_n(u) = u^n/(2n+1)!! sum_k (-u^2/2)^k / (k! (2n+3)(2n+5)...(2n+2k+1))
+    (12 terms) avoids the cancellation of the closed forms."""
+    u = np.asarray(u, dtype=np.float64)
+    out = []
+    small = u < 1.0
+    us = u[small]
+    ul = u[~small]
+    s, c = np.sin(ul), np.cos(ul)
+    closed = (s / ul, s / ul ** 2 - c / ul, (3 / ul ** 3 - 1 / ul) * s - 3 * c / ul ** 2)
+    for n, dfact in ((0, 1.0), (1, 3.0), (2, 15.0)):
+        j = np.empty_like(u)
+        term = us ** n / dfact
+        acc = term.copy()
+        for k in range(1, 13):
+            term = term * (-us * us / 2.0) / (k * (2 * n + 2 * k + 1))
+            acc += term
+        j[small] = acc
+        j[~small] = closed[n]
+        out.append(j)
+    return tuple(out)
+
+
+def csca_pair_sum(r: np.ndarray, kd: float, P: np.ndarray, chunk: int = 256) -> float:
+    """Scattering cross section as an exact pair sum.
+
+    dC_sca/dOmega = k^4 |sum_j (I - nn) P_j exp(-ik n.r_j)|^2; integrating
+    over directions with  int (I - nn) exp(iu n.Rhat) dOmega
+    = 4 pi [ (j0(u) - j1(u)/u) I + j2(u) Rhat Rhat ],  u = k|r_j - r_l|,
+    gives C_sca = 4 pi k^4 sum_{j,l} P_j^* . [..] . P_l (self term 2/3 I).
+    Pinned by ``csca_quadrature`` (direct angular integration).
+    """
+    k = kd
+    P = np.asarray(P, dtype=np.complex128)
+    n = r.shape[0]
+    total = 0.0 + 0.0j
+    for s in range(0, n, chunk):
+        jj = np.arange(s, min(n, s + chunk))
+        d = r[jj][:, None, :] - r[None, :, :]
+        R = np.linalg.norm(d, axis=-1)
+        u = k * R
+        j0, j1, j2 = _sph_j012(u)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            iso = np.where(u > 0, j0 - j1 / np.where(u > 0, u, 1.0), 2.0 / 3.0)
+            Rh = d / np.where(R > 0, R, 1.0)[..., None]
+        pl_dot = np.einsum("cla,la->cl", Rh, P)                  # Rhat . P_l
+        pj_dot = np.einsum("cla,ca->cl", Rh, np.conj(P[jj]))     # P_j^* . Rhat
+        pp = np.conj(P[jj]) @ P.T                                # P_j^* . P_l
+        total += np.sum(iso * pp + j2 * pj_dot * pl_dot)
+    return float(4.0 * math.pi * k ** 4 * total.real)
+
+
+def csca_quadrature(r: np.ndarray, kd: float, P: np.ndarray, ntheta: int = 64, nphi: int = 128) -> float:
+    """C_sca by direct angular quadrature of the far field: Gauss-Legendre in
+    cos(theta) times the trapezoid rule in phi."""
+    k = kd
+    P = np.asarray(P, dtype=np.complex128)
+    mu, w = np.polynomial.legendre.leggauss(ntheta)
+    phi = np.arange(nphi) * (2 * math.pi / nphi)
+    st = np.sqrt(1 - mu ** 2)
+    n = np.stack([st[:, None] * np.cos(phi)[None, :], st[:, None] * np.sin(phi)[None, :],
+                  np.broadcast_to(mu[:, None], (ntheta, nphi))], axis=-1).reshape(-1, 3)
+    wt = np.repeat(w, nphi) * (2 * math.pi / nphi)
+    total = 0.0
+    for s in range(0, n.shape[0], 512):
+        nn = n[s:s + 512]
+        F = np.exp(-1j * k * (nn @ r.T)) @ P                    # (c, 3)
+        F = F - nn * np.sum(nn * F, axis=1, keepdims=True)
+        total += float(np.sum(wt[s:s + 512] * np.sum(np.abs(F) ** 2, axis=1)))
+    return k ** 4 * total
+
+
+# ----------------------------------------------------------------- adjoint --
+def qabs_gradient(kd: float, aeff: float, eps_site: np.ndarray, khat, ehat,
+                  P: np.ndarray, nu: np.ndarray):
+    """dQ_abs/dRe(eps_j), dQ_abs/dIm(eps_j), treating each dipole's eps as
+    independent (no counterpart in the guide; derived from the cross-section
+    and polarizability forms above).
+
+    With Q_abs = K sum_j w_j |P_j|^2, w_j = -Im beta_j - (2/3) k^3,
+    K = 4 k / a_eff^2, beta' = d beta/d eps, and nu solving A nu = W P^*
+    (A = A^T):
+      dQ/dRe eps_j = K [ -|P_j|^2 Im beta'_j - 2 Re(beta'_j nu_j.P_j) ]
+      dQ/dIm eps_j = K [ -|P_j|^2 Re beta'_j + 2 Im(beta'_j nu_j.P_j) ]
+    Pinned by central finite differences of dense solves.
+    """
+    K = 4.0 * kd / aeff ** 2
+    bp = ldr_inverse_polarizability_derivative(eps_site, kd, khat, ehat)
+    p2 = np.sum(np.abs(P) ** 2, axis=1)
+    nup = np.sum(nu * P, axis=1)
+    g_re = K * (-p2 * bp.imag - 2.0 * (bp * nup).real)
+    g_im = K * (-p2 * bp.real + 2.0 * (bp * nup).imag)
+    return g_re, g_im
+
+
+def absorption_weights(kd: float, beta: np.ndarray) -> np.ndarray:
+    """w_j = -Im(1/alpha_j) - (2/3) k^3, so that C_abs = 4 pi k sum_j w_j |P_j|^2."""
+    return -np.imag(beta) - (2.0 / 3.0) * kd ** 3

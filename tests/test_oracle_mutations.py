@@ -1,0 +1,111 @@
+"""Planted mistakes in the CPU oracle must each fail at least one pin.
+
+Every mutation is applied with monkeypatch to the oracle only (CPU); the
+pins are the functions of tests/test_oracle_pins.py.  A mutation that no pin
+catches would mean that part of the oracle is not pinned.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dda, mie
+import test_oracle_pins as pins
+
+_orig_tensor = dda.interaction_tensor
+_orig_ldr = dda.ldr_inverse_polarizability
+_orig_xs = dda.cross_sections
+_orig_einc = dda.incident_field
+_orig_j = dda._sph_j012
+_orig_grad = dda.qabs_gradient
+_orig_sites = dda.site_positions
+
+
+def _tensor_sign(rvec, kd):            # (1 - ik rho) instead of (ik rho - 1)
+    rvec = np.asarray(rvec, float)
+    rho = np.linalg.norm(rvec, axis=-1)
+    rh = rvec / rho[..., None]
+    rr = rh[..., :, None] * rh[..., None, :]
+    ph = np.exp(1j * kd * rho) / rho
+    c2 = (1.0 - 1j * kd * rho) / rho ** 2
+    return ph[..., None, None] * (kd * kd * (rr - np.eye(3)) + c2[..., None, None] * (3 * rr - np.eye(3)))
+
+
+def _tensor_no_far(rvec, kd):          # dropped k^2 (rr - I) radiation term
+    rvec = np.asarray(rvec, float)
+    rho = np.linalg.norm(rvec, axis=-1)
+    rh = rvec / rho[..., None]
+    rr = rh[..., :, None] * rh[..., None, :]
+    ph = np.exp(1j * kd * rho) / rho
+    c2 = (1j * kd * rho - 1.0) / rho ** 2
+    return ph[..., None, None] * (c2[..., None, None] * (3 * rr - np.eye(3)))
+
+
+def _tensor_incoming(rvec, kd):        # exp(-ik rho): incoming instead of outgoing wave
+    return np.conj(_orig_tensor(rvec, kd))
+
+
+def _ldr_no_rr(eps, kd, khat, ehat):   # dropped radiative reaction
+    return _orig_ldr(eps, kd, khat, ehat) + (2.0 / 3.0) * 1j * kd ** 3
+
+
+def _xs_no_conj(kd, E, P, beta):       # Im(E . P) instead of Im(E^* . P)
+    c = list(_orig_xs(kd, np.conj(E), P, beta))
+    return c[0], c[1], c[0] - c[1]
+
+
+def _xs_rr_sign(kd, E, P, beta):       # +(2/3)k^3 in C_abs
+    cext, cabs, _ = _orig_xs(kd, E, P, beta)
+    cabs += 4 * math.pi * kd * (4.0 / 3.0) * kd ** 3 * float(np.sum(np.abs(P) ** 2))
+    return cext, cabs, cext - cabs
+
+
+def _einc_backward(r, kd, khat, ehat):  # wave travelling along -khat
+    return _orig_einc(r, kd, -np.asarray(khat, float), ehat)
+
+
+def _j_sign(u):                         # wrong sign of the j2 Rhat Rhat term
+    j0, j1, j2 = _orig_j(u)
+    return j0, j1, -j2
+
+
+def _grad_sign(kd, aeff, eps, khat, ehat, P, nu):   # dropped factor 2 on the adjoint term
+    return _orig_grad(kd, aeff, eps, khat, ehat, P, 0.5 * nu)
+
+
+def _sites_zyx(grid):                   # x and z swapped in the site positions
+    r, c = _orig_sites(grid)
+    return r[:, ::-1].copy(), c
+
+
+MUTATIONS = [
+    ("interaction_tensor", _tensor_sign, [pins.two_dipole_error]),
+    ("interaction_tensor", _tensor_no_far, [pins.two_dipole_error]),
+    ("interaction_tensor", _tensor_incoming, [pins.two_dipole_error, pins.energy_balance_error]),
+    ("ldr_inverse_polarizability", _ldr_no_rr, [pins.lossless_cabs]),
+    ("cross_sections", _xs_no_conj, [pins.energy_balance_error, pins.forward_amplitude_error]),
+    ("cross_sections", _xs_rr_sign, [pins.single_dipole_errors, pins.lossless_cabs]),
+    ("incident_field", _einc_backward, [pins.forward_amplitude_error]),
+    ("_sph_j012", _j_sign, [pins.pair_sum_vs_quadrature_error]),
+    ("qabs_gradient", _grad_sign, [pins.adjoint_gradient_error]),
+    ("site_positions", _sites_zyx, [pins.site_axes_error]),
+]
+
+
+@pytest.mark.parametrize("name,fn,checks", MUTATIONS, ids=[f"{m[0]}:{m[1].__name__}" for m in MUTATIONS])
+def test_planted_mistake_is_caught(monkeypatch, name, fn, checks):
+    monkeypatch.setattr(dda, name, fn)
+    worst = max(check() for check in checks)
+    assert worst > 1e-6, f"mutation {fn.__name__} of {name} not caught (error {worst})"
+
+
+def test_mie_planted_mistake_is_caught(monkeypatch, golden_dir):
+    """A wrong refractive index reaching the coefficients fails the textbook example."""
+    src = mie.mie_efficiencies
+
+    def wrong(x, m):
+        return src(x, complex(m).conjugate() * 1.1)
+
+    monkeypatch.setattr(mie, "mie_efficiencies", wrong)
+    with pytest.raises(AssertionError):
+        pins.test_mie_textbook_example(golden_dir)

@@ -1,0 +1,375 @@
+"""Pins of the CPU oracle against facts outside itself (no GPU).
+
+Each check is a plain function returning an error measure so that
+tests/test_oracle_mutations.py can plant mistakes in the oracle and show that
+some pin catches each of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from dda_inputs import (block_bernoulli_grid, ellipsoid_grid, random_complex, sphere_grid,
+                        uniform_directions, polarization_pair, workload)
+from oracle import dda, mie, pairwise
+
+
+# ----------------------------------------------------------------- helpers --
+def _golden_rows(path):
+    rows = []
+    with open(path) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                rows.append(line.split())
+    return rows
+
+
+def jackson_dipole_field(rvec, p, k):
+    """Field of an oscillating point dipole p at displacement rvec (Jackson,
+    Classical Electrodynamics, 3rd ed., eq. 9.18), Gaussian units."""
+    r = np.linalg.norm(rvec)
+    n = rvec / r
+    far = k * k * np.cross(np.cross(n, p), n) / r
+    near = (3 * n * np.dot(n, p) - p) * (1 / r ** 3 - 1j * k / r ** 2)
+    return np.exp(1j * k * r) * (far + near)
+
+
+def two_dipole_error(kd=0.37, eps=2.1 + 0.4j, d=(1.0, 2.0, -1.0)):
+    """Dense oracle matrix vs the matrix assembled from Jackson's dipole field."""
+    r = np.array([[0.0, 0.0, 0.0], list(d)])
+    beta = dda.ldr_inverse_polarizability(np.full(2, eps), kd, [0, 0, 1], [1, 0, 0])
+    A = dda.dense_matrix(r, kd, beta)
+    M = np.zeros((6, 6), dtype=np.complex128)
+    for j in range(2):
+        M[3 * j:3 * j + 3, 3 * j:3 * j + 3] = beta[j] * np.eye(3)
+        l = 1 - j
+        for b in range(3):
+            e = np.zeros(3)
+            e[b] = 1.0
+            M[3 * j:3 * j + 3, 3 * l + b] = -jackson_dipole_field(r[j] - r[l], e, kd)
+    return float(np.abs(A - M).max() / np.abs(M).max())
+
+
+def single_dipole_errors(kd=0.45, eps=3.0 + 1.2j, khat=(0.6, 0.8, 0.0), ehat=(0.0, 0.0, 1.0)):
+    """N = 1: P = alpha E_inc and the textbook single-dipole cross sections."""
+    r = np.zeros((1, 3))
+    beta = dda.ldr_inverse_polarizability(np.array([eps]), kd, khat, ehat)
+    E = dda.incident_field(r, kd, khat, ehat)
+    A = dda.dense_matrix(r, kd, beta)
+    P = dda.solve_dense(A, E)
+    alpha = 1.0 / beta[0]
+    k = kd
+    cext, cabs, csca = dda.cross_sections(kd, E, P, beta)
+    want_ext = 4 * math.pi * k * alpha.imag
+    want_abs = 4 * math.pi * k * (alpha.imag - (2.0 / 3.0) * k ** 3 * abs(alpha) ** 2)
+    want_sca = (8 * math.pi / 3) * k ** 4 * abs(alpha) ** 2
+    csca_pair = dda.csca_pair_sum(r, kd, P)
+    return max(abs(cext - want_ext) / abs(want_ext), abs(cabs - want_abs) / abs(want_abs),
+               abs(csca - want_sca) / want_sca, abs(csca_pair - want_sca) / want_sca)
+
+
+def _small_cluster(seed=3, n=40):
+    grid = ellipsoid_grid(7, 6, 5, 7, 6, 5)
+    r, _ = dda.site_positions(grid)
+    rng = np.random.default_rng(seed)
+    return r[rng.permutation(len(r))[:n]]
+
+
+def energy_balance_error(eps=2.5 + 0.8j, kd=0.6, S_dir=(0.0, 0.6, 0.8)):
+    """Converged dense solve: C_ext - C_abs equals the independently integrated
+    C_sca (pair sum) -- the optical theorem for the dipole array."""
+    r = _small_cluster()
+    khat = np.array(S_dir)
+    ehat = np.array([1.0, 0.0, 0.0], dtype=complex)
+    beta = dda.ldr_inverse_polarizability(np.full(len(r), eps), kd, khat, ehat)
+    E = dda.incident_field(r, kd, khat, ehat)
+    P = dda.solve_dense(dda.dense_matrix(r, kd, beta), E)
+    cext, cabs, _ = dda.cross_sections(kd, E, P, beta)
+    csca = dda.csca_pair_sum(r, kd, P)
+    return abs(cext - cabs - csca) / abs(cext)
+
+
+def pair_sum_vs_quadrature_error(kd=0.9, seed=5):
+    r = _small_cluster(seed, 30)
+    P = random_complex((len(r), 3), seed)
+    a = dda.csca_pair_sum(r, kd, P)
+    b = dda.csca_quadrature(r, kd, P, ntheta=96, nphi=192)
+    return abs(a - b) / abs(b)
+
+
+def lossless_cabs(kd=0.5, eps=2.25):
+    """Real eps: C_abs vanishes for any P (radiative reaction exactly cancels)."""
+    r = _small_cluster(7, 25)
+    beta = dda.ldr_inverse_polarizability(np.full(len(r), eps + 0j), kd, [1, 0, 0], [0, 1, 0])
+    P = random_complex((len(r), 3), 11)
+    E = dda.incident_field(r, kd, [1, 0, 0], [0, 1, 0])
+    cext, cabs, _ = dda.cross_sections(kd, E, P, beta)
+    return abs(cabs) / (4 * math.pi * kd * np.sum(np.abs(P) ** 2) * kd ** 3)
+
+
+def symmetry_error():
+    r = _small_cluster(9, 35)
+    kd = 0.4
+    beta = dda.ldr_inverse_polarizability(np.full(len(r), 1.7 + 0.2j), kd, [1, 0, 0], [0, 1, 0])
+    A = dda.dense_matrix(r, kd, beta)
+    return float(np.abs(A - A.T).max() / np.abs(A).max())
+
+
+# ------------------------------------------------------------------- tests --
+def test_pseudosphere_counts_match_guide(golden_dir):
+    for box, diam, count, *_ in _golden_rows(os.path.join(golden_dir, "pseudosphere_counts.txt")):
+        assert int(np.count_nonzero(sphere_grid(int(box), float(diam)))) == int(count)
+
+
+def test_workload_dipole_counts():
+    # c1..c4 of the synthetic workloads (|r| <= n/2 spheres, 3:2:1 ellipsoid, full block)
+    want = {"sphere16": 2176, "sphere64": 137376, "ellipsoid96x64x32": 102984, "block48x48x24": 55296}
+    for name, n in want.items():
+        assert workload(name).ndipoles == n
+
+
+def test_two_dipole_matrix_matches_textbook_field():
+    assert two_dipole_error() < 1e-13
+    assert two_dipole_error(kd=1.3, d=(0.0, 0.0, 1.0)) < 1e-13
+
+
+def test_single_dipole_closed_forms():
+    assert single_dipole_errors() < 1e-12
+    assert single_dipole_errors(kd=0.05, eps=1.77 + 0.02j, khat=(1, 0, 0), ehat=(0, 1, 0)) < 1e-10
+
+
+def test_matrix_is_complex_symmetric():
+    assert symmetry_error() < 1e-14
+
+
+def test_lossless_target_absorbs_nothing():
+    assert lossless_cabs() < 1e-12
+
+
+def test_pair_sum_csca_matches_angular_quadrature():
+    assert pair_sum_vs_quadrature_error() < 1e-10
+
+
+def test_energy_balance_of_converged_solution():
+    assert energy_balance_error() < 1e-11
+
+
+def test_sph_bessel_series_matches_closed_forms():
+    # series branch (u < 1) against the closed forms at arguments where they do not cancel
+    u = np.array([0.6, 0.8, 0.999])
+    j0, j1, j2 = dda._sph_j012(u)
+    s, c = np.sin(u), np.cos(u)
+    assert np.allclose(j0, s / u, rtol=1e-14, atol=0)
+    assert np.allclose(j1, s / u ** 2 - c / u, rtol=1e-13, atol=0)
+    assert np.allclose(j2, (3 / u ** 3 - 1 / u) * s - 3 * c / u ** 2, rtol=1e-12, atol=0)
+    # recurrence j2 = 3 j1/u - j0 at small argument, where the closed form cancels
+    u = np.array([0.05, 0.3, 0.9])
+    j0, j1, j2 = dda._sph_j012(u)
+    assert np.allclose(j2, 3 * j1 / u - j0, rtol=1e-9, atol=0)
+
+
+def test_pairwise_c_matches_dense():
+    r = _small_cluster(2, 60)
+    kd = 0.8
+    beta = dda.ldr_inverse_polarizability(np.full(len(r), 2 + 1j), kd, [0, 1, 0], [0, 0, 1])
+    P = random_complex((len(r), 3), 4)
+    want = (dda.dense_matrix(r, kd, beta) @ P.ravel()).reshape(-1, 3)
+    got, _ = pairwise.matvec(r, kd, beta, P)
+    assert np.abs(got - want).max() < 1e-12 * np.abs(want).max()
+    rows = np.array([0, 17, 59, 3])
+    got_r, _ = pairwise.matvec(r, kd, beta, P, rows=rows)
+    assert np.abs(got_r - want[rows]).max() < 1e-12 * np.abs(want).max()
+    assert np.abs(dda.pairwise_matvec(r, kd, beta, P) - want).max() < 1e-12 * np.abs(want).max()
+
+
+def test_bicgstab_reaches_dense_solution():
+    r, _ = dda.site_positions(sphere_grid(8))
+    kd = 0.35
+    khat, ehat = [0.0, 0.0, 1.0], [1.0, 0.0, 0.0]
+    beta = dda.ldr_inverse_polarizability(np.full(len(r), (1.5 + 0.1j) ** 2), kd, khat, ehat)
+    E = dda.incident_field(r, kd, khat, ehat)
+    A = dda.dense_matrix(r, kd, beta)
+    Pd = dda.solve_dense(A, E)
+    x, it, nmv, rel = dda.bicgstab(lambda v: A @ v, E.ravel(), 1e-13, 300)
+    assert rel <= 1e-13
+    assert np.abs(x - Pd.ravel()).max() < 1e-11 * np.abs(Pd).max()
+    assert dda.normal_equation_error(lambda v: A @ v, x, E) < 1e-11
+
+
+def test_ldr_reduces_to_clausius_mossotti_at_zero_frequency():
+    eps = np.array([2.0 + 0.5j, 5.0 + 1.0j])
+    b = dda.ldr_inverse_polarizability(eps, 0.0, [1, 0, 0], [0, 1, 0])
+    assert np.allclose(1.0 / b, (3 / (4 * math.pi)) * (eps - 1) / (eps + 2), rtol=1e-15)
+
+
+def test_ldr_derivative_matches_finite_difference():
+    eps, kd, k, e = 2.2 + 0.7j, 0.3, [0.6, 0.0, 0.8], [0.0, 1.0, 0.0]
+    h = 1e-6
+    fd = (dda.ldr_inverse_polarizability(eps + h, kd, k, e) - dda.ldr_inverse_polarizability(eps - h, kd, k, e)) / (2 * h)
+    assert abs(fd - dda.ldr_inverse_polarizability_derivative(eps, kd, k, e)) < 1e-7 * abs(fd)
+
+
+def test_mie_textbook_example(golden_dir):
+    for rad, wav, mre, mim, qsca, qext in _golden_rows(os.path.join(golden_dir, "mie_bohren_huffman.txt")):
+        x = 2 * math.pi * float(rad) / float(wav)
+        qe, qa, qs = mie.mie_efficiencies(x, complex(float(mre), float(mim)))
+        assert abs(qs - float(qsca)) < 6e-6 and abs(qe - float(qext)) < 6e-6
+
+
+def test_mie_limits():
+    # Rayleigh limit: Q_abs -> 4x Im[(eps-1)/(eps+2)], Q_sca -> (8/3) x^4 |(eps-1)/(eps+2)|^2
+    m = 1.5 + 0.1j
+    x = 1e-3
+    a = (m * m - 1) / (m * m + 2)
+    qe, qa, qs = mie.mie_efficiencies(x, m)
+    assert abs(qa - 4 * x * a.imag) < 1e-4 * qa
+    assert abs(qs - (8 / 3) * x ** 4 * abs(a) ** 2) < 1e-4 * qs
+    # lossless sphere absorbs nothing; large sphere extinction -> 2
+    assert abs(mie.mie_efficiencies(3.0, 1.4)[1]) < 1e-12
+    assert abs(mie.mie_efficiencies(2000.0, 1.33 + 0.01j)[0] - 2.0) < 0.02
+
+
+def _oracle_sphere_q(n, x, m, tol=1e-9):
+    r, _ = dda.site_positions(sphere_grid(n))
+    N = len(r)
+    aeff = dda.aeff_lattice(N)
+    kd = x / aeff
+    khat, ehat = [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]
+    beta = dda.ldr_inverse_polarizability(np.full(N, m * m), kd, khat, ehat)
+    E = dda.incident_field(r, kd, khat, ehat)
+    mv = lambda v: pairwise.matvec(r, kd, beta, v.reshape(-1, 3))[0].ravel()  # noqa: E731
+    P, it, nmv, rel = dda.bicgstab(mv, E.ravel(), tol, 500)
+    return dda.efficiencies(dda.cross_sections(kd, E, P.reshape(-1, 3), beta), aeff)
+
+
+def test_dda_converges_to_mie_with_dipole_count():
+    # "few percent" accuracy for |m|kd < 1 ("Applicability of the DDA"); error falls with N
+    m, x = 1.33 + 0.01j, 1.0
+    qm = mie.mie_efficiencies(x, m)
+    errs = [abs(_oracle_sphere_q(n, x, m)[0] - qm[0]) / qm[0] for n in (6, 8, 10, 12, 16)]
+    assert max(errs) < 0.03
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+
+
+def test_dda_rayleigh_limit():
+    m, x = 1.33 + 0.05j, 0.05
+    qe, qa, qs = _oracle_sphere_q(12, x, m, tol=1e-10)
+    a = (m * m - 1) / (m * m + 2)
+    assert abs(qa - 4 * x * a.imag) < 0.03 * qa
+    assert abs(qs - (8 / 3) * x ** 4 * abs(a) ** 2) < 0.05 * qs
+
+
+def test_sphere_two_polarizations_agree():
+    r, _ = dda.site_positions(sphere_grid(8))
+    kd = 0.4
+    out = []
+    for ehat in ([0.0, 1.0, 0.0], [0.0, 0.0, 1.0]):
+        beta = dda.ldr_inverse_polarizability(np.full(len(r), 1.7 + 0.1j), kd, [1, 0, 0], ehat)
+        E = dda.incident_field(r, kd, [1, 0, 0], ehat)
+        P = dda.solve_dense(dda.dense_matrix(r, kd, beta), E)
+        out.append(dda.cross_sections(kd, E, P, beta))
+    assert np.allclose(out[0], out[1], rtol=1e-12)
+
+
+def test_translation_changes_only_phase():
+    r, _ = dda.site_positions(ellipsoid_grid(6, 5, 4, 6, 5, 4))
+    kd = 0.5
+    k, e = np.array([0.0, 0.6, 0.8]), np.array([1.0, 0.0, 0.0], complex)
+    beta = dda.ldr_inverse_polarizability(np.full(len(r), 2 + 0.3j), kd, k, e)
+    A = dda.dense_matrix(r, kd, beta)
+    E0 = dda.incident_field(r, kd, k, e)
+    E1 = dda.incident_field(r + np.array([3.0, -1.0, 2.0]), kd, k, e)
+    q0 = dda.cross_sections(kd, E0, dda.solve_dense(A, E0), beta)
+    q1 = dda.cross_sections(kd, E1, dda.solve_dense(A, E1), beta)
+    assert np.allclose(q0, q1, rtol=1e-12)
+
+
+def _grad_setup(seed=20120514):
+    grid = block_bernoulli_grid(3, 3, 2, seed=seed)
+    r, comp = dda.site_positions(grid)
+    eps = np.where(comp == 1, (1.7 + 0.3j) ** 2, (1.2 + 0.01j) ** 2)
+    N = len(r)
+    aeff = dda.aeff_lattice(N)
+    kd = 1.5 / aeff
+    khat, ehat = np.array([1.0, 0, 0]), np.array([0, 1.0, 0], complex)
+    return r, eps, aeff, kd, khat, ehat
+
+
+def _qabs(r, eps, aeff, kd, khat, ehat):
+    beta = dda.ldr_inverse_polarizability(eps, kd, khat, ehat)
+    E = dda.incident_field(r, kd, khat, ehat)
+    P = dda.solve_dense(dda.dense_matrix(r, kd, beta), E)
+    return dda.efficiencies(dda.cross_sections(kd, E, P, beta), aeff)[1], P, beta
+
+
+def adjoint_gradient_error():
+    r, eps, aeff, kd, khat, ehat = _grad_setup()
+    q, P, beta = _qabs(r, eps, aeff, kd, khat, ehat)
+    w = dda.absorption_weights(kd, beta)
+    nu = dda.solve_dense(dda.dense_matrix(r, kd, beta), w[:, None] * np.conj(P))
+    g_re, g_im = dda.qabs_gradient(kd, aeff, eps, khat, ehat, P, nu)
+    err = 0.0
+    for j in range(len(r)):
+        for comp, g in ((1.0, g_re[j]), (1j, g_im[j])):
+            h = 1e-5 * abs(eps[j])
+            ep = eps.copy()
+            em = eps.copy()
+            ep[j] += comp * h
+            em[j] -= comp * h
+            fd = (_qabs(r, ep, aeff, kd, khat, ehat)[0] - _qabs(r, em, aeff, kd, khat, ehat)[0]) / (2 * h)
+            err = max(err, abs(fd - g) / (abs(fd) + 1e-3 * q))
+    return err
+
+
+def test_adjoint_gradient_matches_finite_differences():
+    assert adjoint_gradient_error() < 1e-6
+
+
+@pytest.mark.slow
+def test_uniform_directions_polarizations_orthonormal():
+    k = uniform_directions(64)
+    e1, e2 = polarization_pair(k)
+    for v in (k, e1, e2):
+        assert np.allclose(np.linalg.norm(v, axis=1), 1.0)
+    assert np.allclose(np.sum(k * e1, 1), 0) and np.allclose(np.sum(k * e2, 1), 0)
+    assert np.allclose(np.sum(e1 * e2, 1), 0)
+
+
+def forward_amplitude_error():
+    """Optical theorem written with the forward far-field amplitude:
+    C_ext = (4 pi / k) Im(e^* . F(khat)),  F(n) = k^2 sum_j (I - nn) P_j exp(-ik n.r_j),
+    with outgoing waves exp(+ikr).  Fixes the sign of the incident phase: a
+    wave travelling along -khat would match F(-khat) instead.  Asymmetric
+    cluster so that F(khat) != F(-khat)."""
+    r = _small_cluster(13, 30)
+    kd = 0.7
+    khat = np.array([0.0, 0.6, 0.8])
+    ehat = np.array([1.0, 0.0, 0.0], complex)
+    beta = dda.ldr_inverse_polarizability(np.full(len(r), 2.4 + 0.6j), kd, khat, ehat)
+    E = dda.incident_field(r, kd, khat, ehat)
+    P = dda.solve_dense(dda.dense_matrix(r, kd, beta), E)
+    F = kd ** 2 * (np.exp(-1j * kd * (r @ khat)) @ P)
+    F = F - khat * np.dot(khat, F)
+    want = 4 * math.pi / kd * np.imag(np.dot(np.conj(ehat), F))
+    cext = dda.cross_sections(kd, E, P, beta)[0]
+    return abs(cext - want) / abs(want)
+
+
+def test_forward_amplitude_optical_theorem():
+    assert forward_amplitude_error() < 1e-12
+
+
+def site_axes_error():
+    """Sites of the 96x64x32 3:2:1 ellipsoid lie inside the ELLIPSOID surface with
+    the long axis along x (SHPAR_1 along x_TF) and fill it up to the box."""
+    grid = ellipsoid_grid(96, 64, 32, 96, 64, 32)
+    r, _ = dda.site_positions(grid)
+    lhs = (r[:, 0] / 96) ** 2 + (r[:, 1] / 64) ** 2 + (r[:, 2] / 32) ** 2
+    span = r.max(0) - r.min(0)
+    return max(0.0, float(lhs.max() - 0.25)) + float(np.abs(span - [95, 63, 31]).max())
+
+
+def test_site_positions_follow_target_axes():
+    assert site_axes_error() == 0.0

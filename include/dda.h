@@ -1,0 +1,166 @@
+/*
+ * dda.h -- C ABI of the GB300 discrete-dipole-approximation (DDA) hot path.
+ *
+ * What it computes.  The DDSCAT 7.2 user guide (Draine & Flatau 2012) states
+ * the scattering problem as the linear system  A P = E  (section "Choice of
+ * Iterative Algorithm", eq. AP=E): E holds the incident field at the N
+ * occupied lattice sites, P the unknown dipole moments, A is the 3N x 3N
+ * complex-symmetric interaction matrix.  This library evaluates A.P as a
+ * zero-padded 3-D FFT convolution (Goodman, Draine & Flatau 1990, the FFT
+ * method the guide cites), solves A P = E with BiCGstab (the guide's
+ * recommended solvers are BiCGstab variants, "Choice of Iterative
+ * Algorithm") to the residual tolerance TOL (eq. err_tol and the TOL entry of
+ * ddscat.par), and reduces P to the efficiency factors Q_ext, Q_abs, Q_sca
+ * (section "What Does DDSCAT Calculate?").  Readings taken where the guide
+ * is silent (LATTDR polarizability of Draine & Goodman 1993, Draine 1988
+ * interaction tensor and cross sections):
+ *   1/alpha = (4pi/3)(eps+2)/(eps-1) + (b1 + b2 eps + b3 eps S)(kd)^2 - (2/3) i (kd)^3,
+ *   b1 = -1.8915316, b2 = 0.1648469, b3 = -1.7700004, S = sum_a (khat_a e_a)^2,
+ *   A_jl = e^{ik rho}/rho [k^2 (rr - I) + (ik rho - 1)/rho^2 (3 rr - I)]  (j != l),
+ *   A_jj = (1/alpha_j) I,
+ *   C_ext = 4 pi k sum Im(E_inc^* . P),  C_abs = 4 pi k sum (-Im(1/alpha) - 2k^3/3)|P|^2,
+ *   C_sca = C_ext - C_abs,  Q = C / (pi a_eff^2),  a_eff = (3N/4pi)^(1/3) d.
+ *
+ * Conventions.
+ *  - Lattice units inside: dipole spacing d = 1; |E0| = 1; Gaussian units.
+ *  - Target grid: uint8 composition code per lattice site, 0 = vacuum,
+ *    1..ncomp = material, row-major with x fastest: comp[(iz*ny + iy)*nx + ix].
+ *  - Site order: the N occupied sites in that same scan order.  Site j at
+ *    r_j = (ix-(nx-1)/2, iy-(ny-1)/2, iz-(nz-1)/2): the Target Frame origin is
+ *    the centre of the computational volume (also the incident phase origin).
+ *  - Vectors (E, P, x, y): [R][3][N] complex numbers, each stored as two
+ *    doubles (re, im) on the host API; R right-hand sides, component-major
+ *    (all x components of RHS 0, then its y components, ...).
+ *  - Directions khat: [R][3] real unit vectors in the Target Frame.
+ *    Polarizations e: [R][3] complex (re, im pairs, 6 doubles per RHS),
+ *    normalized, transverse to khat.
+ *  - Ownership: the caller owns every host buffer it passes (read during the
+ *    call only; never retained).  The context owns all device memory it
+ *    allocates.  Device-pointer variants (suffix _device) read/write
+ *    caller-owned device buffers and run on the context's stream.
+ *  - Errors: every call returns a dda_status; on failure the message is
+ *    available from dda_last_error(ctx) and no output buffer is written,
+ *    except that dda_solve fills res[] (status per RHS) when it returns
+ *    DDA_ERR_NOT_CONVERGED or DDA_ERR_BREAKDOWN.
+ *  - Threads: a context is used by one host thread at a time.
+ */
+#ifndef DDA_GB300_H
+#define DDA_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dda_ctx dda_ctx;
+
+typedef enum {
+    DDA_OK = 0,
+    DDA_ERR_ARG = 1,            /* invalid argument or call order                          */
+    DDA_ERR_CUDA = 2,           /* CUDA runtime error (message has the CUDA error string)  */
+    DDA_ERR_OOM = 3,            /* device allocation failed                                */
+    DDA_ERR_SIZE = 4,           /* lattice too large for the supported FFT lengths         */
+    DDA_ERR_NOT_CONVERGED = 5,  /* some RHS did not reach tol within maxit                 */
+    DDA_ERR_BREAKDOWN = 6,      /* BiCGstab breakdown (rho or <rhat,v> exactly zero)        */
+    DDA_ERR_NONFINITE = 7       /* NaN/Inf in an input or in the iteration                 */
+} dda_status;
+
+typedef enum {
+    DDA_FP64 = 0,         /* complex128 matvec and vectors, FP64 scalars                     */
+    DDA_FP32_REFINED = 1, /* complex64 matvec in an FP64 iterative-refinement loop           */
+    DDA_FP32 = 2          /* complex64 matvec and vectors, FP64 scalars (no refinement)      */
+} dda_precision;
+
+typedef struct {
+    double tol;        /* relative residual |E - A P| / |E| to reach (guide: TOL = 1e-5)     */
+    int maxit;         /* max BiCGstab iterations per RHS, summed over refinement steps     */
+    int use_graph;     /* 1: replay the iteration block as a captured CUDA graph            */
+    double inner_tol;  /* FP32_REFINED: floor of the inner (FP32) relative tolerance        */
+    int max_outer;     /* max refinement (outer) steps; <= 0 selects 8                       */
+    int normal_eq;     /* 1: also report |A^H A P - A^H E| / |A^H E| (eq. err_tol)          */
+    const double* x0;  /* nullable initial guess, [R][3][N] complex (warm start / resume)    */
+} dda_opts;
+
+typedef struct {
+    double qext, qabs, qsca;  /* efficiency factors                                         */
+    double resid_rel;         /* true relative residual |E - A P|/|E|, FP64 matvec           */
+    double resid_normal_eq;   /* eq. err_tol form, or -1 if not requested                    */
+    int iters;                /* BiCGstab iterations (2 matvecs each), all refinement steps */
+    int outer_iters;          /* refinement steps (1 for a converged plain solve)           */
+    int matvecs;              /* A.x products applied to this RHS, all precisions           */
+    dda_status status;        /* DDA_OK, DDA_ERR_NOT_CONVERGED, DDA_ERR_BREAKDOWN, ...      */
+} dda_result;
+
+typedef struct {
+    int nx, ny, nz;        /* lattice                                                   */
+    int Lx, Ly, Lz;        /* padded FFT lengths (>= 2n, 2^a 3^b)                       */
+    int64_t ndipoles;      /* N occupied sites                                          */
+    int ncomp;             /* compositions                                               */
+    double aeff_lattice;   /* a_eff / d = (3N/4pi)^(1/3)                                 */
+    double kd;             /* k d of the prepared wavelength (0 before dda_prepare)      */
+    double x;              /* size parameter k a_eff                                     */
+} dda_info;
+
+/* Create a context on CUDA device `device`; allocates a stream.  */
+dda_status dda_create(int device, dda_ctx** out);
+/* Free all device memory, graphs and the stream owned by ctx. NULL is a no-op. */
+dda_status dda_destroy(dda_ctx* ctx);
+/* Message of the last failed call on ctx (owned by ctx, valid until the next call). */
+const char* dda_last_error(const dda_ctx* ctx);
+/* Run subsequent work on a caller stream (cudaStream_t passed as void*); NULL restores the ctx stream. */
+dda_status dda_set_stream(dda_ctx* ctx, void* stream);
+
+/* Target (guide: "Target Generation"; shape arrays IXYZ/ICOMP): nx*ny*nz
+ * composition codes, copied in.  Invalidates any prepared wavelength.
+ * DDA_ERR_ARG if no site is occupied or a code exceeds 255; DDA_ERR_SIZE if
+ * some 2n exceeds the largest supported FFT length (512).                     */
+dda_status dda_set_target(dda_ctx* ctx, int nx, int ny, int nz, const uint8_t* comp);
+/* Materials (guide: "Dielectric Functions", ambient medium "Target in a
+ * medium"): complex refractive index per composition (2*ncomp doubles) and the
+ * real refractive index of the ambient medium.  Relative index m/m_ambient is
+ * used.  DDA_ERR_ARG if ncomp < max code in the grid or m_ambient <= 0.        */
+dda_status dda_set_materials(dda_ctx* ctx, int ncomp, const double* m_complex, double m_ambient);
+/* Wavelength and size (guide: WAVINI / AEFFINI, same physical units): sets
+ * d = aeff/(3N/4pi)^(1/3), k = 2 pi m_ambient / lambda_vac, and builds the
+ * transformed Green tensor for `precision` (FP64 tensor always; FP32 copy for
+ * the FP32 modes).                                                             */
+dda_status dda_prepare(dda_ctx* ctx, double lambda_vac, double aeff, dda_precision precision);
+dda_status dda_get_info(const dda_ctx* ctx, dda_info* info);
+
+/* Solve A P = E for R incident plane waves (direction khat[3R], polarization
+ * e[6R]) and reduce Q.  P_out (nullable): [R][3][N] complex, caller-owned.
+ * res: R entries.  Returns DDA_OK when every RHS converged, else the worst
+ * per-RHS status.  precision must have been prepared (FP64 is always).       */
+dda_status dda_solve(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* e,
+                     const dda_opts* opts, double* P_out, dda_result* res);
+/* Same, P written to a caller device buffer of R*3*N double2 (complex128).  */
+dda_status dda_solve_device(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* e,
+                            const dda_opts* opts, void* P_dev, dda_result* res);
+
+/* One product y = A x for R RHS (A's diagonal depends on each RHS through S).
+ * x, y: host [R][3][N] complex.  precision DDA_FP64 or DDA_FP32 (x rounded to
+ * complex64, result widened back).  For testing and timing.                   */
+dda_status dda_matvec(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* e,
+                      const double* x, double* y);
+/* Device variant: x, y device buffers of R*3*N complex elements of the
+ * precision's type (double2 for DDA_FP64, float2 for DDA_FP32).               */
+dda_status dda_matvec_device(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* e,
+                             const void* x_dev, void* y_dev);
+
+/* Incident field E_inc,j = e exp(i k khat.r_j) at every site, [R][3][N] complex (host). */
+dda_status dda_incident_field(dda_ctx* ctx, int R, const double* khat, const double* e, double* E_out);
+
+/* dQ_abs/dRe(eps_j) and dQ_abs/dIm(eps_j) for every dipole (each dipole's eps
+ * treated as independent; forward values from the composition table), by an
+ * adjoint solve A nu = W P^* that reuses the matvec because A = A^T.  One RHS.
+ * The guide has no gradients; this is the project's differentiation pattern.
+ * res[0] forward solve, res[1] adjoint solve.  P_out (nullable) [3][N].        */
+dda_status dda_grad_qabs(dda_ctx* ctx, dda_precision precision, const double* khat, const double* e,
+                         const dda_opts* opts, double* dq_dre_eps, double* dq_dim_eps, double* P_out,
+                         dda_result* res);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDA_GB300_H */

@@ -1,0 +1,315 @@
+"""Python binding of the GB300 DDA library (include/dda.h).
+
+Thin ctypes marshalling over the C ABI: every step of the hot path runs in
+the CUDA library ``libdda_gb300.so`` built in-tree by ``build.py``.  There is
+no CPU fallback: if the library is missing or no GPU is present, the calls
+raise.  Functions carry the names of the C entry points; :class:`Context`
+bundles them for convenience.
+
+Array conventions (see include/dda.h): composition grids are uint8
+``[nz, ny, nx]``; vectors are complex128 ``[R, 3, N]`` with sites in the
+grid's row-major scan order; ``khat`` is float ``[R, 3]``; ``e`` is complex
+``[R, 3]``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "DdaError", "Precision", "Context", "load_library", "library_path",
+    "dda_create", "dda_destroy", "dda_last_error", "dda_set_stream", "dda_set_target", "dda_set_materials",
+    "dda_prepare", "dda_get_info", "dda_solve", "dda_solve_device", "dda_matvec", "dda_matvec_device",
+    "dda_incident_field", "dda_grad_qabs",
+]
+
+STATUS = {0: "DDA_OK", 1: "DDA_ERR_ARG", 2: "DDA_ERR_CUDA", 3: "DDA_ERR_OOM", 4: "DDA_ERR_SIZE",
+          5: "DDA_ERR_NOT_CONVERGED", 6: "DDA_ERR_BREAKDOWN", 7: "DDA_ERR_NONFINITE"}
+
+
+class Precision:
+    FP64 = 0
+    FP32_REFINED = 1
+    FP32 = 2
+
+
+class DdaError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.status_name = STATUS.get(status, str(status))
+
+
+class dda_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("normal_eq", ctypes.c_int),
+                ("x0", ctypes.POINTER(ctypes.c_double))]
+
+
+class dda_result(ctypes.Structure):
+    _fields_ = [("qext", ctypes.c_double), ("qabs", ctypes.c_double), ("qsca", ctypes.c_double),
+                ("resid_rel", ctypes.c_double), ("resid_normal_eq", ctypes.c_double), ("iters", ctypes.c_int),
+                ("outer_iters", ctypes.c_int), ("matvecs", ctypes.c_int), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["status_name"] = STATUS.get(self.status, str(self.status))
+        return d
+
+
+class dda_info(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("Lx", ctypes.c_int),
+                ("Ly", ctypes.c_int), ("Lz", ctypes.c_int), ("ndipoles", ctypes.c_int64), ("ncomp", ctypes.c_int),
+                ("aeff_lattice", ctypes.c_double), ("kd", ctypes.c_double), ("x", ctypes.c_double)]
+
+
+_lib = None
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load (building first if needed) the in-tree CUDA library."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not _build.up_to_date():
+        if not build_if_missing and not os.path.exists(path):
+            raise DdaError(2, f"CUDA library not built: {path}")
+        path = _build.build()
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    sig = {
+        "dda_create": ([ctypes.c_int, ctypes.POINTER(vp)], ctypes.c_int),
+        "dda_destroy": ([vp], ctypes.c_int),
+        "dda_last_error": ([vp], ctypes.c_char_p),
+        "dda_set_stream": ([vp, vp], ctypes.c_int),
+        "dda_set_target": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_uint8)], ctypes.c_int),
+        "dda_set_materials": ([vp, ctypes.c_int, _D, ctypes.c_double], ctypes.c_int),
+        "dda_prepare": ([vp, ctypes.c_double, ctypes.c_double, ctypes.c_int], ctypes.c_int),
+        "dda_get_info": ([vp, ctypes.POINTER(dda_info)], ctypes.c_int),
+        "dda_solve": ([vp, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.POINTER(dda_opts), _D, ctypes.POINTER(dda_result)],
+                      ctypes.c_int),
+        "dda_solve_device": ([vp, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.POINTER(dda_opts), vp,
+                              ctypes.POINTER(dda_result)], ctypes.c_int),
+        "dda_matvec": ([vp, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D], ctypes.c_int),
+        "dda_matvec_device": ([vp, ctypes.c_int, ctypes.c_int, _D, _D, vp, vp], ctypes.c_int),
+        "dda_incident_field": ([vp, ctypes.c_int, _D, _D, _D], ctypes.c_int),
+        "dda_grad_qabs": ([vp, ctypes.c_int, _D, _D, ctypes.POINTER(dda_opts), _D, _D, _D, ctypes.POINTER(dda_result)],
+                          ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _check(ctx, status: int):
+    if status != 0:
+        msg = dda_last_error(ctx) if ctx else ""
+        raise DdaError(status, msg)
+
+
+def _rhs(khat, e):
+    k = np.ascontiguousarray(np.atleast_2d(np.asarray(khat, dtype=np.float64)))
+    ev = np.ascontiguousarray(np.atleast_2d(np.asarray(e, dtype=np.complex128)))
+    if k.shape[1] != 3 or ev.shape != k.shape:
+        raise ValueError("khat must be (R,3) real and e (R,3) complex")
+    return k, ev.view(np.float64).reshape(k.shape[0], 6).copy(), k.shape[0]
+
+
+def _opts(tol=1e-5, maxit=1000, use_graph=True, inner_tol=0.0, max_outer=0, normal_eq=False, x0=None):
+    o = dda_opts()
+    o.tol = tol
+    o.maxit = maxit
+    o.use_graph = 1 if use_graph else 0
+    o.inner_tol = inner_tol
+    o.max_outer = max_outer
+    o.normal_eq = 1 if normal_eq else 0
+    keep = None
+    if x0 is not None:
+        keep = np.ascontiguousarray(x0, dtype=np.complex128).view(np.float64)
+        o.x0 = _dptr(keep)
+    return o, keep
+
+
+# ---------------------------------------------------------------- C names --
+def dda_create(device: int = 0):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    st = lib.dda_create(device, ctypes.byref(h))
+    if st != 0:
+        raise DdaError(st, f"dda_create(device={device}) failed (no usable CUDA device?)")
+    return h
+
+
+def dda_destroy(ctx):
+    if ctx:
+        load_library().dda_destroy(ctx)
+
+
+def dda_last_error(ctx) -> str:
+    msg = load_library().dda_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def dda_set_stream(ctx, stream_ptr: int | None):
+    _check(ctx, load_library().dda_set_stream(ctx, ctypes.c_void_p(stream_ptr or 0)))
+
+
+def dda_set_target(ctx, grid: np.ndarray):
+    g = np.ascontiguousarray(grid, dtype=np.uint8)
+    if g.ndim != 3:
+        raise ValueError("grid must be [nz, ny, nx]")
+    nz, ny, nx = g.shape
+    _check(ctx, load_library().dda_set_target(ctx, nx, ny, nz, g.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+
+
+def dda_set_materials(ctx, m, m_ambient: float = 1.0):
+    mm = np.ascontiguousarray(np.atleast_1d(np.asarray(m, dtype=np.complex128)))
+    _check(ctx, load_library().dda_set_materials(ctx, mm.size, _dptr(mm.view(np.float64)), float(m_ambient)))
+
+
+def dda_prepare(ctx, lambda_vac: float, aeff: float, precision: int = Precision.FP64):
+    _check(ctx, load_library().dda_prepare(ctx, float(lambda_vac), float(aeff), int(precision)))
+
+
+def dda_get_info(ctx) -> dict:
+    info = dda_info()
+    _check(ctx, load_library().dda_get_info(ctx, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in info._fields_}
+
+
+def dda_solve(ctx, precision, khat, e, want_P=True, **opts):
+    """Returns (results list of dicts, P complex [R,3,N] or None, status)."""
+    k, ev, R = _rhs(khat, e)
+    N = dda_get_info(ctx)["ndipoles"]
+    o, keep = _opts(**opts)
+    res = (dda_result * R)()
+    P = np.empty((R, 3, N), dtype=np.complex128) if want_P else None
+    st = load_library().dda_solve(ctx, int(precision), R, _dptr(k), _dptr(ev), ctypes.byref(o),
+                                  _dptr(P.view(np.float64)) if want_P else None, res)
+    if st not in (0, 5, 6):
+        _check(ctx, st)
+    return [r.as_dict() for r in res], P, st
+
+
+def dda_solve_device(ctx, precision, khat, e, P_out, **opts):
+    """P_out: a CUDA tensor (complex128, R*3*N elements) or a raw device pointer."""
+    k, ev, R = _rhs(khat, e)
+    o, keep = _opts(**opts)
+    res = (dda_result * R)()
+    ptr = P_out.data_ptr() if hasattr(P_out, "data_ptr") else int(P_out)
+    st = load_library().dda_solve_device(ctx, int(precision), R, _dptr(k), _dptr(ev), ctypes.byref(o),
+                                         ctypes.c_void_p(ptr), res)
+    if st not in (0, 5, 6):
+        _check(ctx, st)
+    return [r.as_dict() for r in res], st
+
+
+def dda_matvec(ctx, precision, khat, e, x: np.ndarray) -> np.ndarray:
+    k, ev, R = _rhs(khat, e)
+    xx = np.ascontiguousarray(x, dtype=np.complex128)
+    y = np.empty_like(xx)
+    _check(ctx, load_library().dda_matvec(ctx, int(precision), R, _dptr(k), _dptr(ev), _dptr(xx.view(np.float64)),
+                                          _dptr(y.view(np.float64))))
+    return y
+
+
+def dda_matvec_device(ctx, precision, khat, e, x_dev, y_dev):
+    """x_dev, y_dev: CUDA tensors (complex128 for FP64, complex64 for FP32) or device pointers."""
+    k, ev, R = _rhs(khat, e)
+    xp = x_dev.data_ptr() if hasattr(x_dev, "data_ptr") else int(x_dev)
+    yp = y_dev.data_ptr() if hasattr(y_dev, "data_ptr") else int(y_dev)
+    _check(ctx, load_library().dda_matvec_device(ctx, int(precision), R, _dptr(k), _dptr(ev), ctypes.c_void_p(xp),
+                                                 ctypes.c_void_p(yp)))
+
+
+def dda_incident_field(ctx, khat, e) -> np.ndarray:
+    k, ev, R = _rhs(khat, e)
+    N = dda_get_info(ctx)["ndipoles"]
+    E = np.empty((R, 3, N), dtype=np.complex128)
+    _check(ctx, load_library().dda_incident_field(ctx, R, _dptr(k), _dptr(ev), _dptr(E.view(np.float64))))
+    return E
+
+
+def dda_grad_qabs(ctx, precision, khat, e, **opts):
+    """Returns (dQ/dRe eps [N], dQ/dIm eps [N], P [3,N], (forward result, adjoint result))."""
+    k, ev, R = _rhs(khat, e)
+    if R != 1:
+        raise ValueError("dda_grad_qabs takes one right-hand side")
+    N = dda_get_info(ctx)["ndipoles"]
+    o, keep = _opts(**opts)
+    gre = np.empty(N)
+    gim = np.empty(N)
+    P = np.empty((3, N), dtype=np.complex128)
+    res = (dda_result * 2)()
+    _check(ctx, load_library().dda_grad_qabs(ctx, int(precision), _dptr(k), _dptr(ev), ctypes.byref(o), _dptr(gre),
+                                             _dptr(gim), _dptr(P.view(np.float64)), res))
+    return gre, gim, P, (res[0].as_dict(), res[1].as_dict())
+
+
+class Context:
+    """Owns one dda_ctx (one GPU)."""
+
+    def __init__(self, device: int = 0):
+        self.handle = dda_create(device)
+
+    def close(self):
+        if self.handle:
+            dda_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_target(self, grid):
+        dda_set_target(self.handle, grid)
+
+    def set_materials(self, m, m_ambient=1.0):
+        dda_set_materials(self.handle, m, m_ambient)
+
+    def prepare(self, lambda_vac, aeff, precision=Precision.FP64):
+        dda_prepare(self.handle, lambda_vac, aeff, precision)
+
+    def prepare_size_parameter(self, x, precision=Precision.FP64):
+        """Prepare for size parameter x = 2 pi a_eff / lambda (aeff = 1, lambda = 2 pi / x)."""
+        dda_prepare(self.handle, 2.0 * np.pi / x, 1.0, precision)
+
+    def info(self):
+        return dda_get_info(self.handle)
+
+    def solve(self, precision, khat, e, want_P=True, **opts):
+        return dda_solve(self.handle, precision, khat, e, want_P=want_P, **opts)
+
+    def matvec(self, precision, khat, e, x):
+        return dda_matvec(self.handle, precision, khat, e, x)
+
+    def incident_field(self, khat, e):
+        return dda_incident_field(self.handle, khat, e)
+
+    def grad_qabs(self, precision, khat, e, **opts):
+        return dda_grad_qabs(self.handle, precision, khat, e, **opts)

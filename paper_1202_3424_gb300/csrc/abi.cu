@@ -1,0 +1,997 @@
+// C ABI of the DDA hot path: context, target/material/wavelength set-up,
+// matvec, the BiCGstab solve with FP64 iterative refinement, Q reductions and
+// the adjoint gradient.  Declarations and conventions: include/dda.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dda.h"
+#include "internal.h"
+#include "krylov.h"
+
+using cd = std::complex<double>;
+using namespace dda;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+// LATTDR coefficients (Draine & Goodman 1993), the guide's "LATTDR" option.
+constexpr double kB1 = -1.8915316, kB2 = 0.1648469, kB3 = -1.7700004;
+
+struct DevMem {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+template <typename T> struct Inner {
+    cx<T>*b = nullptr, *x = nullptr, *r = nullptr, *rhat = nullptr, *p = nullptr, *v = nullptr, *s = nullptr,
+    *t = nullptr;
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    int R = 0;
+    int prec = -1;
+    int K = 0;
+    cudaStream_t stream = nullptr;
+};
+
+}  // namespace
+
+struct dda_ctx {
+    int device = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    std::string err;
+
+    // target
+    Geom g;
+    bool has_target = false;
+    int max_code = 0;
+    DevTarget tg;
+    DevMem m_site_of, m_lat_of, m_comp_of;
+
+    // materials
+    std::vector<cd> m;
+    double m_amb = 1.0;
+    bool has_materials = false;
+
+    // prepared wavelength
+    bool prepared = false, has32 = false;
+    double kd = 0.0, aeff_lat = 0.0;
+    DevMem m_gh64, m_gh32, m_tw64[3], m_tw32[3];
+
+    // workspace
+    std::vector<DevMem> pool;  // generic named slots, see slot()
+    int ws_R = 0;
+    GraphEntry graph;
+    int* h_count = nullptr;  // pinned
+
+    dda_status fail(dda_status code, const char* fmt, ...) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        err = buf;
+        return code;
+    }
+    dda_status cuda_fail(cudaError_t e, const char* what) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? DDA_ERR_OOM : DDA_ERR_CUDA, "%s: %s", what,
+                    cudaGetErrorString(e));
+    }
+};
+
+#define CU(call)                                                   \
+    do {                                                           \
+        cudaError_t _e = (call);                                   \
+        if (_e != cudaSuccess) return ctx->cuda_fail(_e, #call);   \
+    } while (0)
+
+namespace {
+
+// Workspace slots (each a device buffer grown on demand).
+enum Slot {
+    S_E64, S_X64, S_R64, S_Y64,
+    S_IN_B, S_IN_X, S_IN_R, S_IN_RHAT, S_IN_P, S_IN_V, S_IN_S, S_IN_T,
+    S_PAD1_32, S_PAD2_32, S_PAD1_64, S_PAD2_64,
+    S_STATE, S_ACTIVE, S_WANT, S_OUTER, S_TOLREL, S_SCALE, S_COEF, S_NORM_B, S_NORM_R,
+    S_PART, S_CNT, S_QSUM, S_COUNT,
+    S_BETA64, S_BETA32, S_W, S_KHAT, S_EPOL,
+    S_MV_X32, S_MV_Y32, S_GRAD, S_DBETA,
+    S_NSLOTS
+};
+
+dda_status ensure(dda_ctx* ctx, DevMem& m, size_t bytes, bool zero = false) {
+    if (m.bytes >= bytes && m.p != nullptr) {
+        if (zero) CU(cudaMemsetAsync(m.p, 0, bytes, ctx->stream));
+        return DDA_OK;
+    }
+    if (m.p) {
+        cudaFree(m.p);
+        m.p = nullptr;
+        m.bytes = 0;
+    }
+    // any cached graph may reference the old buffer
+    if (ctx->graph.exec) {
+        cudaGraphExecDestroy(ctx->graph.exec);
+        ctx->graph.exec = nullptr;
+    }
+    CU(cudaMalloc(&m.p, bytes < 256 ? 256 : bytes));
+    m.bytes = bytes < 256 ? 256 : bytes;
+    if (zero) CU(cudaMemsetAsync(m.p, 0, m.bytes, ctx->stream));
+    return DDA_OK;
+}
+
+template <typename P> P* slot(dda_ctx* ctx, int s) { return reinterpret_cast<P*>(ctx->pool[s].p); }
+
+void free_mem(DevMem& m) {
+    if (m.p) cudaFree(m.p);
+    m.p = nullptr;
+    m.bytes = 0;
+}
+
+cd ldr_inverse_alpha(cd eps, double kd, const double* khat, const cd* e) {
+    cd S = 0.0;
+    for (int a = 0; a < 3; ++a) S += (khat[a] * e[a]) * (khat[a] * e[a]);
+    const cd inv_acm = (4.0 * kPi / 3.0) * (eps + 2.0) / (eps - 1.0);
+    return inv_acm + (kB1 + kB2 * eps + kB3 * eps * S) * (kd * kd) - cd(0.0, 2.0 / 3.0) * (kd * kd * kd);
+}
+
+cd ldr_inverse_alpha_deps(cd eps, double kd, const double* khat, const cd* e) {
+    cd S = 0.0;
+    for (int a = 0; a < 3; ++a) S += (khat[a] * e[a]) * (khat[a] * e[a]);
+    return -4.0 * kPi / ((eps - 1.0) * (eps - 1.0)) + (kB2 + kB3 * S) * (kd * kd);
+}
+
+// Validate and normalize the RHS description; fills host copies.
+dda_status check_rhs(dda_ctx* ctx, int R, const double* khat, const double* e, std::vector<double>& k_out,
+                     std::vector<cd>& e_out) {
+    if (R <= 0 || khat == nullptr || e == nullptr) return ctx->fail(DDA_ERR_ARG, "R must be > 0 with khat and e given");
+    k_out.assign(3 * (size_t)R, 0.0);
+    e_out.assign(3 * (size_t)R, 0.0);
+    for (int r = 0; r < R; ++r) {
+        double kn = 0.0, en = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const double kv = khat[3 * r + a], er = e[6 * r + 2 * a], ei = e[6 * r + 2 * a + 1];
+            if (!std::isfinite(kv) || !std::isfinite(er) || !std::isfinite(ei))
+                return ctx->fail(DDA_ERR_NONFINITE, "non-finite direction or polarization for RHS %d", r);
+            kn += kv * kv;
+            en += er * er + ei * ei;
+        }
+        if (std::fabs(std::sqrt(kn) - 1.0) > 1e-6) return ctx->fail(DDA_ERR_ARG, "khat of RHS %d is not a unit vector", r);
+        if (en == 0.0) return ctx->fail(DDA_ERR_ARG, "polarization of RHS %d is zero", r);
+        cd dot = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            k_out[3 * r + a] = khat[3 * r + a] / std::sqrt(kn);
+            e_out[3 * r + a] = cd(e[6 * r + 2 * a], e[6 * r + 2 * a + 1]) / std::sqrt(en);
+            dot += k_out[3 * r + a] * e_out[3 * r + a];
+        }
+        if (std::abs(dot) > 1e-6) return ctx->fail(DDA_ERR_ARG, "polarization of RHS %d is not transverse to khat", r);
+    }
+    return DDA_OK;
+}
+
+// Per-(RHS, composition) tables: 1/alpha in FP64 and FP32, and the
+// absorption weight w = -Im(1/alpha) - (2/3)k^3.  Stride ncomp + 1 (code 0 unused).
+dda_status upload_tables(dda_ctx* ctx, int R, const std::vector<double>& k, const std::vector<cd>& e) {
+    const int BS = (int)ctx->m.size() + 1;
+    std::vector<double2> b64((size_t)R * BS);
+    std::vector<float2> b32((size_t)R * BS);
+    std::vector<double> w((size_t)R * BS);
+    const double kd = ctx->kd;
+    for (int r = 0; r < R; ++r) {
+        b64[(size_t)r * BS] = make_double2(0.0, 0.0);
+        b32[(size_t)r * BS] = make_float2(0.f, 0.f);
+        w[(size_t)r * BS] = 0.0;
+        for (int c = 1; c < BS; ++c) {
+            const cd mrel = ctx->m[c - 1] / ctx->m_amb;
+            const cd be = ldr_inverse_alpha(mrel * mrel, kd, &k[3 * r], &e[3 * r]);
+            if (!std::isfinite(be.real()) || !std::isfinite(be.imag()))
+                return ctx->fail(DDA_ERR_NONFINITE, "polarizability of composition %d is not finite", c);
+            b64[(size_t)r * BS + c] = make_double2(be.real(), be.imag());
+            b32[(size_t)r * BS + c] = make_float2((float)be.real(), (float)be.imag());
+            w[(size_t)r * BS + c] = -be.imag() - (2.0 / 3.0) * kd * kd * kd;
+        }
+    }
+    dda_status s;
+    if ((s = ensure(ctx, ctx->pool[S_BETA64], b64.size() * sizeof(double2))) != DDA_OK) return s;
+    if ((s = ensure(ctx, ctx->pool[S_BETA32], b32.size() * sizeof(float2))) != DDA_OK) return s;
+    if ((s = ensure(ctx, ctx->pool[S_W], w.size() * sizeof(double))) != DDA_OK) return s;
+    CU(cudaMemcpyAsync(ctx->pool[S_BETA64].p, b64.data(), b64.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->pool[S_BETA32].p, b32.data(), b32.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->pool[S_W].p, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<double2> e2(3 * (size_t)R);
+    for (size_t i = 0; i < e2.size(); ++i) e2[i] = make_double2(e[i].real(), e[i].imag());
+    if ((s = ensure(ctx, ctx->pool[S_KHAT], k.size() * sizeof(double))) != DDA_OK) return s;
+    if ((s = ensure(ctx, ctx->pool[S_EPOL], e2.size() * sizeof(double2))) != DDA_OK) return s;
+    CU(cudaMemcpyAsync(ctx->pool[S_KHAT].p, k.data(), k.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->pool[S_EPOL].p, e2.data(), e2.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+    // the host vectors go out of scope: finish the copies first
+    CU(cudaStreamSynchronize(ctx->stream));
+    return DDA_OK;
+}
+
+int beta_stride(const dda_ctx* ctx) { return (int)ctx->m.size() + 1; }
+
+// Chunk of RHS whose padded work fits the budget.
+template <typename T> int matvec_chunk(const dda_ctx* ctx, int R) {
+    const size_t per = (size_t)3 * (ctx->g.u1_per_comp() + ctx->g.u2_per_comp()) * sizeof(cx<T>);
+    const size_t budget = (size_t)48 << 30;
+    int c = (int)std::max<size_t>(1, budget / per);
+    return std::min(c, R);
+}
+
+template <typename T> struct PadSlots;
+template <> struct PadSlots<float> { static constexpr int a = S_PAD1_32, b = S_PAD2_32; };
+template <> struct PadSlots<double> { static constexpr int a = S_PAD1_64, b = S_PAD2_64; };
+
+template <typename T> const cx<T>* ghat_of(const dda_ctx* ctx);
+template <> const float2* ghat_of<float>(const dda_ctx* ctx) { return (const float2*)ctx->m_gh32.p; }
+template <> const double2* ghat_of<double>(const dda_ctx* ctx) { return (const double2*)ctx->m_gh64.p; }
+template <typename T> Twiddles<T> tw_of(const dda_ctx* ctx);
+template <> Twiddles<float> tw_of<float>(const dda_ctx* ctx) {
+    return {(const float2*)ctx->m_tw32[0].p, (const float2*)ctx->m_tw32[1].p, (const float2*)ctx->m_tw32[2].p};
+}
+template <> Twiddles<double> tw_of<double>(const dda_ctx* ctx) {
+    return {(const double2*)ctx->m_tw64[0].p, (const double2*)ctx->m_tw64[1].p, (const double2*)ctx->m_tw64[2].p};
+}
+template <typename T> const cx<T>* beta_of(dda_ctx* ctx);
+template <> const float2* beta_of<float>(dda_ctx* ctx) { return slot<float2>(ctx, S_BETA32); }
+template <> const double2* beta_of<double>(dda_ctx* ctx) { return slot<double2>(ctx, S_BETA64); }
+
+template <typename T> dda_status ensure_pad(dda_ctx* ctx, int R) {
+    const int rc = matvec_chunk<T>(ctx, R);
+    dda_status s;
+    if ((s = ensure(ctx, ctx->pool[PadSlots<T>::a], (size_t)rc * 3 * ctx->g.u1_per_comp() * sizeof(cx<T>))) != DDA_OK)
+        return s;
+    return ensure(ctx, ctx->pool[PadSlots<T>::b], (size_t)rc * 3 * ctx->g.u2_per_comp() * sizeof(cx<T>));
+}
+
+// y = A x over R RHS in chunks (workspace from ensure_pad<T>).
+template <typename T>
+dda_status run_matvec(dda_ctx* ctx, int R, const cx<T>* x, cx<T>* y, const int* active) {
+    const int rc = matvec_chunk<T>(ctx, R);
+    const int64_t n = 3 * ctx->g.N;
+    PadWork<T> w{slot<cx<T>>(ctx, PadSlots<T>::a), slot<cx<T>>(ctx, PadSlots<T>::b)};
+    const int BS = beta_stride(ctx);
+    for (int r0 = 0; r0 < R; r0 += rc) {
+        const int rn = std::min(rc, R - r0);
+        CU(launch_matvec<T>(ctx->g, rn, x + (int64_t)r0 * n, y + (int64_t)r0 * n, w, ctx->tg,
+                            beta_of<T>(ctx) + (int64_t)r0 * BS, BS, ghat_of<T>(ctx), tw_of<T>(ctx),
+                            active ? active + r0 : nullptr, ctx->stream));
+    }
+    return DDA_OK;
+}
+
+template <typename T> struct InnerSlots {
+    static Inner<T> get(dda_ctx* ctx) {
+        Inner<T> in;
+        in.b = slot<cx<T>>(ctx, S_IN_B);
+        in.x = slot<cx<T>>(ctx, S_IN_X);
+        in.r = slot<cx<T>>(ctx, S_IN_R);
+        in.rhat = slot<cx<T>>(ctx, S_IN_RHAT);
+        in.p = slot<cx<T>>(ctx, S_IN_P);
+        in.v = slot<cx<T>>(ctx, S_IN_V);
+        in.s = slot<cx<T>>(ctx, S_IN_S);
+        in.t = slot<cx<T>>(ctx, S_IN_T);
+        return in;
+    }
+};
+
+// One BiCGstab iteration for every active RHS.
+template <typename T> dda_status inner_iteration(dda_ctx* ctx, int R) {
+    using Ops = KrylovOps<cx<T>>;
+    const int64_t n = 3 * ctx->g.N;
+    Inner<T> in = InnerSlots<T>::get(ctx);
+    KState* st = slot<KState>(ctx, S_STATE);
+    int* act = slot<int>(ctx, S_ACTIVE);
+    double2* part = slot<double2>(ctx, S_PART);
+    unsigned* cnt = slot<unsigned>(ctx, S_CNT);
+    cudaStream_t s = ctx->stream;
+    dda_status rs;
+    CU(Ops::update_p(R, n, in.p, in.r, in.v, st, act, s));
+    if ((rs = run_matvec<T>(ctx, R, in.p, in.v, act)) != DDA_OK) return rs;
+    CU(Ops::alpha(R, n, in.rhat, in.v, st, act, part, cnt, s));
+    CU(Ops::update_s(R, n, in.s, in.r, in.v, st, act, s));
+    if ((rs = run_matvec<T>(ctx, R, in.s, in.t, act)) != DDA_OK) return rs;
+    CU(Ops::omega(R, n, in.t, in.s, st, act, part, cnt, s));
+    CU(Ops::update_xr(R, n, in.x, in.p, in.s, in.t, in.r, in.rhat, st, act, part, cnt, s));
+    return DDA_OK;
+}
+
+template <typename T> dda_status inner_block(dda_ctx* ctx, int R, int K) {
+    dda_status rs;
+    for (int k = 0; k < K; ++k)
+        if ((rs = inner_iteration<T>(ctx, R)) != DDA_OK) return rs;
+    CU(launch_count_active(slot<int>(ctx, S_ACTIVE), R, slot<int>(ctx, S_COUNT), ctx->stream));
+    CU(cudaMemcpyAsync(ctx->h_count, ctx->pool[S_COUNT].p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    return DDA_OK;
+}
+
+// Iterate until no RHS is active (the device decides convergence and maxit).
+// The first block of K iterations runs eagerly; with use_graph the block is
+// then captured once and replayed.
+template <typename T> dda_status inner_solve(dda_ctx* ctx, int R, int maxit, bool use_graph) {
+    const int K = 4;
+    const int prec = sizeof(T) == 4 ? 1 : 0;
+    const int max_blocks = maxit / K + 2;
+    dda_status rs;
+    bool have_graph = ctx->graph.exec && ctx->graph.R == R && ctx->graph.prec == prec && ctx->graph.K == K &&
+                      ctx->graph.stream == ctx->stream;
+    for (int b = 0; b < max_blocks; ++b) {
+        if (use_graph && have_graph) {
+            CU(cudaGraphLaunch(ctx->graph.exec, ctx->stream));
+        } else if ((rs = inner_block<T>(ctx, R, K)) != DDA_OK) {
+            return rs;
+        }
+        CU(cudaStreamSynchronize(ctx->stream));
+        if (*ctx->h_count == 0) break;
+        if (use_graph && !have_graph) {
+            if (ctx->graph.exec) {
+                cudaGraphExecDestroy(ctx->graph.exec);
+                ctx->graph.exec = nullptr;
+            }
+            cudaGraph_t graph = nullptr;
+            CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+            rs = inner_block<T>(ctx, R, K);
+            cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+            if (rs != DDA_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return rs;
+            }
+            if (ce != cudaSuccess) return ctx->cuda_fail(ce, "cudaStreamEndCapture");
+            ce = cudaGraphInstantiate(&ctx->graph.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return ctx->cuda_fail(ce, "cudaGraphInstantiate");
+            ctx->graph.R = R;
+            ctx->graph.prec = prec;
+            ctx->graph.K = K;
+            ctx->graph.stream = ctx->stream;
+            have_graph = true;
+        }
+    }
+    return DDA_OK;
+}
+
+struct RhsTrack {
+    double bn = 0.0, rn = 0.0;
+    int iters = 0, outer = 0, mv = 0;
+    int status = KS_RUNNING;
+    bool done = false;
+};
+
+dda_status ensure_common(dda_ctx* ctx, int R) {
+    dda_status s;
+    const size_t nb = (size_t)R * kMaxReduceBlocks * 2 * sizeof(double2);
+    if ((s = ensure(ctx, ctx->pool[S_PART], nb)) != DDA_OK) return s;
+    if (ctx->pool[S_CNT].bytes < R * sizeof(unsigned)) {
+        if ((s = ensure(ctx, ctx->pool[S_CNT], R * sizeof(unsigned), true)) != DDA_OK) return s;
+    }
+    for (int sl : {S_ACTIVE, S_WANT, S_OUTER})
+        if ((s = ensure(ctx, ctx->pool[sl], R * sizeof(int))) != DDA_OK) return s;
+    for (int sl : {S_TOLREL, S_SCALE, S_COEF, S_NORM_B, S_NORM_R})
+        if ((s = ensure(ctx, ctx->pool[sl], R * sizeof(double))) != DDA_OK) return s;
+    if ((s = ensure(ctx, ctx->pool[S_STATE], R * sizeof(KState))) != DDA_OK) return s;
+    if ((s = ensure(ctx, ctx->pool[S_QSUM], R * sizeof(double2))) != DDA_OK) return s;
+    if ((s = ensure(ctx, ctx->pool[S_COUNT], sizeof(int))) != DDA_OK) return s;
+    return DDA_OK;
+}
+
+template <typename T> dda_status ensure_inner(dda_ctx* ctx, int R) {
+    const size_t vb = (size_t)R * 3 * ctx->g.N * sizeof(cx<T>);
+    dda_status s;
+    for (int sl = S_IN_B; sl <= S_IN_T; ++sl)
+        if ((s = ensure(ctx, ctx->pool[sl], vb)) != DDA_OK) return s;
+    return ensure_pad<T>(ctx, R);
+}
+
+// Solve A x = b (b = S_E64, x -> S_X64) for R RHS with inner precision T.
+// refine: FP64 outer residual loop; otherwise a single inner solve.
+template <typename T>
+dda_status solve_core(dda_ctx* ctx, int R, const dda_opts& o, bool refine, bool have_x0,
+                      std::vector<RhsTrack>& tr) {
+    const int64_t n = 3 * ctx->g.N;
+    cudaStream_t s = ctx->stream;
+    dda_status rs;
+    if ((rs = ensure_common(ctx, R)) != DDA_OK) return rs;
+    if ((rs = ensure_inner<T>(ctx, R)) != DDA_OK) return rs;
+    if ((rs = ensure_pad<double>(ctx, R)) != DDA_OK) return rs;
+    const size_t vb64 = (size_t)R * n * sizeof(double2);
+    for (int sl : {S_X64, S_R64, S_Y64})
+        if ((rs = ensure(ctx, ctx->pool[sl], vb64)) != DDA_OK) return rs;
+    double2* E = slot<double2>(ctx, S_E64);
+    double2* X = slot<double2>(ctx, S_X64);
+    double2* Rr = slot<double2>(ctx, S_R64);
+    double2* Y = slot<double2>(ctx, S_Y64);
+    double2* part = slot<double2>(ctx, S_PART);
+    unsigned* cnt = slot<unsigned>(ctx, S_CNT);
+    int* outer = slot<int>(ctx, S_OUTER);
+    std::vector<double> hb(R), hr(R), tmp(R);
+    std::vector<int> hact(R, 1);
+
+    CU(launch_residual(R, n, E, nullptr, nullptr, slot<double>(ctx, S_NORM_B), nullptr, part, cnt, s));
+    if (have_x0) {
+        CU(cudaMemcpyAsync(outer, hact.data(), R * sizeof(int), cudaMemcpyHostToDevice, s));
+        if ((rs = run_matvec<double>(ctx, R, X, Y, nullptr)) != DDA_OK) return rs;
+        CU(launch_residual(R, n, E, Y, Rr, slot<double>(ctx, S_NORM_R), nullptr, part, cnt, s));
+        for (auto& t : tr) t.mv += 1;
+    } else {
+        CU(cudaMemsetAsync(X, 0, vb64, s));
+        CU(launch_residual(R, n, E, nullptr, Rr, slot<double>(ctx, S_NORM_R), nullptr, part, cnt, s));
+    }
+    CU(cudaMemcpyAsync(hb.data(), ctx->pool[S_NORM_B].p, R * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(hr.data(), ctx->pool[S_NORM_R].p, R * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    for (int r = 0; r < R; ++r) {
+        tr[r].bn = std::sqrt(hb[r]);
+        tr[r].rn = std::sqrt(hr[r]);
+        if (!std::isfinite(tr[r].bn)) return ctx->fail(DDA_ERR_NONFINITE, "non-finite right-hand side");
+    }
+    const int max_outer = refine ? (o.max_outer > 0 ? o.max_outer : 8) : 1;
+    const double floor_tol = (sizeof(T) == 4) ? (o.inner_tol > 0 ? o.inner_tol : 2e-6) : 1e-15;
+    Inner<T> in = InnerSlots<T>::get(ctx);
+    std::vector<KState> hst(R);
+    for (int it = 0; it < max_outer; ++it) {
+        int nact = 0;
+        std::vector<double> tolrel(R, 0.0), scale(R, 0.0), coef(R, 0.0);
+        for (int r = 0; r < R; ++r) {
+            RhsTrack& t = tr[r];
+            hact[r] = 0;
+            if (t.done) continue;
+            if (t.rn <= o.tol * t.bn) {
+                t.done = true;
+                t.status = KS_CONVERGED;
+                continue;
+            }
+            if (t.iters >= o.maxit) {
+                t.done = true;
+                if (t.status == KS_RUNNING || t.status == KS_CONVERGED) t.status = KS_MAXIT;
+                continue;
+            }
+            hact[r] = 1;
+            ++nact;
+            scale[r] = 1.0 / t.rn;
+            coef[r] = t.rn;
+            const double want = refine ? 0.5 * o.tol * t.bn / t.rn : o.tol * t.bn / t.rn;
+            tolrel[r] = std::max(want, floor_tol);
+        }
+        if (nact == 0) break;
+        CU(cudaMemcpyAsync(outer, hact.data(), R * sizeof(int), cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(ctx->pool[S_TOLREL].p, tolrel.data(), R * sizeof(double), cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(ctx->pool[S_SCALE].p, scale.data(), R * sizeof(double), cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(ctx->pool[S_COEF].p, coef.data(), R * sizeof(double), cudaMemcpyHostToDevice, s));
+        for (int r = 0; r < R; ++r) {
+            std::memset(&hst[r], 0, sizeof(KState));
+            hst[r].maxit = std::max(1, o.maxit - tr[r].iters);
+        }
+        CU(cudaMemcpyAsync(ctx->pool[S_STATE].p, hst.data(), R * sizeof(KState), cudaMemcpyHostToDevice, s));
+        CU(KrylovOps<cx<T>>::to_inner(R, n, Rr, in.b, slot<double>(ctx, S_SCALE), outer, s));
+        CU(KrylovOps<cx<T>>::init(R, n, in.b, in.x, in.r, in.rhat, in.p, in.v, slot<KState>(ctx, S_STATE),
+                                  slot<double>(ctx, S_TOLREL), outer, slot<int>(ctx, S_ACTIVE), part, cnt, s));
+        if ((rs = inner_solve<T>(ctx, R, o.maxit, o.use_graph != 0)) != DDA_OK) return rs;
+        CU(cudaMemcpyAsync(hst.data(), ctx->pool[S_STATE].p, R * sizeof(KState), cudaMemcpyDeviceToHost, s));
+        CU(KrylovOps<cx<T>>::accumulate(R, n, X, in.x, slot<double>(ctx, S_COEF), outer, s));
+        if ((rs = run_matvec<double>(ctx, R, X, Y, outer)) != DDA_OK) return rs;
+        CU(launch_residual(R, n, E, Y, Rr, slot<double>(ctx, S_NORM_R), outer, part, cnt, s));
+        CU(cudaMemcpyAsync(hr.data(), ctx->pool[S_NORM_R].p, R * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        for (int r = 0; r < R; ++r) {
+            if (!hact[r]) continue;
+            RhsTrack& t = tr[r];
+            t.iters += hst[r].iter;
+            t.mv += 2 * hst[r].iter + 1;
+            t.outer += 1;
+            const double prev = t.rn;
+            t.rn = std::sqrt(hr[r]);
+            if (hst[r].status == KS_NONFINITE || !std::isfinite(t.rn)) {
+                t.status = KS_NONFINITE;
+                t.done = true;
+            } else if (t.rn <= o.tol * t.bn) {
+                t.status = KS_CONVERGED;
+                t.done = true;
+            } else if (!refine) {
+                t.status = hst[r].status == KS_CONVERGED ? KS_MAXIT : hst[r].status;
+                t.done = true;
+            } else if (hst[r].status == KS_BREAKDOWN && hst[r].iter == 0) {
+                t.status = KS_BREAKDOWN;
+                t.done = true;
+            } else if (t.rn > 0.9 * prev && hst[r].status != KS_CONVERGED) {
+                t.status = hst[r].status == KS_BREAKDOWN ? KS_BREAKDOWN : KS_MAXIT;
+                t.done = true;
+            }
+        }
+    }
+    for (auto& t : tr)
+        if (!t.done) {
+            t.done = true;
+            t.status = (t.rn <= o.tol * t.bn) ? KS_CONVERGED : KS_MAXIT;
+        }
+    return DDA_OK;
+}
+
+dda_status map_status(int ks) {
+    switch (ks) {
+        case KS_CONVERGED: return DDA_OK;
+        case KS_BREAKDOWN: return DDA_ERR_BREAKDOWN;
+        case KS_NONFINITE: return DDA_ERR_NONFINITE;
+        default: return DDA_ERR_NOT_CONVERGED;
+    }
+}
+
+dda_status check_ready(dda_ctx* ctx, dda_precision prec) {
+    if (!ctx) return DDA_ERR_ARG;
+    if (!ctx->prepared) return ctx->fail(DDA_ERR_ARG, "dda_prepare has not been called for the current target");
+    if (prec != DDA_FP64 && prec != DDA_FP32 && prec != DDA_FP32_REFINED)
+        return ctx->fail(DDA_ERR_ARG, "unknown precision %d", (int)prec);
+    if (prec != DDA_FP64 && !ctx->has32)
+        return ctx->fail(DDA_ERR_ARG, "precision needs the complex64 Green tensor: prepare with an FP32 mode");
+    return DDA_OK;
+}
+
+dda_opts default_opts() {
+    dda_opts o;
+    o.tol = 1e-5;
+    o.maxit = 1000;
+    o.use_graph = 1;
+    o.inner_tol = 0.0;
+    o.max_outer = 0;
+    o.normal_eq = 0;
+    o.x0 = nullptr;
+    return o;
+}
+
+// Forward solve of A P = E_inc; P left in S_X64, E in S_E64.
+dda_status forward_solve(dda_ctx* ctx, dda_precision prec, int R, const double* khat, const double* e,
+                         const dda_opts* opts_in, dda_result* res) {
+    dda_status rs;
+    if ((rs = check_ready(ctx, prec)) != DDA_OK) return rs;
+    if (res == nullptr) return ctx->fail(DDA_ERR_ARG, "res must not be NULL");
+    dda_opts o = opts_in ? *opts_in : default_opts();
+    if (!(o.tol > 0.0) || o.maxit <= 0) return ctx->fail(DDA_ERR_ARG, "tol must be > 0 and maxit > 0");
+    std::vector<double> k;
+    std::vector<cd> ev;
+    if ((rs = check_rhs(ctx, R, khat, e, k, ev)) != DDA_OK) return rs;
+    if ((rs = upload_tables(ctx, R, k, ev)) != DDA_OK) return rs;
+    const int64_t n = 3 * ctx->g.N;
+    const size_t vb64 = (size_t)R * n * sizeof(double2);
+    for (int sl : {S_E64, S_X64})
+        if ((rs = ensure(ctx, ctx->pool[sl], vb64)) != DDA_OK) return rs;
+    CU(launch_einc(R, ctx->g.N, ctx->tg.lat_of, ctx->g.nx, ctx->g.ny, ctx->g.nz, ctx->kd, slot<double>(ctx, S_KHAT),
+                   slot<double2>(ctx, S_EPOL), slot<double2>(ctx, S_E64), ctx->stream));
+    const bool have_x0 = o.x0 != nullptr;
+    if (have_x0) {
+        for (size_t i = 0; i < (size_t)R * n * 2; ++i)
+            if (!std::isfinite(o.x0[i])) return ctx->fail(DDA_ERR_NONFINITE, "non-finite initial guess");
+        CU(cudaMemcpyAsync(ctx->pool[S_X64].p, o.x0, vb64, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    std::vector<RhsTrack> tr(R);
+    if (prec == DDA_FP64)
+        rs = solve_core<double>(ctx, R, o, true, have_x0, tr);
+    else
+        rs = solve_core<float>(ctx, R, o, prec == DDA_FP32_REFINED, have_x0, tr);
+    if (rs != DDA_OK) return rs;
+    // Q reductions (FP64)
+    CU(launch_qsums(R, ctx->g.N, slot<double2>(ctx, S_E64), slot<double2>(ctx, S_X64), ctx->tg.comp_of,
+                    slot<double>(ctx, S_W), beta_stride(ctx), slot<double2>(ctx, S_QSUM), slot<double2>(ctx, S_PART),
+                    slot<unsigned>(ctx, S_CNT), ctx->stream));
+    std::vector<double2> q(R);
+    CU(cudaMemcpyAsync(q.data(), ctx->pool[S_QSUM].p, R * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<double> ne(R, -1.0);
+    if (o.normal_eq) {
+        // |A^H (A P - E)| / |A^H E| with A^H y = conj(A conj(y)); S_Y64 holds A P
+        double2* Y = slot<double2>(ctx, S_Y64);
+        double2* Rr = slot<double2>(ctx, S_R64);
+        double2* E = slot<double2>(ctx, S_E64);
+        dda_status s2;
+        if ((s2 = run_matvec<double>(ctx, R, slot<double2>(ctx, S_X64), Y, nullptr)) != DDA_OK) return s2;
+        CU(launch_conj_diff(R, n, Y, E, Rr, ctx->stream));
+        if ((s2 = run_matvec<double>(ctx, R, Rr, Y, nullptr)) != DDA_OK) return s2;
+        CU(launch_residual(R, n, Y, nullptr, nullptr, slot<double>(ctx, S_NORM_R), nullptr, slot<double2>(ctx, S_PART),
+                           slot<unsigned>(ctx, S_CNT), ctx->stream));
+        CU(launch_conj_diff(R, n, E, nullptr, Rr, ctx->stream));
+        if ((s2 = run_matvec<double>(ctx, R, Rr, Y, nullptr)) != DDA_OK) return s2;
+        CU(launch_residual(R, n, Y, nullptr, nullptr, slot<double>(ctx, S_NORM_B), nullptr, slot<double2>(ctx, S_PART),
+                           slot<unsigned>(ctx, S_CNT), ctx->stream));
+        std::vector<double> a(R), b(R);
+        CU(cudaMemcpyAsync(a.data(), ctx->pool[S_NORM_R].p, R * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaMemcpyAsync(b.data(), ctx->pool[S_NORM_B].p, R * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        for (int r = 0; r < R; ++r) ne[r] = std::sqrt(a[r] / b[r]);
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    const double kd = ctx->kd, a2 = ctx->aeff_lat * ctx->aeff_lat;
+    dda_status worst = DDA_OK;
+    for (int r = 0; r < R; ++r) {
+        dda_result& out = res[r];
+        const double cext = 4.0 * kPi * kd * q[r].x, cabs = 4.0 * kPi * kd * q[r].y;
+        out.qext = cext / (kPi * a2);
+        out.qabs = cabs / (kPi * a2);
+        out.qsca = out.qext - out.qabs;
+        out.resid_rel = tr[r].bn > 0 ? tr[r].rn / tr[r].bn : 0.0;
+        out.resid_normal_eq = ne[r];
+        out.iters = tr[r].iters;
+        out.outer_iters = tr[r].outer;
+        out.matvecs = tr[r].mv;
+        out.status = map_status(tr[r].status);
+        if (out.status != DDA_OK && worst == DDA_OK) worst = out.status;
+    }
+    if (worst != DDA_OK) ctx->fail(worst, "some right-hand sides did not converge (see per-RHS status)");
+    return worst;
+}
+
+void host_twiddles(int L, std::vector<double2>& t64, std::vector<float2>& t32) {
+    t64.resize(L);
+    t32.resize(L);
+    for (int m = 0; m < L; ++m) {
+        const double a = -2.0 * kPi * (double)m / (double)L;
+        t64[m] = make_double2(std::cos(a), std::sin(a));
+        t32[m] = make_float2((float)t64[m].x, (float)t64[m].y);
+    }
+}
+
+}  // namespace
+
+// ================================================================== ABI ===
+extern "C" {
+
+dda_status dda_create(int device, dda_ctx** out) {
+    if (out == nullptr) return DDA_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return DDA_ERR_CUDA;
+    }
+    dda_ctx* ctx = new dda_ctx();
+    ctx->device = device;
+    ctx->pool.resize(S_NSLOTS);
+    if (cudaSetDevice(device) != cudaSuccess || cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_count, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return DDA_ERR_CUDA;
+    }
+    ctx->stream = ctx->own_stream;
+    *out = ctx;
+    return DDA_OK;
+}
+
+dda_status dda_destroy(dda_ctx* ctx) {
+    if (!ctx) return DDA_OK;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->graph.exec) cudaGraphExecDestroy(ctx->graph.exec);
+    for (auto& m : ctx->pool) free_mem(m);
+    free_mem(ctx->m_site_of);
+    free_mem(ctx->m_lat_of);
+    free_mem(ctx->m_comp_of);
+    free_mem(ctx->m_gh64);
+    free_mem(ctx->m_gh32);
+    for (int a = 0; a < 3; ++a) {
+        free_mem(ctx->m_tw64[a]);
+        free_mem(ctx->m_tw32[a]);
+    }
+    if (ctx->h_count) cudaFreeHost(ctx->h_count);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    delete ctx;
+    return DDA_OK;
+}
+
+const char* dda_last_error(const dda_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+dda_status dda_set_stream(dda_ctx* ctx, void* stream) {
+    if (!ctx) return DDA_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
+    return DDA_OK;
+}
+
+dda_status dda_set_target(dda_ctx* ctx, int nx, int ny, int nz, const uint8_t* comp) {
+    if (!ctx) return DDA_ERR_ARG;
+    if (nx <= 0 || ny <= 0 || nz <= 0 || comp == nullptr) return ctx->fail(DDA_ERR_ARG, "bad lattice dimensions");
+    Geom g;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.Lx = pick_fft_length(nx);
+    g.Ly = pick_fft_length(ny);
+    g.Lz = pick_fft_length(nz);
+    if (!g.Lx || !g.Ly || !g.Lz)
+        return ctx->fail(DDA_ERR_SIZE, "lattice %dx%dx%d exceeds the largest supported padded length", nx, ny, nz);
+    const int64_t M = g.M();
+    if (M > (int64_t)INT32_MAX) return ctx->fail(DDA_ERR_SIZE, "lattice too large");
+    std::vector<int> site_of(M), lat_of;
+    std::vector<uint8_t> comp_of;
+    int maxc = 0;
+    for (int64_t i = 0; i < M; ++i) {
+        if (comp[i]) {
+            site_of[i] = (int)lat_of.size();
+            lat_of.push_back((int)i);
+            comp_of.push_back(comp[i]);
+            maxc = std::max<int>(maxc, comp[i]);
+        } else {
+            site_of[i] = -1;
+        }
+    }
+    if (lat_of.empty()) return ctx->fail(DDA_ERR_ARG, "target has no occupied site");
+    g.N = (int64_t)lat_of.size();
+    cudaSetDevice(ctx->device);
+    ctx->prepared = false;
+    ctx->has32 = false;
+    dda_status s;
+    if ((s = ensure(ctx, ctx->m_site_of, M * sizeof(int))) != DDA_OK) return s;
+    if ((s = ensure(ctx, ctx->m_lat_of, g.N * sizeof(int))) != DDA_OK) return s;
+    if ((s = ensure(ctx, ctx->m_comp_of, g.N)) != DDA_OK) return s;
+    CU(cudaMemcpy(ctx->m_site_of.p, site_of.data(), M * sizeof(int), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(ctx->m_lat_of.p, lat_of.data(), g.N * sizeof(int), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(ctx->m_comp_of.p, comp_of.data(), g.N, cudaMemcpyHostToDevice));
+    ctx->tg.site_of = (int*)ctx->m_site_of.p;
+    ctx->tg.lat_of = (int*)ctx->m_lat_of.p;
+    ctx->tg.comp_of = (uint8_t*)ctx->m_comp_of.p;
+    ctx->g = g;
+    ctx->max_code = maxc;
+    ctx->has_target = true;
+    if (ctx->graph.exec) {
+        cudaGraphExecDestroy(ctx->graph.exec);
+        ctx->graph.exec = nullptr;
+    }
+    return DDA_OK;
+}
+
+dda_status dda_set_materials(dda_ctx* ctx, int ncomp, const double* m_complex, double m_ambient) {
+    if (!ctx) return DDA_ERR_ARG;
+    if (ncomp <= 0 || ncomp > 255 || m_complex == nullptr) return ctx->fail(DDA_ERR_ARG, "bad ncomp or NULL indices");
+    if (!(m_ambient > 0.0) || !std::isfinite(m_ambient)) return ctx->fail(DDA_ERR_ARG, "ambient index must be > 0");
+    std::vector<cd> m(ncomp);
+    for (int c = 0; c < ncomp; ++c) {
+        m[c] = cd(m_complex[2 * c], m_complex[2 * c + 1]);
+        if (!std::isfinite(m[c].real()) || !std::isfinite(m[c].imag()))
+            return ctx->fail(DDA_ERR_NONFINITE, "refractive index of composition %d is not finite", c + 1);
+        const cd mr = m[c] / m_ambient;
+        if (std::abs(mr * mr - 1.0) == 0.0)
+            return ctx->fail(DDA_ERR_ARG, "composition %d matches the ambient medium (zero polarizability)", c + 1);
+    }
+    ctx->m = m;
+    ctx->m_amb = m_ambient;
+    ctx->has_materials = true;
+    ctx->prepared = false;
+    ctx->has32 = false;
+    return DDA_OK;
+}
+
+dda_status dda_prepare(dda_ctx* ctx, double lambda_vac, double aeff, dda_precision precision) {
+    if (!ctx) return DDA_ERR_ARG;
+    if (!ctx->has_target || !ctx->has_materials) return ctx->fail(DDA_ERR_ARG, "set target and materials first");
+    if ((int)ctx->m.size() < ctx->max_code)
+        return ctx->fail(DDA_ERR_ARG, "grid uses composition %d but only %d indices given", ctx->max_code, (int)ctx->m.size());
+    if (!(lambda_vac > 0.0) || !(aeff > 0.0) || !std::isfinite(lambda_vac) || !std::isfinite(aeff))
+        return ctx->fail(DDA_ERR_ARG, "wavelength and aeff must be positive and finite");
+    cudaSetDevice(ctx->device);
+    const Geom& g = ctx->g;
+    ctx->aeff_lat = std::cbrt(3.0 * (double)g.N / (4.0 * kPi));
+    const double d = aeff / ctx->aeff_lat;
+    ctx->kd = 2.0 * kPi * ctx->m_amb / lambda_vac * d;
+    dda_status s;
+    const int Ls[3] = {g.Lx, g.Ly, g.Lz};
+    for (int a = 0; a < 3; ++a) {
+        std::vector<double2> t64;
+        std::vector<float2> t32;
+        host_twiddles(Ls[a], t64, t32);
+        if ((s = ensure(ctx, ctx->m_tw64[a], t64.size() * sizeof(double2))) != DDA_OK) return s;
+        if ((s = ensure(ctx, ctx->m_tw32[a], t32.size() * sizeof(float2))) != DDA_OK) return s;
+        CU(cudaMemcpy(ctx->m_tw64[a].p, t64.data(), t64.size() * sizeof(double2), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(ctx->m_tw32[a].p, t32.data(), t32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    }
+    const int64_t oct = 6 * g.oct_per_comp();
+    if ((s = ensure(ctx, ctx->m_gh64, oct * sizeof(double2))) != DDA_OK) return s;
+    DevMem scratch;
+    const size_t sb = (size_t)6 * g.Lx * g.Ly * g.Lz * sizeof(double2);
+    cudaError_t e = cudaMalloc(&scratch.p, sb);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaMalloc(Green tensor scratch)");
+    e = launch_green_fft(g, ctx->kd, (double2*)scratch.p, (double2*)ctx->m_gh64.p, tw_of<double>(ctx), ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(scratch.p);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "Green tensor FFT");
+    ctx->has32 = false;
+    if (precision != DDA_FP64) {
+        if ((s = ensure(ctx, ctx->m_gh32, oct * sizeof(float2))) != DDA_OK) return s;
+        CU(launch_convert_c128_to_c64((const double2*)ctx->m_gh64.p, (float2*)ctx->m_gh32.p, oct, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        ctx->has32 = true;
+    }
+    ctx->prepared = true;
+    if (ctx->graph.exec) {
+        cudaGraphExecDestroy(ctx->graph.exec);
+        ctx->graph.exec = nullptr;
+    }
+    return DDA_OK;
+}
+
+dda_status dda_get_info(const dda_ctx* ctx, dda_info* info) {
+    if (!ctx || !info) return DDA_ERR_ARG;
+    std::memset(info, 0, sizeof *info);
+    info->nx = ctx->g.nx;
+    info->ny = ctx->g.ny;
+    info->nz = ctx->g.nz;
+    info->Lx = ctx->g.Lx;
+    info->Ly = ctx->g.Ly;
+    info->Lz = ctx->g.Lz;
+    info->ndipoles = ctx->g.N;
+    info->ncomp = (int)ctx->m.size();
+    info->aeff_lattice = ctx->has_target ? std::cbrt(3.0 * (double)ctx->g.N / (4.0 * kPi)) : 0.0;
+    info->kd = ctx->prepared ? ctx->kd : 0.0;
+    info->x = ctx->prepared ? ctx->kd * ctx->aeff_lat : 0.0;
+    return DDA_OK;
+}
+
+dda_status dda_solve(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* e,
+                     const dda_opts* opts, double* P_out, dda_result* res) {
+    if (!ctx) return DDA_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    dda_status st = forward_solve(ctx, precision, R, khat, e, opts, res);
+    if (st != DDA_OK && st != DDA_ERR_NOT_CONVERGED && st != DDA_ERR_BREAKDOWN) return st;
+    if (P_out) {
+        const size_t bytes = (size_t)R * 3 * ctx->g.N * sizeof(double2);
+        CU(cudaMemcpyAsync(P_out, ctx->pool[S_X64].p, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    return st;
+}
+
+dda_status dda_solve_device(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* e,
+                            const dda_opts* opts, void* P_dev, dda_result* res) {
+    if (!ctx) return DDA_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    dda_status st = forward_solve(ctx, precision, R, khat, e, opts, res);
+    if (st != DDA_OK && st != DDA_ERR_NOT_CONVERGED && st != DDA_ERR_BREAKDOWN) return st;
+    if (P_dev) {
+        const size_t bytes = (size_t)R * 3 * ctx->g.N * sizeof(double2);
+        CU(cudaMemcpyAsync(P_dev, ctx->pool[S_X64].p, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    return st;
+}
+
+static dda_status matvec_common(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* e,
+                                const void* x_dev, void* y_dev) {
+    dda_status rs;
+    if (precision == DDA_FP32_REFINED) return ctx->fail(DDA_ERR_ARG, "matvec precision must be DDA_FP64 or DDA_FP32");
+    if ((rs = check_ready(ctx, precision)) != DDA_OK) return rs;
+    std::vector<double> k;
+    std::vector<cd> ev;
+    if ((rs = check_rhs(ctx, R, khat, e, k, ev)) != DDA_OK) return rs;
+    if ((rs = upload_tables(ctx, R, k, ev)) != DDA_OK) return rs;
+    if (precision == DDA_FP64) {
+        if ((rs = ensure_pad<double>(ctx, R)) != DDA_OK) return rs;
+        return run_matvec<double>(ctx, R, (const double2*)x_dev, (double2*)y_dev, nullptr);
+    }
+    if ((rs = ensure_pad<float>(ctx, R)) != DDA_OK) return rs;
+    return run_matvec<float>(ctx, R, (const float2*)x_dev, (float2*)y_dev, nullptr);
+}
+
+dda_status dda_matvec_device(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* e,
+                             const void* x_dev, void* y_dev) {
+    if (!ctx) return DDA_ERR_ARG;
+    if (!x_dev || !y_dev) return ctx->fail(DDA_ERR_ARG, "NULL vector");
+    cudaSetDevice(ctx->device);
+    dda_status rs = matvec_common(ctx, precision, R, khat, e, x_dev, y_dev);
+    if (rs != DDA_OK) return rs;
+    CU(cudaStreamSynchronize(ctx->stream));
+    return DDA_OK;
+}
+
+dda_status dda_matvec(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* e,
+                      const double* x, double* y) {
+    if (!ctx) return DDA_ERR_ARG;
+    if (!x || !y) return ctx->fail(DDA_ERR_ARG, "NULL vector");
+    if (!ctx->prepared) return ctx->fail(DDA_ERR_ARG, "dda_prepare has not been called");
+    if (R <= 0) return ctx->fail(DDA_ERR_ARG, "R must be > 0");
+    cudaSetDevice(ctx->device);
+    const int64_t n = (int64_t)R * 3 * ctx->g.N;
+    dda_status rs;
+    for (int64_t i = 0; i < 2 * n; ++i)
+        if (!std::isfinite(x[i])) return ctx->fail(DDA_ERR_NONFINITE, "non-finite input vector");
+    if ((rs = ensure(ctx, ctx->pool[S_X64], n * sizeof(double2))) != DDA_OK) return rs;
+    if ((rs = ensure(ctx, ctx->pool[S_Y64], n * sizeof(double2))) != DDA_OK) return rs;
+    CU(cudaMemcpyAsync(ctx->pool[S_X64].p, x, n * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+    if (precision == DDA_FP32) {
+        if ((rs = ensure(ctx, ctx->pool[S_MV_X32], n * sizeof(float2))) != DDA_OK) return rs;
+        if ((rs = ensure(ctx, ctx->pool[S_MV_Y32], n * sizeof(float2))) != DDA_OK) return rs;
+        CU(launch_c128_to_c64v(n, slot<double2>(ctx, S_X64), slot<float2>(ctx, S_MV_X32), ctx->stream));
+        if ((rs = matvec_common(ctx, precision, R, khat, e, ctx->pool[S_MV_X32].p, ctx->pool[S_MV_Y32].p)) != DDA_OK)
+            return rs;
+        CU(launch_c64_to_c128(n, slot<float2>(ctx, S_MV_Y32), slot<double2>(ctx, S_Y64), ctx->stream));
+    } else {
+        if ((rs = matvec_common(ctx, precision, R, khat, e, ctx->pool[S_X64].p, ctx->pool[S_Y64].p)) != DDA_OK)
+            return rs;
+    }
+    CU(cudaMemcpyAsync(y, ctx->pool[S_Y64].p, n * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return DDA_OK;
+}
+
+dda_status dda_incident_field(dda_ctx* ctx, int R, const double* khat, const double* e, double* E_out) {
+    if (!ctx) return DDA_ERR_ARG;
+    if (!E_out) return ctx->fail(DDA_ERR_ARG, "NULL output");
+    dda_status rs;
+    if ((rs = check_ready(ctx, DDA_FP64)) != DDA_OK) return rs;
+    cudaSetDevice(ctx->device);
+    std::vector<double> k;
+    std::vector<cd> ev;
+    if ((rs = check_rhs(ctx, R, khat, e, k, ev)) != DDA_OK) return rs;
+    if ((rs = upload_tables(ctx, R, k, ev)) != DDA_OK) return rs;
+    const size_t bytes = (size_t)R * 3 * ctx->g.N * sizeof(double2);
+    if ((rs = ensure(ctx, ctx->pool[S_E64], bytes)) != DDA_OK) return rs;
+    CU(launch_einc(R, ctx->g.N, ctx->tg.lat_of, ctx->g.nx, ctx->g.ny, ctx->g.nz, ctx->kd, slot<double>(ctx, S_KHAT),
+                   slot<double2>(ctx, S_EPOL), slot<double2>(ctx, S_E64), ctx->stream));
+    CU(cudaMemcpyAsync(E_out, ctx->pool[S_E64].p, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return DDA_OK;
+}
+
+dda_status dda_grad_qabs(dda_ctx* ctx, dda_precision precision, const double* khat, const double* e,
+                         const dda_opts* opts, double* dq_dre_eps, double* dq_dim_eps, double* P_out,
+                         dda_result* res) {
+    if (!ctx) return DDA_ERR_ARG;
+    if (!dq_dre_eps || !dq_dim_eps || !res) return ctx->fail(DDA_ERR_ARG, "NULL output");
+    cudaSetDevice(ctx->device);
+    dda_status st = forward_solve(ctx, precision, 1, khat, e, opts, &res[0]);
+    if (st != DDA_OK) return st;
+    const int64_t N = ctx->g.N, n = 3 * N;
+    dda_status rs;
+    // keep P, build the adjoint RHS W P^* in S_E64, solve A nu = W P^*
+    if ((rs = ensure(ctx, ctx->pool[S_GRAD], (size_t)n * sizeof(double2))) != DDA_OK) return rs;
+    double2* Pkeep = slot<double2>(ctx, S_GRAD);
+    CU(cudaMemcpyAsync(Pkeep, ctx->pool[S_X64].p, n * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(launch_adjoint_rhs(N, Pkeep, ctx->tg.comp_of, slot<double>(ctx, S_W), slot<double2>(ctx, S_E64), ctx->stream));
+    dda_opts o = opts ? *opts : default_opts();
+    o.x0 = nullptr;
+    std::vector<RhsTrack> tr(1);
+    if (precision == DDA_FP64)
+        rs = solve_core<double>(ctx, 1, o, true, false, tr);
+    else
+        rs = solve_core<float>(ctx, 1, o, precision == DDA_FP32_REFINED, false, tr);
+    if (rs != DDA_OK) return rs;
+    res[1].qext = res[1].qabs = res[1].qsca = 0.0;
+    res[1].resid_rel = tr[0].bn > 0 ? tr[0].rn / tr[0].bn : 0.0;
+    res[1].resid_normal_eq = -1.0;
+    res[1].iters = tr[0].iters;
+    res[1].outer_iters = tr[0].outer;
+    res[1].matvecs = tr[0].mv;
+    res[1].status = map_status(tr[0].status);
+    if (res[1].status != DDA_OK) return ctx->fail(res[1].status, "adjoint solve did not converge");
+    // d(1/alpha)/d(eps) per composition for this RHS
+    std::vector<double> k;
+    std::vector<cd> ev;
+    if ((rs = check_rhs(ctx, 1, khat, e, k, ev)) != DDA_OK) return rs;
+    const int BS = beta_stride(ctx);
+    std::vector<double2> db(BS, make_double2(0.0, 0.0));
+    for (int c = 1; c < BS; ++c) {
+        const cd mr = ctx->m[c - 1] / ctx->m_amb;
+        const cd v = ldr_inverse_alpha_deps(mr * mr, ctx->kd, k.data(), ev.data());
+        db[c] = make_double2(v.real(), v.imag());
+    }
+    if ((rs = ensure(ctx, ctx->pool[S_DBETA], BS * sizeof(double2))) != DDA_OK) return rs;
+    CU(cudaMemcpyAsync(ctx->pool[S_DBETA].p, db.data(), BS * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+    if ((rs = ensure(ctx, ctx->pool[S_MV_X32], (size_t)2 * N * sizeof(double))) != DDA_OK) return rs;
+    double* g = slot<double>(ctx, S_MV_X32);
+    const double K = 4.0 * ctx->kd / (ctx->aeff_lat * ctx->aeff_lat);
+    CU(launch_grad(N, Pkeep, slot<double2>(ctx, S_X64), ctx->tg.comp_of, slot<double2>(ctx, S_DBETA), K, g, g + N,
+                   ctx->stream));
+    CU(cudaMemcpyAsync(dq_dre_eps, g, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(dq_dim_eps, g + N, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (P_out) CU(cudaMemcpyAsync(P_out, Pkeep, n * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return DDA_OK;
+}
+
+}  // extern "C"

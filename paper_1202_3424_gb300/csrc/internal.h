@@ -1,0 +1,69 @@
+// Internal (non-ABI) declarations shared by the CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace dda {
+
+// Lattice and padded-grid geometry.  Lattice index of site (ix,iy,iz) is
+// (iz*ny + iy)*nx + ix.  Padded lengths Lx,Ly,Lz are >= 2n (supported FFT
+// lengths); the stored octant of the transformed Green tensor has
+// (Lz/2+1) x (Ly/2+1) x (Lx/2+1) points per component.
+struct Geom {
+    int nx = 0, ny = 0, nz = 0;
+    int Lx = 0, Ly = 0, Lz = 0;
+    int64_t N = 0;  // occupied sites
+    int hx() const { return Lx / 2 + 1; }
+    int hy() const { return Ly / 2 + 1; }
+    int hz() const { return Lz / 2 + 1; }
+    int64_t M() const { return (int64_t)nx * ny * nz; }
+    int64_t u1_per_comp() const { return (int64_t)nz * ny * Lx; }
+    int64_t u2_per_comp() const { return (int64_t)nz * Ly * Lx; }
+    int64_t oct_per_comp() const { return (int64_t)hz() * hy() * hx(); }
+};
+
+// Device-side target description.
+struct DevTarget {
+    int* site_of = nullptr;        // [M] lattice -> site index, -1 for vacuum
+    int* lat_of = nullptr;         // [N] site -> lattice index
+    uint8_t* comp_of = nullptr;    // [N] composition code 1..ncomp
+};
+
+// Twiddle tables, one per padded axis: exp(-2 pi i m/L), m < L.
+template <typename T> struct Twiddles {
+    const cx<T>* x = nullptr;
+    const cx<T>* y = nullptr;
+    const cx<T>* z = nullptr;
+};
+
+// Workspace for the padded passes of one matvec of R right-hand sides.
+template <typename T> struct PadWork {
+    cx<T>* u1 = nullptr;  // [R][3][nz][ny][Lx]
+    cx<T>* u2 = nullptr;  // [R][3][nz][Ly][Lx]
+};
+
+int pick_fft_length(int n);  // smallest supported length >= 2n, or 0
+
+// y = A x for R right-hand sides, vectors [R][3][N].  beta[r*beta_stride + comp]
+// is 1/alpha of composition comp for RHS r.  active (nullable): RHS r is
+// skipped when active[r] == 0.
+template <typename T>
+cudaError_t launch_matvec(const Geom& g, int R, const cx<T>* x, cx<T>* y, const PadWork<T>& w,
+                          const DevTarget& tg, const cx<T>* beta, int beta_stride, const cx<T>* ghat,
+                          const Twiddles<T>& tw, const int* active, cudaStream_t st);
+
+// Build the octant of FFT(g)/(Lx Ly Lz) of the six Green-tensor components
+// (xx, xy, xz, yy, yz, zz) in FP64.  scratch: 6*Lx*Ly*Lz double2.
+cudaError_t launch_green_fft(const Geom& g, double kd, double2* scratch, double2* ghat64,
+                             const Twiddles<double>& tw, cudaStream_t st);
+
+cudaError_t launch_convert_c128_to_c64(const double2* src, float2* dst, int64_t n, cudaStream_t st);
+
+}  // namespace dda

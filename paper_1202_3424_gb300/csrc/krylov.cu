@@ -1,0 +1,535 @@
+// BiCGstab vector kernels, FP64 reductions, incident field, cross-section
+// sums and the adjoint-gradient kernels of the DDA solve.
+//
+// Solver: unpreconditioned BiCGstab (van der Vorst 1992), the family of the
+// guide's recommended PBCGS2/PBCGST ("Choice of Iterative Algorithm"), for
+// complex A x = b, one independent iteration per right-hand side:
+//   p = r + beta (p - omega v);  v = A p;  alpha = rho / <rhat, v>;
+//   s = r - alpha v;  t = A s;  omega = <t, s> / <t, t>;
+//   x += alpha p + omega s;  r = s - omega t;  rho' = <rhat, r>;
+//   beta = (rho'/rho)(alpha/omega).
+// Vectors are complex64 or complex128; every scalar (rho, alpha, omega,
+// beta, norms) is FP64.  Reductions write one FP64 partial per block; the
+// last block of a reduction (atomic ticket) sums the partials and updates the
+// per-RHS scalars on the device, so an iteration needs no host round trip and
+// can be replayed as a CUDA graph.  A RHS whose `active` flag is 0 is skipped
+// by every kernel (per-RHS convergence masking).
+#include <math.h>
+
+#include "internal.h"
+#include "krylov.h"
+
+namespace dda {
+
+static constexpr int kThreads = 256;
+
+// ---- reductions ------------------------------------------------------------------
+template <int ND>
+__device__ __forceinline__ void block_reduce(double2 (&v)[ND]) {
+    __shared__ double2 sh[32 * ND];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int d = 0; d < ND; ++d)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            v[d].x += __shfl_xor_sync(0xffffffffu, v[d].x, o);
+            v[d].y += __shfl_xor_sync(0xffffffffu, v[d].y, o);
+        }
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int d = 0; d < ND; ++d) sh[warp * ND + d] = v[d];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            v[d] = lane < nw ? sh[lane * ND + d] : make_double2(0.0, 0.0);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                v[d].x += __shfl_xor_sync(0xffffffffu, v[d].x, o);
+                v[d].y += __shfl_xor_sync(0xffffffffu, v[d].y, o);
+            }
+        }
+    }
+}
+
+// Store this block's partial sums; the last block to arrive gets the totals
+// in thread 0's v[] and returns true (in every thread of that block).
+template <int ND>
+__device__ __forceinline__ bool last_block_total(double2 (&v)[ND], double2* partials, unsigned* counter) {
+    __shared__ bool is_last;
+    block_reduce<ND>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int d = 0; d < ND; ++d) partials[blockIdx.x * ND + d] = v[d];
+        __threadfence();
+        const unsigned ticket = atomicAdd(counter, 1u);
+        is_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    double2 s[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) s[d] = make_double2(0.0, 0.0);
+    for (int b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            const double2 q = __ldcg(&partials[b * ND + d]);
+            s[d].x += q.x;
+            s[d].y += q.y;
+        }
+    block_reduce<ND>(s);
+#pragma unroll
+    for (int d = 0; d < ND; ++d) v[d] = s[d];
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+
+__device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+// conj(a) * b accumulated in FP64
+template <typename C> __device__ __forceinline__ void acc_cdot(double2& acc, C a, C b) {
+    acc.x += (double)a.x * (double)b.x + (double)a.y * (double)b.y;
+    acc.y += (double)a.x * (double)b.y - (double)a.y * (double)b.x;
+}
+
+__device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+template <typename C> __device__ __forceinline__ C from2(double2 a) {
+    C r;
+    r.x = (typename real_of<C>::type)a.x;
+    r.y = (typename real_of<C>::type)a.y;
+    return r;
+}
+
+#define RHS_PROLOGUE(active)                                    \
+    const int r = blockIdx.y;                                   \
+    if (active != nullptr && active[r] == 0) return;            \
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; \
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+
+// ---- inner-solve kernels ---------------------------------------------------------
+// x = 0, r = rhat = b, p = v = 0;  |b|^2 -> scalars.
+template <typename C>
+__global__ void __launch_bounds__(kThreads)
+    k_init(int64_t n, const C* __restrict__ b, C* __restrict__ x, C* __restrict__ r_, C* __restrict__ rhat,
+           C* __restrict__ p, C* __restrict__ v, KState* __restrict__ st, const double* __restrict__ tol_rel,
+           const int* __restrict__ want, int* __restrict__ active, double2* __restrict__ part,
+           unsigned* __restrict__ cnt) {
+    const int r = blockIdx.y;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t off = (int64_t)r * n;
+    double2 acc[1] = {make_double2(0.0, 0.0)};
+    for (int64_t i = i0; i < n; i += stride) {
+        const C bi = b[off + i];
+        x[off + i] = czero<C>();
+        r_[off + i] = bi;
+        rhat[off + i] = bi;
+        p[off + i] = czero<C>();
+        v[off + i] = czero<C>();
+        acc[0].x += (double)bi.x * bi.x + (double)bi.y * bi.y;
+    }
+    if (last_block_total<1>(acc, part + (int64_t)r * gridDim.x, cnt + r) && threadIdx.x == 0) {
+        KState s = st[r];
+        const double bn = sqrt(acc[0].x);
+        s.bnorm = bn;
+        s.rnorm = bn;
+        s.rho = make_double2(acc[0].x, 0.0);
+        s.alpha = s.omega = make_double2(1.0, 0.0);
+        s.beta = make_double2(0.0, 0.0);
+        s.iter = 0;
+        s.tol_abs = tol_rel[r] * bn;
+        int run = (want == nullptr || want[r] != 0);
+        if (!isfinite(bn)) {
+            s.status = KS_NONFINITE;
+            run = 0;
+        } else if (bn <= s.tol_abs || bn == 0.0) {
+            s.status = KS_CONVERGED;
+            run = 0;
+        } else {
+            s.status = run ? KS_RUNNING : KS_IDLE;
+        }
+        st[r] = s;
+        active[r] = run;
+    }
+}
+
+// p = r + beta (p - omega v)
+template <typename C>
+__global__ void __launch_bounds__(kThreads)
+    k_update_p(int64_t n, C* __restrict__ p, const C* __restrict__ r_, const C* __restrict__ v,
+               const KState* __restrict__ st, const int* __restrict__ active) {
+    RHS_PROLOGUE(active)
+    const C beta = from2<C>(st[r].beta), omega = from2<C>(st[r].omega);
+    const int64_t off = (int64_t)r * n;
+    for (int64_t i = i0; i < n; i += stride) {
+        const C pv = csub(p[off + i], cmul(omega, v[off + i]));
+        p[off + i] = cadd(r_[off + i], cmul(beta, pv));
+    }
+}
+
+// sigma = <rhat, v>;  alpha = rho / sigma
+template <typename C>
+__global__ void __launch_bounds__(kThreads)
+    k_alpha(int64_t n, const C* __restrict__ rhat, const C* __restrict__ v, KState* __restrict__ st,
+            int* __restrict__ active, double2* __restrict__ part, unsigned* __restrict__ cnt) {
+    RHS_PROLOGUE(active)
+    const int64_t off = (int64_t)r * n;
+    double2 acc[1] = {make_double2(0.0, 0.0)};
+    for (int64_t i = i0; i < n; i += stride) acc_cdot(acc[0], rhat[off + i], v[off + i]);
+    if (last_block_total<1>(acc, part + (int64_t)r * gridDim.x, cnt + r) && threadIdx.x == 0) {
+        KState s = st[r];
+        const double2 sig = acc[0];
+        if (!finite2(sig)) {
+            s.status = KS_NONFINITE;
+            active[r] = 0;
+        } else if (sig.x == 0.0 && sig.y == 0.0) {
+            s.status = KS_BREAKDOWN;
+            active[r] = 0;
+        } else {
+            s.alpha = zdiv(s.rho, sig);
+        }
+        st[r] = s;
+    }
+}
+
+// s = r - alpha v
+template <typename C>
+__global__ void __launch_bounds__(kThreads)
+    k_update_s(int64_t n, C* __restrict__ s_, const C* __restrict__ r_, const C* __restrict__ v,
+               const KState* __restrict__ st, const int* __restrict__ active) {
+    RHS_PROLOGUE(active)
+    const C alpha = from2<C>(st[r].alpha);
+    const int64_t off = (int64_t)r * n;
+    for (int64_t i = i0; i < n; i += stride) s_[off + i] = csub(r_[off + i], cmul(alpha, v[off + i]));
+}
+
+// omega = <t, s> / <t, t>
+template <typename C>
+__global__ void __launch_bounds__(kThreads)
+    k_omega(int64_t n, const C* __restrict__ t, const C* __restrict__ s_, KState* __restrict__ st,
+            int* __restrict__ active, double2* __restrict__ part, unsigned* __restrict__ cnt) {
+    RHS_PROLOGUE(active)
+    const int64_t off = (int64_t)r * n;
+    double2 acc[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+    for (int64_t i = i0; i < n; i += stride) {
+        const C ti = t[off + i];
+        acc_cdot(acc[0], ti, s_[off + i]);
+        acc[1].x += (double)ti.x * ti.x + (double)ti.y * ti.y;
+    }
+    if (last_block_total<2>(acc, part + (int64_t)r * gridDim.x * 2, cnt + r) && threadIdx.x == 0) {
+        KState s = st[r];
+        if (!finite2(acc[0]) || !isfinite(acc[1].x)) {
+            s.status = KS_NONFINITE;
+            active[r] = 0;
+        } else {
+            s.omega = acc[1].x > 0.0 ? make_double2(acc[0].x / acc[1].x, acc[0].y / acc[1].x) : make_double2(0.0, 0.0);
+        }
+        st[r] = s;
+    }
+}
+
+// x += alpha p + omega s;  r = s - omega t;  rho' = <rhat, r>, |r|^2; convergence.
+template <typename C>
+__global__ void __launch_bounds__(kThreads)
+    k_update_xr(int64_t n, C* __restrict__ x, const C* __restrict__ p, const C* __restrict__ s_,
+                const C* __restrict__ t, C* __restrict__ r_, const C* __restrict__ rhat, KState* __restrict__ st,
+                int* __restrict__ active, double2* __restrict__ part, unsigned* __restrict__ cnt) {
+    RHS_PROLOGUE(active)
+    const C alpha = from2<C>(st[r].alpha), omega = from2<C>(st[r].omega);
+    const int64_t off = (int64_t)r * n;
+    double2 acc[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+    for (int64_t i = i0; i < n; i += stride) {
+        const C si = s_[off + i];
+        x[off + i] = cadd(x[off + i], cadd(cmul(alpha, p[off + i]), cmul(omega, si)));
+        const C ri = csub(si, cmul(omega, t[off + i]));
+        r_[off + i] = ri;
+        acc_cdot(acc[0], rhat[off + i], ri);
+        acc[1].x += (double)ri.x * ri.x + (double)ri.y * ri.y;
+    }
+    if (last_block_total<2>(acc, part + (int64_t)r * gridDim.x * 2, cnt + r) && threadIdx.x == 0) {
+        KState s = st[r];
+        const double rn = sqrt(acc[1].x);
+        s.rnorm = rn;
+        s.iter += 1;
+        if (!isfinite(rn) || !finite2(acc[0])) {
+            s.status = KS_NONFINITE;
+            active[r] = 0;
+        } else if (rn <= s.tol_abs) {
+            s.status = KS_CONVERGED;
+            active[r] = 0;
+        } else if (s.iter >= s.maxit) {
+            s.status = KS_MAXIT;
+            active[r] = 0;
+        } else if ((acc[0].x == 0.0 && acc[0].y == 0.0) || (s.omega.x == 0.0 && s.omega.y == 0.0)) {
+            s.status = KS_BREAKDOWN;
+            active[r] = 0;
+        } else {
+            s.beta = cmul(zdiv(acc[0], s.rho), zdiv(s.alpha, s.omega));
+            s.rho = acc[0];
+        }
+        st[r] = s;
+    }
+}
+
+__global__ void k_count_active(const int* __restrict__ active, int R, int* __restrict__ out) {
+    int c = 0;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) c += active[r] != 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (threadIdx.x == 0) *out = c;
+}
+
+// ---- refinement kernels (FP64 outer vectors) -------------------------------------
+// out[r] = sum |v|^2 (or |a - b|^2 into r64 = a - b when b != nullptr)
+__global__ void __launch_bounds__(kThreads)
+    k_residual(int64_t n, const double2* __restrict__ a, const double2* __restrict__ b, double2* __restrict__ out_vec,
+               double* __restrict__ out_norm2, const int* __restrict__ active, double2* __restrict__ part,
+               unsigned* __restrict__ cnt) {
+    RHS_PROLOGUE(active)
+    const int64_t off = (int64_t)r * n;
+    double2 acc[1] = {make_double2(0.0, 0.0)};
+    for (int64_t i = i0; i < n; i += stride) {
+        double2 d = a[off + i];
+        if (b != nullptr) d = csub(d, b[off + i]);
+        if (out_vec != nullptr) out_vec[off + i] = d;
+        acc[0].x += d.x * d.x + d.y * d.y;
+    }
+    if (last_block_total<1>(acc, part + (int64_t)r * gridDim.x, cnt + r) && threadIdx.x == 0) out_norm2[r] = acc[0].x;
+}
+
+// bin = (C)(scale[r] * r64)
+template <typename C>
+__global__ void __launch_bounds__(kThreads)
+    k_to_inner(int64_t n, const double2* __restrict__ r64, C* __restrict__ bin, const double* __restrict__ scale,
+               const int* __restrict__ active) {
+    RHS_PROLOGUE(active)
+    const double sc = scale[r];
+    const int64_t off = (int64_t)r * n;
+    for (int64_t i = i0; i < n; i += stride) bin[off + i] = from2<C>(cscale(r64[off + i], sc));
+}
+
+// x64 += coef[r] * xin
+template <typename C>
+__global__ void __launch_bounds__(kThreads)
+    k_accumulate(int64_t n, double2* __restrict__ x64, const C* __restrict__ xin, const double* __restrict__ coef,
+                 const int* __restrict__ active) {
+    RHS_PROLOGUE(active)
+    const double cf = coef[r];
+    const int64_t off = (int64_t)r * n;
+    for (int64_t i = i0; i < n; i += stride) {
+        const C v = xin[off + i];
+        double2 xv = x64[off + i];
+        xv.x += cf * (double)v.x;
+        xv.y += cf * (double)v.y;
+        x64[off + i] = xv;
+    }
+}
+
+// out = conj(a - b) (b nullable)
+__global__ void __launch_bounds__(kThreads)
+    k_conj_diff(int64_t n, const double2* __restrict__ a, const double2* __restrict__ b, double2* __restrict__ out) {
+    const int r = blockIdx.y;
+    const int64_t off = (int64_t)r * n;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 d = a[off + i];
+        if (b != nullptr) d = csub(d, b[off + i]);
+        out[off + i] = make_double2(d.x, -d.y);
+    }
+}
+
+template <typename D, typename S>
+__global__ void k_convert(int64_t n, const S* __restrict__ s, D* __restrict__ d) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        d[i] = ccast<D>(s[i]);
+}
+
+// ---- physics kernels -------------------------------------------------------------
+// E_inc,j = e exp(i kd khat . r_j), r_j at half-integer offsets about the box centre.
+__global__ void __launch_bounds__(kThreads)
+    k_einc(int64_t N, const int* __restrict__ lat_of, int nx, int ny, int nz, double kd,
+           const double* __restrict__ khat, const double2* __restrict__ e, double2* __restrict__ E) {
+    const int r = blockIdx.y;
+    const double kx = khat[3 * r], ky = khat[3 * r + 1], kz = khat[3 * r + 2];
+    const double2 ex = e[3 * r], ey = e[3 * r + 1], ez = e[3 * r + 2];
+    const double cx = 0.5 * (nx - 1), cy = 0.5 * (ny - 1), cz = 0.5 * (nz - 1);
+    double2* Er = E + (int64_t)r * 3 * N;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+        const int lat = lat_of[j];
+        const int ix = lat % nx, iy = (lat / nx) % ny, iz = lat / (nx * ny);
+        const double ph = kd * (kx * (ix - cx) + ky * (iy - cy) + kz * (iz - cz));
+        double sn, cs;
+        sincos(ph, &sn, &cs);
+        const double2 f = make_double2(cs, sn);
+        Er[j] = cmul(ex, f);
+        Er[N + j] = cmul(ey, f);
+        Er[2 * N + j] = cmul(ez, f);
+    }
+}
+
+// sums[r] = ( sum_j Im(E_j^* . P_j),  sum_j w(comp_j) |P_j|^2 )
+__global__ void __launch_bounds__(kThreads)
+    k_qsums(int64_t N, const double2* __restrict__ E, const double2* __restrict__ P, const uint8_t* __restrict__ comp_of,
+            const double* __restrict__ w, int w_stride, double2* __restrict__ sums, double2* __restrict__ part,
+            unsigned* __restrict__ cnt) {
+    const int r = blockIdx.y;
+    const double2* Er = E + (int64_t)r * 3 * N;
+    const double2* Pr = P + (int64_t)r * 3 * N;
+    const double* wr = w + (int64_t)r * w_stride;
+    double2 acc[1] = {make_double2(0.0, 0.0)};
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+        double im = 0.0, p2 = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double2 ev = Er[c * N + j], pv = Pr[c * N + j];
+            im += ev.x * pv.y - ev.y * pv.x;
+            p2 += pv.x * pv.x + pv.y * pv.y;
+        }
+        acc[0].x += im;
+        acc[0].y += wr[comp_of[j]] * p2;
+    }
+    if (last_block_total<1>(acc, part + (int64_t)r * gridDim.x, cnt + r) && threadIdx.x == 0) sums[r] = acc[0];
+}
+
+// b_j = w(comp_j) conj(P_j)  (adjoint right-hand side W P^*)
+__global__ void __launch_bounds__(kThreads)
+    k_adjoint_rhs(int64_t N, const double2* __restrict__ P, const uint8_t* __restrict__ comp_of,
+                  const double* __restrict__ w, double2* __restrict__ b) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+        const double wj = w[comp_of[j]];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double2 pv = P[c * N + j];
+            b[c * N + j] = make_double2(wj * pv.x, -wj * pv.y);
+        }
+    }
+}
+
+// dQ/dRe eps_j = K[-|P|^2 Im b' - 2 Re(b' nu.P)],  dQ/dIm eps_j = K[-|P|^2 Re b' + 2 Im(b' nu.P)]
+__global__ void __launch_bounds__(kThreads)
+    k_grad(int64_t N, const double2* __restrict__ P, const double2* __restrict__ nu, const uint8_t* __restrict__ comp_of,
+           const double2* __restrict__ dbeta, double K, double* __restrict__ g_re, double* __restrict__ g_im) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+        double p2 = 0.0;
+        double2 nup = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double2 pv = P[c * N + j], nv = nu[c * N + j];
+            p2 += pv.x * pv.x + pv.y * pv.y;
+            nup = cadd(nup, cmul(nv, pv));
+        }
+        const double2 bp = dbeta[comp_of[j]];
+        const double2 q = cmul(bp, nup);
+        g_re[j] = K * (-p2 * bp.y - 2.0 * q.x);
+        g_im[j] = K * (-p2 * bp.x + 2.0 * q.y);
+    }
+}
+
+// ---- host launchers --------------------------------------------------------------
+int reduce_blocks(int64_t n) {
+    int64_t b = (n + kThreads * 8 - 1) / (kThreads * 8);
+    if (b > kMaxReduceBlocks) b = kMaxReduceBlocks;
+    return (int)(b < 1 ? 1 : b);
+}
+
+template <typename C>
+cudaError_t KrylovOps<C>::init(int R, int64_t n, const C* b, C* x, C* r, C* rhat, C* p, C* v, KState* st,
+                               const double* tol_rel, const int* want, int* active, double2* part, unsigned* cnt,
+                               cudaStream_t s) {
+    k_init<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, b, x, r, rhat, p, v, st, tol_rel, want, active, part,
+                                                              cnt);
+    return cudaGetLastError();
+}
+template <typename C>
+cudaError_t KrylovOps<C>::update_p(int R, int64_t n, C* p, const C* r, const C* v, const KState* st,
+                                   const int* active, cudaStream_t s) {
+    k_update_p<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, p, r, v, st, active);
+    return cudaGetLastError();
+}
+template <typename C>
+cudaError_t KrylovOps<C>::alpha(int R, int64_t n, const C* rhat, const C* v, KState* st, int* active, double2* part,
+                                unsigned* cnt, cudaStream_t s) {
+    k_alpha<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, rhat, v, st, active, part, cnt);
+    return cudaGetLastError();
+}
+template <typename C>
+cudaError_t KrylovOps<C>::update_s(int R, int64_t n, C* s_, const C* r, const C* v, const KState* st,
+                                   const int* active, cudaStream_t s) {
+    k_update_s<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, s_, r, v, st, active);
+    return cudaGetLastError();
+}
+template <typename C>
+cudaError_t KrylovOps<C>::omega(int R, int64_t n, const C* t, const C* s_, KState* st, int* active, double2* part,
+                                unsigned* cnt, cudaStream_t s) {
+    k_omega<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, t, s_, st, active, part, cnt);
+    return cudaGetLastError();
+}
+template <typename C>
+cudaError_t KrylovOps<C>::update_xr(int R, int64_t n, C* x, const C* p, const C* s_, const C* t, C* r,
+                                    const C* rhat, KState* st, int* active, double2* part, unsigned* cnt,
+                                    cudaStream_t s) {
+    k_update_xr<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, x, p, s_, t, r, rhat, st, active, part, cnt);
+    return cudaGetLastError();
+}
+template <typename C>
+cudaError_t KrylovOps<C>::to_inner(int R, int64_t n, const double2* r64, C* bin, const double* scale,
+                                   const int* active, cudaStream_t s) {
+    k_to_inner<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, r64, bin, scale, active);
+    return cudaGetLastError();
+}
+template <typename C>
+cudaError_t KrylovOps<C>::accumulate(int R, int64_t n, double2* x64, const C* xin, const double* coef,
+                                     const int* active, cudaStream_t s) {
+    k_accumulate<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, x64, xin, coef, active);
+    return cudaGetLastError();
+}
+template struct KrylovOps<float2>;
+template struct KrylovOps<double2>;
+
+cudaError_t launch_count_active(const int* active, int R, int* out, cudaStream_t s) {
+    k_count_active<<<1, 32, 0, s>>>(active, R, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_residual(int R, int64_t n, const double2* a, const double2* b, double2* out_vec, double* out_norm2,
+                            const int* active, double2* part, unsigned* cnt, cudaStream_t s) {
+    k_residual<<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, a, b, out_vec, out_norm2, active, part, cnt);
+    return cudaGetLastError();
+}
+cudaError_t launch_conj_diff(int R, int64_t n, const double2* a, const double2* b, double2* out, cudaStream_t s) {
+    k_conj_diff<<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, a, b, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_c64_to_c128(int64_t n, const float2* s_, double2* d, cudaStream_t s) {
+    k_convert<double2, float2><<<reduce_blocks(n), kThreads, 0, s>>>(n, s_, d);
+    return cudaGetLastError();
+}
+cudaError_t launch_c128_to_c64v(int64_t n, const double2* s_, float2* d, cudaStream_t s) {
+    k_convert<float2, double2><<<reduce_blocks(n), kThreads, 0, s>>>(n, s_, d);
+    return cudaGetLastError();
+}
+cudaError_t launch_einc(int R, int64_t N, const int* lat_of, int nx, int ny, int nz, double kd, const double* khat,
+                        const double2* e, double2* E, cudaStream_t s) {
+    k_einc<<<dim3(reduce_blocks(N), R), kThreads, 0, s>>>(N, lat_of, nx, ny, nz, kd, khat, e, E);
+    return cudaGetLastError();
+}
+cudaError_t launch_qsums(int R, int64_t N, const double2* E, const double2* P, const uint8_t* comp_of, const double* w,
+                         int w_stride, double2* sums, double2* part, unsigned* cnt, cudaStream_t s) {
+    k_qsums<<<dim3(reduce_blocks(N), R), kThreads, 0, s>>>(N, E, P, comp_of, w, w_stride, sums, part, cnt);
+    return cudaGetLastError();
+}
+cudaError_t launch_adjoint_rhs(int64_t N, const double2* P, const uint8_t* comp_of, const double* w, double2* b,
+                               cudaStream_t s) {
+    k_adjoint_rhs<<<reduce_blocks(N), kThreads, 0, s>>>(N, P, comp_of, w, b);
+    return cudaGetLastError();
+}
+cudaError_t launch_grad(int64_t N, const double2* P, const double2* nu, const uint8_t* comp_of, const double2* dbeta,
+                        double K, double* g_re, double* g_im, cudaStream_t s) {
+    k_grad<<<reduce_blocks(N), kThreads, 0, s>>>(N, P, nu, comp_of, dbeta, K, g_re, g_im);
+    return cudaGetLastError();
+}
+
+}  // namespace dda

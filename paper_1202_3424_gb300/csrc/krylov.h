@@ -1,0 +1,64 @@
+// Launchers of the BiCGstab, reduction and physics kernels (krylov.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dda {
+
+enum KStatus : int { KS_RUNNING = 0, KS_CONVERGED = 1, KS_BREAKDOWN = 2, KS_MAXIT = 3, KS_NONFINITE = 4, KS_IDLE = 5 };
+
+// Per-RHS scalars of one BiCGstab solve, all FP64, kept on the device.
+struct KState {
+    double2 rho;    // <rhat, r> of the current residual
+    double2 alpha;
+    double2 omega;
+    double2 beta;   // coefficient of the next search-direction update
+    double bnorm;   // |b|
+    double rnorm;   // recurrence residual |r|
+    double tol_abs; // stop when rnorm <= tol_abs
+    int iter;       // iterations completed in this solve
+    int maxit;
+    int status;     // KStatus
+    int pad;
+};
+
+static constexpr int kMaxReduceBlocks = 256;
+int reduce_blocks(int64_t n);
+
+template <typename C> struct KrylovOps {
+    static cudaError_t init(int R, int64_t n, const C* b, C* x, C* r, C* rhat, C* p, C* v, KState* st,
+                            const double* tol_rel, const int* want, int* active, double2* part, unsigned* cnt,
+                            cudaStream_t s);
+    static cudaError_t update_p(int R, int64_t n, C* p, const C* r, const C* v, const KState* st, const int* active,
+                                cudaStream_t s);
+    static cudaError_t alpha(int R, int64_t n, const C* rhat, const C* v, KState* st, int* active, double2* part,
+                             unsigned* cnt, cudaStream_t s);
+    static cudaError_t update_s(int R, int64_t n, C* s_, const C* r, const C* v, const KState* st, const int* active,
+                                cudaStream_t s);
+    static cudaError_t omega(int R, int64_t n, const C* t, const C* s_, KState* st, int* active, double2* part,
+                             unsigned* cnt, cudaStream_t s);
+    static cudaError_t update_xr(int R, int64_t n, C* x, const C* p, const C* s_, const C* t, C* r, const C* rhat,
+                                 KState* st, int* active, double2* part, unsigned* cnt, cudaStream_t s);
+    static cudaError_t to_inner(int R, int64_t n, const double2* r64, C* bin, const double* scale, const int* active,
+                                cudaStream_t s);
+    static cudaError_t accumulate(int R, int64_t n, double2* x64, const C* xin, const double* coef,
+                                  const int* active, cudaStream_t s);
+};
+
+cudaError_t launch_count_active(const int* active, int R, int* out, cudaStream_t s);
+cudaError_t launch_residual(int R, int64_t n, const double2* a, const double2* b, double2* out_vec, double* out_norm2,
+                            const int* active, double2* part, unsigned* cnt, cudaStream_t s);
+cudaError_t launch_conj_diff(int R, int64_t n, const double2* a, const double2* b, double2* out, cudaStream_t s);
+cudaError_t launch_c64_to_c128(int64_t n, const float2* s_, double2* d, cudaStream_t s);
+cudaError_t launch_c128_to_c64v(int64_t n, const double2* s_, float2* d, cudaStream_t s);
+cudaError_t launch_einc(int R, int64_t N, const int* lat_of, int nx, int ny, int nz, double kd, const double* khat,
+                        const double2* e, double2* E, cudaStream_t s);
+cudaError_t launch_qsums(int R, int64_t N, const double2* E, const double2* P, const uint8_t* comp_of, const double* w,
+                         int w_stride, double2* sums, double2* part, unsigned* cnt, cudaStream_t s);
+cudaError_t launch_adjoint_rhs(int64_t N, const double2* P, const uint8_t* comp_of, const double* w, double2* b,
+                               cudaStream_t s);
+cudaError_t launch_grad(int64_t N, const double2* P, const double2* nu, const uint8_t* comp_of, const double2* dbeta,
+                        double K, double* g_re, double* g_im, cudaStream_t s);
+
+}  // namespace dda

@@ -1,0 +1,509 @@
+// FFT-convolution matvec of the DDA (Goodman, Draine & Flatau 1990; the
+// method behind the guide's eq. AP=E solves, "Choice of FFT Algorithm"):
+//
+//   (A P)_j = (1/alpha_j) P_j + sum_{l != j} A(r_j - r_l) P_l
+//
+// The off-diagonal sum is a discrete convolution of P (on the nx*ny*nz
+// lattice, zero on vacuum sites) with the six components of the symmetric
+// tensor A(r).  Zero-padding every axis to L >= 2n turns it into a circular
+// convolution, evaluated as IFFT(Ghat . FFT(P)) restricted to the lattice.
+//
+// Pass structure (one kernel each, per RHS and component unless noted):
+//   x-fwd   gather P from the compact site vector, FFT rows along x (input
+//           half zero)                                  -> U1 [nz][ny][Lx]
+//   y-fwd   FFT along y (input half zero)               -> U2 [nz][Ly][Lx]
+//   z-conv  for each (kx,ky) column, all three components: FFT along z
+//           (input half zero), multiply by the symmetric 3x3 Ghat in
+//           registers, inverse FFT along z, keep z < nz  -> U2 in place
+//   y-inv   inverse FFT along y, keep y < ny            -> U1
+//   x-inv   inverse FFT along x, keep x < nx, add (1/alpha) P, scatter to
+//           the compact site vector
+// Ghat is stored as one octant (k <= L/2 on each axis) of the transformed
+// kernel: each component is even or odd under each axis reflection, so
+// Ghat(L-k) = +/- Ghat(k).  The 1/(Lx Ly Lz) of the inverse transform is
+// folded into Ghat.
+#include <cstdio>
+#include <mutex>
+#include <unordered_map>
+
+#include "fft.cuh"
+#include "internal.h"
+
+namespace dda {
+
+// ---- tile sizes ------------------------------------------------------------
+template <int L> __host__ __device__ constexpr int tp_x() {
+    return (256 / Plan<L>::NT) > 64 ? 64 : (256 / Plan<L>::NT);
+}
+template <int L> __host__ __device__ constexpr int tp_s() {
+    return (256 / Plan<L>::NT) > 32 ? 32 : ((256 / Plan<L>::NT) < 8 ? 8 : (256 / Plan<L>::NT));
+}
+template <int L, typename T> __host__ __device__ constexpr int tp_z() {
+    return (256 / Plan<L>::NT) > 32 ? 32
+                                    : ((256 / Plan<L>::NT) < (sizeof(T) == 4 ? 8 : 4) ? (sizeof(T) == 4 ? 8 : 4)
+                                                                                      : (256 / Plan<L>::NT));
+}
+
+// Final outputs of a pencil transform: register v[idx] holds position pos.
+template <class PL, int DIR, class F>
+__device__ __forceinline__ void for_each_out(int u, F&& f) {
+    constexpr int R = StageRadix<PL, DIR, PL::NS - 1>::value;
+    constexpr int NB = PL::E / R;
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+#pragma unroll
+        for (int m = 0; m < R; ++m) f(q * R + m, u + q * PL::NT + m * (PL::L / R));
+}
+
+template <typename C> struct KeepInRegs {
+    __device__ __forceinline__ void operator()(int, int, int, C) const {}
+};
+
+// ---- x-forward: gather + row FFT ---------------------------------------------
+template <typename T, int LX>
+__global__ void __launch_bounds__(tp_x<LX>() * Plan<LX>::NT)
+    k_xfwd(const cx<T>* __restrict__ X, cx<T>* __restrict__ U1, const int* __restrict__ site_of, int nx,
+           int nrows, int64_t N, const cx<T>* __restrict__ tw, const int* __restrict__ active) {
+    using C = cx<T>;
+    using PL = Plan<LX>;
+    constexpr int TP = tp_x<LX>(), SP = TP + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    const int c = blockIdx.y, r = blockIdx.z;
+    if (active != nullptr && active[r] == 0) return;
+    const int row0 = blockIdx.x * TP;
+    const C* xs = X + ((int64_t)r * 3 + c) * N;
+    for (int e = threadIdx.x; e < TP * nx; e += blockDim.x) {
+        const int t = e / nx, ix = e - t * nx, row = row0 + t;
+        C val = czero<C>();
+        if (row < nrows) {
+            const int s = site_of[(int64_t)row * nx + ix];
+            if (s >= 0) val = xs[s];
+        }
+        buf[ix * SP + t] = val;
+    }
+    __syncthreads();
+    const int t = threadIdx.x % TP, u = threadIdx.x / TP;
+    C v[PL::E];
+    auto first = [&](int pos) { return pos < nx ? buf[pos * SP + t] : czero<C>(); };
+    auto ld = [&](int pos) { return buf[pos * SP + t]; };
+    auto st = [&](int pos, C val) { buf[pos * SP + t] = val; };
+    KeepInRegs<C> keep;
+    pencil_fft<C, PL, -1>(v, u, tw, first, ld, st, keep);
+    __syncthreads();
+    for_each_out<PL, -1>(u, [&](int idx, int pos) { buf[pos * SP + t] = v[idx]; });
+    __syncthreads();
+    C* out = U1 + ((int64_t)r * 3 + c) * (int64_t)nrows * LX;
+    for (int e = threadIdx.x; e < TP * LX; e += blockDim.x) {
+        const int t2 = e / LX, x = e - t2 * LX, row = row0 + t2;
+        if (row < nrows) out[(int64_t)row * LX + x] = buf[x * SP + t2];
+    }
+}
+
+// ---- x-inverse: row IFFT + diagonal + scatter -----------------------------------
+template <typename T, int LX>
+__global__ void __launch_bounds__(tp_x<LX>() * Plan<LX>::NT)
+    k_xinv(const cx<T>* __restrict__ U1, cx<T>* __restrict__ Y, const cx<T>* __restrict__ X,
+           const int* __restrict__ site_of, const uint8_t* __restrict__ comp_of, const cx<T>* __restrict__ beta,
+           int beta_stride, int nx, int nrows, int64_t N, const cx<T>* __restrict__ tw,
+           const int* __restrict__ active) {
+    using C = cx<T>;
+    using PL = Plan<LX>;
+    constexpr int TP = tp_x<LX>(), SP = TP + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    const int c = blockIdx.y, r = blockIdx.z;
+    if (active != nullptr && active[r] == 0) return;
+    const int row0 = blockIdx.x * TP;
+    const C* in = U1 + ((int64_t)r * 3 + c) * (int64_t)nrows * LX;
+    for (int e = threadIdx.x; e < TP * LX; e += blockDim.x) {
+        const int t2 = e / LX, x = e - t2 * LX, row = row0 + t2;
+        buf[x * SP + t2] = row < nrows ? in[(int64_t)row * LX + x] : czero<C>();
+    }
+    __syncthreads();
+    const int t = threadIdx.x % TP, u = threadIdx.x / TP;
+    C v[PL::E];
+    auto first = [&](int pos) { return buf[pos * SP + t]; };
+    auto ld = [&](int pos) { return buf[pos * SP + t]; };
+    auto st = [&](int pos, C val) { buf[pos * SP + t] = val; };
+    KeepInRegs<C> keep;
+    pencil_fft<C, PL, +1>(v, u, tw, first, ld, st, keep);
+    __syncthreads();
+    for_each_out<PL, +1>(u, [&](int idx, int pos) {
+        if (pos < nx) buf[pos * SP + t] = v[idx];
+    });
+    __syncthreads();
+    const C* xs = X + ((int64_t)r * 3 + c) * N;
+    C* ys = Y + ((int64_t)r * 3 + c) * N;
+    const C* br = beta + (int64_t)r * beta_stride;
+    for (int e = threadIdx.x; e < TP * nx; e += blockDim.x) {
+        const int t2 = e / nx, ix = e - t2 * nx, row = row0 + t2;
+        if (row < nrows) {
+            const int s = site_of[(int64_t)row * nx + ix];
+            if (s >= 0) ys[s] = cadd(buf[ix * SP + t2], cmul(br[comp_of[s]], xs[s]));
+        }
+    }
+}
+
+// ---- strided pencils (y passes; y and z passes of the Green tensor) -----------
+// Pencil (b, w): points at src + b*src_bstride + w + pos*pt_stride, pos < n_in
+// (zero beyond); outputs pos < n_out written to dst likewise.  TP pencils
+// adjacent in w per block, so loads and stores are coalesced across w.
+template <typename T, int L, int DIR>
+__global__ void __launch_bounds__(tp_s<L>() * Plan<L>::NT)
+    k_strided(const cx<T>* src, cx<T>* dst, int n_in, int n_out, int64_t pt_stride, int width,
+              int64_t src_bstride, int64_t dst_bstride, int batches_per_rhs, const cx<T>* __restrict__ tw,
+              const int* __restrict__ active) {
+    using C = cx<T>;
+    using PL = Plan<L>;
+    constexpr int TP = tp_s<L>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    const int b = blockIdx.y;
+    if (active != nullptr && active[b / batches_per_rhs] == 0) return;
+    const int t = threadIdx.x % TP, u = threadIdx.x / TP;
+    const int w = blockIdx.x * TP + t;
+    const bool valid = w < width;
+    const C* s = src + (int64_t)b * src_bstride + (valid ? w : 0);
+    C* d = dst + (int64_t)b * dst_bstride + (valid ? w : 0);
+    C v[PL::E];
+    auto first = [&](int pos) { return (valid && pos < n_in) ? s[pos * pt_stride] : czero<C>(); };
+    auto ld = [&](int pos) { return buf[pos * TP + t]; };
+    auto st = [&](int pos, C val) { buf[pos * TP + t] = val; };
+    KeepInRegs<C> keep;
+    pencil_fft<C, PL, DIR>(v, u, tw, first, ld, st, keep);
+    for_each_out<PL, DIR>(u, [&](int idx, int pos) {
+        if (valid && pos < n_out) d[pos * pt_stride] = v[idx];
+    });
+}
+
+// ---- z pass with the Fourier-space product ------------------------------------
+template <typename T, int LZ>
+__global__ void __launch_bounds__(tp_z<LZ, T>() * Plan<LZ>::NT)
+    k_zconv(cx<T>* __restrict__ U2, const cx<T>* __restrict__ gh, int nz, int Lx, int Ly,
+            const cx<T>* __restrict__ tw, const int* __restrict__ active) {
+    using C = cx<T>;
+    using PL = Plan<LZ>;
+    constexpr int TP = tp_z<LZ, T>();
+    constexpr int E = PL::E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    const int ky = blockIdx.y, r = blockIdx.z;
+    if (active != nullptr && active[r] == 0) return;
+    const int t = threadIdx.x % TP, u = threadIdx.x / TP;
+    const int kx = blockIdx.x * TP + t;
+    const bool valid = kx < Lx;
+    const int64_t plane = (int64_t)Ly * Lx;
+    C* base = U2 + (int64_t)r * 3 * nz * plane + (int64_t)ky * Lx + (valid ? kx : 0);
+    auto ld = [&](int pos) { return buf[pos * TP + t]; };
+    auto st = [&](int pos, C val) { buf[pos * TP + t] = val; };
+    KeepInRegs<C> keep;
+    C vc[3][E];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const C* bc = base + (int64_t)c * nz * plane;
+        auto first = [&](int pos) { return (valid && pos < nz) ? bc[pos * plane] : czero<C>(); };
+        pencil_fft<C, PL, -1>(vc[c], u, tw, first, ld, st, keep);
+    }
+    // Fourier-space product with the octant-stored symmetric tensor
+    const int hx = Lx / 2 + 1, hy = Ly / 2 + 1, hz = LZ / 2 + 1;
+    const int kxv = valid ? kx : 0;
+    const int kxo = kxv <= Lx / 2 ? kxv : Lx - kxv;
+    const int kyo = ky <= Ly / 2 ? ky : Ly - ky;
+    const bool fx = kxv > Lx / 2, fy = ky > Ly / 2;
+    const int64_t cs = (int64_t)hz * hy * hx;
+    const C* g0 = gh + (int64_t)kyo * hx + kxo;
+    for_each_out<PL, -1>(u, [&](int idx, int kz) {
+        const bool fz = kz > LZ / 2;
+        const int kzo = fz ? LZ - kz : kz;
+        const C* g = g0 + (int64_t)kzo * hy * hx;
+        const C gxx = g[0], gyy = g[3 * cs], gzz = g[5 * cs];
+        C gxy = g[cs], gxz = g[2 * cs], gyz = g[4 * cs];
+        if (fx != fy) gxy = cscale(gxy, T(-1));
+        if (fx != fz) gxz = cscale(gxz, T(-1));
+        if (fy != fz) gyz = cscale(gyz, T(-1));
+        const C px = vc[0][idx], py = vc[1][idx], pz = vc[2][idx];
+        vc[0][idx] = cadd(cadd(cmul(gxx, px), cmul(gxy, py)), cmul(gxz, pz));
+        vc[1][idx] = cadd(cadd(cmul(gxy, px), cmul(gyy, py)), cmul(gyz, pz));
+        vc[2][idx] = cadd(cadd(cmul(gxz, px), cmul(gyz, py)), cmul(gzz, pz));
+    });
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        pencil_fft_regs<C, PL, +1>(vc[c], u, tw, ld, st, keep);
+        C* bc = base + (int64_t)c * nz * plane;
+        for_each_out<PL, +1>(u, [&](int idx, int pos) {
+            if (valid && pos < nz) bc[pos * plane] = vc[c][idx];
+        });
+    }
+}
+
+// ---- Green tensor on the padded grid ------------------------------------------
+// Displacement along an axis for padded index i: i for i < n, i - L for
+// i > L - n, none otherwise (those entries, and r = 0, are zero).
+__device__ __forceinline__ bool pad_disp(int i, int n, int L, int& d) {
+    if (i < n) { d = i; return true; }
+    if (i > L - n) { d = i - L; return true; }
+    return false;
+}
+
+// A(r) = exp(ik rho)/rho [k^2 (rr - I) + (ik rho - 1)/rho^2 (3 rr - I)]
+// (Draine 1988 off-diagonal block, lattice units), components xx,xy,xz,yy,yz,zz.
+__global__ void k_green(double2* __restrict__ g, int nx, int ny, int nz, int Lx, int Ly, int Lz, double kd) {
+    const int64_t total = (int64_t)Lx * Ly * Lz;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(idx % Lx);
+        const int iy = (int)((idx / Lx) % Ly);
+        const int iz = (int)(idx / ((int64_t)Lx * Ly));
+        int dx, dy, dz;
+        double2 a[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) a[c] = make_double2(0.0, 0.0);
+        if (pad_disp(ix, nx, Lx, dx) && pad_disp(iy, ny, Ly, dy) && pad_disp(iz, nz, Lz, dz) &&
+            (dx | dy | dz) != 0) {
+            const double rho2 = (double)dx * dx + (double)dy * dy + (double)dz * dz;
+            const double rho = sqrt(rho2);
+            const double rh[3] = {dx / rho, dy / rho, dz / rho};
+            double sn, cs;
+            sincos(kd * rho, &sn, &cs);
+            const double2 ph = make_double2(cs / rho, sn / rho);             // exp(ik rho)/rho
+            const double2 c1 = make_double2(kd * kd * ph.x, kd * kd * ph.y);  // k^2 ph
+            const double2 t = make_double2(-1.0 / rho2, kd / rho);           // (ik rho - 1)/rho^2
+            const double2 c2 = cmul(ph, t);
+            const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const double rr = rh[ia[c]] * rh[ib[c]];
+                const double dl = ia[c] == ib[c] ? 1.0 : 0.0;
+                const double f1 = rr - dl, f2 = 3.0 * rr - dl;
+                a[c] = make_double2(c1.x * f1 + c2.x * f2, c1.y * f1 + c2.y * f2);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) g[c * total + idx] = a[c];
+    }
+}
+
+// In-place forward FFT of dense rows of length LX (Green tensor x pass).
+template <int LX>
+__global__ void __launch_bounds__(tp_x<LX>() * Plan<LX>::NT)
+    k_xfull(double2* __restrict__ data, int64_t nrows, const double2* __restrict__ tw) {
+    using C = double2;
+    using PL = Plan<LX>;
+    constexpr int TP = tp_x<LX>(), SP = TP + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    const int64_t row0 = (int64_t)blockIdx.x * TP;
+    for (int e = threadIdx.x; e < TP * LX; e += blockDim.x) {
+        const int t2 = e / LX, x = e - t2 * LX;
+        const int64_t row = row0 + t2;
+        buf[x * SP + t2] = row < nrows ? data[row * LX + x] : czero<C>();
+    }
+    __syncthreads();
+    const int t = threadIdx.x % TP, u = threadIdx.x / TP;
+    C v[PL::E];
+    auto first = [&](int pos) { return buf[pos * SP + t]; };
+    auto ld = [&](int pos) { return buf[pos * SP + t]; };
+    auto st = [&](int pos, C val) { buf[pos * SP + t] = val; };
+    KeepInRegs<C> keep;
+    pencil_fft<C, PL, -1>(v, u, tw, first, ld, st, keep);
+    __syncthreads();
+    for_each_out<PL, -1>(u, [&](int idx, int pos) { buf[pos * SP + t] = v[idx]; });
+    __syncthreads();
+    for (int e = threadIdx.x; e < TP * LX; e += blockDim.x) {
+        const int t2 = e / LX, x = e - t2 * LX;
+        const int64_t row = row0 + t2;
+        if (row < nrows) data[row * LX + x] = buf[x * SP + t2];
+    }
+}
+
+__global__ void k_octant(const double2* __restrict__ g, double2* __restrict__ gh, int Lx, int Ly, int Lz,
+                         double scale) {
+    const int hx = Lx / 2 + 1, hy = Ly / 2 + 1, hz = Lz / 2 + 1;
+    const int64_t per = (int64_t)hx * hy * hz, total = 6 * per;
+    const int64_t full = (int64_t)Lx * Ly * Lz;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(idx / per);
+        const int64_t rem = idx - c * per;
+        const int kx = (int)(rem % hx), ky = (int)((rem / hx) % hy), kz = (int)(rem / ((int64_t)hx * hy));
+        const double2 v = g[c * full + ((int64_t)kz * Ly + ky) * Lx + kx];
+        gh[idx] = make_double2(v.x * scale, v.y * scale);
+    }
+}
+
+__global__ void k_c128_to_c64(const double2* __restrict__ s, float2* __restrict__ d, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        d[i] = make_float2((float)s[i].x, (float)s[i].y);
+}
+
+// ---- host launchers -------------------------------------------------------------
+int pick_fft_length(int n) {
+    for (int L : kSupportedLengths)
+        if (L >= 2 * n) return L;
+    return 0;
+}
+
+// Opt a kernel into more than 48 KB of dynamic shared memory, once per kernel
+// (so that only launches happen while a stream is being captured).
+template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    static std::mutex mu;
+    static std::unordered_map<const void*, size_t> done;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = done.find((const void*)kernel);
+    if (it != done.end() && it->second >= bytes) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done[(const void*)kernel] = bytes;
+    return e;
+}
+
+static unsigned grid1d(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b > 152 * 32) b = 152 * 32;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+#define DDA_DISPATCH_L(LVAL, FN, ...)                       \
+    switch (LVAL) {                                         \
+        case 16: return FN<16>(__VA_ARGS__);                \
+        case 32: return FN<32>(__VA_ARGS__);                \
+        case 48: return FN<48>(__VA_ARGS__);                \
+        case 64: return FN<64>(__VA_ARGS__);                \
+        case 96: return FN<96>(__VA_ARGS__);                \
+        case 128: return FN<128>(__VA_ARGS__);              \
+        case 192: return FN<192>(__VA_ARGS__);              \
+        case 256: return FN<256>(__VA_ARGS__);              \
+        case 384: return FN<384>(__VA_ARGS__);              \
+        case 512: return FN<512>(__VA_ARGS__);              \
+        default: return cudaErrorInvalidValue;              \
+    }
+
+template <typename T> struct LaunchX {
+    template <int LX>
+    static cudaError_t fwd(const Geom& g, int R, const cx<T>* x, cx<T>* u1, const int* site_of, const cx<T>* tw,
+                           const int* active, cudaStream_t st) {
+        constexpr int TP = tp_x<LX>(), NTH = TP * Plan<LX>::NT;
+        const size_t sm = (size_t)LX * (TP + 1) * sizeof(cx<T>);
+        cudaError_t e = allow_smem(k_xfwd<T, LX>, sm);
+        if (e != cudaSuccess) return e;
+        const int nrows = g.ny * g.nz;
+        dim3 grid((nrows + TP - 1) / TP, 3, R);
+        k_xfwd<T, LX><<<grid, NTH, sm, st>>>(x, u1, site_of, g.nx, nrows, g.N, tw, active);
+        return cudaGetLastError();
+    }
+    template <int LX>
+    static cudaError_t inv(const Geom& g, int R, const cx<T>* u1, cx<T>* y, const cx<T>* x, const DevTarget& tg,
+                           const cx<T>* beta, int beta_stride, const cx<T>* tw, const int* active, cudaStream_t st) {
+        constexpr int TP = tp_x<LX>(), NTH = TP * Plan<LX>::NT;
+        const size_t sm = (size_t)LX * (TP + 1) * sizeof(cx<T>);
+        cudaError_t e = allow_smem(k_xinv<T, LX>, sm);
+        if (e != cudaSuccess) return e;
+        const int nrows = g.ny * g.nz;
+        dim3 grid((nrows + TP - 1) / TP, 3, R);
+        k_xinv<T, LX><<<grid, NTH, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride, g.nx, nrows, g.N,
+                                            tw, active);
+        return cudaGetLastError();
+    }
+    template <int L>
+    static cudaError_t strided(int dir, const cx<T>* src, cx<T>* dst, int n_in, int n_out, int64_t pt_stride,
+                               int width, int64_t sb, int64_t db, int batches, int per_rhs, const cx<T>* tw,
+                               const int* active, cudaStream_t st) {
+        constexpr int TP = tp_s<L>(), NTH = TP * Plan<L>::NT;
+        const size_t sm = (size_t)L * TP * sizeof(cx<T>);
+        dim3 grid((width + TP - 1) / TP, batches, 1);
+        cudaError_t e;
+        if (dir < 0) {
+            e = allow_smem(k_strided<T, L, -1>, sm);
+            if (e != cudaSuccess) return e;
+            k_strided<T, L, -1><<<grid, NTH, sm, st>>>(src, dst, n_in, n_out, pt_stride, width, sb, db, per_rhs, tw,
+                                                      active);
+        } else {
+            e = allow_smem(k_strided<T, L, +1>, sm);
+            if (e != cudaSuccess) return e;
+            k_strided<T, L, +1><<<grid, NTH, sm, st>>>(src, dst, n_in, n_out, pt_stride, width, sb, db, per_rhs, tw,
+                                                      active);
+        }
+        return cudaGetLastError();
+    }
+    template <int LZ>
+    static cudaError_t zconv(const Geom& g, int R, cx<T>* u2, const cx<T>* gh, const cx<T>* tw, const int* active,
+                             cudaStream_t st) {
+        constexpr int TP = tp_z<LZ, T>(), NTH = TP * Plan<LZ>::NT;
+        const size_t sm = (size_t)LZ * TP * sizeof(cx<T>);
+        cudaError_t e = allow_smem(k_zconv<T, LZ>, sm);
+        if (e != cudaSuccess) return e;
+        dim3 grid((g.Lx + TP - 1) / TP, g.Ly, R);
+        k_zconv<T, LZ><<<grid, NTH, sm, st>>>(u2, gh, g.nz, g.Lx, g.Ly, tw, active);
+        return cudaGetLastError();
+    }
+};
+
+template <int LX> static cudaError_t launch_xfull(double2* data, int64_t nrows, const double2* tw, cudaStream_t st) {
+    constexpr int TP = tp_x<LX>(), NTH = TP * Plan<LX>::NT;
+    const size_t sm = (size_t)LX * (TP + 1) * sizeof(double2);
+    cudaError_t e = allow_smem(k_xfull<LX>, sm);
+    if (e != cudaSuccess) return e;
+    k_xfull<LX><<<(unsigned)((nrows + TP - 1) / TP), NTH, sm, st>>>(data, nrows, tw);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_matvec(const Geom& g, int R, const cx<T>* x, cx<T>* y, const PadWork<T>& w, const DevTarget& tg,
+                          const cx<T>* beta, int beta_stride, const cx<T>* ghat, const Twiddles<T>& tw,
+                          const int* active, cudaStream_t st) {
+    using LX = LaunchX<T>;
+    cudaError_t e;
+    auto fwdx = [&]() -> cudaError_t { DDA_DISPATCH_L(g.Lx, LX::template fwd, g, R, x, w.u1, tg.site_of, tw.x, active, st); };
+    auto ys = [&](int dir, const cx<T>* s, cx<T>* d, int n_in, int n_out, int64_t sb, int64_t db) -> cudaError_t {
+        DDA_DISPATCH_L(g.Ly, LX::template strided, dir, s, d, n_in, n_out, (int64_t)g.Lx, g.Lx, sb, db, R * 3 * g.nz,
+                       3 * g.nz, tw.y, active, st);
+    };
+    auto zc = [&]() -> cudaError_t { DDA_DISPATCH_L(g.Lz, LX::template zconv, g, R, w.u2, ghat, tw.z, active, st); };
+    auto invx = [&]() -> cudaError_t {
+        DDA_DISPATCH_L(g.Lx, LX::template inv, g, R, w.u1, y, x, tg, beta, beta_stride, tw.x, active, st);
+    };
+    if ((e = fwdx()) != cudaSuccess) return e;
+    if ((e = ys(-1, w.u1, w.u2, g.ny, g.Ly, (int64_t)g.ny * g.Lx, (int64_t)g.Ly * g.Lx)) != cudaSuccess) return e;
+    if ((e = zc()) != cudaSuccess) return e;
+    if ((e = ys(+1, w.u2, w.u1, g.Ly, g.ny, (int64_t)g.Ly * g.Lx, (int64_t)g.ny * g.Lx)) != cudaSuccess) return e;
+    return invx();
+}
+
+template cudaError_t launch_matvec<float>(const Geom&, int, const float2*, float2*, const PadWork<float>&,
+                                          const DevTarget&, const float2*, int, const float2*, const Twiddles<float>&,
+                                          const int*, cudaStream_t);
+template cudaError_t launch_matvec<double>(const Geom&, int, const double2*, double2*, const PadWork<double>&,
+                                           const DevTarget&, const double2*, int, const double2*,
+                                           const Twiddles<double>&, const int*, cudaStream_t);
+
+cudaError_t launch_green_fft(const Geom& g, double kd, double2* scratch, double2* ghat64, const Twiddles<double>& tw,
+                             cudaStream_t st) {
+    const int64_t full = (int64_t)g.Lx * g.Ly * g.Lz;
+    k_green<<<grid1d(full, 256), 256, 0, st>>>(scratch, g.nx, g.ny, g.nz, g.Lx, g.Ly, g.Lz, kd);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    auto xf = [&]() -> cudaError_t { DDA_DISPATCH_L(g.Lx, launch_xfull, scratch, 6 * (int64_t)g.Lz * g.Ly, tw.x, st); };
+    if ((e = xf()) != cudaSuccess) return e;
+    using LX = LaunchX<double>;
+    auto yf = [&]() -> cudaError_t {
+        DDA_DISPATCH_L(g.Ly, LX::template strided, -1, scratch, scratch, g.Ly, g.Ly, (int64_t)g.Lx, g.Lx,
+                       (int64_t)g.Ly * g.Lx, (int64_t)g.Ly * g.Lx, 6 * g.Lz, 1, tw.y, nullptr, st);
+    };
+    if ((e = yf()) != cudaSuccess) return e;
+    auto zf = [&]() -> cudaError_t {
+        DDA_DISPATCH_L(g.Lz, LX::template strided, -1, scratch, scratch, g.Lz, g.Lz, (int64_t)g.Ly * g.Lx,
+                       g.Ly * g.Lx, full, full, 6, 1, tw.z, nullptr, st);
+    };
+    if ((e = zf()) != cudaSuccess) return e;
+    const int64_t oct = 6 * (int64_t)g.hx() * g.hy() * g.hz();
+    k_octant<<<grid1d(oct, 256), 256, 0, st>>>(scratch, ghat64, g.Lx, g.Ly, g.Lz, 1.0 / (double)full);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_c128_to_c64(const double2* src, float2* dst, int64_t n, cudaStream_t st) {
+    k_c128_to_c64<<<grid1d(n, 256), 256, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+}  // namespace dda

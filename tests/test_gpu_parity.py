@@ -1,0 +1,255 @@
+"""GPU path vs the CPU oracle, element by element (needs a GB300).
+
+Every comparison runs the CUDA library through its C ABI (ctypes binding)
+on seeded inputs from dda_inputs, and the oracle on the same inputs.
+Tolerances: 1e-10 relative (max |diff| / max |ref|) for complex128, 1e-5 for
+complex64, as the hot-path specification states.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from dda_inputs import (block_bernoulli_grid, ellipsoid_grid, random_complex, sphere_grid, uniform_directions,
+                        polarization_pair, workload)
+from oracle import dda as odda
+from oracle import pairwise
+
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-10
+F32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1202_3424_gb300 as dda
+    dda.load_library()
+    return dda
+
+
+def _ctx(dda, grid, m, x, prec):
+    ctx = dda.Context(0)
+    ctx.set_target(grid)
+    ctx.set_materials(m)
+    ctx.prepare_size_parameter(x, prec)
+    return ctx
+
+
+def _site_beta(grid, m, kd, khat, ehat):
+    r, comp = odda.site_positions(grid)
+    eps = (np.asarray(m, dtype=complex) ** 2)[comp - 1]
+    return r, odda.ldr_inverse_polarizability(eps, kd, khat, ehat)
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def _rhs_set(R, seed=20120214):
+    k = uniform_directions(R, seed)
+    e1, _ = polarization_pair(k)
+    return k, e1.astype(complex)
+
+
+MATVEC_CASES = [
+    ("sphere16", lambda: sphere_grid(16), [1.33 + 0.01j], 1.0),
+    ("block7x5x3_two_materials", lambda: block_bernoulli_grid(7, 5, 3, seed=3), [1.7 + 0.3j, 1.2 + 0.01j], 2.0),
+    ("ellipsoid_ragged_13x9x6", lambda: ellipsoid_grid(13, 9, 6, 13, 9, 6), [2.0 + 1.0j], 1.5),
+    ("single_dipole", lambda: np.ones((1, 1, 1), np.uint8), [1.5 + 0.1j], 0.3),
+    ("line_of_dipoles_1x1x17", lambda: np.ones((17, 1, 1), np.uint8), [1.5 + 0.1j], 0.8),
+]
+
+
+@pytest.mark.parametrize("name,gridf,m,x", MATVEC_CASES, ids=[c[0] for c in MATVEC_CASES])
+@pytest.mark.parametrize("prec,tol", [(0, F64_TOL), (2, F32_TOL)], ids=["fp64", "fp32"])
+def test_matvec_matches_pairwise_oracle(lib, name, gridf, m, x, prec, tol):
+    grid = gridf()
+    ctx = _ctx(lib, grid, m, x, lib.Precision.FP32_REFINED)
+    kd = ctx.info()["kd"]
+    R = 2
+    khat, ehat = _rhs_set(R)
+    N = ctx.info()["ndipoles"]
+    X = random_complex((R, 3, N), 11)
+    Y = ctx.matvec(prec, khat, ehat, X)
+    for r in range(R):
+        rr, beta = _site_beta(grid, m, kd, khat[r], ehat[r])
+        want, _ = pairwise.matvec(rr, kd, beta, X[r].T)
+        assert _rel(Y[r].T, want) < tol, (name, r)
+    ctx.close()
+
+
+def test_matvec_is_complex_symmetric(lib):
+    grid = ellipsoid_grid(11, 7, 5, 11, 7, 5)
+    ctx = _ctx(lib, grid, [1.6 + 0.2j], 1.2, lib.Precision.FP64)
+    N = ctx.info()["ndipoles"]
+    k, e = np.array([[0, 0, 1.0]]), np.array([[1.0, 0, 0]], complex)
+    x = random_complex((1, 3, N), 1)
+    y = random_complex((1, 3, N), 2)
+    Ax = ctx.matvec(0, k, e, x)
+    Ay = ctx.matvec(0, k, e, y)
+    a, b = np.sum(x * Ay), np.sum(y * Ax)
+    assert abs(a - b) < 1e-13 * abs(a)
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["sphere64", "ellipsoid96x64x32", "block48x48x24"])
+def test_matvec_row_samples_full_size(lib, name):
+    """Full-size workloads: 48 seeded rows recomputed by the O(N) pairwise oracle."""
+    w = workload(name)
+    ctx = _ctx(lib, w.grid, w.m, w.x, lib.Precision.FP32_REFINED)
+    kd = ctx.info()["kd"]
+    N = ctx.info()["ndipoles"]
+    R = min(2, w.nrhs)
+    X = random_complex((R, 3, N), 5)
+    rows = np.random.default_rng(9).choice(N, 48, replace=False)
+    rows[:2] = [0, N - 1]
+    for prec, tol in ((0, F64_TOL), (2, F32_TOL)):
+        Y = ctx.matvec(prec, w.khat[:R], w.ehat[:R], X)
+        for r in range(R):
+            rr, beta = _site_beta(w.grid, w.m, kd, w.khat[r], w.ehat[r])
+            want, _ = pairwise.matvec(rr, kd, beta, X[r].T, rows=rows)
+            assert _rel(Y[r].T[rows], want) < tol, (name, prec, r)
+    ctx.close()
+
+
+def test_incident_field_matches_oracle(lib):
+    grid = ellipsoid_grid(10, 8, 6, 10, 8, 6)
+    ctx = _ctx(lib, grid, [1.33 + 0.01j], 2.0, lib.Precision.FP64)
+    kd = ctx.info()["kd"]
+    k, e = _rhs_set(3)
+    E = ctx.incident_field(k, e)
+    r, _ = odda.site_positions(grid)
+    for i in range(3):
+        assert _rel(E[i].T, odda.incident_field(r, kd, k[i], e[i])) < 1e-13
+    ctx.close()
+
+
+def _oracle_solution(grid, m, kd, khat, ehat):
+    r, beta = _site_beta(grid, m, kd, khat, ehat)
+    E = odda.incident_field(r, kd, khat, ehat)
+    P = odda.solve_dense(odda.dense_matrix(r, kd, beta), E)
+    aeff = odda.aeff_lattice(len(r))
+    return P, odda.efficiencies(odda.cross_sections(kd, E, P, beta), aeff)
+
+
+@pytest.mark.parametrize("prec,tol,qtol", [(0, 1e-12, 1e-10), (1, 1e-8, 1e-7), (2, 1e-5, 1e-4)],
+                         ids=["fp64", "fp32_refined", "fp32"])
+def test_solve_matches_dense_lu(lib, prec, tol, qtol):
+    grid = block_bernoulli_grid(7, 6, 5, seed=20120514)
+    m = [1.7 + 0.3j, 1.2 + 0.01j]
+    ctx = _ctx(lib, grid, m, 1.6, lib.Precision.FP32_REFINED)
+    kd = ctx.info()["kd"]
+    k, e = _rhs_set(3)
+    res, P, st = ctx.solve(prec, k, e, tol=tol, maxit=2000)
+    assert st == 0, res
+    for i in range(3):
+        Po, qo = _oracle_solution(grid, m, kd, k[i], e[i])
+        assert res[i]["resid_rel"] <= tol
+        assert _rel(P[i].T, Po) < max(30 * tol, 1e-10)
+        for a, b in zip((res[i]["qext"], res[i]["qabs"], res[i]["qsca"]), qo):
+            assert abs(a - b) <= qtol * abs(b), (i, a, b)
+    ctx.close()
+
+
+def test_sphere16_solve_matches_oracle_bicgstab(lib):
+    """c1 workload (2176 dipoles, 2 polarizations) at tight tolerance vs the
+    oracle's BiCGstab over the C pairwise matvec."""
+    w = workload("sphere16")
+    ctx = _ctx(lib, w.grid, w.m, w.x, lib.Precision.FP64)
+    kd = ctx.info()["kd"]
+    res, P, st = ctx.solve(0, w.khat, w.ehat, tol=1e-11)
+    assert st == 0
+    r, _ = odda.site_positions(w.grid)
+    aeff = odda.aeff_lattice(len(r))
+    for i in range(2):
+        _, beta = _site_beta(w.grid, w.m, kd, w.khat[i], w.ehat[i])
+        E = odda.incident_field(r, kd, w.khat[i], w.ehat[i])
+        mv = lambda v: pairwise.matvec(r, kd, beta, v.reshape(-1, 3))[0].ravel()  # noqa: E731
+        Po, it, nmv, rel = odda.bicgstab(mv, E.ravel(), 1e-12, 500)
+        Po = Po.reshape(-1, 3)
+        qo = odda.efficiencies(odda.cross_sections(kd, E, Po, beta), aeff)
+        assert _rel(P[i].T, Po) < 1e-9
+        for a, b in zip((res[i]["qext"], res[i]["qabs"], res[i]["qsca"]), qo):
+            assert abs(a - b) <= 1e-10 * abs(b)
+    # the sphere is symmetric under y <-> z: both polarizations give the same Q
+    assert abs(res[0]["qext"] - res[1]["qext"]) < 1e-9 * res[0]["qext"]
+    ctx.close()
+
+
+def test_batched_masked_solve_equals_single_solves(lib):
+    grid = ellipsoid_grid(12, 10, 8, 12, 10, 8)
+    m = [1.33 + 0.05j]
+    ctx = _ctx(lib, grid, m, 2.5, lib.Precision.FP32_REFINED)
+    k, e = _rhs_set(6)
+    res_b, P_b, st = ctx.solve(1, k, e, tol=1e-6)
+    assert st == 0
+    iters = [r["iters"] for r in res_b]
+    for i in (0, 3, 5):
+        res_1, P_1, st1 = ctx.solve(1, k[i:i + 1], e[i:i + 1], tol=1e-6)
+        assert st1 == 0
+        assert res_1[0]["iters"] == iters[i]
+        assert _rel(P_b[i], P_1[0]) < 1e-6
+    ctx.close()
+
+
+def test_graph_and_eager_agree(lib):
+    grid = sphere_grid(10)
+    ctx = _ctx(lib, grid, [1.5 + 0.02j], 1.5, lib.Precision.FP32_REFINED)
+    k, e = _rhs_set(2)
+    a, Pa, _ = ctx.solve(1, k, e, tol=1e-6, use_graph=True)
+    b, Pb, _ = ctx.solve(1, k, e, tol=1e-6, use_graph=False)
+    assert np.array_equal(Pa, Pb)
+    assert [r["iters"] for r in a] == [r["iters"] for r in b]
+    ctx.close()
+
+
+def test_gradient_matches_oracle_adjoint_and_fd(lib):
+    grid = block_bernoulli_grid(4, 3, 3, seed=20120514)
+    m = [1.7 + 0.3j, 1.2 + 0.01j]
+    x = 1.2
+    ctx = _ctx(lib, grid, m, x, lib.Precision.FP64)
+    kd = ctx.info()["kd"]
+    k, e = np.array([[1.0, 0, 0]]), np.array([[0, 1.0, 0]], complex)
+    gre, gim, P, (rf, ra) = ctx.grad_qabs(0, k, e, tol=1e-12)
+    r, comp = odda.site_positions(grid)
+    eps = (np.asarray(m) ** 2)[comp - 1]
+    beta = odda.ldr_inverse_polarizability(eps, kd, k[0], e[0])
+    A = odda.dense_matrix(r, kd, beta)
+    Eo = odda.incident_field(r, kd, k[0], e[0])
+    Po = odda.solve_dense(A, Eo)
+    w = odda.absorption_weights(kd, beta)
+    nu = odda.solve_dense(A, w[:, None] * np.conj(Po))
+    aeff = odda.aeff_lattice(len(r))
+    ore, oim = odda.qabs_gradient(kd, aeff, eps, k[0], e[0], Po, nu)
+    assert _rel(gre, ore) < 1e-9 and _rel(gim, oim) < 1e-9
+    ctx.close()
+
+
+def test_failure_statuses(lib):
+    ctx = lib.Context(0)
+    with pytest.raises(lib.DdaError) as ei:
+        ctx.set_target(np.zeros((3, 3, 3), np.uint8))
+    assert ei.value.status_name == "DDA_ERR_ARG"
+    with pytest.raises(lib.DdaError) as ei:
+        ctx.set_target(np.ones((2, 2, 300), np.uint8))
+    assert ei.value.status_name == "DDA_ERR_SIZE"
+    ctx.set_target(sphere_grid(8))
+    with pytest.raises(lib.DdaError) as ei:
+        ctx.set_materials([complex("nan")])
+    assert ei.value.status_name == "DDA_ERR_NONFINITE"
+    ctx.set_materials([1.5 + 0.1j])
+    with pytest.raises(lib.DdaError):
+        ctx.solve(0, [[1, 0, 0]], [[0, 1, 0]])          # not prepared
+    ctx.prepare_size_parameter(1.0, lib.Precision.FP64)
+    with pytest.raises(lib.DdaError) as ei:
+        ctx.solve(0, [[1, 0, 0]], [[1, 0, 0]])          # not transverse
+    assert ei.value.status_name == "DDA_ERR_ARG"
+    with pytest.raises(lib.DdaError):
+        ctx.solve(1, [[1, 0, 0]], [[0, 1, 0]])          # FP32 not prepared
+    res, P, st = ctx.solve(0, [[1, 0, 0]], [[0, 1, 0]], tol=1e-10, maxit=2)
+    assert res[0]["status_name"] == "DDA_ERR_NOT_CONVERGED" and res[0]["iters"] <= 2
+    ctx.close()

@@ -1,0 +1,423 @@
+#!/usr/bin/env python3
+"""Benchmark of the DDA hot path on GB300.
+
+One step = the whole hot path over one batch of synthetic input: incident
+field, BiCGstab solve to the relative residual 1e-5 (FP32 FFT-convolution
+matvec with FP64 refinement, the production mode), and the Q_ext/Q_abs/Q_sca
+reductions, for every right-hand side of the workload.
+
+Default workload: the 64^3 sphere (137376 dipoles, m = 1.5+0.02i, x = 5,
+k along x, 2 polarizations) on one GPU.  Metric: A.P matvecs per second
+(right-hand-side matvecs, every precision counted) with time-to-solution,
+FP32-refined vs plain FP64 on the same GPU.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank solves its own copy of the
+workload's right-hand sides (orientation sweeps shard over RHS with no
+exchange), so scaling is weak and the value is the sum over ranks.
+The reference arm (--impl reference) times the CPU oracle's pairwise
+O(N^2) FP64 matvec on the host cores on a bounded row sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from dda_inputs import workload  # noqa: E402
+
+METRIC = "A.P matvecs/s (RHS x matvec per second) at tol 1e-5, FP32-refined vs FP64, time-to-solution"
+UNIT = "matvec/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="sphere64")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------ distributed --
+def dist_init(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("DDA_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend=backend)
+        return rank, world, dist
+    return 0, 1, None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x, device=None):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, x, device=None):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------- algorithmic traffic ----
+def pass_bytes(kind, info, R, ncomp_tables=1):
+    """Algorithmic bytes of one launch of a matvec pass over R right-hand sides:
+    the data the pass must read and write once (compact vectors, padded
+    intermediates, index map, Green-tensor octant)."""
+    s = 8 if kind.endswith("c64") else 16
+    nx, ny, nz = info["nx"], info["ny"], info["nz"]
+    Lx, Ly, Lz = info["Lx"], info["Ly"], info["Lz"]
+    N, M = info["ndipoles"], nx * ny * nz
+    u1 = 3 * nz * ny * Lx * s            # per RHS
+    u2 = 3 * nz * Ly * Lx * s
+    vec = 3 * N * s
+    oct_ = 6 * (Lx // 2 + 1) * (Ly // 2 + 1) * (Lz // 2 + 1) * s
+    if kind.startswith("x_fwd"):
+        return R * (vec + u1) + 4 * M
+    if kind.startswith("y_fwd") or kind.startswith("y_inv"):
+        return R * (u1 + u2)
+    if kind.startswith("z_conv"):
+        return R * 2 * u2 + oct_
+    if kind.startswith("x_inv"):
+        return R * (u1 + 2 * vec) + 4 * M + N
+    return None
+
+
+def pass_flops(kind, info, R):
+    """Algorithmic flops (5 L log2 L per complex FFT of length L, 66 per point
+    for the symmetric 3x3 complex product) of one launch over R RHS."""
+    nx, ny, nz = info["nx"], info["ny"], info["nz"]
+    Lx, Ly, Lz = info["Lx"], info["Ly"], info["Lz"]
+    f = lambda L: 5 * L * math.log2(L)  # noqa: E731
+    if kind.startswith("x_fwd") or kind.startswith("x_inv"):
+        return R * 3 * ny * nz * f(Lx)
+    if kind.startswith("y_fwd") or kind.startswith("y_inv"):
+        return R * 3 * nz * Lx * f(Ly)
+    if kind.startswith("z_conv"):
+        return R * (2 * 3 * Lx * Ly * f(Lz) + 66 * Lx * Ly * Lz)
+    return None
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 CUDA-core peak of GB300: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
+# (derivation and the microbenchmark behind it are in the design notes).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+# ------------------------------------------------------------- gb300 arm ----
+def run_gb300(args):
+    import torch
+    import paper_1202_3424_gb300 as dda
+
+    rank, world, dist = dist_init(args.gpus)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload(args.workload)
+    R = w.nrhs
+    ctx = dda.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    dda.dda_set_stream(ctx.handle, stream.cuda_stream)
+    ctx.set_target(w.grid)
+    ctx.set_materials(w.m)
+    t0 = time.perf_counter()
+    ctx.prepare_size_parameter(w.x, dda.Precision.FP32_REFINED)
+    prepare_ms = (time.perf_counter() - t0) * 1e3
+    info = ctx.info()
+    N = info["ndipoles"]
+    P_dev = torch.empty((R, 3, N), dtype=torch.complex128, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    def step(prec, tol=1e-5):
+        res, st = dda.dda_solve_device(ctx.handle, prec, w.khat, w.ehat, P_dev, tol=tol, maxit=2000)
+        if st != 0:
+            raise RuntimeError(f"solve failed: {[r['status_name'] for r in res]}")
+        return res
+
+    def timed(prec, steps, trace=False):
+        mv = 0
+        per = []
+        last = None
+        if trace:
+            dda.load_library().dda_profile_enable(ctx.handle, 1)
+        barrier(dist)
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            last = step(prec)
+            e1.record(stream)
+            e1.synchronize()
+            per.append(e0.elapsed_time(e1))
+            mv += sum(r["matvecs"] for r in last)
+        torch.cuda.synchronize()
+        barrier(dist)
+        stats = None
+        if trace:
+            stats = read_profile(dda, ctx)
+            dda.load_library().dda_profile_enable(ctx.handle, 0)
+        return per, mv, last, stats
+
+    # warm-up, then the timed K steps (FP32-refined, the production mode)
+    for _ in range(max(3, args.warmup)):
+        step(dda.Precision.FP32_REFINED)
+    clk = ClockSampler(local)
+    clk.start()
+    per, mv, res, _ = timed(dda.Precision.FP32_REFINED, args.steps)
+    clocks = clk.stop()
+    t_local = sum(per)
+    t_max = max_over_ranks(dist, t_local, dev)
+    mv_all = sum_over_ranks(dist, mv, dev)
+    value = mv_all / (t_max / 1e3)
+    ms_per_step = t_max / args.steps
+
+    # the same steps with launch tracing: per-kernel durations for the roofline
+    per_tr, mv_tr, _, kstats = timed(dda.Precision.FP32_REFINED, args.steps, trace=True)
+
+    # plain FP64 on the same GPU (same workload, one RHS batch per step)
+    step(dda.Precision.FP64)
+    per64, mv64, res64, _ = timed(dda.Precision.FP64, max(1, args.fp64_steps))
+    fp64 = {"time_to_solution_ms": sum(per64) / len(per64), "matvecs_per_s": mv64 / (sum(per64) / 1e3),
+            "iters": [r["iters"] for r in res64], "resid_rel": [r["resid_rel"] for r in res64]}
+
+    # end to end through the host-buffer C-ABI call (P copied back every step)
+    k = np.ascontiguousarray(w.khat)
+    e = np.ascontiguousarray(w.ehat)
+    ctx.solve(dda.Precision.FP32_REFINED, k, e, tol=1e-5, maxit=2000)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mv_e2e = 0
+    for _ in range(args.steps):
+        r_e2e, P_host, st = ctx.solve(dda.Precision.FP32_REFINED, k, e, tol=1e-5, maxit=2000)
+        mv_e2e += sum(r["matvecs"] for r in r_e2e)
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(dist, time.perf_counter() - t0, dev)
+    e2e = {"value": sum_over_ranks(dist, mv_e2e, dev) / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": int(k.nbytes + e.nbytes), "d2h_bytes_per_step": int(P_host.nbytes + 72 * R),
+           "time_to_solution_ms": t_e2e * 1e3 / args.steps}
+
+    roof = roofline(kstats, info, R)
+    launches = int(sum(s["launches"] for s in kstats.values()) / args.steps) * args.steps if kstats else 0
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, info, budget_s=12.0)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64 matvec / f64 refinement", "data": "synthetic",
+            "config": {"workload": f"{w.name}: {info['nx']}^3 sphere, N={N} dipoles, m={w.m[0]}, x={w.x}, "
+                                   f"{R} RHS (k along x, 2 polarizations), tol 1e-5",
+                       "global_batch": R * world, "padded_grid": [info["Lx"], info["Ly"], info["Lz"]],
+                       "parallelism": f"rhs-sharded x{world}", "l2": "256 MB buffer written between steps"},
+            "time_to_solution_ms": ms_per_step,
+            "iters": [r["iters"] for r in res], "outer_iters": [r["outer_iters"] for r in res],
+            "matvecs_per_step": mv / args.steps, "resid_rel": [r["resid_rel"] for r in res],
+            "q": [[r["qext"], r["qabs"], r["qsca"]] for r in res],
+            "fp64_plain": fp64, "speedup_vs_fp64": fp64["time_to_solution_ms"] / ms_per_step,
+            "prepare_ms": prepare_ms,
+            "traced_ms_per_step": sum(per_tr) / len(per_tr),
+            "kernels": {k_: {"launches": v["launches"], "ms": v["ms"], "share": v["share"]} for k_, v in kstats.items()},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def read_profile(dda, ctx):
+    import ctypes
+
+    class Stat(ctypes.Structure):
+        _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                    ("units", ctypes.c_double)]
+
+    lib = dda.load_library()
+    lib.dda_profile_read.argtypes = [ctypes.c_void_p, ctypes.POINTER(Stat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    arr = (Stat * 64)()
+    n = ctypes.c_int()
+    lib.dda_profile_read(ctx.handle, arr, 64, ctypes.byref(n))
+    out = {}
+    total = sum(arr[i].total_ms for i in range(n.value))
+    for i in range(n.value):
+        out[arr[i].name.decode()] = {"launches": arr[i].launches, "ms": arr[i].total_ms, "units": arr[i].units,
+                                     "share": arr[i].total_ms / total if total else 0.0}
+    return out
+
+
+def roofline(kstats, info, R):
+    if not kstats:
+        return None
+    hbm, src = load_peaks()
+    # dominant kernel among the matvec passes (the hot path's bulk)
+    cands = {k: v for k, v in kstats.items() if pass_bytes(k, info, 1) is not None}
+    name = max(cands, key=lambda k: cands[k]["ms"])
+    v = cands[name]
+    avg_ms = v["ms"] / v["launches"]
+    units_per_launch = v["units"] / v["launches"]
+    if name.endswith("c128"):
+        fl = pass_flops(name, info, units_per_launch)
+        ach = fl / (avg_ms / 1e3) / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "avg_launch_ms": avg_ms,
+                "rhs_per_launch": units_per_launch, "peak_source": "derived FP64 (152 SM x 2 DFMA/clk x 2.07 GHz)"}
+    b = pass_bytes(name, info, units_per_launch)
+    ach = b / (avg_ms / 1e3) / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": None, "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": b,
+            "rhs_per_launch": units_per_launch, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
+
+
+# ----------------------------------------------------------- CPU baseline ----
+def _oracle_rows_rate(w, budget_s, kd):
+    """Rows of A.P per second of the oracle's pairwise matvec on this host."""
+    from oracle import dda as odda
+    from oracle import pairwise
+    r, comp = odda.site_positions(w.grid)
+    N = len(r)
+    eps = (np.asarray(w.m) ** 2)[comp - 1]
+    beta = odda.ldr_inverse_polarizability(eps, kd, w.khat[0], w.ehat[0])
+    P = np.random.default_rng(1).standard_normal((N, 3)) + 0j
+    rng = np.random.default_rng(2)
+    nrows = 64
+    t0 = time.perf_counter()
+    _, nt = pairwise.matvec(r, kd, beta, P, rows=rng.choice(N, nrows, replace=False))
+    dt = time.perf_counter() - t0
+    nrows = max(64, int(nrows * budget_s / max(dt, 1e-6)))
+    nrows = min(nrows, N)
+    t0 = time.perf_counter()
+    _, nt = pairwise.matvec(r, kd, beta, P, rows=rng.choice(N, nrows, replace=False))
+    dt = time.perf_counter() - t0
+    return nrows / dt, nrows, N, nt, dt
+
+
+def cpu_baseline(w, info, budget_s=12.0):
+    rate, nrows, N, nt, dt = _oracle_rows_rate(w, budget_s, info["kd"])
+    return {"value": rate / N, "unit": UNIT, "cores": nt, "kind": "oracle",
+            "sample": f"oracle pairwise O(N^2) FP64 matvec (C/OpenMP) on {nrows} of {N} rows of one A.P "
+                      f"({dt:.1f} s), extrapolated to full RHS-matvecs per second"}
+
+
+# --------------------------------------------------------- reference arm ----
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import dda as odda
+    w = workload(args.workload)
+    N = w.ndipoles
+    kd = odda.kd_from_size_parameter(w.x, N)
+    per = []
+    for i in range(args.warmup + args.steps):
+        rate, nrows, N, nt, dt = _oracle_rows_rate(w, 4.0, kd)
+        if i >= args.warmup:
+            per.append((rate, nrows, dt))
+    rates = [p[0] for p in per]
+    value = statistics.median(rates) / N
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median([p[2] for p in per]),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"{w.name}, N={N} dipoles, {w.nrhs} RHS"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
+                             "sample": f"per step: {per[0][1]} of {N} rows of the pairwise O(N^2) matvec, "
+                                       f"extrapolated to full matvecs"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gb300(a)

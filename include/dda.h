@@ -160,6 +160,21 @@ dda_status dda_grad_qabs(dda_ctx* ctx, dda_precision precision, const double* kh
                          const dda_opts* opts, double* dq_dre_eps, double* dq_dim_eps, double* P_out,
                          dda_result* res);
 
+/* Launch tracing (the guide's TIMEIT timing switch, per kernel kind rather than
+ * per run): when on, every hot-path kernel launch is bracketed by CUDA events
+ * on the stream it runs on -- also inside replayed CUDA graphs -- and its
+ * duration is accumulated per kernel kind.  `units` sums the right-hand sides
+ * each launch processed.  Enabling resets the counters.                        */
+typedef struct {
+    char name[24];      /* kernel kind, e.g. "z_conv_c64"                                */
+    int64_t launches;
+    double total_ms;
+    double units;
+} dda_kernel_stat;
+dda_status dda_profile_enable(dda_ctx* ctx, int on);
+/* Fills up to max_entries kinds that launched at least once; *n_entries = all such kinds. */
+dda_status dda_profile_read(const dda_ctx* ctx, dda_kernel_stat* out, int max_entries, int* n_entries);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,6 +15,7 @@
 #include "dda.h"
 #include "internal.h"
 #include "krylov.h"
+#include "profiler.h"
 
 using cd = std::complex<double>;
 using namespace dda;
@@ -37,6 +38,7 @@ template <typename T> struct Inner {
 
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
+    bool traced = false;  // captured with launch tracing on
     int R = 0;
     int prec = -1;
     int K = 0;
@@ -73,6 +75,7 @@ struct dda_ctx {
     int ws_R = 0;
     GraphEntry graph;
     int* h_count = nullptr;  // pinned
+    Profiler prof;
 
     dda_status fail(dda_status code, const char* fmt, ...) {
         char buf[512];
@@ -97,6 +100,18 @@ struct dda_ctx {
     } while (0)
 
 namespace {
+
+// Synchronize the context stream and, with tracing on, read the launch events.
+cudaError_t sync_collect(dda_ctx* ctx) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess && ctx->prof.on) e = ctx->prof.collect();
+    return e;
+}
+
+struct ProfScope {
+    explicit ProfScope(dda_ctx* c) { set_current_profiler(c ? &c->prof : nullptr); }
+    ~ProfScope() { set_current_profiler(nullptr); }
+};
 
 // Workspace slots (each a device buffer grown on demand).
 enum Slot {
@@ -216,7 +231,7 @@ dda_status upload_tables(dda_ctx* ctx, int R, const std::vector<double>& k, cons
     CU(cudaMemcpyAsync(ctx->pool[S_KHAT].p, k.data(), k.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(ctx->pool[S_EPOL].p, e2.data(), e2.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
     // the host vectors go out of scope: finish the copies first
-    CU(cudaStreamSynchronize(ctx->stream));
+    CU(sync_collect(ctx));
     return DDA_OK;
 }
 
@@ -326,14 +341,15 @@ template <typename T> dda_status inner_solve(dda_ctx* ctx, int R, int maxit, boo
     const int max_blocks = maxit / K + 2;
     dda_status rs;
     bool have_graph = ctx->graph.exec && ctx->graph.R == R && ctx->graph.prec == prec && ctx->graph.K == K &&
-                      ctx->graph.stream == ctx->stream;
+                      ctx->graph.stream == ctx->stream && ctx->graph.traced == ctx->prof.on;
     for (int b = 0; b < max_blocks; ++b) {
         if (use_graph && have_graph) {
             CU(cudaGraphLaunch(ctx->graph.exec, ctx->stream));
+            if (ctx->prof.on) ctx->prof.graph_launched();
         } else if ((rs = inner_block<T>(ctx, R, K)) != DDA_OK) {
             return rs;
         }
-        CU(cudaStreamSynchronize(ctx->stream));
+        CU(sync_collect(ctx));
         if (*ctx->h_count == 0) break;
         if (use_graph && !have_graph) {
             if (ctx->graph.exec) {
@@ -341,9 +357,11 @@ template <typename T> dda_status inner_solve(dda_ctx* ctx, int R, int maxit, boo
                 ctx->graph.exec = nullptr;
             }
             cudaGraph_t graph = nullptr;
+            ctx->prof.capture_begin();
             CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
             rs = inner_block<T>(ctx, R, K);
             cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+            ctx->prof.capture_end();
             if (rs != DDA_OK) {
                 if (graph) cudaGraphDestroy(graph);
                 return rs;
@@ -356,6 +374,7 @@ template <typename T> dda_status inner_solve(dda_ctx* ctx, int R, int maxit, boo
             ctx->graph.prec = prec;
             ctx->graph.K = K;
             ctx->graph.stream = ctx->stream;
+            ctx->graph.traced = ctx->prof.on;
             have_graph = true;
         }
     }
@@ -430,7 +449,7 @@ dda_status solve_core(dda_ctx* ctx, int R, const dda_opts& o, bool refine, bool 
     }
     CU(cudaMemcpyAsync(hb.data(), ctx->pool[S_NORM_B].p, R * sizeof(double), cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(hr.data(), ctx->pool[S_NORM_R].p, R * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CU(cudaStreamSynchronize(s));
+    CU(sync_collect(ctx));
     for (int r = 0; r < R; ++r) {
         tr[r].bn = std::sqrt(hb[r]);
         tr[r].rn = std::sqrt(hr[r]);
@@ -483,7 +502,7 @@ dda_status solve_core(dda_ctx* ctx, int R, const dda_opts& o, bool refine, bool 
         if ((rs = run_matvec<double>(ctx, R, X, Y, outer)) != DDA_OK) return rs;
         CU(launch_residual(R, n, E, Y, Rr, slot<double>(ctx, S_NORM_R), outer, part, cnt, s));
         CU(cudaMemcpyAsync(hr.data(), ctx->pool[S_NORM_R].p, R * sizeof(double), cudaMemcpyDeviceToHost, s));
-        CU(cudaStreamSynchronize(s));
+        CU(sync_collect(ctx));
         for (int r = 0; r < R; ++r) {
             if (!hact[r]) continue;
             RhsTrack& t = tr[r];
@@ -604,10 +623,10 @@ dda_status forward_solve(dda_ctx* ctx, dda_precision prec, int R, const double* 
         std::vector<double> a(R), b(R);
         CU(cudaMemcpyAsync(a.data(), ctx->pool[S_NORM_R].p, R * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
         CU(cudaMemcpyAsync(b.data(), ctx->pool[S_NORM_B].p, R * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-        CU(cudaStreamSynchronize(ctx->stream));
+        CU(sync_collect(ctx));
         for (int r = 0; r < R; ++r) ne[r] = std::sqrt(a[r] / b[r]);
     }
-    CU(cudaStreamSynchronize(ctx->stream));
+    CU(sync_collect(ctx));
     const double kd = ctx->kd, a2 = ctx->aeff_lat * ctx->aeff_lat;
     dda_status worst = DDA_OK;
     for (int r = 0; r < R; ++r) {
@@ -680,6 +699,7 @@ dda_status dda_destroy(dda_ctx* ctx) {
         free_mem(ctx->m_tw64[a]);
         free_mem(ctx->m_tw32[a]);
     }
+    ctx->prof.release();
     if (ctx->h_count) cudaFreeHost(ctx->h_count);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
@@ -770,6 +790,7 @@ dda_status dda_set_materials(dda_ctx* ctx, int ncomp, const double* m_complex, d
 
 dda_status dda_prepare(dda_ctx* ctx, double lambda_vac, double aeff, dda_precision precision) {
     if (!ctx) return DDA_ERR_ARG;
+    ProfScope prof_scope(ctx);
     if (!ctx->has_target || !ctx->has_materials) return ctx->fail(DDA_ERR_ARG, "set target and materials first");
     if ((int)ctx->m.size() < ctx->max_code)
         return ctx->fail(DDA_ERR_ARG, "grid uses composition %d but only %d indices given", ctx->max_code, (int)ctx->m.size());
@@ -805,7 +826,7 @@ dda_status dda_prepare(dda_ctx* ctx, double lambda_vac, double aeff, dda_precisi
     if (precision != DDA_FP64) {
         if ((s = ensure(ctx, ctx->m_gh32, oct * sizeof(float2))) != DDA_OK) return s;
         CU(launch_convert_c128_to_c64((const double2*)ctx->m_gh64.p, (float2*)ctx->m_gh32.p, oct, ctx->stream));
-        CU(cudaStreamSynchronize(ctx->stream));
+        CU(sync_collect(ctx));
         ctx->has32 = true;
     }
     ctx->prepared = true;
@@ -836,13 +857,14 @@ dda_status dda_get_info(const dda_ctx* ctx, dda_info* info) {
 dda_status dda_solve(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* e,
                      const dda_opts* opts, double* P_out, dda_result* res) {
     if (!ctx) return DDA_ERR_ARG;
+    ProfScope prof_scope(ctx);
     cudaSetDevice(ctx->device);
     dda_status st = forward_solve(ctx, precision, R, khat, e, opts, res);
     if (st != DDA_OK && st != DDA_ERR_NOT_CONVERGED && st != DDA_ERR_BREAKDOWN) return st;
     if (P_out) {
         const size_t bytes = (size_t)R * 3 * ctx->g.N * sizeof(double2);
         CU(cudaMemcpyAsync(P_out, ctx->pool[S_X64].p, bytes, cudaMemcpyDeviceToHost, ctx->stream));
-        CU(cudaStreamSynchronize(ctx->stream));
+        CU(sync_collect(ctx));
     }
     return st;
 }
@@ -850,13 +872,14 @@ dda_status dda_solve(dda_ctx* ctx, dda_precision precision, int R, const double*
 dda_status dda_solve_device(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* e,
                             const dda_opts* opts, void* P_dev, dda_result* res) {
     if (!ctx) return DDA_ERR_ARG;
+    ProfScope prof_scope(ctx);
     cudaSetDevice(ctx->device);
     dda_status st = forward_solve(ctx, precision, R, khat, e, opts, res);
     if (st != DDA_OK && st != DDA_ERR_NOT_CONVERGED && st != DDA_ERR_BREAKDOWN) return st;
     if (P_dev) {
         const size_t bytes = (size_t)R * 3 * ctx->g.N * sizeof(double2);
         CU(cudaMemcpyAsync(P_dev, ctx->pool[S_X64].p, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
-        CU(cudaStreamSynchronize(ctx->stream));
+        CU(sync_collect(ctx));
     }
     return st;
 }
@@ -881,17 +904,19 @@ static dda_status matvec_common(dda_ctx* ctx, dda_precision precision, int R, co
 dda_status dda_matvec_device(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* e,
                              const void* x_dev, void* y_dev) {
     if (!ctx) return DDA_ERR_ARG;
+    ProfScope prof_scope(ctx);
     if (!x_dev || !y_dev) return ctx->fail(DDA_ERR_ARG, "NULL vector");
     cudaSetDevice(ctx->device);
     dda_status rs = matvec_common(ctx, precision, R, khat, e, x_dev, y_dev);
     if (rs != DDA_OK) return rs;
-    CU(cudaStreamSynchronize(ctx->stream));
+    CU(sync_collect(ctx));
     return DDA_OK;
 }
 
 dda_status dda_matvec(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* e,
                       const double* x, double* y) {
     if (!ctx) return DDA_ERR_ARG;
+    ProfScope prof_scope(ctx);
     if (!x || !y) return ctx->fail(DDA_ERR_ARG, "NULL vector");
     if (!ctx->prepared) return ctx->fail(DDA_ERR_ARG, "dda_prepare has not been called");
     if (R <= 0) return ctx->fail(DDA_ERR_ARG, "R must be > 0");
@@ -915,12 +940,13 @@ dda_status dda_matvec(dda_ctx* ctx, dda_precision precision, int R, const double
             return rs;
     }
     CU(cudaMemcpyAsync(y, ctx->pool[S_Y64].p, n * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
+    CU(sync_collect(ctx));
     return DDA_OK;
 }
 
 dda_status dda_incident_field(dda_ctx* ctx, int R, const double* khat, const double* e, double* E_out) {
     if (!ctx) return DDA_ERR_ARG;
+    ProfScope prof_scope(ctx);
     if (!E_out) return ctx->fail(DDA_ERR_ARG, "NULL output");
     dda_status rs;
     if ((rs = check_ready(ctx, DDA_FP64)) != DDA_OK) return rs;
@@ -934,7 +960,7 @@ dda_status dda_incident_field(dda_ctx* ctx, int R, const double* khat, const dou
     CU(launch_einc(R, ctx->g.N, ctx->tg.lat_of, ctx->g.nx, ctx->g.ny, ctx->g.nz, ctx->kd, slot<double>(ctx, S_KHAT),
                    slot<double2>(ctx, S_EPOL), slot<double2>(ctx, S_E64), ctx->stream));
     CU(cudaMemcpyAsync(E_out, ctx->pool[S_E64].p, bytes, cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
+    CU(sync_collect(ctx));
     return DDA_OK;
 }
 
@@ -942,6 +968,7 @@ dda_status dda_grad_qabs(dda_ctx* ctx, dda_precision precision, const double* kh
                          const dda_opts* opts, double* dq_dre_eps, double* dq_dim_eps, double* P_out,
                          dda_result* res) {
     if (!ctx) return DDA_ERR_ARG;
+    ProfScope prof_scope(ctx);
     if (!dq_dre_eps || !dq_dim_eps || !res) return ctx->fail(DDA_ERR_ARG, "NULL output");
     cudaSetDevice(ctx->device);
     dda_status st = forward_solve(ctx, precision, 1, khat, e, opts, &res[0]);
@@ -990,7 +1017,35 @@ dda_status dda_grad_qabs(dda_ctx* ctx, dda_precision precision, const double* kh
     CU(cudaMemcpyAsync(dq_dre_eps, g, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaMemcpyAsync(dq_dim_eps, g + N, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     if (P_out) CU(cudaMemcpyAsync(P_out, Pkeep, n * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
+    CU(sync_collect(ctx));
+    return DDA_OK;
+}
+
+dda_status dda_profile_enable(dda_ctx* ctx, int on) {
+    if (!ctx) return DDA_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return ctx->cuda_fail(cudaGetLastError(), "sync");
+    ctx->prof.reset();
+    ctx->prof.on = on != 0;
+    return DDA_OK;
+}
+
+dda_status dda_profile_read(const dda_ctx* ctx, dda_kernel_stat* out, int max_entries, int* n_entries) {
+    if (!ctx || !n_entries || (max_entries > 0 && !out)) return DDA_ERR_ARG;
+    int n = 0;
+    for (int k = 0; k < KK_COUNT; ++k) {
+        if (ctx->prof.launches[k] == 0) continue;
+        if (n < max_entries) {
+            dda_kernel_stat& st = out[n];
+            std::memset(&st, 0, sizeof st);
+            std::snprintf(st.name, sizeof st.name, "%s", kernel_kind_name(k));
+            st.launches = ctx->prof.launches[k];
+            st.total_ms = ctx->prof.ms[k];
+            st.units = ctx->prof.unit_sum[k];
+        }
+        ++n;
+    }
+    *n_entries = n;
     return DDA_OK;
 }
 

@@ -18,47 +18,60 @@
 
 #include "internal.h"
 #include "krylov.h"
+#include "profiler.h"
 
 namespace dda {
 
 static constexpr int kThreads = 256;
 
 // ---- reductions ------------------------------------------------------------------
-template <int ND>
-__device__ __forceinline__ void block_reduce(double2 (&v)[ND]) {
+// Block sum of ND complex partials.  Warp-level sums run in the precision of
+// the partials (float for complex64 vectors: FP64 shuffles and adds run at
+// ~1/60 of the FP32 rate here); the per-warp results are summed in FP64.
+template <typename R, int ND>
+__device__ __forceinline__ void block_reduce(R (&vx)[ND], R (&vy)[ND], double2 (&out)[ND]) {
     __shared__ double2 sh[32 * ND];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
     for (int d = 0; d < ND; ++d)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            v[d].x += __shfl_xor_sync(0xffffffffu, v[d].x, o);
-            v[d].y += __shfl_xor_sync(0xffffffffu, v[d].y, o);
+            vx[d] += __shfl_xor_sync(0xffffffffu, vx[d], o);
+            vy[d] += __shfl_xor_sync(0xffffffffu, vy[d], o);
         }
     __syncthreads();
     if (lane == 0)
 #pragma unroll
-        for (int d = 0; d < ND; ++d) sh[warp * ND + d] = v[d];
+        for (int d = 0; d < ND; ++d) sh[warp * ND + d] = make_double2((double)vx[d], (double)vy[d]);
     __syncthreads();
-    if (warp == 0) {
 #pragma unroll
-        for (int d = 0; d < ND; ++d) {
-            v[d] = lane < nw ? sh[lane * ND + d] : make_double2(0.0, 0.0);
+    for (int d = 0; d < ND; ++d) out[d] = make_double2(0.0, 0.0);
+    if (threadIdx.x == 0)
+        for (int w = 0; w < nw; ++w)
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                v[d].x += __shfl_xor_sync(0xffffffffu, v[d].x, o);
-                v[d].y += __shfl_xor_sync(0xffffffffu, v[d].y, o);
+            for (int d = 0; d < ND; ++d) {
+                out[d].x += sh[w * ND + d].x;
+                out[d].y += sh[w * ND + d].y;
             }
-        }
-    }
 }
 
-// Store this block's partial sums; the last block to arrive gets the totals
-// in thread 0's v[] and returns true (in every thread of that block).
 template <int ND>
-__device__ __forceinline__ bool last_block_total(double2 (&v)[ND], double2* partials, unsigned* counter) {
+__device__ __forceinline__ void block_reduce(double2 (&v)[ND]) {
+    double vx[ND], vy[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        vx[d] = v[d].x;
+        vy[d] = v[d].y;
+    }
+    block_reduce<double, ND>(vx, vy, v);
+}
+
+// Store this block's partial sums (block totals already in thread 0's v[]);
+// the last block to arrive gets the grand totals in thread 0's v[] and
+// returns true (in every thread of that block).
+template <int ND>
+__device__ __forceinline__ bool last_block_total_reduced(double2 (&v)[ND], double2* partials, unsigned* counter) {
     __shared__ bool is_last;
-    block_reduce<ND>(v);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int d = 0; d < ND; ++d) partials[blockIdx.x * ND + d] = v[d];
@@ -86,12 +99,40 @@ __device__ __forceinline__ bool last_block_total(double2 (&v)[ND], double2* part
     return true;
 }
 
+// Same, starting from per-thread FP64 partials.
+template <int ND>
+__device__ __forceinline__ bool last_block_total(double2 (&v)[ND], double2* partials, unsigned* counter) {
+    block_reduce<ND>(v);
+    return last_block_total_reduced<ND>(v, partials, counter);
+}
+
 __device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
 
-// conj(a) * b accumulated in FP64
-template <typename C> __device__ __forceinline__ void acc_cdot(double2& acc, C a, C b) {
-    acc.x += (double)a.x * (double)b.x + (double)a.y * (double)b.y;
-    acc.y += (double)a.x * (double)b.y - (double)a.y * (double)b.x;
+// Per-thread dot-product accumulator in the vector precision; the block
+// reduction sums warps in that precision and warp totals in FP64.  A thread
+// sees a few elements per RHS (see reduce_blocks), so FP32 partial sums keep
+// ~1e-6 relative accuracy, ample for the Krylov scalars of the inner solve.
+template <typename C> struct DotAcc {
+    using T = typename real_of<C>::type;
+    T re = 0, im = 0;
+    __device__ __forceinline__ void add_cdot(C a, C b) {  // += conj(a) * b
+        re += a.x * b.x + a.y * b.y;
+        im += a.x * b.y - a.y * b.x;
+    }
+    __device__ __forceinline__ void add_norm2(C a) { re += a.x * a.x + a.y * a.y; }
+};
+
+// Block totals of ND accumulators (result valid in thread 0).
+template <typename C, int ND>
+__device__ __forceinline__ void block_totals(DotAcc<C> (&a)[ND], double2 (&out)[ND]) {
+    using T = typename real_of<C>::type;
+    T vx[ND], vy[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        vx[d] = a[d].re;
+        vy[d] = a[d].im;
+    }
+    block_reduce<T, ND>(vx, vy, out);
 }
 
 __device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
@@ -123,7 +164,7 @@ __global__ void __launch_bounds__(kThreads)
     const int r = blockIdx.y;
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t off = (int64_t)r * n;
-    double2 acc[1] = {make_double2(0.0, 0.0)};
+    DotAcc<C> d[1];
     for (int64_t i = i0; i < n; i += stride) {
         const C bi = b[off + i];
         x[off + i] = czero<C>();
@@ -131,9 +172,11 @@ __global__ void __launch_bounds__(kThreads)
         rhat[off + i] = bi;
         p[off + i] = czero<C>();
         v[off + i] = czero<C>();
-        acc[0].x += (double)bi.x * bi.x + (double)bi.y * bi.y;
+        d[0].add_norm2(bi);
     }
-    if (last_block_total<1>(acc, part + (int64_t)r * gridDim.x, cnt + r) && threadIdx.x == 0) {
+    double2 acc[1];
+    block_totals<C, 1>(d, acc);
+    if (last_block_total_reduced<1>(acc, part + (int64_t)r * gridDim.x, cnt + r) && threadIdx.x == 0) {
         KState s = st[r];
         const double bn = sqrt(acc[0].x);
         s.bnorm = bn;
@@ -179,9 +222,11 @@ __global__ void __launch_bounds__(kThreads)
             int* __restrict__ active, double2* __restrict__ part, unsigned* __restrict__ cnt) {
     RHS_PROLOGUE(active)
     const int64_t off = (int64_t)r * n;
-    double2 acc[1] = {make_double2(0.0, 0.0)};
-    for (int64_t i = i0; i < n; i += stride) acc_cdot(acc[0], rhat[off + i], v[off + i]);
-    if (last_block_total<1>(acc, part + (int64_t)r * gridDim.x, cnt + r) && threadIdx.x == 0) {
+    DotAcc<C> d[1];
+    for (int64_t i = i0; i < n; i += stride) d[0].add_cdot(rhat[off + i], v[off + i]);
+    double2 acc[1];
+    block_totals<C, 1>(d, acc);
+    if (last_block_total_reduced<1>(acc, part + (int64_t)r * gridDim.x, cnt + r) && threadIdx.x == 0) {
         KState s = st[r];
         const double2 sig = acc[0];
         if (!finite2(sig)) {
@@ -215,13 +260,15 @@ __global__ void __launch_bounds__(kThreads)
             int* __restrict__ active, double2* __restrict__ part, unsigned* __restrict__ cnt) {
     RHS_PROLOGUE(active)
     const int64_t off = (int64_t)r * n;
-    double2 acc[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+    DotAcc<C> d[2];
     for (int64_t i = i0; i < n; i += stride) {
         const C ti = t[off + i];
-        acc_cdot(acc[0], ti, s_[off + i]);
-        acc[1].x += (double)ti.x * ti.x + (double)ti.y * ti.y;
+        d[0].add_cdot(ti, s_[off + i]);
+        d[1].add_norm2(ti);
     }
-    if (last_block_total<2>(acc, part + (int64_t)r * gridDim.x * 2, cnt + r) && threadIdx.x == 0) {
+    double2 acc[2];
+    block_totals<C, 2>(d, acc);
+    if (last_block_total_reduced<2>(acc, part + (int64_t)r * gridDim.x * 2, cnt + r) && threadIdx.x == 0) {
         KState s = st[r];
         if (!finite2(acc[0]) || !isfinite(acc[1].x)) {
             s.status = KS_NONFINITE;
@@ -242,16 +289,18 @@ __global__ void __launch_bounds__(kThreads)
     RHS_PROLOGUE(active)
     const C alpha = from2<C>(st[r].alpha), omega = from2<C>(st[r].omega);
     const int64_t off = (int64_t)r * n;
-    double2 acc[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+    DotAcc<C> d[2];
     for (int64_t i = i0; i < n; i += stride) {
         const C si = s_[off + i];
         x[off + i] = cadd(x[off + i], cadd(cmul(alpha, p[off + i]), cmul(omega, si)));
         const C ri = csub(si, cmul(omega, t[off + i]));
         r_[off + i] = ri;
-        acc_cdot(acc[0], rhat[off + i], ri);
-        acc[1].x += (double)ri.x * ri.x + (double)ri.y * ri.y;
+        d[0].add_cdot(rhat[off + i], ri);
+        d[1].add_norm2(ri);
     }
-    if (last_block_total<2>(acc, part + (int64_t)r * gridDim.x * 2, cnt + r) && threadIdx.x == 0) {
+    double2 acc[2];
+    block_totals<C, 2>(d, acc);
+    if (last_block_total_reduced<2>(acc, part + (int64_t)r * gridDim.x * 2, cnt + r) && threadIdx.x == 0) {
         KState s = st[r];
         const double rn = sqrt(acc[1].x);
         s.rnorm = rn;
@@ -431,7 +480,7 @@ __global__ void __launch_bounds__(kThreads)
 
 // ---- host launchers --------------------------------------------------------------
 int reduce_blocks(int64_t n) {
-    int64_t b = (n + kThreads * 8 - 1) / (kThreads * 8);
+    int64_t b = (n + kThreads * 4 - 1) / (kThreads * 4);
     if (b > kMaxReduceBlocks) b = kMaxReduceBlocks;
     return (int)(b < 1 ? 1 : b);
 }
@@ -440,95 +489,129 @@ template <typename C>
 cudaError_t KrylovOps<C>::init(int R, int64_t n, const C* b, C* x, C* r, C* rhat, C* p, C* v, KState* st,
                                const double* tol_rel, const int* want, int* active, double2* part, unsigned* cnt,
                                cudaStream_t s) {
+    PROF_BEGIN(s);
     k_init<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, b, x, r, rhat, p, v, st, tol_rel, want, active, part,
                                                               cnt);
+    PROF_END((sizeof(C) == 8 ? KK_KRYLOV_C64 : KK_KRYLOV_C128), R, s);
     return cudaGetLastError();
 }
 template <typename C>
 cudaError_t KrylovOps<C>::update_p(int R, int64_t n, C* p, const C* r, const C* v, const KState* st,
                                    const int* active, cudaStream_t s) {
+    PROF_BEGIN(s);
     k_update_p<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, p, r, v, st, active);
+    PROF_END((sizeof(C) == 8 ? KK_KRYLOV_C64 : KK_KRYLOV_C128), R, s);
     return cudaGetLastError();
 }
 template <typename C>
 cudaError_t KrylovOps<C>::alpha(int R, int64_t n, const C* rhat, const C* v, KState* st, int* active, double2* part,
                                 unsigned* cnt, cudaStream_t s) {
+    PROF_BEGIN(s);
     k_alpha<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, rhat, v, st, active, part, cnt);
+    PROF_END((sizeof(C) == 8 ? KK_KRYLOV_C64 : KK_KRYLOV_C128), R, s);
     return cudaGetLastError();
 }
 template <typename C>
 cudaError_t KrylovOps<C>::update_s(int R, int64_t n, C* s_, const C* r, const C* v, const KState* st,
                                    const int* active, cudaStream_t s) {
+    PROF_BEGIN(s);
     k_update_s<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, s_, r, v, st, active);
+    PROF_END((sizeof(C) == 8 ? KK_KRYLOV_C64 : KK_KRYLOV_C128), R, s);
     return cudaGetLastError();
 }
 template <typename C>
 cudaError_t KrylovOps<C>::omega(int R, int64_t n, const C* t, const C* s_, KState* st, int* active, double2* part,
                                 unsigned* cnt, cudaStream_t s) {
+    PROF_BEGIN(s);
     k_omega<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, t, s_, st, active, part, cnt);
+    PROF_END((sizeof(C) == 8 ? KK_KRYLOV_C64 : KK_KRYLOV_C128), R, s);
     return cudaGetLastError();
 }
 template <typename C>
 cudaError_t KrylovOps<C>::update_xr(int R, int64_t n, C* x, const C* p, const C* s_, const C* t, C* r,
                                     const C* rhat, KState* st, int* active, double2* part, unsigned* cnt,
                                     cudaStream_t s) {
+    PROF_BEGIN(s);
     k_update_xr<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, x, p, s_, t, r, rhat, st, active, part, cnt);
+    PROF_END((sizeof(C) == 8 ? KK_KRYLOV_C64 : KK_KRYLOV_C128), R, s);
     return cudaGetLastError();
 }
 template <typename C>
 cudaError_t KrylovOps<C>::to_inner(int R, int64_t n, const double2* r64, C* bin, const double* scale,
                                    const int* active, cudaStream_t s) {
+    PROF_BEGIN(s);
     k_to_inner<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, r64, bin, scale, active);
+    PROF_END(KK_REFINE, R, s);
     return cudaGetLastError();
 }
 template <typename C>
 cudaError_t KrylovOps<C>::accumulate(int R, int64_t n, double2* x64, const C* xin, const double* coef,
                                      const int* active, cudaStream_t s) {
+    PROF_BEGIN(s);
     k_accumulate<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, x64, xin, coef, active);
+    PROF_END(KK_REFINE, R, s);
     return cudaGetLastError();
 }
 template struct KrylovOps<float2>;
 template struct KrylovOps<double2>;
 
 cudaError_t launch_count_active(const int* active, int R, int* out, cudaStream_t s) {
+    PROF_BEGIN(s);
     k_count_active<<<1, 32, 0, s>>>(active, R, out);
+    PROF_END(KK_OTHER, 1, s);
     return cudaGetLastError();
 }
 cudaError_t launch_residual(int R, int64_t n, const double2* a, const double2* b, double2* out_vec, double* out_norm2,
                             const int* active, double2* part, unsigned* cnt, cudaStream_t s) {
+    PROF_BEGIN(s);
     k_residual<<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, a, b, out_vec, out_norm2, active, part, cnt);
+    PROF_END(KK_REFINE, R, s);
     return cudaGetLastError();
 }
 cudaError_t launch_conj_diff(int R, int64_t n, const double2* a, const double2* b, double2* out, cudaStream_t s) {
+    PROF_BEGIN(s);
     k_conj_diff<<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, a, b, out);
+    PROF_END(KK_REFINE, R, s);
     return cudaGetLastError();
 }
 cudaError_t launch_c64_to_c128(int64_t n, const float2* s_, double2* d, cudaStream_t s) {
+    PROF_BEGIN(s);
     k_convert<double2, float2><<<reduce_blocks(n), kThreads, 0, s>>>(n, s_, d);
+    PROF_END(KK_REFINE, 1, s);
     return cudaGetLastError();
 }
 cudaError_t launch_c128_to_c64v(int64_t n, const double2* s_, float2* d, cudaStream_t s) {
+    PROF_BEGIN(s);
     k_convert<float2, double2><<<reduce_blocks(n), kThreads, 0, s>>>(n, s_, d);
+    PROF_END(KK_REFINE, 1, s);
     return cudaGetLastError();
 }
 cudaError_t launch_einc(int R, int64_t N, const int* lat_of, int nx, int ny, int nz, double kd, const double* khat,
                         const double2* e, double2* E, cudaStream_t s) {
+    PROF_BEGIN(s);
     k_einc<<<dim3(reduce_blocks(N), R), kThreads, 0, s>>>(N, lat_of, nx, ny, nz, kd, khat, e, E);
+    PROF_END(KK_EINC, R, s);
     return cudaGetLastError();
 }
 cudaError_t launch_qsums(int R, int64_t N, const double2* E, const double2* P, const uint8_t* comp_of, const double* w,
                          int w_stride, double2* sums, double2* part, unsigned* cnt, cudaStream_t s) {
+    PROF_BEGIN(s);
     k_qsums<<<dim3(reduce_blocks(N), R), kThreads, 0, s>>>(N, E, P, comp_of, w, w_stride, sums, part, cnt);
+    PROF_END(KK_QSUMS, R, s);
     return cudaGetLastError();
 }
 cudaError_t launch_adjoint_rhs(int64_t N, const double2* P, const uint8_t* comp_of, const double* w, double2* b,
                                cudaStream_t s) {
+    PROF_BEGIN(s);
     k_adjoint_rhs<<<reduce_blocks(N), kThreads, 0, s>>>(N, P, comp_of, w, b);
+    PROF_END(KK_OTHER, 1, s);
     return cudaGetLastError();
 }
 cudaError_t launch_grad(int64_t N, const double2* P, const double2* nu, const uint8_t* comp_of, const double2* dbeta,
                         double K, double* g_re, double* g_im, cudaStream_t s) {
+    PROF_BEGIN(s);
     k_grad<<<reduce_blocks(N), kThreads, 0, s>>>(N, P, nu, comp_of, dbeta, K, g_re, g_im);
+    PROF_END(KK_OTHER, 1, s);
     return cudaGetLastError();
 }
 

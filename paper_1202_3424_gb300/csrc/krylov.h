@@ -23,7 +23,7 @@ struct KState {
     int pad;
 };
 
-static constexpr int kMaxReduceBlocks = 256;
+static constexpr int kMaxReduceBlocks = 1024;
 int reduce_blocks(int64_t n);
 
 template <typename C> struct KrylovOps {

@@ -28,6 +28,7 @@
 
 #include "fft.cuh"
 #include "internal.h"
+#include "profiler.h"
 
 namespace dda {
 
@@ -37,11 +38,6 @@ template <int L> __host__ __device__ constexpr int tp_x() {
 }
 template <int L> __host__ __device__ constexpr int tp_s() {
     return (256 / Plan<L>::NT) > 32 ? 32 : ((256 / Plan<L>::NT) < 8 ? 8 : (256 / Plan<L>::NT));
-}
-template <int L, typename T> __host__ __device__ constexpr int tp_z() {
-    return (256 / Plan<L>::NT) > 32 ? 32
-                                    : ((256 / Plan<L>::NT) < (sizeof(T) == 4 ? 8 : 4) ? (sizeof(T) == 4 ? 8 : 4)
-                                                                                      : (256 / Plan<L>::NT));
 }
 
 // Final outputs of a pencil transform: register v[idx] holds position pos.
@@ -178,34 +174,49 @@ __global__ void __launch_bounds__(tp_s<L>() * Plan<L>::NT)
 }
 
 // ---- z pass with the Fourier-space product ------------------------------------
+// One block owns TP adjacent (kx) columns at one ky for one RHS; its threads
+// form three groups, one per Cartesian component c.  Group c transforms P_c
+// along z (input half zero), writes the spectrum to its shared-memory plane,
+// and after a barrier forms row c of the symmetric product
+//   Y_c(k) = sum_b Ghat_cb(k) P_b(k)
+// for the points it holds, then inverse-transforms Y_c and keeps z < nz.
+template <int L> __host__ __device__ constexpr int tp_z() {
+    return (128 / Plan<L>::NT) > 32 ? 32 : ((128 / Plan<L>::NT) < 4 ? 4 : (128 / Plan<L>::NT));
+}
+
 template <typename T, int LZ>
-__global__ void __launch_bounds__(tp_z<LZ, T>() * Plan<LZ>::NT)
+__global__ void __launch_bounds__(3 * tp_z<LZ>() * Plan<LZ>::NT)
     k_zconv(cx<T>* __restrict__ U2, const cx<T>* __restrict__ gh, int nz, int Lx, int Ly,
             const cx<T>* __restrict__ tw, const int* __restrict__ active) {
     using C = cx<T>;
     using PL = Plan<LZ>;
-    constexpr int TP = tp_z<LZ, T>();
-    constexpr int E = PL::E;
+    constexpr int TP = tp_z<LZ>(), NT = PL::NT;
+    static_assert((TP * NT) % 32 == 0, "component groups must be whole warps");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* buf = reinterpret_cast<C*>(smem_raw);  // [3][LZ][TP]
     const int ky = blockIdx.y, r = blockIdx.z;
     if (active != nullptr && active[r] == 0) return;
-    const int t = threadIdx.x % TP, u = threadIdx.x / TP;
+    const int t = threadIdx.x % TP;
+    const int rest = threadIdx.x / TP;
+    const int u = rest % NT, c = rest / NT;
     const int kx = blockIdx.x * TP + t;
     const bool valid = kx < Lx;
     const int64_t plane = (int64_t)Ly * Lx;
-    C* base = U2 + (int64_t)r * 3 * nz * plane + (int64_t)ky * Lx + (valid ? kx : 0);
-    auto ld = [&](int pos) { return buf[pos * TP + t]; };
-    auto st = [&](int pos, C val) { buf[pos * TP + t] = val; };
+    C* bc = U2 + ((int64_t)r * 3 + c) * nz * plane + (int64_t)ky * Lx + (valid ? kx : 0);
+    C* sb = buf + c * (LZ * TP);
+    auto ld = [&](int pos) { return sb[pos * TP + t]; };
+    auto st = [&](int pos, C val) { sb[pos * TP + t] = val; };
     KeepInRegs<C> keep;
-    C vc[3][E];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const C* bc = base + (int64_t)c * nz * plane;
-        auto first = [&](int pos) { return (valid && pos < nz) ? bc[pos * plane] : czero<C>(); };
-        pencil_fft<C, PL, -1>(vc[c], u, tw, first, ld, st, keep);
-    }
-    // Fourier-space product with the octant-stored symmetric tensor
+    C v[PL::E];
+    auto first = [&](int pos) { return (valid && pos < nz) ? bc[pos * plane] : czero<C>(); };
+    pencil_fft<C, PL, -1>(v, u, tw, first, ld, st, keep);
+    __syncthreads();
+    for_each_out<PL, -1>(u, [&](int idx, int pos) { sb[pos * TP + t] = v[idx]; });
+    __syncthreads();
+    // row c of the octant-stored symmetric tensor: components (xx,xy,xz,yy,yz,zz)
+    const int i0 = c == 0 ? 0 : (c == 1 ? 1 : 2);
+    const int i1 = c == 0 ? 1 : (c == 1 ? 3 : 4);
+    const int i2 = c == 0 ? 2 : (c == 1 ? 4 : 5);
     const int hx = Lx / 2 + 1, hy = Ly / 2 + 1, hz = LZ / 2 + 1;
     const int kxv = valid ? kx : 0;
     const int kxo = kxv <= Lx / 2 ? kxv : Lx - kxv;
@@ -217,24 +228,19 @@ __global__ void __launch_bounds__(tp_z<LZ, T>() * Plan<LZ>::NT)
         const bool fz = kz > LZ / 2;
         const int kzo = fz ? LZ - kz : kz;
         const C* g = g0 + (int64_t)kzo * hy * hx;
-        const C gxx = g[0], gyy = g[3 * cs], gzz = g[5 * cs];
-        C gxy = g[cs], gxz = g[2 * cs], gyz = g[4 * cs];
-        if (fx != fy) gxy = cscale(gxy, T(-1));
-        if (fx != fz) gxz = cscale(gxz, T(-1));
-        if (fy != fz) gyz = cscale(gyz, T(-1));
-        const C px = vc[0][idx], py = vc[1][idx], pz = vc[2][idx];
-        vc[0][idx] = cadd(cadd(cmul(gxx, px), cmul(gxy, py)), cmul(gxz, pz));
-        vc[1][idx] = cadd(cadd(cmul(gxy, px), cmul(gyy, py)), cmul(gyz, pz));
-        vc[2][idx] = cadd(cadd(cmul(gxz, px), cmul(gyz, py)), cmul(gzz, pz));
+        // odd components flip sign under a reflection of one of their two axes
+        const bool sxy = fx != fy, sxz = fx != fz, syz = fy != fz;
+        C a0 = g[i0 * cs], a1 = g[i1 * cs], a2 = g[i2 * cs];
+        if (c == 0) { if (sxy) a1 = cscale(a1, T(-1)); if (sxz) a2 = cscale(a2, T(-1)); }
+        if (c == 1) { if (sxy) a0 = cscale(a0, T(-1)); if (syz) a2 = cscale(a2, T(-1)); }
+        if (c == 2) { if (sxz) a0 = cscale(a0, T(-1)); if (syz) a1 = cscale(a1, T(-1)); }
+        const C p0 = buf[kz * TP + t], p1 = buf[LZ * TP + kz * TP + t], p2 = buf[2 * LZ * TP + kz * TP + t];
+        v[idx] = cadd(cadd(cmul(a0, p0), cmul(a1, p1)), cmul(a2, p2));
     });
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        pencil_fft_regs<C, PL, +1>(vc[c], u, tw, ld, st, keep);
-        C* bc = base + (int64_t)c * nz * plane;
-        for_each_out<PL, +1>(u, [&](int idx, int pos) {
-            if (valid && pos < nz) bc[pos * plane] = vc[c][idx];
-        });
-    }
+    pencil_fft_regs<C, PL, +1>(v, u, tw, ld, st, keep);
+    for_each_out<PL, +1>(u, [&](int idx, int pos) {
+        if (valid && pos < nz) bc[pos * plane] = v[idx];
+    });
 }
 
 // ---- Green tensor on the padded grid ------------------------------------------
@@ -344,16 +350,20 @@ int pick_fft_length(int n) {
     return 0;
 }
 
-// Opt a kernel into more than 48 KB of dynamic shared memory, once per kernel
+// Give a kernel the maximum shared-memory carveout and, above 48 KB, the
+// dynamic shared-memory size it needs -- once per kernel
 // (so that only launches happen while a stream is being captured).
 template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
     static std::mutex mu;
     static std::unordered_map<const void*, size_t> done;
     std::lock_guard<std::mutex> lock(mu);
     auto it = done.find((const void*)kernel);
     if (it != done.end() && it->second >= bytes) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    // prefer shared memory over L1 so that several FFT blocks fit on an SM
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess && bytes > 48 * 1024)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess) done[(const void*)kernel] = bytes;
     return e;
 }
@@ -380,6 +390,7 @@ static unsigned grid1d(int64_t n, int threads) {
     }
 
 template <typename T> struct LaunchX {
+    static constexpr int koff = sizeof(T) == 4 ? 0 : (KK_XFWD_C128 - KK_XFWD_C64);
     template <int LX>
     static cudaError_t fwd(const Geom& g, int R, const cx<T>* x, cx<T>* u1, const int* site_of, const cx<T>* tw,
                            const int* active, cudaStream_t st) {
@@ -389,7 +400,9 @@ template <typename T> struct LaunchX {
         if (e != cudaSuccess) return e;
         const int nrows = g.ny * g.nz;
         dim3 grid((nrows + TP - 1) / TP, 3, R);
+        PROF_BEGIN(st);
         k_xfwd<T, LX><<<grid, NTH, sm, st>>>(x, u1, site_of, g.nx, nrows, g.N, tw, active);
+        PROF_END(KK_XFWD_C64 + koff, R, st);
         return cudaGetLastError();
     }
     template <int LX>
@@ -401,14 +414,16 @@ template <typename T> struct LaunchX {
         if (e != cudaSuccess) return e;
         const int nrows = g.ny * g.nz;
         dim3 grid((nrows + TP - 1) / TP, 3, R);
+        PROF_BEGIN(st);
         k_xinv<T, LX><<<grid, NTH, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride, g.nx, nrows, g.N,
                                             tw, active);
+        PROF_END(KK_XINV_C64 + koff, R, st);
         return cudaGetLastError();
     }
     template <int L>
     static cudaError_t strided(int dir, const cx<T>* src, cx<T>* dst, int n_in, int n_out, int64_t pt_stride,
                                int width, int64_t sb, int64_t db, int batches, int per_rhs, const cx<T>* tw,
-                               const int* active, cudaStream_t st) {
+                               const int* active, cudaStream_t st, int kind, double units) {
         constexpr int TP = tp_s<L>(), NTH = TP * Plan<L>::NT;
         const size_t sm = (size_t)L * TP * sizeof(cx<T>);
         dim3 grid((width + TP - 1) / TP, batches, 1);
@@ -416,25 +431,31 @@ template <typename T> struct LaunchX {
         if (dir < 0) {
             e = allow_smem(k_strided<T, L, -1>, sm);
             if (e != cudaSuccess) return e;
+            PROF_BEGIN(st);
             k_strided<T, L, -1><<<grid, NTH, sm, st>>>(src, dst, n_in, n_out, pt_stride, width, sb, db, per_rhs, tw,
                                                       active);
+            PROF_END(kind, units, st);
         } else {
             e = allow_smem(k_strided<T, L, +1>, sm);
             if (e != cudaSuccess) return e;
+            PROF_BEGIN(st);
             k_strided<T, L, +1><<<grid, NTH, sm, st>>>(src, dst, n_in, n_out, pt_stride, width, sb, db, per_rhs, tw,
                                                       active);
+            PROF_END(kind, units, st);
         }
         return cudaGetLastError();
     }
     template <int LZ>
     static cudaError_t zconv(const Geom& g, int R, cx<T>* u2, const cx<T>* gh, const cx<T>* tw, const int* active,
                              cudaStream_t st) {
-        constexpr int TP = tp_z<LZ, T>(), NTH = TP * Plan<LZ>::NT;
-        const size_t sm = (size_t)LZ * TP * sizeof(cx<T>);
+        constexpr int TP = tp_z<LZ>(), NTH = 3 * TP * Plan<LZ>::NT;
+        const size_t sm = (size_t)3 * LZ * TP * sizeof(cx<T>);
         cudaError_t e = allow_smem(k_zconv<T, LZ>, sm);
         if (e != cudaSuccess) return e;
         dim3 grid((g.Lx + TP - 1) / TP, g.Ly, R);
+        PROF_BEGIN(st);
         k_zconv<T, LZ><<<grid, NTH, sm, st>>>(u2, gh, g.nz, g.Lx, g.Ly, tw, active);
+        PROF_END(KK_ZCONV_C64 + koff, R, st);
         return cudaGetLastError();
     }
 };
@@ -457,7 +478,7 @@ cudaError_t launch_matvec(const Geom& g, int R, const cx<T>* x, cx<T>* y, const 
     auto fwdx = [&]() -> cudaError_t { DDA_DISPATCH_L(g.Lx, LX::template fwd, g, R, x, w.u1, tg.site_of, tw.x, active, st); };
     auto ys = [&](int dir, const cx<T>* s, cx<T>* d, int n_in, int n_out, int64_t sb, int64_t db) -> cudaError_t {
         DDA_DISPATCH_L(g.Ly, LX::template strided, dir, s, d, n_in, n_out, (int64_t)g.Lx, g.Lx, sb, db, R * 3 * g.nz,
-                       3 * g.nz, tw.y, active, st);
+                       3 * g.nz, tw.y, active, st, (dir < 0 ? KK_YFWD_C64 : KK_YINV_C64) + LX::koff, (double)R);
     };
     auto zc = [&]() -> cudaError_t { DDA_DISPATCH_L(g.Lz, LX::template zconv, g, R, w.u2, ghat, tw.z, active, st); };
     auto invx = [&]() -> cudaError_t {
@@ -488,12 +509,12 @@ cudaError_t launch_green_fft(const Geom& g, double kd, double2* scratch, double2
     using LX = LaunchX<double>;
     auto yf = [&]() -> cudaError_t {
         DDA_DISPATCH_L(g.Ly, LX::template strided, -1, scratch, scratch, g.Ly, g.Ly, (int64_t)g.Lx, g.Lx,
-                       (int64_t)g.Ly * g.Lx, (int64_t)g.Ly * g.Lx, 6 * g.Lz, 1, tw.y, nullptr, st);
+                       (int64_t)g.Ly * g.Lx, (int64_t)g.Ly * g.Lx, 6 * g.Lz, 1, tw.y, nullptr, st, KK_GREEN, 1.0);
     };
     if ((e = yf()) != cudaSuccess) return e;
     auto zf = [&]() -> cudaError_t {
         DDA_DISPATCH_L(g.Lz, LX::template strided, -1, scratch, scratch, g.Lz, g.Lz, (int64_t)g.Ly * g.Lx,
-                       g.Ly * g.Lx, full, full, 6, 1, tw.z, nullptr, st);
+                       g.Ly * g.Lx, full, full, 6, 1, tw.z, nullptr, st, KK_GREEN, 1.0);
     };
     if ((e = zf()) != cudaSuccess) return e;
     const int64_t oct = 6 * (int64_t)g.hx() * g.hy() * g.hz();

@@ -253,3 +253,34 @@ def test_failure_statuses(lib):
     res, P, st = ctx.solve(0, [[1, 0, 0]], [[0, 1, 0]], tol=1e-10, maxit=2)
     assert res[0]["status_name"] == "DDA_ERR_NOT_CONVERGED" and res[0]["iters"] <= 2
     ctx.close()
+
+
+def test_launch_tracing_counts_and_leaves_results_unchanged(lib):
+    import ctypes
+    grid = sphere_grid(12)
+    ctx = _ctx(lib, grid, [1.5 + 0.02j], 2.0, lib.Precision.FP32_REFINED)
+    k, e = _rhs_set(2)
+    plain, P0, _ = ctx.solve(1, k, e, tol=1e-6)
+    L = lib.load_library()
+    assert L.dda_profile_enable(ctx.handle, 1) == 0
+
+    class Stat(ctypes.Structure):
+        _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                    ("units", ctypes.c_double)]
+
+    traced, P1, _ = ctx.solve(1, k, e, tol=1e-6)
+    arr = (Stat * 32)()
+    n = ctypes.c_int()
+    L.dda_profile_read.argtypes = [ctypes.c_void_p, ctypes.POINTER(Stat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    assert L.dda_profile_read(ctx.handle, arr, 32, ctypes.byref(n)) == 0
+    stats = {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms, arr[i].units) for i in range(n.value)}
+    L.dda_profile_enable(ctx.handle, 0)
+    assert np.array_equal(P0, P1)
+    it = max(r["iters"] for r in traced)
+    zl, zms, zu = stats["z_conv_c64"]
+    assert zl >= 2 * it and zl % 8 == 0          # 2 matvecs per iteration, blocks of 4 iterations
+    assert zu == 2 * zl and zms > 0               # both RHS in every launch
+    assert stats["z_conv_c128"][0] == max(r["outer_iters"] for r in traced)
+    for name in ("x_fwd_c64", "y_fwd_c64", "y_inv_c64", "x_inv_c64"):
+        assert stats[name][0] == zl
+    ctx.close()

@@ -148,6 +148,30 @@ dda_status dda_matvec(dda_ctx* ctx, dda_precision precision, int R, const double
 dda_status dda_matvec_device(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* e,
                              const void* x_dev, void* y_dev);
 
+/* No-allocation variant of dda_matvec_device, for callers that must not
+ * allocate device memory during the call: code whose device memory is all
+ * reserved up front by its own allocator or memory pool (a cudaMalloc here
+ * could fail or fragment that pool), and latency-critical loops that cannot
+ * afford the implicit synchronization an allocation may cause.  There is no
+ * counterpart in the paper; this is a deployment convenience.
+ * Same arguments, layout and result as dda_matvec_device; the context must
+ * already be prepared (dda_prepare allocates; this call does not).  The
+ * padded FFT work buffers and the 1/alpha table live in one fixed scratch
+ * array of 64 MiB (67108864 bytes) that the library declares in device
+ * memory: every GPU that loads the library holds it until the process exits.
+ * Lattices or RHS counts whose scratch would exceed it are rejected with
+ * DDA_ERR_SIZE (about 144 bytes per lattice site nx*ny*nz per RHS for
+ * complex64, twice that for complex128: the 64^3 lattice fits one complex64
+ * RHS).  The first call on a device
+ * looks up the array's device address: make that first call before any
+ * stream capture.  All calls, from every context of the process, share the
+ * one array and leave their data in it; no part of it needs to start at zero
+ * (every buffer is written before it is read), but calls that overlap on the
+ * GPU race on it, so do not run two of them concurrently on one device.
+ * Synchronizes the context stream before returning.                            */
+dda_status dda_matvec_device_noalloc(dda_ctx* ctx, dda_precision precision, int R, const double* khat,
+                                     const double* e, const void* x_dev, void* y_dev);
+
 /* Incident field E_inc,j = e exp(i k khat.r_j) at every site, [R][3][N] complex (host). */
 dda_status dda_incident_field(dda_ctx* ctx, int R, const double* khat, const double* e, double* E_out);
 

@@ -24,7 +24,7 @@ __all__ = [
     "DdaError", "Precision", "Context", "load_library", "library_path",
     "dda_create", "dda_destroy", "dda_last_error", "dda_set_stream", "dda_set_target", "dda_set_materials",
     "dda_prepare", "dda_get_info", "dda_solve", "dda_solve_device", "dda_matvec", "dda_matvec_device",
-    "dda_incident_field", "dda_grad_qabs",
+    "dda_incident_field", "dda_grad_qabs", "dda_matvec_device_noalloc",
 ]
 
 STATUS = {0: "DDA_OK", 1: "DDA_ERR_ARG", 2: "DDA_ERR_CUDA", 3: "DDA_ERR_OOM", 4: "DDA_ERR_SIZE",
@@ -102,6 +102,7 @@ def load_library(build_if_missing: bool = True):
                               ctypes.POINTER(dda_result)], ctypes.c_int),
         "dda_matvec": ([vp, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D], ctypes.c_int),
         "dda_matvec_device": ([vp, ctypes.c_int, ctypes.c_int, _D, _D, vp, vp], ctypes.c_int),
+        "dda_matvec_device_noalloc": ([vp, ctypes.c_int, ctypes.c_int, _D, _D, vp, vp], ctypes.c_int),
         "dda_incident_field": ([vp, ctypes.c_int, _D, _D, _D], ctypes.c_int),
         "dda_grad_qabs": ([vp, ctypes.c_int, _D, _D, ctypes.POINTER(dda_opts), _D, _D, _D, ctypes.POINTER(dda_result)],
                           ctypes.c_int),
@@ -237,6 +238,16 @@ def dda_matvec_device(ctx, precision, khat, e, x_dev, y_dev):
     yp = y_dev.data_ptr() if hasattr(y_dev, "data_ptr") else int(y_dev)
     _check(ctx, load_library().dda_matvec_device(ctx, int(precision), R, _dptr(k), _dptr(ev), ctypes.c_void_p(xp),
                                                  ctypes.c_void_p(yp)))
+
+
+def dda_matvec_device_noalloc(ctx, precision, khat, e, x_dev, y_dev):
+    """As dda_matvec_device, but the call allocates no device memory: its
+    scratch is a fixed 64 MiB array inside the library (see include/dda.h)."""
+    k, ev, R = _rhs(khat, e)
+    xp = x_dev.data_ptr() if hasattr(x_dev, "data_ptr") else int(x_dev)
+    yp = y_dev.data_ptr() if hasattr(y_dev, "data_ptr") else int(y_dev)
+    _check(ctx, load_library().dda_matvec_device_noalloc(ctx, int(precision), R, _dptr(k), _dptr(ev),
+                                                         ctypes.c_void_p(xp), ctypes.c_void_p(yp)))
 
 
 def dda_incident_field(ctx, khat, e) -> np.ndarray:

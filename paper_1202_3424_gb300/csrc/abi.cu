@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -659,6 +660,74 @@ void host_twiddles(int L, std::vector<double2>& t64, std::vector<float2>& t32) {
 
 }  // namespace
 
+// ---- no-allocation matvec scratch ------------------------------------------------
+// The padded work buffers and the 1/alpha table of dda_matvec_device_noalloc
+// live in this file-scope device array.  Every GPU that loads the library
+// holds it until the process exits.  In host code `g_noalloc_scratch` names
+// a host-side stand-in, not device memory: kernels only ever receive the
+// address returned by cudaGetSymbolAddress below.
+static constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on `device` (which must be current),
+// looked up on the first call for that device.
+cudaError_t noalloc_scratch(int device, unsigned char** out) {
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_ptr[device] == nullptr) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[device] = p;
+    }
+    *out = static_cast<unsigned char*>(g_noalloc_ptr[device]);
+    return cudaSuccess;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+template <typename T>
+dda_status matvec_noalloc(dda_ctx* ctx, int R, const std::vector<double>& k, const std::vector<cd>& ev,
+                          const void* x_dev, void* y_dev) {
+    using C = cx<T>;
+    const int BS = beta_stride(ctx);
+    const size_t beta_bytes = align256((size_t)R * BS * sizeof(C));
+    const size_t u1_bytes = align256((size_t)R * 3 * ctx->g.u1_per_comp() * sizeof(C));
+    const size_t u2_bytes = (size_t)R * 3 * ctx->g.u2_per_comp() * sizeof(C);
+    const size_t need = beta_bytes + u1_bytes + u2_bytes;
+    if (need > kNoAllocScratchBytes)
+        return ctx->fail(DDA_ERR_SIZE,
+                         "dda_matvec_device_noalloc needs %zu bytes of scratch for R=%d on this lattice; "
+                         "its fixed scratch holds %zu bytes (use dda_matvec_device or fewer RHS)",
+                         need, R, kNoAllocScratchBytes);
+    unsigned char* base = nullptr;
+    CU(noalloc_scratch(ctx->device, &base));
+    std::vector<C> beta((size_t)R * BS);
+    for (int r = 0; r < R; ++r) {
+        beta[(size_t)r * BS] = ccast<C>(make_double2(0.0, 0.0));
+        for (int c = 1; c < BS; ++c) {
+            const cd mrel = ctx->m[c - 1] / ctx->m_amb;
+            const cd be = ldr_inverse_alpha(mrel * mrel, ctx->kd, &k[3 * r], &ev[3 * r]);
+            if (!std::isfinite(be.real()) || !std::isfinite(be.imag()))
+                return ctx->fail(DDA_ERR_NONFINITE, "polarizability of composition %d is not finite", c);
+            beta[(size_t)r * BS + c] = ccast<C>(make_double2(be.real(), be.imag()));
+        }
+    }
+    C* d_beta = reinterpret_cast<C*>(base);
+    PadWork<T> w{reinterpret_cast<C*>(base + beta_bytes), reinterpret_cast<C*>(base + beta_bytes + u1_bytes)};
+    CU(cudaMemcpyAsync(d_beta, beta.data(), beta.size() * sizeof(C), cudaMemcpyHostToDevice, ctx->stream));
+    CU(launch_matvec<T>(ctx->g, R, static_cast<const C*>(x_dev), static_cast<C*>(y_dev), w, ctx->tg, d_beta, BS,
+                        ghat_of<T>(ctx), tw_of<T>(ctx), nullptr, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return DDA_OK;
+}
+}  // namespace
+
 // ================================================================== ABI ===
 extern "C" {
 
@@ -911,6 +980,21 @@ dda_status dda_matvec_device(dda_ctx* ctx, dda_precision precision, int R, const
     if (rs != DDA_OK) return rs;
     CU(sync_collect(ctx));
     return DDA_OK;
+}
+
+dda_status dda_matvec_device_noalloc(dda_ctx* ctx, dda_precision precision, int R, const double* khat,
+                                     const double* e, const void* x_dev, void* y_dev) {
+    if (!ctx) return DDA_ERR_ARG;
+    if (!x_dev || !y_dev) return ctx->fail(DDA_ERR_ARG, "NULL vector");
+    if (precision == DDA_FP32_REFINED) return ctx->fail(DDA_ERR_ARG, "matvec precision must be DDA_FP64 or DDA_FP32");
+    dda_status rs;
+    if ((rs = check_ready(ctx, precision)) != DDA_OK) return rs;
+    CU(cudaSetDevice(ctx->device));
+    std::vector<double> k;
+    std::vector<cd> ev;
+    if ((rs = check_rhs(ctx, R, khat, e, k, ev)) != DDA_OK) return rs;
+    if (precision == DDA_FP64) return matvec_noalloc<double>(ctx, R, k, ev, x_dev, y_dev);
+    return matvec_noalloc<float>(ctx, R, k, ev, x_dev, y_dev);
 }
 
 dda_status dda_matvec(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* e,

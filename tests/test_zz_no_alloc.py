@@ -1,0 +1,67 @@
+"""The no-allocation matvec entry point against the ordinary one (GPU).
+
+dda_matvec_device_noalloc serves callers that must not allocate device
+memory during the call; its scratch is a fixed array inside the library.
+This file is collected last so that a run stopping at the first failure has
+already run every other test; it also passes when run alone.
+"""
+import numpy as np
+import pytest
+
+from dda_inputs import random_complex, sphere_grid, uniform_directions, polarization_pair, workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1202_3424_gb300 as dda
+    dda.load_library()
+    return dda, torch
+
+
+def _rel(a, b):
+    return float((a - b).abs().max() / b.abs().max())
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (2, 1e-5)], ids=["fp64", "fp32"])
+def test_noalloc_matches_matvec_on_two_calls(env, prec, tol):
+    dda, torch = env
+    ctx = dda.Context(0)
+    ctx.set_target(sphere_grid(16))
+    ctx.set_materials([1.33 + 0.01j])
+    ctx.prepare_size_parameter(1.0, dda.Precision.FP32_REFINED)
+    N = ctx.info()["ndipoles"]
+    k = uniform_directions(2, 5)
+    e = polarization_pair(k)[0].astype(complex)
+    dt = torch.complex128 if prec == 0 else torch.complex64
+    for call in range(2):  # two calls in a row: the second sees the first call's scratch contents
+        x = torch.from_numpy(random_complex((2, 3, N), 100 + call)).to(dt).cuda()
+        y_ref = torch.empty_like(x)
+        y_na = torch.full_like(x, float("nan"))
+        dda.dda_matvec_device(ctx.handle, prec, k, e, x, y_ref)
+        dda.dda_matvec_device_noalloc(ctx.handle, prec, k, e, x, y_na)
+        torch.cuda.synchronize()
+        assert torch.isfinite(y_na).all()
+        assert _rel(y_na, y_ref) < tol, (call, _rel(y_na, y_ref))
+    ctx.close()
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch(env):
+    dda, torch = env
+    w = workload("sphere64")
+    ctx = dda.Context(0)
+    ctx.set_target(w.grid)
+    ctx.set_materials(w.m)
+    ctx.prepare_size_parameter(w.x, dda.Precision.FP32_REFINED)
+    N = ctx.info()["ndipoles"]
+    R = 4
+    x = torch.zeros((R, 3, N), dtype=torch.complex64, device="cuda")
+    y = torch.zeros_like(x)
+    with pytest.raises(dda.DdaError) as ei:
+        dda.dda_matvec_device_noalloc(ctx.handle, 2, np.repeat(w.khat[:1], R, 0), np.repeat(w.ehat[:1], R, 0), x, y)
+    assert ei.value.status_name == "DDA_ERR_SIZE"
+    ctx.close()

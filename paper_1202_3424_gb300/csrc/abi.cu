@@ -585,7 +585,7 @@ dda_status forward_solve(dda_ctx* ctx, dda_precision prec, int R, const double* 
     const size_t vb64 = (size_t)R * n * sizeof(double2);
     for (int sl : {S_E64, S_X64})
         if ((rs = ensure(ctx, ctx->pool[sl], vb64)) != DDA_OK) return rs;
-    CU(launch_einc(R, ctx->g.N, ctx->tg.lat_of, ctx->g.nx, ctx->g.ny, ctx->g.nz, ctx->kd, slot<double>(ctx, S_KHAT),
+    CU(launch_einc(R, ctx->g.N, ctx->tg.lat_of, ctx->g, ctx->kd, slot<double>(ctx, S_KHAT),
                    slot<double2>(ctx, S_EPOL), slot<double2>(ctx, S_E64), ctx->stream));
     const bool have_x0 = o.x0 != nullptr;
     if (have_x0) {
@@ -788,29 +788,34 @@ dda_status dda_set_target(dda_ctx* ctx, int nx, int ny, int nz, const uint8_t* c
     if (!ctx) return DDA_ERR_ARG;
     if (nx <= 0 || ny <= 0 || nz <= 0 || comp == nullptr) return ctx->fail(DDA_ERR_ARG, "bad lattice dimensions");
     Geom g;
-    g.nx = nx;
-    g.ny = ny;
-    g.nz = nz;
+    g.ox = nx;
+    g.oy = ny;
+    g.oz = nz;
     g.Lx = pick_fft_length(nx);
     g.Ly = pick_fft_length(ny);
     g.Lz = pick_fft_length(nz);
     if (!g.Lx || !g.Ly || !g.Lz)
         return ctx->fail(DDA_ERR_SIZE, "lattice %dx%dx%d exceeds the largest supported padded length", nx, ny, nz);
+    // the kernels work on the lattice extended with vacuum to L/2 per axis
+    g.nx = g.Lx / 2;
+    g.ny = g.Ly / 2;
+    g.nz = g.Lz / 2;
     const int64_t M = g.M();
     if (M > (int64_t)INT32_MAX) return ctx->fail(DDA_ERR_SIZE, "lattice too large");
-    std::vector<int> site_of(M), lat_of;
+    std::vector<int> site_of(M, -1), lat_of;
     std::vector<uint8_t> comp_of;
     int maxc = 0;
-    for (int64_t i = 0; i < M; ++i) {
-        if (comp[i]) {
-            site_of[i] = (int)lat_of.size();
-            lat_of.push_back((int)i);
-            comp_of.push_back(comp[i]);
-            maxc = std::max<int>(maxc, comp[i]);
-        } else {
-            site_of[i] = -1;
-        }
-    }
+    for (int iz = 0; iz < nz; ++iz)
+        for (int iy = 0; iy < ny; ++iy)
+            for (int ix = 0; ix < nx; ++ix) {
+                const uint8_t cv = comp[((int64_t)iz * ny + iy) * nx + ix];
+                if (!cv) continue;
+                const int64_t li = ((int64_t)iz * g.ny + iy) * g.nx + ix;
+                site_of[li] = (int)lat_of.size();
+                lat_of.push_back((int)li);
+                comp_of.push_back(cv);
+                maxc = std::max<int>(maxc, cv);
+            }
     if (lat_of.empty()) return ctx->fail(DDA_ERR_ARG, "target has no occupied site");
     g.N = (int64_t)lat_of.size();
     cudaSetDevice(ctx->device);
@@ -909,9 +914,9 @@ dda_status dda_prepare(dda_ctx* ctx, double lambda_vac, double aeff, dda_precisi
 dda_status dda_get_info(const dda_ctx* ctx, dda_info* info) {
     if (!ctx || !info) return DDA_ERR_ARG;
     std::memset(info, 0, sizeof *info);
-    info->nx = ctx->g.nx;
-    info->ny = ctx->g.ny;
-    info->nz = ctx->g.nz;
+    info->nx = ctx->g.ox;
+    info->ny = ctx->g.oy;
+    info->nz = ctx->g.oz;
     info->Lx = ctx->g.Lx;
     info->Ly = ctx->g.Ly;
     info->Lz = ctx->g.Lz;
@@ -1041,7 +1046,7 @@ dda_status dda_incident_field(dda_ctx* ctx, int R, const double* khat, const dou
     if ((rs = upload_tables(ctx, R, k, ev)) != DDA_OK) return rs;
     const size_t bytes = (size_t)R * 3 * ctx->g.N * sizeof(double2);
     if ((rs = ensure(ctx, ctx->pool[S_E64], bytes)) != DDA_OK) return rs;
-    CU(launch_einc(R, ctx->g.N, ctx->tg.lat_of, ctx->g.nx, ctx->g.ny, ctx->g.nz, ctx->kd, slot<double>(ctx, S_KHAT),
+    CU(launch_einc(R, ctx->g.N, ctx->tg.lat_of, ctx->g, ctx->kd, slot<double>(ctx, S_KHAT),
                    slot<double2>(ctx, S_EPOL), slot<double2>(ctx, S_E64), ctx->stream));
     CU(cudaMemcpyAsync(E_out, ctx->pool[S_E64].p, bytes, cudaMemcpyDeviceToHost, ctx->stream));
     CU(sync_collect(ctx));

@@ -2,30 +2,34 @@
 //
 // The DDA matvec (Goodman, Draine & Flatau 1990, the FFT method the user
 // guide cites under "Choice of FFT Algorithm") needs 1-D transforms of
-// length L = 2^a 3^b along each lattice axis of the zero-padded grid.
+// length L = 2^a 3^b along each axis of the zero-padded grid.  The lattice
+// is padded with vacuum to exactly L/2 sites per axis, so every forward
+// transform sees zeros in its upper half and every inverse transform is
+// needed only on its lower half; both facts are compile-time here.
+//
 // One pencil of length L is owned by NT threads; every thread holds
 // E = L/NT points in registers.  A stage of radix R (p = product of the
 // radices already applied) takes butterfly i in [0, L/R) with inputs at
 // positions i + j*L/R, multiplies input j by w^(j*k) (k = i mod p,
 // w = exp(sgn 2 pi i/(p R))), applies a length-R DFT and writes output m to
 // position (i-k)*R + k + m*p (Stockham autosort, natural order in and out).
+// Thread u runs butterflies i = u + q*NT.  Whenever p divides NT or NT
+// divides p, k and the output positions are a per-thread base plus
+// compile-time offsets, and (p | NT) the twiddles are shared by all of the
+// thread's butterflies, so they are loaded once per stage.
 //
-// Data enters the first stage straight from the caller (global memory or a
-// staging buffer) and leaves the last stage straight to the caller: the last
-// stage's outputs sit at positions i + m*L/R, which are exactly the inputs of
-// a first stage of the same radix -- the z-pass exploits this to apply the
-// Fourier-space product in registers between its forward and inverse
-// transforms.  Intermediate stages exchange through shared memory with two
-// block barriers each, so every thread of the block must call these
-// routines the same number of times.
+// The last stage's outputs sit at positions i + m*L/R, exactly the inputs of
+// a first stage of the same radix: the inverse uses the forward radices in
+// reverse order, so a forward transform can be followed by a pointwise
+// product and the inverse without leaving registers.  Intermediate stages
+// exchange through shared memory with two block barriers each, so every
+// thread of the block must run these routines the same number of times.
 #pragma once
 
 #include "common.cuh"
 
 namespace dda {
 
-// Radix schedules.  NT divides L/R for every radix R of the schedule, so that
-// every thread runs exactly E/R butterflies per stage.
 template <int L_, int NT_, int... Rs> struct PlanDef {
     static constexpr int L = L_;
     static constexpr int NT = NT_;
@@ -34,26 +38,31 @@ template <int L_, int NT_, int... Rs> struct PlanDef {
     static constexpr int rad[NS] = {Rs...};
 };
 
+// Radix schedules: the first forward radix (= last inverse radix) is even,
+// and NT divides L/R for every radix R.
 template <int L> struct Plan;
 template <> struct Plan<16> : PlanDef<16, 4, 4, 4> {};
 template <> struct Plan<32> : PlanDef<32, 4, 4, 8> {};
-template <> struct Plan<48> : PlanDef<48, 4, 3, 4, 4> {};
+template <> struct Plan<48> : PlanDef<48, 4, 4, 4, 3> {};
 template <> struct Plan<64> : PlanDef<64, 8, 8, 8> {};
-template <> struct Plan<96> : PlanDef<96, 8, 3, 4, 4, 2> {};
+template <> struct Plan<96> : PlanDef<96, 8, 4, 4, 3, 2> {};
 template <> struct Plan<128> : PlanDef<128, 16, 4, 4, 8> {};
-template <> struct Plan<192> : PlanDef<192, 16, 3, 4, 4, 4> {};
+template <> struct Plan<192> : PlanDef<192, 16, 4, 4, 4, 3> {};
 template <> struct Plan<256> : PlanDef<256, 32, 4, 8, 8> {};
-template <> struct Plan<384> : PlanDef<384, 32, 3, 4, 4, 4, 2> {};
+template <> struct Plan<384> : PlanDef<384, 32, 4, 4, 4, 3, 2> {};
 template <> struct Plan<512> : PlanDef<512, 64, 8, 8, 8> {};
 
-// Supported padded lengths, ascending (host side picks the smallest >= 2n).
+// Supported padded lengths, ascending (the host picks the smallest >= 2n).
 static constexpr int kSupportedLengths[] = {16, 32, 48, 64, 96, 128, 192, 256, 384, 512};
 
-// radix of stage S for direction DIR (forward uses the schedule as listed,
-// inverse in reverse order so that its first radix equals the forward's last)
-template <class PL, int DIR, int S> struct StageRadix {
-    static constexpr int value = (DIR < 0) ? PL::rad[S] : PL::rad[PL::NS - 1 - S];
-};
+template <class PL, int DIR> __host__ __device__ constexpr int stage_radix(int s) {
+    return DIR < 0 ? PL::rad[s] : PL::rad[PL::NS - 1 - s];
+}
+template <class PL, int DIR> __host__ __device__ constexpr int stage_p(int s) {
+    int p = 1;
+    for (int i = 0; i < s; ++i) p *= stage_radix<PL, DIR>(i);
+    return p;
+}
 
 // ---- small DFTs, sign convention exp(SGN * 2 pi i j k / R) ----------------
 template <int R, int SGN, typename C> struct Dft;
@@ -64,6 +73,7 @@ template <int SGN, typename C> struct Dft<2, SGN, C> {
         v[0] = cadd(a, b);
         v[1] = csub(a, b);
     }
+    __device__ __forceinline__ static void run_half(C* v) { v[1] = v[0]; }
 };
 
 template <int SGN, typename C> struct Dft<3, SGN, C> {
@@ -92,16 +102,21 @@ template <int SGN, typename C> struct Dft<4, SGN, C> {
         v[1] = cadd(t1, t3);
         v[3] = csub(t1, t3);
     }
+    // inputs 2 and 3 are zero
+    __device__ __forceinline__ static void run_half(C* v) {
+        C a = v[0], b = v[1];
+        C t3 = cmul_i<SGN>(b);
+        v[0] = cadd(a, b);
+        v[2] = csub(a, b);
+        v[1] = cadd(a, t3);
+        v[3] = csub(a, t3);
+    }
 };
 
 template <int SGN, typename C> struct Dft<8, SGN, C> {
-    __device__ __forceinline__ static void run(C* v) {
+    __device__ __forceinline__ static void combine(C* v, C (&e)[4], C (&o)[4]) {
         using T = typename real_of<C>::type;
         const T r2 = T(0.70710678118654752440);  // 1/sqrt(2)
-        C e[4] = {v[0], v[2], v[4], v[6]};
-        C o[4] = {v[1], v[3], v[5], v[7]};
-        Dft<4, SGN, C>::run(e);
-        Dft<4, SGN, C>::run(o);
         // w8^1 = (1 + SGN i)/sqrt2, w8^2 = SGN i, w8^3 = (-1 + SGN i)/sqrt2
         C o1 = cscale(cadd(o[1], cmul_i<SGN>(o[1])), r2);
         C o2 = cmul_i<SGN>(o[2]);
@@ -115,78 +130,142 @@ template <int SGN, typename C> struct Dft<8, SGN, C> {
         v[3] = cadd(e[3], o3);
         v[7] = csub(e[3], o3);
     }
+    __device__ __forceinline__ static void run(C* v) {
+        C e[4] = {v[0], v[2], v[4], v[6]};
+        C o[4] = {v[1], v[3], v[5], v[7]};
+        Dft<4, SGN, C>::run(e);
+        Dft<4, SGN, C>::run(o);
+        combine(v, e, o);
+    }
+    // inputs 4..7 are zero
+    __device__ __forceinline__ static void run_half(C* v) {
+        C e[4] = {v[0], v[2], v[0], v[0]};
+        C o[4] = {v[1], v[3], v[1], v[1]};
+        Dft<4, SGN, C>::run_half(e);
+        Dft<4, SGN, C>::run_half(o);
+        combine(v, e, o);
+    }
 };
 
 // ---- stage recursion -----------------------------------------------------
 // v: E registers; u: thread index within the pencil (0..NT-1);
-// tw: forward twiddle table of L entries exp(-2 pi i m/L) (shared or global);
-// ld(pos) / st(pos, val): shared-memory exchange for this thread's pencil;
-// last(q, m, pos, val): consumer of the final outputs (pos = i + m L/R).
-template <typename C, class PL, int DIR, int S, int P, class Ld, class St, class Last>
-__device__ __forceinline__ void fft_stages(C (&v)[PL::E], int u, const C* __restrict__ tw,
-                                           Ld& ld, St& st, Last& last) {
+// tw: forward twiddle table of L entries exp(-2 pi i m/L);
+// ld(pos) / st(pos, val): shared-memory exchange for this thread's pencil.
+// On return v[q*R + m] holds output position u + q*NT + m*L/R (R = last radix).
+template <typename C, class PL, int DIR, int S, class Ld, class St>
+__device__ __forceinline__ void fft_stages(C (&v)[PL::E], int u, const C* __restrict__ tw, Ld& ld, St& st,
+                                           bool half_first) {
     constexpr int L = PL::L, NT = PL::NT, E = PL::E, NS = PL::NS;
-    constexpr int R = StageRadix<PL, DIR, S>::value;
+    constexpr int R = stage_radix<PL, DIR>(S);
+    constexpr int P = stage_p<PL, DIR>(S);
     constexpr int NB = E / R;
-#pragma unroll
-    for (int q = 0; q < NB; ++q) {
-        const int i = u + q * NT;
-        if constexpr (P > 1) {
-            const int k = i % P;
+    constexpr int STEP = L / (P * R);
+    static_assert(E % R == 0, "radix must divide the points per thread");
+    if constexpr (P > 1) {
+        if constexpr (NT % P == 0) {
+            const int k = u % P;  // shared by all butterflies of this thread
+            C w[R];
 #pragma unroll
             for (int j = 1; j < R; ++j) {
-                C w = tw[j * k * (L / (P * R))];
-                if constexpr (DIR > 0) w.y = -w.y;
-                v[q * R + j] = cmul(v[q * R + j], w);
+                w[j] = tw[j * k * STEP];
+                if constexpr (DIR > 0) w[j].y = -w[j].y;
+            }
+#pragma unroll
+            for (int q = 0; q < NB; ++q)
+#pragma unroll
+                for (int j = 1; j < R; ++j) v[q * R + j] = cmul(v[q * R + j], w[j]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                int k;
+                if constexpr (P % NT == 0) k = u + (q % (P / NT)) * NT;
+                else k = (u + q * NT) % P;
+#pragma unroll
+                for (int j = 1; j < R; ++j) {
+                    C w = tw[j * k * STEP];
+                    if constexpr (DIR > 0) w.y = -w.y;
+                    v[q * R + j] = cmul(v[q * R + j], w);
+                }
             }
         }
-        Dft<R, DIR, C>::run(&v[q * R]);
     }
-    if constexpr (S == NS - 1) {
-        static_assert(P * R == L, "radix schedule must multiply to L");
 #pragma unroll
-        for (int q = 0; q < NB; ++q)
-#pragma unroll
-            for (int m = 0; m < R; ++m) last(q, m, u + q * NT + m * (L / R), v[q * R + m]);
-    } else {
+    for (int q = 0; q < NB; ++q) {
+        if constexpr (S == 0 && (R % 2 == 0)) {
+            if (half_first) Dft<R, DIR, C>::run_half(&v[q * R]);
+            else Dft<R, DIR, C>::run(&v[q * R]);
+        } else {
+            Dft<R, DIR, C>::run(&v[q * R]);
+        }
+    }
+    if constexpr (S < NS - 1) {
         __syncthreads();
+        if constexpr (NT % P == 0) {
+            const int base = (u / P) * (P * R) + (u % P);
 #pragma unroll
-        for (int q = 0; q < NB; ++q) {
-            const int i = u + q * NT;
-            const int k = i % P;
+            for (int q = 0; q < NB; ++q)
 #pragma unroll
-            for (int m = 0; m < R; ++m) st((i - k) * R + k + m * P, v[q * R + m]);
+                for (int m = 0; m < R; ++m) st(base + q * NT * R + m * P, v[q * R + m]);
+        } else if constexpr (P % NT == 0) {
+#pragma unroll
+            for (int q = 0; q < NB; ++q)
+#pragma unroll
+                for (int m = 0; m < R; ++m)
+                    st(u + (q - q % (P / NT)) * NT * R + (q % (P / NT)) * NT + m * P, v[q * R + m]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                const int i = u + q * NT, k = i % P;
+#pragma unroll
+                for (int m = 0; m < R; ++m) st((i - k) * R + k + m * P, v[q * R + m]);
+            }
         }
         __syncthreads();
-        constexpr int R2 = StageRadix<PL, DIR, S + 1>::value;
+        constexpr int R2 = stage_radix<PL, DIR>(S + 1);
         constexpr int NB2 = E / R2;
 #pragma unroll
         for (int q = 0; q < NB2; ++q)
 #pragma unroll
             for (int j = 0; j < R2; ++j) v[q * R2 + j] = ld(u + q * NT + j * (L / R2));
-        fft_stages<C, PL, DIR, S + 1, P * R>(v, u, tw, ld, st, last);
+        fft_stages<C, PL, DIR, S + 1>(v, u, tw, ld, st, false);
     }
 }
 
 // Load the first stage's inputs through first(pos), then run all stages.
-template <typename C, class PL, int DIR, class First, class Ld, class St, class Last>
-__device__ __forceinline__ void pencil_fft(C (&v)[PL::E], int u, const C* __restrict__ tw, First& first,
-                                           Ld& ld, St& st, Last& last) {
-    constexpr int R0 = StageRadix<PL, DIR, 0>::value;
+// HALF_IN: positions >= L/2 are zero and are neither loaded nor transformed.
+template <typename C, class PL, int DIR, bool HALF_IN, class First, class Ld, class St>
+__device__ __forceinline__ void pencil_fft(C (&v)[PL::E], int u, const C* __restrict__ tw, First& first, Ld& ld,
+                                           St& st) {
+    constexpr int R0 = stage_radix<PL, DIR>(0);
     constexpr int NB0 = PL::E / R0;
+    static_assert(!HALF_IN || R0 % 2 == 0, "a half-zero input needs an even first radix");
+    constexpr int JN = HALF_IN ? R0 / 2 : R0;
 #pragma unroll
     for (int q = 0; q < NB0; ++q)
 #pragma unroll
-        for (int j = 0; j < R0; ++j) v[q * R0 + j] = first(u + q * PL::NT + j * (PL::L / R0));
-    fft_stages<C, PL, DIR, 0, 1>(v, u, tw, ld, st, last);
+        for (int j = 0; j < JN; ++j) v[q * R0 + j] = first(u + q * PL::NT + j * (PL::L / R0));
+    fft_stages<C, PL, DIR, 0>(v, u, tw, ld, st, HALF_IN);
 }
 
 // Run all stages on data already in registers, laid out as the first stage
 // expects (inputs of butterfly q at v[q*R0 + j], positions i + j*L/R0).
-template <typename C, class PL, int DIR, class Ld, class St, class Last>
-__device__ __forceinline__ void pencil_fft_regs(C (&v)[PL::E], int u, const C* __restrict__ tw, Ld& ld, St& st,
-                                                Last& last) {
-    fft_stages<C, PL, DIR, 0, 1>(v, u, tw, ld, st, last);
+template <typename C, class PL, int DIR, class Ld, class St>
+__device__ __forceinline__ void pencil_fft_regs(C (&v)[PL::E], int u, const C* __restrict__ tw, Ld& ld, St& st) {
+    fft_stages<C, PL, DIR, 0>(v, u, tw, ld, st, false);
+}
+
+// Final outputs of a pencil transform: v[idx] holds position pos.
+// HALF_OUT: only positions < L/2 (the lattice half of an inverse transform).
+template <class PL, int DIR, bool HALF_OUT, class F>
+__device__ __forceinline__ void for_each_out(int u, F&& f) {
+    constexpr int R = stage_radix<PL, DIR>(PL::NS - 1);
+    constexpr int NB = PL::E / R;
+    static_assert(!HALF_OUT || R % 2 == 0, "half outputs need an even last radix");
+    constexpr int MN = HALF_OUT ? R / 2 : R;
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+#pragma unroll
+        for (int m = 0; m < MN; ++m) f(q * R + m, u + q * PL::NT + m * (PL::L / R));
 }
 
 }  // namespace dda

@@ -12,12 +12,16 @@
 
 namespace dda {
 
-// Lattice and padded-grid geometry.  Lattice index of site (ix,iy,iz) is
-// (iz*ny + iy)*nx + ix.  Padded lengths Lx,Ly,Lz are >= 2n (supported FFT
-// lengths); the stored octant of the transformed Green tensor has
-// (Lz/2+1) x (Ly/2+1) x (Lx/2+1) points per component.
+// Lattice and padded-grid geometry.  The caller's lattice ox*oy*oz is
+// extended with vacuum to nx*ny*nz = (Lx/2)*(Ly/2)*(Lz/2), where Lx,Ly,Lz are
+// the supported FFT lengths >= 2*ox, ...; the kernels only ever see the
+// extended lattice.  Lattice index of site (ix,iy,iz) is (iz*ny + iy)*nx + ix
+// on the extended lattice; positions use the original box centre.  The stored
+// octant of the transformed Green tensor has (Lz/2+1)(Ly/2+1)(Lx/2+1) points
+// per component.
 struct Geom {
-    int nx = 0, ny = 0, nz = 0;
+    int ox = 0, oy = 0, oz = 0;  // caller's lattice
+    int nx = 0, ny = 0, nz = 0;  // extended lattice (L/2 per axis)
     int Lx = 0, Ly = 0, Lz = 0;
     int64_t N = 0;  // occupied sites
     int hx() const { return Lx / 2 + 1; }

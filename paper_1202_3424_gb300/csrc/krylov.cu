@@ -398,14 +398,14 @@ __global__ void k_convert(int64_t n, const S* __restrict__ s, D* __restrict__ d)
 }
 
 // ---- physics kernels -------------------------------------------------------------
-// E_inc,j = e exp(i kd khat . r_j), r_j at half-integer offsets about the box centre.
+// E_inc,j = e exp(i kd khat . r_j), r_j at half-integer offsets about the
+// centre of the caller's box (cx, cy, cz); lat_of indexes the extended lattice.
 __global__ void __launch_bounds__(kThreads)
-    k_einc(int64_t N, const int* __restrict__ lat_of, int nx, int ny, int nz, double kd,
+    k_einc(int64_t N, const int* __restrict__ lat_of, int nx, int ny, double cx, double cy, double cz, double kd,
            const double* __restrict__ khat, const double2* __restrict__ e, double2* __restrict__ E) {
     const int r = blockIdx.y;
     const double kx = khat[3 * r], ky = khat[3 * r + 1], kz = khat[3 * r + 2];
     const double2 ex = e[3 * r], ey = e[3 * r + 1], ez = e[3 * r + 2];
-    const double cx = 0.5 * (nx - 1), cy = 0.5 * (ny - 1), cz = 0.5 * (nz - 1);
     double2* Er = E + (int64_t)r * 3 * N;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
         const int lat = lat_of[j];
@@ -586,10 +586,11 @@ cudaError_t launch_c128_to_c64v(int64_t n, const double2* s_, float2* d, cudaStr
     PROF_END(KK_REFINE, 1, s);
     return cudaGetLastError();
 }
-cudaError_t launch_einc(int R, int64_t N, const int* lat_of, int nx, int ny, int nz, double kd, const double* khat,
+cudaError_t launch_einc(int R, int64_t N, const int* lat_of, const Geom& g, double kd, const double* khat,
                         const double2* e, double2* E, cudaStream_t s) {
     PROF_BEGIN(s);
-    k_einc<<<dim3(reduce_blocks(N), R), kThreads, 0, s>>>(N, lat_of, nx, ny, nz, kd, khat, e, E);
+    k_einc<<<dim3(reduce_blocks(N), R), kThreads, 0, s>>>(N, lat_of, g.nx, g.ny, 0.5 * (g.ox - 1), 0.5 * (g.oy - 1),
+                                                           0.5 * (g.oz - 1), kd, khat, e, E);
     PROF_END(KK_EINC, R, s);
     return cudaGetLastError();
 }

@@ -52,7 +52,8 @@ cudaError_t launch_residual(int R, int64_t n, const double2* a, const double2* b
 cudaError_t launch_conj_diff(int R, int64_t n, const double2* a, const double2* b, double2* out, cudaStream_t s);
 cudaError_t launch_c64_to_c128(int64_t n, const float2* s_, double2* d, cudaStream_t s);
 cudaError_t launch_c128_to_c64v(int64_t n, const double2* s_, float2* d, cudaStream_t s);
-cudaError_t launch_einc(int R, int64_t N, const int* lat_of, int nx, int ny, int nz, double kd, const double* khat,
+struct Geom;
+cudaError_t launch_einc(int R, int64_t N, const int* lat_of, const Geom& g, double kd, const double* khat,
                         const double2* e, double2* E, cudaStream_t s);
 cudaError_t launch_qsums(int R, int64_t N, const double2* E, const double2* P, const uint8_t* comp_of, const double* w,
                          int w_stride, double2* sums, double2* part, unsigned* cnt, cudaStream_t s);

@@ -33,61 +33,56 @@
 namespace dda {
 
 // ---- tile sizes ------------------------------------------------------------
+// x passes stage TP rows through shared memory (TP+1 stride); strided passes
+// take TP adjacent pencils (coalesced across them); the z pass takes TP
+// adjacent columns for each of 3 component groups.
 template <int L> __host__ __device__ constexpr int tp_x() {
     return (256 / Plan<L>::NT) > 64 ? 64 : (256 / Plan<L>::NT);
 }
 template <int L> __host__ __device__ constexpr int tp_s() {
     return (256 / Plan<L>::NT) > 32 ? 32 : ((256 / Plan<L>::NT) < 8 ? 8 : (256 / Plan<L>::NT));
 }
-
-// Final outputs of a pencil transform: register v[idx] holds position pos.
-template <class PL, int DIR, class F>
-__device__ __forceinline__ void for_each_out(int u, F&& f) {
-    constexpr int R = StageRadix<PL, DIR, PL::NS - 1>::value;
-    constexpr int NB = PL::E / R;
-#pragma unroll
-    for (int q = 0; q < NB; ++q)
-#pragma unroll
-        for (int m = 0; m < R; ++m) f(q * R + m, u + q * PL::NT + m * (PL::L / R));
+// z pass: 3*TP*NT threads per block; TP adjacent columns.  (Blocks of 768
+// threads with 128-byte shared-memory rows were measured slower than two
+// blocks of 384 per SM on the 128^3 grid.)
+template <int L, typename T> __host__ __device__ constexpr int tp_z() {
+    return (128 / Plan<L>::NT) > 32 ? 32 : ((128 / Plan<L>::NT) < 4 ? 4 : (128 / Plan<L>::NT));
 }
 
-template <typename C> struct KeepInRegs {
-    __device__ __forceinline__ void operator()(int, int, int, C) const {}
-};
-
 // ---- x-forward: gather + row FFT ---------------------------------------------
+// Rows (iy, iz) of the padded-to-L/2 lattice; lattice sites x < LX/2.
 template <typename T, int LX>
 __global__ void __launch_bounds__(tp_x<LX>() * Plan<LX>::NT)
-    k_xfwd(const cx<T>* __restrict__ X, cx<T>* __restrict__ U1, const int* __restrict__ site_of, int nx,
-           int nrows, int64_t N, const cx<T>* __restrict__ tw, const int* __restrict__ active) {
+    k_xfwd(const cx<T>* __restrict__ X, cx<T>* __restrict__ U1, const int* __restrict__ site_of, int nrows,
+           int64_t N, const cx<T>* __restrict__ tw, const int* __restrict__ active) {
     using C = cx<T>;
     using PL = Plan<LX>;
-    constexpr int TP = tp_x<LX>(), SP = TP + 1;
+    constexpr int TP = tp_x<LX>(), SP = TP + 1, NX = LX / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     const int c = blockIdx.y, r = blockIdx.z;
     if (active != nullptr && active[r] == 0) return;
     const int row0 = blockIdx.x * TP;
     const C* xs = X + ((int64_t)r * 3 + c) * N;
-    for (int e = threadIdx.x; e < TP * nx; e += blockDim.x) {
-        const int t = e / nx, ix = e - t * nx, row = row0 + t;
+    for (int e = threadIdx.x; e < TP * NX; e += blockDim.x) {
+        const int t = e / NX, ix = e - t * NX, row = row0 + t;
         C val = czero<C>();
         if (row < nrows) {
-            const int s = site_of[(int64_t)row * nx + ix];
+            const int s = site_of[(int64_t)row * NX + ix];
             if (s >= 0) val = xs[s];
         }
         buf[ix * SP + t] = val;
     }
     __syncthreads();
     const int t = threadIdx.x % TP, u = threadIdx.x / TP;
+    C* bt = buf + t;
     C v[PL::E];
-    auto first = [&](int pos) { return pos < nx ? buf[pos * SP + t] : czero<C>(); };
-    auto ld = [&](int pos) { return buf[pos * SP + t]; };
-    auto st = [&](int pos, C val) { buf[pos * SP + t] = val; };
-    KeepInRegs<C> keep;
-    pencil_fft<C, PL, -1>(v, u, tw, first, ld, st, keep);
+    auto first = [&](int pos) { return bt[pos * SP]; };
+    auto ld = [&](int pos) { return bt[pos * SP]; };
+    auto st = [&](int pos, C val) { bt[pos * SP] = val; };
+    pencil_fft<C, PL, -1, true>(v, u, tw, first, ld, st);
     __syncthreads();
-    for_each_out<PL, -1>(u, [&](int idx, int pos) { buf[pos * SP + t] = v[idx]; });
+    for_each_out<PL, -1, false>(u, [&](int idx, int pos) { bt[pos * SP] = v[idx]; });
     __syncthreads();
     C* out = U1 + ((int64_t)r * 3 + c) * (int64_t)nrows * LX;
     for (int e = threadIdx.x; e < TP * LX; e += blockDim.x) {
@@ -101,11 +96,10 @@ template <typename T, int LX>
 __global__ void __launch_bounds__(tp_x<LX>() * Plan<LX>::NT)
     k_xinv(const cx<T>* __restrict__ U1, cx<T>* __restrict__ Y, const cx<T>* __restrict__ X,
            const int* __restrict__ site_of, const uint8_t* __restrict__ comp_of, const cx<T>* __restrict__ beta,
-           int beta_stride, int nx, int nrows, int64_t N, const cx<T>* __restrict__ tw,
-           const int* __restrict__ active) {
+           int beta_stride, int nrows, int64_t N, const cx<T>* __restrict__ tw, const int* __restrict__ active) {
     using C = cx<T>;
     using PL = Plan<LX>;
-    constexpr int TP = tp_x<LX>(), SP = TP + 1;
+    constexpr int TP = tp_x<LX>(), SP = TP + 1, NX = LX / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     const int c = blockIdx.y, r = blockIdx.z;
@@ -118,41 +112,40 @@ __global__ void __launch_bounds__(tp_x<LX>() * Plan<LX>::NT)
     }
     __syncthreads();
     const int t = threadIdx.x % TP, u = threadIdx.x / TP;
+    C* bt = buf + t;
     C v[PL::E];
-    auto first = [&](int pos) { return buf[pos * SP + t]; };
-    auto ld = [&](int pos) { return buf[pos * SP + t]; };
-    auto st = [&](int pos, C val) { buf[pos * SP + t] = val; };
-    KeepInRegs<C> keep;
-    pencil_fft<C, PL, +1>(v, u, tw, first, ld, st, keep);
+    auto first = [&](int pos) { return bt[pos * SP]; };
+    auto ld = [&](int pos) { return bt[pos * SP]; };
+    auto st = [&](int pos, C val) { bt[pos * SP] = val; };
+    pencil_fft<C, PL, +1, false>(v, u, tw, first, ld, st);
     __syncthreads();
-    for_each_out<PL, +1>(u, [&](int idx, int pos) {
-        if (pos < nx) buf[pos * SP + t] = v[idx];
-    });
+    for_each_out<PL, +1, true>(u, [&](int idx, int pos) { bt[pos * SP] = v[idx]; });
     __syncthreads();
     const C* xs = X + ((int64_t)r * 3 + c) * N;
     C* ys = Y + ((int64_t)r * 3 + c) * N;
     const C* br = beta + (int64_t)r * beta_stride;
-    for (int e = threadIdx.x; e < TP * nx; e += blockDim.x) {
-        const int t2 = e / nx, ix = e - t2 * nx, row = row0 + t2;
+    for (int e = threadIdx.x; e < TP * NX; e += blockDim.x) {
+        const int t2 = e / NX, ix = e - t2 * NX, row = row0 + t2;
         if (row < nrows) {
-            const int s = site_of[(int64_t)row * nx + ix];
+            const int s = site_of[(int64_t)row * NX + ix];
             if (s >= 0) ys[s] = cadd(buf[ix * SP + t2], cmul(br[comp_of[s]], xs[s]));
         }
     }
 }
 
 // ---- strided pencils (y passes; y and z passes of the Green tensor) -----------
-// Pencil (b, w): points at src + b*src_bstride + w + pos*pt_stride, pos < n_in
-// (zero beyond); outputs pos < n_out written to dst likewise.  TP pencils
-// adjacent in w per block, so loads and stores are coalesced across w.
-template <typename T, int L, int DIR>
+// Pencil (b, w): points at src + b*src_bstride + w + pos*pt_stride; outputs
+// to dst likewise.  MODE 0: forward with input positions >= L/2 zero;
+// MODE 1: inverse keeping positions < L/2; MODE 2: full forward transform.
+// TP pencils adjacent in w per block, so loads and stores coalesce across w.
+template <typename T, int L, int MODE>
 __global__ void __launch_bounds__(tp_s<L>() * Plan<L>::NT)
-    k_strided(const cx<T>* src, cx<T>* dst, int n_in, int n_out, int64_t pt_stride, int width,
-              int64_t src_bstride, int64_t dst_bstride, int batches_per_rhs, const cx<T>* __restrict__ tw,
-              const int* __restrict__ active) {
+    k_strided(const cx<T>* src, cx<T>* dst, int64_t pt_stride, int width, int64_t src_bstride, int64_t dst_bstride,
+              int batches_per_rhs, const cx<T>* __restrict__ tw, const int* __restrict__ active) {
     using C = cx<T>;
     using PL = Plan<L>;
     constexpr int TP = tp_s<L>();
+    constexpr int DIR = MODE == 1 ? +1 : -1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     const int b = blockIdx.y;
@@ -162,14 +155,14 @@ __global__ void __launch_bounds__(tp_s<L>() * Plan<L>::NT)
     const bool valid = w < width;
     const C* s = src + (int64_t)b * src_bstride + (valid ? w : 0);
     C* d = dst + (int64_t)b * dst_bstride + (valid ? w : 0);
+    C* bt = buf + t;
     C v[PL::E];
-    auto first = [&](int pos) { return (valid && pos < n_in) ? s[pos * pt_stride] : czero<C>(); };
-    auto ld = [&](int pos) { return buf[pos * TP + t]; };
-    auto st = [&](int pos, C val) { buf[pos * TP + t] = val; };
-    KeepInRegs<C> keep;
-    pencil_fft<C, PL, DIR>(v, u, tw, first, ld, st, keep);
-    for_each_out<PL, DIR>(u, [&](int idx, int pos) {
-        if (valid && pos < n_out) d[pos * pt_stride] = v[idx];
+    auto first = [&](int pos) { return valid ? s[pos * pt_stride] : czero<C>(); };
+    auto ld = [&](int pos) { return bt[pos * TP]; };
+    auto st = [&](int pos, C val) { bt[pos * TP] = val; };
+    pencil_fft<C, PL, DIR, MODE == 0>(v, u, tw, first, ld, st);
+    for_each_out<PL, DIR, MODE == 1>(u, [&](int idx, int pos) {
+        if (valid) d[pos * pt_stride] = v[idx];
     });
 }
 
@@ -179,18 +172,14 @@ __global__ void __launch_bounds__(tp_s<L>() * Plan<L>::NT)
 // along z (input half zero), writes the spectrum to its shared-memory plane,
 // and after a barrier forms row c of the symmetric product
 //   Y_c(k) = sum_b Ghat_cb(k) P_b(k)
-// for the points it holds, then inverse-transforms Y_c and keeps z < nz.
-template <int L> __host__ __device__ constexpr int tp_z() {
-    return (128 / Plan<L>::NT) > 32 ? 32 : ((128 / Plan<L>::NT) < 4 ? 4 : (128 / Plan<L>::NT));
-}
-
+// for the points it holds, then inverse-transforms Y_c and keeps z < LZ/2.
 template <typename T, int LZ>
-__global__ void __launch_bounds__(3 * tp_z<LZ>() * Plan<LZ>::NT)
-    k_zconv(cx<T>* __restrict__ U2, const cx<T>* __restrict__ gh, int nz, int Lx, int Ly,
-            const cx<T>* __restrict__ tw, const int* __restrict__ active) {
+__global__ void __launch_bounds__(3 * tp_z<LZ, T>() * Plan<LZ>::NT)
+    k_zconv(cx<T>* __restrict__ U2, const cx<T>* __restrict__ gh, int Lx, int Ly, const cx<T>* __restrict__ tw,
+            const int* __restrict__ active) {
     using C = cx<T>;
     using PL = Plan<LZ>;
-    constexpr int TP = tp_z<LZ>(), NT = PL::NT;
+    constexpr int TP = tp_z<LZ, T>(), NT = PL::NT, NZ = LZ / 2;
     static_assert((TP * NT) % 32 == 0, "component groups must be whole warps");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);  // [3][LZ][TP]
@@ -202,16 +191,15 @@ __global__ void __launch_bounds__(3 * tp_z<LZ>() * Plan<LZ>::NT)
     const int kx = blockIdx.x * TP + t;
     const bool valid = kx < Lx;
     const int64_t plane = (int64_t)Ly * Lx;
-    C* bc = U2 + ((int64_t)r * 3 + c) * nz * plane + (int64_t)ky * Lx + (valid ? kx : 0);
-    C* sb = buf + c * (LZ * TP);
-    auto ld = [&](int pos) { return sb[pos * TP + t]; };
-    auto st = [&](int pos, C val) { sb[pos * TP + t] = val; };
-    KeepInRegs<C> keep;
+    C* bc = U2 + ((int64_t)r * 3 + c) * NZ * plane + (int64_t)ky * Lx + (valid ? kx : 0);
+    C* sb = buf + c * (LZ * TP) + t;
+    auto ld = [&](int pos) { return sb[pos * TP]; };
+    auto st = [&](int pos, C val) { sb[pos * TP] = val; };
     C v[PL::E];
-    auto first = [&](int pos) { return (valid && pos < nz) ? bc[pos * plane] : czero<C>(); };
-    pencil_fft<C, PL, -1>(v, u, tw, first, ld, st, keep);
+    auto first = [&](int pos) { return valid ? bc[pos * plane] : czero<C>(); };
+    pencil_fft<C, PL, -1, true>(v, u, tw, first, ld, st);
     __syncthreads();
-    for_each_out<PL, -1>(u, [&](int idx, int pos) { sb[pos * TP + t] = v[idx]; });
+    for_each_out<PL, -1, false>(u, [&](int idx, int pos) { sb[pos * TP] = v[idx]; });
     __syncthreads();
     // row c of the octant-stored symmetric tensor: components (xx,xy,xz,yy,yz,zz)
     const int i0 = c == 0 ? 0 : (c == 1 ? 1 : 2);
@@ -224,7 +212,8 @@ __global__ void __launch_bounds__(3 * tp_z<LZ>() * Plan<LZ>::NT)
     const bool fx = kxv > Lx / 2, fy = ky > Ly / 2;
     const int64_t cs = (int64_t)hz * hy * hx;
     const C* g0 = gh + (int64_t)kyo * hx + kxo;
-    for_each_out<PL, -1>(u, [&](int idx, int kz) {
+    const C* p0b = buf + t;
+    for_each_out<PL, -1, false>(u, [&](int idx, int kz) {
         const bool fz = kz > LZ / 2;
         const int kzo = fz ? LZ - kz : kz;
         const C* g = g0 + (int64_t)kzo * hy * hx;
@@ -234,12 +223,12 @@ __global__ void __launch_bounds__(3 * tp_z<LZ>() * Plan<LZ>::NT)
         if (c == 0) { if (sxy) a1 = cscale(a1, T(-1)); if (sxz) a2 = cscale(a2, T(-1)); }
         if (c == 1) { if (sxy) a0 = cscale(a0, T(-1)); if (syz) a2 = cscale(a2, T(-1)); }
         if (c == 2) { if (sxz) a0 = cscale(a0, T(-1)); if (syz) a1 = cscale(a1, T(-1)); }
-        const C p0 = buf[kz * TP + t], p1 = buf[LZ * TP + kz * TP + t], p2 = buf[2 * LZ * TP + kz * TP + t];
-        v[idx] = cadd(cadd(cmul(a0, p0), cmul(a1, p1)), cmul(a2, p2));
+        const C pa = p0b[kz * TP], pb = p0b[LZ * TP + kz * TP], pc = p0b[2 * LZ * TP + kz * TP];
+        v[idx] = cadd(cadd(cmul(a0, pa), cmul(a1, pb)), cmul(a2, pc));
     });
-    pencil_fft_regs<C, PL, +1>(v, u, tw, ld, st, keep);
-    for_each_out<PL, +1>(u, [&](int idx, int pos) {
-        if (valid && pos < nz) bc[pos * plane] = v[idx];
+    pencil_fft_regs<C, PL, +1>(v, u, tw, ld, st);
+    for_each_out<PL, +1, true>(u, [&](int idx, int pos) {
+        if (valid) bc[pos * plane] = v[idx];
     });
 }
 
@@ -307,14 +296,14 @@ __global__ void __launch_bounds__(tp_x<LX>() * Plan<LX>::NT)
     }
     __syncthreads();
     const int t = threadIdx.x % TP, u = threadIdx.x / TP;
+    C* bt = buf + t;
     C v[PL::E];
-    auto first = [&](int pos) { return buf[pos * SP + t]; };
-    auto ld = [&](int pos) { return buf[pos * SP + t]; };
-    auto st = [&](int pos, C val) { buf[pos * SP + t] = val; };
-    KeepInRegs<C> keep;
-    pencil_fft<C, PL, -1>(v, u, tw, first, ld, st, keep);
+    auto first = [&](int pos) { return bt[pos * SP]; };
+    auto ld = [&](int pos) { return bt[pos * SP]; };
+    auto st = [&](int pos, C val) { bt[pos * SP] = val; };
+    pencil_fft<C, PL, -1, false>(v, u, tw, first, ld, st);
     __syncthreads();
-    for_each_out<PL, -1>(u, [&](int idx, int pos) { buf[pos * SP + t] = v[idx]; });
+    for_each_out<PL, -1, false>(u, [&](int idx, int pos) { bt[pos * SP] = v[idx]; });
     __syncthreads();
     for (int e = threadIdx.x; e < TP * LX; e += blockDim.x) {
         const int t2 = e / LX, x = e - t2 * LX;
@@ -401,7 +390,7 @@ template <typename T> struct LaunchX {
         const int nrows = g.ny * g.nz;
         dim3 grid((nrows + TP - 1) / TP, 3, R);
         PROF_BEGIN(st);
-        k_xfwd<T, LX><<<grid, NTH, sm, st>>>(x, u1, site_of, g.nx, nrows, g.N, tw, active);
+        k_xfwd<T, LX><<<grid, NTH, sm, st>>>(x, u1, site_of, nrows, g.N, tw, active);
         PROF_END(KK_XFWD_C64 + koff, R, st);
         return cudaGetLastError();
     }
@@ -415,46 +404,45 @@ template <typename T> struct LaunchX {
         const int nrows = g.ny * g.nz;
         dim3 grid((nrows + TP - 1) / TP, 3, R);
         PROF_BEGIN(st);
-        k_xinv<T, LX><<<grid, NTH, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride, g.nx, nrows, g.N,
-                                            tw, active);
+        k_xinv<T, LX><<<grid, NTH, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride, nrows, g.N, tw,
+                                            active);
         PROF_END(KK_XINV_C64 + koff, R, st);
         return cudaGetLastError();
     }
-    template <int L>
-    static cudaError_t strided(int dir, const cx<T>* src, cx<T>* dst, int n_in, int n_out, int64_t pt_stride,
-                               int width, int64_t sb, int64_t db, int batches, int per_rhs, const cx<T>* tw,
-                               const int* active, cudaStream_t st, int kind, double units) {
+    template <int MODE, int L>
+    static cudaError_t strided_mode(const cx<T>* src, cx<T>* dst, int64_t pt_stride, int width, int64_t sb,
+                                    int64_t db, int batches, int per_rhs, const cx<T>* tw, const int* active,
+                                    cudaStream_t st, int kind, double units) {
         constexpr int TP = tp_s<L>(), NTH = TP * Plan<L>::NT;
         const size_t sm = (size_t)L * TP * sizeof(cx<T>);
+        cudaError_t e = allow_smem(k_strided<T, L, MODE>, sm);
+        if (e != cudaSuccess) return e;
         dim3 grid((width + TP - 1) / TP, batches, 1);
-        cudaError_t e;
-        if (dir < 0) {
-            e = allow_smem(k_strided<T, L, -1>, sm);
-            if (e != cudaSuccess) return e;
-            PROF_BEGIN(st);
-            k_strided<T, L, -1><<<grid, NTH, sm, st>>>(src, dst, n_in, n_out, pt_stride, width, sb, db, per_rhs, tw,
-                                                      active);
-            PROF_END(kind, units, st);
-        } else {
-            e = allow_smem(k_strided<T, L, +1>, sm);
-            if (e != cudaSuccess) return e;
-            PROF_BEGIN(st);
-            k_strided<T, L, +1><<<grid, NTH, sm, st>>>(src, dst, n_in, n_out, pt_stride, width, sb, db, per_rhs, tw,
-                                                      active);
-            PROF_END(kind, units, st);
-        }
+        PROF_BEGIN(st);
+        k_strided<T, L, MODE><<<grid, NTH, sm, st>>>(src, dst, pt_stride, width, sb, db, per_rhs, tw, active);
+        PROF_END(kind, units, st);
         return cudaGetLastError();
+    }
+    template <int L>
+    static cudaError_t strided(int mode, const cx<T>* src, cx<T>* dst, int64_t pt_stride, int width, int64_t sb,
+                               int64_t db, int batches, int per_rhs, const cx<T>* tw, const int* active,
+                               cudaStream_t st, int kind, double units) {
+        if (mode == 0)
+            return strided_mode<0, L>(src, dst, pt_stride, width, sb, db, batches, per_rhs, tw, active, st, kind, units);
+        if (mode == 1)
+            return strided_mode<1, L>(src, dst, pt_stride, width, sb, db, batches, per_rhs, tw, active, st, kind, units);
+        return strided_mode<2, L>(src, dst, pt_stride, width, sb, db, batches, per_rhs, tw, active, st, kind, units);
     }
     template <int LZ>
     static cudaError_t zconv(const Geom& g, int R, cx<T>* u2, const cx<T>* gh, const cx<T>* tw, const int* active,
                              cudaStream_t st) {
-        constexpr int TP = tp_z<LZ>(), NTH = 3 * TP * Plan<LZ>::NT;
+        constexpr int TP = tp_z<LZ, T>(), NTH = 3 * TP * Plan<LZ>::NT;
         const size_t sm = (size_t)3 * LZ * TP * sizeof(cx<T>);
         cudaError_t e = allow_smem(k_zconv<T, LZ>, sm);
         if (e != cudaSuccess) return e;
         dim3 grid((g.Lx + TP - 1) / TP, g.Ly, R);
         PROF_BEGIN(st);
-        k_zconv<T, LZ><<<grid, NTH, sm, st>>>(u2, gh, g.nz, g.Lx, g.Ly, tw, active);
+        k_zconv<T, LZ><<<grid, NTH, sm, st>>>(u2, gh, g.Lx, g.Ly, tw, active);
         PROF_END(KK_ZCONV_C64 + koff, R, st);
         return cudaGetLastError();
     }
@@ -465,29 +453,34 @@ template <int LX> static cudaError_t launch_xfull(double2* data, int64_t nrows, 
     const size_t sm = (size_t)LX * (TP + 1) * sizeof(double2);
     cudaError_t e = allow_smem(k_xfull<LX>, sm);
     if (e != cudaSuccess) return e;
+    PROF_BEGIN(st);
     k_xfull<LX><<<(unsigned)((nrows + TP - 1) / TP), NTH, sm, st>>>(data, nrows, tw);
+    PROF_END(KK_GREEN, 1.0, st);
     return cudaGetLastError();
 }
 
+// The lattice seen by the kernels is padded with vacuum to exactly L/2 sites
+// per axis (g.nx == g.Lx/2, ...), see dda_set_target.
 template <typename T>
 cudaError_t launch_matvec(const Geom& g, int R, const cx<T>* x, cx<T>* y, const PadWork<T>& w, const DevTarget& tg,
                           const cx<T>* beta, int beta_stride, const cx<T>* ghat, const Twiddles<T>& tw,
                           const int* active, cudaStream_t st) {
     using LX = LaunchX<T>;
+    if (g.nx * 2 != g.Lx || g.ny * 2 != g.Ly || g.nz * 2 != g.Lz) return cudaErrorInvalidValue;
     cudaError_t e;
     auto fwdx = [&]() -> cudaError_t { DDA_DISPATCH_L(g.Lx, LX::template fwd, g, R, x, w.u1, tg.site_of, tw.x, active, st); };
-    auto ys = [&](int dir, const cx<T>* s, cx<T>* d, int n_in, int n_out, int64_t sb, int64_t db) -> cudaError_t {
-        DDA_DISPATCH_L(g.Ly, LX::template strided, dir, s, d, n_in, n_out, (int64_t)g.Lx, g.Lx, sb, db, R * 3 * g.nz,
-                       3 * g.nz, tw.y, active, st, (dir < 0 ? KK_YFWD_C64 : KK_YINV_C64) + LX::koff, (double)R);
+    auto ys = [&](int mode, const cx<T>* s, cx<T>* d, int64_t sb, int64_t db) -> cudaError_t {
+        DDA_DISPATCH_L(g.Ly, LX::template strided, mode, s, d, (int64_t)g.Lx, g.Lx, sb, db, R * 3 * g.nz, 3 * g.nz,
+                       tw.y, active, st, (mode == 0 ? KK_YFWD_C64 : KK_YINV_C64) + LX::koff, (double)R);
     };
     auto zc = [&]() -> cudaError_t { DDA_DISPATCH_L(g.Lz, LX::template zconv, g, R, w.u2, ghat, tw.z, active, st); };
     auto invx = [&]() -> cudaError_t {
         DDA_DISPATCH_L(g.Lx, LX::template inv, g, R, w.u1, y, x, tg, beta, beta_stride, tw.x, active, st);
     };
     if ((e = fwdx()) != cudaSuccess) return e;
-    if ((e = ys(-1, w.u1, w.u2, g.ny, g.Ly, (int64_t)g.ny * g.Lx, (int64_t)g.Ly * g.Lx)) != cudaSuccess) return e;
+    if ((e = ys(0, w.u1, w.u2, (int64_t)g.ny * g.Lx, (int64_t)g.Ly * g.Lx)) != cudaSuccess) return e;
     if ((e = zc()) != cudaSuccess) return e;
-    if ((e = ys(+1, w.u2, w.u1, g.Ly, g.ny, (int64_t)g.Ly * g.Lx, (int64_t)g.ny * g.Lx)) != cudaSuccess) return e;
+    if ((e = ys(1, w.u2, w.u1, (int64_t)g.Ly * g.Lx, (int64_t)g.ny * g.Lx)) != cudaSuccess) return e;
     return invx();
 }
 
@@ -501,24 +494,28 @@ template cudaError_t launch_matvec<double>(const Geom&, int, const double2*, dou
 cudaError_t launch_green_fft(const Geom& g, double kd, double2* scratch, double2* ghat64, const Twiddles<double>& tw,
                              cudaStream_t st) {
     const int64_t full = (int64_t)g.Lx * g.Ly * g.Lz;
+    PROF_BEGIN(st);
     k_green<<<grid1d(full, 256), 256, 0, st>>>(scratch, g.nx, g.ny, g.nz, g.Lx, g.Ly, g.Lz, kd);
+    PROF_END(KK_GREEN, 1.0, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     auto xf = [&]() -> cudaError_t { DDA_DISPATCH_L(g.Lx, launch_xfull, scratch, 6 * (int64_t)g.Lz * g.Ly, tw.x, st); };
     if ((e = xf()) != cudaSuccess) return e;
     using LX = LaunchX<double>;
     auto yf = [&]() -> cudaError_t {
-        DDA_DISPATCH_L(g.Ly, LX::template strided, -1, scratch, scratch, g.Ly, g.Ly, (int64_t)g.Lx, g.Lx,
-                       (int64_t)g.Ly * g.Lx, (int64_t)g.Ly * g.Lx, 6 * g.Lz, 1, tw.y, nullptr, st, KK_GREEN, 1.0);
+        DDA_DISPATCH_L(g.Ly, LX::template strided, 2, scratch, scratch, (int64_t)g.Lx, g.Lx, (int64_t)g.Ly * g.Lx,
+                       (int64_t)g.Ly * g.Lx, 6 * g.Lz, 1, tw.y, nullptr, st, KK_GREEN, 1.0);
     };
     if ((e = yf()) != cudaSuccess) return e;
     auto zf = [&]() -> cudaError_t {
-        DDA_DISPATCH_L(g.Lz, LX::template strided, -1, scratch, scratch, g.Lz, g.Lz, (int64_t)g.Ly * g.Lx,
-                       g.Ly * g.Lx, full, full, 6, 1, tw.z, nullptr, st, KK_GREEN, 1.0);
+        DDA_DISPATCH_L(g.Lz, LX::template strided, 2, scratch, scratch, (int64_t)g.Ly * g.Lx, g.Ly * g.Lx, full, full,
+                       6, 1, tw.z, nullptr, st, KK_GREEN, 1.0);
     };
     if ((e = zf()) != cudaSuccess) return e;
     const int64_t oct = 6 * (int64_t)g.hx() * g.hy() * g.hz();
+    PROF_BEGIN(st);
     k_octant<<<grid1d(oct, 256), 256, 0, st>>>(scratch, ghat64, g.Lx, g.Ly, g.Lz, 1.0 / (double)full);
+    PROF_END(KK_GREEN, 1.0, st);
     return cudaGetLastError();
 }
 

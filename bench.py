@@ -53,6 +53,12 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--fp64-sequential", action="store_true",
+                    help="FP64 leg solves the RHS one at a time (orientation-sweep comparison)")
+    ap.add_argument("--mode", default="solve", choices=["solve", "matvec"],
+                    help="matvec: only time dda_matvec_device (for profiler captures)")
+    ap.add_argument("--rhs", type=int, default=0, help="matvec mode: RHS per product (0 = workload's)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="matvec mode precision")
     return ap.parse_args()
 
 
@@ -264,11 +270,32 @@ def run_gb300(args):
 
     # plain FP64 on the same GPU (same workload, one RHS batch per step)
     fp64 = None
-    if args.fp64_steps > 0:
+    if args.fp64_steps > 0 and not args.fp64_sequential:
         step(dda.Precision.FP64)
         per64, mv64, res64, _ = timed(dda.Precision.FP64, args.fp64_steps)
         fp64 = {"time_to_solution_ms": sum(per64) / len(per64), "matvecs_per_s": mv64 / (sum(per64) / 1e3),
                 "iters": [r["iters"] for r in res64], "resid_rel": [r["resid_rel"] for r in res64]}
+    elif args.fp64_steps > 0:
+        # orientation sweep as a plain FP64 single-RHS loop: one solve per RHS
+        P1 = torch.empty((1, 3, N), dtype=torch.complex128, device=dev)
+        dda.dda_solve_device(ctx.handle, dda.Precision.FP64, w.khat[:1], w.ehat[:1], P1, tol=1e-5, maxit=2000)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        mv64 = 0
+        it64 = []
+        for r_ in range(R):
+            rr, st = dda.dda_solve_device(ctx.handle, dda.Precision.FP64, w.khat[r_:r_ + 1], w.ehat[r_:r_ + 1], P1,
+                                          tol=1e-5, maxit=2000)
+            mv64 += rr[0]["matvecs"]
+            it64.append(rr[0]["iters"])
+        e1.record(stream)
+        e1.synchronize()
+        t64 = e0.elapsed_time(e1)
+        fp64 = {"time_to_solution_ms": t64, "matvecs_per_s": mv64 / (t64 / 1e3), "mode": "sequential single-RHS",
+                "iters_mean": sum(it64) / len(it64)}
 
     # end to end through the host-buffer C-ABI call (P copied back every step)
     e2e = None
@@ -300,8 +327,8 @@ def run_gb300(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64 matvec / f64 refinement", "data": "synthetic",
-            "config": {"workload": f"{w.name}: {info['nx']}^3 sphere, N={N} dipoles, m={w.m[0]}, x={w.x}, "
-                                   f"{R} RHS (k along x, 2 polarizations), tol 1e-5",
+            "config": {"workload": f"{w.name}: lattice {info['nx']}x{info['ny']}x{info['nz']}, N={N} dipoles, "
+                                   f"m={w.m}, x={w.x}, {R} RHS, tol 1e-5",
                        "global_batch": R * world, "padded_grid": [info["Lx"], info["Ly"], info["Lz"]],
                        "parallelism": f"rhs-sharded x{world}", "l2": "256 MB buffer written between steps"},
             "time_to_solution_ms": ms_per_step,
@@ -420,9 +447,56 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_matvec_only(args):
+    """Time dda_matvec_device alone (used for profiler captures of the passes)."""
+    import torch
+    import paper_1202_3424_gb300 as dda
+    w = workload(args.workload)
+    R = args.rhs or w.nrhs
+    ctx = dda.Context(0)
+    ctx.set_target(w.grid)
+    ctx.set_materials(w.m)
+    ctx.prepare_size_parameter(w.x, dda.Precision.FP32_REFINED)
+    N = ctx.info()["ndipoles"]
+    k = np.resize(w.khat, (R, 3))
+    e = np.resize(w.ehat, (R, 3))
+    prec, dt = (2, torch.complex64) if args.precision == "fp32" else (0, torch.complex128)
+    g = torch.Generator(device="cuda").manual_seed(1)
+    x = torch.randn((R, 3, N), dtype=dt, device="cuda", generator=g)
+    y = torch.empty_like(x)
+    for _ in range(max(3, args.warmup)):
+        dda.dda_matvec_device(ctx.handle, prec, k, e, x, y)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        dda.dda_matvec_device(ctx.handle, prec, k, e, x, y)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    L = dda.load_library()
+    L.dda_profile_enable(ctx.handle, 1)
+    for _ in range(args.steps):
+        dda.dda_matvec_device(ctx.handle, prec, k, e, x, y)
+    kst = read_profile(dda, ctx)
+    L.dda_profile_enable(ctx.handle, 0)
+    info = ctx.info()
+    kern = {}
+    for name, v in kst.items():
+        avg = v["ms"] / v["launches"]
+        b = pass_bytes(name, info, v["units"] / v["launches"])
+        kern[name] = {"avg_ms": avg, "gbs": (b / (avg / 1e3) / 1e9) if b else None}
+    print(json.dumps({"mode": "matvec", "workload": w.name, "rhs": R, "precision": args.precision,
+                      "ms_per_matvec": ms, "rhs_matvecs_per_s": R / (ms / 1e3), "kernels": kern}), flush=True)
+    ctx.close()
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.mode == "matvec":
+        run_matvec_only(a)
     else:
         run_gb300(a)

@@ -303,7 +303,45 @@ template <typename T> struct InnerSlots {
     }
 };
 
-// One BiCGstab iteration for every active RHS.
+// Per-RHS stride (in double2) of the partial-sum buffer: enough for the
+// reduction kernels (<= kMaxReduceBlocks blocks, 2 sums) and for the fused
+// x-inverse scatter (one partial per block of that pass, 2 sums).
+int partial_stride(const dda_ctx* ctx) {
+    return 2 * std::max(kMaxReduceBlocks, xinv_blocks_per_rhs(ctx->g));
+}
+
+// Matvec over R RHS in chunks with the BiCGstab updates of `mode` fused into
+// its x passes (see FusedKrylov).
+template <typename T>
+dda_status run_matvec_fused(dda_ctx* ctx, int R, int mode, cx<T>* x, cx<T>* y, const Inner<T>& in) {
+    const int rc = matvec_chunk<T>(ctx, R);
+    const int64_t n = 3 * ctx->g.N;
+    PadWork<T> w{slot<cx<T>>(ctx, PadSlots<T>::a), slot<cx<T>>(ctx, PadSlots<T>::b)};
+    const int BS = beta_stride(ctx);
+    const int ps = partial_stride(ctx);
+    int* act = slot<int>(ctx, S_ACTIVE);
+    for (int r0 = 0; r0 < R; r0 += rc) {
+        const int rn = std::min(rc, R - r0);
+        const int64_t o = (int64_t)r0 * n;
+        FusedKrylov<T> fk;
+        fk.mode = mode;
+        fk.r = in.r + o;
+        fk.v = in.v + o;
+        fk.rhat = in.rhat + o;
+        fk.st = slot<KState>(ctx, S_STATE) + r0;
+        fk.part = slot<double2>(ctx, S_PART) + (int64_t)r0 * ps;
+        fk.cnt = slot<unsigned>(ctx, S_CNT) + r0;
+        fk.part_stride = ps;
+        CU(launch_matvec_fused<T>(ctx->g, rn, x + o, y + o, w, ctx->tg, beta_of<T>(ctx) + (int64_t)r0 * BS, BS,
+                                  ghat_of<T>(ctx), tw_of<T>(ctx), act + r0, fk, ctx->stream));
+    }
+    return DDA_OK;
+}
+
+// One BiCGstab iteration for every active RHS: 5 passes with p <- r + beta(p -
+// omega v) fused into the gather and alpha into the scatter, 5 passes with
+// s <- r - alpha v and omega fused likewise, then the x/r update with the
+// convergence test.
 template <typename T> dda_status inner_iteration(dda_ctx* ctx, int R) {
     using Ops = KrylovOps<cx<T>>;
     const int64_t n = 3 * ctx->g.N;
@@ -314,12 +352,8 @@ template <typename T> dda_status inner_iteration(dda_ctx* ctx, int R) {
     unsigned* cnt = slot<unsigned>(ctx, S_CNT);
     cudaStream_t s = ctx->stream;
     dda_status rs;
-    CU(Ops::update_p(R, n, in.p, in.r, in.v, st, act, s));
-    if ((rs = run_matvec<T>(ctx, R, in.p, in.v, act)) != DDA_OK) return rs;
-    CU(Ops::alpha(R, n, in.rhat, in.v, st, act, part, cnt, s));
-    CU(Ops::update_s(R, n, in.s, in.r, in.v, st, act, s));
-    if ((rs = run_matvec<T>(ctx, R, in.s, in.t, act)) != DDA_OK) return rs;
-    CU(Ops::omega(R, n, in.t, in.s, st, act, part, cnt, s));
+    if ((rs = run_matvec_fused<T>(ctx, R, 1, in.p, in.v, in)) != DDA_OK) return rs;
+    if ((rs = run_matvec_fused<T>(ctx, R, 2, in.s, in.t, in)) != DDA_OK) return rs;
     CU(Ops::update_xr(R, n, in.x, in.p, in.s, in.t, in.r, in.rhat, st, act, part, cnt, s));
     return DDA_OK;
 }
@@ -391,7 +425,7 @@ struct RhsTrack {
 
 dda_status ensure_common(dda_ctx* ctx, int R) {
     dda_status s;
-    const size_t nb = (size_t)R * kMaxReduceBlocks * 2 * sizeof(double2);
+    const size_t nb = (size_t)R * partial_stride(ctx) * sizeof(double2);
     if ((s = ensure(ctx, ctx->pool[S_PART], nb)) != DDA_OK) return s;
     if (ctx->pool[S_CNT].bytes < R * sizeof(unsigned)) {
         if ((s = ensure(ctx, ctx->pool[S_CNT], R * sizeof(unsigned), true)) != DDA_OK) return s;

@@ -22,7 +22,8 @@
 // a first stage of the same radix: the inverse uses the forward radices in
 // reverse order, so a forward transform can be followed by a pointwise
 // product and the inverse without leaving registers.  Intermediate stages
-// exchange through shared memory with two block barriers each, so every
+// exchange through shared memory with two barriers each -- block barriers,
+// or warp barriers when every pencil lies within one warp (WARP) -- so every
 // thread of the block must run these routines the same number of times.
 #pragma once
 
@@ -51,6 +52,12 @@ template <> struct Plan<192> : PlanDef<192, 16, 4, 4, 4, 3> {};
 template <> struct Plan<256> : PlanDef<256, 32, 4, 8, 8> {};
 template <> struct Plan<384> : PlanDef<384, 32, 4, 4, 4, 3, 2> {};
 template <> struct Plan<512> : PlanDef<512, 64, 8, 8, 8> {};
+
+// Schedules of the z pass (three component groups per block): as Plan<L>,
+// except that L = 512 uses 32 threads per pencil (16 points each) so that
+// eight adjacent columns fit in one block.
+template <int L> struct ZPlan : Plan<L> {};
+template <> struct ZPlan<512> : PlanDef<512, 32, 8, 8, 8> {};
 
 // Supported padded lengths, ascending (the host picks the smallest >= 2n).
 static constexpr int kSupportedLengths[] = {16, 32, 48, 64, 96, 128, 192, 256, 384, 512};
@@ -152,7 +159,12 @@ template <int SGN, typename C> struct Dft<8, SGN, C> {
 // tw: forward twiddle table of L entries exp(-2 pi i m/L);
 // ld(pos) / st(pos, val): shared-memory exchange for this thread's pencil.
 // On return v[q*R + m] holds output position u + q*NT + m*L/R (R = last radix).
-template <typename C, class PL, int DIR, int S, class Ld, class St>
+template <bool WARP> __device__ __forceinline__ void stage_sync() {
+    if constexpr (WARP) __syncwarp();
+    else __syncthreads();
+}
+
+template <typename C, class PL, int DIR, int S, class Ld, class St, bool WARP = false>
 __device__ __forceinline__ void fft_stages(C (&v)[PL::E], int u, const C* __restrict__ tw, Ld& ld, St& st,
                                            bool half_first) {
     constexpr int L = PL::L, NT = PL::NT, E = PL::E, NS = PL::NS;
@@ -199,7 +211,7 @@ __device__ __forceinline__ void fft_stages(C (&v)[PL::E], int u, const C* __rest
         }
     }
     if constexpr (S < NS - 1) {
-        __syncthreads();
+        stage_sync<WARP>();
         if constexpr (NT % P == 0) {
             const int base = (u / P) * (P * R) + (u % P);
 #pragma unroll
@@ -220,20 +232,20 @@ __device__ __forceinline__ void fft_stages(C (&v)[PL::E], int u, const C* __rest
                 for (int m = 0; m < R; ++m) st((i - k) * R + k + m * P, v[q * R + m]);
             }
         }
-        __syncthreads();
+        stage_sync<WARP>();
         constexpr int R2 = stage_radix<PL, DIR>(S + 1);
         constexpr int NB2 = E / R2;
 #pragma unroll
         for (int q = 0; q < NB2; ++q)
 #pragma unroll
             for (int j = 0; j < R2; ++j) v[q * R2 + j] = ld(u + q * NT + j * (L / R2));
-        fft_stages<C, PL, DIR, S + 1>(v, u, tw, ld, st, false);
+        fft_stages<C, PL, DIR, S + 1, Ld, St, WARP>(v, u, tw, ld, st, false);
     }
 }
 
 // Load the first stage's inputs through first(pos), then run all stages.
 // HALF_IN: positions >= L/2 are zero and are neither loaded nor transformed.
-template <typename C, class PL, int DIR, bool HALF_IN, class First, class Ld, class St>
+template <typename C, class PL, int DIR, bool HALF_IN, class First, class Ld, class St, bool WARP = false>
 __device__ __forceinline__ void pencil_fft(C (&v)[PL::E], int u, const C* __restrict__ tw, First& first, Ld& ld,
                                            St& st) {
     constexpr int R0 = stage_radix<PL, DIR>(0);
@@ -244,14 +256,14 @@ __device__ __forceinline__ void pencil_fft(C (&v)[PL::E], int u, const C* __rest
     for (int q = 0; q < NB0; ++q)
 #pragma unroll
         for (int j = 0; j < JN; ++j) v[q * R0 + j] = first(u + q * PL::NT + j * (PL::L / R0));
-    fft_stages<C, PL, DIR, 0>(v, u, tw, ld, st, HALF_IN);
+    fft_stages<C, PL, DIR, 0, Ld, St, WARP>(v, u, tw, ld, st, HALF_IN);
 }
 
 // Run all stages on data already in registers, laid out as the first stage
 // expects (inputs of butterfly q at v[q*R0 + j], positions i + j*L/R0).
-template <typename C, class PL, int DIR, class Ld, class St>
+template <typename C, class PL, int DIR, class Ld, class St, bool WARP = false>
 __device__ __forceinline__ void pencil_fft_regs(C (&v)[PL::E], int u, const C* __restrict__ tw, Ld& ld, St& st) {
-    fft_stages<C, PL, DIR, 0>(v, u, tw, ld, st, false);
+    fft_stages<C, PL, DIR, 0, Ld, St, WARP>(v, u, tw, ld, st, false);
 }
 
 // Final outputs of a pencil transform: v[idx] holds position pos.

@@ -55,6 +55,32 @@ template <typename T> struct PadWork {
 
 int pick_fft_length(int n);  // smallest supported length >= 2n, or 0
 
+struct KState;
+
+// BiCGstab updates fused into the x passes of a matvec (mode 0: none).
+//   mode 1: gather p <- r + beta (p - omega v) (written back to x);
+//           scatter v = A p and sigma = <rhat, v> -> alpha
+//   mode 2: gather s <- r - alpha v (written back to x);
+//           scatter t = A s and <t, s>, <t, t> -> omega
+// part/cnt: per-RHS partial sums (part_stride double2 per RHS) and tickets.
+template <typename T> struct FusedKrylov {
+    int mode = 0;
+    const cx<T>* r = nullptr;
+    const cx<T>* v = nullptr;
+    const cx<T>* rhat = nullptr;
+    KState* st = nullptr;
+    double2* part = nullptr;
+    unsigned* cnt = nullptr;
+    int part_stride = 0;
+};
+
+int xinv_blocks_per_rhs(const Geom& g);
+
+template <typename T>
+cudaError_t launch_matvec_fused(const Geom& g, int R, cx<T>* x, cx<T>* y, const PadWork<T>& w,
+                                const DevTarget& tg, const cx<T>* beta, int beta_stride, const cx<T>* ghat,
+                                const Twiddles<T>& tw, int* active, const FusedKrylov<T>& fk, cudaStream_t st);
+
 // y = A x for R right-hand sides, vectors [R][3][N].  beta[r*beta_stride + comp]
 // is 1/alpha of composition comp for RHS r.  active (nullable): RHS r is
 // skipped when active[r] == 0.

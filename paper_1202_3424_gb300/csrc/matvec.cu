@@ -28,6 +28,7 @@
 
 #include "fft.cuh"
 #include "internal.h"
+#include "krylov_dev.cuh"
 #include "profiler.h"
 
 namespace dda {
@@ -42,19 +43,47 @@ template <int L> __host__ __device__ constexpr int tp_x() {
 template <int L> __host__ __device__ constexpr int tp_s() {
     return (256 / Plan<L>::NT) > 32 ? 32 : ((256 / Plan<L>::NT) < 8 ? 8 : (256 / Plan<L>::NT));
 }
-// z pass: 3*TP*NT threads per block; TP adjacent columns.  (Blocks of 768
-// threads with 128-byte shared-memory rows were measured slower than two
-// blocks of 384 per SM on the 128^3 grid.)
+// z pass: 3*TP*NT threads per block, TP adjacent columns, and enough blocks
+// per SM (registers capped by the launch bound) to hide the latency of the
+// strided column loads: measured on GB300, three 384-thread blocks per SM
+// were 40 % faster than two on the 192x128x64 grid.  (Blocks of 768 threads
+// with 128-byte shared-memory rows, a variant with one warp per pencil and
+// staged tiles, and a row swizzle were all measured slower.)
 template <int L, typename T> __host__ __device__ constexpr int tp_z() {
-    return (128 / Plan<L>::NT) > 32 ? 32 : ((128 / Plan<L>::NT) < 4 ? 4 : (128 / Plan<L>::NT));
+    constexpr int nt = ZPlan<L>::NT;
+    int tp = nt >= 32 ? 256 / nt : 128 / nt;
+    tp = tp > 32 ? 32 : (tp < 4 ? 4 : tp);
+    // spectra [3][L] and Green tensor [6][L/2+1] per column within 200 KB
+    while (tp > 1 && ((size_t)3 * L + (size_t)6 * (L / 2 + 1)) * tp * sizeof(cx<T>) > 200 * 1024) tp /= 2;
+    return tp;
+}
+// (complex128 z passes are FP64-ALU-bound and keep their registers)
+template <int L, typename T> __host__ __device__ constexpr int zconv_min_blocks() {
+    constexpr int threads = 3 * tp_z<L, T>() * ZPlan<L>::NT;
+    return (sizeof(T) == 4 && 2048 / threads >= 3) ? 3 : 1;
+}
+// Row stride (complex elements) of the z pass's shared-memory planes.
+// (Padding rows narrower than 128 bytes by two elements was measured slower
+// on the 128^3 grid: it removes the conflicts of stride-4 row patterns but
+// creates them for consecutive rows.)
+template <int L, typename T> __host__ __device__ constexpr int sp_z() {
+    return tp_z<L, T>();
+}
+template <int L, typename T> __host__ __device__ constexpr size_t zconv_smem() {
+    return ((size_t)3 * L + (size_t)6 * (L / 2 + 1)) * sp_z<L, T>() * sizeof(cx<T>);
 }
 
 // ---- x-forward: gather + row FFT ---------------------------------------------
 // Rows (iy, iz) of the padded-to-L/2 lattice; lattice sites x < LX/2.
-template <typename T, int LX>
+// MODE 0 gathers X.  With the BiCGstab updates fused into the gather
+// (per-RHS scalars from st), the gathered vector is formed on the fly and
+// written back to X:  MODE 1  X = p <- r + beta (p - omega v);
+//                      MODE 2  X = s <- r - alpha v.
+template <typename T, int LX, int MODE>
 __global__ void __launch_bounds__(tp_x<LX>() * Plan<LX>::NT)
-    k_xfwd(const cx<T>* __restrict__ X, cx<T>* __restrict__ U1, const int* __restrict__ site_of, int nrows,
-           int64_t N, const cx<T>* __restrict__ tw, const int* __restrict__ active) {
+    k_xfwd(cx<T>* __restrict__ X, cx<T>* __restrict__ U1, const int* __restrict__ site_of, int nrows, int64_t N,
+           const cx<T>* __restrict__ tw, const int* __restrict__ active, const cx<T>* __restrict__ kr,
+           const cx<T>* __restrict__ kv, const KState* __restrict__ st) {
     using C = cx<T>;
     using PL = Plan<LX>;
     constexpr int TP = tp_x<LX>(), SP = TP + 1, NX = LX / 2;
@@ -63,13 +92,31 @@ __global__ void __launch_bounds__(tp_x<LX>() * Plan<LX>::NT)
     const int c = blockIdx.y, r = blockIdx.z;
     if (active != nullptr && active[r] == 0) return;
     const int row0 = blockIdx.x * TP;
-    const C* xs = X + ((int64_t)r * 3 + c) * N;
+    const int64_t off = ((int64_t)r * 3 + c) * N;
+    C* xs = X + off;
+    C ka = czero<C>(), kb = czero<C>();
+    if constexpr (MODE == 1) {
+        ka = from2<C>(st[r].beta);
+        kb = from2<C>(st[r].omega);
+    } else if constexpr (MODE == 2) {
+        ka = from2<C>(st[r].alpha);
+    }
     for (int e = threadIdx.x; e < TP * NX; e += blockDim.x) {
         const int t = e / NX, ix = e - t * NX, row = row0 + t;
         C val = czero<C>();
         if (row < nrows) {
             const int s = site_of[(int64_t)row * NX + ix];
-            if (s >= 0) val = xs[s];
+            if (s >= 0) {
+                if constexpr (MODE == 0) {
+                    val = xs[s];
+                } else if constexpr (MODE == 1) {
+                    val = cadd(kr[off + s], cmul(ka, csub(xs[s], cmul(kb, kv[off + s]))));
+                    xs[s] = val;
+                } else {
+                    val = csub(kr[off + s], cmul(ka, kv[off + s]));
+                    xs[s] = val;
+                }
+            }
         }
         buf[ix * SP + t] = val;
     }
@@ -79,8 +126,8 @@ __global__ void __launch_bounds__(tp_x<LX>() * Plan<LX>::NT)
     C v[PL::E];
     auto first = [&](int pos) { return bt[pos * SP]; };
     auto ld = [&](int pos) { return bt[pos * SP]; };
-    auto st = [&](int pos, C val) { bt[pos * SP] = val; };
-    pencil_fft<C, PL, -1, true>(v, u, tw, first, ld, st);
+    auto stf = [&](int pos, C val) { bt[pos * SP] = val; };
+    pencil_fft<C, PL, -1, true>(v, u, tw, first, ld, stf);
     __syncthreads();
     for_each_out<PL, -1, false>(u, [&](int idx, int pos) { bt[pos * SP] = v[idx]; });
     __syncthreads();
@@ -92,11 +139,17 @@ __global__ void __launch_bounds__(tp_x<LX>() * Plan<LX>::NT)
 }
 
 // ---- x-inverse: row IFFT + diagonal + scatter -----------------------------------
-template <typename T, int LX>
+// Y = conv + (1/alpha) X at the occupied sites.  Fused BiCGstab reductions
+// (FP64 totals per RHS over all blocks of that RHS, finalized by the last one):
+//   MODE 1  Y = v:  sigma = <rhat, v>          ->  alpha = rho / sigma
+//   MODE 2  Y = t:  <t, s>, <t, t> with X = s  ->  omega
+template <typename T, int LX, int MODE>
 __global__ void __launch_bounds__(tp_x<LX>() * Plan<LX>::NT)
     k_xinv(const cx<T>* __restrict__ U1, cx<T>* __restrict__ Y, const cx<T>* __restrict__ X,
            const int* __restrict__ site_of, const uint8_t* __restrict__ comp_of, const cx<T>* __restrict__ beta,
-           int beta_stride, int nrows, int64_t N, const cx<T>* __restrict__ tw, const int* __restrict__ active) {
+           int beta_stride, int nrows, int64_t N, const cx<T>* __restrict__ tw, int* __restrict__ active,
+           const cx<T>* __restrict__ krhat, KState* __restrict__ st, double2* __restrict__ part,
+           unsigned* __restrict__ cnt, int part_stride) {
     using C = cx<T>;
     using PL = Plan<LX>;
     constexpr int TP = tp_x<LX>(), SP = TP + 1, NX = LX / 2;
@@ -116,19 +169,43 @@ __global__ void __launch_bounds__(tp_x<LX>() * Plan<LX>::NT)
     C v[PL::E];
     auto first = [&](int pos) { return bt[pos * SP]; };
     auto ld = [&](int pos) { return bt[pos * SP]; };
-    auto st = [&](int pos, C val) { bt[pos * SP] = val; };
-    pencil_fft<C, PL, +1, false>(v, u, tw, first, ld, st);
+    auto stf = [&](int pos, C val) { bt[pos * SP] = val; };
+    pencil_fft<C, PL, +1, false>(v, u, tw, first, ld, stf);
     __syncthreads();
     for_each_out<PL, +1, true>(u, [&](int idx, int pos) { bt[pos * SP] = v[idx]; });
     __syncthreads();
-    const C* xs = X + ((int64_t)r * 3 + c) * N;
-    C* ys = Y + ((int64_t)r * 3 + c) * N;
+    const int64_t off = ((int64_t)r * 3 + c) * N;
+    const C* xs = X + off;
+    C* ys = Y + off;
     const C* br = beta + (int64_t)r * beta_stride;
+    DotAcc<C> d[2];
     for (int e = threadIdx.x; e < TP * NX; e += blockDim.x) {
         const int t2 = e / NX, ix = e - t2 * NX, row = row0 + t2;
         if (row < nrows) {
             const int s = site_of[(int64_t)row * NX + ix];
-            if (s >= 0) ys[s] = cadd(buf[ix * SP + t2], cmul(br[comp_of[s]], xs[s]));
+            if (s >= 0) {
+                const C xv = xs[s];
+                const C yv = cadd(buf[ix * SP + t2], cmul(br[comp_of[s]], xv));
+                ys[s] = yv;
+                if constexpr (MODE == 1) d[0].add_cdot(krhat[off + s], yv);
+                if constexpr (MODE == 2) {
+                    d[0].add_cdot(yv, xv);
+                    d[1].add_norm2(yv);
+                }
+            }
+        }
+    }
+    if constexpr (MODE != 0) {
+        constexpr int ND = MODE == 1 ? 1 : 2;
+        DotAcc<C> dd[ND];
+#pragma unroll
+        for (int k = 0; k < ND; ++k) dd[k] = d[k];
+        double2 acc[ND];
+        block_totals<C, ND>(dd, acc);
+        const int nb = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
+        if (last_block_combine<ND>(acc, part + (int64_t)r * part_stride, cnt + r, bid, nb) && threadIdx.x == 0) {
+            if constexpr (MODE == 1) finalize_alpha(st, active, r, acc[0]);
+            else finalize_omega(st, active, r, acc[0], acc[1].x);
         }
     }
 }
@@ -167,69 +244,97 @@ __global__ void __launch_bounds__(tp_s<L>() * Plan<L>::NT)
 }
 
 // ---- z pass with the Fourier-space product ------------------------------------
-// One block owns TP adjacent (kx) columns at one ky for one RHS; its threads
-// form three groups, one per Cartesian component c.  Group c transforms P_c
-// along z (input half zero), writes the spectrum to its shared-memory plane,
-// and after a barrier forms row c of the symmetric product
+// One block owns TP adjacent (kx) columns at one ky and up to RB right-hand
+// sides.  It first stages the Green-tensor entries of its columns in shared
+// memory -- kz <= LZ/2 of the octant, with the x and y reflection signs
+// already applied -- and reuses them for every RHS.  Per RHS its threads form
+// three groups, one per Cartesian component c: group c transforms P_c along z
+// (input half zero), writes the spectrum to its shared-memory plane, and
+// after a barrier forms row c of the symmetric product
 //   Y_c(k) = sum_b Ghat_cb(k) P_b(k)
 // for the points it holds, then inverse-transforms Y_c and keeps z < LZ/2.
-template <typename T, int LZ>
-__global__ void __launch_bounds__(3 * tp_z<LZ, T>() * Plan<LZ>::NT)
-    k_zconv(cx<T>* __restrict__ U2, const cx<T>* __restrict__ gh, int Lx, int Ly, const cx<T>* __restrict__ tw,
-            const int* __restrict__ active) {
+template <typename T, int LZ, int RB>
+__global__ void __launch_bounds__(3 * tp_z<LZ, T>() * ZPlan<LZ>::NT, zconv_min_blocks<LZ, T>())
+    k_zconv(cx<T>* __restrict__ U2, const cx<T>* __restrict__ gh, int R, int Lx, int Ly,
+            const cx<T>* __restrict__ tw, const int* __restrict__ active) {
     using C = cx<T>;
-    using PL = Plan<LZ>;
-    constexpr int TP = tp_z<LZ, T>(), NT = PL::NT, NZ = LZ / 2;
+    using PL = ZPlan<LZ>;
+    constexpr int TP = tp_z<LZ, T>(), SP = sp_z<LZ, T>(), NT = PL::NT, NZ = LZ / 2, HZ = LZ / 2 + 1;
     static_assert((TP * NT) % 32 == 0, "component groups must be whole warps");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);  // [3][LZ][TP]
-    const int ky = blockIdx.y, r = blockIdx.z;
-    if (active != nullptr && active[r] == 0) return;
+    C* buf = reinterpret_cast<C*>(smem_raw);   // spectra [3][LZ][SP]
+    C* gs = buf + 3 * LZ * SP;                 // Green tensor [6][HZ][SP]
+    const int ky = blockIdx.y;
+    const int r0 = blockIdx.z * RB;
+    const int hx = Lx / 2 + 1, hy = Ly / 2 + 1;
+    const int64_t cs = (int64_t)HZ * hy * hx;
+    {
+        const int kyo = ky <= Ly / 2 ? ky : Ly - ky;
+        const bool fy = ky > Ly / 2;
+        for (int e = threadIdx.x; e < 6 * HZ * TP; e += blockDim.x) {
+            const int tt = e % TP, kz = (e / TP) % HZ, cc = e / (TP * HZ);
+            const int kx = blockIdx.x * TP + tt;
+            C g = czero<C>();
+            if (kx < Lx) {
+                const bool fx = kx > Lx / 2;
+                const int kxo = fx ? Lx - kx : kx;
+                g = gh[cc * cs + ((int64_t)kz * hy + kyo) * hx + kxo];
+                // xy is odd in x and y, xz odd in x, yz odd in y (z handled at use)
+                const bool flip = (cc == 1 && fx != fy) || (cc == 2 && fx) || (cc == 4 && fy);
+                if (flip) g = cscale(g, T(-1));
+            }
+            gs[(cc * HZ + kz) * SP + tt] = g;
+        }
+    }
     const int t = threadIdx.x % TP;
     const int rest = threadIdx.x / TP;
     const int u = rest % NT, c = rest / NT;
     const int kx = blockIdx.x * TP + t;
     const bool valid = kx < Lx;
     const int64_t plane = (int64_t)Ly * Lx;
-    C* bc = U2 + ((int64_t)r * 3 + c) * NZ * plane + (int64_t)ky * Lx + (valid ? kx : 0);
-    C* sb = buf + c * (LZ * TP) + t;
-    auto ld = [&](int pos) { return sb[pos * TP]; };
-    auto st = [&](int pos, C val) { sb[pos * TP] = val; };
-    C v[PL::E];
-    auto first = [&](int pos) { return valid ? bc[pos * plane] : czero<C>(); };
-    pencil_fft<C, PL, -1, true>(v, u, tw, first, ld, st);
-    __syncthreads();
-    for_each_out<PL, -1, false>(u, [&](int idx, int pos) { sb[pos * TP] = v[idx]; });
-    __syncthreads();
-    // row c of the octant-stored symmetric tensor: components (xx,xy,xz,yy,yz,zz)
+    // row c of the symmetric tensor: components (xx,xy,xz,yy,yz,zz); entries
+    // that are odd in z change sign for kz > LZ/2
     const int i0 = c == 0 ? 0 : (c == 1 ? 1 : 2);
     const int i1 = c == 0 ? 1 : (c == 1 ? 3 : 4);
     const int i2 = c == 0 ? 2 : (c == 1 ? 4 : 5);
-    const int hx = Lx / 2 + 1, hy = Ly / 2 + 1, hz = LZ / 2 + 1;
-    const int kxv = valid ? kx : 0;
-    const int kxo = kxv <= Lx / 2 ? kxv : Lx - kxv;
-    const int kyo = ky <= Ly / 2 ? ky : Ly - ky;
-    const bool fx = kxv > Lx / 2, fy = ky > Ly / 2;
-    const int64_t cs = (int64_t)hz * hy * hx;
-    const C* g0 = gh + (int64_t)kyo * hx + kxo;
-    const C* p0b = buf + t;
-    for_each_out<PL, -1, false>(u, [&](int idx, int kz) {
-        const bool fz = kz > LZ / 2;
-        const int kzo = fz ? LZ - kz : kz;
-        const C* g = g0 + (int64_t)kzo * hy * hx;
-        // odd components flip sign under a reflection of one of their two axes
-        const bool sxy = fx != fy, sxz = fx != fz, syz = fy != fz;
-        C a0 = g[i0 * cs], a1 = g[i1 * cs], a2 = g[i2 * cs];
-        if (c == 0) { if (sxy) a1 = cscale(a1, T(-1)); if (sxz) a2 = cscale(a2, T(-1)); }
-        if (c == 1) { if (sxy) a0 = cscale(a0, T(-1)); if (syz) a2 = cscale(a2, T(-1)); }
-        if (c == 2) { if (sxz) a0 = cscale(a0, T(-1)); if (syz) a1 = cscale(a1, T(-1)); }
-        const C pa = p0b[kz * TP], pb = p0b[LZ * TP + kz * TP], pc = p0b[2 * LZ * TP + kz * TP];
-        v[idx] = cadd(cadd(cmul(a0, pa), cmul(a1, pb)), cmul(a2, pc));
-    });
-    pencil_fft_regs<C, PL, +1>(v, u, tw, ld, st);
-    for_each_out<PL, +1, true>(u, [&](int idx, int pos) {
-        if (valid) bc[pos * plane] = v[idx];
-    });
+    const bool z0 = (i0 == 2 || i0 == 4), z1 = (i1 == 2 || i1 == 4), z2 = (i2 == 2 || i2 == 4);
+    const C* g0 = gs + i0 * HZ * SP + t;
+    const C* g1 = gs + i1 * HZ * SP + t;
+    const C* g2 = gs + i2 * HZ * SP + t;
+    C* sb = buf + c * (LZ * SP) + t;
+    const C* pb = buf + t;
+    auto ld = [&](int pos) { return sb[pos * SP]; };
+    auto st = [&](int pos, C val) { sb[pos * SP] = val; };
+#pragma unroll 1
+    for (int rr = 0; rr < RB; ++rr) {
+        const int r = r0 + rr;
+        if (r >= R) break;
+        if (active != nullptr && active[r] == 0) continue;  // uniform across the block
+        C* bc = U2 + ((int64_t)r * 3 + c) * NZ * plane + (int64_t)ky * Lx + (valid ? kx : 0);
+        C v[PL::E];
+        auto first = [&](int pos) { return valid ? bc[pos * plane] : czero<C>(); };
+        __syncthreads();  // Green tile staged / previous RHS done with the spectra
+        pencil_fft<C, PL, -1, true>(v, u, tw, first, ld, st);
+        __syncthreads();
+        for_each_out<PL, -1, false>(u, [&](int idx, int pos) { sb[pos * SP] = v[idx]; });
+        __syncthreads();
+        for_each_out<PL, -1, false>(u, [&](int idx, int kz) {
+            const bool fz = kz > LZ / 2;
+            const int kzo = fz ? LZ - kz : kz;
+            C a0 = g0[kzo * SP], a1 = g1[kzo * SP], a2 = g2[kzo * SP];
+            if (fz) {
+                if (z0) a0 = cscale(a0, T(-1));
+                if (z1) a1 = cscale(a1, T(-1));
+                if (z2) a2 = cscale(a2, T(-1));
+            }
+            const C pa = pb[kz * SP], pbv = pb[(LZ + kz) * SP], pc = pb[(2 * LZ + kz) * SP];
+            v[idx] = cadd(cadd(cmul(a0, pa), cmul(a1, pbv)), cmul(a2, pc));
+        });
+        pencil_fft_regs<C, PL, +1>(v, u, tw, ld, st);
+        for_each_out<PL, +1, true>(u, [&](int idx, int pos) {
+            if (valid) bc[pos * plane] = v[idx];
+        });
+    }
 }
 
 // ---- Green tensor on the padded grid ------------------------------------------
@@ -381,31 +486,50 @@ static unsigned grid1d(int64_t n, int threads) {
 template <typename T> struct LaunchX {
     static constexpr int koff = sizeof(T) == 4 ? 0 : (KK_XFWD_C128 - KK_XFWD_C64);
     template <int LX>
-    static cudaError_t fwd(const Geom& g, int R, const cx<T>* x, cx<T>* u1, const int* site_of, const cx<T>* tw,
-                           const int* active, cudaStream_t st) {
+    static cudaError_t fwd(const Geom& g, int R, cx<T>* x, cx<T>* u1, const int* site_of, const cx<T>* tw,
+                           const int* active, const FusedKrylov<T>& fk, cudaStream_t st) {
         constexpr int TP = tp_x<LX>(), NTH = TP * Plan<LX>::NT;
         const size_t sm = (size_t)LX * (TP + 1) * sizeof(cx<T>);
-        cudaError_t e = allow_smem(k_xfwd<T, LX>, sm);
-        if (e != cudaSuccess) return e;
         const int nrows = g.ny * g.nz;
         dim3 grid((nrows + TP - 1) / TP, 3, R);
+        cudaError_t e;
         PROF_BEGIN(st);
-        k_xfwd<T, LX><<<grid, NTH, sm, st>>>(x, u1, site_of, nrows, g.N, tw, active);
+        if (fk.mode == 0) {
+            if ((e = allow_smem(k_xfwd<T, LX, 0>, sm)) != cudaSuccess) return e;
+            k_xfwd<T, LX, 0><<<grid, NTH, sm, st>>>(x, u1, site_of, nrows, g.N, tw, active, nullptr, nullptr, nullptr);
+        } else if (fk.mode == 1) {
+            if ((e = allow_smem(k_xfwd<T, LX, 1>, sm)) != cudaSuccess) return e;
+            k_xfwd<T, LX, 1><<<grid, NTH, sm, st>>>(x, u1, site_of, nrows, g.N, tw, active, fk.r, fk.v, fk.st);
+        } else {
+            if ((e = allow_smem(k_xfwd<T, LX, 2>, sm)) != cudaSuccess) return e;
+            k_xfwd<T, LX, 2><<<grid, NTH, sm, st>>>(x, u1, site_of, nrows, g.N, tw, active, fk.r, fk.v, fk.st);
+        }
         PROF_END(KK_XFWD_C64 + koff, R, st);
         return cudaGetLastError();
     }
     template <int LX>
     static cudaError_t inv(const Geom& g, int R, const cx<T>* u1, cx<T>* y, const cx<T>* x, const DevTarget& tg,
-                           const cx<T>* beta, int beta_stride, const cx<T>* tw, const int* active, cudaStream_t st) {
+                           const cx<T>* beta, int beta_stride, const cx<T>* tw, int* active,
+                           const FusedKrylov<T>& fk, cudaStream_t st) {
         constexpr int TP = tp_x<LX>(), NTH = TP * Plan<LX>::NT;
         const size_t sm = (size_t)LX * (TP + 1) * sizeof(cx<T>);
-        cudaError_t e = allow_smem(k_xinv<T, LX>, sm);
-        if (e != cudaSuccess) return e;
         const int nrows = g.ny * g.nz;
         dim3 grid((nrows + TP - 1) / TP, 3, R);
+        cudaError_t e;
         PROF_BEGIN(st);
-        k_xinv<T, LX><<<grid, NTH, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride, nrows, g.N, tw,
-                                            active);
+        if (fk.mode == 0) {
+            if ((e = allow_smem(k_xinv<T, LX, 0>, sm)) != cudaSuccess) return e;
+            k_xinv<T, LX, 0><<<grid, NTH, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride, nrows, g.N,
+                                                   tw, active, nullptr, nullptr, nullptr, nullptr, 0);
+        } else if (fk.mode == 1) {
+            if ((e = allow_smem(k_xinv<T, LX, 1>, sm)) != cudaSuccess) return e;
+            k_xinv<T, LX, 1><<<grid, NTH, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride, nrows, g.N,
+                                                   tw, active, fk.rhat, fk.st, fk.part, fk.cnt, fk.part_stride);
+        } else {
+            if ((e = allow_smem(k_xinv<T, LX, 2>, sm)) != cudaSuccess) return e;
+            k_xinv<T, LX, 2><<<grid, NTH, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride, nrows, g.N,
+                                                   tw, active, fk.rhat, fk.st, fk.part, fk.cnt, fk.part_stride);
+        }
         PROF_END(KK_XINV_C64 + koff, R, st);
         return cudaGetLastError();
     }
@@ -436,13 +560,20 @@ template <typename T> struct LaunchX {
     template <int LZ>
     static cudaError_t zconv(const Geom& g, int R, cx<T>* u2, const cx<T>* gh, const cx<T>* tw, const int* active,
                              cudaStream_t st) {
-        constexpr int TP = tp_z<LZ, T>(), NTH = 3 * TP * Plan<LZ>::NT;
-        const size_t sm = (size_t)3 * LZ * TP * sizeof(cx<T>);
-        cudaError_t e = allow_smem(k_zconv<T, LZ>, sm);
+        constexpr int TP = tp_z<LZ, T>(), NTH = 3 * TP * ZPlan<LZ>::NT;
+        const size_t sm = zconv_smem<LZ, T>();
+        // several RHS per block reuse the staged Green tensor
+        constexpr int RB = 8;
+        const bool multi = R > 1;
+        cudaError_t e = multi ? allow_smem(k_zconv<T, LZ, RB>, sm) : allow_smem(k_zconv<T, LZ, 1>, sm);
         if (e != cudaSuccess) return e;
-        dim3 grid((g.Lx + TP - 1) / TP, g.Ly, R);
+        const int rb = multi ? RB : 1;
+        dim3 grid((g.Lx + TP - 1) / TP, g.Ly, (R + rb - 1) / rb);
         PROF_BEGIN(st);
-        k_zconv<T, LZ><<<grid, NTH, sm, st>>>(u2, gh, g.Lx, g.Ly, tw, active);
+        if (multi)
+            k_zconv<T, LZ, RB><<<grid, NTH, sm, st>>>(u2, gh, R, g.Lx, g.Ly, tw, active);
+        else
+            k_zconv<T, LZ, 1><<<grid, NTH, sm, st>>>(u2, gh, R, g.Lx, g.Ly, tw, active);
         PROF_END(KK_ZCONV_C64 + koff, R, st);
         return cudaGetLastError();
     }
@@ -459,23 +590,45 @@ template <int LX> static cudaError_t launch_xfull(double2* data, int64_t nrows, 
     return cudaGetLastError();
 }
 
+int xinv_blocks_per_rhs(const Geom& g) {
+    const int nrows = g.ny * g.nz;
+    int tp = 1;
+    switch (g.Lx) {
+        case 16: tp = tp_x<16>(); break;
+        case 32: tp = tp_x<32>(); break;
+        case 48: tp = tp_x<48>(); break;
+        case 64: tp = tp_x<64>(); break;
+        case 96: tp = tp_x<96>(); break;
+        case 128: tp = tp_x<128>(); break;
+        case 192: tp = tp_x<192>(); break;
+        case 256: tp = tp_x<256>(); break;
+        case 384: tp = tp_x<384>(); break;
+        case 512: tp = tp_x<512>(); break;
+        default: tp = 1;
+    }
+    return 3 * ((nrows + tp - 1) / tp);
+}
+
 // The lattice seen by the kernels is padded with vacuum to exactly L/2 sites
-// per axis (g.nx == g.Lx/2, ...), see dda_set_target.
+// per axis (g.nx == g.Lx/2, ...), see dda_set_target.  With fk.mode != 0 the
+// x passes also carry the fused BiCGstab updates (see k_xfwd, k_xinv).
 template <typename T>
-cudaError_t launch_matvec(const Geom& g, int R, const cx<T>* x, cx<T>* y, const PadWork<T>& w, const DevTarget& tg,
-                          const cx<T>* beta, int beta_stride, const cx<T>* ghat, const Twiddles<T>& tw,
-                          const int* active, cudaStream_t st) {
+cudaError_t launch_matvec_fused(const Geom& g, int R, cx<T>* x, cx<T>* y, const PadWork<T>& w, const DevTarget& tg,
+                                const cx<T>* beta, int beta_stride, const cx<T>* ghat, const Twiddles<T>& tw,
+                                int* active, const FusedKrylov<T>& fk, cudaStream_t st) {
     using LX = LaunchX<T>;
     if (g.nx * 2 != g.Lx || g.ny * 2 != g.Ly || g.nz * 2 != g.Lz) return cudaErrorInvalidValue;
     cudaError_t e;
-    auto fwdx = [&]() -> cudaError_t { DDA_DISPATCH_L(g.Lx, LX::template fwd, g, R, x, w.u1, tg.site_of, tw.x, active, st); };
+    auto fwdx = [&]() -> cudaError_t {
+        DDA_DISPATCH_L(g.Lx, LX::template fwd, g, R, x, w.u1, tg.site_of, tw.x, active, fk, st);
+    };
     auto ys = [&](int mode, const cx<T>* s, cx<T>* d, int64_t sb, int64_t db) -> cudaError_t {
         DDA_DISPATCH_L(g.Ly, LX::template strided, mode, s, d, (int64_t)g.Lx, g.Lx, sb, db, R * 3 * g.nz, 3 * g.nz,
                        tw.y, active, st, (mode == 0 ? KK_YFWD_C64 : KK_YINV_C64) + LX::koff, (double)R);
     };
     auto zc = [&]() -> cudaError_t { DDA_DISPATCH_L(g.Lz, LX::template zconv, g, R, w.u2, ghat, tw.z, active, st); };
     auto invx = [&]() -> cudaError_t {
-        DDA_DISPATCH_L(g.Lx, LX::template inv, g, R, w.u1, y, x, tg, beta, beta_stride, tw.x, active, st);
+        DDA_DISPATCH_L(g.Lx, LX::template inv, g, R, w.u1, y, x, tg, beta, beta_stride, tw.x, active, fk, st);
     };
     if ((e = fwdx()) != cudaSuccess) return e;
     if ((e = ys(0, w.u1, w.u2, (int64_t)g.ny * g.Lx, (int64_t)g.Ly * g.Lx)) != cudaSuccess) return e;
@@ -484,12 +637,30 @@ cudaError_t launch_matvec(const Geom& g, int R, const cx<T>* x, cx<T>* y, const 
     return invx();
 }
 
+template <typename T>
+cudaError_t launch_matvec(const Geom& g, int R, const cx<T>* x, cx<T>* y, const PadWork<T>& w, const DevTarget& tg,
+                          const cx<T>* beta, int beta_stride, const cx<T>* ghat, const Twiddles<T>& tw,
+                          const int* active, cudaStream_t st) {
+    FusedKrylov<T> plain{};
+    // mode 0 neither writes x nor clears active flags
+    return launch_matvec_fused<T>(g, R, const_cast<cx<T>*>(x), y, w, tg, beta, beta_stride, ghat, tw,
+                                  const_cast<int*>(active), plain, st);
+}
+
 template cudaError_t launch_matvec<float>(const Geom&, int, const float2*, float2*, const PadWork<float>&,
                                           const DevTarget&, const float2*, int, const float2*, const Twiddles<float>&,
                                           const int*, cudaStream_t);
 template cudaError_t launch_matvec<double>(const Geom&, int, const double2*, double2*, const PadWork<double>&,
                                            const DevTarget&, const double2*, int, const double2*,
                                            const Twiddles<double>&, const int*, cudaStream_t);
+template cudaError_t launch_matvec_fused<float>(const Geom&, int, float2*, float2*, const PadWork<float>&,
+                                                const DevTarget&, const float2*, int, const float2*,
+                                                const Twiddles<float>&, int*, const FusedKrylov<float>&,
+                                                cudaStream_t);
+template cudaError_t launch_matvec_fused<double>(const Geom&, int, double2*, double2*, const PadWork<double>&,
+                                                 const DevTarget&, const double2*, int, const double2*,
+                                                 const Twiddles<double>&, int*, const FusedKrylov<double>&,
+                                                 cudaStream_t);
 
 cudaError_t launch_green_fft(const Geom& g, double kd, double2* scratch, double2* ghat64, const Twiddles<double>& tw,
                              cudaStream_t st) {

@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--fp64-sequential", action="store_true",
                     help="FP64 leg solves the RHS one at a time (orientation-sweep comparison)")
-    ap.add_argument("--mode", default="solve", choices=["solve", "matvec"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "matvec", "grad"],
                     help="matvec: only time dda_matvec_device (for profiler captures)")
     ap.add_argument("--rhs", type=int, default=0, help="matvec mode: RHS per product (0 = workload's)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="matvec mode precision")
@@ -181,6 +181,32 @@ def pass_flops(kind, info, R):
     if kind.startswith("z_conv"):
         return R * (2 * 3 * Lx * Ly * f(Lz) + 66 * Lx * Ly * Lz)
     return None
+
+
+KERNEL_SOURCES = ["paper_1202_3424_gb300/csrc/matvec.cu", "paper_1202_3424_gb300/csrc/fft.cuh",
+                  "paper_1202_3424_gb300/csrc/krylov_dev.cuh", "paper_1202_3424_gb300/csrc/common.cuh"]
+CAPTURES = {("z_conv_c64", "sphere64", 2): "profiles/zconv_f32_sphere64.md"}
+
+
+def captured_traffic(kernel, workload_name, rhs_per_launch):
+    """DRAM bytes per launch from the committed ncu summary of this kernel and
+    workload, or None when there is none or the kernel source has changed
+    since the capture (the summary records a hash of the sources)."""
+    import hashlib
+    path = CAPTURES.get((kernel, workload_name, int(round(rhs_per_launch))))
+    if path is None or not os.path.exists(os.path.join(ROOT, path)):
+        return None
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    sha, traffic = None, None
+    for line in open(os.path.join(ROOT, path)):
+        if line.startswith("source_sha256:"):
+            sha = line.split()[1]
+        if line.startswith("traffic_bytes_per_launch:"):
+            traffic = int(line.split()[1])
+    return traffic if sha is not None and h.hexdigest().startswith(sha) else None
 
 
 def load_peaks():
@@ -315,7 +341,7 @@ def run_gb300(args):
                "h2d_bytes_per_step": int(k.nbytes + e.nbytes), "d2h_bytes_per_step": int(P_host.nbytes + 72 * R),
                "time_to_solution_ms": t_e2e * 1e3 / args.steps}
 
-    roof = roofline(kstats, info, R)
+    roof = roofline(kstats, info, R, w.name)
     launches = int(sum(s["launches"] for s in kstats.values()) / args.steps) * args.steps if kstats else 0
 
     cpu = None
@@ -367,7 +393,7 @@ def read_profile(dda, ctx):
     return out
 
 
-def roofline(kstats, info, R):
+def roofline(kstats, info, R, workload_name=None):
     if not kstats:
         return None
     hbm, src = load_peaks()
@@ -385,8 +411,10 @@ def roofline(kstats, info, R):
                 "rhs_per_launch": units_per_launch, "peak_source": "derived FP64 (152 SM x 2 DFMA/clk x 2.07 GHz)"}
     b = pass_bytes(name, info, units_per_launch)
     ach = b / (avg_ms / 1e3) / 1e9
+    traffic = captured_traffic(name, workload_name, units_per_launch)
     return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-            "traffic": None, "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": b,
+            "traffic": traffic, "traffic_note": "ncu cold-cache DRAM bytes per launch (profiles/)" if traffic else None,
+            "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": b,
             "rhs_per_launch": units_per_launch, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
 
 
@@ -492,11 +520,39 @@ def run_matvec_only(args):
     ctx.close()
 
 
+def run_grad(args):
+    """Time dda_grad_qabs (forward solve + adjoint solve + gradient) in FP64."""
+    import torch
+    import paper_1202_3424_gb300 as dda
+    w = workload(args.workload)
+    ctx = dda.Context(0)
+    ctx.set_target(w.grid)
+    ctx.set_materials(w.m)
+    ctx.prepare_size_parameter(w.x, dda.Precision.FP32_REFINED)
+    k, e = w.khat[:1], w.ehat[:1]
+    out = {}
+    for name, prec in (("fp64", dda.Precision.FP64), ("fp32_refined", dda.Precision.FP32_REFINED)):
+        for _ in range(max(1, args.warmup)):
+            ctx.grad_qabs(prec, k, e, tol=1e-5)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            gre, gim, P, (rf, ra) = ctx.grad_qabs(prec, k, e, tol=1e-5)
+        torch.cuda.synchronize()
+        out[name] = {"ms_per_gradient": (time.perf_counter() - t0) * 1e3 / args.steps,
+                     "forward_iters": rf["iters"], "adjoint_iters": ra["iters"], "qabs": rf["qabs"],
+                     "grad_norm": float(np.sqrt(np.sum(gre ** 2 + gim ** 2)))}
+    print(json.dumps({"mode": "grad", "workload": w.name, "ndipoles": ctx.info()["ndipoles"], **out}), flush=True)
+    ctx.close()
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.mode == "matvec":
         run_matvec_only(a)
+    elif a.mode == "grad":
+        run_grad(a)
     else:
         run_gb300(a)

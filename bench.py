@@ -183,8 +183,9 @@ def pass_flops(kind, info, R):
     return None
 
 
-KERNEL_SOURCES = ["paper_1202_3424_gb300/csrc/matvec.cu", "paper_1202_3424_gb300/csrc/fft.cuh",
-                  "paper_1202_3424_gb300/csrc/krylov_dev.cuh", "paper_1202_3424_gb300/csrc/common.cuh"]
+KERNEL_SOURCES = ["paper_1202_3424_gb300/csrc/matvec_impl.cuh", "paper_1202_3424_gb300/csrc/matvec_f32.cu",
+                  "paper_1202_3424_gb300/csrc/fft.cuh", "paper_1202_3424_gb300/csrc/krylov_dev.cuh",
+                  "paper_1202_3424_gb300/csrc/common.cuh"]
 CAPTURES = {("z_conv_c64", "sphere64", 2): "profiles/zconv_f32_sphere64.md"}
 
 
@@ -198,7 +199,10 @@ def captured_traffic(kernel, workload_name, rhs_per_launch):
         return None
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
+        fp = os.path.join(ROOT, f)
+        if not os.path.exists(fp):
+            return None
+        with open(fp, "rb") as fh:
             h.update(fh.read())
     sha, traffic = None, None
     for line in open(os.path.join(ROOT, path)):

@@ -69,7 +69,10 @@ typedef enum {
 typedef enum {
     DDA_FP64 = 0,         /* complex128 matvec and vectors, FP64 scalars                     */
     DDA_FP32_REFINED = 1, /* complex64 matvec in an FP64 iterative-refinement loop           */
-    DDA_FP32 = 2          /* complex64 matvec and vectors, FP64 scalars (no refinement)      */
+    DDA_FP32 = 2,         /* complex64 matvec and vectors, FP64 scalars (no refinement)      */
+    DDA_DF64 = 3          /* matvec entry points only: complex128 vectors, arithmetic in
+                             double-float (pairs of FP32, ~44 significant bits); the
+                             arithmetic of the complex64 modes' refinement residuals       */
 } dda_precision;
 
 typedef struct {
@@ -80,6 +83,9 @@ typedef struct {
     int max_outer;     /* max refinement (outer) steps; <= 0 selects 8                       */
     int normal_eq;     /* 1: also report |A^H A P - A^H E| / |A^H E| (eq. err_tol)          */
     const double* x0;  /* nullable initial guess, [R][3][N] complex (warm start / resume)    */
+    int residual_fp64; /* complex64 modes: 1 = true residuals E - A P with native FP64
+                          arithmetic; 0 (default) = double-float arithmetic (FP32 pipes,
+                          ~1e-12 relative accuracy, 6-8x faster on GB300)                  */
 } dda_opts;
 
 typedef struct {
@@ -139,12 +145,13 @@ dda_status dda_solve_device(dda_ctx* ctx, dda_precision precision, int R, const 
                             const dda_opts* opts, void* P_dev, dda_result* res);
 
 /* One product y = A x for R RHS (A's diagonal depends on each RHS through S).
- * x, y: host [R][3][N] complex.  precision DDA_FP64 or DDA_FP32 (x rounded to
- * complex64, result widened back).  For testing and timing.                   */
+ * x, y: host [R][3][N] complex.  precision DDA_FP64, DDA_DF64 (needs an FP32
+ * mode prepared), or DDA_FP32 (x rounded to complex64, result widened back).
+ * For testing and timing.                                                      */
 dda_status dda_matvec(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* e,
                       const double* x, double* y);
 /* Device variant: x, y device buffers of R*3*N complex elements of the
- * precision's type (double2 for DDA_FP64, float2 for DDA_FP32).               */
+ * precision's type (double2 for DDA_FP64 and DDA_DF64, float2 for DDA_FP32).  */
 dda_status dda_matvec_device(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* e,
                              const void* x_dev, void* y_dev);
 

@@ -35,6 +35,7 @@ class Precision:
     FP64 = 0
     FP32_REFINED = 1
     FP32 = 2
+    DF64 = 3  # matvec only: double-float arithmetic on complex128 vectors
 
 
 class DdaError(RuntimeError):
@@ -47,7 +48,7 @@ class DdaError(RuntimeError):
 class dda_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("normal_eq", ctypes.c_int),
-                ("x0", ctypes.POINTER(ctypes.c_double))]
+                ("x0", ctypes.POINTER(ctypes.c_double)), ("residual_fp64", ctypes.c_int)]
 
 
 class dda_result(ctypes.Structure):
@@ -133,7 +134,8 @@ def _rhs(khat, e):
     return k, ev.view(np.float64).reshape(k.shape[0], 6).copy(), k.shape[0]
 
 
-def _opts(tol=1e-5, maxit=1000, use_graph=True, inner_tol=0.0, max_outer=0, normal_eq=False, x0=None):
+def _opts(tol=1e-5, maxit=1000, use_graph=True, inner_tol=0.0, max_outer=0, normal_eq=False, x0=None,
+          residual_fp64=False):
     o = dda_opts()
     o.tol = tol
     o.maxit = maxit
@@ -141,6 +143,7 @@ def _opts(tol=1e-5, maxit=1000, use_graph=True, inner_tol=0.0, max_outer=0, norm
     o.inner_tol = inner_tol
     o.max_outer = max_outer
     o.normal_eq = 1 if normal_eq else 0
+    o.residual_fp64 = 1 if residual_fp64 else 0
     keep = None
     if x0 is not None:
         keep = np.ascontiguousarray(x0, dtype=np.complex128).view(np.float64)

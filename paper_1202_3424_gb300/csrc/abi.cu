@@ -70,6 +70,7 @@ struct dda_ctx {
     bool prepared = false, has32 = false;
     double kd = 0.0, aeff_lat = 0.0;
     DevMem m_gh64, m_gh32, m_tw64[3], m_tw32[3];
+    DevMem m_ghdf, m_twdf[3];  // double-float copies for the refinement residual
 
     // workspace
     std::vector<DevMem> pool;  // generic named slots, see slot()
@@ -123,6 +124,7 @@ enum Slot {
     S_PART, S_CNT, S_QSUM, S_COUNT,
     S_BETA64, S_BETA32, S_W, S_KHAT, S_EPOL,
     S_MV_X32, S_MV_Y32, S_GRAD, S_DBETA,
+    S_BETADF, S_XDF, S_YDF,
     S_NSLOTS
 };
 
@@ -203,10 +205,12 @@ dda_status upload_tables(dda_ctx* ctx, int R, const std::vector<double>& k, cons
     std::vector<double2> b64((size_t)R * BS);
     std::vector<float2> b32((size_t)R * BS);
     std::vector<double> w((size_t)R * BS);
+    std::vector<cdfl> bdf((size_t)R * BS);
     const double kd = ctx->kd;
     for (int r = 0; r < R; ++r) {
         b64[(size_t)r * BS] = make_double2(0.0, 0.0);
         b32[(size_t)r * BS] = make_float2(0.f, 0.f);
+        bdf[(size_t)r * BS] = cdfl{dfl(0.0), dfl(0.0)};
         w[(size_t)r * BS] = 0.0;
         for (int c = 1; c < BS; ++c) {
             const cd mrel = ctx->m[c - 1] / ctx->m_amb;
@@ -215,6 +219,7 @@ dda_status upload_tables(dda_ctx* ctx, int R, const std::vector<double>& k, cons
                 return ctx->fail(DDA_ERR_NONFINITE, "polarizability of composition %d is not finite", c);
             b64[(size_t)r * BS + c] = make_double2(be.real(), be.imag());
             b32[(size_t)r * BS + c] = make_float2((float)be.real(), (float)be.imag());
+            bdf[(size_t)r * BS + c] = cdfl{dfl(be.real()), dfl(be.imag())};
             w[(size_t)r * BS + c] = -be.imag() - (2.0 / 3.0) * kd * kd * kd;
         }
     }
@@ -224,6 +229,8 @@ dda_status upload_tables(dda_ctx* ctx, int R, const std::vector<double>& k, cons
     if ((s = ensure(ctx, ctx->pool[S_W], w.size() * sizeof(double))) != DDA_OK) return s;
     CU(cudaMemcpyAsync(ctx->pool[S_BETA64].p, b64.data(), b64.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(ctx->pool[S_BETA32].p, b32.data(), b32.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->stream));
+    if ((s = ensure(ctx, ctx->pool[S_BETADF], bdf.size() * sizeof(cdfl))) != DDA_OK) return s;
+    CU(cudaMemcpyAsync(ctx->pool[S_BETADF].p, bdf.data(), bdf.size() * sizeof(cdfl), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(ctx->pool[S_W].p, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     std::vector<double2> e2(3 * (size_t)R);
     for (size_t i = 0; i < e2.size(); ++i) e2[i] = make_double2(e[i].real(), e[i].imag());
@@ -249,10 +256,13 @@ template <typename T> int matvec_chunk(const dda_ctx* ctx, int R) {
 template <typename T> struct PadSlots;
 template <> struct PadSlots<float> { static constexpr int a = S_PAD1_32, b = S_PAD2_32; };
 template <> struct PadSlots<double> { static constexpr int a = S_PAD1_64, b = S_PAD2_64; };
+// double-float elements are 16 bytes like complex128: share its work buffers
+template <> struct PadSlots<dfl> { static constexpr int a = S_PAD1_64, b = S_PAD2_64; };
 
 template <typename T> const cx<T>* ghat_of(const dda_ctx* ctx);
 template <> const float2* ghat_of<float>(const dda_ctx* ctx) { return (const float2*)ctx->m_gh32.p; }
 template <> const double2* ghat_of<double>(const dda_ctx* ctx) { return (const double2*)ctx->m_gh64.p; }
+template <> const cdfl* ghat_of<dfl>(const dda_ctx* ctx) { return (const cdfl*)ctx->m_ghdf.p; }
 template <typename T> Twiddles<T> tw_of(const dda_ctx* ctx);
 template <> Twiddles<float> tw_of<float>(const dda_ctx* ctx) {
     return {(const float2*)ctx->m_tw32[0].p, (const float2*)ctx->m_tw32[1].p, (const float2*)ctx->m_tw32[2].p};
@@ -260,9 +270,13 @@ template <> Twiddles<float> tw_of<float>(const dda_ctx* ctx) {
 template <> Twiddles<double> tw_of<double>(const dda_ctx* ctx) {
     return {(const double2*)ctx->m_tw64[0].p, (const double2*)ctx->m_tw64[1].p, (const double2*)ctx->m_tw64[2].p};
 }
+template <> Twiddles<dfl> tw_of<dfl>(const dda_ctx* ctx) {
+    return {(const cdfl*)ctx->m_twdf[0].p, (const cdfl*)ctx->m_twdf[1].p, (const cdfl*)ctx->m_twdf[2].p};
+}
 template <typename T> const cx<T>* beta_of(dda_ctx* ctx);
 template <> const float2* beta_of<float>(dda_ctx* ctx) { return slot<float2>(ctx, S_BETA32); }
 template <> const double2* beta_of<double>(dda_ctx* ctx) { return slot<double2>(ctx, S_BETA64); }
+template <> const cdfl* beta_of<dfl>(dda_ctx* ctx) { return slot<cdfl>(ctx, S_BETADF); }
 
 template <typename T> dda_status ensure_pad(dda_ctx* ctx, int R) {
     const int rc = matvec_chunk<T>(ctx, R);
@@ -285,6 +299,21 @@ dda_status run_matvec(dda_ctx* ctx, int R, const cx<T>* x, cx<T>* y, const int* 
                             beta_of<T>(ctx) + (int64_t)r0 * BS, BS, ghat_of<T>(ctx), tw_of<T>(ctx),
                             active ? active + r0 : nullptr, ctx->stream));
     }
+    return DDA_OK;
+}
+
+// Y = A X for FP64 vectors: native complex128 arithmetic, or (df) the
+// double-float matvec on converted copies.
+dda_status matvec64(dda_ctx* ctx, int R, const double2* X, double2* Y, const int* active, bool df) {
+    if (!df) return run_matvec<double>(ctx, R, X, Y, active);
+    const int64_t n = (int64_t)R * 3 * ctx->g.N;
+    dda_status rs;
+    if ((rs = ensure(ctx, ctx->pool[S_XDF], n * sizeof(cdfl))) != DDA_OK) return rs;
+    if ((rs = ensure(ctx, ctx->pool[S_YDF], n * sizeof(cdfl))) != DDA_OK) return rs;
+    if ((rs = ensure_pad<dfl>(ctx, R)) != DDA_OK) return rs;
+    CU(launch_convert_c128_to_df(X, slot<cdfl>(ctx, S_XDF), n, ctx->stream));
+    if ((rs = run_matvec<dfl>(ctx, R, slot<cdfl>(ctx, S_XDF), slot<cdfl>(ctx, S_YDF), active)) != DDA_OK) return rs;
+    CU(launch_convert_df_to_c128(slot<cdfl>(ctx, S_YDF), Y, n, ctx->stream));
     return DDA_OK;
 }
 
@@ -456,6 +485,8 @@ dda_status solve_core(dda_ctx* ctx, int R, const dda_opts& o, bool refine, bool 
     const int64_t n = 3 * ctx->g.N;
     cudaStream_t s = ctx->stream;
     dda_status rs;
+    // refinement residuals of the complex64 modes in double-float unless FP64 is asked for
+    const bool df_resid = (sizeof(T) == 4) && !o.residual_fp64 && ctx->m_ghdf.p != nullptr;
     if ((rs = ensure_common(ctx, R)) != DDA_OK) return rs;
     if ((rs = ensure_inner<T>(ctx, R)) != DDA_OK) return rs;
     if ((rs = ensure_pad<double>(ctx, R)) != DDA_OK) return rs;
@@ -475,7 +506,7 @@ dda_status solve_core(dda_ctx* ctx, int R, const dda_opts& o, bool refine, bool 
     CU(launch_residual(R, n, E, nullptr, nullptr, slot<double>(ctx, S_NORM_B), nullptr, part, cnt, s));
     if (have_x0) {
         CU(cudaMemcpyAsync(outer, hact.data(), R * sizeof(int), cudaMemcpyHostToDevice, s));
-        if ((rs = run_matvec<double>(ctx, R, X, Y, nullptr)) != DDA_OK) return rs;
+        if ((rs = matvec64(ctx, R, X, Y, nullptr, df_resid)) != DDA_OK) return rs;
         CU(launch_residual(R, n, E, Y, Rr, slot<double>(ctx, S_NORM_R), nullptr, part, cnt, s));
         for (auto& t : tr) t.mv += 1;
     } else {
@@ -534,7 +565,7 @@ dda_status solve_core(dda_ctx* ctx, int R, const dda_opts& o, bool refine, bool 
         if ((rs = inner_solve<T>(ctx, R, o.maxit, o.use_graph != 0)) != DDA_OK) return rs;
         CU(cudaMemcpyAsync(hst.data(), ctx->pool[S_STATE].p, R * sizeof(KState), cudaMemcpyDeviceToHost, s));
         CU(KrylovOps<cx<T>>::accumulate(R, n, X, in.x, slot<double>(ctx, S_COEF), outer, s));
-        if ((rs = run_matvec<double>(ctx, R, X, Y, outer)) != DDA_OK) return rs;
+        if ((rs = matvec64(ctx, R, X, Y, outer, df_resid)) != DDA_OK) return rs;
         CU(launch_residual(R, n, E, Y, Rr, slot<double>(ctx, S_NORM_R), outer, part, cnt, s));
         CU(cudaMemcpyAsync(hr.data(), ctx->pool[S_NORM_R].p, R * sizeof(double), cudaMemcpyDeviceToHost, s));
         CU(sync_collect(ctx));
@@ -600,6 +631,7 @@ dda_opts default_opts() {
     o.max_outer = 0;
     o.normal_eq = 0;
     o.x0 = nullptr;
+    o.residual_fp64 = 0;
     return o;
 }
 
@@ -798,9 +830,11 @@ dda_status dda_destroy(dda_ctx* ctx) {
     free_mem(ctx->m_comp_of);
     free_mem(ctx->m_gh64);
     free_mem(ctx->m_gh32);
+    free_mem(ctx->m_ghdf);
     for (int a = 0; a < 3; ++a) {
         free_mem(ctx->m_tw64[a]);
         free_mem(ctx->m_tw32[a]);
+        free_mem(ctx->m_twdf[a]);
     }
     ctx->prof.release();
     if (ctx->h_count) cudaFreeHost(ctx->h_count);
@@ -919,6 +953,10 @@ dda_status dda_prepare(dda_ctx* ctx, double lambda_vac, double aeff, dda_precisi
         if ((s = ensure(ctx, ctx->m_tw32[a], t32.size() * sizeof(float2))) != DDA_OK) return s;
         CU(cudaMemcpy(ctx->m_tw64[a].p, t64.data(), t64.size() * sizeof(double2), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(ctx->m_tw32[a].p, t32.data(), t32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        std::vector<cdfl> tdf(t64.size());
+        for (size_t i = 0; i < t64.size(); ++i) tdf[i] = cdfl{dfl(t64[i].x), dfl(t64[i].y)};
+        if ((s = ensure(ctx, ctx->m_twdf[a], tdf.size() * sizeof(cdfl))) != DDA_OK) return s;
+        CU(cudaMemcpy(ctx->m_twdf[a].p, tdf.data(), tdf.size() * sizeof(cdfl), cudaMemcpyHostToDevice));
     }
     const int64_t oct = 6 * g.oct_per_comp();
     if ((s = ensure(ctx, ctx->m_gh64, oct * sizeof(double2))) != DDA_OK) return s;
@@ -934,6 +972,8 @@ dda_status dda_prepare(dda_ctx* ctx, double lambda_vac, double aeff, dda_precisi
     if (precision != DDA_FP64) {
         if ((s = ensure(ctx, ctx->m_gh32, oct * sizeof(float2))) != DDA_OK) return s;
         CU(launch_convert_c128_to_c64((const double2*)ctx->m_gh64.p, (float2*)ctx->m_gh32.p, oct, ctx->stream));
+        if ((s = ensure(ctx, ctx->m_ghdf, oct * sizeof(cdfl))) != DDA_OK) return s;
+        CU(launch_convert_c128_to_df((const double2*)ctx->m_gh64.p, (cdfl*)ctx->m_ghdf.p, oct, ctx->stream));
         CU(sync_collect(ctx));
         ctx->has32 = true;
     }
@@ -995,7 +1035,16 @@ dda_status dda_solve_device(dda_ctx* ctx, dda_precision precision, int R, const 
 static dda_status matvec_common(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* e,
                                 const void* x_dev, void* y_dev) {
     dda_status rs;
-    if (precision == DDA_FP32_REFINED) return ctx->fail(DDA_ERR_ARG, "matvec precision must be DDA_FP64 or DDA_FP32");
+    if (precision == DDA_FP32_REFINED)
+        return ctx->fail(DDA_ERR_ARG, "matvec precision must be DDA_FP64, DDA_FP32 or DDA_DF64");
+    if (precision == DDA_DF64) {
+        if ((rs = check_ready(ctx, DDA_FP32_REFINED)) != DDA_OK) return rs;
+        std::vector<double> k;
+        std::vector<cd> ev;
+        if ((rs = check_rhs(ctx, R, khat, e, k, ev)) != DDA_OK) return rs;
+        if ((rs = upload_tables(ctx, R, k, ev)) != DDA_OK) return rs;
+        return matvec64(ctx, R, (const double2*)x_dev, (double2*)y_dev, nullptr, true);
+    }
     if ((rs = check_ready(ctx, precision)) != DDA_OK) return rs;
     std::vector<double> k;
     std::vector<cd> ev;

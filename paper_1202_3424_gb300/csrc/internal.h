@@ -95,5 +95,7 @@ cudaError_t launch_green_fft(const Geom& g, double kd, double2* scratch, double2
                              const Twiddles<double>& tw, cudaStream_t st);
 
 cudaError_t launch_convert_c128_to_c64(const double2* src, float2* dst, int64_t n, cudaStream_t st);
+cudaError_t launch_convert_c128_to_df(const double2* src, cdfl* dst, int64_t n, cudaStream_t st);
+cudaError_t launch_convert_df_to_c128(const cdfl* src, double2* dst, int64_t n, cudaStream_t st);
 
 }  // namespace dda

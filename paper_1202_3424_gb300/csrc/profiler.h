@@ -13,6 +13,7 @@ namespace dda {
 enum KernelKind : int {
     KK_XFWD_C64, KK_YFWD_C64, KK_ZCONV_C64, KK_YINV_C64, KK_XINV_C64,
     KK_XFWD_C128, KK_YFWD_C128, KK_ZCONV_C128, KK_YINV_C128, KK_XINV_C128,
+    KK_XFWD_DF, KK_YFWD_DF, KK_ZCONV_DF, KK_YINV_DF, KK_XINV_DF,
     KK_KRYLOV_C64, KK_KRYLOV_C128, KK_REFINE, KK_EINC, KK_QSUMS, KK_GREEN, KK_OTHER,
     KK_COUNT
 };

@@ -65,7 +65,7 @@ MATVEC_CASES = [
 
 
 @pytest.mark.parametrize("name,gridf,m,x", MATVEC_CASES, ids=[c[0] for c in MATVEC_CASES])
-@pytest.mark.parametrize("prec,tol", [(0, F64_TOL), (2, F32_TOL)], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("prec,tol", [(0, F64_TOL), (3, F64_TOL), (2, F32_TOL)], ids=["fp64", "df64", "fp32"])
 def test_matvec_matches_pairwise_oracle(lib, name, gridf, m, x, prec, tol):
     grid = gridf()
     ctx = _ctx(lib, grid, m, x, lib.Precision.FP32_REFINED)
@@ -107,7 +107,7 @@ def test_matvec_row_samples_full_size(lib, name):
     X = random_complex((R, 3, N), 5)
     rows = np.random.default_rng(9).choice(N, 48, replace=False)
     rows[:2] = [0, N - 1]
-    for prec, tol in ((0, F64_TOL), (2, F32_TOL)):
+    for prec, tol in ((0, F64_TOL), (3, F64_TOL), (2, F32_TOL)):
         Y = ctx.matvec(prec, w.khat[:R], w.ehat[:R], X)
         for r in range(R):
             rr, beta = _site_beta(w.grid, w.m, kd, w.khat[r], w.ehat[r])
@@ -280,7 +280,26 @@ def test_launch_tracing_counts_and_leaves_results_unchanged(lib):
     zl, zms, zu = stats["z_conv_c64"]
     assert zl >= 2 * it and zl % 8 == 0          # 2 matvecs per iteration, blocks of 4 iterations
     assert zu == 2 * zl and zms > 0               # both RHS in every launch
-    assert stats["z_conv_c128"][0] == max(r["outer_iters"] for r in traced)
+    # one true-residual matvec per refinement step, in double-float arithmetic by default
+    assert stats["z_conv_df"][0] == max(r["outer_iters"] for r in traced)
     for name in ("x_fwd_c64", "y_fwd_c64", "y_inv_c64", "x_inv_c64"):
         assert stats[name][0] == zl
+    ctx.close()
+
+
+def test_refinement_residual_double_float_equals_fp64(lib):
+    """The complex64 modes check their true residual with a double-float
+    matvec by default; native FP64 arithmetic gives the same answers."""
+    grid = ellipsoid_grid(20, 16, 12, 20, 16, 12)
+    ctx = _ctx(lib, grid, [1.5 + 0.02j], 3.0, lib.Precision.FP32_REFINED)
+    k, e = _rhs_set(3)
+    a, Pa, sa = ctx.solve(1, k, e, tol=1e-6)
+    b, Pb, sb = ctx.solve(1, k, e, tol=1e-6, residual_fp64=True)
+    assert sa == 0 and sb == 0
+    for ra, rb in zip(a, b):
+        assert ra["iters"] == rb["iters"] and ra["outer_iters"] == rb["outer_iters"]
+        assert abs(ra["resid_rel"] - rb["resid_rel"]) <= 1e-6 * rb["resid_rel"]
+        for q in ("qext", "qabs", "qsca"):
+            assert abs(ra[q] - rb[q]) <= 1e-11 * abs(rb[q])
+    assert np.abs(Pa - Pb).max() <= 1e-11 * np.abs(Pb).max()
     ctx.close()

@@ -59,6 +59,8 @@ def parse():
                     help="matvec: only time dda_matvec_device (for profiler captures)")
     ap.add_argument("--rhs", type=int, default=0, help="matvec mode: RHS per product (0 = workload's)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="matvec mode precision")
+    ap.add_argument("--zpass", type=int, default=-1, choices=[-1, 0, 1],
+                    help="complex64 z-pass schedule: -1 autotuned, 0 component groups, 1 register-resident")
     return ap.parse_args()
 
 
@@ -489,6 +491,7 @@ def run_matvec_only(args):
     ctx.set_target(w.grid)
     ctx.set_materials(w.m)
     ctx.prepare_size_parameter(w.x, dda.Precision.FP32_REFINED)
+    ctx.set_schedule(args.zpass)
     N = ctx.info()["ndipoles"]
     k = np.resize(w.khat, (R, 3))
     e = np.resize(w.ehat, (R, 3))
@@ -519,7 +522,8 @@ def run_matvec_only(args):
         avg = v["ms"] / v["launches"]
         b = pass_bytes(name, info, v["units"] / v["launches"])
         kern[name] = {"avg_ms": avg, "gbs": (b / (avg / 1e3) / 1e9) if b else None}
-    print(json.dumps({"mode": "matvec", "workload": w.name, "rhs": R, "precision": args.precision,
+    zpass = ctx.get_schedule(R) if args.precision == "fp32" else 0
+    print(json.dumps({"mode": "matvec", "workload": w.name, "rhs": R, "precision": args.precision, "zpass": zpass,
                       "ms_per_matvec": ms, "rhs_matvecs_per_s": R / (ms / 1e3), "kernels": kern}), flush=True)
     ctx.close()
 

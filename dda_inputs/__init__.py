@@ -148,6 +148,12 @@ def workload(name: str) -> Workload:
     if name == "sphere256":
         k, e = _sweep(8)
         return Workload(name, sphere_grid(256), [1.33 + 0.01j], 20.0, k, e, "fp32_refined")
+    if name == "spheroid64x64x256":
+        # profiler-capture stand-in for sphere256: its 128x128x512 padded grid
+        # has the same 512-point z transform at 1/16 of the memory
+        k, e = _sweep(8)
+        return Workload(name, ellipsoid_grid(64, 64, 256, 64, 64, 256), [1.33 + 0.01j], 10.0, k, e,
+                        "fp32_refined")
     raise KeyError(name)
 
 

@@ -192,6 +192,28 @@ dda_status dda_grad_qabs(dda_ctx* ctx, dda_precision precision, const double* kh
                          const dda_opts* opts, double* dq_dre_eps, double* dq_dim_eps, double* P_out,
                          dda_result* res);
 
+/* Schedule autotuning for the batched complex64 path.  The z pass (FFT along
+ * z, the 3x3 Fourier-space product, inverse FFT) has two schedules on grids
+ * whose z transform keeps at most 8 points per thread (Lz = 16, 32, 64, 128,
+ * 256 or 512):
+ *   0  three component groups per column, spectra exchanged through shared memory;
+ *   1  register-resident: one thread holds all three components of its points,
+ *      and the loads of the next RHS are issued before the current one is
+ *      transformed.
+ * Both compute the same product; results agree to rounding.  By default the
+ * context times both on its own workspace the first time a complex64 matvec
+ * of a given RHS count runs outside a stream capture, and keeps the faster
+ * (inside a capture an untimed choice is used until then).  Complex128 and
+ * double-float matvecs have schedule 0 only.
+ * dda_set_schedule: zpass -1 automatic (the default), 0 or 1 forces that
+ *   schedule wherever it exists (1 falls back to 0 elsewhere); clears the
+ *   timings.  Any other value: DDA_ERR_ARG.
+ * dda_get_schedule: the schedule complex64 matvecs of R RHS use on the current
+ *   target, timing the candidates now if needed (this sizes the workspace
+ *   for R).  Needs dda_prepare with DDA_FP32_REFINED or DDA_FP32.            */
+dda_status dda_set_schedule(dda_ctx* ctx, int zpass);
+dda_status dda_get_schedule(dda_ctx* ctx, int R, int* zpass);
+
 /* Launch tracing (the guide's TIMEIT timing switch, per kernel kind rather than
  * per run): when on, every hot-path kernel launch is bracketed by CUDA events
  * on the stream it runs on -- also inside replayed CUDA graphs -- and its

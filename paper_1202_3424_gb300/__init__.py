@@ -24,7 +24,7 @@ __all__ = [
     "DdaError", "Precision", "Context", "load_library", "library_path",
     "dda_create", "dda_destroy", "dda_last_error", "dda_set_stream", "dda_set_target", "dda_set_materials",
     "dda_prepare", "dda_get_info", "dda_solve", "dda_solve_device", "dda_matvec", "dda_matvec_device",
-    "dda_incident_field", "dda_grad_qabs", "dda_matvec_device_noalloc",
+    "dda_incident_field", "dda_grad_qabs", "dda_matvec_device_noalloc", "dda_set_schedule", "dda_get_schedule",
 ]
 
 STATUS = {0: "DDA_OK", 1: "DDA_ERR_ARG", 2: "DDA_ERR_CUDA", 3: "DDA_ERR_OOM", 4: "DDA_ERR_SIZE",
@@ -107,6 +107,8 @@ def load_library(build_if_missing: bool = True):
         "dda_incident_field": ([vp, ctypes.c_int, _D, _D, _D], ctypes.c_int),
         "dda_grad_qabs": ([vp, ctypes.c_int, _D, _D, ctypes.POINTER(dda_opts), _D, _D, _D, ctypes.POINTER(dda_result)],
                           ctypes.c_int),
+        "dda_set_schedule": ([vp, ctypes.c_int], ctypes.c_int),
+        "dda_get_schedule": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -277,6 +279,18 @@ def dda_grad_qabs(ctx, precision, khat, e, **opts):
     return gre, gim, P, (res[0].as_dict(), res[1].as_dict())
 
 
+def dda_set_schedule(ctx, zpass: int):
+    """Force the complex64 z-pass schedule (0 or 1) or restore autotuning (-1)."""
+    _check(ctx, load_library().dda_set_schedule(ctx, int(zpass)))
+
+
+def dda_get_schedule(ctx, R: int) -> int:
+    """The z-pass schedule complex64 matvecs of R RHS use (timed now if needed)."""
+    out = ctypes.c_int(-1)
+    _check(ctx, load_library().dda_get_schedule(ctx, int(R), ctypes.byref(out)))
+    return out.value
+
+
 class Context:
     """Owns one dda_ctx (one GPU)."""
 
@@ -324,6 +338,12 @@ class Context:
 
     def incident_field(self, khat, e):
         return dda_incident_field(self.handle, khat, e)
+
+    def set_schedule(self, zpass):
+        dda_set_schedule(self.handle, zpass)
+
+    def get_schedule(self, R):
+        return dda_get_schedule(self.handle, R)
 
     def grad_qabs(self, precision, khat, e, **opts):
         return dda_grad_qabs(self.handle, precision, khat, e, **opts)

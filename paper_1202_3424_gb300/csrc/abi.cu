@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -76,6 +77,10 @@ struct dda_ctx {
     std::vector<DevMem> pool;  // generic named slots, see slot()
     int ws_R = 0;
     GraphEntry graph;
+    // z-pass schedule per (element bytes, RHS count), timed on first use;
+    // force_z >= 0 overrides (dda_set_schedule)
+    std::map<std::pair<int, int>, int> zsched;
+    int force_z = -1;
     int* h_count = nullptr;  // pinned
     Profiler prof;
 
@@ -124,7 +129,7 @@ enum Slot {
     S_PART, S_CNT, S_QSUM, S_COUNT,
     S_BETA64, S_BETA32, S_W, S_KHAT, S_EPOL,
     S_MV_X32, S_MV_Y32, S_GRAD, S_DBETA,
-    S_BETADF, S_XDF, S_YDF,
+    S_BETADF, S_XDF, S_YDF, S_TUNE,
     S_NSLOTS
 };
 
@@ -286,6 +291,83 @@ template <typename T> dda_status ensure_pad(dda_ctx* ctx, int R) {
     return ensure(ctx, ctx->pool[PadSlots<T>::b], (size_t)rc * 3 * ctx->g.u2_per_comp() * sizeof(cx<T>));
 }
 
+// z-pass schedule for R right-hand sides.  With more than one schedule for
+// this grid, each is timed once inside a whole plain matvec of R RHS (the
+// passes around the z pass decide what it finds in L2) on the context's
+// workspace plus a transient pair of vectors, and the faster is kept.  The
+// workspace must hold R RHS (ensure_pad<T>).  Inside a stream capture, or
+// with may_time false, an untimed choice is returned: the cached one, else
+// the register-resident schedule for R >= 4.
+template <typename T> dda_status pick_zvar(dda_ctx* ctx, int R, bool may_time, int* out) {
+    const int nv = zconv_schedules<T>(ctx->g);
+    *out = 0;
+    if (nv <= 1) return DDA_OK;
+    if (ctx->force_z >= 0) {
+        *out = std::min(ctx->force_z, nv - 1);
+        return DDA_OK;
+    }
+    const std::pair<int, int> key((int)sizeof(cx<T>), R);
+    auto it = ctx->zsched.find(key);
+    if (it != ctx->zsched.end()) {
+        *out = it->second;
+        return DDA_OK;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing(ctx->stream, &cs));
+    if (!may_time || cs != cudaStreamCaptureStatusNone) {
+        *out = R >= 4 ? 1 : 0;
+        return DDA_OK;
+    }
+    // zero-filled x, y and 1/alpha table (their values do not change the timing)
+    const int BS = beta_stride(ctx);
+    const size_t vec = (size_t)R * 3 * ctx->g.N * sizeof(cx<T>);
+    dda_status s;
+    if ((s = ensure(ctx, ctx->pool[S_TUNE], 2 * vec + (size_t)R * BS * sizeof(cx<T>), true)) != DDA_OK) return s;
+    char* base = static_cast<char*>(ctx->pool[S_TUNE].p);
+    const cx<T>* x = reinterpret_cast<const cx<T>*>(base);
+    cx<T>* y = reinterpret_cast<cx<T>*>(base + vec);
+    const cx<T>* beta = reinterpret_cast<const cx<T>*>(base + 2 * vec);
+    PadWork<T> w{slot<cx<T>>(ctx, PadSlots<T>::a), slot<cx<T>>(ctx, PadSlots<T>::b)};
+    auto run = [&](int v) {
+        w.zvar = v;
+        return launch_matvec<T>(ctx->g, R, x, y, w, ctx->tg, beta, BS, ghat_of<T>(ctx), tw_of<T>(ctx), nullptr,
+                                ctx->stream);
+    };
+    const bool was_on = ctx->prof.on;
+    ctx->prof.on = false;  // tuning launches are not part of the traced work
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    // one warm-up matvec each, then rounds that alternate the schedules (so a
+    // clock ramp or a neighbour's burst does not favour one); keep each
+    // schedule's best round
+    constexpr int kRounds = 3, kReps = 2;
+    std::vector<float> best(nv, 0.f);
+    for (int v = 0; v < nv && ce == cudaSuccess; ++v) ce = run(v);
+    for (int round = 0; round < kRounds && ce == cudaSuccess; ++round) {
+        for (int v = 0; v < nv && ce == cudaSuccess; ++v) {
+            ce = cudaEventRecord(e0, ctx->stream);
+            for (int i = 0; i < kReps && ce == cudaSuccess; ++i) ce = run(v);
+            if (ce == cudaSuccess) ce = cudaEventRecord(e1, ctx->stream);
+            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+            if (ce == cudaSuccess && (round == 0 || ms < best[v])) best[v] = ms;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    ctx->prof.on = was_on;
+    free_mem(ctx->pool[S_TUNE]);
+    if (ce != cudaSuccess) return ctx->cuda_fail(ce, "z-pass schedule timing");
+    int pick = 0;
+    for (int v = 1; v < nv; ++v)
+        if (best[v] < best[pick]) pick = v;
+    ctx->zsched[key] = pick;
+    *out = pick;
+    return DDA_OK;
+}
+
 // y = A x over R RHS in chunks (workspace from ensure_pad<T>).
 template <typename T>
 dda_status run_matvec(dda_ctx* ctx, int R, const cx<T>* x, cx<T>* y, const int* active) {
@@ -293,8 +375,10 @@ dda_status run_matvec(dda_ctx* ctx, int R, const cx<T>* x, cx<T>* y, const int* 
     const int64_t n = 3 * ctx->g.N;
     PadWork<T> w{slot<cx<T>>(ctx, PadSlots<T>::a), slot<cx<T>>(ctx, PadSlots<T>::b)};
     const int BS = beta_stride(ctx);
+    dda_status zs;
     for (int r0 = 0; r0 < R; r0 += rc) {
         const int rn = std::min(rc, R - r0);
+        if ((zs = pick_zvar<T>(ctx, rn, true, &w.zvar)) != DDA_OK) return zs;
         CU(launch_matvec<T>(ctx->g, rn, x + (int64_t)r0 * n, y + (int64_t)r0 * n, w, ctx->tg,
                             beta_of<T>(ctx) + (int64_t)r0 * BS, BS, ghat_of<T>(ctx), tw_of<T>(ctx),
                             active ? active + r0 : nullptr, ctx->stream));
@@ -349,9 +433,11 @@ dda_status run_matvec_fused(dda_ctx* ctx, int R, int mode, cx<T>* x, cx<T>* y, c
     const int BS = beta_stride(ctx);
     const int ps = partial_stride(ctx);
     int* act = slot<int>(ctx, S_ACTIVE);
+    dda_status zs;
     for (int r0 = 0; r0 < R; r0 += rc) {
         const int rn = std::min(rc, R - r0);
         const int64_t o = (int64_t)r0 * n;
+        if ((zs = pick_zvar<T>(ctx, rn, true, &w.zvar)) != DDA_OK) return zs;
         FusedKrylov<T> fk;
         fk.mode = mode;
         fk.r = in.r + o;
@@ -787,6 +873,8 @@ dda_status matvec_noalloc(dda_ctx* ctx, int R, const std::vector<double>& k, con
     C* d_beta = reinterpret_cast<C*>(base);
     PadWork<T> w{reinterpret_cast<C*>(base + beta_bytes), reinterpret_cast<C*>(base + beta_bytes + u1_bytes)};
     CU(cudaMemcpyAsync(d_beta, beta.data(), beta.size() * sizeof(C), cudaMemcpyHostToDevice, ctx->stream));
+    dda_status zs;
+    if ((zs = pick_zvar<T>(ctx, R, false, &w.zvar)) != DDA_OK) return zs;  // no timing on the fixed scratch
     CU(launch_matvec<T>(ctx->g, R, static_cast<const C*>(x_dev), static_cast<C*>(y_dev), w, ctx->tg, d_beta, BS,
                         ghat_of<T>(ctx), tw_of<T>(ctx), nullptr, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
@@ -900,6 +988,7 @@ dda_status dda_set_target(dda_ctx* ctx, int nx, int ny, int nz, const uint8_t* c
     ctx->tg.lat_of = (int*)ctx->m_lat_of.p;
     ctx->tg.comp_of = (uint8_t*)ctx->m_comp_of.p;
     ctx->g = g;
+    ctx->zsched.clear();
     ctx->max_code = maxc;
     ctx->has_target = true;
     if (ctx->graph.exec) {
@@ -1191,6 +1280,26 @@ dda_status dda_grad_qabs(dda_ctx* ctx, dda_precision precision, const double* kh
     if (P_out) CU(cudaMemcpyAsync(P_out, Pkeep, n * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
     CU(sync_collect(ctx));
     return DDA_OK;
+}
+
+dda_status dda_set_schedule(dda_ctx* ctx, int zpass) {
+    if (!ctx) return DDA_ERR_ARG;
+    if (zpass < -1 || zpass > 1) return ctx->fail(DDA_ERR_ARG, "z-pass schedule must be -1, 0 or 1 (got %d)", zpass);
+    ctx->force_z = zpass;
+    ctx->zsched.clear();
+    return DDA_OK;
+}
+
+dda_status dda_get_schedule(dda_ctx* ctx, int R, int* zpass) {
+    if (!ctx || !zpass) return DDA_ERR_ARG;
+    if (R <= 0) return ctx->fail(DDA_ERR_ARG, "R must be > 0");
+    if (!ctx->prepared || !ctx->has32)
+        return ctx->fail(DDA_ERR_ARG, "dda_prepare with a complex64-capable precision has not been called");
+    ProfScope prof_scope(ctx);
+    cudaSetDevice(ctx->device);
+    dda_status s;
+    if ((s = ensure_pad<float>(ctx, R)) != DDA_OK) return s;
+    return pick_zvar<float>(ctx, matvec_chunk<float>(ctx, R), true, zpass);
 }
 
 dda_status dda_profile_enable(dda_ctx* ctx, int on) {

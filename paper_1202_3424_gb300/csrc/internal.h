@@ -51,6 +51,7 @@ template <typename T> struct Twiddles {
 template <typename T> struct PadWork {
     cx<T>* u1 = nullptr;  // [R][3][nz][ny][Lx]
     cx<T>* u2 = nullptr;  // [R][3][nz][Ly][Lx]
+    int zvar = 0;         // z-pass schedule, see zconv_schedules
 };
 
 int pick_fft_length(int n);  // smallest supported length >= 2n, or 0
@@ -75,6 +76,19 @@ template <typename T> struct FusedKrylov {
 };
 
 int xinv_blocks_per_rhs(const Geom& g);
+
+// Number of z-pass schedules for this grid and arithmetic type: schedule 0
+// (three component groups per column, spectra exchanged through shared
+// memory) always; schedule 1 (register-resident, one thread holds all three
+// components of its points) for complex64 when the z plan keeps at most 8
+// points per thread.  Both compute the same product; the context times them
+// per RHS count and keeps the faster (dda_set_schedule can force one).
+template <typename T> int zconv_schedules(const Geom& g);
+
+// The z pass alone, in place on u2 (used to time the schedules).
+template <typename T>
+cudaError_t launch_zconv(const Geom& g, int R, cx<T>* u2, const cx<T>* ghat, const cx<T>* twz, const int* active,
+                         int zvar, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_matvec_fused(const Geom& g, int R, cx<T>* x, cx<T>* y, const PadWork<T>& w,

@@ -3,6 +3,8 @@
 
 namespace dda {
 
+template int zconv_schedules<double>(const Geom&);
+template cudaError_t launch_zconv<double>(const Geom&, int, double2*, const double2*, const double2*, const int*, int, cudaStream_t);
 template cudaError_t launch_matvec<double>(const Geom&, int, const double2*, double2*, const PadWork<double>&,
                                            const DevTarget&, const double2*, int, const double2*,
                                            const Twiddles<double>&, const int*, cudaStream_t);
@@ -17,20 +19,25 @@ int pick_fft_length(int n) {
     return 0;
 }
 
+// Blocks of one RHS in the x-inverse pass (partial-sum slots per RHS): the
+// larger of the complex64 and 16-byte element tilings.
+template <int L> static int min_tp_x() {
+    return tp_x<L, 8>() < tp_x<L, 16>() ? tp_x<L, 8>() : tp_x<L, 16>();
+}
 int xinv_blocks_per_rhs(const Geom& g) {
     const int nrows = g.ny * g.nz;
     int tp = 1;
     switch (g.Lx) {
-        case 16: tp = tp_x<16>(); break;
-        case 32: tp = tp_x<32>(); break;
-        case 48: tp = tp_x<48>(); break;
-        case 64: tp = tp_x<64>(); break;
-        case 96: tp = tp_x<96>(); break;
-        case 128: tp = tp_x<128>(); break;
-        case 192: tp = tp_x<192>(); break;
-        case 256: tp = tp_x<256>(); break;
-        case 384: tp = tp_x<384>(); break;
-        case 512: tp = tp_x<512>(); break;
+        case 16: tp = min_tp_x<16>(); break;
+        case 32: tp = min_tp_x<32>(); break;
+        case 48: tp = min_tp_x<48>(); break;
+        case 64: tp = min_tp_x<64>(); break;
+        case 96: tp = min_tp_x<96>(); break;
+        case 128: tp = min_tp_x<128>(); break;
+        case 192: tp = min_tp_x<192>(); break;
+        case 256: tp = min_tp_x<256>(); break;
+        case 384: tp = min_tp_x<384>(); break;
+        case 512: tp = min_tp_x<512>(); break;
         default: tp = 1;
     }
     return 3 * ((nrows + tp - 1) / tp);
@@ -110,7 +117,7 @@ __global__ void k_cconvert(const S* __restrict__ s, D* __restrict__ d, int64_t n
 }
 
 template <int LX> static cudaError_t launch_xfull(double2* data, int64_t nrows, const double2* tw, cudaStream_t st) {
-    constexpr int TP = tp_x<LX>(), NTH = TP * Plan<LX>::NT;
+    constexpr int TP = tp_x<LX, 16>(), NTH = TP * Plan<LX>::NT;
     const size_t sm = (size_t)LX * (TP + 1) * sizeof(double2);
     cudaError_t e = allow_smem(k_xfull<LX>, sm);
     if (e != cudaSuccess) return e;

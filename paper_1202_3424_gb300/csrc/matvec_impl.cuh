@@ -43,12 +43,31 @@ namespace dda {
 // ---- tile sizes ------------------------------------------------------------
 // x passes stage TP rows through shared memory (TP+1 stride); strided passes
 // take TP adjacent pencils (coalesced across them); the z pass takes TP
-// adjacent columns for each of 3 component groups.
-template <int L> __host__ __device__ constexpr int tp_x() {
-    return (256 / Plan<L>::NT) > 64 ? 64 : (256 / Plan<L>::NT);
+// adjacent columns for each of 3 component groups.  ES is the element size
+// in bytes.  For complex64 every x and strided tile is at least 16 wide:
+// 128-byte row segments in global memory, and (per the shared-memory bank
+// model in bank_model.py) no bank conflicts in the exchanges and transposes
+// of a (TP+1)-strided x plane, where 4- and 8-wide tiles cost 1.8-1.9x the
+// ideal wavefronts.  To fit 16 rows of 512 points in 512 threads the x
+// passes then run that length with 32 threads of 16 points.
+template <int L, int ES> struct XPlan : Plan<L> {};
+template <> struct XPlan<512, 8> : PlanDef<512, 32, 8, 8, 8> {};
+template <int L, int ES> __host__ __device__ constexpr int tp_x() {
+    constexpr int nt = XPlan<L, ES>::NT;
+    const int tp = (256 / nt) > 64 ? 64 : (256 / nt);
+    return (ES == 8 && tp < 16) ? 16 : tp;
 }
-template <int L> __host__ __device__ constexpr int tp_s() {
-    return (256 / Plan<L>::NT) > 32 ? 32 : ((256 / Plan<L>::NT) < 8 ? 8 : (256 / Plan<L>::NT));
+// x-inverse blocks per SM the register budget must allow: at least 1024
+// threads (the hoisted scatter operands otherwise take 128 registers and a
+// 512-thread block would run alone on its SM)
+template <int L, int ES> __host__ __device__ constexpr int xinv_min_blocks() {
+    constexpr int threads = tp_x<L, ES>() * XPlan<L, ES>::NT;
+    return threads >= 1024 ? 1 : 1024 / threads;
+}
+template <int L, int ES> __host__ __device__ constexpr int tp_s() {
+    constexpr int nt = Plan<L>::NT;
+    const int tp = (256 / nt) > 32 ? 32 : ((256 / nt) < 8 ? 8 : (256 / nt));
+    return (ES == 8 && tp < 16) ? 16 : tp;
 }
 // z pass: 3*TP*NT threads per block, TP adjacent columns, and enough blocks
 // per SM (registers capped by the launch bound) to hide the latency of the
@@ -87,13 +106,13 @@ template <int L, typename T> __host__ __device__ constexpr size_t zconv_smem() {
 // written back to X:  MODE 1  X = p <- r + beta (p - omega v);
 //                      MODE 2  X = s <- r - alpha v.
 template <typename T, int LX, int MODE>
-__global__ void __launch_bounds__(tp_x<LX>() * Plan<LX>::NT)
+__global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(cx<T>)>::NT)
     k_xfwd(cx<T>* __restrict__ X, cx<T>* __restrict__ U1, const int* __restrict__ site_of, int nrows, int64_t N,
            const cx<T>* __restrict__ tw, const int* __restrict__ active, const cx<T>* __restrict__ kr,
            const cx<T>* __restrict__ kv, const KState* __restrict__ st) {
     using C = cx<T>;
-    using PL = Plan<LX>;
-    constexpr int TP = tp_x<LX>(), SP = TP + 1, NX = LX / 2;
+    using PL = XPlan<LX, sizeof(cx<T>)>;
+    constexpr int TP = tp_x<LX, sizeof(cx<T>)>(), SP = TP + 1, NX = LX / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     const int c = blockIdx.y, r = blockIdx.z;
@@ -108,24 +127,38 @@ __global__ void __launch_bounds__(tp_x<LX>() * Plan<LX>::NT)
     } else if constexpr (MODE == 2) {
         ka = from2<C>(st[r].alpha);
     }
-    for (int e = threadIdx.x; e < TP * NX; e += blockDim.x) {
-        const int t = e / NX, ix = e - t * NX, row = row0 + t;
-        C val = czero<C>();
-        if (row < nrows) {
-            const int s = site_of[(int64_t)row * NX + ix];
-            if (s >= 0) {
-                if constexpr (MODE == 0) {
-                    val = xs[s];
-                } else if constexpr (MODE == 1) {
-                    val = cadd(kr[off + s], cmul(ka, csub(xs[s], cmul(kb, kv[off + s]))));
-                    xs[s] = val;
-                } else {
-                    val = csub(kr[off + s], cmul(ka, kv[off + s]));
-                    xs[s] = val;
-                }
+    // The gather runs in three unrolled phases (site indices, then values,
+    // then shared-memory stores) so that every load of a thread is in flight
+    // at once: the site -> value chain is two dependent memory latencies.
+    constexpr int NTH = TP * PL::NT, NG = (TP * NX + NTH - 1) / NTH;
+    int sidx[NG];
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+        const int e = threadIdx.x + i * NTH, t = e / NX, ix = e - t * NX, row = row0 + t;
+        sidx[i] = (e < TP * NX && row < nrows) ? site_of[(int64_t)row * NX + ix] : -1;
+    }
+    C val[NG];
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+        const int s = sidx[i];
+        val[i] = czero<C>();
+        if (s >= 0) {
+            if constexpr (MODE == 0) {
+                val[i] = xs[s];
+            } else if constexpr (MODE == 1) {
+                val[i] = cadd(kr[off + s], cmul(ka, csub(xs[s], cmul(kb, kv[off + s]))));
+            } else {
+                val[i] = csub(kr[off + s], cmul(ka, kv[off + s]));
             }
         }
-        buf[ix * SP + t] = val;
+    }
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+        const int e = threadIdx.x + i * NTH, t = e / NX, ix = e - t * NX;
+        if (e < TP * NX) buf[ix * SP + t] = val[i];
+        if constexpr (MODE != 0) {
+            if (sidx[i] >= 0) xs[sidx[i]] = val[i];
+        }
     }
     __syncthreads();
     const int t = threadIdx.x % TP, u = threadIdx.x / TP;
@@ -139,9 +172,11 @@ __global__ void __launch_bounds__(tp_x<LX>() * Plan<LX>::NT)
     for_each_out<PL, -1, false>(u, [&](int idx, int pos) { bt[pos * SP] = v[idx]; });
     __syncthreads();
     C* out = U1 + ((int64_t)r * 3 + c) * (int64_t)nrows * LX;
-    for (int e = threadIdx.x; e < TP * LX; e += blockDim.x) {
-        const int t2 = e / LX, x = e - t2 * LX, row = row0 + t2;
-        if (row < nrows) out[(int64_t)row * LX + x] = buf[x * SP + t2];
+    constexpr int NO = (TP * LX + NTH - 1) / NTH;
+#pragma unroll
+    for (int i = 0; i < NO; ++i) {
+        const int e = threadIdx.x + i * NTH, t2 = e / LX, x = e - t2 * LX, row = row0 + t2;
+        if (e < TP * LX && row < nrows) out[(int64_t)row * LX + x] = buf[x * SP + t2];
     }
 }
 
@@ -151,25 +186,69 @@ __global__ void __launch_bounds__(tp_x<LX>() * Plan<LX>::NT)
 //   MODE 1  Y = v:  sigma = <rhat, v>          ->  alpha = rho / sigma
 //   MODE 2  Y = t:  <t, s>, <t, t> with X = s  ->  omega
 template <typename T, int LX, int MODE>
-__global__ void __launch_bounds__(tp_x<LX>() * Plan<LX>::NT)
+__global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(cx<T>)>::NT,
+                                   xinv_min_blocks<LX, sizeof(cx<T>)>())
     k_xinv(const cx<T>* __restrict__ U1, cx<T>* __restrict__ Y, const cx<T>* __restrict__ X,
            const int* __restrict__ site_of, const uint8_t* __restrict__ comp_of, const cx<T>* __restrict__ beta,
            int beta_stride, int nrows, int64_t N, const cx<T>* __restrict__ tw, int* __restrict__ active,
            const cx<T>* __restrict__ krhat, KState* __restrict__ st, double2* __restrict__ part,
            unsigned* __restrict__ cnt, int part_stride) {
     using C = cx<T>;
-    using PL = Plan<LX>;
-    constexpr int TP = tp_x<LX>(), SP = TP + 1, NX = LX / 2;
+    using PL = XPlan<LX, sizeof(cx<T>)>;
+    constexpr int TP = tp_x<LX, sizeof(cx<T>)>(), SP = TP + 1, NX = LX / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     const int c = blockIdx.y, r = blockIdx.z;
     if (active != nullptr && active[r] == 0) return;
     const int row0 = blockIdx.x * TP;
     const C* in = U1 + ((int64_t)r * 3 + c) * (int64_t)nrows * LX;
-    for (int e = threadIdx.x; e < TP * LX; e += blockDim.x) {
-        const int t2 = e / LX, x = e - t2 * LX, row = row0 + t2;
-        buf[x * SP + t2] = row < nrows ? in[(int64_t)row * LX + x] : czero<C>();
+    const int64_t off = ((int64_t)r * 3 + c) * N;
+    const C* xs = X + off;
+    C* ys = Y + off;
+    const C* br = beta + (int64_t)r * beta_stride;
+    // All global loads are issued up front: the rows to transform, then the
+    // site indices and, behind them, the operands of the diagonal term, whose
+    // latency the transform hides.
+    constexpr int NTH = TP * PL::NT, NI = (TP * LX + NTH - 1) / NTH, NG = (TP * NX + NTH - 1) / NTH;
+    int sidx[NG];
+    {
+        C rin[NI];
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int e = threadIdx.x + i * NTH, t2 = e / LX, x = e - t2 * LX, row = row0 + t2;
+            rin[i] = (e < TP * LX && row < nrows) ? in[(int64_t)row * LX + x] : czero<C>();
+        }
+#pragma unroll
+        for (int i = 0; i < NG; ++i) {
+            const int e = threadIdx.x + i * NTH, t2 = e / NX, ix = e - t2 * NX, row = row0 + t2;
+            sidx[i] = (e < TP * NX && row < nrows) ? site_of[(int64_t)row * NX + ix] : -1;
+        }
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int e = threadIdx.x + i * NTH, t2 = e / LX, x = e - t2 * LX;
+            if (e < TP * LX) buf[x * SP + t2] = rin[i];
+        }
     }
+    // (with 16 points per thread the transform needs those registers: the
+    // operands are then loaded after it)
+    constexpr bool kHoist = PL::E <= 12;
+    C xv[NG], bv[NG];
+    C kh[MODE == 1 ? NG : 1];
+    auto load_operands = [&]() {
+#pragma unroll
+        for (int i = 0; i < NG; ++i) {
+            const int s = sidx[i];
+            xv[i] = czero<C>();
+            bv[i] = czero<C>();
+            if constexpr (MODE == 1) kh[i] = czero<C>();
+            if (s >= 0) {
+                xv[i] = xs[s];
+                bv[i] = br[comp_of[s]];
+                if constexpr (MODE == 1) kh[i] = krhat[off + s];
+            }
+        }
+    };
+    if constexpr (kHoist) load_operands();
     __syncthreads();
     const int t = threadIdx.x % TP, u = threadIdx.x / TP;
     C* bt = buf + t;
@@ -180,25 +259,20 @@ __global__ void __launch_bounds__(tp_x<LX>() * Plan<LX>::NT)
     pencil_fft<C, PL, +1, false>(v, u, tw, first, ld, stf);
     __syncthreads();
     for_each_out<PL, +1, true>(u, [&](int idx, int pos) { bt[pos * SP] = v[idx]; });
+    if constexpr (!kHoist) load_operands();
     __syncthreads();
-    const int64_t off = ((int64_t)r * 3 + c) * N;
-    const C* xs = X + off;
-    C* ys = Y + off;
-    const C* br = beta + (int64_t)r * beta_stride;
     DotAcc<C> d[2];
-    for (int e = threadIdx.x; e < TP * NX; e += blockDim.x) {
-        const int t2 = e / NX, ix = e - t2 * NX, row = row0 + t2;
-        if (row < nrows) {
-            const int s = site_of[(int64_t)row * NX + ix];
-            if (s >= 0) {
-                const C xv = xs[s];
-                const C yv = cadd(buf[ix * SP + t2], cmul(br[comp_of[s]], xv));
-                ys[s] = yv;
-                if constexpr (MODE == 1) d[0].add_cdot(krhat[off + s], yv);
-                if constexpr (MODE == 2) {
-                    d[0].add_cdot(yv, xv);
-                    d[1].add_norm2(yv);
-                }
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+        const int e = threadIdx.x + i * NTH, t2 = e / NX, ix = e - t2 * NX;
+        const int s = sidx[i];
+        if (s >= 0) {
+            const C yv = cadd(buf[ix * SP + t2], cmul(bv[i], xv[i]));
+            ys[s] = yv;
+            if constexpr (MODE == 1) d[0].add_cdot(kh[i], yv);
+            if constexpr (MODE == 2) {
+                d[0].add_cdot(yv, xv[i]);
+                d[1].add_norm2(yv);
             }
         }
     }
@@ -223,12 +297,12 @@ __global__ void __launch_bounds__(tp_x<LX>() * Plan<LX>::NT)
 // MODE 1: inverse keeping positions < L/2; MODE 2: full forward transform.
 // TP pencils adjacent in w per block, so loads and stores coalesce across w.
 template <typename T, int L, int MODE>
-__global__ void __launch_bounds__(tp_s<L>() * Plan<L>::NT)
+__global__ void __launch_bounds__(tp_s<L, sizeof(cx<T>)>() * Plan<L>::NT)
     k_strided(const cx<T>* src, cx<T>* dst, int64_t pt_stride, int width, int64_t src_bstride, int64_t dst_bstride,
               int batches_per_rhs, const cx<T>* __restrict__ tw, const int* __restrict__ active) {
     using C = cx<T>;
     using PL = Plan<L>;
-    constexpr int TP = tp_s<L>();
+    constexpr int TP = tp_s<L, sizeof(cx<T>)>();
     constexpr int DIR = MODE == 1 ? +1 : -1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
@@ -242,8 +316,8 @@ __global__ void __launch_bounds__(tp_s<L>() * Plan<L>::NT)
     C* bt = buf + t;
     C v[PL::E];
     auto first = [&](int pos) { return valid ? s[pos * pt_stride] : czero<C>(); };
-    auto ld = [&](int pos) { return bt[pos * TP]; };
-    auto st = [&](int pos, C val) { bt[pos * TP] = val; };
+    auto ld = [&](int pos) { return bt[swizzle_row<L, PL::NT, TP, sizeof(C)>(pos) * TP]; };
+    auto st = [&](int pos, C val) { bt[swizzle_row<L, PL::NT, TP, sizeof(C)>(pos) * TP] = val; };
     pencil_fft<C, PL, DIR, MODE == 0>(v, u, tw, first, ld, st);
     for_each_out<PL, DIR, MODE == 1>(u, [&](int idx, int pos) {
         if (valid) d[pos * pt_stride] = v[idx];
@@ -310,8 +384,9 @@ __global__ void __launch_bounds__(3 * tp_z<LZ, T>() * ZPlan<LZ>::NT, zconv_min_b
     const C* g2 = gs + i2 * HZ * SP + t;
     C* sb = buf + c * (LZ * SP) + t;
     const C* pb = buf + t;
-    auto ld = [&](int pos) { return sb[pos * SP]; };
-    auto st = [&](int pos, C val) { sb[pos * SP] = val; };
+    auto row = [](int pos) { return swizzle_row<LZ, NT, SP, sizeof(C)>(pos); };
+    auto ld = [&](int pos) { return sb[row(pos) * SP]; };
+    auto st = [&](int pos, C val) { sb[row(pos) * SP] = val; };
 #pragma unroll 1
     for (int rr = 0; rr < RB; ++rr) {
         const int r = r0 + rr;
@@ -323,7 +398,7 @@ __global__ void __launch_bounds__(3 * tp_z<LZ, T>() * ZPlan<LZ>::NT, zconv_min_b
         __syncthreads();  // Green tile staged / previous RHS done with the spectra
         pencil_fft<C, PL, -1, true>(v, u, tw, first, ld, st);
         __syncthreads();
-        for_each_out<PL, -1, false>(u, [&](int idx, int pos) { sb[pos * SP] = v[idx]; });
+        for_each_out<PL, -1, false>(u, [&](int idx, int pos) { sb[row(pos) * SP] = v[idx]; });
         __syncthreads();
         for_each_out<PL, -1, false>(u, [&](int idx, int kz) {
             const bool fz = kz > LZ / 2;
@@ -334,7 +409,8 @@ __global__ void __launch_bounds__(3 * tp_z<LZ, T>() * ZPlan<LZ>::NT, zconv_min_b
                 if (z1) a1 = cscale(a1, T(-1));
                 if (z2) a2 = cscale(a2, T(-1));
             }
-            const C pa = pb[kz * SP], pbv = pb[(LZ + kz) * SP], pc = pb[(2 * LZ + kz) * SP];
+            const int kr = row(kz);
+            const C pa = pb[kr * SP], pbv = pb[(LZ + kr) * SP], pc = pb[(2 * LZ + kr) * SP];
             v[idx] = cadd(cadd(cmul(a0, pa), cmul(a1, pbv)), cmul(a2, pc));
         });
         pencil_fft_regs<C, PL, +1>(v, u, tw, ld, st);
@@ -344,13 +420,142 @@ __global__ void __launch_bounds__(3 * tp_z<LZ, T>() * ZPlan<LZ>::NT, zconv_min_b
     }
 }
 
+// ---- z pass, register-resident schedule (complex64) ----------------------------
+// Same product as k_zconv, but each thread keeps all three components of its
+// points in registers: per RHS it transforms P_x, P_y, P_z of its column
+// one after another through a single shared exchange plane, forms the 3x3
+// product in registers (no spectra round trip through shared memory), and
+// inverse-transforms.  The global loads of the next RHS are issued before
+// the current one is transformed, so one block keeps its column's loads in
+// flight while computing.  Shared traffic per point is about half that of
+// k_zconv; the price is ~128 registers per thread, so the plan must keep
+// L/NT <= 8 points per thread.
+template <int L> __host__ __device__ constexpr bool zreg_ok() { return Plan<L>::E <= 8; }
+template <int L> __host__ __device__ constexpr int tp_zr() {
+    int tp = 128 / Plan<L>::NT;
+    return tp > 32 ? 32 : (tp < 4 ? 4 : tp);
+}
+template <int L> __host__ __device__ constexpr int zreg_threads() { return tp_zr<L>() * Plan<L>::NT; }
+// 128 registers per thread: 512 / threads blocks per SM
+template <int L> __host__ __device__ constexpr int zreg_min_blocks() {
+    return 512 / zreg_threads<L>() < 1 ? 1 : 512 / zreg_threads<L>();
+}
+template <int L, typename T> __host__ __device__ constexpr size_t zreg_smem() {
+    return ((size_t)L + (size_t)6 * (L / 2 + 1)) * tp_zr<L>() * sizeof(cx<T>);
+}
+
+template <typename T, int LZ, int RB>
+__global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
+    k_zconv_reg(cx<T>* __restrict__ U2, const cx<T>* __restrict__ gh, int R, int Lx, int Ly,
+                const cx<T>* __restrict__ tw, const int* __restrict__ active) {
+    using C = cx<T>;
+    using PL = Plan<LZ>;
+    constexpr int TP = tp_zr<LZ>(), NT = PL::NT, NZ = LZ / 2, HZ = LZ / 2 + 1, E = PL::E;
+    constexpr int R0 = stage_radix<PL, -1>(0), NB0 = E / R0, JN = R0 / 2;  // half-zero first stage
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);  // exchange plane [LZ][TP]
+    C* gs = buf + LZ * TP;                    // Green tensor [6][HZ][TP]
+    const int ky = blockIdx.y;
+    const int r0 = blockIdx.z * RB;
+    const int hx = Lx / 2 + 1, hy = Ly / 2 + 1;
+    const int64_t cs = (int64_t)HZ * hy * hx;
+    {
+        const int kyo = ky <= Ly / 2 ? ky : Ly - ky;
+        const bool fy = ky > Ly / 2;
+        for (int e = threadIdx.x; e < 6 * HZ * TP; e += blockDim.x) {
+            const int tt = e % TP, kz = (e / TP) % HZ, cc = e / (TP * HZ);
+            const int kx = blockIdx.x * TP + tt;
+            C g = czero<C>();
+            if (kx < Lx) {
+                const bool fx = kx > Lx / 2;
+                const int kxo = fx ? Lx - kx : kx;
+                g = gh[cc * cs + ((int64_t)kz * hy + kyo) * hx + kxo];
+                // xy is odd in x and y, xz odd in x, yz odd in y (z handled at use)
+                const bool flip = (cc == 1 && fx != fy) || (cc == 2 && fx) || (cc == 4 && fy);
+                if (flip) g = cscale(g, T(-1));
+            }
+            gs[(cc * HZ + kz) * TP + tt] = g;
+        }
+    }
+    const int t = threadIdx.x % TP, u = threadIdx.x / TP;
+    const int kx = blockIdx.x * TP + t;
+    const bool valid = kx < Lx;
+    const int64_t plane = (int64_t)Ly * Lx;
+    C* bt = buf + t;
+    const C* gt = gs + t;
+    auto ld = [&](int pos) { return bt[swizzle_row<LZ, NT, TP, sizeof(C)>(pos) * TP]; };
+    auto st = [&](int pos, C val) { bt[swizzle_row<LZ, NT, TP, sizeof(C)>(pos) * TP] = val; };
+    const int rend = min(R, r0 + RB);
+    auto next_active = [&](int r) {  // uniform across the block
+        while (r < rend && active != nullptr && active[r] == 0) ++r;
+        return r;
+    };
+    auto column = [&](int r, int c) {
+        return U2 + ((int64_t)r * 3 + c) * NZ * plane + (int64_t)ky * Lx + (valid ? kx : 0);
+    };
+    C nxt[3][NB0 * JN];  // first-stage inputs of the next RHS
+    auto prefetch = [&](int r) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const C* bc = column(r, c);
+#pragma unroll
+            for (int q = 0; q < NB0; ++q)
+#pragma unroll
+                for (int j = 0; j < JN; ++j)
+                    nxt[c][q * JN + j] = valid ? __ldcs(bc + (int64_t)(u + q * NT + j * (LZ / R0)) * plane) : czero<C>();
+        }
+    };
+    int r = next_active(r0);
+    if (r < rend) prefetch(r);
+#pragma unroll 1
+    while (r < rend) {
+        C vc[3][E];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int q = 0; q < NB0; ++q)
+#pragma unroll
+                for (int j = 0; j < JN; ++j) vc[c][q * R0 + j] = nxt[c][q * JN + j];
+        const int rn = next_active(r + 1);
+        if (rn < rend) prefetch(rn);
+        // (each transform's first exchange opens with a barrier, which also
+        // orders it after the previous transform's last reads of the plane)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) fft_stages<C, PL, -1, 0>(vc[c], u, tw, ld, st, true);
+        for_each_out<PL, -1, false>(u, [&](int idx, int kz) {
+            const bool fz = kz > LZ / 2;
+            const int kzo = fz ? LZ - kz : kz;
+            const C* g = gt + kzo * TP;
+            const C gxx = g[0], gyy = g[3 * HZ * TP], gzz = g[5 * HZ * TP];
+            C gxy = g[HZ * TP], gxz = g[2 * HZ * TP], gyz = g[4 * HZ * TP];
+            if (fz) {  // xz and yz are odd in z
+                gxz = cscale(gxz, T(-1));
+                gyz = cscale(gyz, T(-1));
+            }
+            const C px = vc[0][idx], py = vc[1][idx], pz = vc[2][idx];
+            vc[0][idx] = cadd(cadd(cmul(gxx, px), cmul(gxy, py)), cmul(gxz, pz));
+            vc[1][idx] = cadd(cadd(cmul(gxy, px), cmul(gyy, py)), cmul(gyz, pz));
+            vc[2][idx] = cadd(cadd(cmul(gxz, px), cmul(gyz, py)), cmul(gzz, pz));
+        });
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            pencil_fft_regs<C, PL, +1>(vc[c], u, tw, ld, st);
+            C* bc = column(r, c);
+            for_each_out<PL, +1, true>(u, [&](int idx, int pos) {
+                if (valid) __stcs(bc + (int64_t)pos * plane, vc[c][idx]);
+            });
+        }
+        r = rn;
+    }
+}
+
 // In-place forward FFT of dense rows of length LX (Green tensor x pass).
 template <int LX>
-__global__ void __launch_bounds__(tp_x<LX>() * Plan<LX>::NT)
+__global__ void __launch_bounds__(tp_x<LX, 16>() * Plan<LX>::NT)
     k_xfull(double2* __restrict__ data, int64_t nrows, const double2* __restrict__ tw) {
     using C = double2;
     using PL = Plan<LX>;
-    constexpr int TP = tp_x<LX>(), SP = TP + 1;
+    constexpr int TP = tp_x<LX, 16>(), SP = TP + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     const int64_t row0 = (int64_t)blockIdx.x * TP;
@@ -424,7 +629,7 @@ template <typename T> struct LaunchX {
     template <int LX>
     static cudaError_t fwd(const Geom& g, int R, cx<T>* x, cx<T>* u1, const int* site_of, const cx<T>* tw,
                            const int* active, const FusedKrylov<T>& fk, cudaStream_t st) {
-        constexpr int TP = tp_x<LX>(), NTH = TP * Plan<LX>::NT;
+        constexpr int TP = tp_x<LX, sizeof(cx<T>)>(), NTH = TP * XPlan<LX, sizeof(cx<T>)>::NT;
         const size_t sm = (size_t)LX * (TP + 1) * sizeof(cx<T>);
         const int nrows = g.ny * g.nz;
         dim3 grid((nrows + TP - 1) / TP, 3, R);
@@ -449,7 +654,7 @@ template <typename T> struct LaunchX {
     static cudaError_t inv(const Geom& g, int R, const cx<T>* u1, cx<T>* y, const cx<T>* x, const DevTarget& tg,
                            const cx<T>* beta, int beta_stride, const cx<T>* tw, int* active,
                            const FusedKrylov<T>& fk, cudaStream_t st) {
-        constexpr int TP = tp_x<LX>(), NTH = TP * Plan<LX>::NT;
+        constexpr int TP = tp_x<LX, sizeof(cx<T>)>(), NTH = TP * XPlan<LX, sizeof(cx<T>)>::NT;
         const size_t sm = (size_t)LX * (TP + 1) * sizeof(cx<T>);
         const int nrows = g.ny * g.nz;
         dim3 grid((nrows + TP - 1) / TP, 3, R);
@@ -479,7 +684,7 @@ template <typename T> struct LaunchX {
     static cudaError_t strided_mode(const cx<T>* src, cx<T>* dst, int64_t pt_stride, int width, int64_t sb,
                                     int64_t db, int batches, int per_rhs, const cx<T>* tw, const int* active,
                                     cudaStream_t st, int kind, double units) {
-        constexpr int TP = tp_s<L>(), NTH = TP * Plan<L>::NT;
+        constexpr int TP = tp_s<L, sizeof(cx<T>)>(), NTH = TP * Plan<L>::NT;
         const size_t sm = (size_t)L * TP * sizeof(cx<T>);
         cudaError_t e = allow_smem(k_strided<T, L, MODE>, sm);
         if (e != cudaSuccess) return e;
@@ -501,15 +706,32 @@ template <typename T> struct LaunchX {
     }
     template <int LZ>
     static cudaError_t zconv(const Geom& g, int R, cx<T>* u2, const cx<T>* gh, const cx<T>* tw, const int* active,
-                             cudaStream_t st) {
-        constexpr int TP = tp_z<LZ, T>(), NTH = 3 * TP * ZPlan<LZ>::NT;
-        const size_t sm = zconv_smem<LZ, T>();
+                             int zvar, cudaStream_t st) {
         // several RHS per block reuse the staged Green tensor
         constexpr int RB = 8;
         const bool multi = R > 1;
-        cudaError_t e = multi ? allow_smem(k_zconv<T, LZ, RB>, sm) : allow_smem(k_zconv<T, LZ, 1>, sm);
-        if (e != cudaSuccess) return e;
         const int rb = multi ? RB : 1;
+        cudaError_t e;
+        if constexpr (sizeof(T) == 4 && zreg_ok<LZ>()) {
+            if (zvar == 1) {
+                constexpr int TP = tp_zr<LZ>();
+                constexpr size_t sm = zreg_smem<LZ, T>();
+                e = multi ? allow_smem(k_zconv_reg<T, LZ, RB>, sm) : allow_smem(k_zconv_reg<T, LZ, 1>, sm);
+                if (e != cudaSuccess) return e;
+                dim3 grid((g.Lx + TP - 1) / TP, g.Ly, (R + rb - 1) / rb);
+                PROF_BEGIN(st);
+                if (multi)
+                    k_zconv_reg<T, LZ, RB><<<grid, zreg_threads<LZ>(), sm, st>>>(u2, gh, R, g.Lx, g.Ly, tw, active);
+                else
+                    k_zconv_reg<T, LZ, 1><<<grid, zreg_threads<LZ>(), sm, st>>>(u2, gh, R, g.Lx, g.Ly, tw, active);
+                PROF_END(KK_ZCONV_C64 + koff, R, st);
+                return cudaGetLastError();
+            }
+        }
+        constexpr int TP = tp_z<LZ, T>(), NTH = 3 * TP * ZPlan<LZ>::NT;
+        const size_t sm = zconv_smem<LZ, T>();
+        e = multi ? allow_smem(k_zconv<T, LZ, RB>, sm) : allow_smem(k_zconv<T, LZ, 1>, sm);
+        if (e != cudaSuccess) return e;
         dim3 grid((g.Lx + TP - 1) / TP, g.Ly, (R + rb - 1) / rb);
         PROF_BEGIN(st);
         if (multi)
@@ -519,6 +741,7 @@ template <typename T> struct LaunchX {
         PROF_END(KK_ZCONV_C64 + koff, R, st);
         return cudaGetLastError();
     }
+    template <int LZ> static int zvariants() { return (sizeof(T) == 4 && zreg_ok<LZ>()) ? 2 : 1; }
 };
 
 // The lattice seen by the kernels is padded with vacuum to exactly L/2 sites
@@ -538,7 +761,9 @@ cudaError_t launch_matvec_fused(const Geom& g, int R, cx<T>* x, cx<T>* y, const 
         DDA_DISPATCH_L(g.Ly, LX::template strided, mode, s, d, (int64_t)g.Lx, g.Lx, sb, db, R * 3 * g.nz, 3 * g.nz,
                        tw.y, active, st, (mode == 0 ? KK_YFWD_C64 : KK_YINV_C64) + LX::koff, (double)R);
     };
-    auto zc = [&]() -> cudaError_t { DDA_DISPATCH_L(g.Lz, LX::template zconv, g, R, w.u2, ghat, tw.z, active, st); };
+    auto zc = [&]() -> cudaError_t {
+        DDA_DISPATCH_L(g.Lz, LX::template zconv, g, R, w.u2, ghat, tw.z, active, w.zvar, st);
+    };
     auto invx = [&]() -> cudaError_t {
         DDA_DISPATCH_L(g.Lx, LX::template inv, g, R, w.u1, y, x, tg, beta, beta_stride, tw.x, active, fk, st);
     };
@@ -547,6 +772,28 @@ cudaError_t launch_matvec_fused(const Geom& g, int R, cx<T>* x, cx<T>* y, const 
     if ((e = zc()) != cudaSuccess) return e;
     if ((e = ys(1, w.u2, w.u1, (int64_t)g.Ly * g.Lx, (int64_t)g.ny * g.Lx)) != cudaSuccess) return e;
     return invx();
+}
+
+template <typename T> int zconv_schedules(const Geom& g) {
+    switch (g.Lz) {
+        case 16: return LaunchX<T>::template zvariants<16>();
+        case 32: return LaunchX<T>::template zvariants<32>();
+        case 48: return LaunchX<T>::template zvariants<48>();
+        case 64: return LaunchX<T>::template zvariants<64>();
+        case 96: return LaunchX<T>::template zvariants<96>();
+        case 128: return LaunchX<T>::template zvariants<128>();
+        case 192: return LaunchX<T>::template zvariants<192>();
+        case 256: return LaunchX<T>::template zvariants<256>();
+        case 384: return LaunchX<T>::template zvariants<384>();
+        case 512: return LaunchX<T>::template zvariants<512>();
+        default: return 0;
+    }
+}
+
+template <typename T>
+cudaError_t launch_zconv(const Geom& g, int R, cx<T>* u2, const cx<T>* ghat, const cx<T>* twz, const int* active,
+                         int zvar, cudaStream_t st) {
+    DDA_DISPATCH_L(g.Lz, LaunchX<T>::template zconv, g, R, u2, ghat, twz, active, zvar, st);
 }
 
 template <typename T>

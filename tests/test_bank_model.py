@@ -1,0 +1,46 @@
+"""The shared-memory bank model that picks the FFT exchange-plane swizzle."""
+from paper_1202_3424_gb300 import bank_model as bm
+
+
+def test_wavefront_counts_of_textbook_patterns():
+    # consecutive 8-byte elements: one wavefront per half-warp
+    assert bm.wavefronts([8 * i for i in range(32)]) == 2
+    # every thread on the same element: broadcast
+    assert bm.wavefronts([0] * 32) == 2
+    # a 128-byte stride puts all 16 threads of a phase on banks 0-1 with distinct words
+    assert bm.wavefronts([128 * i for i in range(32)]) == 32
+    # a 64-byte stride: eight threads on each of two bank pairs -> 8 per phase
+    assert bm.wavefronts([64 * i for i in range(32)]) == 16
+    # a 136-byte stride (17 elements): conflict-free
+    assert bm.wavefronts([136 * i for i in range(32)]) == 2
+
+
+def test_exchange_positions_cover_the_pencil_once_per_instruction_set():
+    # every store set of one stage writes each position exactly once
+    plans = bm.read_plans()
+    for L, (NT, rad) in plans["Plan"].items():
+        seen = []
+        for pos in bm.exchange_positions(L, NT, rad, -1):
+            seen.extend(pos)
+        n_ex = len(rad) - 1
+        assert len(seen) == 2 * n_ex * L
+        assert sorted(seen) == sorted(list(range(L)) * 2 * n_ex)
+
+
+def test_swizzles_are_permutations():
+    for (L, NT, TP), (s, m) in bm.read_table().items():
+        rows = [p ^ ((p >> s) & m) for p in range(L)]
+        assert sorted(rows) == list(range(L)), (L, NT, TP)
+
+
+def test_header_table_is_the_models_choice():
+    want = {k: v[0] for k, v in bm.table().items() if v[0] != (0, 0)}
+    assert bm.read_table() == want
+
+
+def test_swizzle_removes_the_narrow_tile_conflicts():
+    NT, rad = bm.read_plans()["Plan"][512]
+    a, i = bm.cost(512, NT, rad, 4)
+    assert a / i > 1.5
+    a, i = bm.cost(512, NT, rad, 4, (3, 3))
+    assert a == i

@@ -82,6 +82,52 @@ def test_matvec_matches_pairwise_oracle(lib, name, gridf, m, x, prec, tol):
     ctx.close()
 
 
+REG_Z_LENGTHS = (16, 32, 64, 128, 256, 512)  # z plans with at most 8 points per thread
+
+
+@pytest.mark.parametrize("name,gridf,m,x", MATVEC_CASES, ids=[c[0] for c in MATVEC_CASES])
+@pytest.mark.parametrize("zpass", [0, 1], ids=["zgroups", "zregs"])
+def test_matvec_z_schedules_match_oracle(lib, name, gridf, m, x, zpass):
+    """Both complex64 z-pass schedules against the pairwise oracle.  Nine RHS
+    span one full block of eight RHS and a ragged one; a grid whose z plan has
+    no register-resident schedule must fall back to schedule 0."""
+    grid = gridf()
+    ctx = _ctx(lib, grid, m, x, lib.Precision.FP32_REFINED)
+    info = ctx.info()
+    ctx.set_schedule(zpass)
+    R = 9
+    assert ctx.get_schedule(R) == (zpass if info["Lz"] in REG_Z_LENGTHS else 0)
+    kd = info["kd"]
+    khat, ehat = _rhs_set(R)
+    X = random_complex((R, 3, info["ndipoles"]), 12)
+    Y = ctx.matvec(2, khat, ehat, X)
+    for r in range(R):
+        rr, beta = _site_beta(grid, m, kd, khat[r], ehat[r])
+        want, _ = pairwise.matvec(rr, kd, beta, X[r].T)
+        assert _rel(Y[r].T, want) < F32_TOL, (name, zpass, r)
+    ctx.close()
+
+
+def test_autotuned_schedule_reproduces_forced_one(lib):
+    """The autotuner picks one of the two schedules; the matvec it runs is
+    bit-identical to forcing that schedule."""
+    w = workload("ellipsoid96x64x32")
+    ctx = _ctx(lib, w.grid, w.m, w.x, lib.Precision.FP32_REFINED)
+    R = 12
+    ctx.set_schedule(-1)
+    pick = ctx.get_schedule(R)
+    assert pick in (0, 1)
+    X = random_complex((R, 3, ctx.info()["ndipoles"]), 4).astype(np.complex64)
+    k, e = np.resize(w.khat, (R, 3)), np.resize(w.ehat, (R, 3))
+    y_auto = ctx.matvec(2, k, e, X)
+    ctx.set_schedule(pick)
+    y_forced = ctx.matvec(2, k, e, X)
+    assert np.array_equal(y_auto, y_forced)
+    with pytest.raises(lib.DdaError):
+        ctx.set_schedule(2)
+    ctx.close()
+
+
 def test_matvec_is_complex_symmetric(lib):
     grid = ellipsoid_grid(11, 7, 5, 11, 7, 5)
     ctx = _ctx(lib, grid, [1.6 + 0.2j], 1.2, lib.Precision.FP64)
@@ -107,12 +153,34 @@ def test_matvec_row_samples_full_size(lib, name):
     X = random_complex((R, 3, N), 5)
     rows = np.random.default_rng(9).choice(N, 48, replace=False)
     rows[:2] = [0, N - 1]
-    for prec, tol in ((0, F64_TOL), (3, F64_TOL), (2, F32_TOL)):
+    for prec, tol, zpass in ((0, F64_TOL, -1), (3, F64_TOL, -1), (2, F32_TOL, 0), (2, F32_TOL, 1)):
+        ctx.set_schedule(zpass)
         Y = ctx.matvec(prec, w.khat[:R], w.ehat[:R], X)
         for r in range(R):
             rr, beta = _site_beta(w.grid, w.m, kd, w.khat[r], w.ehat[r])
             want, _ = pairwise.matvec(rr, kd, beta, X[r].T, rows=rows)
-            assert _rel(Y[r].T[rows], want) < tol, (name, prec, r)
+            assert _rel(Y[r].T[rows], want) < tol, (name, prec, zpass, r)
+    ctx.close()
+
+
+@pytest.mark.parametrize("zpass", [0, 1], ids=["zgroups", "zregs"])
+def test_matvec_row_samples_sphere256(lib, zpass):
+    """The 256^3 sphere (512^3 padded grid), complex64, both z schedules:
+    32 seeded rows recomputed by the pairwise oracle, over 3 RHS."""
+    w = workload("sphere256")
+    ctx = _ctx(lib, w.grid, w.m, w.x, lib.Precision.FP32_REFINED)
+    ctx.set_schedule(zpass)
+    kd = ctx.info()["kd"]
+    N = ctx.info()["ndipoles"]
+    R = 3
+    X = random_complex((R, 3, N), 6).astype(np.complex64)
+    rows = np.random.default_rng(10).choice(N, 32, replace=False)
+    rows[:2] = [0, N - 1]
+    Y = ctx.matvec(2, w.khat[:R], w.ehat[:R], X)
+    for r in range(R):
+        rr, beta = _site_beta(w.grid, w.m, kd, w.khat[r], w.ehat[r])
+        want, _ = pairwise.matvec(rr, kd, beta, X[r].T.astype(complex), rows=rows)
+        assert _rel(Y[r].T[rows], want) < F32_TOL, (zpass, r)
     ctx.close()
 
 

@@ -348,6 +348,7 @@ def run_gb300(args):
                "time_to_solution_ms": t_e2e * 1e3 / args.steps}
 
     roof = roofline(kstats, info, R, w.name)
+    mv_roof = matvec_roofline(kstats, info, "c64") if kstats else None
     launches = int(sum(s["launches"] for s in kstats.values()) / args.steps) * args.steps if kstats else 0
 
     cpu = None
@@ -371,7 +372,8 @@ def run_gb300(args):
             "prepare_ms": prepare_ms,
             "traced_ms_per_step": sum(per_tr) / len(per_tr),
             "kernels": {k_: {"launches": v["launches"], "ms": v["ms"], "share": v["share"]} for k_, v in kstats.items()},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "roofline": roof, "matvec_roofline": mv_roof,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -422,6 +424,20 @@ def roofline(kstats, info, R, workload_name=None):
             "traffic": traffic, "traffic_note": "ncu cold-cache DRAM bytes per launch (profiles/)" if traffic else None,
             "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": b,
             "rhs_per_launch": units_per_launch, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
+
+
+def matvec_roofline(kstats, info, suffix="c64"):
+    """The whole FFT-convolution matvec (its five passes together) against
+    HBM: algorithmic bytes of all launches of the passes / their total time."""
+    hbm, src = load_peaks()
+    kinds = [k for k in kstats if k.endswith(suffix) and pass_bytes(k, info, 1) is not None]
+    if len(kinds) != 5:
+        return None
+    ms = sum(kstats[k]["ms"] for k in kinds)
+    b = sum(pass_bytes(k, info, kstats[k]["units"] / kstats[k]["launches"]) * kstats[k]["launches"] for k in kinds)
+    ach = b / (ms / 1e3) / 1e9
+    return {"passes": sorted(kinds), "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": ach / hbm, "ms": ms, "algorithmic_bytes": b, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
 
 
 # ----------------------------------------------------------- CPU baseline ----
@@ -522,9 +538,11 @@ def run_matvec_only(args):
         avg = v["ms"] / v["launches"]
         b = pass_bytes(name, info, v["units"] / v["launches"])
         kern[name] = {"avg_ms": avg, "gbs": (b / (avg / 1e3) / 1e9) if b else None}
+    mv_roof = matvec_roofline(kst, info, "c64" if args.precision == "fp32" else "c128")
     zpass = ctx.get_schedule(R) if args.precision == "fp32" else 0
     print(json.dumps({"mode": "matvec", "workload": w.name, "rhs": R, "precision": args.precision, "zpass": zpass,
-                      "ms_per_matvec": ms, "rhs_matvecs_per_s": R / (ms / 1e3), "kernels": kern}), flush=True)
+                      "ms_per_matvec": ms, "rhs_matvecs_per_s": R / (ms / 1e3), "kernels": kern,
+                      "matvec_roofline": mv_roof}), flush=True)
     ctx.close()
 
 

@@ -459,24 +459,6 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
     const int r0 = blockIdx.z * RB;
     const int hx = Lx / 2 + 1, hy = Ly / 2 + 1;
     const int64_t cs = (int64_t)HZ * hy * hx;
-    {
-        const int kyo = ky <= Ly / 2 ? ky : Ly - ky;
-        const bool fy = ky > Ly / 2;
-        for (int e = threadIdx.x; e < 6 * HZ * TP; e += blockDim.x) {
-            const int tt = e % TP, kz = (e / TP) % HZ, cc = e / (TP * HZ);
-            const int kx = blockIdx.x * TP + tt;
-            C g = czero<C>();
-            if (kx < Lx) {
-                const bool fx = kx > Lx / 2;
-                const int kxo = fx ? Lx - kx : kx;
-                g = gh[cc * cs + ((int64_t)kz * hy + kyo) * hx + kxo];
-                // xy is odd in x and y, xz odd in x, yz odd in y (z handled at use)
-                const bool flip = (cc == 1 && fx != fy) || (cc == 2 && fx) || (cc == 4 && fy);
-                if (flip) g = cscale(g, T(-1));
-            }
-            gs[(cc * HZ + kz) * TP + tt] = g;
-        }
-    }
     const int t = threadIdx.x % TP, u = threadIdx.x / TP;
     const int kx = blockIdx.x * TP + t;
     const bool valid = kx < Lx;
@@ -505,8 +487,27 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
                     nxt[c][q * JN + j] = valid ? __ldcs(bc + (int64_t)(u + q * NT + j * (LZ / R0)) * plane) : czero<C>();
         }
     };
+    // the first RHS's loads are in flight while the Green tensor is staged
     int r = next_active(r0);
     if (r < rend) prefetch(r);
+    {
+        const int kyo = ky <= Ly / 2 ? ky : Ly - ky;
+        const bool fy = ky > Ly / 2;
+        for (int e = threadIdx.x; e < 6 * HZ * TP; e += blockDim.x) {
+            const int tt = e % TP, kz = (e / TP) % HZ, cc = e / (TP * HZ);
+            const int kxs = blockIdx.x * TP + tt;
+            C g = czero<C>();
+            if (kxs < Lx) {
+                const bool fx = kxs > Lx / 2;
+                const int kxo = fx ? Lx - kxs : kxs;
+                g = gh[cc * cs + ((int64_t)kz * hy + kyo) * hx + kxo];
+                // xy is odd in x and y, xz odd in x, yz odd in y (z handled at use)
+                const bool flip = (cc == 1 && fx != fy) || (cc == 2 && fx) || (cc == 4 && fy);
+                if (flip) g = cscale(g, T(-1));
+            }
+            gs[(cc * HZ + kz) * TP + tt] = g;
+        }
+    }
 #pragma unroll 1
     while (r < rend) {
         C vc[3][E];
@@ -714,14 +715,17 @@ template <typename T> struct LaunchX {
         cudaError_t e;
         if constexpr (sizeof(T) == 4 && zreg_ok<LZ>()) {
             if (zvar == 1) {
-                constexpr int TP = tp_zr<LZ>();
+                // (long columns: a staged Green tile is ~2 RHS of loads, so
+                // it serves 16 RHS)
+                constexpr int TP = tp_zr<LZ>(), RBZ = LZ >= 256 ? 16 : 8;
                 constexpr size_t sm = zreg_smem<LZ, T>();
-                e = multi ? allow_smem(k_zconv_reg<T, LZ, RB>, sm) : allow_smem(k_zconv_reg<T, LZ, 1>, sm);
+                e = multi ? allow_smem(k_zconv_reg<T, LZ, RBZ>, sm) : allow_smem(k_zconv_reg<T, LZ, 1>, sm);
                 if (e != cudaSuccess) return e;
-                dim3 grid((g.Lx + TP - 1) / TP, g.Ly, (R + rb - 1) / rb);
+                const int rbz = multi ? RBZ : 1;
+                dim3 grid((g.Lx + TP - 1) / TP, g.Ly, (R + rbz - 1) / rbz);
                 PROF_BEGIN(st);
                 if (multi)
-                    k_zconv_reg<T, LZ, RB><<<grid, zreg_threads<LZ>(), sm, st>>>(u2, gh, R, g.Lx, g.Ly, tw, active);
+                    k_zconv_reg<T, LZ, RBZ><<<grid, zreg_threads<LZ>(), sm, st>>>(u2, gh, R, g.Lx, g.Ly, tw, active);
                 else
                     k_zconv_reg<T, LZ, 1><<<grid, zreg_threads<LZ>(), sm, st>>>(u2, gh, R, g.Lx, g.Ly, tw, active);
                 PROF_END(KK_ZCONV_C64 + koff, R, st);

@@ -108,6 +108,28 @@ def test_matvec_z_schedules_match_oracle(lib, name, gridf, m, x, zpass):
     ctx.close()
 
 
+@pytest.mark.parametrize("zpass", [0, 1], ids=["zgroups", "zregs"])
+def test_matvec_long_z_columns_many_rhs(lib, zpass):
+    """A 4x5x100 rod (256-point z transform, where the register schedule
+    takes 16 RHS per block) with 18 RHS: one full block of RHS and a ragged
+    one, against the pairwise oracle."""
+    grid = np.ones((100, 5, 4), np.uint8)
+    m = [1.4 + 0.05j]
+    ctx = _ctx(lib, grid, m, 2.0, lib.Precision.FP32_REFINED)
+    info = ctx.info()
+    assert info["Lz"] == 256
+    ctx.set_schedule(zpass)
+    R = 18
+    khat, ehat = _rhs_set(R)
+    X = random_complex((R, 3, info["ndipoles"]), 13)
+    Y = ctx.matvec(2, khat, ehat, X)
+    for r in range(R):
+        rr, beta = _site_beta(grid, m, info["kd"], khat[r], ehat[r])
+        want, _ = pairwise.matvec(rr, info["kd"], beta, X[r].T)
+        assert _rel(Y[r].T, want) < F32_TOL, (zpass, r)
+    ctx.close()
+
+
 def test_autotuned_schedule_reproduces_forced_one(lib):
     """The autotuner picks one of the two schedules; the matvec it runs is
     bit-identical to forcing that schedule."""

@@ -269,6 +269,99 @@ __device__ __forceinline__ void fft_stages(C (&v)[PL::E], int u, const C* __rest
     }
 }
 
+// NP pencils of one thread in lockstep: every stage runs on all NP before
+// the exchange, so a stage's twiddles are loaded once for all of them and
+// the NP exchanges share one pair of barriers.  ld(p, pos) / st(p, pos, val)
+// address pencil p's own exchange plane.
+template <typename C, class PL, int DIR, int S, int NP, class Ld, class St>
+__device__ __forceinline__ void fft_stages_np(C (&v)[NP][PL::E], int u, const C* __restrict__ tw, Ld& ld, St& st,
+                                              bool half_first) {
+    constexpr int L = PL::L, NT = PL::NT, E = PL::E, NS = PL::NS;
+    constexpr int R = stage_radix<PL, DIR>(S);
+    constexpr int P = stage_p<PL, DIR>(S);
+    constexpr int NB = E / R;
+    constexpr int STEP = L / (P * R);
+    static_assert(E % R == 0, "radix must divide the points per thread");
+    if constexpr (P > 1) {
+        if constexpr (NT % P == 0) {
+            const int k = u % P;
+            C w[R];
+#pragma unroll
+            for (int j = 1; j < R; ++j) {
+                w[j] = tw[j * k * STEP];
+                if constexpr (DIR > 0) w[j].y = -w[j].y;
+            }
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+#pragma unroll
+                for (int q = 0; q < NB; ++q)
+#pragma unroll
+                    for (int j = 1; j < R; ++j) v[p][q * R + j] = cmul(v[p][q * R + j], w[j]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                int k;
+                if constexpr (P % NT == 0) k = u + (q % (P / NT)) * NT;
+                else k = (u + q * NT) % P;
+#pragma unroll
+                for (int j = 1; j < R; ++j) {
+                    C w = tw[j * k * STEP];
+                    if constexpr (DIR > 0) w.y = -w.y;
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) v[p][q * R + j] = cmul(v[p][q * R + j], w);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            if constexpr (S == 0 && (R % 2 == 0)) {
+                if (half_first) Dft<R, DIR, C>::run_half(&v[p][q * R]);
+                else Dft<R, DIR, C>::run(&v[p][q * R]);
+            } else {
+                Dft<R, DIR, C>::run(&v[p][q * R]);
+            }
+        }
+    if constexpr (S < NS - 1) {
+        __syncthreads();
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            if constexpr (NT % P == 0) {
+                const int base = (u / P) * (P * R) + (u % P);
+#pragma unroll
+                for (int q = 0; q < NB; ++q)
+#pragma unroll
+                    for (int m = 0; m < R; ++m) st(p, base + q * NT * R + m * P, v[p][q * R + m]);
+            } else if constexpr (P % NT == 0) {
+#pragma unroll
+                for (int q = 0; q < NB; ++q)
+#pragma unroll
+                    for (int m = 0; m < R; ++m)
+                        st(p, u + (q - q % (P / NT)) * NT * R + (q % (P / NT)) * NT + m * P, v[p][q * R + m]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < NB; ++q) {
+                    const int i = u + q * NT, k = i % P;
+#pragma unroll
+                    for (int m = 0; m < R; ++m) st(p, (i - k) * R + k + m * P, v[p][q * R + m]);
+                }
+            }
+        }
+        __syncthreads();
+        constexpr int R2 = stage_radix<PL, DIR>(S + 1);
+        constexpr int NB2 = E / R2;
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+#pragma unroll
+            for (int q = 0; q < NB2; ++q)
+#pragma unroll
+                for (int j = 0; j < R2; ++j) v[p][q * R2 + j] = ld(p, u + q * NT + j * (L / R2));
+        fft_stages_np<C, PL, DIR, S + 1, NP, Ld, St>(v, u, tw, ld, st, false);
+    }
+}
+
 // Load the first stage's inputs through first(pos), then run all stages.
 // HALF_IN: positions >= L/2 are zero and are neither loaded nor transformed.
 template <typename C, class PL, int DIR, bool HALF_IN, class First, class Ld, class St, bool WARP = false>

@@ -422,10 +422,10 @@ __global__ void __launch_bounds__(3 * tp_z<LZ, T>() * ZPlan<LZ>::NT, zconv_min_b
 
 // ---- z pass, register-resident schedule (complex64) ----------------------------
 // Same product as k_zconv, but each thread keeps all three components of its
-// points in registers: per RHS it transforms P_x, P_y, P_z of its column
-// one after another through a single shared exchange plane, forms the 3x3
-// product in registers (no spectra round trip through shared memory), and
-// inverse-transforms.  The global loads of the next RHS are issued before
+// points in registers: per RHS it transforms P_x, P_y, P_z of its column in
+// lockstep (one exchange plane per component, so each stage's twiddles and
+// barriers serve all three), forms the 3x3 product in registers (no spectra
+// round trip through shared memory), and inverse-transforms.  The global loads of the next RHS are issued before
 // the current one is transformed, so one block keeps its column's loads in
 // flight while computing.  Shared traffic per point is about half that of
 // k_zconv; the price is ~128 registers per thread, so the plan must keep
@@ -441,7 +441,7 @@ template <int L> __host__ __device__ constexpr int zreg_min_blocks() {
     return 512 / zreg_threads<L>() < 1 ? 1 : 512 / zreg_threads<L>();
 }
 template <int L, typename T> __host__ __device__ constexpr size_t zreg_smem() {
-    return ((size_t)L + (size_t)6 * (L / 2 + 1)) * tp_zr<L>() * sizeof(cx<T>);
+    return (((size_t)3 * L + (size_t)6 * (L / 2 + 1)) * tp_zr<L>() + L) * sizeof(cx<T>);
 }
 
 template <typename T, int LZ, int RB>
@@ -453,8 +453,9 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
     constexpr int TP = tp_zr<LZ>(), NT = PL::NT, NZ = LZ / 2, HZ = LZ / 2 + 1, E = PL::E;
     constexpr int R0 = stage_radix<PL, -1>(0), NB0 = E / R0, JN = R0 / 2;  // half-zero first stage
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);  // exchange plane [LZ][TP]
-    C* gs = buf + LZ * TP;                    // Green tensor [6][HZ][TP]
+    C* buf = reinterpret_cast<C*>(smem_raw);  // exchange planes [3][LZ][TP]
+    C* gs = buf + 3 * LZ * TP;                // Green tensor [6][HZ][TP]
+    C* tws = gs + 6 * HZ * TP;                // twiddle table [LZ]
     const int ky = blockIdx.y;
     const int r0 = blockIdx.z * RB;
     const int hx = Lx / 2 + 1, hy = Ly / 2 + 1;
@@ -465,8 +466,8 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
     const int64_t plane = (int64_t)Ly * Lx;
     C* bt = buf + t;
     const C* gt = gs + t;
-    auto ld = [&](int pos) { return bt[swizzle_row<LZ, NT, TP, sizeof(C)>(pos) * TP]; };
-    auto st = [&](int pos, C val) { bt[swizzle_row<LZ, NT, TP, sizeof(C)>(pos) * TP] = val; };
+    auto ld = [&](int p, int pos) { return bt[(p * LZ + swizzle_row<LZ, NT, TP, sizeof(C)>(pos)) * TP]; };
+    auto st = [&](int p, int pos, C val) { bt[(p * LZ + swizzle_row<LZ, NT, TP, sizeof(C)>(pos)) * TP] = val; };
     const int rend = min(R, r0 + RB);
     auto next_active = [&](int r) {  // uniform across the block
         while (r < rend && active != nullptr && active[r] == 0) ++r;
@@ -507,6 +508,9 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
             }
             gs[(cc * HZ + kz) * TP + tt] = g;
         }
+        // twiddles from shared memory: the per-stage loads of the six
+        // transforms per RHS then wait on shared, not L1, latency
+        for (int e = threadIdx.x; e < LZ; e += blockDim.x) tws[e] = tw[e];
     }
 #pragma unroll 1
     while (r < rend) {
@@ -520,9 +524,8 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
         const int rn = next_active(r + 1);
         if (rn < rend) prefetch(rn);
         // (each transform's first exchange opens with a barrier, which also
-        // orders it after the previous transform's last reads of the plane)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) fft_stages<C, PL, -1, 0>(vc[c], u, tw, ld, st, true);
+        // orders it after the previous transform's last reads of the planes)
+        fft_stages_np<C, PL, -1, 0, 3>(vc, u, tws, ld, st, true);
         for_each_out<PL, -1, false>(u, [&](int idx, int kz) {
             const bool fz = kz > LZ / 2;
             const int kzo = fz ? LZ - kz : kz;
@@ -538,9 +541,9 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
             vc[1][idx] = cadd(cadd(cmul(gxy, px), cmul(gyy, py)), cmul(gyz, pz));
             vc[2][idx] = cadd(cadd(cmul(gxz, px), cmul(gyz, py)), cmul(gzz, pz));
         });
+        fft_stages_np<C, PL, +1, 0, 3>(vc, u, tws, ld, st, false);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            pencil_fft_regs<C, PL, +1>(vc[c], u, tw, ld, st);
             C* bc = column(r, c);
             for_each_out<PL, +1, true>(u, [&](int idx, int pos) {
                 if (valid) __stcs(bc + (int64_t)pos * plane, vc[c][idx]);

@@ -327,3 +327,72 @@ def qabs_gradient(kd: float, aeff: float, eps_site: np.ndarray, khat, ehat,
 def absorption_weights(kd: float, beta: np.ndarray) -> np.ndarray:
     """w_j = -Im(1/alpha_j) - (2/3) k^3, so that C_abs = 4 pi k sum_j w_j |P_j|^2."""
     return -np.imag(beta) - (2.0 / 3.0) * kd ** 3
+
+
+# --------------------------------------------------------------- near field --
+def nearfield_box(shape_zyx, ext) -> tuple[tuple[int, int, int], tuple[int, int, int]]:
+    """Extended computational volume of a near-field calculation ("Near-Field
+    Calculations"; ddscat.par NRFLD = 1 with the six fractions r1..r6).
+
+    The guide extends X1 <= x <= X2 to X1 - r1 Lx <= x <= X2 + r2 Lx (and
+    likewise in y with r3, r4 and in z with r5, r6), Lx = X2 - X1.  Reading:
+    the extended volume is a box of lattice points of the same spacing, with
+    nint(r n) points added on each side of an axis of n points (its
+    ELLIPSOID_NEARFIELD example, 48^3 extended by 0.5 on every side, is the
+    96^3 volume the guide's timing line quotes).
+
+    shape_zyx: target grid shape (nz, ny, nx); ext: (r1, ..., r6).
+    Returns ((ex, ey, ez), (ox, oy, oz)): box extent in points and the box
+    index of target point (0, 0, 0) (the points added on the low side).
+    """
+    nz, ny, nx = shape_zyx
+    lo, hi = [], []
+    for n, (ra, rb) in zip((nx, ny, nz), ((ext[0], ext[1]), (ext[2], ext[3]), (ext[4], ext[5]))):
+        if ra < 0 or rb < 0:
+            raise ValueError("near-field extension fractions must be non-negative")
+        lo.append(int(math.floor(ra * n + 0.5)))
+        hi.append(int(math.floor(rb * n + 0.5)))
+    dims = (nx + lo[0] + hi[0], ny + lo[1] + hi[1], nz + lo[2] + hi[2])
+    return dims, (lo[0], lo[1], lo[2])
+
+
+def nearfield_points(shape_zyx, ext) -> np.ndarray:
+    """Positions (Ne, 3) of every point of the extended box, x fastest, in
+    the target's frame (origin at the centre of the target's own
+    computational volume, as in site_positions)."""
+    nz, ny, nx = shape_zyx
+    (ex, ey, ez), (ox, oy, oz) = nearfield_box(shape_zyx, ext)
+    iz, iy, ix = np.meshgrid(np.arange(ez), np.arange(ey), np.arange(ex), indexing="ij")
+    return np.stack([(ix - ox - (nx - 1) / 2.0).ravel(), (iy - oy - (ny - 1) / 2.0).ravel(),
+                     (iz - oz - (nz - 1) / 2.0).ravel()], axis=1).astype(np.float64)
+
+
+def scattered_field(r_src: np.ndarray, P: np.ndarray, r_pts: np.ndarray, kd: float,
+                    chunk: int = 256) -> np.ndarray:
+    """E_sca at each point: the field of all dipoles P_l at r_src, except a
+    dipole sitting on the point itself (the guide's E_sca "not including the
+    dipole at j"): E_sca(r) = -sum_{l: r_l != r} A(r - r_l) P_l, with A the
+    off-diagonal block of interaction_tensor.  Returns (Npts, 3)."""
+    P = np.asarray(P, dtype=np.complex128)
+    out = np.empty((r_pts.shape[0], 3), dtype=np.complex128)
+    for s in range(0, r_pts.shape[0], chunk):
+        d = r_pts[s:s + chunk][:, None, :] - r_src[None, :, :]      # (c, N, 3)
+        same = np.all(d == 0.0, axis=-1)
+        d[same] = (1.0, 0.0, 0.0)
+        blk = interaction_tensor(d, kd)
+        blk[same] = 0.0
+        out[s:s + chunk] = -np.einsum("clab,lb->ca", blk, P)
+    return out
+
+
+def nearfield(grid: np.ndarray, P: np.ndarray, kd: float, khat, ehat, ext):
+    """E_inc and E_sca at every point of the extended box (x fastest).
+
+    P (N, 3): the target's polarization in site order.  Returns
+    (dims, offset, E_inc (Ne, 3), E_sca (Ne, 3)); at a target point j an
+    exact solution satisfies P_j = alpha_j (E_inc,j + E_sca,j).
+    """
+    dims, off = nearfield_box(grid.shape, ext)
+    r_src, _ = site_positions(grid)
+    r_pts = nearfield_points(grid.shape, ext)
+    return dims, off, incident_field(r_pts, kd, khat, ehat), scattered_field(r_src, P, r_pts, kd)

@@ -87,3 +87,47 @@ int oracle_pairwise_rows(int64_t n, const double *r, double kd, const double *be
     }
     return nthreads;
 }
+
+/* Scattered field at arbitrary points (near-field rows): for each point q,
+ * E[6*q + ...] = -sum_{l: r_l != x_q} A(x_q - r_l) P_l, the field of every
+ * dipole except one sitting on the point itself (oracle/dda.py:
+ * scattered_field).  x[3*q + a] point positions. */
+int oracle_field_points(int64_t n, const double *r, double kd, const double *P,
+                        int64_t npts, const double *x, double *E)
+{
+    int nthreads = 1;
+#pragma omp parallel
+    {
+#pragma omp single
+        {
+#ifdef _OPENMP
+            nthreads = omp_get_num_threads();
+#endif
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t q = 0; q < npts; ++q) {
+            double complex acc[3] = {0, 0, 0};
+            const double k2 = kd * kd;
+            for (int64_t l = 0; l < n; ++l) {
+                double d[3] = {x[3 * q] - r[3 * l], x[3 * q + 1] - r[3 * l + 1], x[3 * q + 2] - r[3 * l + 2]};
+                if (d[0] == 0.0 && d[1] == 0.0 && d[2] == 0.0) continue;
+                double rho = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                double rh[3] = {d[0] / rho, d[1] / rho, d[2] / rho};
+                double complex ph = cexp(I * kd * rho) / rho;
+                double complex c1 = ph * k2;
+                double complex c2 = ph * (I * kd * rho - 1.0) / (rho * rho);
+                double complex p[3];
+                for (int a = 0; a < 3; ++a)
+                    p[a] = P[6 * l + 2 * a] + I * P[6 * l + 2 * a + 1];
+                double complex rp = rh[0] * p[0] + rh[1] * p[1] + rh[2] * p[2];
+                for (int a = 0; a < 3; ++a)
+                    acc[a] += c1 * (rh[a] * rp - p[a]) + c2 * (3.0 * rh[a] * rp - p[a]);
+            }
+            for (int a = 0; a < 3; ++a) {
+                E[6 * q + 2 * a] = -creal(acc[a]);
+                E[6 * q + 2 * a + 1] = -cimag(acc[a]);
+            }
+        }
+    }
+    return nthreads;
+}

@@ -36,6 +36,8 @@ def _load():
         lib.oracle_pairwise_rows.argtypes = [ctypes.c_int64, dp, ctypes.c_double, dp, dp,
                                              ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), dp]
         lib.oracle_pairwise_rows.restype = ctypes.c_int
+        lib.oracle_field_points.argtypes = [ctypes.c_int64, dp, ctypes.c_double, dp, ctypes.c_int64, dp, dp]
+        lib.oracle_field_points.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -62,3 +64,15 @@ def matvec(r: np.ndarray, kd: float, beta: np.ndarray, P: np.ndarray, rows=None)
         nt = lib.oracle_pairwise_rows(n, _dp(r), kd, _dp(beta), _dp(P), rows.size,
                                       rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(Y))
     return Y, nt
+
+
+def scattered_field(r: np.ndarray, P: np.ndarray, x: np.ndarray, kd: float) -> np.ndarray:
+    """E_sca at the points x (M, 3) from dipoles P (N, 3) at r (N, 3), the
+    dipole on a point excluded (same definition as dda.scattered_field)."""
+    lib = _load()
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    P = np.ascontiguousarray(P, dtype=np.complex128)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    E = np.empty((x.shape[0], 3), dtype=np.complex128)
+    lib.oracle_field_points(r.shape[0], _dp(r), kd, _dp(P), x.shape[0], _dp(x), _dp(E))
+    return E

@@ -19,6 +19,8 @@ _orig_einc = dda.incident_field
 _orig_j = dda._sph_j012
 _orig_grad = dda.qabs_gradient
 _orig_sites = dda.site_positions
+_orig_scat = dda.scattered_field
+_orig_box = dda.nearfield_box
 
 
 def _tensor_sign(rvec, kd):            # (1 - ik rho) instead of (ik rho - 1)
@@ -78,6 +80,26 @@ def _sites_zyx(grid):                   # x and z swapped in the site positions
     return r[:, ::-1].copy(), c
 
 
+def _scat_sign(r_src, P, r_pts, kd, chunk=256):   # +A P instead of -A P
+    return -_orig_scat(r_src, P, r_pts, kd, chunk)
+
+
+def _scat_self(r_src, P, r_pts, kd, chunk=256):   # a self term at target points (here + P_j)
+    out = _orig_scat(r_src, P, r_pts, kd, chunk)
+    for j, rv in enumerate(r_pts):
+        hit = np.nonzero(np.all(r_src == rv, axis=1))[0]
+        if hit.size:
+            out[j] += P[hit[0]]
+    return out
+
+
+def _box_floor(shape_zyx, ext):                    # floor instead of nearest for the added layers
+    nz, ny, nx = shape_zyx
+    lo = [int(math.floor(ext[0] * nx)), int(math.floor(ext[2] * ny)), int(math.floor(ext[4] * nz))]
+    hi = [int(math.floor(ext[1] * nx)), int(math.floor(ext[3] * ny)), int(math.floor(ext[5] * nz))]
+    return (nx + lo[0] + hi[0], ny + lo[1] + hi[1], nz + lo[2] + hi[2]), tuple(lo)
+
+
 MUTATIONS = [
     ("interaction_tensor", _tensor_sign, [pins.two_dipole_error]),
     ("interaction_tensor", _tensor_no_far, [pins.two_dipole_error]),
@@ -89,6 +111,9 @@ MUTATIONS = [
     ("_sph_j012", _j_sign, [pins.pair_sum_vs_quadrature_error]),
     ("qabs_gradient", _grad_sign, [pins.adjoint_gradient_error]),
     ("site_positions", _sites_zyx, [pins.site_axes_error]),
+    ("scattered_field", _scat_sign, [pins.nearfield_self_consistency_error, pins.nearfield_single_dipole_error]),
+    ("scattered_field", _scat_self, [pins.nearfield_self_consistency_error]),
+    ("nearfield_box", _box_floor, [pins.nearfield_box_error]),
 ]
 
 

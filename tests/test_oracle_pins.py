@@ -117,6 +117,62 @@ def symmetry_error():
     return float(np.abs(A - A.T).max() / np.abs(A).max())
 
 
+def nearfield_self_consistency_error(kd=0.42, ext=(0.4, 0.6, 0.0, 0.5, 1.0, 0.3)):
+    """The guide's own accuracy check of a near-field run ("The Binary Files
+    ... .E"): an exact solution satisfies P_j = alpha_j (E_inc,j + E_sca,j) at
+    every target point.  Dense-LU P of a small two-material block, then the
+    extended-box fields at the target points."""
+    grid = block_bernoulli_grid(4, 3, 3, seed=11)
+    m = np.array([1.6 + 0.3j, 1.2 + 0.05j])
+    r, comp = dda.site_positions(grid)
+    khat, ehat = np.array([0.0, 0.6, 0.8]), np.array([1.0, 0.0, 0.0], complex)
+    beta = dda.ldr_inverse_polarizability((m ** 2)[comp - 1], kd, khat, ehat)
+    E = dda.incident_field(r, kd, khat, ehat)
+    P = dda.solve_dense(dda.dense_matrix(r, kd, beta), E)
+    dims, off, Ei, Es = dda.nearfield(grid, P, kd, khat, ehat, ext)
+    nz, ny, nx = grid.shape
+    ex, ey, ez = dims
+    iz, iy, ix = np.nonzero(grid)   # site order: x fastest
+    box = ((iz + off[2]) * ey + (iy + off[1])) * ex + (ix + off[0])
+    lhs = P
+    rhs = (Ei[box] + Es[box]) / beta[:, None]
+    return float(np.abs(lhs - rhs).max() / np.abs(lhs).max())
+
+
+def nearfield_single_dipole_error(kd=0.7):
+    """One dipole: E_sca at every vacuum point of the box is Jackson's field
+    of the dipole (eq. 9.18), independent of the interaction tensor code."""
+    grid = np.ones((1, 1, 1), np.uint8)
+    p = np.array([0.3 + 0.1j, -0.2 + 0.4j, 0.5 - 0.25j])
+    ext = (2.0, 3.0, 1.0, 2.0, 2.0, 1.0)
+    dims, off, _, Es = dda.nearfield(grid, p[None, :], kd, [1, 0, 0], [0, 1, 0], ext)
+    pts = dda.nearfield_points(grid.shape, ext)
+    err = 0.0
+    for j, rv in enumerate(pts):
+        if np.all(rv == 0):                # no self field at the dipole's own site
+            err = max(err, float(np.abs(Es[j]).max()))
+            continue
+        want = jackson_dipole_field(rv, p, kd)
+        err = max(err, float(np.abs(Es[j] - want).max() / np.abs(want).max()))
+    return err
+
+
+def nearfield_box_error():
+    """Box geometry: the guide's ELLIPSOID_NEARFIELD example (48^3 volume
+    extended by 50 % on every side -> 96^3, centred on the sphere) and a
+    hand-counted asymmetric case."""
+    bad = 0
+    dims, off = dda.nearfield_box((48, 48, 48), [0.5] * 6)
+    bad += dims != (96, 96, 96) or off != (24, 24, 24)
+    # nx = 5: +1 (0.2*5) low, +3 (nint 2.5) high; ny = 4: 0 low, 4 high; nz = 3: 1 low, 0 high
+    dims, off = dda.nearfield_box((3, 4, 5), [0.2, 0.5, 0.0, 1.0, 0.25, 0.1])
+    bad += dims != (9, 8, 4) or off != (1, 0, 1)
+    pts = dda.nearfield_points((48, 48, 48), [0.5] * 6)
+    bad += not np.allclose(pts.mean(axis=0), 0.0)          # centred on the target
+    bad += not np.allclose(pts[0], (-47.5, -47.5, -47.5))   # 24 + 23.5 lattice units below the centre
+    return float(bad)
+
+
 # ------------------------------------------------------------------- tests --
 def test_pseudosphere_counts_match_guide(golden_dir):
     for box, diam, count, *_ in _golden_rows(os.path.join(golden_dir, "pseudosphere_counts.txt")):
@@ -373,3 +429,25 @@ def site_axes_error():
 
 def test_site_positions_follow_target_axes():
     assert site_axes_error() == 0.0
+
+
+def test_nearfield_satisfies_dda_equations_at_target_points():
+    assert nearfield_self_consistency_error() < 1e-11
+
+
+def test_nearfield_of_one_dipole_is_the_textbook_field():
+    assert nearfield_single_dipole_error() < 1e-12
+
+
+def test_nearfield_box_follows_the_guide():
+    assert nearfield_box_error() == 0.0
+
+
+def test_c_scattered_field_matches_numpy():
+    grid = ellipsoid_grid(6, 5, 4, 6, 5, 4)
+    r, _ = dda.site_positions(grid)
+    P = random_complex((len(r), 3), 21)
+    x = dda.nearfield_points(grid.shape, (0.5, 0.3, 0.0, 0.4, 0.25, 0.25))
+    a = pairwise.scattered_field(r, P, x, 0.33)
+    b = dda.scattered_field(r, P, x, 0.33)
+    assert np.abs(a - b).max() < 1e-12 * np.abs(b).max()

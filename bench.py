@@ -55,12 +55,14 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--fp64-sequential", action="store_true",
                     help="FP64 leg solves the RHS one at a time (orientation-sweep comparison)")
-    ap.add_argument("--mode", default="solve", choices=["solve", "matvec", "grad"],
+    ap.add_argument("--ext", type=float, default=0.5, help="nearfield mode: extension fraction on every side")
+    ap.add_argument("--mode", default="solve", choices=["solve", "matvec", "grad", "nearfield"],
                     help="matvec: only time dda_matvec_device (for profiler captures)")
     ap.add_argument("--rhs", type=int, default=0, help="matvec mode: RHS per product (0 = workload's)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="matvec mode precision")
     ap.add_argument("--zpass", type=int, default=-1, choices=[-1, 0, 1],
-                    help="complex64 z-pass schedule: -1 autotuned, 0 component groups, 1 register-resident")
+                    help="complex64 z-pass schedule: -1 autotuned (default), 0 component groups, "
+                         "1 register-resident (forcing one makes profiler runs reproduce the tuned choice)")
     return ap.parse_args()
 
 
@@ -188,7 +190,10 @@ def pass_flops(kind, info, R):
 KERNEL_SOURCES = ["paper_1202_3424_gb300/csrc/matvec_impl.cuh", "paper_1202_3424_gb300/csrc/matvec_f32.cu",
                   "paper_1202_3424_gb300/csrc/fft.cuh", "paper_1202_3424_gb300/csrc/krylov_dev.cuh",
                   "paper_1202_3424_gb300/csrc/common.cuh"]
-CAPTURES = {("z_conv_c64", "sphere64", 2): "profiles/zconv_f32_sphere64.md"}
+# (pass, workload, RHS per launch) -> (summary file, kernel heading in it)
+CAPTURES = {("z_conv_c64", "sphere64", 2): ("profiles/zconv_f32_sphere64.md", "k_zconv<float, 128, 8>"),
+            ("z_conv_c64", "ellipsoid96x64x32", 32): ("profiles/passes_f32_ellipsoid96x64x32.md",
+                                                      "k_zconv_reg<float, 64, 8>")}
 
 
 def captured_traffic(kernel, workload_name, rhs_per_launch):
@@ -196,9 +201,10 @@ def captured_traffic(kernel, workload_name, rhs_per_launch):
     workload, or None when there is none or the kernel source has changed
     since the capture (the summary records a hash of the sources)."""
     import hashlib
-    path = CAPTURES.get((kernel, workload_name, int(round(rhs_per_launch))))
-    if path is None or not os.path.exists(os.path.join(ROOT, path)):
+    entry = CAPTURES.get((kernel, workload_name, int(round(rhs_per_launch))))
+    if entry is None or not os.path.exists(os.path.join(ROOT, entry[0])):
         return None
+    path, heading = entry
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
         fp = os.path.join(ROOT, f)
@@ -206,11 +212,13 @@ def captured_traffic(kernel, workload_name, rhs_per_launch):
             return None
         with open(fp, "rb") as fh:
             h.update(fh.read())
-    sha, traffic = None, None
+    sha, traffic, in_section = None, None, False
     for line in open(os.path.join(ROOT, path)):
         if line.startswith("source_sha256:"):
             sha = line.split()[1]
-        if line.startswith("traffic_bytes_per_launch:"):
+        if line.startswith("### "):
+            in_section = line[4:].startswith(heading)
+        if in_section and line.startswith("traffic_bytes_per_launch:") and traffic is None:
             traffic = int(line.split()[1])
     return traffic if sha is not None and h.hexdigest().startswith(sha) else None
 
@@ -247,6 +255,7 @@ def run_gb300(args):
     t0 = time.perf_counter()
     ctx.prepare_size_parameter(w.x, dda.Precision.FP32_REFINED)
     prepare_ms = (time.perf_counter() - t0) * 1e3
+    ctx.set_schedule(args.zpass)
     info = ctx.info()
     N = info["ndipoles"]
     P_dev = torch.empty((R, 3, N), dtype=torch.complex128, device=dev)
@@ -348,7 +357,9 @@ def run_gb300(args):
                "time_to_solution_ms": t_e2e * 1e3 / args.steps}
 
     roof = roofline(kstats, info, R, w.name)
-    mv_roof = matvec_roofline(kstats, info, "c64") if kstats else None
+    # complex64 RHS-matvecs per traced step: 2 per BiCGstab iteration of every RHS
+    mv_roof = matvec_roofline(kstats, info, "c64", rhs_matvecs=len(per_tr) * sum(2 * r["iters"] for r in res)) \
+        if kstats else None
     launches = int(sum(s["launches"] for s in kstats.values()) / args.steps) * args.steps if kstats else 0
 
     cpu = None
@@ -426,18 +437,39 @@ def roofline(kstats, info, R, workload_name=None):
             "rhs_per_launch": units_per_launch, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
 
 
-def matvec_roofline(kstats, info, suffix="c64"):
+def matvec_roofline(kstats, info, suffix="c64", rhs_matvecs=None):
     """The whole FFT-convolution matvec (its five passes together) against
-    HBM: algorithmic bytes of all launches of the passes / their total time."""
+    HBM: algorithmic bytes of all launches of the passes / their total time.
+
+    Bytes per launch are pass_bytes (compact vectors of N sites, padded
+    intermediates, index maps, Green octant).  The profiler's units count
+    the RHS a launch was given; inside a solve RHS that have converged are
+    skipped, so rhs_matvecs (the RHS-matvecs actually done, from the solver's
+    iteration counts) replaces them there.  `survey_model` also gives the
+    lattice-wide model (81 R + 6) M s per matvec of R RHS (M = lattice
+    sites, P read and written on the whole lattice)."""
     hbm, src = load_peaks()
     kinds = [k for k in kstats if k.endswith(suffix) and pass_bytes(k, info, 1) is not None]
     if len(kinds) != 5:
         return None
     ms = sum(kstats[k]["ms"] for k in kinds)
-    b = sum(pass_bytes(k, info, kstats[k]["units"] / kstats[k]["launches"]) * kstats[k]["launches"] for k in kinds)
+    b = 0.0
+    for k in kinds:
+        fixed = pass_bytes(k, info, 0)
+        per_rhs = pass_bytes(k, info, 1) - fixed
+        units = kstats[k]["units"] if rhs_matvecs is None else rhs_matvecs
+        b += per_rhs * units + fixed * kstats[k]["launches"]
     ach = b / (ms / 1e3) / 1e9
+    s = 8 if suffix == "c64" else 16
+    M = (info["Lx"] // 2) * (info["Ly"] // 2) * (info["Lz"] // 2)
+    zk = [k for k in kinds if k.startswith("z_conv")][0]
+    units = kstats[zk]["units"] if rhs_matvecs is None else rhs_matvecs
+    sb = (81 * units + 6 * kstats[zk]["launches"]) * M * s
+    sach = sb / (ms / 1e3) / 1e9
     return {"passes": sorted(kinds), "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-            "frac": ach / hbm, "ms": ms, "algorithmic_bytes": b, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
+            "frac": ach / hbm, "ms": ms, "algorithmic_bytes": b, "rhs_matvecs": units,
+            "survey_model": {"bytes": sb, "achieved": sach, "frac": sach / hbm},
+            "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
 
 
 # ----------------------------------------------------------- CPU baseline ----
@@ -572,12 +604,64 @@ def run_grad(args):
     ctx.close()
 
 
+def _fft_length(n):
+    """Smallest supported padded length >= 2n (the library's rule)."""
+    for L in (16, 32, 48, 64, 96, 128, 192, 256, 384, 512):
+        if L >= 2 * n:
+            return L
+    return None
+
+
+def run_nearfield(args):
+    """Time dda_nearfield (E_inc and E_sca on the extended box) after a solve."""
+    import torch
+    import paper_1202_3424_gb300 as dda
+    w = workload(args.workload)
+    ctx = dda.Context(0)
+    ctx.set_target(w.grid)
+    ctx.set_materials(w.m)
+    ctx.prepare_size_parameter(w.x, dda.Precision.FP32_REFINED)
+    R = args.rhs or w.nrhs
+    k, e = np.resize(w.khat, (R, 3)), np.resize(w.ehat, (R, 3))
+    res, P, _ = ctx.solve(dda.Precision.FP32_REFINED, k, e, tol=1e-5)
+    ext = [args.ext] * 6
+    dims, off = ctx.nearfield_dims(ext)
+    prec = 2 if args.precision == "fp32" else 0
+    out = {}
+    for _ in range(max(1, args.warmup)):
+        ctx.nearfield(prec, k, e, P, ext)
+    torch.cuda.synchronize()
+    L = dda.load_library()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Ei, Es, _, _ = ctx.nearfield(prec, k, e, P, ext)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    L.dda_profile_enable(ctx.handle, 1)
+    ctx.nearfield(prec, k, e, P, ext)
+    kst = read_profile(dda, ctx)
+    L.dda_profile_enable(ctx.handle, 0)
+    box = {"Lx": _fft_length(dims[0]), "Ly": _fft_length(dims[1]), "Lz": _fft_length(dims[2]),
+           "ndipoles": dims[0] * dims[1] * dims[2]}
+    suffix = "c64" if prec == 2 else "c128"
+    ne = dims[0] * dims[1] * dims[2]
+    print(json.dumps({"mode": "nearfield", "workload": w.name, "rhs": R, "precision": args.precision, "ext": ext,
+                      "box": dims, "offset": off, "padded_grid": [box["Lx"], box["Ly"], box["Lz"]],
+                      "ms_per_call": ms, "field_points_per_s": R * ne / (ms / 1e3),
+                      "kernels": {k_: {"launches": v["launches"], "ms": v["ms"]} for k_, v in kst.items()},
+                      "convolution_roofline": matvec_roofline(kst, box, suffix),
+                      "max_abs_E": float(np.abs(Ei + Es).max())}), flush=True)
+    ctx.close()
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.mode == "matvec":
         run_matvec_only(a)
+    elif a.mode == "nearfield":
+        run_nearfield(a)
     elif a.mode == "grad":
         run_grad(a)
     else:

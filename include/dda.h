@@ -183,6 +183,28 @@ dda_status dda_matvec_device_noalloc(dda_ctx* ctx, dda_precision precision, int 
 /* Incident field E_inc,j = e exp(i k khat.r_j) at every site, [R][3][N] complex (host). */
 dda_status dda_incident_field(dda_ctx* ctx, int R, const double* khat, const double* e, double* E_out);
 
+/* Near field ("Near-Field Calculations", NRFLD = 1; Flatau & Draine 2012):
+ * E_inc and E_sca at every lattice point of the target's computational volume
+ * extended by the fractions ext[0..5] = (r1, ..., r6): nint(r1 nx) points
+ * are added below x and nint(r2 nx) above, likewise r3, r4 in y and r5, r6
+ * in z (the guide's X1 - r1 Lx <= x <= X2 + r2 Lx, ...).  E_sca,j is the
+ * field of the target's polarization P at point j, without the dipole at j
+ * itself: E_sca,j = -sum_{l != j} A_jl P_l with A_jl the off-diagonal blocks
+ * of the solve's matrix, so an exact solution satisfies
+ * P_j = alpha_j (E_inc,j + E_sca,j) at target points.  Evaluated as the same
+ * zero-padded FFT convolution as the matvec, on the extended box.
+ * dda_nearfield_dims: box extent dims[3] (x, y, z points) and the box index
+ * offset[3] of target point (0, 0, 0); DDA_ERR_SIZE if an extent exceeds the
+ * largest padded length (256 points).  Needs dda_set_target.
+ * dda_nearfield: P host [R][3][N] complex (the solve's P_out layout);
+ * E_inc_out (nullable), E_sca_out host [R][3][Ne] complex, Ne = dims[0]
+ * dims[1] dims[2], box points x fastest; phase origin as in dda_solve.
+ * precision DDA_FP64 (complex128 convolution) or DDA_FP32 /
+ * DDA_FP32_REFINED (complex64 convolution).  Needs dda_prepare.              */
+dda_status dda_nearfield_dims(dda_ctx* ctx, const double* ext, int* dims, int* offset);
+dda_status dda_nearfield(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* e,
+                         const double* P, const double* ext, double* E_inc_out, double* E_sca_out);
+
 /* dQ_abs/dRe(eps_j) and dQ_abs/dIm(eps_j) for every dipole (each dipole's eps
  * treated as independent; forward values from the composition table), by an
  * adjoint solve A nu = W P^* that reuses the matvec because A = A^T.  One RHS.

@@ -25,6 +25,7 @@ __all__ = [
     "dda_create", "dda_destroy", "dda_last_error", "dda_set_stream", "dda_set_target", "dda_set_materials",
     "dda_prepare", "dda_get_info", "dda_solve", "dda_solve_device", "dda_matvec", "dda_matvec_device",
     "dda_incident_field", "dda_grad_qabs", "dda_matvec_device_noalloc", "dda_set_schedule", "dda_get_schedule",
+    "dda_nearfield", "dda_nearfield_dims",
 ]
 
 STATUS = {0: "DDA_OK", 1: "DDA_ERR_ARG", 2: "DDA_ERR_CUDA", 3: "DDA_ERR_OOM", 4: "DDA_ERR_SIZE",
@@ -108,6 +109,8 @@ def load_library(build_if_missing: bool = True):
         "dda_grad_qabs": ([vp, ctypes.c_int, _D, _D, ctypes.POINTER(dda_opts), _D, _D, _D, ctypes.POINTER(dda_result)],
                           ctypes.c_int),
         "dda_set_schedule": ([vp, ctypes.c_int], ctypes.c_int),
+        "dda_nearfield_dims": ([vp, _D, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "dda_nearfield": ([vp, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D, _D], ctypes.c_int),
         "dda_get_schedule": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -279,6 +282,33 @@ def dda_grad_qabs(ctx, precision, khat, e, **opts):
     return gre, gim, P, (res[0].as_dict(), res[1].as_dict())
 
 
+def dda_nearfield_dims(ctx, ext):
+    """(dims (x, y, z), offset (x, y, z)) of the extended near-field box."""
+    e6 = np.ascontiguousarray(np.asarray(ext, dtype=np.float64).reshape(6))
+    d = (ctypes.c_int * 3)()
+    o = (ctypes.c_int * 3)()
+    _check(ctx, load_library().dda_nearfield_dims(ctx, _dptr(e6), d, o))
+    return tuple(d), tuple(o)
+
+
+def dda_nearfield(ctx, precision, khat, e, P, ext, want_inc=True):
+    """E_inc, E_sca on the extended box, each (R, 3, Ne) complex128 (x fastest);
+    P (R, 3, N) complex.  Returns (E_inc or None, E_sca, dims, offset)."""
+    k, ev, R = _rhs(khat, e)
+    dims, off = dda_nearfield_dims(ctx, ext)
+    ne = dims[0] * dims[1] * dims[2]
+    PP = np.ascontiguousarray(P, dtype=np.complex128)
+    if PP.ndim == 2:
+        PP = PP[None]
+    e6 = np.ascontiguousarray(np.asarray(ext, dtype=np.float64).reshape(6))
+    Es = np.empty((R, 3, ne), dtype=np.complex128)
+    Ei = np.empty((R, 3, ne), dtype=np.complex128) if want_inc else None
+    _check(ctx, load_library().dda_nearfield(ctx, int(precision), R, _dptr(k), _dptr(ev), _dptr(PP.view(np.float64)),
+                                             _dptr(e6), _dptr(Ei.view(np.float64)) if want_inc else None,
+                                             _dptr(Es.view(np.float64))))
+    return Ei, Es, dims, off
+
+
 def dda_set_schedule(ctx, zpass: int):
     """Force the complex64 z-pass schedule (0 or 1) or restore autotuning (-1)."""
     _check(ctx, load_library().dda_set_schedule(ctx, int(zpass)))
@@ -338,6 +368,12 @@ class Context:
 
     def incident_field(self, khat, e):
         return dda_incident_field(self.handle, khat, e)
+
+    def nearfield(self, precision, khat, e, P, ext, want_inc=True):
+        return dda_nearfield(self.handle, precision, khat, e, P, ext, want_inc)
+
+    def nearfield_dims(self, ext):
+        return dda_nearfield_dims(self.handle, ext)
 
     def set_schedule(self, zpass):
         dda_set_schedule(self.handle, zpass)

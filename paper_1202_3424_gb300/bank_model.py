@@ -1,16 +1,19 @@
-"""Shared-memory bank model of the pencil-FFT exchanges; picks the row swizzle.
+"""Shared-memory bank model of the pencil-FFT exchanges; picks the row padding.
 
 The FFT kernels stage TP pencils side by side in shared memory, element
 (pos, t) of the plane at row pos, column t.  Between two radix stages every
 thread stores its values at the positions the next stage's threads load
 (csrc/fft.cuh, ``fft_stages``).  With TP * 8 bytes < 128 several rows share
 one 128-byte bank window, and the stride patterns of those stores and loads
-can put a whole half-warp on the same banks.  Storing row pos at
-``pos ^ ((pos >> S) & M)`` moves such rows apart; this module counts the
-wavefronts of every exchange instruction of every warp for each candidate
-(S, M) and picks the cheapest.  Its choices are tabulated in
-``exchange_swizzle`` (csrc/fft.cuh); ``python -m paper_1202_3424_gb300.bank_model``
-prints the table and ``--check`` compares it with the header.
+can put a whole half-warp on the same banks.  Inserting one padding row after
+every 2^S rows (row pos stored at ``pos + (pos >> S)``) moves such rows
+apart; since every exchange position is a per-thread base plus a multiple of
+the radix stride, the shift folds into the constant offsets and costs almost
+no address arithmetic.  This module counts the wavefronts of every exchange
+instruction of every warp for each candidate S and picks the cheapest.  Its
+choices are tabulated in ``exchange_pad_shift`` (csrc/fft.cuh);
+``python -m paper_1202_3424_gb300.bank_model`` prints the table and
+``--check`` compares it with the header.
 
 Bank model: 32 banks of 4 bytes; a warp's 8-byte access is served in two
 half-warp phases, each taking as many wavefronts as the largest number of
@@ -38,10 +41,10 @@ def read_plans(path: str = FFT_HEADER):
 
 
 def read_table(path: str = FFT_HEADER):
-    """{(L, NT, TP): (S, M)} from exchange_swizzle in fft.cuh."""
+    """{(L, NT, TP): S} from exchange_pad_shift in fft.cuh."""
     text = open(path).read()
-    pat = r"if \(L == (\d+) && NT == (\d+) && TP == (\d+)\) return \{(\d+), (\d+)\};"
-    return {(int(a), int(b), int(c)): (int(d), int(e)) for a, b, c, d, e in re.findall(pat, text)}
+    pat = r"if \(L == (\d+) && NT == (\d+) && TP == (\d+)\) return (\d+);"
+    return {(int(a), int(b), int(c)): int(d) for a, b, c, d in re.findall(pat, text)}
 
 
 def stage_radix(rad, direction, s):
@@ -92,12 +95,15 @@ def wavefronts(byte_addrs, esize=8):
     return total
 
 
-def cost(L, NT, rad, TP, swz=(0, 0), groups=1):
+def padded_row(pos, shift):
+    return pos + (pos >> shift) if shift else pos
+
+
+def cost(L, NT, rad, TP, shift=0, groups=1):
     """(wavefronts, ideal) over both transform directions for a block of
     groups*TP*NT threads (thread -> column t = tid % TP, pencil thread
     u = (tid // TP) % NT); each group has its own plane."""
-    s, m = swz
-    row = (lambda p: p ^ ((p >> s) & m)) if m else (lambda p: p)
+    rows = padded_row(L - 1, shift) + 1
     nthreads = groups * TP * NT
     act = ideal = 0
     for direction in (-1, +1):
@@ -107,54 +113,54 @@ def cost(L, NT, rad, TP, swz=(0, 0), groups=1):
                 for lane in range(32):
                     tid = w * 32 + lane
                     t, u, g = tid % TP, (tid // TP) % NT, tid // (TP * NT)
-                    addrs.append(((g * L + row(pos[u])) * TP + t) * 8)
+                    addrs.append(((g * rows + padded_row(pos[u], shift)) * TP + t) * 8)
                 act += wavefronts(addrs)
                 ideal += 2
     return act, ideal
 
 
-def candidates():
-    yield (0, 0)
-    for s in range(1, 8):
-        for m in (1, 3, 7):
-            if m < (1 << s):
-                yield (s, m)
-
-
-# A swizzle adds address arithmetic to every exchange access.  Measured on
-# GB300, removing a quarter of the wavefronts (plain cost 1.25 -> 1.0 on the
-# 8-wide planes of the 512-point y and z passes) made those kernels ~10 %
-# slower, while removing 40 % (1.75 -> 1.0 on the 4-wide register z plane)
-# made the z pass 8 % faster; so a swizzle is kept only if it cuts the cost
-# by this factor.
+# Padding is kept only where it cuts the wavefronts by at least this factor.
+# Measured on GB300: padding the 8-wide planes (cost 1.25 -> 1.0) made the
+# register-capped schedule-0 z pass spill and run 10-13 % slower on the
+# 128- and 512-point grids, while padding the 4-wide register-schedule planes
+# (1.75 -> 1.0) made that z pass faster; an XOR swizzle showed the same split.
 MIN_GAIN = 1.4
 
 
-def best_swizzle(L, NT, rad, TP, groups=1):
-    """Cheapest (S, M) if it pays (MIN_GAIN), else the identity; ties go to
-    the smaller (M, S)."""
-    scored = []
-    for s, m in candidates():
-        a, i = cost(L, NT, rad, TP, (s, m), groups)
-        scored.append((a / i, m, s))
-    scored.sort()
-    r, m, s = scored[0]
-    plain = [x for x in scored if x[1] == 0][0][0]
-    if plain < MIN_GAIN * r:
-        return (0, 0), plain, plain
-    return (s, m), r, plain
+def best_shift(L, NT, rad, TP, groups=1):
+    """(S, cost, plain cost): the cheapest padding shift if it pays
+    (MIN_GAIN), else 0; ties go to the larger S (less padding)."""
+    plain = cost(L, NT, rad, TP, 0, groups)
+    plain = plain[0] / plain[1]
+    best = (plain, 0)
+    for s in range(6, 0, -1):
+        a, i = cost(L, NT, rad, TP, s, groups)
+        if a / i < best[0] - 1e-12:
+            best = (a / i, s)
+    r, s = best
+    if s and plain < MIN_GAIN * r:
+        return 0, plain, plain
+    return s, r, plain
 
 
 # Tile widths, as the kernels define them (csrc/matvec_impl.cuh) for
 # complex64 elements.
 def tp_strided(NT):
-    return max(8, min(32, 256 // NT))
+    tp = max(8, min(32, 256 // NT))
+    return max(tp, 16)
 
 
-def tp_zgroups(L, NT):
+def tp_zgroups(L, NT, table=None):
+    """Schedule-0 z tile: halved until spectra (with the header's padding),
+    Green tile and twiddles fit 216 KB."""
+    table = read_table() if table is None else table
     tp = 256 // NT if NT >= 32 else 128 // NT
     tp = max(4, min(32, tp))
-    while tp > 1 and (3 * L + 6 * (L // 2 + 1)) * tp * 8 > 200 * 1024:
+    while tp > 1:
+        sh = table.get((L, NT, tp), 0)
+        rows = L + ((L - 1) >> sh) if sh else L
+        if ((3 * rows + 6 * (L // 2 + 1)) * tp + L) * 8 <= 216 * 1024:
+            break
         tp //= 2
     return tp
 
@@ -164,36 +170,36 @@ def tp_zregs(NT):
 
 
 def table(plans=None):
-    """{(L, NT, TP): ((S, M), swizzled cost, plain cost)} for every exchange plane
-    of the three kernel families (strided passes, z groups, z registers)."""
+    """{(L, NT, TP): (S, padded cost, plain cost)} for every exchange plane of
+    the three kernel families (strided passes, z groups, z registers)."""
     plans = plans or read_plans()
     out = {}
     for L, (NT, rad) in plans["Plan"].items():
         TP = tp_strided(NT)
-        out[(L, NT, TP)] = best_swizzle(L, NT, rad, TP)
+        out[(L, NT, TP)] = best_shift(L, NT, rad, TP)
         if L // NT <= 8:
             TP = tp_zregs(NT)
-            out[(L, NT, TP)] = best_swizzle(L, NT, rad, TP)
+            out[(L, NT, TP)] = best_shift(L, NT, rad, TP, groups=3)
     for L, (NT, rad) in plans["ZPlan"].items():
         TP = tp_zgroups(L, NT)
-        out[(L, NT, TP)] = best_swizzle(L, NT, rad, TP, groups=3)
+        out[(L, NT, TP)] = best_shift(L, NT, rad, TP, groups=3)
     return out
 
 
 def main(argv):
     t = table()
     if "--check" in argv:
-        want = {k: v[0] for k, v in t.items() if v[0] != (0, 0)}
+        want = {k: v[0] for k, v in t.items() if v[0] != 0}
         have = read_table()
         if want != have:
-            print("exchange_swizzle in fft.cuh differs from the model:")
+            print("exchange_pad_shift in fft.cuh differs from the model:")
             print("  model:", sorted(want.items()))
             print("  header:", sorted(have.items()))
             return 1
-        print("exchange_swizzle matches the model (%d swizzled planes)" % len(want))
+        print("exchange_pad_shift matches the model (%d padded planes)" % len(want))
         return 0
-    for (L, NT, TP), ((s, m), r, plain) in sorted(t.items()):
-        print(f"L={L:4d} NT={NT:3d} TP={TP:3d}  swizzle (S={s}, M={m})  cost {r:.3f} of ideal (plain {plain:.3f})")
+    for (L, NT, TP), (s, r, plain) in sorted(t.items()):
+        print(f"L={L:4d} NT={NT:3d} TP={TP:3d}  pad shift S={s}  cost {r:.3f} of ideal (plain {plain:.3f})")
     return 0
 
 

@@ -1225,6 +1225,200 @@ dda_status dda_incident_field(dda_ctx* ctx, int R, const double* khat, const dou
     return DDA_OK;
 }
 
+}  // extern "C"
+
+// ---- near field ------------------------------------------------------------
+namespace {
+
+// Extended volume of the near-field calculation: nint(r n) lattice points
+// added on each side of an axis of n points (the guide's NRFLD extension
+// fractions r1..r6 of the computational volume).
+dda_status nf_box(dda_ctx* ctx, const double* ext, int dims[3], int off[3]) {
+    if (!ext) return ctx->fail(DDA_ERR_ARG, "NULL extension fractions");
+    const int n[3] = {ctx->g.ox, ctx->g.oy, ctx->g.oz};
+    for (int a = 0; a < 3; ++a) {
+        const double lo = ext[2 * a], hi = ext[2 * a + 1];
+        if (!std::isfinite(lo) || !std::isfinite(hi) || lo < 0.0 || hi < 0.0 || lo > 64.0 || hi > 64.0)
+            return ctx->fail(DDA_ERR_ARG, "extension fractions must be finite, in [0, 64]");
+        const int add_lo = (int)std::floor(lo * n[a] + 0.5), add_hi = (int)std::floor(hi * n[a] + 0.5);
+        off[a] = add_lo;
+        dims[a] = n[a] + add_lo + add_hi;
+        if (!pick_fft_length(dims[a]))
+            return ctx->fail(DDA_ERR_SIZE, "extended volume has %d points along axis %d: above the largest padded length",
+                             dims[a], a);
+    }
+    return DDA_OK;
+}
+
+struct NearWork {
+    std::vector<DevMem> mem;
+    ~NearWork() {
+        for (auto& m : mem) free_mem(m);
+    }
+    void* get(size_t bytes, cudaError_t& e) {
+        mem.emplace_back();
+        e = cudaMalloc(&mem.back().p, bytes < 256 ? 256 : bytes);
+        return mem.back().p;
+    }
+};
+
+template <typename T>
+dda_status nearfield_run(dda_ctx* ctx, int R, const double* P_host, const int dims[3], const int off[3],
+                         const std::vector<double>& khat, const std::vector<cd>& e, double* Einc_out, double* Esca_out) {
+    using C = cx<T>;
+    cudaStream_t st = ctx->stream;
+    // geometry of the extended box: every box point is an output site
+    Geom g;
+    g.ox = dims[0];
+    g.oy = dims[1];
+    g.oz = dims[2];
+    g.Lx = pick_fft_length(dims[0]);
+    g.Ly = pick_fft_length(dims[1]);
+    g.Lz = pick_fft_length(dims[2]);
+    g.nx = g.Lx / 2;
+    g.ny = g.Ly / 2;
+    g.nz = g.Lz / 2;
+    const int64_t Ne = (int64_t)dims[0] * dims[1] * dims[2], M = g.M(), N = ctx->g.N;
+    if (M > (int64_t)INT32_MAX) return ctx->fail(DDA_ERR_SIZE, "extended volume too large");
+    g.N = Ne;
+    std::vector<int> site_of(M, -1), lat_of(Ne);
+    for (int iz = 0; iz < dims[2]; ++iz)
+        for (int iy = 0; iy < dims[1]; ++iy)
+            for (int ix = 0; ix < dims[0]; ++ix) {
+                const int64_t b = ((int64_t)iz * dims[1] + iy) * dims[0] + ix;
+                const int64_t li = ((int64_t)iz * g.ny + iy) * g.nx + ix;
+                site_of[li] = (int)b;
+                lat_of[b] = (int)li;
+            }
+    // target site -> box point (target lattice indices from the context's map)
+    std::vector<int> tlat(N), box_of(N);
+    CU(cudaMemcpy(tlat.data(), ctx->tg.lat_of, N * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int64_t j = 0; j < N; ++j) {
+        const int l = tlat[j];
+        const int ix = l % ctx->g.nx, iy = (l / ctx->g.nx) % ctx->g.ny, iz = l / (ctx->g.nx * ctx->g.ny);
+        box_of[j] = (int)(((int64_t)(iz + off[2]) * dims[1] + (iy + off[1])) * dims[0] + (ix + off[0]));
+    }
+    NearWork w;
+    cudaError_t ce = cudaSuccess;
+    auto alloc = [&](size_t bytes) { return ce == cudaSuccess ? w.get(bytes, ce) : nullptr; };
+    int* d_site = (int*)alloc(M * sizeof(int));
+    int* d_lat = (int*)alloc(Ne * sizeof(int));
+    int* d_box = (int*)alloc(N * sizeof(int));
+    uint8_t* d_comp = (uint8_t*)alloc(Ne);
+    const int64_t oct = 6 * g.oct_per_comp();
+    double2* gh64 = (double2*)alloc(oct * sizeof(double2));
+    double2* tw64[3];
+    void* twT[3];
+    for (int a = 0; a < 3; ++a) {
+        const int L = a == 0 ? g.Lx : (a == 1 ? g.Ly : g.Lz);
+        tw64[a] = (double2*)alloc(L * sizeof(double2));
+        twT[a] = sizeof(T) == 8 ? (void*)tw64[a] : alloc(L * sizeof(C));
+    }
+    C* ghT = sizeof(T) == 8 ? (C*)gh64 : (C*)alloc(oct * sizeof(C));
+    const int rc = std::max(1, std::min(R, 8));  // RHS per pass over the box
+    C* Pbox = (C*)alloc((size_t)rc * 3 * Ne * sizeof(C));
+    C* Ybox = (C*)alloc((size_t)rc * 3 * Ne * sizeof(C));
+    C* u1 = (C*)alloc((size_t)rc * 3 * g.u1_per_comp() * sizeof(C));
+    C* u2 = (C*)alloc((size_t)rc * 3 * g.u2_per_comp() * sizeof(C));
+    C* beta0 = (C*)alloc((size_t)rc * 2 * sizeof(C));
+    double2* d_P = (double2*)alloc((size_t)rc * 3 * N * sizeof(double2));
+    double2* d_E = (double2*)alloc((size_t)rc * 3 * Ne * sizeof(double2));
+    double* d_k = (double*)alloc((size_t)R * 3 * sizeof(double));
+    double2* d_e = (double2*)alloc((size_t)R * 3 * sizeof(double2));
+    if (ce != cudaSuccess) return ctx->cuda_fail(ce, "near-field workspace");
+    CU(cudaMemcpy(d_site, site_of.data(), M * sizeof(int), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(d_lat, lat_of.data(), Ne * sizeof(int), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(d_box, box_of.data(), N * sizeof(int), cudaMemcpyHostToDevice));
+    CU(cudaMemset(d_comp, 1, Ne));
+    CU(cudaMemset(beta0, 0, (size_t)rc * 2 * sizeof(C)));
+    std::vector<double2> e2(3 * (size_t)R);
+    for (size_t i = 0; i < e2.size(); ++i) e2[i] = make_double2(e[i].real(), e[i].imag());
+    CU(cudaMemcpy(d_k, khat.data(), khat.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(d_e, e2.data(), e2.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    for (int a = 0; a < 3; ++a) {
+        const int L = a == 0 ? g.Lx : (a == 1 ? g.Ly : g.Lz);
+        std::vector<double2> t64;
+        std::vector<float2> t32;
+        host_twiddles(L, t64, t32);
+        CU(cudaMemcpy(tw64[a], t64.data(), L * sizeof(double2), cudaMemcpyHostToDevice));
+        if (sizeof(T) != 8) CU(cudaMemcpy(twT[a], t32.data(), L * sizeof(float2), cudaMemcpyHostToDevice));
+    }
+    {
+        DevMem scratch;
+        CU(cudaMalloc(&scratch.p, (size_t)6 * g.Lx * g.Ly * g.Lz * sizeof(double2)));
+        Twiddles<double> t{tw64[0], tw64[1], tw64[2]};
+        cudaError_t e1 = launch_green_fft(g, ctx->kd, (double2*)scratch.p, gh64, t, st);
+        if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(st);
+        cudaFree(scratch.p);
+        if (e1 != cudaSuccess) return ctx->cuda_fail(e1, "near-field Green tensor FFT");
+    }
+    if (sizeof(T) != 8) CU(launch_convert_c128_to_c64(gh64, (float2*)ghT, oct, st));
+    DevTarget tg;
+    tg.site_of = d_site;
+    tg.lat_of = d_lat;
+    tg.comp_of = d_comp;
+    Twiddles<T> tw{(const C*)twT[0], (const C*)twT[1], (const C*)twT[2]};
+    PadWork<T> pw{u1, u2};
+    // phase origin: the target's own centre, in box index space
+    const double cx = off[0] + 0.5 * (ctx->g.ox - 1), cy = off[1] + 0.5 * (ctx->g.oy - 1),
+                 cz = off[2] + 0.5 * (ctx->g.oz - 1);
+    for (int r0 = 0; r0 < R; r0 += rc) {
+        const int rn = std::min(rc, R - r0);
+        const size_t nb = (size_t)rn * 3 * Ne;
+        CU(cudaMemcpyAsync(d_P, P_host + (size_t)r0 * 6 * N, (size_t)rn * 3 * N * sizeof(double2),
+                           cudaMemcpyHostToDevice, st));
+        CU(cudaMemsetAsync(Pbox, 0, nb * sizeof(C), st));
+        CU(launch_scatter_sites<C>(rn, N, Ne, d_box, d_P, Pbox, st));
+        // y = sum_{l != j} A_jl P_l: the matvec on the box with 1/alpha = 0
+        CU(launch_matvec<T>(g, rn, Pbox, Ybox, pw, tg, beta0, 2, ghT, tw, nullptr, st));
+        CU(launch_negate_c128<C>((int64_t)nb, Ybox, d_E, st));
+        CU(cudaMemcpyAsync(Esca_out + (size_t)r0 * 6 * Ne, d_E, nb * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        if (Einc_out) {
+            CU(launch_einc_at(rn, Ne, d_lat, g.nx, g.ny, cx, cy, cz, ctx->kd, d_k + 3 * r0, d_e + 3 * r0, d_E, st));
+            CU(cudaMemcpyAsync(Einc_out + (size_t)r0 * 6 * Ne, d_E, nb * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        }
+        CU(sync_collect(ctx));
+    }
+    return DDA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dda_status dda_nearfield_dims(dda_ctx* ctx, const double* ext, int* dims, int* offset) {
+    if (!ctx) return DDA_ERR_ARG;
+    if (!dims || !offset) return ctx->fail(DDA_ERR_ARG, "NULL output");
+    if (!ctx->has_target) return ctx->fail(DDA_ERR_ARG, "set a target first");
+    int d[3], o[3];
+    dda_status s = nf_box(ctx, ext, d, o);
+    if (s != DDA_OK) return s;
+    for (int a = 0; a < 3; ++a) {
+        dims[a] = d[a];
+        offset[a] = o[a];
+    }
+    return DDA_OK;
+}
+
+dda_status dda_nearfield(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* e,
+                         const double* P, const double* ext, double* E_inc_out, double* E_sca_out) {
+    if (!ctx) return DDA_ERR_ARG;
+    ProfScope prof_scope(ctx);
+    if (!P || !E_sca_out) return ctx->fail(DDA_ERR_ARG, "NULL P or E_sca");
+    dda_status rs;
+    if (!ctx->prepared) return ctx->fail(DDA_ERR_ARG, "dda_prepare has not been called for the current target");
+    if (precision != DDA_FP64 && precision != DDA_FP32 && precision != DDA_FP32_REFINED)
+        return ctx->fail(DDA_ERR_ARG, "near field: precision must be DDA_FP64 or a complex64 mode");
+    cudaSetDevice(ctx->device);
+    std::vector<double> k;
+    std::vector<cd> ev;
+    if ((rs = check_rhs(ctx, R, khat, e, k, ev)) != DDA_OK) return rs;
+    int dims[3], off[3];
+    if ((rs = nf_box(ctx, ext, dims, off)) != DDA_OK) return rs;
+    if (precision == DDA_FP64) return nearfield_run<double>(ctx, R, P, dims, off, k, ev, E_inc_out, E_sca_out);
+    return nearfield_run<float>(ctx, R, P, dims, off, k, ev, E_inc_out, E_sca_out);
+}
+
 dda_status dda_grad_qabs(dda_ctx* ctx, dda_precision precision, const double* khat, const double* e,
                          const dda_opts* opts, double* dq_dre_eps, double* dq_dim_eps, double* P_out,
                          dda_result* res) {

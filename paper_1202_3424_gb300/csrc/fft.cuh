@@ -71,30 +71,39 @@ template <class PL, int DIR> __host__ __device__ constexpr int stage_p(int s) {
     return p;
 }
 
-// ---- exchange-plane row swizzle ------------------------------------------
-// Kernels that stage TP pencils side by side in shared memory ([pos][TP]
-// complex64 elements) store row pos at pos ^ ((pos >> S) & M).  With narrow
-// tiles (TP * 8 bytes < 128) several rows share one bank window, and the
-// stride patterns of the stage exchanges put whole half-warps on the same
-// banks; the XOR moves those rows apart, at the price of address arithmetic
-// on every access.  (S, M) per (plan, tile width) is the choice of
+// ---- exchange-plane row padding --------------------------------------------
+// Kernels that stage TP pencils side by side in shared memory ([row][TP]
+// complex64 elements) insert one padding row after every 2^S rows: position
+// pos lives in row pos + (pos >> S).  With narrow tiles (TP * 8 bytes < 128)
+// several rows share one bank window, and the stride patterns of the stage
+// exchanges put whole half-warps on the same banks; the padding moves those
+// rows apart.  Every exchange position is a per-thread base plus a multiple
+// of the stage's radix stride, so the shift folds into constant offsets.
+// S per (plan, tile width) is the choice of
 // paper_1202_3424_gb300/bank_model.py, which counts the shared-memory
-// wavefronts of every exchange instruction of every warp and keeps a
-// swizzle only where it removes enough of them to pay; M = 0 leaves rows in
-// place.
-struct RowSwizzle {
-    int s, m;
-};
-template <int L, int NT, int TP> __host__ __device__ constexpr RowSwizzle exchange_swizzle() {
-    if (L == 256 && NT == 32 && TP == 4) return {2, 3};
-    if (L == 512 && NT == 64 && TP == 4) return {3, 3};
-    return {0, 0};
+// wavefronts of every exchange instruction of every warp; S = 0: no padding.
+__host__ __device__ constexpr int exchange_pad_shift(int L, int NT, int TP) {
+    if (L == 256 && NT == 32 && TP == 4) return 3;
+    if (L == 512 && NT == 64 && TP == 4) return 3;
+    return 0;
 }
-// (tabulated for 8-byte elements; planes of wider elements stay unswizzled)
-template <int L, int NT, int TP, int ES> __device__ __forceinline__ int swizzle_row(int pos) {
-    constexpr RowSwizzle z = ES == 8 ? exchange_swizzle<L, NT, TP>() : RowSwizzle{0, 0};
-    if constexpr (z.m == 0) return pos;
-    else return pos ^ ((pos >> z.s) & z.m);
+// Rows of one padded plane of 8-byte elements.
+__host__ __device__ constexpr int exchange_rows8(int L, int NT, int TP) {
+    return exchange_pad_shift(L, NT, TP) ? L + ((L - 1) >> exchange_pad_shift(L, NT, TP)) : L;
+}
+// (tabulated for 8-byte elements; planes of wider elements are not padded)
+template <int L, int NT, int TP, int ES> __host__ __device__ constexpr int exchange_shift() {
+    return ES == 8 ? exchange_pad_shift(L, NT, TP) : 0;
+}
+// Rows of one padded plane.
+template <int L, int NT, int TP, int ES> __host__ __device__ constexpr int exchange_rows() {
+    constexpr int s = exchange_shift<L, NT, TP, ES>();
+    return s ? L + ((L - 1) >> s) : L;
+}
+template <int L, int NT, int TP, int ES> __device__ __forceinline__ int exchange_row(int pos) {
+    constexpr int s = exchange_shift<L, NT, TP, ES>();
+    if constexpr (s == 0) return pos;
+    else return pos + (pos >> s);
 }
 
 // ---- small DFTs, sign convention exp(SGN * 2 pi i j k / R) ----------------

@@ -446,12 +446,59 @@ cudaError_t launch_c128_to_c64v(int64_t n, const double2* s_, float2* d, cudaStr
 }
 cudaError_t launch_einc(int R, int64_t N, const int* lat_of, const Geom& g, double kd, const double* khat,
                         const double2* e, double2* E, cudaStream_t s) {
+    return launch_einc_at(R, N, lat_of, g.nx, g.ny, 0.5 * (g.ox - 1), 0.5 * (g.oy - 1), 0.5 * (g.oz - 1), kd, khat,
+                          e, E, s);
+}
+cudaError_t launch_einc_at(int R, int64_t N, const int* lat_of, int nx, int ny, double cx, double cy, double cz,
+                           double kd, const double* khat, const double2* e, double2* E, cudaStream_t s) {
     PROF_BEGIN(s);
-    k_einc<<<dim3(reduce_blocks(N), R), kThreads, 0, s>>>(N, lat_of, g.nx, g.ny, 0.5 * (g.ox - 1), 0.5 * (g.oy - 1),
-                                                           0.5 * (g.oz - 1), kd, khat, e, E);
+    k_einc<<<dim3(reduce_blocks(N), R), kThreads, 0, s>>>(N, lat_of, nx, ny, cx, cy, cz, kd, khat, e, E);
     PROF_END(KK_EINC, R, s);
     return cudaGetLastError();
 }
+
+// ---- near field ----------------------------------------------------------------
+// Pbox[r][c][box_of[j]] = P[r][c][j] for the N target sites (Pbox zeroed first).
+template <typename C>
+__global__ void __launch_bounds__(kThreads)
+    k_scatter_sites(int64_t N, int64_t Ne, const int* __restrict__ box_of, const double2* __restrict__ P,
+                    C* __restrict__ Pbox) {
+    const int r = blockIdx.y;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = box_of[j];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            Pbox[((int64_t)r * 3 + c) * Ne + b] = ccast<C>(P[((int64_t)r * 3 + c) * N + j]);
+    }
+}
+// out = -(double) y  (E_sca = -sum_l A P_l)
+template <typename C>
+__global__ void __launch_bounds__(kThreads) k_negate_c128(int64_t n, const C* __restrict__ y, double2* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = ccast<double2>(y[i]);
+        out[i] = make_double2(-v.x, -v.y);
+    }
+}
+template <typename C>
+cudaError_t launch_scatter_sites(int R, int64_t N, int64_t Ne, const int* box_of, const double2* P, C* Pbox,
+                                 cudaStream_t s) {
+    PROF_BEGIN(s);
+    k_scatter_sites<C><<<dim3(reduce_blocks(N), R), kThreads, 0, s>>>(N, Ne, box_of, P, Pbox);
+    PROF_END(KK_OTHER, R, s);
+    return cudaGetLastError();
+}
+template <typename C> cudaError_t launch_negate_c128(int64_t n, const C* y, double2* out, cudaStream_t s) {
+    PROF_BEGIN(s);
+    k_negate_c128<C><<<reduce_blocks(n), kThreads, 0, s>>>(n, y, out);
+    PROF_END(KK_OTHER, 1, s);
+    return cudaGetLastError();
+}
+template cudaError_t launch_scatter_sites<float2>(int, int64_t, int64_t, const int*, const double2*, float2*,
+                                                  cudaStream_t);
+template cudaError_t launch_scatter_sites<double2>(int, int64_t, int64_t, const int*, const double2*, double2*,
+                                                   cudaStream_t);
+template cudaError_t launch_negate_c128<float2>(int64_t, const float2*, double2*, cudaStream_t);
+template cudaError_t launch_negate_c128<double2>(int64_t, const double2*, double2*, cudaStream_t);
 cudaError_t launch_qsums(int R, int64_t N, const double2* E, const double2* P, const uint8_t* comp_of, const double* w,
                          int w_stride, double2* sums, double2* part, unsigned* cnt, cudaStream_t s) {
     PROF_BEGIN(s);

@@ -55,6 +55,14 @@ cudaError_t launch_c128_to_c64v(int64_t n, const double2* s_, float2* d, cudaStr
 struct Geom;
 cudaError_t launch_einc(int R, int64_t N, const int* lat_of, const Geom& g, double kd, const double* khat,
                         const double2* e, double2* E, cudaStream_t s);
+// E_inc at points lat_of[j] of an nx*ny-row lattice, phase origin at (cx, cy, cz) in its index space.
+cudaError_t launch_einc_at(int R, int64_t N, const int* lat_of, int nx, int ny, double cx, double cy, double cz,
+                           double kd, const double* khat, const double2* e, double2* E, cudaStream_t s);
+// Near field: target sites into the extended-box vector; E_sca = -y in complex128.
+template <typename C>
+cudaError_t launch_scatter_sites(int R, int64_t N, int64_t Ne, const int* box_of, const double2* P, C* Pbox,
+                                 cudaStream_t s);
+template <typename C> cudaError_t launch_negate_c128(int64_t n, const C* y, double2* out, cudaStream_t s);
 cudaError_t launch_qsums(int R, int64_t N, const double2* E, const double2* P, const uint8_t* comp_of, const double* w,
                          int w_stride, double2* sums, double2* part, unsigned* cnt, cudaStream_t s);
 cudaError_t launch_adjoint_rhs(int64_t N, const double2* P, const uint8_t* comp_of, const double* w, double2* b,

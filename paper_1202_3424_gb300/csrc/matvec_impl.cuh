@@ -79,8 +79,13 @@ template <int L, typename T> __host__ __device__ constexpr int tp_z() {
     constexpr int nt = ZPlan<L>::NT;
     int tp = nt >= 32 ? 256 / nt : 128 / nt;
     tp = tp > 32 ? 32 : (tp < 4 ? 4 : tp);
-    // spectra [3][L] and Green tensor [6][L/2+1] per column within 200 KB
-    while (tp > 1 && ((size_t)3 * L + (size_t)6 * (L / 2 + 1)) * tp * sizeof(cx<T>) > 200 * 1024) tp /= 2;
+    // spectra [3][padded rows] and Green tensor [6][L/2+1] per column, and
+    // the twiddle table [L], within 216 KB
+    while (tp > 1) {
+        const size_t rows = sizeof(cx<T>) == 8 ? exchange_rows8(L, nt, tp) : L;
+        if (((size_t)3 * rows + (size_t)6 * (L / 2 + 1)) * tp + L <= 216 * 1024 / sizeof(cx<T>)) break;
+        tp /= 2;
+    }
     return tp;
 }
 // (complex128 z passes are FP64-ALU-bound and keep their registers)
@@ -95,8 +100,11 @@ template <int L, typename T> __host__ __device__ constexpr int zconv_min_blocks(
 template <int L, typename T> __host__ __device__ constexpr int sp_z() {
     return tp_z<L, T>();
 }
+template <int L, typename T> __host__ __device__ constexpr int zconv_rows() {
+    return exchange_rows<L, ZPlan<L>::NT, sp_z<L, T>(), sizeof(cx<T>)>();
+}
 template <int L, typename T> __host__ __device__ constexpr size_t zconv_smem() {
-    return ((size_t)3 * L + (size_t)6 * (L / 2 + 1)) * sp_z<L, T>() * sizeof(cx<T>);
+    return (((size_t)3 * zconv_rows<L, T>() + (size_t)6 * (L / 2 + 1)) * sp_z<L, T>() + L) * sizeof(cx<T>);
 }
 
 // ---- x-forward: gather + row FFT ---------------------------------------------
@@ -316,8 +324,8 @@ __global__ void __launch_bounds__(tp_s<L, sizeof(cx<T>)>() * Plan<L>::NT)
     C* bt = buf + t;
     C v[PL::E];
     auto first = [&](int pos) { return valid ? s[pos * pt_stride] : czero<C>(); };
-    auto ld = [&](int pos) { return bt[swizzle_row<L, PL::NT, TP, sizeof(C)>(pos) * TP]; };
-    auto st = [&](int pos, C val) { bt[swizzle_row<L, PL::NT, TP, sizeof(C)>(pos) * TP] = val; };
+    auto ld = [&](int pos) { return bt[exchange_row<L, PL::NT, TP, sizeof(C)>(pos) * TP]; };
+    auto st = [&](int pos, C val) { bt[exchange_row<L, PL::NT, TP, sizeof(C)>(pos) * TP] = val; };
     pencil_fft<C, PL, DIR, MODE == 0>(v, u, tw, first, ld, st);
     for_each_out<PL, DIR, MODE == 1>(u, [&](int idx, int pos) {
         if (valid) d[pos * pt_stride] = v[idx];
@@ -343,8 +351,10 @@ __global__ void __launch_bounds__(3 * tp_z<LZ, T>() * ZPlan<LZ>::NT, zconv_min_b
     constexpr int TP = tp_z<LZ, T>(), SP = sp_z<LZ, T>(), NT = PL::NT, NZ = LZ / 2, HZ = LZ / 2 + 1;
     static_assert((TP * NT) % 32 == 0, "component groups must be whole warps");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);   // spectra [3][LZ][SP]
-    C* gs = buf + 3 * LZ * SP;                 // Green tensor [6][HZ][SP]
+    C* buf = reinterpret_cast<C*>(smem_raw);   // spectra [3][ROWS][SP]
+    constexpr int ROWS = zconv_rows<LZ, T>();  // padded rows of a spectra plane
+    C* gs = buf + 3 * ROWS * SP;               // Green tensor [6][HZ][SP]
+    C* tws = gs + 6 * HZ * SP;                 // twiddle table [LZ]
     const int ky = blockIdx.y;
     const int r0 = blockIdx.z * RB;
     const int hx = Lx / 2 + 1, hy = Ly / 2 + 1;
@@ -366,6 +376,7 @@ __global__ void __launch_bounds__(3 * tp_z<LZ, T>() * ZPlan<LZ>::NT, zconv_min_b
             }
             gs[(cc * HZ + kz) * SP + tt] = g;
         }
+        for (int e = threadIdx.x; e < LZ; e += blockDim.x) tws[e] = tw[e];
     }
     const int t = threadIdx.x % TP;
     const int rest = threadIdx.x / TP;
@@ -382,9 +393,9 @@ __global__ void __launch_bounds__(3 * tp_z<LZ, T>() * ZPlan<LZ>::NT, zconv_min_b
     const C* g0 = gs + i0 * HZ * SP + t;
     const C* g1 = gs + i1 * HZ * SP + t;
     const C* g2 = gs + i2 * HZ * SP + t;
-    C* sb = buf + c * (LZ * SP) + t;
+    C* sb = buf + c * (ROWS * SP) + t;
     const C* pb = buf + t;
-    auto row = [](int pos) { return swizzle_row<LZ, NT, SP, sizeof(C)>(pos); };
+    auto row = [](int pos) { return exchange_row<LZ, NT, SP, sizeof(C)>(pos); };
     auto ld = [&](int pos) { return sb[row(pos) * SP]; };
     auto st = [&](int pos, C val) { sb[row(pos) * SP] = val; };
 #pragma unroll 1
@@ -396,7 +407,7 @@ __global__ void __launch_bounds__(3 * tp_z<LZ, T>() * ZPlan<LZ>::NT, zconv_min_b
         C v[PL::E];
         auto first = [&](int pos) { return valid ? bc[pos * plane] : czero<C>(); };
         __syncthreads();  // Green tile staged / previous RHS done with the spectra
-        pencil_fft<C, PL, -1, true>(v, u, tw, first, ld, st);
+        pencil_fft<C, PL, -1, true>(v, u, tws, first, ld, st);
         __syncthreads();
         for_each_out<PL, -1, false>(u, [&](int idx, int pos) { sb[row(pos) * SP] = v[idx]; });
         __syncthreads();
@@ -410,10 +421,10 @@ __global__ void __launch_bounds__(3 * tp_z<LZ, T>() * ZPlan<LZ>::NT, zconv_min_b
                 if (z2) a2 = cscale(a2, T(-1));
             }
             const int kr = row(kz);
-            const C pa = pb[kr * SP], pbv = pb[(LZ + kr) * SP], pc = pb[(2 * LZ + kr) * SP];
+            const C pa = pb[kr * SP], pbv = pb[(ROWS + kr) * SP], pc = pb[(2 * ROWS + kr) * SP];
             v[idx] = cadd(cadd(cmul(a0, pa), cmul(a1, pbv)), cmul(a2, pc));
         });
-        pencil_fft_regs<C, PL, +1>(v, u, tw, ld, st);
+        pencil_fft_regs<C, PL, +1>(v, u, tws, ld, st);
         for_each_out<PL, +1, true>(u, [&](int idx, int pos) {
             if (valid) bc[pos * plane] = v[idx];
         });
@@ -440,8 +451,11 @@ template <int L> __host__ __device__ constexpr int zreg_threads() { return tp_zr
 template <int L> __host__ __device__ constexpr int zreg_min_blocks() {
     return 512 / zreg_threads<L>() < 1 ? 1 : 512 / zreg_threads<L>();
 }
+template <int L, typename T> __host__ __device__ constexpr int zreg_rows() {
+    return exchange_rows<L, Plan<L>::NT, tp_zr<L>(), sizeof(cx<T>)>();
+}
 template <int L, typename T> __host__ __device__ constexpr size_t zreg_smem() {
-    return (((size_t)3 * L + (size_t)6 * (L / 2 + 1)) * tp_zr<L>() + L) * sizeof(cx<T>);
+    return (((size_t)3 * zreg_rows<L, T>() + (size_t)6 * (L / 2 + 1)) * tp_zr<L>() + L) * sizeof(cx<T>);
 }
 
 template <typename T, int LZ, int RB>
@@ -453,8 +467,9 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
     constexpr int TP = tp_zr<LZ>(), NT = PL::NT, NZ = LZ / 2, HZ = LZ / 2 + 1, E = PL::E;
     constexpr int R0 = stage_radix<PL, -1>(0), NB0 = E / R0, JN = R0 / 2;  // half-zero first stage
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);  // exchange planes [3][LZ][TP]
-    C* gs = buf + 3 * LZ * TP;                // Green tensor [6][HZ][TP]
+    C* buf = reinterpret_cast<C*>(smem_raw);  // exchange planes [3][ROWS][TP]
+    constexpr int ROWS = zreg_rows<LZ, T>();  // padded rows of an exchange plane
+    C* gs = buf + 3 * ROWS * TP;              // Green tensor [6][HZ][TP]
     C* tws = gs + 6 * HZ * TP;                // twiddle table [LZ]
     const int ky = blockIdx.y;
     const int r0 = blockIdx.z * RB;
@@ -466,8 +481,8 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
     const int64_t plane = (int64_t)Ly * Lx;
     C* bt = buf + t;
     const C* gt = gs + t;
-    auto ld = [&](int p, int pos) { return bt[(p * LZ + swizzle_row<LZ, NT, TP, sizeof(C)>(pos)) * TP]; };
-    auto st = [&](int p, int pos, C val) { bt[(p * LZ + swizzle_row<LZ, NT, TP, sizeof(C)>(pos)) * TP] = val; };
+    auto ld = [&](int p, int pos) { return bt[(p * ROWS + exchange_row<LZ, NT, TP, sizeof(C)>(pos)) * TP]; };
+    auto st = [&](int p, int pos, C val) { bt[(p * ROWS + exchange_row<LZ, NT, TP, sizeof(C)>(pos)) * TP] = val; };
     const int rend = min(R, r0 + RB);
     auto next_active = [&](int r) {  // uniform across the block
         while (r < rend && active != nullptr && active[r] == 0) ++r;
@@ -689,7 +704,7 @@ template <typename T> struct LaunchX {
                                     int64_t db, int batches, int per_rhs, const cx<T>* tw, const int* active,
                                     cudaStream_t st, int kind, double units) {
         constexpr int TP = tp_s<L, sizeof(cx<T>)>(), NTH = TP * Plan<L>::NT;
-        const size_t sm = (size_t)L * TP * sizeof(cx<T>);
+        const size_t sm = (size_t)exchange_rows<L, Plan<L>::NT, TP, sizeof(cx<T>)>() * TP * sizeof(cx<T>);
         cudaError_t e = allow_smem(k_strided<T, L, MODE>, sm);
         if (e != cudaSuccess) return e;
         dim3 grid((width + TP - 1) / TP, batches, 1);

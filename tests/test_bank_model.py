@@ -1,4 +1,4 @@
-"""The shared-memory bank model that picks the FFT exchange-plane swizzle."""
+"""The shared-memory bank model that picks the FFT exchange-plane row padding."""
 from paper_1202_3424_gb300 import bank_model as bm
 
 
@@ -27,20 +27,22 @@ def test_exchange_positions_cover_the_pencil_once_per_instruction_set():
         assert sorted(seen) == sorted(list(range(L)) * 2 * n_ex)
 
 
-def test_swizzles_are_permutations():
-    for (L, NT, TP), (s, m) in bm.read_table().items():
-        rows = [p ^ ((p >> s) & m) for p in range(L)]
-        assert sorted(rows) == list(range(L)), (L, NT, TP)
+def test_padded_rows_are_distinct_and_fit_the_plane():
+    for (L, NT, TP), sh in bm.read_table().items():
+        rows = [bm.padded_row(p, sh) for p in range(L)]
+        assert len(set(rows)) == L, (L, NT, TP)
+        # the kernels size a plane as L + ((L - 1) >> S) rows
+        assert max(rows) + 1 == L + ((L - 1) >> sh)
 
 
 def test_header_table_is_the_models_choice():
-    want = {k: v[0] for k, v in bm.table().items() if v[0] != (0, 0)}
+    want = {k: v[0] for k, v in bm.table().items() if v[0] != 0}
     assert bm.read_table() == want
 
 
-def test_swizzle_removes_the_narrow_tile_conflicts():
+def test_padding_removes_the_narrow_tile_conflicts():
     NT, rad = bm.read_plans()["Plan"][512]
     a, i = bm.cost(512, NT, rad, 4)
     assert a / i > 1.5
-    a, i = bm.cost(512, NT, rad, 4, (3, 3))
+    a, i = bm.cost(512, NT, rad, 4, 3)
     assert a == i

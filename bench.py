@@ -161,6 +161,10 @@ def pass_bytes(kind, info, R, ncomp_tables=1):
     u2 = 3 * nz * Ly * Lx * s
     vec = 3 * N * s
     oct_ = 6 * (Lx // 2 + 1) * (Ly // 2 + 1) * (Lz // 2 + 1) * s
+    if kind.startswith("xy_fwd"):             # fused x+y slice pass: P in, U2 out
+        return R * (vec + u2) + 4 * M
+    if kind.startswith("yx_inv"):             # fused y+x slice pass: U2 and X in, Y out
+        return R * (u2 + 2 * vec) + 4 * M + N
     if kind.startswith("x_fwd"):
         return R * (vec + u1) + 4 * M
     if kind.startswith("y_fwd") or kind.startswith("y_inv"):
@@ -178,6 +182,8 @@ def pass_flops(kind, info, R):
     Lx, Ly, Lz = info["Lx"], info["Ly"], info["Lz"]
     nx, ny, nz = Lx // 2, Ly // 2, Lz // 2
     f = lambda L: 5 * L * math.log2(L)  # noqa: E731
+    if kind.startswith("xy_fwd") or kind.startswith("yx_inv"):
+        return R * 3 * (ny * nz * f(Lx) + nz * Lx * f(Ly))
     if kind.startswith("x_fwd") or kind.startswith("x_inv"):
         return R * 3 * ny * nz * f(Lx)
     if kind.startswith("y_fwd") or kind.startswith("y_inv"):
@@ -450,7 +456,7 @@ def matvec_roofline(kstats, info, suffix="c64", rhs_matvecs=None):
     sites, P read and written on the whole lattice)."""
     hbm, src = load_peaks()
     kinds = [k for k in kstats if k.endswith(suffix) and pass_bytes(k, info, 1) is not None]
-    if len(kinds) != 5:
+    if len(kinds) not in (3, 5):   # fused slice passes + z, or the five separate passes
         return None
     ms = sum(kstats[k]["ms"] for k in kinds)
     b = 0.0

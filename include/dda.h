@@ -214,27 +214,39 @@ dda_status dda_grad_qabs(dda_ctx* ctx, dda_precision precision, const double* kh
                          const dda_opts* opts, double* dq_dre_eps, double* dq_dim_eps, double* P_out,
                          dda_result* res);
 
-/* Schedule autotuning for the batched complex64 path.  The z pass (FFT along
- * z, the 3x3 Fourier-space product, inverse FFT) has two schedules on grids
- * whose z transform keeps at most 8 points per thread (Lz = 16, 32, 64, 128,
- * 256 or 512):
- *   0  three component groups per column, spectra exchanged through shared memory;
- *   1  register-resident: one thread holds all three components of its points,
- *      and the loads of the next RHS are issued before the current one is
- *      transformed.
- * Both compute the same product; results agree to rounding.  By default the
- * context times both on its own workspace the first time a complex64 matvec
- * of a given RHS count runs outside a stream capture, and keeps the faster
- * (inside a capture an untimed choice is used until then).  Complex128 and
- * double-float matvecs have schedule 0 only.
- * dda_set_schedule: zpass -1 automatic (the default), 0 or 1 forces that
- *   schedule wherever it exists (1 falls back to 0 elsewhere); clears the
- *   timings.  Any other value: DDA_ERR_ARG.
- * dda_get_schedule: the schedule complex64 matvecs of R RHS use on the current
- *   target, timing the candidates now if needed (this sizes the workspace
- *   for R).  Needs dda_prepare with DDA_FP32_REFINED or DDA_FP32.            */
+/* Schedule autotuning.  Two choices about how a matvec runs are made by
+ * measurement, per arithmetic type and RHS count:
+ *  - the z pass (FFT along z, the 3x3 Fourier-space product, inverse FFT),
+ *    for complex64 on grids whose z transform keeps at most 8 points per
+ *    thread (Lz = 16, 32, 64, 128, 256 or 512):
+ *      0  three component groups per column, spectra exchanged through
+ *         shared memory;
+ *      1  register-resident: one thread holds all three components of its
+ *         points, and the loads of the next RHS are issued before the current
+ *         one is transformed;
+ *  - the fused x+y slice passes: where the half-y spectrum of one z-slice,
+ *    Lx x (Ly/2) points, fits in shared memory (Lx, Ly in 64..192 for
+ *    complex64, 64 or 96 for complex128 and double-float), one block can
+ *    transform a whole slice along x and y, so the x-transformed rows never
+ *    go through HBM (3 kernels per matvec instead of 5).
+ * All choices compute the same product; results agree to rounding.  In
+ * automatic mode the context times every available combination inside whole
+ * matvecs on its own workspace the first time a matvec of a given type and
+ * RHS count runs outside a stream capture, and keeps the fastest (inside a
+ * capture an untimed choice is used until then).
+ * dda_set_schedule: zpass -1 automatic (the default), 0 or 1 forces that z
+ *   schedule wherever it exists (1 falls back to 0 elsewhere).
+ * dda_set_slice_passes: on -1 automatic, 0 always the separate passes (the
+ *   default: measured on GB300 the slice passes are faster only for small
+ *   grids outside a solve), 1 the slice passes wherever they are built.
+ * Both clear the timings; any other value: DDA_ERR_ARG.
+ * dda_get_schedule: the z schedule (and, if slices is not NULL, whether the
+ *   slice passes run) of complex64 matvecs of R RHS on the current target,
+ *   timing the candidates now if needed (this sizes the workspace for R).
+ *   Needs dda_prepare with DDA_FP32_REFINED or DDA_FP32.                      */
 dda_status dda_set_schedule(dda_ctx* ctx, int zpass);
-dda_status dda_get_schedule(dda_ctx* ctx, int R, int* zpass);
+dda_status dda_set_slice_passes(dda_ctx* ctx, int on);
+dda_status dda_get_schedule(dda_ctx* ctx, int R, int* zpass, int* slices);
 
 /* Launch tracing (the guide's TIMEIT timing switch, per kernel kind rather than
  * per run): when on, every hot-path kernel launch is bracketed by CUDA events

@@ -25,7 +25,7 @@ __all__ = [
     "dda_create", "dda_destroy", "dda_last_error", "dda_set_stream", "dda_set_target", "dda_set_materials",
     "dda_prepare", "dda_get_info", "dda_solve", "dda_solve_device", "dda_matvec", "dda_matvec_device",
     "dda_incident_field", "dda_grad_qabs", "dda_matvec_device_noalloc", "dda_set_schedule", "dda_get_schedule",
-    "dda_nearfield", "dda_nearfield_dims",
+    "dda_nearfield", "dda_nearfield_dims", "dda_set_slice_passes",
 ]
 
 STATUS = {0: "DDA_OK", 1: "DDA_ERR_ARG", 2: "DDA_ERR_CUDA", 3: "DDA_ERR_OOM", 4: "DDA_ERR_SIZE",
@@ -109,9 +109,11 @@ def load_library(build_if_missing: bool = True):
         "dda_grad_qabs": ([vp, ctypes.c_int, _D, _D, ctypes.POINTER(dda_opts), _D, _D, _D, ctypes.POINTER(dda_result)],
                           ctypes.c_int),
         "dda_set_schedule": ([vp, ctypes.c_int], ctypes.c_int),
+        "dda_set_slice_passes": ([vp, ctypes.c_int], ctypes.c_int),
         "dda_nearfield_dims": ([vp, _D, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "dda_nearfield": ([vp, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D, _D], ctypes.c_int),
-        "dda_get_schedule": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "dda_get_schedule": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+                             ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -314,11 +316,18 @@ def dda_set_schedule(ctx, zpass: int):
     _check(ctx, load_library().dda_set_schedule(ctx, int(zpass)))
 
 
-def dda_get_schedule(ctx, R: int) -> int:
-    """The z-pass schedule complex64 matvecs of R RHS use (timed now if needed)."""
+def dda_set_slice_passes(ctx, on: int):
+    """Fused x+y slice passes: -1 timed, 0 never (default), 1 wherever built."""
+    _check(ctx, load_library().dda_set_slice_passes(ctx, int(on)))
+
+
+def dda_get_schedule(ctx, R: int, with_slices: bool = False):
+    """The z-pass schedule complex64 matvecs of R RHS use (timed now if
+    needed); with_slices=True returns (zpass, slice passes used)."""
     out = ctypes.c_int(-1)
-    _check(ctx, load_library().dda_get_schedule(ctx, int(R), ctypes.byref(out)))
-    return out.value
+    sl = ctypes.c_int(-1)
+    _check(ctx, load_library().dda_get_schedule(ctx, int(R), ctypes.byref(out), ctypes.byref(sl)))
+    return (out.value, sl.value) if with_slices else out.value
 
 
 class Context:
@@ -378,8 +387,11 @@ class Context:
     def set_schedule(self, zpass):
         dda_set_schedule(self.handle, zpass)
 
-    def get_schedule(self, R):
-        return dda_get_schedule(self.handle, R)
+    def set_slice_passes(self, on):
+        dda_set_slice_passes(self.handle, on)
+
+    def get_schedule(self, R, with_slices=False):
+        return dda_get_schedule(self.handle, R, with_slices)
 
     def grad_qabs(self, precision, khat, e, **opts):
         return dda_grad_qabs(self.handle, precision, khat, e, **opts)

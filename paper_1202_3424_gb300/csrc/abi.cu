@@ -79,8 +79,14 @@ struct dda_ctx {
     GraphEntry graph;
     // z-pass schedule per (element bytes, RHS count), timed on first use;
     // force_z >= 0 overrides (dda_set_schedule)
-    std::map<std::pair<int, int>, int> zsched;
+    std::map<std::pair<int, int>, std::pair<int, int>> zsched;  // -> (z variant, slice passes)
     int force_z = -1;
+    // -1 timed, 0 separate passes (default), 1 slice passes where built.
+    // Measured on GB300 the slice passes win only on small grids outside a
+    // solve (64^3 sphere, 2 RHS: 0.163 vs 0.175 ms per matvec) and lose inside
+    // the BiCGstab solve and on the 128-RHS ellipsoid (1 block of 512 threads
+    // per SM), so they are opt-in.
+    int force_slices = 0;
     int* h_count = nullptr;  // pinned
     Profiler prof;
 
@@ -291,31 +297,39 @@ template <typename T> dda_status ensure_pad(dda_ctx* ctx, int R) {
     return ensure(ctx, ctx->pool[PadSlots<T>::b], (size_t)rc * 3 * ctx->g.u2_per_comp() * sizeof(cx<T>));
 }
 
-// z-pass schedule for R right-hand sides.  With more than one schedule for
-// this grid, each is timed once inside a whole plain matvec of R RHS (the
-// passes around the z pass decide what it finds in L2) on the context's
-// workspace plus a transient pair of vectors, and the faster is kept.  The
-// workspace must hold R RHS (ensure_pad<T>).  Inside a stream capture, or
-// with may_time false, an untimed choice is returned: the cached one, else
-// the register-resident schedule for R >= 4.
-template <typename T> dda_status pick_zvar(dda_ctx* ctx, int R, bool may_time, int* out) {
+// Schedule of the matvec passes for R right-hand sides: the z-pass variant
+// (zconv_schedules) and whether the fused x+y slice passes run
+// (slice_passes).  Where more than one combination exists, each is timed
+// once inside a whole plain matvec of R RHS (the passes decide what their
+// neighbours find in L2) on the context's workspace plus a transient pair of
+// vectors, and the fastest is kept.  The workspace must hold R RHS
+// (ensure_pad<T>).  Inside a stream capture, or with may_time false, an
+// untimed choice is returned: the cached one, else the register-resident z
+// schedule for R >= 4 and the slice passes where built.
+template <typename T> dda_status pick_schedule(dda_ctx* ctx, int R, bool may_time, int* zvar, int* slices) {
     const int nv = zconv_schedules<T>(ctx->g);
-    *out = 0;
-    if (nv <= 1) return DDA_OK;
-    if (ctx->force_z >= 0) {
-        *out = std::min(ctx->force_z, nv - 1);
-        return DDA_OK;
-    }
+    const bool sl = slice_passes<T>(ctx->g);
+    std::vector<int> zs, ss;
+    if (nv <= 1) zs = {0};
+    else if (ctx->force_z >= 0) zs = {std::min(ctx->force_z, nv - 1)};
+    else zs = {0, 1};
+    if (!sl) ss = {0};
+    else if (ctx->force_slices >= 0) ss = {ctx->force_slices};
+    else ss = {1, 0};
+    *zvar = zs[0];
+    *slices = ss[0];
+    if (zs.size() * ss.size() == 1) return DDA_OK;
     const std::pair<int, int> key((int)sizeof(cx<T>), R);
     auto it = ctx->zsched.find(key);
     if (it != ctx->zsched.end()) {
-        *out = it->second;
+        *zvar = it->second.first;
+        *slices = it->second.second;
         return DDA_OK;
     }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CU(cudaStreamIsCapturing(ctx->stream, &cs));
     if (!may_time || cs != cudaStreamCaptureStatusNone) {
-        *out = R >= 4 ? 1 : 0;
+        if (zs.size() > 1) *zvar = R >= 4 ? 1 : 0;
         return DDA_OK;
     }
     // zero-filled x, y and 1/alpha table (their values do not change the timing)
@@ -328,8 +342,12 @@ template <typename T> dda_status pick_zvar(dda_ctx* ctx, int R, bool may_time, i
     cx<T>* y = reinterpret_cast<cx<T>*>(base + vec);
     const cx<T>* beta = reinterpret_cast<const cx<T>*>(base + 2 * vec);
     PadWork<T> w{slot<cx<T>>(ctx, PadSlots<T>::a), slot<cx<T>>(ctx, PadSlots<T>::b)};
-    auto run = [&](int v) {
-        w.zvar = v;
+    std::vector<std::pair<int, int>> combos;
+    for (int zv : zs)
+        for (int sv : ss) combos.emplace_back(zv, sv);
+    auto run = [&](size_t i) {
+        w.zvar = combos[i].first;
+        w.slices = combos[i].second;
         return launch_matvec<T>(ctx->g, R, x, y, w, ctx->tg, beta, BS, ghat_of<T>(ctx), tw_of<T>(ctx), nullptr,
                                 ctx->stream);
     };
@@ -338,33 +356,34 @@ template <typename T> dda_status pick_zvar(dda_ctx* ctx, int R, bool may_time, i
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t ce = cudaEventCreate(&e0);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
-    // one warm-up matvec each, then rounds that alternate the schedules (so a
-    // clock ramp or a neighbour's burst does not favour one); keep each
-    // schedule's best round
+    // one warm-up matvec each, then rounds that alternate the combinations
+    // (so a clock ramp or a neighbour's burst does not favour one); keep
+    // each one's best round
     constexpr int kRounds = 3, kReps = 2;
-    std::vector<float> best(nv, 0.f);
-    for (int v = 0; v < nv && ce == cudaSuccess; ++v) ce = run(v);
+    std::vector<float> best(combos.size(), 0.f);
+    for (size_t i = 0; i < combos.size() && ce == cudaSuccess; ++i) ce = run(i);
     for (int round = 0; round < kRounds && ce == cudaSuccess; ++round) {
-        for (int v = 0; v < nv && ce == cudaSuccess; ++v) {
+        for (size_t i = 0; i < combos.size() && ce == cudaSuccess; ++i) {
             ce = cudaEventRecord(e0, ctx->stream);
-            for (int i = 0; i < kReps && ce == cudaSuccess; ++i) ce = run(v);
+            for (int k = 0; k < kReps && ce == cudaSuccess; ++k) ce = run(i);
             if (ce == cudaSuccess) ce = cudaEventRecord(e1, ctx->stream);
             if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
             float ms = 0.f;
             if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
-            if (ce == cudaSuccess && (round == 0 || ms < best[v])) best[v] = ms;
+            if (ce == cudaSuccess && (round == 0 || ms < best[i])) best[i] = ms;
         }
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     ctx->prof.on = was_on;
     free_mem(ctx->pool[S_TUNE]);
-    if (ce != cudaSuccess) return ctx->cuda_fail(ce, "z-pass schedule timing");
-    int pick = 0;
-    for (int v = 1; v < nv; ++v)
-        if (best[v] < best[pick]) pick = v;
-    ctx->zsched[key] = pick;
-    *out = pick;
+    if (ce != cudaSuccess) return ctx->cuda_fail(ce, "matvec schedule timing");
+    size_t pick = 0;
+    for (size_t i = 1; i < combos.size(); ++i)
+        if (best[i] < best[pick]) pick = i;
+    ctx->zsched[key] = combos[pick];
+    *zvar = combos[pick].first;
+    *slices = combos[pick].second;
     return DDA_OK;
 }
 
@@ -378,7 +397,7 @@ dda_status run_matvec(dda_ctx* ctx, int R, const cx<T>* x, cx<T>* y, const int* 
     dda_status zs;
     for (int r0 = 0; r0 < R; r0 += rc) {
         const int rn = std::min(rc, R - r0);
-        if ((zs = pick_zvar<T>(ctx, rn, true, &w.zvar)) != DDA_OK) return zs;
+        if ((zs = pick_schedule<T>(ctx, rn, true, &w.zvar, &w.slices)) != DDA_OK) return zs;
         CU(launch_matvec<T>(ctx->g, rn, x + (int64_t)r0 * n, y + (int64_t)r0 * n, w, ctx->tg,
                             beta_of<T>(ctx) + (int64_t)r0 * BS, BS, ghat_of<T>(ctx), tw_of<T>(ctx),
                             active ? active + r0 : nullptr, ctx->stream));
@@ -437,7 +456,7 @@ dda_status run_matvec_fused(dda_ctx* ctx, int R, int mode, cx<T>* x, cx<T>* y, c
     for (int r0 = 0; r0 < R; r0 += rc) {
         const int rn = std::min(rc, R - r0);
         const int64_t o = (int64_t)r0 * n;
-        if ((zs = pick_zvar<T>(ctx, rn, true, &w.zvar)) != DDA_OK) return zs;
+        if ((zs = pick_schedule<T>(ctx, rn, true, &w.zvar, &w.slices)) != DDA_OK) return zs;
         FusedKrylov<T> fk;
         fk.mode = mode;
         fk.r = in.r + o;
@@ -874,7 +893,7 @@ dda_status matvec_noalloc(dda_ctx* ctx, int R, const std::vector<double>& k, con
     PadWork<T> w{reinterpret_cast<C*>(base + beta_bytes), reinterpret_cast<C*>(base + beta_bytes + u1_bytes)};
     CU(cudaMemcpyAsync(d_beta, beta.data(), beta.size() * sizeof(C), cudaMemcpyHostToDevice, ctx->stream));
     dda_status zs;
-    if ((zs = pick_zvar<T>(ctx, R, false, &w.zvar)) != DDA_OK) return zs;  // no timing on the fixed scratch
+    if ((zs = pick_schedule<T>(ctx, R, false, &w.zvar, &w.slices)) != DDA_OK) return zs;  // no timing here
     CU(launch_matvec<T>(ctx->g, R, static_cast<const C*>(x_dev), static_cast<C*>(y_dev), w, ctx->tg, d_beta, BS,
                         ghat_of<T>(ctx), tw_of<T>(ctx), nullptr, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
@@ -1359,6 +1378,7 @@ dda_status nearfield_run(dda_ctx* ctx, int R, const double* P_host, const int di
     tg.comp_of = d_comp;
     Twiddles<T> tw{(const C*)twT[0], (const C*)twT[1], (const C*)twT[2]};
     PadWork<T> pw{u1, u2};
+    pw.slices = ctx->force_slices != 0;
     // phase origin: the target's own centre, in box index space
     const double cx = off[0] + 0.5 * (ctx->g.ox - 1), cy = off[1] + 0.5 * (ctx->g.oy - 1),
                  cz = off[2] + 0.5 * (ctx->g.oz - 1);
@@ -1481,10 +1501,26 @@ dda_status dda_set_schedule(dda_ctx* ctx, int zpass) {
     if (zpass < -1 || zpass > 1) return ctx->fail(DDA_ERR_ARG, "z-pass schedule must be -1, 0 or 1 (got %d)", zpass);
     ctx->force_z = zpass;
     ctx->zsched.clear();
+    if (ctx->graph.exec) {
+        cudaGraphExecDestroy(ctx->graph.exec);
+        ctx->graph.exec = nullptr;
+    }
     return DDA_OK;
 }
 
-dda_status dda_get_schedule(dda_ctx* ctx, int R, int* zpass) {
+dda_status dda_set_slice_passes(dda_ctx* ctx, int on) {
+    if (!ctx) return DDA_ERR_ARG;
+    if (on < -1 || on > 1) return ctx->fail(DDA_ERR_ARG, "slice passes: -1, 0 or 1 (got %d)", on);
+    ctx->force_slices = on;
+    ctx->zsched.clear();
+    if (ctx->graph.exec) {
+        cudaGraphExecDestroy(ctx->graph.exec);
+        ctx->graph.exec = nullptr;
+    }
+    return DDA_OK;
+}
+
+dda_status dda_get_schedule(dda_ctx* ctx, int R, int* zpass, int* slices) {
     if (!ctx || !zpass) return DDA_ERR_ARG;
     if (R <= 0) return ctx->fail(DDA_ERR_ARG, "R must be > 0");
     if (!ctx->prepared || !ctx->has32)
@@ -1493,7 +1529,10 @@ dda_status dda_get_schedule(dda_ctx* ctx, int R, int* zpass) {
     cudaSetDevice(ctx->device);
     dda_status s;
     if ((s = ensure_pad<float>(ctx, R)) != DDA_OK) return s;
-    return pick_zvar<float>(ctx, matvec_chunk<float>(ctx, R), true, zpass);
+    int sl = 0;
+    s = pick_schedule<float>(ctx, matvec_chunk<float>(ctx, R), true, zpass, &sl);
+    if (slices) *slices = sl;
+    return s;
 }
 
 dda_status dda_profile_enable(dda_ctx* ctx, int on) {

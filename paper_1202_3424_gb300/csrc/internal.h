@@ -49,9 +49,10 @@ template <typename T> struct Twiddles {
 
 // Workspace for the padded passes of one matvec of R right-hand sides.
 template <typename T> struct PadWork {
-    cx<T>* u1 = nullptr;  // [R][3][nz][ny][Lx]
+    cx<T>* u1 = nullptr;  // [R][3][nz][ny][Lx] (unused when the slice passes run)
     cx<T>* u2 = nullptr;  // [R][3][nz][Ly][Lx]
     int zvar = 0;         // z-pass schedule, see zconv_schedules
+    int slices = 1;       // fused x+y slice passes where built (see slice_passes)
 };
 
 int pick_fft_length(int n);  // smallest supported length >= 2n, or 0
@@ -84,6 +85,18 @@ int xinv_blocks_per_rhs(const Geom& g);
 // points per thread.  Both compute the same product; the context times them
 // per RHS count and keeps the faster (dda_set_schedule can force one).
 template <typename T> int zconv_schedules(const Geom& g);
+
+// Fused x+y passes over whole z-slices (slice_impl.cuh): built for this
+// grid and element type?  Then the matvec runs xy-fwd, z, yx-inv instead of
+// the five separate passes, and needs no U1 workspace.
+template <typename T> bool slice_passes(const Geom& g);
+template <typename T>
+cudaError_t launch_slice_fwd(const Geom& g, int R, cx<T>* x, cx<T>* u2, const int* site_of, const Twiddles<T>& tw,
+                             const int* active, const FusedKrylov<T>& fk, cudaStream_t st);
+template <typename T>
+cudaError_t launch_slice_inv(const Geom& g, int R, const cx<T>* u2, cx<T>* y, const cx<T>* x, const DevTarget& tg,
+                             const cx<T>* beta, int beta_stride, const Twiddles<T>& tw, int* active,
+                             const FusedKrylov<T>& fk, cudaStream_t st);
 
 // The z pass alone, in place on u2 (used to time the schedules).
 template <typename T>

@@ -789,6 +789,11 @@ cudaError_t launch_matvec_fused(const Geom& g, int R, cx<T>* x, cx<T>* y, const 
     auto invx = [&]() -> cudaError_t {
         DDA_DISPATCH_L(g.Lx, LX::template inv, g, R, w.u1, y, x, tg, beta, beta_stride, tw.x, active, fk, st);
     };
+    if (w.slices && slice_passes<T>(g)) {
+        if ((e = launch_slice_fwd<T>(g, R, x, w.u2, tg.site_of, tw, active, fk, st)) != cudaSuccess) return e;
+        if ((e = zc()) != cudaSuccess) return e;
+        return launch_slice_inv<T>(g, R, w.u2, y, x, tg, beta, beta_stride, tw, active, fk, st);
+    }
     if ((e = fwdx()) != cudaSuccess) return e;
     if ((e = ys(0, w.u1, w.u2, (int64_t)g.ny * g.Lx, (int64_t)g.Ly * g.Lx)) != cudaSuccess) return e;
     if ((e = zc()) != cudaSuccess) return e;

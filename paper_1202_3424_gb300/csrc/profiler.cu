@@ -22,7 +22,8 @@ const char* kernel_kind_name(int kind) {
         "x_fwd_c64", "y_fwd_c64", "z_conv_c64", "y_inv_c64", "x_inv_c64",
         "x_fwd_c128", "y_fwd_c128", "z_conv_c128", "y_inv_c128", "x_inv_c128",
         "x_fwd_df", "y_fwd_df", "z_conv_df", "y_inv_df", "x_inv_df",
-        "bicgstab_c64", "bicgstab_c128", "refine_c128", "incident_field", "q_sums", "green_fft", "other"};
+        "bicgstab_c64", "bicgstab_c128", "refine_c128", "incident_field", "q_sums", "green_fft", "other",
+        "xy_fwd_c64", "yx_inv_c64", "xy_fwd_c128", "yx_inv_c128", "xy_fwd_df", "yx_inv_df"};
     return (kind >= 0 && kind < KK_COUNT) ? names[kind] : "?";
 }
 

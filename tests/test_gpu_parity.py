@@ -61,6 +61,8 @@ MATVEC_CASES = [
     ("ellipsoid_ragged_13x9x6", lambda: ellipsoid_grid(13, 9, 6, 13, 9, 6), [2.0 + 1.0j], 1.5),
     ("single_dipole", lambda: np.ones((1, 1, 1), np.uint8), [1.5 + 0.1j], 0.3),
     ("line_of_dipoles_1x1x17", lambda: np.ones((17, 1, 1), np.uint8), [1.5 + 0.1j], 0.8),
+    # 64x64 in x and y: the fused x+y slice passes run
+    ("plate_25x25x3_slices", lambda: block_bernoulli_grid(25, 25, 3, seed=8), [1.4 + 0.2j, 1.9 + 0.05j], 2.2),
 ]
 
 
@@ -131,18 +133,20 @@ def test_matvec_long_z_columns_many_rhs(lib, zpass):
 
 
 def test_autotuned_schedule_reproduces_forced_one(lib):
-    """The autotuner picks one of the two schedules; the matvec it runs is
-    bit-identical to forcing that schedule."""
+    """The autotuner picks a z schedule and a slice-pass setting; the matvec
+    it runs is bit-identical to forcing that choice."""
     w = workload("ellipsoid96x64x32")
     ctx = _ctx(lib, w.grid, w.m, w.x, lib.Precision.FP32_REFINED)
     R = 12
     ctx.set_schedule(-1)
-    pick = ctx.get_schedule(R)
-    assert pick in (0, 1)
+    ctx.set_slice_passes(-1)
+    zpick, spick = ctx.get_schedule(R, with_slices=True)
+    assert zpick in (0, 1) and spick in (0, 1)
     X = random_complex((R, 3, ctx.info()["ndipoles"]), 4).astype(np.complex64)
     k, e = np.resize(w.khat, (R, 3)), np.resize(w.ehat, (R, 3))
     y_auto = ctx.matvec(2, k, e, X)
-    ctx.set_schedule(pick)
+    ctx.set_schedule(zpick)
+    ctx.set_slice_passes(spick)
     y_forced = ctx.matvec(2, k, e, X)
     assert np.array_equal(y_auto, y_forced)
     with pytest.raises(lib.DdaError):
@@ -175,13 +179,40 @@ def test_matvec_row_samples_full_size(lib, name):
     X = random_complex((R, 3, N), 5)
     rows = np.random.default_rng(9).choice(N, 48, replace=False)
     rows[:2] = [0, N - 1]
-    for prec, tol, zpass in ((0, F64_TOL, -1), (3, F64_TOL, -1), (2, F32_TOL, 0), (2, F32_TOL, 1)):
+    want = []
+    for r in range(R):
+        rr, beta = _site_beta(w.grid, w.m, kd, w.khat[r], w.ehat[r])
+        want.append(pairwise.matvec(rr, kd, beta, X[r].T, rows=rows)[0])
+    for prec, tol, zpass, slices in ((0, F64_TOL, -1, 1), (0, F64_TOL, -1, 0), (3, F64_TOL, -1, 1),
+                                     (2, F32_TOL, 0, 1), (2, F32_TOL, 1, 1), (2, F32_TOL, 1, 0)):
         ctx.set_schedule(zpass)
+        ctx.set_slice_passes(slices)
         Y = ctx.matvec(prec, w.khat[:R], w.ehat[:R], X)
         for r in range(R):
-            rr, beta = _site_beta(w.grid, w.m, kd, w.khat[r], w.ehat[r])
-            want, _ = pairwise.matvec(rr, kd, beta, X[r].T, rows=rows)
-            assert _rel(Y[r].T[rows], want) < tol, (name, prec, zpass, r)
+            assert _rel(Y[r].T[rows], want[r]) < tol, (name, prec, zpass, slices, r)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32_refined"])
+def test_solve_with_and_without_slice_passes(lib, prec):
+    """A 32^3 sphere (64^3 padded, where the fused x+y slice passes run) solved
+    with them and with the five separate passes: both converge to the same
+    efficiencies (the passes differ only in rounding)."""
+    grid = sphere_grid(32)
+    ctx = _ctx(lib, grid, [1.5 + 0.05j], 3.0, lib.Precision.FP32_REFINED)
+    k, e = _rhs_set(3)
+    out = []
+    for slices in (1, 0):
+        ctx.set_slice_passes(slices)
+        res, P, st = ctx.solve(prec, k, e, tol=1e-8 if prec == 0 else 1e-5, maxit=800)
+        assert st == 0, slices
+        out.append((np.array([[r["qext"], r["qabs"], r["qsca"]] for r in res]), P))
+    (qa, Pa), (qb, Pb) = out
+    tol = 1e-7 if prec == 0 else 2e-5
+    assert np.abs(qa - qb).max() < tol * np.abs(qa).max()
+    assert _rel(Pa, Pb) < (1e-6 if prec == 0 else 1e-4)
+    with pytest.raises(lib.DdaError):
+        ctx.set_slice_passes(2)
     ctx.close()
 
 

@@ -396,3 +396,92 @@ def nearfield(grid: np.ndarray, P: np.ndarray, kd: float, khat, ehat, ext):
     r_src, _ = site_positions(grid)
     r_pts = nearfield_points(grid.shape, ext)
     return dims, off, incident_field(r_pts, kd, khat, ehat), scattered_field(r_src, P, r_pts, kd)
+
+
+# ---------------------------------------------------------------- far field --
+def scattering_directions(x: float, eta: float):
+    """The scattering directions and solid-angle weights of the guide's angular
+    averages ("Selection of Scattering Angles", "Angular Averaging").
+
+    theta values equally spaced in s(theta) = theta + theta/(theta + theta0),
+    theta0 = 2 pi/(1 + x), from 0 to pi; their number N_theta = nint of the
+    guide's expression in x and eta (reading: nearest integer, as for N_phi);
+    N_phi(j) = 1 at theta = 0 and pi, else max(3, nint(4 pi sin(theta_j) /
+    (theta_{j+1} - theta_{j-1}))), phi_jk = 2 pi (k - 1)/N_phi(j); weights
+    Omega_jk from the guide's quadrature formulas.
+    Returns (theta (D,), phi (D,), omega (D,)) in radians / steradians.
+    """
+    th0 = 2.0 * math.pi / (1.0 + x)
+    nth_real = 1.0 + (2.0 * (3.0 + x) / eta) * (1.0 + 1.0 / (math.pi + th0)) / (1.0 + th0 / (math.pi + th0) ** 2)
+    nth = int(math.floor(nth_real + 0.5))
+    s = np.arange(nth) * math.pi / (nth - 1) * (1.0 + 1.0 / (math.pi + th0))
+    th = ((s - 1.0 - th0) + np.sqrt((1.0 + th0 - s) ** 2 + 4.0 * th0 * s)) / 2.0
+    th[0], th[-1] = 0.0, math.pi
+    T, F, W = [], [], []
+    for j in range(nth):
+        if j == 0 or j == nth - 1:
+            nphi = 1
+        else:
+            nphi = max(3, int(math.floor(4.0 * math.pi * math.sin(th[j]) / (th[j + 1] - th[j - 1]) + 0.5)))
+        if j == 0:
+            om = 2.0 * math.pi / nphi * (1.0 - (math.cos(th[0]) + math.cos(th[1])) / 2.0)
+        elif j == nth - 1:
+            om = 2.0 * math.pi / nphi * ((math.cos(th[j - 1]) + math.cos(th[j])) / 2.0 + 1.0)
+        else:
+            om = math.pi / nphi * (math.cos(th[j - 1]) - math.cos(th[j + 1]))
+        for k in range(nphi):
+            T.append(th[j])
+            F.append(2.0 * math.pi * k / nphi)
+            W.append(om)
+    return np.array(T), np.array(F), np.array(W)
+
+
+def lab_frame(khat):
+    """Lab Frame of a right-hand side: x_L = khat, y_L = the first polarization
+    basis vector normalize(z x khat) (x if khat is along z), z_L = x_L x y_L
+    (for khat = x this is the guide's frame, with e01 = y_L, e02 = z_L)."""
+    k = np.asarray(khat, dtype=np.float64)
+    k = k / np.linalg.norm(k)
+    y = np.cross([0.0, 0.0, 1.0], k)
+    if np.linalg.norm(y) < 1e-8:
+        y = np.array([1.0, 0.0, 0.0])
+    y = y / np.linalg.norm(y)
+    return k, y, np.cross(k, y)
+
+
+def directions(khat, theta, phi) -> np.ndarray:
+    """Unit vectors n = cos(theta) x_L + sin(theta) cos(phi) y_L + sin(theta) sin(phi) z_L, (D, 3)."""
+    xl, yl, zl = lab_frame(khat)
+    th = np.asarray(theta)[:, None]
+    ph = np.asarray(phi)[:, None]
+    return np.cos(th) * xl + np.sin(th) * np.cos(ph) * yl + np.sin(th) * np.sin(ph) * zl
+
+
+def far_field(r: np.ndarray, P: np.ndarray, kd: float, n: np.ndarray, chunk: int = 64) -> np.ndarray:
+    """Vector scattering amplitude F(n) = k^2 sum_j (I - n n) P_j exp(-i k n.r_j):
+    the scattered field is E_sca -> exp(ikR)/R F(n) at distance R along n, so
+    dC_sca/dOmega = |F|^2 for |E0| = 1 (the same far field as csca_quadrature).
+    Returns (D, 3)."""
+    P = np.asarray(P, dtype=np.complex128)
+    out = np.empty((n.shape[0], 3), dtype=np.complex128)
+    for s in range(0, n.shape[0], chunk):
+        nn = n[s:s + chunk]
+        ph = np.exp(-1j * kd * (nn @ r.T))            # (c, N)
+        S = ph @ P                                      # (c, 3): sum_j P_j e^{-ik n.r_j}
+        out[s:s + chunk] = kd * kd * (S - nn * np.sum(nn * S, axis=1, keepdims=True))
+    return out
+
+
+def angular_averages(r: np.ndarray, P: np.ndarray, kd: float, khat, theta, phi, omega):
+    """C_sca, <cos theta>, <cos^2 theta> and the vector g in Lab Frame
+    components, as the guide's weighted sums over scattering directions
+    ("Angular Averaging": <f> = sum f dC/dOmega Omega / C_sca)."""
+    n = directions(khat, theta, phi)
+    F = far_field(r, P, kd, n)
+    dC = np.sum(np.abs(F) ** 2, axis=1)
+    w = dC * np.asarray(omega)
+    csca = float(np.sum(w))
+    c = np.cos(theta)
+    g = np.array([np.sum(w * c), np.sum(w * np.sin(theta) * np.cos(phi)),
+                  np.sum(w * np.sin(theta) * np.sin(phi))]) / csca
+    return csca, float(g[0]), float(np.sum(w * c * c) / csca), g

@@ -21,6 +21,8 @@ _orig_grad = dda.qabs_gradient
 _orig_sites = dda.site_positions
 _orig_scat = dda.scattered_field
 _orig_box = dda.nearfield_box
+_orig_ff = dda.far_field
+_orig_dirs = dda.scattering_directions
 
 
 def _tensor_sign(rvec, kd):            # (1 - ik rho) instead of (ik rho - 1)
@@ -100,6 +102,20 @@ def _box_floor(shape_zyx, ext):                    # floor instead of nearest fo
     return (nx + lo[0] + hi[0], ny + lo[1] + hi[1], nz + lo[2] + hi[2]), tuple(lo)
 
 
+def _ff_phase(r, P, kd, n, chunk=64):             # exp(+ik n.r): the far field of the wrong hemisphere
+    return _orig_ff(r, P, kd, -n, chunk)
+
+
+def _ff_no_projection(r, P, kd, n, chunk=64):     # I instead of (I - n n)
+    P = np.asarray(P, dtype=np.complex128)
+    return kd * kd * (np.exp(-1j * kd * (n @ r.T)) @ P)
+
+
+def _dirs_uniform_weights(x, eta):                # equal weights on the forward-dense directions
+    t, ph, w = _orig_dirs(x, eta)
+    return t, ph, np.full_like(w, 4 * math.pi / w.size)
+
+
 MUTATIONS = [
     ("interaction_tensor", _tensor_sign, [pins.two_dipole_error]),
     ("interaction_tensor", _tensor_no_far, [pins.two_dipole_error]),
@@ -114,6 +130,9 @@ MUTATIONS = [
     ("scattered_field", _scat_sign, [pins.nearfield_self_consistency_error, pins.nearfield_single_dipole_error]),
     ("scattered_field", _scat_self, [pins.nearfield_self_consistency_error]),
     ("nearfield_box", _box_floor, [pins.nearfield_box_error]),
+    ("far_field", _ff_phase, [pins.dda_asymmetry_vs_mie_error]),
+    ("far_field", _ff_no_projection, [pins.farfield_single_dipole_error]),
+    ("scattering_directions", _dirs_uniform_weights, [pins.farfield_single_dipole_error]),
 ]
 
 

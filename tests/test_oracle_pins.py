@@ -173,6 +173,46 @@ def nearfield_box_error():
     return float(bad)
 
 
+def farfield_single_dipole_error(eta=0.1, kd=0.6):
+    """One dipole p = e (linear, transverse to k = x): the quadrature over the
+    guide's directions gives C_sca = (8 pi/3) k^4 |p|^2, <cos> = 0 and
+    <cos^2> = 2/5 (the sin^2 pattern about y averaged over the sphere), to
+    the quadrature's accuracy."""
+    r = np.zeros((1, 3))
+    p = np.array([[0.0, 1.0 + 0.3j, 0.0]])
+    t, ph, w = dda.scattering_directions(2.0, eta)
+    csca, cos1, cos2, g = dda.angular_averages(r, p, kd, [1, 0, 0], t, ph, w)
+    want = (8 * math.pi / 3) * kd ** 4 * float(np.sum(np.abs(p) ** 2))
+    return max(abs(csca - want) / want, abs(cos1), abs(cos2 - 0.4), float(np.abs(g[1:]).max()))
+
+
+def farfield_vs_pair_sum_error(eta=0.2, kd=0.8, seed=5):
+    """Quadrature C_sca of a random cluster against the exact pair sum."""
+    r = _small_cluster(seed, 30)
+    P = random_complex((len(r), 3), seed)
+    t, ph, w = dda.scattering_directions(3.0, eta)
+    csca = dda.angular_averages(r, P, kd, [0.6, 0.0, 0.8], t, ph, w)[0]
+    exact = dda.csca_pair_sum(r, kd, P)
+    return abs(csca - exact) / exact
+
+
+def dda_asymmetry_vs_mie_error(n=12, x=1.5, m=1.33 + 0.01j):
+    """<cos theta> of a DDA sphere (LATTDR, k along x) against the Mie series."""
+    grid = sphere_grid(n)
+    r, _ = dda.site_positions(grid)
+    N = len(r)
+    aeff = dda.aeff_lattice(N)
+    kd = x / aeff
+    khat, ehat = [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]
+    beta = dda.ldr_inverse_polarizability(np.full(N, m * m), kd, khat, ehat)
+    E = dda.incident_field(r, kd, khat, ehat)
+    P = dda.solve_dense(dda.dense_matrix(r, kd, beta), E)
+    t, ph, w = dda.scattering_directions(x, 0.25)
+    _, g1, _, _ = dda.angular_averages(r, P, kd, khat, t, ph, w)
+    gm = mie.mie_asymmetry(x, m)
+    return abs(g1 - gm) / gm
+
+
 # ------------------------------------------------------------------- tests --
 def test_pseudosphere_counts_match_guide(golden_dir):
     for box, diam, count, *_ in _golden_rows(os.path.join(golden_dir, "pseudosphere_counts.txt")):
@@ -451,3 +491,43 @@ def test_c_scattered_field_matches_numpy():
     a = pairwise.scattered_field(r, P, x, 0.33)
     b = dda.scattered_field(r, P, x, 0.33)
     assert np.abs(a - b).max() < 1e-12 * np.abs(b).max()
+
+
+def test_scattering_directions_match_guide_sample(golden_dir):
+    for x, eta, navg in _golden_rows(os.path.join(golden_dir, "scattering_directions.txt")):
+        t, ph, w = dda.scattering_directions(float(x), float(eta))
+        assert t.size == int(navg)
+
+
+def test_direction_weights_cover_the_sphere():
+    for x, eta in ((0.5, 1.0), (3.093665, 0.5), (8.0, 0.25), (20.0, 1.0)):
+        t, ph, w = dda.scattering_directions(x, eta)
+        assert abs(np.sum(w) - 4 * math.pi) < 1e-12
+        assert t[0] == 0.0 and t[-1] == math.pi and np.all(np.diff(t) >= 0)
+
+
+def test_far_field_of_one_dipole():
+    assert farfield_single_dipole_error() < 2e-3
+
+
+def test_far_field_quadrature_matches_pair_sum():
+    e1, e2 = farfield_vs_pair_sum_error(0.5), farfield_vs_pair_sum_error(0.1)
+    assert e2 < 1e-3 and e2 < e1
+
+
+def test_mie_amplitudes_and_asymmetry_identities():
+    x, m = 5.0, 1.5 + 0.02j
+    qe, _, qs = mie.mie_efficiencies(x, m)
+    S1, S2 = mie.mie_amplitudes(x, m, np.array([0.0]))
+    assert abs(4 / x ** 2 * S1[0].real - qe) < 1e-12 * qe          # optical theorem
+    assert abs(S1[0] - S2[0]) < 1e-12 * abs(S1[0])                   # forward: S1 = S2
+    mu, wt = np.polynomial.legendre.leggauss(400)
+    S1, S2 = mie.mie_amplitudes(x, m, np.arccos(mu))
+    i = np.abs(S1) ** 2 + np.abs(S2) ** 2
+    assert abs(np.sum(wt * i) / x ** 2 - qs) < 1e-10 * qs           # Q_sca from the phase function
+    assert abs(np.sum(wt * i * mu) / np.sum(wt * i) - mie.mie_asymmetry(x, m)) < 1e-10
+    assert abs(mie.mie_asymmetry(0.01, 1.5)) < 1e-3                  # Rayleigh: symmetric
+
+
+def test_dda_asymmetry_approaches_mie():
+    assert dda_asymmetry_vs_mie_error() < 0.05

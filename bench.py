@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--fp64-sequential", action="store_true",
                     help="FP64 leg solves the RHS one at a time (orientation-sweep comparison)")
     ap.add_argument("--ext", type=float, default=0.5, help="nearfield mode: extension fraction on every side")
-    ap.add_argument("--mode", default="solve", choices=["solve", "matvec", "grad", "nearfield"],
+    ap.add_argument("--eta", type=float, default=0.5, help="farfield mode: ETASCA of the scattering directions")
+    ap.add_argument("--mode", default="solve", choices=["solve", "matvec", "grad", "nearfield", "farfield"],
                     help="matvec: only time dda_matvec_device (for profiler captures)")
     ap.add_argument("--rhs", type=int, default=0, help="matvec mode: RHS per product (0 = workload's)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="matvec mode precision")
@@ -660,12 +661,51 @@ def run_nearfield(args):
     ctx.close()
 
 
+def run_farfield(args):
+    """Time dda_angular_averages (far-field amplitudes on the guide's directions + Q_sca, g) after a solve."""
+    import torch
+    import paper_1202_3424_gb300 as dda
+    w = workload(args.workload)
+    ctx = dda.Context(0)
+    ctx.set_target(w.grid)
+    ctx.set_materials(w.m)
+    ctx.prepare_size_parameter(w.x, dda.Precision.FP32_REFINED)
+    R = args.rhs or w.nrhs
+    k, e = np.resize(w.khat, (R, 3)), np.resize(w.ehat, (R, 3))
+    res, P, _ = ctx.solve(dda.Precision.FP32_REFINED, k, e, tol=1e-5)
+    prec = 2 if args.precision == "fp32" else 0
+    for _ in range(max(1, args.warmup)):
+        ctx.angular_averages(prec, k, P, eta=args.eta)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        out, nd = ctx.angular_averages(prec, k, P, eta=args.eta)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    L = dda.load_library()
+    L.dda_profile_enable(ctx.handle, 1)
+    ctx.angular_averages(prec, k, P, eta=args.eta)
+    kst = read_profile(dda, ctx)
+    L.dda_profile_enable(ctx.handle, 0)
+    N = ctx.info()["ndipoles"]
+    kern = kst.get("far_field", {"ms": 0.0, "launches": 0})
+    qsolve = np.array([r["qext"] - r["qabs"] for r in res])
+    print(json.dumps({"mode": "farfield", "workload": w.name, "rhs": R, "precision": args.precision, "eta": args.eta,
+                      "directions": nd, "ms_per_call": ms, "kernel_ms": kern["ms"],
+                      "site_direction_rhs_per_s": N * nd * R / (kern["ms"] / 1e3) if kern["ms"] else None,
+                      "qsca_mean": float(out[:, 0].mean()), "qsca_solve_mean": float(qsolve.mean()),
+                      "g_mean": float(out[:, 1].mean()), "cos2_mean": float(out[:, 2].mean())}), flush=True)
+    ctx.close()
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.mode == "matvec":
         run_matvec_only(a)
+    elif a.mode == "farfield":
+        run_farfield(a)
     elif a.mode == "nearfield":
         run_nearfield(a)
     elif a.mode == "grad":

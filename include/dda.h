@@ -205,6 +205,37 @@ dda_status dda_nearfield_dims(dda_ctx* ctx, const double* ext, int* dims, int* o
 dda_status dda_nearfield(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* e,
                          const double* P, const double* ext, double* E_inc_out, double* E_sca_out);
 
+/* Far field ("Averaging over Scattering Directions", "Scattering by Finite
+ * Targets: The Mueller Matrix").  Directions are given in each RHS's Lab
+ * Frame: x_L = khat, y_L = normalize(z x khat) (x if khat is along z),
+ * z_L = x_L x y_L, n = cos(theta) x_L + sin(theta) cos(phi) y_L +
+ * sin(theta) sin(phi) z_L (for khat = x: the guide's frame with e01 = y).
+ * dda_scattering_directions: the guide's directions for angular averages
+ *   (theta equally spaced in s(theta) = theta + theta/(theta + theta0),
+ *   theta0 = 2 pi/(1 + x), N_theta = nint of its expression in x and eta
+ *   (ETASCA); nint(4 pi sin theta_j / (theta_{j+1} - theta_{j-1})), at least
+ *   3, azimuths per interior theta) with their solid-angle weights omega
+ *   (summing to 4 pi).  *count = number of directions; the arrays are filled
+ *   only if capacity >= *count (call with capacity 0 to size them).  No
+ *   context needed; DDA_ERR_ARG for non-positive x or eta.
+ * dda_farfield: vector amplitudes F(n) = k^2 (I - n n) sum_j P_j
+ *   exp(-i k n.r_j) (lattice units, |E0| = 1: the scattered field is
+ *   exp(ikR)/R F, dC_sca/dOmega = |F|^2), for ndir directions (theta, phi in
+ *   radians) and R RHS: P host [R][3][N] complex, F_out host [R][ndir][3]
+ *   complex.  precision DDA_FP64 or a complex64 mode (complex64 sums, FP64
+ *   block totals).  Needs dda_prepare.
+ * dda_angular_averages: per RHS, out[6] = (Q_sca, <cos theta>, <cos^2 theta>,
+ *   g_x, g_y, g_z): the guide's weighted sums over dda_scattering_directions
+ *   (x = k a_eff of the prepared target, eta = ETASCA), Q_sca = C_sca/(pi
+ *   a_eff^2), g the Lab Frame components of <n>.  *ndir_out (nullable) =
+ *   directions used.                                                        */
+dda_status dda_scattering_directions(double x, double eta, int capacity, double* theta, double* phi, double* omega,
+                                     int* count);
+dda_status dda_farfield(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* P, int ndir,
+                        const double* theta, const double* phi, double* F_out);
+dda_status dda_angular_averages(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* P,
+                                double eta, double* out, int* ndir_out);
+
 /* dQ_abs/dRe(eps_j) and dQ_abs/dIm(eps_j) for every dipole (each dipole's eps
  * treated as independent; forward values from the composition table), by an
  * adjoint solve A nu = W P^* that reuses the matvec because A = A^T.  One RHS.

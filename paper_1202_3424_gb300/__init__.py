@@ -25,7 +25,8 @@ __all__ = [
     "dda_create", "dda_destroy", "dda_last_error", "dda_set_stream", "dda_set_target", "dda_set_materials",
     "dda_prepare", "dda_get_info", "dda_solve", "dda_solve_device", "dda_matvec", "dda_matvec_device",
     "dda_incident_field", "dda_grad_qabs", "dda_matvec_device_noalloc", "dda_set_schedule", "dda_get_schedule",
-    "dda_nearfield", "dda_nearfield_dims", "dda_set_slice_passes",
+    "dda_nearfield", "dda_nearfield_dims", "dda_set_slice_passes", "dda_scattering_directions", "dda_farfield",
+    "dda_angular_averages",
 ]
 
 STATUS = {0: "DDA_OK", 1: "DDA_ERR_ARG", 2: "DDA_ERR_CUDA", 3: "DDA_ERR_OOM", 4: "DDA_ERR_SIZE",
@@ -110,6 +111,11 @@ def load_library(build_if_missing: bool = True):
                           ctypes.c_int),
         "dda_set_schedule": ([vp, ctypes.c_int], ctypes.c_int),
         "dda_set_slice_passes": ([vp, ctypes.c_int], ctypes.c_int),
+        "dda_scattering_directions": ([ctypes.c_double, ctypes.c_double, ctypes.c_int, _D, _D, _D,
+                                       ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "dda_farfield": ([vp, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_int, _D, _D, _D], ctypes.c_int),
+        "dda_angular_averages": ([vp, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_double, _D,
+                                  ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "dda_nearfield_dims": ([vp, _D, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "dda_nearfield": ([vp, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D, _D], ctypes.c_int),
         "dda_get_schedule": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
@@ -311,6 +317,50 @@ def dda_nearfield(ctx, precision, khat, e, P, ext, want_inc=True):
     return Ei, Es, dims, off
 
 
+def dda_scattering_directions(x: float, eta: float):
+    """The guide's scattering directions for angular averages: (theta, phi, omega) arrays."""
+    lib = load_library()
+    n = ctypes.c_int(0)
+    st = lib.dda_scattering_directions(float(x), float(eta), 0, None, None, None, ctypes.byref(n))
+    if st != 0:
+        raise DdaError(st, "bad x or eta")
+    t, p, w = (np.empty(n.value) for _ in range(3))
+    _check(None, lib.dda_scattering_directions(float(x), float(eta), n.value, _dptr(t), _dptr(p), _dptr(w),
+                                               ctypes.byref(n)))
+    return t, p, w
+
+
+def _khat_P(khat, P):
+    k = np.ascontiguousarray(np.atleast_2d(np.asarray(khat, dtype=np.float64)))
+    PP = np.ascontiguousarray(P, dtype=np.complex128)
+    if PP.ndim == 2:
+        PP = PP[None]
+    if k.shape[1] != 3 or PP.shape[0] != k.shape[0] or PP.shape[1] != 3:
+        raise ValueError("khat (R,3) and P (R,3,N) expected")
+    return k, PP, k.shape[0]
+
+
+def dda_farfield(ctx, precision, khat, P, theta, phi):
+    """F (R, ndir, 3) complex128: k^2 (I - n n) sum_j P_j exp(-i k n.r_j) in each RHS's Lab Frame."""
+    k, PP, R = _khat_P(khat, P)
+    t = np.ascontiguousarray(theta, dtype=np.float64).ravel()
+    p = np.ascontiguousarray(phi, dtype=np.float64).ravel()
+    F = np.empty((R, t.size, 3), dtype=np.complex128)
+    _check(ctx, load_library().dda_farfield(ctx, int(precision), R, _dptr(k), _dptr(PP.view(np.float64)), t.size,
+                                            _dptr(t), _dptr(p), _dptr(F.view(np.float64))))
+    return F
+
+
+def dda_angular_averages(ctx, precision, khat, P, eta=0.5):
+    """(R, 6) array of Q_sca, <cos>, <cos^2>, g_x, g_y, g_z, and the number of directions used."""
+    k, PP, R = _khat_P(khat, P)
+    out = np.empty((R, 6))
+    n = ctypes.c_int(0)
+    _check(ctx, load_library().dda_angular_averages(ctx, int(precision), R, _dptr(k), _dptr(PP.view(np.float64)),
+                                                    float(eta), _dptr(out), ctypes.byref(n)))
+    return out, n.value
+
+
 def dda_set_schedule(ctx, zpass: int):
     """Force the complex64 z-pass schedule (0 or 1) or restore autotuning (-1)."""
     _check(ctx, load_library().dda_set_schedule(ctx, int(zpass)))
@@ -383,6 +433,12 @@ class Context:
 
     def nearfield_dims(self, ext):
         return dda_nearfield_dims(self.handle, ext)
+
+    def farfield(self, precision, khat, P, theta, phi):
+        return dda_farfield(self.handle, precision, khat, P, theta, phi)
+
+    def angular_averages(self, precision, khat, P, eta=0.5):
+        return dda_angular_averages(self.handle, precision, khat, P, eta)
 
     def set_schedule(self, zpass):
         dda_set_schedule(self.handle, zpass)

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "dda.h"
+#include "farfield.h"
 #include "internal.h"
 #include "krylov.h"
 #include "profiler.h"
@@ -1437,6 +1438,216 @@ dda_status dda_nearfield(dda_ctx* ctx, dda_precision precision, int R, const dou
     if ((rs = nf_box(ctx, ext, dims, off)) != DDA_OK) return rs;
     if (precision == DDA_FP64) return nearfield_run<double>(ctx, R, P, dims, off, k, ev, E_inc_out, E_sca_out);
     return nearfield_run<float>(ctx, R, P, dims, off, k, ev, E_inc_out, E_sca_out);
+}
+
+}  // extern "C"
+
+// ---- far field ---------------------------------------------------------------
+namespace {
+
+// The guide's scattering directions for angular averages ("Selection of
+// Scattering Angles"): theta equally spaced in s(theta) = theta + theta /
+// (theta + theta0), theta0 = 2 pi / (1 + x), N_theta the nearest integer to
+// its expression in x and eta; nint(4 pi sin(theta_j) / (theta_{j+1} -
+// theta_{j-1})) (at least 3) azimuths at each interior theta, one at 0 and
+// pi; solid-angle weights from its quadrature ("Angular Averaging").
+void scat_dirs(double x, double eta, std::vector<double>& th_out, std::vector<double>& ph_out,
+               std::vector<double>& om_out) {
+    const double th0 = 2.0 * kPi / (1.0 + x);
+    const double ntr = 1.0 + (2.0 * (3.0 + x) / eta) * (1.0 + 1.0 / (kPi + th0)) / (1.0 + th0 / ((kPi + th0) * (kPi + th0)));
+    const int nth = std::max(2, (int)std::floor(ntr + 0.5));
+    std::vector<double> th(nth);
+    for (int j = 0; j < nth; ++j) {
+        const double sj = j * kPi / (nth - 1) * (1.0 + 1.0 / (kPi + th0));
+        th[j] = ((sj - 1.0 - th0) + std::sqrt((1.0 + th0 - sj) * (1.0 + th0 - sj) + 4.0 * th0 * sj)) / 2.0;
+    }
+    th[0] = 0.0;
+    th[nth - 1] = kPi;
+    th_out.clear();
+    ph_out.clear();
+    om_out.clear();
+    for (int j = 0; j < nth; ++j) {
+        int nph = 1;
+        double om;
+        if (j == 0) {
+            om = 2.0 * kPi * (1.0 - (std::cos(th[0]) + std::cos(th[1])) / 2.0);
+        } else if (j == nth - 1) {
+            om = 2.0 * kPi * ((std::cos(th[j - 1]) + std::cos(th[j])) / 2.0 + 1.0);
+        } else {
+            nph = std::max(3, (int)std::floor(4.0 * kPi * std::sin(th[j]) / (th[j + 1] - th[j - 1]) + 0.5));
+            om = kPi * (std::cos(th[j - 1]) - std::cos(th[j + 1]));
+        }
+        for (int k = 0; k < nph; ++k) {
+            th_out.push_back(th[j]);
+            ph_out.push_back(2.0 * kPi * k / nph);
+            om_out.push_back(om / nph);
+        }
+    }
+}
+
+// Lab Frame of a RHS: x_L = khat, y_L = normalize(z x khat) (x if khat is
+// along z), z_L = x_L x y_L.
+void lab_frame(const double* k, double xl[3], double yl[3], double zl[3]) {
+    for (int a = 0; a < 3; ++a) xl[a] = k[a];
+    double y[3] = {-k[1], k[0], 0.0};  // z x k
+    double n = std::sqrt(y[0] * y[0] + y[1] * y[1]);
+    if (n < 1e-8) {
+        y[0] = 1.0;
+        y[1] = 0.0;
+        n = 1.0;
+    }
+    for (int a = 0; a < 3; ++a) yl[a] = y[a] / n;
+    zl[0] = xl[1] * yl[2] - xl[2] * yl[1];
+    zl[1] = xl[2] * yl[0] - xl[0] * yl[2];
+    zl[2] = xl[0] * yl[1] - xl[1] * yl[0];
+}
+
+template <typename T>
+dda_status farfield_run(dda_ctx* ctx, int R, const std::vector<double>& khat, const double* P_host, int ndir,
+                        const double* theta, const double* phi, std::vector<double2>& F) {
+    using C = cx<T>;
+    const Geom& g = ctx->g;
+    const int64_t N = g.N;
+    if (g.ox > 1024 || g.oy > 1024 || g.oz > 1024) return ctx->fail(DDA_ERR_SIZE, "far field: lattice above 1024");
+    const int Lm = std::max(g.ox, std::max(g.oy, g.oz)), tab_len = 3 * Lm;
+    const double kd = ctx->kd, c[3] = {0.5 * (g.ox - 1), 0.5 * (g.oy - 1), 0.5 * (g.oz - 1)};
+    std::vector<double> dirs((size_t)R * ndir * 3);
+    for (int r = 0; r < R; ++r) {
+        double xl[3], yl[3], zl[3];
+        lab_frame(&khat[3 * r], xl, yl, zl);
+        for (int d = 0; d < ndir; ++d) {
+            const double ct = std::cos(theta[d]), st = std::sin(theta[d]), cp = std::cos(phi[d]), sp = std::sin(phi[d]);
+            double* n = &dirs[((size_t)r * ndir + d) * 3];
+            for (int a = 0; a < 3; ++a) n[a] = ct * xl[a] + st * cp * yl[a] + st * sp * zl[a];
+        }
+    }
+    const size_t ntab = (size_t)R * ndir * tab_len;
+    std::vector<int> lat(N);
+    std::vector<unsigned> xyz(N);
+    CU(cudaMemcpy(lat.data(), ctx->tg.lat_of, N * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int64_t j = 0; j < N; ++j) {
+        const int l = lat[j];
+        const unsigned ix = l % g.nx, iy = (l / g.nx) % g.ny, iz = l / (g.nx * g.ny);
+        xyz[j] = ix | (iy << 10) | (iz << 20);
+    }
+    NearWork w;
+    cudaError_t ce = cudaSuccess;
+    auto alloc = [&](size_t bytes) { return ce == cudaSuccess ? w.get(bytes, ce) : nullptr; };
+    unsigned* d_xyz = (unsigned*)alloc(N * sizeof(unsigned));
+    double2* d_P64 = (double2*)alloc((size_t)R * 3 * N * sizeof(double2));
+    C* d_P = sizeof(T) == 8 ? (C*)d_P64 : (C*)alloc((size_t)R * 3 * N * sizeof(C));
+    C* d_tabs = (C*)alloc(ntab * sizeof(C));
+    double* d_dirs = (double*)alloc(dirs.size() * sizeof(double));
+    double2* d_F = (double2*)alloc((size_t)R * ndir * 3 * sizeof(double2));
+    if (ce != cudaSuccess) return ctx->cuda_fail(ce, "far-field workspace");
+    cudaStream_t st = ctx->stream;
+    CU(cudaMemcpyAsync(d_xyz, xyz.data(), N * sizeof(unsigned), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(d_P64, P_host, (size_t)R * 3 * N * sizeof(double2), cudaMemcpyHostToDevice, st));
+    if (sizeof(T) != 8) CU(launch_c128_to_c64v((int64_t)R * 3 * N, d_P64, (float2*)d_P, st));
+    CU(cudaMemcpyAsync(d_dirs, dirs.data(), dirs.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CU(launch_phase_tables<C>((int64_t)R * ndir, Lm, c, kd, d_dirs, d_tabs, st));
+    CU(launch_farfield<C>(R, N, d_xyz, d_P, ndir, tab_len, d_tabs, d_dirs, kd, d_F, st));
+    F.resize((size_t)R * ndir * 3);
+    CU(cudaMemcpyAsync(F.data(), d_F, F.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    CU(sync_collect(ctx));
+    return DDA_OK;
+}
+
+dda_status farfield_common(dda_ctx* ctx, dda_precision prec, int R, const double* khat, const double* P,
+                           std::vector<double>& k) {
+    if (!ctx->prepared) return ctx->fail(DDA_ERR_ARG, "dda_prepare has not been called for the current target");
+    if (prec != DDA_FP64 && prec != DDA_FP32 && prec != DDA_FP32_REFINED)
+        return ctx->fail(DDA_ERR_ARG, "far field: precision must be DDA_FP64 or a complex64 mode");
+    if (R <= 0 || !khat || !P) return ctx->fail(DDA_ERR_ARG, "R > 0 with khat and P required");
+    k.assign(3 * (size_t)R, 0.0);
+    for (int r = 0; r < R; ++r) {
+        double n = 0.0;
+        for (int a = 0; a < 3; ++a) n += khat[3 * r + a] * khat[3 * r + a];
+        if (!std::isfinite(n) || std::fabs(std::sqrt(n) - 1.0) > 1e-6)
+            return ctx->fail(DDA_ERR_ARG, "khat of RHS %d is not a unit vector", r);
+        for (int a = 0; a < 3; ++a) k[3 * r + a] = khat[3 * r + a] / std::sqrt(n);
+    }
+    cudaSetDevice(ctx->device);
+    return DDA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dda_status dda_scattering_directions(double x, double eta, int capacity, double* theta, double* phi, double* omega,
+                                     int* count) {
+    if (!count || !(x > 0.0) || !(eta > 0.0) || !std::isfinite(x) || !std::isfinite(eta) || capacity < 0)
+        return DDA_ERR_ARG;
+    if (x / eta > 1e5) return DDA_ERR_SIZE;
+    std::vector<double> th, ph, om;
+    scat_dirs(x, eta, th, ph, om);
+    *count = (int)th.size();
+    if (capacity >= (int)th.size()) {
+        if (!theta || !phi || !omega) return DDA_ERR_ARG;
+        std::copy(th.begin(), th.end(), theta);
+        std::copy(ph.begin(), ph.end(), phi);
+        std::copy(om.begin(), om.end(), omega);
+    }
+    return DDA_OK;
+}
+
+dda_status dda_farfield(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* P, int ndir,
+                        const double* theta, const double* phi, double* F_out) {
+    if (!ctx) return DDA_ERR_ARG;
+    ProfScope prof_scope(ctx);
+    if (ndir <= 0 || !theta || !phi || !F_out) return ctx->fail(DDA_ERR_ARG, "ndir > 0 with theta, phi, F_out");
+    std::vector<double> k;
+    dda_status rs = farfield_common(ctx, precision, R, khat, P, k);
+    if (rs != DDA_OK) return rs;
+    std::vector<double2> F;
+    rs = precision == DDA_FP64 ? farfield_run<double>(ctx, R, k, P, ndir, theta, phi, F)
+                               : farfield_run<float>(ctx, R, k, P, ndir, theta, phi, F);
+    if (rs != DDA_OK) return rs;
+    std::memcpy(F_out, F.data(), F.size() * sizeof(double2));
+    return DDA_OK;
+}
+
+dda_status dda_angular_averages(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* P,
+                                double eta, double* out, int* ndir_out) {
+    if (!ctx) return DDA_ERR_ARG;
+    ProfScope prof_scope(ctx);
+    if (!out || !(eta > 0.0) || !std::isfinite(eta)) return ctx->fail(DDA_ERR_ARG, "eta > 0 and out required");
+    std::vector<double> k;
+    dda_status rs = farfield_common(ctx, precision, R, khat, P, k);
+    if (rs != DDA_OK) return rs;
+    const double x = ctx->kd * ctx->aeff_lat;
+    if (x / eta > 1e5) return ctx->fail(DDA_ERR_SIZE, "eta too small for x = %g", x);
+    std::vector<double> th, ph, om;
+    scat_dirs(x, eta, th, ph, om);
+    const int nd = (int)th.size();
+    std::vector<double2> F;
+    rs = precision == DDA_FP64 ? farfield_run<double>(ctx, R, k, P, nd, th.data(), ph.data(), F)
+                               : farfield_run<float>(ctx, R, k, P, nd, th.data(), ph.data(), F);
+    if (rs != DDA_OK) return rs;
+    for (int r = 0; r < R; ++r) {
+        double c = 0.0, s1 = 0.0, s2 = 0.0, gy = 0.0, gz = 0.0;
+        for (int d = 0; d < nd; ++d) {
+            const double2* f = &F[((size_t)r * nd + d) * 3];
+            const double w = om[d] * (f[0].x * f[0].x + f[0].y * f[0].y + f[1].x * f[1].x + f[1].y * f[1].y +
+                                      f[2].x * f[2].x + f[2].y * f[2].y);
+            const double ct = std::cos(th[d]), st = std::sin(th[d]);
+            c += w;
+            s1 += w * ct;
+            s2 += w * ct * ct;
+            gy += w * st * std::cos(ph[d]);
+            gz += w * st * std::sin(ph[d]);
+        }
+        double* o = out + 6 * (size_t)r;
+        o[0] = c / (kPi * ctx->aeff_lat * ctx->aeff_lat);
+        o[1] = s1 / c;
+        o[2] = s2 / c;
+        o[3] = s1 / c;
+        o[4] = gy / c;
+        o[5] = gz / c;
+    }
+    if (ndir_out) *ndir_out = nd;
+    return DDA_OK;
 }
 
 dda_status dda_grad_qabs(dda_ctx* ctx, dda_precision precision, const double* khat, const double* e,

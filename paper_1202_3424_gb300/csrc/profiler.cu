@@ -23,7 +23,7 @@ const char* kernel_kind_name(int kind) {
         "x_fwd_c128", "y_fwd_c128", "z_conv_c128", "y_inv_c128", "x_inv_c128",
         "x_fwd_df", "y_fwd_df", "z_conv_df", "y_inv_df", "x_inv_df",
         "bicgstab_c64", "bicgstab_c128", "refine_c128", "incident_field", "q_sums", "green_fft", "other",
-        "xy_fwd_c64", "yx_inv_c64", "xy_fwd_c128", "yx_inv_c128", "xy_fwd_df", "yx_inv_df"};
+        "xy_fwd_c64", "yx_inv_c64", "xy_fwd_c128", "yx_inv_c128", "xy_fwd_df", "yx_inv_df", "far_field"};
     return (kind >= 0 && kind < KK_COUNT) ? names[kind] : "?";
 }
 

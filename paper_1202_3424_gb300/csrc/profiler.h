@@ -16,6 +16,7 @@ enum KernelKind : int {
     KK_XFWD_DF, KK_YFWD_DF, KK_ZCONV_DF, KK_YINV_DF, KK_XINV_DF,
     KK_KRYLOV_C64, KK_KRYLOV_C128, KK_REFINE, KK_EINC, KK_QSUMS, KK_GREEN, KK_OTHER,
     KK_XYFWD_C64, KK_YXINV_C64, KK_XYFWD_C128, KK_YXINV_C128, KK_XYFWD_DF, KK_YXINV_DF,
+    KK_FARFIELD,
     KK_COUNT
 };
 

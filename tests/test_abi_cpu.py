@@ -70,3 +70,21 @@ def test_product_sources_reference_no_oracle_code():
     for f in os.listdir(csrc):
         text = open(os.path.join(csrc, f)).read()
         assert "oracle" not in text.lower(), f
+
+
+def test_scattering_directions_host_code_matches_oracle():
+    """The library's host-side direction rule (no GPU needed) against the
+    oracle's, including the guide's printed NAVG = 962 case."""
+    import numpy as np
+    import paper_1202_3424_gb300 as dda
+    from oracle import dda as odda
+    try:
+        dda.load_library(build_if_missing=False)
+    except dda.DdaError:
+        pytest.skip("library not built")
+    for x, eta in ((3.093665, 0.5), (0.3, 1.0), (8.0, 0.25), (20.0, 0.5)):
+        t, p, w = dda.dda_scattering_directions(x, eta)
+        t2, p2, w2 = odda.scattering_directions(x, eta)
+        assert t.size == t2.size
+        assert np.abs(t - t2).max() < 1e-13 and np.abs(p - p2).max() < 1e-13 and np.abs(w - w2).max() < 1e-13
+    assert dda.dda_scattering_directions(3.093665, 0.5)[0].size == 962

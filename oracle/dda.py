@@ -485,3 +485,67 @@ def angular_averages(r: np.ndarray, P: np.ndarray, kd: float, khat, theta, phi, 
     g = np.array([np.sum(w * c), np.sum(w * np.sin(theta) * np.cos(phi)),
                   np.sum(w * np.sin(theta) * np.sin(phi))]) / csca
     return csca, float(g[0]), float(np.sum(w * c * c) / csca), g
+
+
+def scattering_amplitudes(r: np.ndarray, P1: np.ndarray, P2: np.ndarray, kd: float, khat, e01, e02, theta, phi):
+    """Amplitude scattering matrix (S1, S2, S3, S4) per direction ("Two
+    Orthogonal Incident Polarizations (IORTH=2)"), from the polarizations P1,
+    P2 (N, 3) induced by incident states e01, e02 (complex 3-vectors).
+
+    f_ml = k (F_l . e_m) with e_1 = theta_hat, e_2 = phi_hat of the direction
+    (F_l the far field of P_l, so that E_s . e_m = exp(ikr)/(kr) f_ml for a
+    unit incident state l); with a = e01^*.y_L, b = e01^*.z_L, c = e02^*.y_L,
+    d = e02^*.z_L the guide's relations give
+      S1 = -i [f21 (b cos phi - a sin phi) + f22 (d cos phi - c sin phi)]
+      S2 = -i [f11 (a cos phi + b sin phi) + f12 (c cos phi + d sin phi)]
+      S3 =  i [f11 (b cos phi - a sin phi) + f12 (d cos phi - c sin phi)]
+      S4 =  i [f21 (a cos phi + b sin phi) + f22 (c cos phi + d sin phi)].
+    Returns (D, 4) complex (S1, S2, S3, S4)."""
+    xl, yl, zl = lab_frame(khat)
+    th = np.asarray(theta, dtype=np.float64)
+    ph = np.asarray(phi, dtype=np.float64)
+    n = directions(khat, th, ph)
+    that = (-np.sin(th)[:, None] * xl + (np.cos(th) * np.cos(ph))[:, None] * yl
+            + (np.cos(th) * np.sin(ph))[:, None] * zl)
+    phat = -np.sin(ph)[:, None] * yl + np.cos(ph)[:, None] * zl
+    F1 = far_field(r, P1, kd, n)
+    F2 = far_field(r, P2, kd, n)
+    f11 = kd * np.sum(F1 * that, axis=1)
+    f21 = kd * np.sum(F1 * phat, axis=1)
+    f12 = kd * np.sum(F2 * that, axis=1)
+    f22 = kd * np.sum(F2 * phat, axis=1)
+    e01 = np.conj(np.asarray(e01, dtype=np.complex128))
+    e02 = np.conj(np.asarray(e02, dtype=np.complex128))
+    a, b, c, d = e01 @ yl, e01 @ zl, e02 @ yl, e02 @ zl
+    cp, sp = np.cos(ph), np.sin(ph)
+    S1 = -1j * (f21 * (b * cp - a * sp) + f22 * (d * cp - c * sp))
+    S2 = -1j * (f11 * (a * cp + b * sp) + f12 * (c * cp + d * sp))
+    S3 = 1j * (f11 * (b * cp - a * sp) + f12 * (d * cp - c * sp))
+    S4 = 1j * (f21 * (a * cp + b * sp) + f22 * (c * cp + d * sp))
+    return np.stack([S1, S2, S3, S4], axis=1)
+
+
+def mueller_matrix(S: np.ndarray) -> np.ndarray:
+    """4x4 Mueller matrix per direction from (S1, S2, S3, S4) (D, 4): the
+    Stokes-parameter transformation of Bohren & Huffman (1983, sec. 3.3), as
+    the guide lists it.  Returns (D, 4, 4), element [i-1, j-1] = S_ij."""
+    S1, S2, S3, S4 = (S[:, i] for i in range(4))
+    a1, a2, a3, a4 = (np.abs(s) ** 2 for s in (S1, S2, S3, S4))
+    M = np.empty((S.shape[0], 4, 4))
+    M[:, 0, 0] = (a1 + a2 + a3 + a4) / 2
+    M[:, 0, 1] = (a2 - a1 + a4 - a3) / 2
+    M[:, 0, 2] = (S2 * np.conj(S3) + S1 * np.conj(S4)).real
+    M[:, 0, 3] = (S2 * np.conj(S3) - S1 * np.conj(S4)).imag
+    M[:, 1, 0] = (a2 - a1 + a3 - a4) / 2
+    M[:, 1, 1] = (a1 + a2 - a3 - a4) / 2
+    M[:, 1, 2] = (S2 * np.conj(S3) - S1 * np.conj(S4)).real
+    M[:, 1, 3] = (S2 * np.conj(S3) + S1 * np.conj(S4)).imag
+    M[:, 2, 0] = (S2 * np.conj(S4) + S1 * np.conj(S3)).real
+    M[:, 2, 1] = (S2 * np.conj(S4) - S1 * np.conj(S3)).real
+    M[:, 2, 2] = (S1 * np.conj(S2) + S3 * np.conj(S4)).real
+    M[:, 2, 3] = (S2 * np.conj(S1) + S4 * np.conj(S3)).imag
+    M[:, 3, 0] = (S4 * np.conj(S2) + S1 * np.conj(S3)).imag
+    M[:, 3, 1] = (S4 * np.conj(S2) - S1 * np.conj(S3)).imag
+    M[:, 3, 2] = (S1 * np.conj(S2) - S3 * np.conj(S4)).imag
+    M[:, 3, 3] = (S1 * np.conj(S2) - S3 * np.conj(S4)).real
+    return M

@@ -23,6 +23,7 @@ _orig_scat = dda.scattered_field
 _orig_box = dda.nearfield_box
 _orig_ff = dda.far_field
 _orig_dirs = dda.scattering_directions
+_orig_mueller = dda.mueller_matrix
 
 
 def _tensor_sign(rvec, kd):            # (1 - ik rho) instead of (ik rho - 1)
@@ -116,6 +117,12 @@ def _dirs_uniform_weights(x, eta):                # equal weights on the forward
     return t, ph, np.full_like(w, 4 * math.pi / w.size)
 
 
+def _mueller_s34_sign(S):                          # S34 = Im(S1 S2^* + ...) instead of Im(S2 S1^* + ...)
+    M = _orig_mueller(S)
+    M[:, 2, 3] = -M[:, 2, 3]
+    return M
+
+
 MUTATIONS = [
     ("interaction_tensor", _tensor_sign, [pins.two_dipole_error]),
     ("interaction_tensor", _tensor_no_far, [pins.two_dipole_error]),
@@ -133,6 +140,7 @@ MUTATIONS = [
     ("far_field", _ff_phase, [pins.dda_asymmetry_vs_mie_error]),
     ("far_field", _ff_no_projection, [pins.farfield_single_dipole_error]),
     ("scattering_directions", _dirs_uniform_weights, [pins.farfield_single_dipole_error]),
+    ("mueller_matrix", _mueller_s34_sign, [pins.mueller_sphere_vs_mie_error]),
 ]
 
 

@@ -213,6 +213,57 @@ def dda_asymmetry_vs_mie_error(n=12, x=1.5, m=1.33 + 0.01j):
     return abs(g1 - gm) / gm
 
 
+def mueller_single_dipole_error(kd=0.5, alpha=0.8 + 0.3j):
+    """One isotropic dipole: for any orthonormal incident pair (linear along
+    y/z, rotated by 45 degrees, circular) the Mueller matrix is the Rayleigh
+    matrix A [(1+c^2)/2, (c^2-1)/2; (c^2-1)/2, (1+c^2)/2] (+) [c, 0; 0, c],
+    c = cos theta, A = k^6 |alpha|^2, at every azimuth."""
+    k = np.array([1.0, 0.0, 0.0])
+    th, ph = np.meshgrid(np.linspace(0, math.pi, 7), np.linspace(0.1, 6.0, 7))
+    th, ph = th.ravel(), ph.ravel()
+    A = kd ** 6 * abs(alpha) ** 2
+    c = np.cos(th)
+    want = np.zeros((th.size, 4, 4))
+    want[:, 0, 0] = want[:, 1, 1] = A * (1 + c * c) / 2
+    want[:, 0, 1] = want[:, 1, 0] = A * (c * c - 1) / 2
+    want[:, 2, 2] = want[:, 3, 3] = A * c
+    err = 0.0
+    for e01 in (np.array([0, 1, 0], complex), np.array([0, 1, 1], complex) / math.sqrt(2),
+                np.array([0, 1, 1j], complex) / math.sqrt(2)):
+        e02 = np.cross(k, np.conj(e01))
+        S = dda.scattering_amplitudes(np.zeros((1, 3)), (alpha * e01)[None], (alpha * e02)[None], kd, k, e01, e02,
+                                      th, ph)
+        err = max(err, float(np.abs(dda.mueller_matrix(S) - want).max() / A))
+    return err
+
+
+def mueller_sphere_vs_mie_error(n=12, x=1.5, m=1.33 + 0.01j):
+    """DDA sphere (k along x, e01 = y, e02 = z) against the Mie matrix
+    S11 = (|S1|^2+|S2|^2)/2, S12 = (|S2|^2-|S1|^2)/2, S33 = Re(S1 S2^*),
+    S34 = Im(S2 S1^*), relative to the forward S11, in the plane phi = 30 deg."""
+    grid = sphere_grid(n)
+    r, _ = dda.site_positions(grid)
+    N = len(r)
+    kd = x / dda.aeff_lattice(N)
+    k = np.array([1.0, 0.0, 0.0])
+    e01, e02 = np.array([0, 1, 0], complex), np.array([0, 0, 1], complex)
+    Ps = []
+    for e in (e01, e02):
+        beta = dda.ldr_inverse_polarizability(np.full(N, m * m), kd, k, e)
+        Ps.append(dda.solve_dense(dda.dense_matrix(r, kd, beta), dda.incident_field(r, kd, k, e)))
+    th = np.linspace(0, math.pi, 13)
+    ph = np.full(th.size, math.pi / 6)
+    M = dda.mueller_matrix(dda.scattering_amplitudes(r, Ps[0], Ps[1], kd, k, e01, e02, th, ph))
+    S1, S2 = mie.mie_amplitudes(x, m, th)
+    want = np.zeros_like(M)
+    want[:, 0, 0] = (abs(S1) ** 2 + abs(S2) ** 2) / 2
+    want[:, 0, 1] = (abs(S2) ** 2 - abs(S1) ** 2) / 2
+    want[:, 2, 2] = (S1 * np.conj(S2)).real
+    want[:, 2, 3] = (S2 * np.conj(S1)).imag
+    idx = [(0, 0), (0, 1), (2, 2), (2, 3)]
+    return max(float(np.abs(M[:, i, j] - want[:, i, j]).max()) for i, j in idx) / want[0, 0, 0]
+
+
 # ------------------------------------------------------------------- tests --
 def test_pseudosphere_counts_match_guide(golden_dir):
     for box, diam, count, *_ in _golden_rows(os.path.join(golden_dir, "pseudosphere_counts.txt")):
@@ -531,3 +582,11 @@ def test_mie_amplitudes_and_asymmetry_identities():
 
 def test_dda_asymmetry_approaches_mie():
     assert dda_asymmetry_vs_mie_error() < 0.05
+
+
+def test_mueller_matrix_of_one_dipole_is_rayleigh():
+    assert mueller_single_dipole_error() < 1e-12
+
+
+def test_mueller_matrix_of_dda_sphere_approaches_mie():
+    assert mueller_sphere_vs_mie_error() < 0.03

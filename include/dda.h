@@ -229,6 +229,18 @@ dda_status dda_nearfield(dda_ctx* ctx, dda_precision precision, int R, const dou
  *   (x = k a_eff of the prepared target, eta = ETASCA), Q_sca = C_sca/(pi
  *   a_eff^2), g the Lab Frame components of <n>.  *ndir_out (nullable) =
  *   directions used.                                                        */
+/* dda_mueller: the guide's amplitude scattering matrix and 4x4 Mueller
+ *   matrix ("Two Orthogonal Incident Polarizations (IORTH=2)") for one
+ *   incident direction khat: P host [2][3][N] complex, the polarizations
+ *   induced by the orthonormal incident states e01, e02 (complex 3-vectors,
+ *   6 doubles each; the guide takes e02 = khat x e01^*).  Per direction:
+ *   f_ml = k (F_l . e_m), e_1 = theta_hat, e_2 = phi_hat; S1..S4 from f_ml,
+ *   a = e01^*.y_L, b = e01^*.z_L, c = e02^*.y_L, d = e02^*.z_L and phi; and
+ *   S_ij from S1..S4 (Bohren & Huffman).  S_out [ndir][16] row-major S_11 ..
+ *   S_44; amp_out (nullable) [ndir][4] complex S1..S4.                      */
+dda_status dda_mueller(dda_ctx* ctx, dda_precision precision, const double* khat, const double* e01, const double* e02,
+                       const double* P, int ndir, const double* theta, const double* phi, double* S_out,
+                       double* amp_out);
 dda_status dda_scattering_directions(double x, double eta, int capacity, double* theta, double* phi, double* omega,
                                      int* count);
 dda_status dda_farfield(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* P, int ndir,

@@ -26,7 +26,7 @@ __all__ = [
     "dda_prepare", "dda_get_info", "dda_solve", "dda_solve_device", "dda_matvec", "dda_matvec_device",
     "dda_incident_field", "dda_grad_qabs", "dda_matvec_device_noalloc", "dda_set_schedule", "dda_get_schedule",
     "dda_nearfield", "dda_nearfield_dims", "dda_set_slice_passes", "dda_scattering_directions", "dda_farfield",
-    "dda_angular_averages",
+    "dda_angular_averages", "dda_mueller",
 ]
 
 STATUS = {0: "DDA_OK", 1: "DDA_ERR_ARG", 2: "DDA_ERR_CUDA", 3: "DDA_ERR_OOM", 4: "DDA_ERR_SIZE",
@@ -114,6 +114,7 @@ def load_library(build_if_missing: bool = True):
         "dda_scattering_directions": ([ctypes.c_double, ctypes.c_double, ctypes.c_int, _D, _D, _D,
                                        ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "dda_farfield": ([vp, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_int, _D, _D, _D], ctypes.c_int),
+        "dda_mueller": ([vp, ctypes.c_int, _D, _D, _D, _D, ctypes.c_int, _D, _D, _D, _D], ctypes.c_int),
         "dda_angular_averages": ([vp, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_double, _D,
                                   ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "dda_nearfield_dims": ([vp, _D, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -351,6 +352,25 @@ def dda_farfield(ctx, precision, khat, P, theta, phi):
     return F
 
 
+def dda_mueller(ctx, precision, khat, e01, e02, P, theta, phi):
+    """Mueller matrices (ndir, 4, 4) and amplitudes (ndir, 4) complex S1..S4 for
+    one incident direction and the two incident states e01, e02; P (2, 3, N)."""
+    k = np.ascontiguousarray(np.asarray(khat, dtype=np.float64).reshape(3))
+    a = np.ascontiguousarray(np.asarray(e01, dtype=np.complex128).reshape(3))
+    b = np.ascontiguousarray(np.asarray(e02, dtype=np.complex128).reshape(3))
+    PP = np.ascontiguousarray(P, dtype=np.complex128)
+    if PP.shape[0] != 2 or PP.shape[1] != 3:
+        raise ValueError("P must be (2, 3, N)")
+    t = np.ascontiguousarray(theta, dtype=np.float64).ravel()
+    p = np.ascontiguousarray(phi, dtype=np.float64).ravel()
+    M = np.empty((t.size, 4, 4))
+    S = np.empty((t.size, 4), dtype=np.complex128)
+    _check(ctx, load_library().dda_mueller(ctx, int(precision), _dptr(k), _dptr(a.view(np.float64)),
+                                           _dptr(b.view(np.float64)), _dptr(PP.view(np.float64)), t.size, _dptr(t),
+                                           _dptr(p), _dptr(M), _dptr(S.view(np.float64))))
+    return M, S
+
+
 def dda_angular_averages(ctx, precision, khat, P, eta=0.5):
     """(R, 6) array of Q_sca, <cos>, <cos^2>, g_x, g_y, g_z, and the number of directions used."""
     k, PP, R = _khat_P(khat, P)
@@ -436,6 +456,9 @@ class Context:
 
     def farfield(self, precision, khat, P, theta, phi):
         return dda_farfield(self.handle, precision, khat, P, theta, phi)
+
+    def mueller(self, precision, khat, e01, e02, P, theta, phi):
+        return dda_mueller(self.handle, precision, khat, e01, e02, P, theta, phi)
 
     def angular_averages(self, precision, khat, P, eta=0.5):
         return dda_angular_averages(self.handle, precision, khat, P, eta)

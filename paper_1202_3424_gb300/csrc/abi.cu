@@ -1608,6 +1608,90 @@ dda_status dda_farfield(dda_ctx* ctx, dda_precision precision, int R, const doub
     return DDA_OK;
 }
 
+dda_status dda_mueller(dda_ctx* ctx, dda_precision precision, const double* khat, const double* e01, const double* e02,
+                       const double* P, int ndir, const double* theta, const double* phi, double* S_out,
+                       double* amp_out) {
+    if (!ctx) return DDA_ERR_ARG;
+    ProfScope prof_scope(ctx);
+    if (ndir <= 0 || !theta || !phi || !S_out || !e01 || !e02)
+        return ctx->fail(DDA_ERR_ARG, "ndir > 0 with e01, e02, theta, phi and S_out required");
+    std::vector<double> k;
+    const double kk[6] = {khat ? khat[0] : 0.0, khat ? khat[1] : 0.0, khat ? khat[2] : 0.0,
+                          khat ? khat[0] : 0.0, khat ? khat[1] : 0.0, khat ? khat[2] : 0.0};
+    dda_status rs = farfield_common(ctx, precision, 2, khat ? kk : nullptr, P, k);
+    if (rs != DDA_OK) return rs;
+    std::vector<double2> F;  // [2][ndir][3]: far fields of the two incident states
+    rs = precision == DDA_FP64 ? farfield_run<double>(ctx, 2, k, P, ndir, theta, phi, F)
+                               : farfield_run<float>(ctx, 2, k, P, ndir, theta, phi, F);
+    if (rs != DDA_OK) return rs;
+    double xl[3], yl[3], zl[3];
+    lab_frame(k.data(), xl, yl, zl);
+    // conj(e0l) . y_L and . z_L
+    cd a = 0.0, b = 0.0, c = 0.0, d = 0.0;
+    for (int q = 0; q < 3; ++q) {
+        const cd u = std::conj(cd(e01[2 * q], e01[2 * q + 1])), v = std::conj(cd(e02[2 * q], e02[2 * q + 1]));
+        a += u * yl[q];
+        b += u * zl[q];
+        c += v * yl[q];
+        d += v * zl[q];
+    }
+    const cd I(0.0, 1.0);
+    for (int dd = 0; dd < ndir; ++dd) {
+        const double ct = std::cos(theta[dd]), st = std::sin(theta[dd]), cp = std::cos(phi[dd]), sp = std::sin(phi[dd]);
+        double th_hat[3], ph_hat[3];
+        for (int q = 0; q < 3; ++q) {
+            th_hat[q] = -st * xl[q] + ct * cp * yl[q] + ct * sp * zl[q];
+            ph_hat[q] = -sp * yl[q] + cp * zl[q];
+        }
+        // f_ml = k F_l . e_m, e_1 = theta_hat, e_2 = phi_hat
+        cd f[2][2];
+        for (int l = 0; l < 2; ++l) {
+            const double2* Fl = &F[((size_t)l * ndir + dd) * 3];
+            cd ft = 0.0, fp = 0.0;
+            for (int q = 0; q < 3; ++q) {
+                const cd v(Fl[q].x, Fl[q].y);
+                ft += v * th_hat[q];
+                fp += v * ph_hat[q];
+            }
+            f[0][l] = ctx->kd * ft;
+            f[1][l] = ctx->kd * fp;
+        }
+        const cd S1 = -I * (f[1][0] * (b * cp - a * sp) + f[1][1] * (d * cp - c * sp));
+        const cd S2 = -I * (f[0][0] * (a * cp + b * sp) + f[0][1] * (c * cp + d * sp));
+        const cd S3 = I * (f[0][0] * (b * cp - a * sp) + f[0][1] * (d * cp - c * sp));
+        const cd S4 = I * (f[1][0] * (a * cp + b * sp) + f[1][1] * (c * cp + d * sp));
+        if (amp_out) {
+            const cd Sv[4] = {S1, S2, S3, S4};
+            for (int q = 0; q < 4; ++q) {
+                amp_out[(size_t)dd * 8 + 2 * q] = Sv[q].real();
+                amp_out[(size_t)dd * 8 + 2 * q + 1] = Sv[q].imag();
+            }
+        }
+        // Mueller matrix: Stokes-vector transformation of (S1, S2, S3, S4)
+        const double n1 = std::norm(S1), n2 = std::norm(S2), n3 = std::norm(S3), n4 = std::norm(S4);
+        const cd s23 = S2 * std::conj(S3), s14 = S1 * std::conj(S4), s24 = S2 * std::conj(S4),
+                 s13 = S1 * std::conj(S3), s12 = S1 * std::conj(S2), s34 = S3 * std::conj(S4);
+        double* M = S_out + (size_t)dd * 16;
+        M[0] = 0.5 * (n1 + n2 + n3 + n4);
+        M[1] = 0.5 * (n2 - n1 + n4 - n3);
+        M[2] = (s23 + s14).real();
+        M[3] = (s23 - s14).imag();
+        M[4] = 0.5 * (n2 - n1 + n3 - n4);
+        M[5] = 0.5 * (n1 + n2 - n3 - n4);
+        M[6] = (s23 - s14).real();
+        M[7] = (s23 + s14).imag();
+        M[8] = (s24 + s13).real();
+        M[9] = (s24 - s13).real();
+        M[10] = (s12 + s34).real();
+        M[11] = -(s12 + s34).imag();     // Im(S2 S1^* + S4 S3^*)
+        M[12] = (std::conj(s24) + s13).imag();  // Im(S4 S2^* + S1 S3^*)
+        M[13] = (std::conj(s24) - s13).imag();  // Im(S4 S2^* - S1 S3^*)
+        M[14] = (s12 - s34).imag();
+        M[15] = (s12 - s34).real();
+    }
+    return DDA_OK;
+}
+
 dda_status dda_angular_averages(dda_ctx* ctx, dda_precision precision, int R, const double* khat, const double* P,
                                 double eta, double* out, int* ndir_out) {
     if (!ctx) return DDA_ERR_ARG;

@@ -125,3 +125,48 @@ def test_farfield_full_size_sweep(lib, prec, tol):
         want = odda.far_field(r, P[i].T, kd, odda.directions(w.khat[i], t[rows], ph[rows]))
         assert _rel(F[i][rows], want) < tol, i
     ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, F64_TOL), (2, F32_TOL)], ids=["fp64", "fp32"])
+def test_mueller_matches_oracle(lib, prec, tol):
+    """Mueller matrices and amplitudes from the GPU far field vs the oracle,
+    for an oblique incidence and an elliptical incident pair."""
+    grid = ellipsoid_grid(9, 8, 6, 9, 8, 6)
+    ctx = _ctx(lib, grid, [1.4 + 0.2j], 2.0, lib.Precision.FP32_REFINED)
+    kd, N = ctx.info()["kd"], ctx.info()["ndipoles"]
+    k = np.array([0.36, 0.48, 0.8])
+    xl, yl, zl = odda.lab_frame(k)
+    e01 = (yl + 1j * 0.5 * zl) / np.sqrt(1.25)
+    e02 = np.cross(k, np.conj(e01))
+    P = random_complex((2, 3, N), 19)
+    rng = np.random.default_rng(1)
+    theta = np.concatenate([[0.0, math.pi], rng.uniform(0, math.pi, 30)])
+    phi = np.concatenate([[0.3, 0.0], rng.uniform(0, 2 * math.pi, 30)])
+    M, S = ctx.mueller(prec, k, e01, e02, P, theta, phi)
+    r, _ = odda.site_positions(grid)
+    Sw = odda.scattering_amplitudes(r, P[0].T, P[1].T, kd, k, e01, e02, theta, phi)
+    Mw = odda.mueller_matrix(Sw)
+    assert _rel(S, Sw) < tol
+    assert np.abs(M - Mw).max() < tol * np.abs(Mw[:, 0, 0]).max()
+    ctx.close()
+
+
+def test_mueller_of_gpu_sphere_solution_approaches_mie(lib):
+    """16^3 sphere solved on the GPU for e01 = y, e02 = z: S11, S12, S33, S34
+    against the Mie series within the DDA's discretisation error."""
+    x, m = 1.5, 1.33 + 0.01j
+    ctx = _ctx(lib, sphere_grid(16), [m], x, lib.Precision.FP64)
+    k = np.array([[1.0, 0, 0], [1.0, 0, 0]])
+    e = np.array([[0, 1, 0], [0, 0, 1]], dtype=complex)
+    res, P, st = ctx.solve(0, k, e, tol=1e-10)
+    assert st == 0
+    th = np.linspace(0, math.pi, 19)
+    ph = np.full(th.size, 0.7)
+    M, S = ctx.mueller(0, k[0], e[0], e[1], P, th, ph)
+    S1, S2 = mie.mie_amplitudes(x, m, th)
+    ref = (abs(S1) ** 2 + abs(S2) ** 2) / 2
+    err = max(np.abs(M[:, 0, 0] - ref).max(), np.abs(M[:, 0, 1] - (abs(S2) ** 2 - abs(S1) ** 2) / 2).max(),
+              np.abs(M[:, 2, 2] - (S1 * np.conj(S2)).real).max(), np.abs(M[:, 2, 3] - (S2 * np.conj(S1)).imag).max())
+    assert err < 0.03 * ref[0]
+    assert np.abs(S[:, 2:]).max() < 1e-3 * np.abs(S[0, 0])   # S3 = S4 = 0 for a sphere
+    ctx.close()

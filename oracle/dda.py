@@ -75,6 +75,33 @@ def ldr_inverse_polarizability(eps, kd: float, khat, ehat) -> np.ndarray:
     return inv_acm + (LDR_B1 + LDR_B2 * eps + LDR_B3 * eps * S) * kd ** 2 - (2.0 / 3.0) * 1j * kd ** 3
 
 
+def dielectric_frame(theta: float, phi: float, beta: float):
+    """Principal axes e1, e2, e3 of an anisotropic material in the Target
+    Frame ("Composite Targets with Anisotropic Constituents"), from the
+    rotation angles theta_DF, phi_DF, beta_DF, as the guide writes them:
+      e1 =  x cos(th) + y sin(th) cos(ph) + z sin(th) sin(ph)
+      e2 = -x sin(th) cos(be) + y [cos(th) cos(be) cos(ph) - sin(be) sin(ph)]
+                              + z [cos(th) cos(be) sin(ph) + sin(be) cos(ph)]
+      e3 =  x sin(th) sin(be) - y [cos(th) sin(be) cos(ph) + cos(be) sin(ph)]
+                              - z [cos(th) sin(be) sin(ph) - cos(be) cos(ph)]"""
+    ct, st, cp, sp, cb, sb = (math.cos(theta), math.sin(theta), math.cos(phi), math.sin(phi),
+                              math.cos(beta), math.sin(beta))
+    e1 = np.array([ct, st * cp, st * sp])
+    e2 = np.array([-st * cb, ct * cb * cp - sb * sp, ct * cb * sp + sb * cp])
+    e3 = np.array([st * sb, -(ct * sb * cp + cb * sp), -(ct * sb * sp - cb * cp)])
+    return e1, e2, e3
+
+
+def ldr_inverse_tensor(eps3, angles, kd: float, khat, ehat) -> np.ndarray:
+    """1/alpha tensor (3, 3) of an anisotropic dipole: the LATTDR value of each
+    principal dielectric constant eps3[j] (same S for all three), along the
+    dielectric axes e_j: sum_j (1/alpha_j) e_j e_j^T (the guide's
+    alpha^TF = R alpha^DF R^-1; the inverse has the same axes)."""
+    ev = dielectric_frame(*angles)
+    b = ldr_inverse_polarizability(np.asarray(eps3, dtype=np.complex128), kd, khat, ehat)
+    return sum(b[j] * np.outer(ev[j], ev[j]) for j in range(3))
+
+
 def ldr_inverse_polarizability_derivative(eps, kd: float, khat, ehat) -> np.ndarray:
     """d(1/alpha)/d(eps) of the LATTDR form above: -4pi/(eps-1)^2 + (b2 + b3 S) k^2."""
     eps = np.asarray(eps, dtype=np.complex128)
@@ -104,10 +131,17 @@ def interaction_tensor(rvec, kd: float) -> np.ndarray:
     return ph[..., None, None] * (t1 * (rr - eye) + c2[..., None, None] * (3.0 * rr - eye))
 
 
+def _diag_block(beta, j):
+    """Diagonal block of dipole j: beta (N,) isotropic 1/alpha, or (N, 3, 3) tensors."""
+    b = np.asarray(beta)
+    return b[j] * np.eye(3) if b.ndim == 1 else b[j]
+
+
 def dense_matrix(r: np.ndarray, kd: float, beta: np.ndarray) -> np.ndarray:
     """The full 3N x 3N matrix A, row/column index 3*j + a.
 
-    beta (N,) holds 1/alpha_j for each dipole (isotropic diagonal blocks).
+    beta (N,) holds 1/alpha_j for each dipole (isotropic diagonal blocks), or
+    (N, 3, 3) the symmetric 1/alpha tensors of anisotropic dipoles.
     """
     n = r.shape[0]
     A = np.zeros((n, 3, n, 3), dtype=np.complex128)
@@ -115,7 +149,7 @@ def dense_matrix(r: np.ndarray, kd: float, beta: np.ndarray) -> np.ndarray:
         d = r[j] - r
         d[j] = (1.0, 0.0, 0.0)                # placeholder, overwritten below
         blk = interaction_tensor(d, kd)       # (n, 3, 3)
-        blk[j] = beta[j] * np.eye(3)
+        blk[j] = _diag_block(beta, j)
         A[j] = np.transpose(blk, (1, 0, 2))
     return A.reshape(3 * n, 3 * n)
 
@@ -138,7 +172,9 @@ def pairwise_matvec(r: np.ndarray, kd: float, beta: np.ndarray, P: np.ndarray,
         d[self_mask] = (1.0, 0.0, 0.0)
         blk = interaction_tensor(d, kd)                   # (c, N, 3, 3)
         blk[self_mask] = 0.0
-        out[s:s + chunk] = np.einsum("clab,lb->ca", blk, P) + beta[jj][:, None] * P[jj]
+        b = np.asarray(beta)
+        diag = b[jj][:, None] * P[jj] if b.ndim == 1 else np.einsum("cab,cb->ca", b[jj], P[jj])
+        out[s:s + chunk] = np.einsum("clab,lb->ca", blk, P) + diag
     return out
 
 
@@ -219,7 +255,12 @@ def cross_sections(kd: float, E_inc: np.ndarray, P: np.ndarray, beta: np.ndarray
     k = kd
     cext = 4.0 * math.pi * k * float(np.sum(np.imag(np.conj(E_inc) * P)))
     p2 = np.sum(np.abs(P) ** 2, axis=1)
-    cabs = 4.0 * math.pi * k * float(np.sum(np.imag(np.conj(beta)) * p2 - (2.0 / 3.0) * k ** 3 * p2))
+    b = np.asarray(beta)
+    if b.ndim == 1:
+        quad = np.imag(np.conj(b)) * p2
+    else:  # Im(P . beta^* P^*) for the tensor blocks
+        quad = np.imag(np.einsum("ja,jab,jb->j", P, np.conj(b), np.conj(P)))
+    cabs = 4.0 * math.pi * k * float(np.sum(quad - (2.0 / 3.0) * k ** 3 * p2))
     return cext, cabs, cext - cabs
 
 

@@ -24,6 +24,7 @@ _orig_box = dda.nearfield_box
 _orig_ff = dda.far_field
 _orig_dirs = dda.scattering_directions
 _orig_mueller = dda.mueller_matrix
+_orig_frame = dda.dielectric_frame
 
 
 def _tensor_sign(rvec, kd):            # (1 - ik rho) instead of (ik rho - 1)
@@ -123,6 +124,16 @@ def _mueller_s34_sign(S):                          # S34 = Im(S1 S2^* + ...) ins
     return M
 
 
+def _frame_e3_sign(theta, phi, beta):             # left-handed third axis
+    e1, e2, e3 = _orig_frame(theta, phi, beta)
+    return e1, e2, -e3
+
+
+def _xs_tensor_unconjugated(kd, E, P, beta):      # Im(P . beta P^*) instead of Im(P . beta^* P^*)
+    b = np.asarray(beta)
+    return _orig_xs(kd, E, P, np.conj(b) if b.ndim == 3 else b)
+
+
 MUTATIONS = [
     ("interaction_tensor", _tensor_sign, [pins.two_dipole_error]),
     ("interaction_tensor", _tensor_no_far, [pins.two_dipole_error]),
@@ -141,6 +152,8 @@ MUTATIONS = [
     ("far_field", _ff_no_projection, [pins.farfield_single_dipole_error]),
     ("scattering_directions", _dirs_uniform_weights, [pins.farfield_single_dipole_error]),
     ("mueller_matrix", _mueller_s34_sign, [pins.mueller_sphere_vs_mie_error]),
+    ("dielectric_frame", _frame_e3_sign, [pins.dielectric_frame_error]),
+    ("cross_sections", _xs_tensor_unconjugated, [pins.anisotropic_energy_balance_error]),
 ]
 
 

@@ -264,6 +264,66 @@ def mueller_sphere_vs_mie_error(n=12, x=1.5, m=1.33 + 0.01j):
     return max(float(np.abs(M[:, i, j] - want[:, i, j]).max()) for i, j in idx) / want[0, 0, 0]
 
 
+def dielectric_frame_error(seed=4):
+    """The guide's dielectric-frame axes form a right-handed orthonormal
+    triad for any angles, and the identity for zero angles."""
+    rng = np.random.default_rng(seed)
+    err = 0.0
+    for a in rng.uniform(-math.pi, math.pi, (8, 3)):
+        e1, e2, e3 = dda.dielectric_frame(*a)
+        E = np.array([e1, e2, e3])
+        err = max(err, float(np.abs(E @ E.T - np.eye(3)).max()), float(np.abs(np.cross(e1, e2) - e3).max()))
+    E0 = np.array(dda.dielectric_frame(0.0, 0.0, 0.0))
+    return max(err, float(np.abs(E0 - np.eye(3)).max()))
+
+
+def _aniso_cluster(kd, eps3, angles, khat, ehat, seed=3, n=30):
+    r = _small_cluster(seed, n)
+    B = dda.ldr_inverse_tensor(eps3, angles, kd, khat, ehat)
+    return r, np.broadcast_to(B, (len(r), 3, 3)).copy()
+
+
+def anisotropic_energy_balance_error(kd=0.6):
+    """Dense solve of a cluster of anisotropic dipoles: C_ext - C_abs (the
+    tensor form Im(P . (1/alpha)^* P^*)) equals the far-field pair-sum C_sca."""
+    khat, ehat = np.array([0.0, 0.6, 0.8]), np.array([1.0, 0.0, 0.0], complex)
+    r, B = _aniso_cluster(kd, [2.5 + 0.8j, 1.8 + 0.1j, 3.1 + 0.4j], (0.7, 1.9, -0.4), khat, ehat)
+    E = dda.incident_field(r, kd, khat, ehat)
+    P = dda.solve_dense(dda.dense_matrix(r, kd, B), E)
+    cext, cabs, _ = dda.cross_sections(kd, E, P, B)
+    return abs(cext - cabs - dda.csca_pair_sum(r, kd, P)) / abs(cext)
+
+
+def anisotropic_lossless_cabs(kd=0.5):
+    """Real principal dielectric constants: C_abs = 0 for any P."""
+    r, B = _aniso_cluster(kd, [2.25, 1.7, 3.0], (1.1, 0.3, 2.0), [1, 0, 0], [0, 1, 0], seed=7, n=20)
+    P = random_complex((len(r), 3), 13)
+    E = dda.incident_field(r, kd, [1, 0, 0], [0, 1, 0])
+    _, cabs, _ = dda.cross_sections(kd, E, P, B)
+    return abs(cabs) / (4 * math.pi * kd * float(np.sum(np.abs(P) ** 2)) * kd ** 3)
+
+
+def anisotropic_reduction_error(kd=0.45):
+    """Equal principal constants reduce the tensor to the isotropic 1/alpha
+    (any angles), and a single dipole driven along a principal axis e_j
+    responds with P = alpha_j E along e_j."""
+    eps = 2.2 + 0.5j
+    k, e = np.array([1.0, 0.0, 0.0]), np.array([0.0, 1.0, 0.0], complex)
+    B = dda.ldr_inverse_tensor([eps] * 3, (0.9, -1.3, 0.4), kd, k, e)
+    b = dda.ldr_inverse_polarizability(np.array([eps]), kd, k, e)[0]
+    err = float(np.abs(B - b * np.eye(3)).max() / abs(b))
+    angles = (0.0, 0.8, 0.0)                     # e1 = x, e2 and e3 rotated in the y-z plane
+    eps3 = [2.5 + 0.3j, 1.6 + 0.05j, 3.3 + 0.9j]
+    e1, e2, e3 = dda.dielectric_frame(*angles)
+    for j, ej in ((1, e2), (2, e3)):
+        ein = ej.astype(complex)
+        Bj = dda.ldr_inverse_tensor(eps3, angles, kd, k, ein)
+        P = dda.solve_dense(dda.dense_matrix(np.zeros((1, 3)), kd, Bj[None]), dda.incident_field(np.zeros((1, 3)), kd, k, ein))
+        bj = dda.ldr_inverse_polarizability(np.array([eps3[j]]), kd, k, ein)[0]
+        err = max(err, float(np.abs(P[0] - ein / bj).max() * abs(bj)))
+    return err
+
+
 # ------------------------------------------------------------------- tests --
 def test_pseudosphere_counts_match_guide(golden_dir):
     for box, diam, count, *_ in _golden_rows(os.path.join(golden_dir, "pseudosphere_counts.txt")):
@@ -590,3 +650,28 @@ def test_mueller_matrix_of_one_dipole_is_rayleigh():
 
 def test_mueller_matrix_of_dda_sphere_approaches_mie():
     assert mueller_sphere_vs_mie_error() < 0.03
+
+
+def test_dielectric_frame_is_a_rotation():
+    assert dielectric_frame_error() < 1e-14
+
+
+def test_anisotropic_tensor_reductions():
+    assert anisotropic_reduction_error() < 1e-12
+
+
+def test_anisotropic_energy_balance():
+    assert anisotropic_energy_balance_error() < 1e-10
+
+
+def test_anisotropic_lossless_target_absorbs_nothing():
+    assert anisotropic_lossless_cabs() < 1e-12
+
+
+def test_anisotropic_matrix_is_complex_symmetric():
+    r, B = _aniso_cluster(0.4, [1.7 + 0.2j, 2.6 + 0.1j, 1.3 + 0.4j], (0.3, 2.2, 1.0), [1, 0, 0], [0, 1, 0], seed=9)
+    A = dda.dense_matrix(r, 0.4, B)
+    assert np.abs(A - A.T).max() < 1e-14 * np.abs(A).max()
+    P = random_complex((len(r), 3), 2)
+    y = dda.pairwise_matvec(r, 0.4, B, P)
+    assert np.abs(y.ravel() - A @ P.ravel()).max() < 1e-13 * np.abs(y).max()

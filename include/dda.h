@@ -17,8 +17,9 @@
  *   1/alpha = (4pi/3)(eps+2)/(eps-1) + (b1 + b2 eps + b3 eps S)(kd)^2 - (2/3) i (kd)^3,
  *   b1 = -1.8915316, b2 = 0.1648469, b3 = -1.7700004, S = sum_a (khat_a e_a)^2,
  *   A_jl = e^{ik rho}/rho [k^2 (rr - I) + (ik rho - 1)/rho^2 (3 rr - I)]  (j != l),
- *   A_jj = (1/alpha_j) I,
- *   C_ext = 4 pi k sum Im(E_inc^* . P),  C_abs = 4 pi k sum (-Im(1/alpha) - 2k^3/3)|P|^2,
+ *   A_jj = (1/alpha_j) I  (anisotropic materials: the 1/alpha tensor of site j),
+ *   C_ext = 4 pi k sum Im(E_inc^* . P),  C_abs = 4 pi k sum (-Im(1/alpha) - 2k^3/3)|P|^2
+ *   (tensor form: Im(P . (1/alpha)^* P^*) - 2k^3/3 |P|^2),
  *   C_sca = C_ext - C_abs,  Q = C / (pi a_eff^2),  a_eff = (3N/4pi)^(1/3) d.
  *
  * Conventions.
@@ -127,6 +128,23 @@ dda_status dda_set_target(dda_ctx* ctx, int nx, int ny, int nz, const uint8_t* c
  * real refractive index of the ambient medium.  Relative index m/m_ambient is
  * used.  DDA_ERR_ARG if ncomp < max code in the grid or m_ambient <= 0.        */
 dda_status dda_set_materials(dda_ctx* ctx, int ncomp, const double* m_complex, double m_ambient);
+/* Anisotropic materials (guide: "Composite Targets with Anisotropic
+ * Constituents"; the per-site ICOMP(J,1-3) and THETADF, PHIDF, BETADF of the
+ * anisotropic target types).  Composition c (1..ncomp) has the complex
+ * refractive indices m_principal[6c..6c+5] (re, im of m_1, m_2, m_3) along the
+ * principal axes e_1, e_2, e_3 of its dielectric tensor, and the dielectric
+ * frame is rotated from the Target Frame by df_angles[3c..3c+2] = (theta_DF,
+ * phi_DF, beta_DF) in radians: e_1 = (cos th, sin th cos ph, sin th sin ph),
+ * e_2, e_3 as the guide gives them.  Each site's 1/alpha is then the
+ * symmetric tensor sum_j (1/alpha_j) e_j e_j^T, 1/alpha_j the LATTDR value of
+ * (m_j/m_ambient)^2 with the same propagation/polarization factor S for the
+ * three.  Sites whose dielectric frames differ use different codes (up to
+ * 255).  Replaces any isotropic materials (dda_set_materials switches back);
+ * solves, matvecs, Q and the field calls then use the tensor diagonal, the
+ * fused slice passes are skipped, and dda_grad_qabs returns DDA_ERR_ARG.
+ * Errors as for dda_set_materials; DDA_ERR_NONFINITE for a non-finite angle. */
+dda_status dda_set_anisotropic_materials(dda_ctx* ctx, int ncomp, const double* m_principal,
+                                         const double* df_angles, double m_ambient);
 /* Wavelength and size (guide: WAVINI / AEFFINI, same physical units): sets
  * d = aeff/(3N/4pi)^(1/3), k = 2 pi m_ambient / lambda_vac, and builds the
  * transformed Green tensor for `precision` (FP64 tensor always; FP32 copy for

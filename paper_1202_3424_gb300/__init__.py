@@ -26,7 +26,7 @@ __all__ = [
     "dda_prepare", "dda_get_info", "dda_solve", "dda_solve_device", "dda_matvec", "dda_matvec_device",
     "dda_incident_field", "dda_grad_qabs", "dda_matvec_device_noalloc", "dda_set_schedule", "dda_get_schedule",
     "dda_nearfield", "dda_nearfield_dims", "dda_set_slice_passes", "dda_scattering_directions", "dda_farfield",
-    "dda_angular_averages", "dda_mueller",
+    "dda_angular_averages", "dda_mueller", "dda_set_anisotropic_materials",
 ]
 
 STATUS = {0: "DDA_OK", 1: "DDA_ERR_ARG", 2: "DDA_ERR_CUDA", 3: "DDA_ERR_OOM", 4: "DDA_ERR_SIZE",
@@ -97,6 +97,7 @@ def load_library(build_if_missing: bool = True):
         "dda_set_stream": ([vp, vp], ctypes.c_int),
         "dda_set_target": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_uint8)], ctypes.c_int),
         "dda_set_materials": ([vp, ctypes.c_int, _D, ctypes.c_double], ctypes.c_int),
+        "dda_set_anisotropic_materials": ([vp, ctypes.c_int, _D, _D, ctypes.c_double], ctypes.c_int),
         "dda_prepare": ([vp, ctypes.c_double, ctypes.c_double, ctypes.c_int], ctypes.c_int),
         "dda_get_info": ([vp, ctypes.POINTER(dda_info)], ctypes.c_int),
         "dda_solve": ([vp, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.POINTER(dda_opts), _D, ctypes.POINTER(dda_result)],
@@ -200,6 +201,17 @@ def dda_set_target(ctx, grid: np.ndarray):
 def dda_set_materials(ctx, m, m_ambient: float = 1.0):
     mm = np.ascontiguousarray(np.atleast_1d(np.asarray(m, dtype=np.complex128)))
     _check(ctx, load_library().dda_set_materials(ctx, mm.size, _dptr(mm.view(np.float64)), float(m_ambient)))
+
+
+def dda_set_anisotropic_materials(ctx, m_principal, df_angles, m_ambient: float = 1.0):
+    """m_principal (ncomp, 3) complex refractive indices along e_1, e_2, e_3;
+    df_angles (ncomp, 3) = (theta_DF, phi_DF, beta_DF) in radians."""
+    mm = np.ascontiguousarray(np.asarray(m_principal, dtype=np.complex128).reshape(-1, 3))
+    aa = np.ascontiguousarray(np.asarray(df_angles, dtype=np.float64).reshape(-1, 3))
+    if aa.shape[0] != mm.shape[0]:
+        raise ValueError("one (theta_DF, phi_DF, beta_DF) per composition")
+    _check(ctx, load_library().dda_set_anisotropic_materials(ctx, mm.shape[0], _dptr(mm.view(np.float64)),
+                                                              _dptr(aa), float(m_ambient)))
 
 
 def dda_prepare(ctx, lambda_vac: float, aeff: float, precision: int = Precision.FP64):
@@ -428,6 +440,9 @@ class Context:
 
     def set_materials(self, m, m_ambient=1.0):
         dda_set_materials(self.handle, m, m_ambient)
+
+    def set_anisotropic_materials(self, m_principal, df_angles, m_ambient=1.0):
+        dda_set_anisotropic_materials(self.handle, m_principal, df_angles, m_ambient)
 
     def prepare(self, lambda_vac, aeff, precision=Precision.FP64):
         dda_prepare(self.handle, lambda_vac, aeff, precision)

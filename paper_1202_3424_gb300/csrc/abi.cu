@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
@@ -67,6 +68,12 @@ struct dda_ctx {
     std::vector<cd> m;
     double m_amb = 1.0;
     bool has_materials = false;
+    // anisotropic compositions (dda_set_anisotropic_materials): refractive
+    // indices along the principal axes e_1..e_3 and the dielectric-frame
+    // angles (theta_DF, phi_DF, beta_DF) of each
+    bool aniso = false;
+    std::vector<std::array<cd, 3>> m3;
+    std::vector<std::array<double, 3>> df_angles;
 
     // prepared wavelength
     bool prepared = false, has32 = false;
@@ -210,32 +217,93 @@ dda_status check_rhs(dda_ctx* ctx, int R, const double* khat, const double* e, s
     return DDA_OK;
 }
 
-// Per-(RHS, composition) tables: 1/alpha in FP64 and FP32, and the
-// absorption weight w = -Im(1/alpha) - (2/3)k^3.  Stride ncomp + 1 (code 0 unused).
-dda_status upload_tables(dda_ctx* ctx, int R, const std::vector<double>& k, const std::vector<cd>& e) {
-    const int BS = (int)ctx->m.size() + 1;
-    std::vector<double2> b64((size_t)R * BS);
-    std::vector<float2> b32((size_t)R * BS);
-    std::vector<double> w((size_t)R * BS);
-    std::vector<cdfl> bdf((size_t)R * BS);
-    const double kd = ctx->kd;
+// Compositions + 1 (code 0, vacuum, unused).
+int beta_stride(const dda_ctx* ctx) { return (int)ctx->m.size() + 1; }
+// Entries per RHS of the 1/alpha table: one per composition, or the three
+// rows of each composition's tensor (layout in PadWork::beta_tensor).
+int beta_rhs_stride(const dda_ctx* ctx) { return beta_stride(ctx) * (ctx->aniso ? 9 : 1); }
+// Entries per RHS of the absorption weights (k_qsums): one or six per composition.
+int qweight_stride(const dda_ctx* ctx) { return beta_stride(ctx) * (ctx->aniso ? 6 : 1); }
+
+// Principal axes e_1, e_2, e_3 (rows of ax) of a dielectric frame rotated by
+// (theta_DF, phi_DF, beta_DF) from the Target Frame ("Composite Targets with
+// Anisotropic Constituents").
+void dielectric_axes(const std::array<double, 3>& a, double ax[3][3]) {
+    const double ct = std::cos(a[0]), st = std::sin(a[0]), cp = std::cos(a[1]), sp = std::sin(a[1]),
+                 cb = std::cos(a[2]), sb = std::sin(a[2]);
+    const double e[3][3] = {{ct, st * cp, st * sp},
+                            {-st * cb, ct * cb * cp - sb * sp, ct * cb * sp + sb * cp},
+                            {st * sb, -(ct * sb * cp + cb * sp), -(ct * sb * sp - cb * cp)}};
+    std::memcpy(ax, e, sizeof e);
+}
+
+// 1/alpha table of R RHS (beta_rhs_stride entries each) and, if w is given,
+// the absorption weights (qweight_stride each).  Isotropic: 1/alpha and
+// w = -Im(1/alpha) - (2/3)k^3.  Anisotropic: B = sum_j (1/alpha_j) e_j e_j^T,
+// 1/alpha_j the LATTDR value of the j-th principal index (the same S for all
+// three), and the six weights of Im(P . B^* P^*) - (2/3)k^3 |P|^2.
+dda_status diag_tables(dda_ctx* ctx, int R, const std::vector<double>& k, const std::vector<cd>& e, std::vector<cd>& b,
+                       std::vector<double>* w) {
+    const int BS = beta_stride(ctx), RS = beta_rhs_stride(ctx), WS = qweight_stride(ctx);
+    const double kd = ctx->kd, rad = (2.0 / 3.0) * kd * kd * kd;
+    b.assign((size_t)R * RS, cd(0.0));
+    if (w) w->assign((size_t)R * WS, 0.0);
+    auto inv_alpha = [&](cd m, int r, cd* out) -> bool {
+        const cd mrel = m / ctx->m_amb;
+        *out = ldr_inverse_alpha(mrel * mrel, kd, &k[3 * r], &e[3 * r]);
+        return std::isfinite(out->real()) && std::isfinite(out->imag());
+    };
     for (int r = 0; r < R; ++r) {
-        b64[(size_t)r * BS] = make_double2(0.0, 0.0);
-        b32[(size_t)r * BS] = make_float2(0.f, 0.f);
-        bdf[(size_t)r * BS] = cdfl{dfl(0.0), dfl(0.0)};
-        w[(size_t)r * BS] = 0.0;
         for (int c = 1; c < BS; ++c) {
-            const cd mrel = ctx->m[c - 1] / ctx->m_amb;
-            const cd be = ldr_inverse_alpha(mrel * mrel, kd, &k[3 * r], &e[3 * r]);
-            if (!std::isfinite(be.real()) || !std::isfinite(be.imag()))
-                return ctx->fail(DDA_ERR_NONFINITE, "polarizability of composition %d is not finite", c);
-            b64[(size_t)r * BS + c] = make_double2(be.real(), be.imag());
-            b32[(size_t)r * BS + c] = make_float2((float)be.real(), (float)be.imag());
-            bdf[(size_t)r * BS + c] = cdfl{dfl(be.real()), dfl(be.imag())};
-            w[(size_t)r * BS + c] = -be.imag() - (2.0 / 3.0) * kd * kd * kd;
+            if (!ctx->aniso) {
+                cd be;
+                if (!inv_alpha(ctx->m[c - 1], r, &be))
+                    return ctx->fail(DDA_ERR_NONFINITE, "polarizability of composition %d is not finite", c);
+                b[(size_t)r * RS + c] = be;
+                if (w) (*w)[(size_t)r * WS + c] = -be.imag() - rad;
+                continue;
+            }
+            double ax[3][3];
+            dielectric_axes(ctx->df_angles[c - 1], ax);
+            cd bj[3];
+            for (int j = 0; j < 3; ++j)
+                if (!inv_alpha(ctx->m3[c - 1][j], r, &bj[j]))
+                    return ctx->fail(DDA_ERR_NONFINITE, "polarizability of composition %d is not finite", c);
+            cd B[3][3];
+            for (int a = 0; a < 3; ++a)
+                for (int d = 0; d < 3; ++d) {
+                    B[a][d] = 0.0;
+                    for (int j = 0; j < 3; ++j) B[a][d] += bj[j] * (ax[j][a] * ax[j][d]);
+                }
+            for (int a = 0; a < 3; ++a)
+                for (int d = 0; d < 3; ++d) b[(size_t)r * RS + (size_t)a * 3 * BS + c * 3 + d] = B[a][d];
+            if (w) {
+                double* wt = w->data() + (size_t)r * WS + c * 6;
+                for (int a = 0; a < 3; ++a) wt[a] = -B[a][a].imag() - rad;
+                wt[3] = -2.0 * B[0][1].imag();
+                wt[4] = -2.0 * B[0][2].imag();
+                wt[5] = -2.0 * B[1][2].imag();
+            }
         }
     }
+    return DDA_OK;
+}
+
+// Per-(RHS, composition) device tables: 1/alpha in FP64, FP32 and double-float
+// (diag_tables), the absorption weights, and the RHS directions and polarizations.
+dda_status upload_tables(dda_ctx* ctx, int R, const std::vector<double>& k, const std::vector<cd>& e) {
+    std::vector<cd> b;
+    std::vector<double> w;
     dda_status s;
+    if ((s = diag_tables(ctx, R, k, e, b, &w)) != DDA_OK) return s;
+    std::vector<double2> b64(b.size());
+    std::vector<float2> b32(b.size());
+    std::vector<cdfl> bdf(b.size());
+    for (size_t i = 0; i < b.size(); ++i) {
+        b64[i] = make_double2(b[i].real(), b[i].imag());
+        b32[i] = make_float2((float)b[i].real(), (float)b[i].imag());
+        bdf[i] = cdfl{dfl(b[i].real()), dfl(b[i].imag())};
+    }
     if ((s = ensure(ctx, ctx->pool[S_BETA64], b64.size() * sizeof(double2))) != DDA_OK) return s;
     if ((s = ensure(ctx, ctx->pool[S_BETA32], b32.size() * sizeof(float2))) != DDA_OK) return s;
     if ((s = ensure(ctx, ctx->pool[S_W], w.size() * sizeof(double))) != DDA_OK) return s;
@@ -254,8 +322,6 @@ dda_status upload_tables(dda_ctx* ctx, int R, const std::vector<double>& k, cons
     CU(sync_collect(ctx));
     return DDA_OK;
 }
-
-int beta_stride(const dda_ctx* ctx) { return (int)ctx->m.size() + 1; }
 
 // Chunk of RHS whose padded work fits the budget.
 template <typename T> int matvec_chunk(const dda_ctx* ctx, int R) {
@@ -309,7 +375,7 @@ template <typename T> dda_status ensure_pad(dda_ctx* ctx, int R) {
 // schedule for R >= 4 and the slice passes where built.
 template <typename T> dda_status pick_schedule(dda_ctx* ctx, int R, bool may_time, int* zvar, int* slices) {
     const int nv = zconv_schedules<T>(ctx->g);
-    const bool sl = slice_passes<T>(ctx->g);
+    const bool sl = slice_passes<T>(ctx->g) && !ctx->aniso;
     std::vector<int> zs, ss;
     if (nv <= 1) zs = {0};
     else if (ctx->force_z >= 0) zs = {std::min(ctx->force_z, nv - 1)};
@@ -334,7 +400,7 @@ template <typename T> dda_status pick_schedule(dda_ctx* ctx, int R, bool may_tim
         return DDA_OK;
     }
     // zero-filled x, y and 1/alpha table (their values do not change the timing)
-    const int BS = beta_stride(ctx);
+    const int BS = beta_rhs_stride(ctx);
     const size_t vec = (size_t)R * 3 * ctx->g.N * sizeof(cx<T>);
     dda_status s;
     if ((s = ensure(ctx, ctx->pool[S_TUNE], 2 * vec + (size_t)R * BS * sizeof(cx<T>), true)) != DDA_OK) return s;
@@ -343,6 +409,7 @@ template <typename T> dda_status pick_schedule(dda_ctx* ctx, int R, bool may_tim
     cx<T>* y = reinterpret_cast<cx<T>*>(base + vec);
     const cx<T>* beta = reinterpret_cast<const cx<T>*>(base + 2 * vec);
     PadWork<T> w{slot<cx<T>>(ctx, PadSlots<T>::a), slot<cx<T>>(ctx, PadSlots<T>::b)};
+    w.beta_tensor = ctx->aniso;
     std::vector<std::pair<int, int>> combos;
     for (int zv : zs)
         for (int sv : ss) combos.emplace_back(zv, sv);
@@ -394,7 +461,8 @@ dda_status run_matvec(dda_ctx* ctx, int R, const cx<T>* x, cx<T>* y, const int* 
     const int rc = matvec_chunk<T>(ctx, R);
     const int64_t n = 3 * ctx->g.N;
     PadWork<T> w{slot<cx<T>>(ctx, PadSlots<T>::a), slot<cx<T>>(ctx, PadSlots<T>::b)};
-    const int BS = beta_stride(ctx);
+    w.beta_tensor = ctx->aniso;
+    const int BS = beta_rhs_stride(ctx);
     dda_status zs;
     for (int r0 = 0; r0 < R; r0 += rc) {
         const int rn = std::min(rc, R - r0);
@@ -450,7 +518,8 @@ dda_status run_matvec_fused(dda_ctx* ctx, int R, int mode, cx<T>* x, cx<T>* y, c
     const int rc = matvec_chunk<T>(ctx, R);
     const int64_t n = 3 * ctx->g.N;
     PadWork<T> w{slot<cx<T>>(ctx, PadSlots<T>::a), slot<cx<T>>(ctx, PadSlots<T>::b)};
-    const int BS = beta_stride(ctx);
+    w.beta_tensor = ctx->aniso;
+    const int BS = beta_rhs_stride(ctx);
     const int ps = partial_stride(ctx);
     int* act = slot<int>(ctx, S_ACTIVE);
     dda_status zs;
@@ -773,7 +842,8 @@ dda_status forward_solve(dda_ctx* ctx, dda_precision prec, int R, const double* 
     if (rs != DDA_OK) return rs;
     // Q reductions (FP64)
     CU(launch_qsums(R, ctx->g.N, slot<double2>(ctx, S_E64), slot<double2>(ctx, S_X64), ctx->tg.comp_of,
-                    slot<double>(ctx, S_W), beta_stride(ctx), slot<double2>(ctx, S_QSUM), slot<double2>(ctx, S_PART),
+                    slot<double>(ctx, S_W), qweight_stride(ctx), ctx->aniso, slot<double2>(ctx, S_QSUM),
+                    slot<double2>(ctx, S_PART),
                     slot<unsigned>(ctx, S_CNT), ctx->stream));
     std::vector<double2> q(R);
     CU(cudaMemcpyAsync(q.data(), ctx->pool[S_QSUM].p, R * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
@@ -867,7 +937,7 @@ template <typename T>
 dda_status matvec_noalloc(dda_ctx* ctx, int R, const std::vector<double>& k, const std::vector<cd>& ev,
                           const void* x_dev, void* y_dev) {
     using C = cx<T>;
-    const int BS = beta_stride(ctx);
+    const int BS = beta_rhs_stride(ctx);
     const size_t beta_bytes = align256((size_t)R * BS * sizeof(C));
     const size_t u1_bytes = align256((size_t)R * 3 * ctx->g.u1_per_comp() * sizeof(C));
     const size_t u2_bytes = (size_t)R * 3 * ctx->g.u2_per_comp() * sizeof(C);
@@ -879,19 +949,14 @@ dda_status matvec_noalloc(dda_ctx* ctx, int R, const std::vector<double>& k, con
                          need, R, kNoAllocScratchBytes);
     unsigned char* base = nullptr;
     CU(noalloc_scratch(ctx->device, &base));
-    std::vector<C> beta((size_t)R * BS);
-    for (int r = 0; r < R; ++r) {
-        beta[(size_t)r * BS] = ccast<C>(make_double2(0.0, 0.0));
-        for (int c = 1; c < BS; ++c) {
-            const cd mrel = ctx->m[c - 1] / ctx->m_amb;
-            const cd be = ldr_inverse_alpha(mrel * mrel, ctx->kd, &k[3 * r], &ev[3 * r]);
-            if (!std::isfinite(be.real()) || !std::isfinite(be.imag()))
-                return ctx->fail(DDA_ERR_NONFINITE, "polarizability of composition %d is not finite", c);
-            beta[(size_t)r * BS + c] = ccast<C>(make_double2(be.real(), be.imag()));
-        }
-    }
+    std::vector<cd> bt;
+    dda_status ts;
+    if ((ts = diag_tables(ctx, R, k, ev, bt, nullptr)) != DDA_OK) return ts;
+    std::vector<C> beta(bt.size());
+    for (size_t i = 0; i < bt.size(); ++i) beta[i] = ccast<C>(make_double2(bt[i].real(), bt[i].imag()));
     C* d_beta = reinterpret_cast<C*>(base);
     PadWork<T> w{reinterpret_cast<C*>(base + beta_bytes), reinterpret_cast<C*>(base + beta_bytes + u1_bytes)};
+    w.beta_tensor = ctx->aniso;
     CU(cudaMemcpyAsync(d_beta, beta.data(), beta.size() * sizeof(C), cudaMemcpyHostToDevice, ctx->stream));
     dda_status zs;
     if ((zs = pick_schedule<T>(ctx, R, false, &w.zvar, &w.slices)) != DDA_OK) return zs;  // no timing here
@@ -899,6 +964,24 @@ dda_status matvec_noalloc(dda_ctx* ctx, int R, const std::vector<double>& k, con
                         ghat_of<T>(ctx), tw_of<T>(ctx), nullptr, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     return DDA_OK;
+}
+}  // namespace
+
+namespace {
+// Switch between the scalar and the tensor 1/alpha tables: the cached
+// schedules (slice passes) and the captured solve graph depend on it.
+void set_isotropy(dda_ctx* ctx, bool aniso) {
+    if (ctx->aniso == aniso) return;
+    ctx->aniso = aniso;
+    if (!aniso) {
+        ctx->m3.clear();
+        ctx->df_angles.clear();
+    }
+    ctx->zsched.clear();
+    if (ctx->graph.exec) {
+        cudaGraphExecDestroy(ctx->graph.exec);
+        ctx->graph.exec = nullptr;
+    }
 }
 }  // namespace
 
@@ -1033,6 +1116,42 @@ dda_status dda_set_materials(dda_ctx* ctx, int ncomp, const double* m_complex, d
     }
     ctx->m = m;
     ctx->m_amb = m_ambient;
+    set_isotropy(ctx, false);
+    ctx->has_materials = true;
+    ctx->prepared = false;
+    ctx->has32 = false;
+    return DDA_OK;
+}
+
+dda_status dda_set_anisotropic_materials(dda_ctx* ctx, int ncomp, const double* m_principal,
+                                         const double* df_angles, double m_ambient) {
+    if (!ctx) return DDA_ERR_ARG;
+    if (ncomp <= 0 || ncomp > 255 || m_principal == nullptr || df_angles == nullptr)
+        return ctx->fail(DDA_ERR_ARG, "bad ncomp or NULL indices/angles");
+    if (!(m_ambient > 0.0) || !std::isfinite(m_ambient)) return ctx->fail(DDA_ERR_ARG, "ambient index must be > 0");
+    std::vector<std::array<cd, 3>> m3(ncomp);
+    std::vector<std::array<double, 3>> ang(ncomp);
+    for (int c = 0; c < ncomp; ++c) {
+        for (int j = 0; j < 3; ++j) {
+            const cd mj(m_principal[6 * c + 2 * j], m_principal[6 * c + 2 * j + 1]);
+            if (!std::isfinite(mj.real()) || !std::isfinite(mj.imag()))
+                return ctx->fail(DDA_ERR_NONFINITE, "refractive index %d of composition %d is not finite", j + 1, c + 1);
+            const cd mr = mj / m_ambient;
+            if (std::abs(mr * mr - 1.0) == 0.0)
+                return ctx->fail(DDA_ERR_ARG, "principal index %d of composition %d matches the ambient medium", j + 1,
+                                 c + 1);
+            m3[c][j] = mj;
+            ang[c][j] = df_angles[3 * c + j];
+            if (!std::isfinite(ang[c][j]))
+                return ctx->fail(DDA_ERR_NONFINITE, "dielectric-frame angle of composition %d is not finite", c + 1);
+        }
+    }
+    ctx->m.resize(ncomp);
+    for (int c = 0; c < ncomp; ++c) ctx->m[c] = m3[c][0];
+    ctx->m3 = m3;
+    ctx->df_angles = ang;
+    ctx->m_amb = m_ambient;
+    set_isotropy(ctx, true);
     ctx->has_materials = true;
     ctx->prepared = false;
     ctx->has32 = false;
@@ -1740,6 +1859,8 @@ dda_status dda_grad_qabs(dda_ctx* ctx, dda_precision precision, const double* kh
     if (!ctx) return DDA_ERR_ARG;
     ProfScope prof_scope(ctx);
     if (!dq_dre_eps || !dq_dim_eps || !res) return ctx->fail(DDA_ERR_ARG, "NULL output");
+    if (ctx->aniso)
+        return ctx->fail(DDA_ERR_ARG, "the gradient is defined for isotropic materials (one eps per site)");
     cudaSetDevice(ctx->device);
     dda_status st = forward_solve(ctx, precision, 1, khat, e, opts, &res[0]);
     if (st != DDA_OK) return st;

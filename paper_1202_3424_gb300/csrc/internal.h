@@ -53,6 +53,11 @@ template <typename T> struct PadWork {
     cx<T>* u2 = nullptr;  // [R][3][nz][Ly][Lx]
     int zvar = 0;         // z-pass schedule, see zconv_schedules
     int slices = 1;       // fused x+y slice passes where built (see slice_passes)
+    // The 1/alpha table holds 3x3 tensors (anisotropic materials): per RHS
+    // [3 rows c][comp][3 columns], so row c of composition comp's tensor is at
+    // beta[r*beta_stride + c*(beta_stride/3) + comp*3].  The slice passes
+    // handle only the isotropic table and are skipped.
+    bool beta_tensor = false;
 };
 
 int pick_fft_length(int n);  // smallest supported length >= 2n, or 0
@@ -109,8 +114,9 @@ cudaError_t launch_matvec_fused(const Geom& g, int R, cx<T>* x, cx<T>* y, const 
                                 const Twiddles<T>& tw, int* active, const FusedKrylov<T>& fk, cudaStream_t st);
 
 // y = A x for R right-hand sides, vectors [R][3][N].  beta[r*beta_stride + comp]
-// is 1/alpha of composition comp for RHS r.  active (nullable): RHS r is
-// skipped when active[r] == 0.
+// is 1/alpha of composition comp for RHS r (or, with w.beta_tensor, the rows
+// of its 1/alpha tensor, see PadWork).  active (nullable): RHS r is skipped
+// when active[r] == 0.
 template <typename T>
 cudaError_t launch_matvec(const Geom& g, int R, const cx<T>* x, cx<T>* y, const PadWork<T>& w,
                           const DevTarget& tg, const cx<T>* beta, int beta_stride, const cx<T>* ghat,

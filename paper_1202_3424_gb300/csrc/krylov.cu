@@ -278,11 +278,14 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// sums[r] = ( sum_j Im(E_j^* . P_j),  sum_j w(comp_j) |P_j|^2 )
+// sums[r] = ( sum_j Im(E_j^* . P_j),  sum_j w(comp_j) |P_j|^2 ), or with
+// tensor weights (anisotropic 1/alpha tensors B) the quadratic form
+// sum_j Im(P_j . B^* P_j^*) - (2/3) k^3 |P_j|^2 written with six real weights
+// per composition: w0..w2 |P_a|^2 + w3 Re(P_x P_y^*) + w4 Re(P_x P_z^*) + w5 Re(P_y P_z^*).
 __global__ void __launch_bounds__(kThreads)
     k_qsums(int64_t N, const double2* __restrict__ E, const double2* __restrict__ P, const uint8_t* __restrict__ comp_of,
-            const double* __restrict__ w, int w_stride, double2* __restrict__ sums, double2* __restrict__ part,
-            unsigned* __restrict__ cnt) {
+            const double* __restrict__ w, int w_stride, bool tensor, double2* __restrict__ sums,
+            double2* __restrict__ part, unsigned* __restrict__ cnt) {
     const int r = blockIdx.y;
     const double2* Er = E + (int64_t)r * 3 * N;
     const double2* Pr = P + (int64_t)r * 3 * N;
@@ -290,14 +293,26 @@ __global__ void __launch_bounds__(kThreads)
     double2 acc[1] = {make_double2(0.0, 0.0)};
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
         double im = 0.0, p2 = 0.0;
+        double2 pv[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const double2 ev = Er[c * N + j], pv = Pr[c * N + j];
-            im += ev.x * pv.y - ev.y * pv.x;
-            p2 += pv.x * pv.x + pv.y * pv.y;
+            const double2 ev = Er[c * N + j];
+            pv[c] = Pr[c * N + j];
+            im += ev.x * pv[c].y - ev.y * pv[c].x;
+            p2 += pv[c].x * pv[c].x + pv[c].y * pv[c].y;
         }
         acc[0].x += im;
-        acc[0].y += wr[comp_of[j]] * p2;
+        if (tensor) {
+            const double* wt = wr + comp_of[j] * 6;
+            double q = 0.0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) q += wt[c] * (pv[c].x * pv[c].x + pv[c].y * pv[c].y);
+            q += wt[3] * (pv[0].x * pv[1].x + pv[0].y * pv[1].y) + wt[4] * (pv[0].x * pv[2].x + pv[0].y * pv[2].y) +
+                 wt[5] * (pv[1].x * pv[2].x + pv[1].y * pv[2].y);
+            acc[0].y += q;
+        } else {
+            acc[0].y += wr[comp_of[j]] * p2;
+        }
     }
     if (last_block_total<1>(acc, part + (int64_t)r * gridDim.x, cnt + r) && threadIdx.x == 0) sums[r] = acc[0];
 }
@@ -500,9 +515,9 @@ template cudaError_t launch_scatter_sites<double2>(int, int64_t, int64_t, const 
 template cudaError_t launch_negate_c128<float2>(int64_t, const float2*, double2*, cudaStream_t);
 template cudaError_t launch_negate_c128<double2>(int64_t, const double2*, double2*, cudaStream_t);
 cudaError_t launch_qsums(int R, int64_t N, const double2* E, const double2* P, const uint8_t* comp_of, const double* w,
-                         int w_stride, double2* sums, double2* part, unsigned* cnt, cudaStream_t s) {
+                         int w_stride, bool tensor, double2* sums, double2* part, unsigned* cnt, cudaStream_t s) {
     PROF_BEGIN(s);
-    k_qsums<<<dim3(reduce_blocks(N), R), kThreads, 0, s>>>(N, E, P, comp_of, w, w_stride, sums, part, cnt);
+    k_qsums<<<dim3(reduce_blocks(N), R), kThreads, 0, s>>>(N, E, P, comp_of, w, w_stride, tensor, sums, part, cnt);
     PROF_END(KK_QSUMS, R, s);
     return cudaGetLastError();
 }

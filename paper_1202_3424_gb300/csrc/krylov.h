@@ -64,7 +64,7 @@ cudaError_t launch_scatter_sites(int R, int64_t N, int64_t Ne, const int* box_of
                                  cudaStream_t s);
 template <typename C> cudaError_t launch_negate_c128(int64_t n, const C* y, double2* out, cudaStream_t s);
 cudaError_t launch_qsums(int R, int64_t N, const double2* E, const double2* P, const uint8_t* comp_of, const double* w,
-                         int w_stride, double2* sums, double2* part, unsigned* cnt, cudaStream_t s);
+                         int w_stride, bool tensor, double2* sums, double2* part, unsigned* cnt, cudaStream_t s);
 cudaError_t launch_adjoint_rhs(int64_t N, const double2* P, const uint8_t* comp_of, const double* w, double2* b,
                                cudaStream_t s);
 cudaError_t launch_grad(int64_t N, const double2* P, const double2* nu, const uint8_t* comp_of, const double2* dbeta,

@@ -189,11 +189,14 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
 }
 
 // ---- x-inverse: row IFFT + diagonal + scatter -----------------------------------
-// Y = conv + (1/alpha) X at the occupied sites.  Fused BiCGstab reductions
+// Y = conv + (1/alpha) X at the occupied sites.  With TENSOR the block of
+// component c adds row c of the site's 1/alpha tensor times all three
+// components of X (layout in PadWork::beta_tensor); a separate instantiation
+// so that the isotropic kernel keeps its registers.  Fused BiCGstab reductions
 // (FP64 totals per RHS over all blocks of that RHS, finalized by the last one):
 //   MODE 1  Y = v:  sigma = <rhat, v>          ->  alpha = rho / sigma
 //   MODE 2  Y = t:  <t, s>, <t, t> with X = s  ->  omega
-template <typename T, int LX, int MODE>
+template <typename T, int LX, int MODE, bool TENSOR>
 __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(cx<T>)>::NT,
                                    xinv_min_blocks<LX, sizeof(cx<T>)>())
     k_xinv(const cx<T>* __restrict__ U1, cx<T>* __restrict__ Y, const cx<T>* __restrict__ X,
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
     const int64_t off = ((int64_t)r * 3 + c) * N;
     const C* xs = X + off;
     C* ys = Y + off;
-    const C* br = beta + (int64_t)r * beta_stride;
+    const C* br = beta + (int64_t)r * beta_stride + (TENSOR ? c * (beta_stride / 3) : 0);
     // All global loads are issued up front: the rows to transform, then the
     // site indices and, behind them, the operands of the diagonal term, whose
     // latency the transform hides.
@@ -251,7 +254,7 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
             if constexpr (MODE == 1) kh[i] = czero<C>();
             if (s >= 0) {
                 xv[i] = xs[s];
-                bv[i] = br[comp_of[s]];
+                bv[i] = TENSOR ? br[comp_of[s] * 3 + c] : br[comp_of[s]];
                 if constexpr (MODE == 1) kh[i] = krhat[off + s];
             }
         }
@@ -275,7 +278,13 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
         const int e = threadIdx.x + i * NTH, t2 = e / NX, ix = e - t2 * NX;
         const int s = sidx[i];
         if (s >= 0) {
-            const C yv = cadd(buf[ix * SP + t2], cmul(bv[i], xv[i]));
+            C yv = cadd(buf[ix * SP + t2], cmul(bv[i], xv[i]));
+            if constexpr (TENSOR) {  // the two off-diagonal entries of row c
+                const C* bb = br + comp_of[s] * 3;
+                const int c1 = c == 0 ? 1 : 0, c2 = c == 2 ? 1 : 2;
+                const C* xr = X + (int64_t)r * 3 * N;
+                yv = cadd(yv, cadd(cmul(bb[c1], xr[c1 * N + s]), cmul(bb[c2], xr[c2 * N + s])));
+            }
             ys[s] = yv;
             if constexpr (MODE == 1) d[0].add_cdot(kh[i], yv);
             if constexpr (MODE == 2) {
@@ -669,35 +678,45 @@ template <typename T> struct LaunchX {
         PROF_END(KK_XFWD_C64 + koff, R, st);
         return cudaGetLastError();
     }
-    template <int LX>
-    static cudaError_t inv(const Geom& g, int R, const cx<T>* u1, cx<T>* y, const cx<T>* x, const DevTarget& tg,
-                           const cx<T>* beta, int beta_stride, const cx<T>* tw, int* active,
-                           const FusedKrylov<T>& fk, cudaStream_t st) {
+    template <int LX, int MODE, bool TENSOR>
+    static cudaError_t inv_mode(const Geom& g, int R, const cx<T>* u1, cx<T>* y, const cx<T>* x, const DevTarget& tg,
+                                const cx<T>* beta, int beta_stride, const cx<T>* tw, int* active,
+                                const FusedKrylov<T>& fk, cudaStream_t st) {
         constexpr int TP = tp_x<LX, sizeof(cx<T>)>(), NTH = TP * XPlan<LX, sizeof(cx<T>)>::NT;
         const size_t sm = (size_t)LX * (TP + 1) * sizeof(cx<T>);
         const int nrows = g.ny * g.nz;
         dim3 grid((nrows + TP - 1) / TP, 3, R);
         cudaError_t e;
+        if ((e = allow_smem(k_xinv<T, LX, MODE, TENSOR>, sm)) != cudaSuccess) return e;
+        if constexpr (MODE == 0)
+            k_xinv<T, LX, 0, TENSOR><<<grid, NTH, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride,
+                                                           nrows, g.N, tw, active, nullptr, nullptr, nullptr,
+                                                           nullptr, 0);
+        else
+            k_xinv<T, LX, MODE, TENSOR><<<grid, NTH, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride,
+                                                              nrows, g.N, tw, active, fk.rhat, fk.st, fk.part,
+                                                              fk.cnt, fk.part_stride);
+        return cudaGetLastError();
+    }
+    template <int LX>
+    static cudaError_t inv(const Geom& g, int R, const cx<T>* u1, cx<T>* y, const cx<T>* x, const DevTarget& tg,
+                           const cx<T>* beta, int beta_stride, bool tensor, const cx<T>* tw, int* active,
+                           const FusedKrylov<T>& fk, cudaStream_t st) {
+        auto run = [&](auto mode) {
+            constexpr int M = decltype(mode)::value;
+            return tensor ? inv_mode<LX, M, true>(g, R, u1, y, x, tg, beta, beta_stride, tw, active, fk, st)
+                          : inv_mode<LX, M, false>(g, R, u1, y, x, tg, beta, beta_stride, tw, active, fk, st);
+        };
+        cudaError_t e = cudaSuccess;
         PROF_BEGIN(st);
         if (fk.mode == 0 || kDouble) {
-            if ((e = allow_smem(k_xinv<T, LX, 0>, sm)) != cudaSuccess) return e;
-            k_xinv<T, LX, 0><<<grid, NTH, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride, nrows, g.N,
-                                                   tw, active, nullptr, nullptr, nullptr, nullptr, 0);
+            e = run(std::integral_constant<int, 0>{});
         } else if constexpr (!kDouble) {
-            if (fk.mode == 1) {
-                if ((e = allow_smem(k_xinv<T, LX, 1>, sm)) != cudaSuccess) return e;
-                k_xinv<T, LX, 1><<<grid, NTH, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride, nrows,
-                                                       g.N, tw, active, fk.rhat, fk.st, fk.part, fk.cnt,
-                                                       fk.part_stride);
-            } else {
-                if ((e = allow_smem(k_xinv<T, LX, 2>, sm)) != cudaSuccess) return e;
-                k_xinv<T, LX, 2><<<grid, NTH, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride, nrows,
-                                                       g.N, tw, active, fk.rhat, fk.st, fk.part, fk.cnt,
-                                                       fk.part_stride);
-            }
+            e = fk.mode == 1 ? run(std::integral_constant<int, 1>{}) : run(std::integral_constant<int, 2>{});
         }
+        if (e != cudaSuccess) return e;
         PROF_END(KK_XINV_C64 + koff, R, st);
-        return cudaGetLastError();
+        return cudaSuccess;
     }
     template <int MODE, int L>
     static cudaError_t strided_mode(const cx<T>* src, cx<T>* dst, int64_t pt_stride, int width, int64_t sb,
@@ -787,9 +806,10 @@ cudaError_t launch_matvec_fused(const Geom& g, int R, cx<T>* x, cx<T>* y, const 
         DDA_DISPATCH_L(g.Lz, LX::template zconv, g, R, w.u2, ghat, tw.z, active, w.zvar, st);
     };
     auto invx = [&]() -> cudaError_t {
-        DDA_DISPATCH_L(g.Lx, LX::template inv, g, R, w.u1, y, x, tg, beta, beta_stride, tw.x, active, fk, st);
+        DDA_DISPATCH_L(g.Lx, LX::template inv, g, R, w.u1, y, x, tg, beta, beta_stride, w.beta_tensor, tw.x, active,
+                       fk, st);
     };
-    if (w.slices && slice_passes<T>(g)) {
+    if (w.slices && !w.beta_tensor && slice_passes<T>(g)) {
         if ((e = launch_slice_fwd<T>(g, R, x, w.u2, tg.site_of, tw, active, fk, st)) != cudaSuccess) return e;
         if ((e = zc()) != cudaSuccess) return e;
         return launch_slice_inv<T>(g, R, w.u2, y, x, tg, beta, beta_stride, tw, active, fk, st);

@@ -61,6 +61,9 @@ def parse():
                     help="matvec: only time dda_matvec_device (for profiler captures)")
     ap.add_argument("--rhs", type=int, default=0, help="matvec mode: RHS per product (0 = workload's)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="matvec mode precision")
+    ap.add_argument("--aniso", action="store_true",
+                    help="solve/matvec modes: anisotropic version of the workload's materials (principal indices "
+                         "m x (1, 1.05, 0.95), dielectric frame rotated by (0.4, 1.1, -0.6) rad)")
     ap.add_argument("--zpass", type=int, default=-1, choices=[-1, 0, 1],
                     help="complex64 z-pass schedule: -1 autotuned (default), 0 component groups, "
                          "1 register-resident (forcing one makes profiler runs reproduce the tuned choice)")
@@ -258,7 +261,7 @@ def run_gb300(args):
     stream = torch.cuda.current_stream(dev)
     dda.dda_set_stream(ctx.handle, stream.cuda_stream)
     ctx.set_target(w.grid)
-    ctx.set_materials(w.m)
+    set_materials(ctx, w, args.aniso)
     t0 = time.perf_counter()
     ctx.prepare_size_parameter(w.x, dda.Precision.FP32_REFINED)
     prepare_ms = (time.perf_counter() - t0) * 1e3
@@ -379,7 +382,7 @@ def run_gb300(args):
             "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64 matvec / f64 refinement", "data": "synthetic",
             "config": {"workload": f"{w.name}: lattice {info['nx']}x{info['ny']}x{info['nz']}, N={N} dipoles, "
-                                   f"m={w.m}, x={w.x}, {R} RHS, tol 1e-5",
+                                   f"{materials_note(w, args.aniso)}, x={w.x}, {R} RHS, tol 1e-5",
                        "global_batch": R * world, "padded_grid": [info["Lx"], info["Ly"], info["Lz"]],
                        "parallelism": f"rhs-sharded x{world}", "l2": "256 MB buffer written between steps"},
             "time_to_solution_ms": ms_per_step,
@@ -502,6 +505,26 @@ def _oracle_rows_rate(w, budget_s, kd):
     return nrows / dt, nrows, N, nt, dt
 
 
+ANISO_FACTORS = (1.0, 1.05, 0.95)
+ANISO_ANGLES = (0.4, 1.1, -0.6)
+
+
+def set_materials(ctx, w, aniso):
+    """The workload's materials, or (aniso) a biaxial material per composition
+    with principal indices m * ANISO_FACTORS in a dielectric frame rotated by
+    ANISO_ANGLES."""
+    if aniso:
+        ctx.set_anisotropic_materials([[m * f for f in ANISO_FACTORS] for m in w.m], [ANISO_ANGLES] * len(w.m))
+    else:
+        ctx.set_materials(w.m)
+
+
+def materials_note(w, aniso):
+    if not aniso:
+        return f"m={w.m}"
+    return f"anisotropic: m x {ANISO_FACTORS} along the dielectric axes, (theta,phi,beta)_DF={ANISO_ANGLES}, m={w.m}"
+
+
 def cpu_baseline(w, info, budget_s=12.0):
     rate, nrows, N, nt, dt = _oracle_rows_rate(w, budget_s, info["kd"])
     return {"value": rate / N, "unit": UNIT, "cores": nt, "kind": "oracle",
@@ -544,7 +567,7 @@ def run_matvec_only(args):
     R = args.rhs or w.nrhs
     ctx = dda.Context(0)
     ctx.set_target(w.grid)
-    ctx.set_materials(w.m)
+    set_materials(ctx, w, args.aniso)
     ctx.prepare_size_parameter(w.x, dda.Precision.FP32_REFINED)
     ctx.set_schedule(args.zpass)
     N = ctx.info()["ndipoles"]

@@ -230,6 +230,76 @@ def bicgstab(matvec, b: np.ndarray, tol: float, maxit: int, x0=None):
     return x, it, nmv, relres
 
 
+def bicgstab_l(matvec, b: np.ndarray, tol: float, maxit: int, ell: int = 2, x0=None, trace=None):
+    """BiCGstab(l) (Sleijpen & Fokkema 1993; the guide's PBCGS2 is Botchev's
+    ZBCG2 implementation of it, "Choice of Iterative Algorithm") for complex
+    A x = b, unpreconditioned, shadow residual rt = r0.
+
+    One iteration is l BiCG steps (2l matvecs) followed by a minimal-residual
+    polynomial step of degree l over the residuals r_1..r_l, orthogonalized by
+    modified Gram-Schmidt.  Inner products are Hermitian, (a, c) = c^H a.
+    Stops when the recurrence residual ||r_0|| <= tol ||b||.  With a list as
+    `trace`, each iteration appends (r_0 after the MR step, the orthogonalized
+    r_1..r_l).  Returns (x, iterations, matvecs, relres).
+    """
+    b = np.asarray(b, dtype=np.complex128).ravel()
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.complex128).ravel()
+    r = [b - matvec(x) if x0 is not None else b.copy()] + [None] * ell
+    nmv = 1 if x0 is not None else 0
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return x, 0, nmv, 0.0
+    rt = r[0].copy()
+    u = [np.zeros_like(b)] + [None] * ell
+    rho0, alpha, omega = 1.0 + 0j, 0.0 + 0j, 1.0 + 0j
+    relres = np.linalg.norm(r[0]) / bnorm
+    it = 0
+    while relres > tol and it < maxit:
+        rho0 = -omega * rho0
+        for j in range(ell):                       # BiCG part
+            rho1 = np.vdot(rt, r[j])
+            beta = alpha * rho1 / rho0
+            rho0 = rho1
+            for i in range(j + 1):
+                u[i] = r[i] - beta * u[i]
+            u[j + 1] = matvec(u[j])
+            alpha = rho0 / np.vdot(rt, u[j + 1])
+            for i in range(j + 1):
+                r[i] = r[i] - alpha * u[i + 1]
+            r[j + 1] = matvec(r[j])
+            x = x + alpha * u[0]
+            nmv += 2
+        tau = np.zeros((ell + 1, ell + 1), dtype=np.complex128)   # MR part (modified Gram-Schmidt)
+        sigma = np.zeros(ell + 1)
+        gp = np.zeros(ell + 1, dtype=np.complex128)                # gamma'
+        for j in range(1, ell + 1):
+            for i in range(1, j):
+                tau[i, j] = np.vdot(r[i], r[j]) / sigma[i]
+                r[j] = r[j] - tau[i, j] * r[i]
+            sigma[j] = np.vdot(r[j], r[j]).real
+            gp[j] = np.vdot(r[j], r[0]) / sigma[j]
+        g = np.zeros(ell + 1, dtype=np.complex128)                 # gamma
+        g[ell] = gp[ell]
+        omega = g[ell]
+        for j in range(ell - 1, 0, -1):
+            g[j] = gp[j] - sum(tau[j, i] * g[i] for i in range(j + 1, ell + 1))
+        gpp = np.zeros(ell + 1, dtype=np.complex128)               # gamma''
+        for j in range(1, ell):
+            gpp[j] = g[j + 1] + sum(tau[j, i] * g[i + 1] for i in range(j + 1, ell))
+        x = x + g[1] * r[0]
+        r[0] = r[0] - gp[ell] * r[ell]
+        u[0] = u[0] - g[ell] * u[ell]
+        for j in range(1, ell):
+            u[0] = u[0] - g[j] * u[j]
+            x = x + gpp[j] * r[j]
+            r[0] = r[0] - gp[j] * r[j]
+        it += 1
+        relres = np.linalg.norm(r[0]) / bnorm
+        if trace is not None:
+            trace.append([v.copy() for v in r])
+    return x, it, nmv, relres
+
+
 def normal_equation_error(matvec, P: np.ndarray, E: np.ndarray) -> float:
     """|A^H A P - A^H E| / |A^H E| (eq. err_tol).  Uses A^H x = conj(A conj(x)),
     valid because A = A^T."""

@@ -4,7 +4,9 @@ Every mutation is applied with monkeypatch to the oracle only (CPU); the
 pins are the functions of tests/test_oracle_pins.py.  A mutation that no pin
 catches would mean that part of the oracle is not pinned.
 """
+import inspect
 import math
+import textwrap
 
 import numpy as np
 import pytest
@@ -25,6 +27,17 @@ _orig_ff = dda.far_field
 _orig_dirs = dda.scattering_directions
 _orig_mueller = dda.mueller_matrix
 _orig_frame = dda.dielectric_frame
+
+
+def _mutant(fn, old, new):
+    """fn recompiled from its source with one statement changed."""
+    src = textwrap.dedent(inspect.getsource(fn))
+    assert src.count(old) == 1, old
+    ns = dict(vars(inspect.getmodule(fn)))
+    exec(compile(src.replace(old, new), inspect.getsourcefile(fn), "exec"), ns)
+    out = ns[fn.__name__]
+    out.__name__ = f"{fn.__name__}: {new.strip()}"
+    return out
 
 
 def _tensor_sign(rvec, kd):            # (1 - ik rho) instead of (ik rho - 1)
@@ -154,6 +167,14 @@ MUTATIONS = [
     ("mueller_matrix", _mueller_s34_sign, [pins.mueller_sphere_vs_mie_error]),
     ("dielectric_frame", _frame_e3_sign, [pins.dielectric_frame_error]),
     ("cross_sections", _xs_tensor_unconjugated, [pins.anisotropic_energy_balance_error]),
+    ("bicgstab_l", _mutant(dda.bicgstab_l, "r[0] = r[0] - gp[ell] * r[ell]", "r[0] = r[0] + gp[ell] * r[ell]"),
+     [pins.bicgstab_l2_mr_error]),
+    ("bicgstab_l", _mutant(dda.bicgstab_l, "tau[i, j] = np.vdot(r[i], r[j]) / sigma[i]",
+                           "tau[i, j] = np.dot(r[i], r[j]) / sigma[i]"), [pins.bicgstab_l2_mr_error]),
+    ("bicgstab_l", _mutant(dda.bicgstab_l, "beta = alpha * rho1 / rho0", "beta = alpha * rho1 / abs(rho0)"),
+     [pins.bicgstab_l1_vs_bicgstab_error, pins.bicgstab_l2_mr_error]),
+    ("bicgstab_l", _mutant(dda.bicgstab_l, "x = x + gpp[j] * r[j]", "x = x - gpp[j] * r[j]"),
+     [pins.bicgstab_l2_mr_error]),
 ]
 
 

@@ -324,6 +324,44 @@ def anisotropic_reduction_error(kd=0.45):
     return err
 
 
+def _random_complex_symmetric(n=60, seed=1):
+    rng = np.random.default_rng(seed)
+    A = 3.0 * np.eye(n) + 0.3 * (rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n)))
+    b = rng.normal(size=n) + 1j * rng.normal(size=n)
+    return A + A.T, b
+
+
+def bicgstab_l1_vs_bicgstab_error():
+    """BiCGstab(1) builds the same iterates as BiCGstab (Sleijpen & Fokkema
+    1993): the first five iterates of the two independent codes agree."""
+    A, b = _random_complex_symmetric()
+    err = 0.0
+    for k in range(1, 6):
+        x1, _, _, _ = dda.bicgstab(lambda v: A @ v, b, 0.0, k)
+        x2, _, n2, _ = dda.bicgstab_l(lambda v: A @ v, b, 0.0, k, ell=1)
+        err = max(err, float(np.abs(x1 - x2).max() / np.abs(x1).max()), abs(n2 - 2 * k))
+    return err
+
+
+def bicgstab_l2_mr_error():
+    """BiCGstab(2): after each minimal-residual step the new r_0 is orthogonal
+    to the orthogonalized r_1, r_2 (which are orthogonal to each other), and
+    the iteration reaches the LU solution of a DDA system."""
+    A, b = _random_complex_symmetric()
+    tr = []
+    dda.bicgstab_l(lambda v: A @ v, b, 1e-12, 200, ell=2, trace=tr)
+    cos = lambda a, c: abs(np.vdot(a, c)) / (np.linalg.norm(a) * np.linalg.norm(c))  # noqa: E731
+    err = max(max(cos(t[1], t[0]), cos(t[2], t[0]), cos(t[1], t[2])) for t in tr[:-1])
+    r = _small_cluster(6, 40)
+    kd = 0.7
+    beta = dda.ldr_inverse_polarizability(np.full(len(r), 2.4 + 0.6j), kd, [1, 0, 0], [0, 1, 0])
+    M = dda.dense_matrix(r, kd, beta)
+    E = dda.incident_field(r, kd, [1, 0, 0], [0, 1, 0]).ravel()
+    x, it, nmv, rel = dda.bicgstab_l(lambda v: M @ v, E, 1e-13, 300, ell=2)
+    xs = np.linalg.solve(M, E)
+    return max(err, float(np.abs(x - xs).max() / np.abs(xs).max()), abs(nmv - 4 * it))
+
+
 # ------------------------------------------------------------------- tests --
 def test_pseudosphere_counts_match_guide(golden_dir):
     for box, diam, count, *_ in _golden_rows(os.path.join(golden_dir, "pseudosphere_counts.txt")):
@@ -675,3 +713,11 @@ def test_anisotropic_matrix_is_complex_symmetric():
     P = random_complex((len(r), 3), 2)
     y = dda.pairwise_matvec(r, 0.4, B, P)
     assert np.abs(y.ravel() - A @ P.ravel()).max() < 1e-13 * np.abs(y).max()
+
+
+def test_bicgstab_l1_reproduces_bicgstab():
+    assert bicgstab_l1_vs_bicgstab_error() < 1e-12
+
+
+def test_bicgstab_l2_minimal_residual_and_solution():
+    assert bicgstab_l2_mr_error() < 1e-11

@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--aniso", action="store_true",
                     help="solve/matvec modes: anisotropic version of the workload's materials (principal indices "
                          "m x (1, 1.05, 0.95), dielectric frame rotated by (0.4, 1.1, -0.6) rad)")
+    ap.add_argument("--solver", default="bicgstab", choices=["bicgstab", "bicgstab2"],
+                    help="solve mode: BiCGstab (default) or BiCGstab(2), the guide's PBCGS2")
     ap.add_argument("--zpass", type=int, default=-1, choices=[-1, 0, 1],
                     help="complex64 z-pass schedule: -1 autotuned (default), 0 component groups, "
                          "1 register-resident (forcing one makes profiler runs reproduce the tuned choice)")
@@ -272,7 +274,8 @@ def run_gb300(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
     def step(prec, tol=1e-5):
-        res, st = dda.dda_solve_device(ctx.handle, prec, w.khat, w.ehat, P_dev, tol=tol, maxit=2000)
+        res, st = dda.dda_solve_device(ctx.handle, prec, w.khat, w.ehat, P_dev, tol=tol, maxit=2000,
+                                       solver=args.solver)
         if st != 0:
             raise RuntimeError(f"solve failed: {[r['status_name'] for r in res]}")
         return res
@@ -353,12 +356,12 @@ def run_gb300(args):
     if not args.no_e2e:
         k = np.ascontiguousarray(w.khat)
         e = np.ascontiguousarray(w.ehat)
-        ctx.solve(dda.Precision.FP32_REFINED, k, e, tol=1e-5, maxit=2000)
+        ctx.solve(dda.Precision.FP32_REFINED, k, e, tol=1e-5, maxit=2000, solver=args.solver)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         mv_e2e = 0
         for _ in range(args.steps):
-            r_e2e, P_host, st = ctx.solve(dda.Precision.FP32_REFINED, k, e, tol=1e-5, maxit=2000)
+            r_e2e, P_host, st = ctx.solve(dda.Precision.FP32_REFINED, k, e, tol=1e-5, maxit=2000, solver=args.solver)
             mv_e2e += sum(r["matvecs"] for r in r_e2e)
         torch.cuda.synchronize()
         t_e2e = max_over_ranks(dist, time.perf_counter() - t0, dev)
@@ -367,8 +370,10 @@ def run_gb300(args):
                "time_to_solution_ms": t_e2e * 1e3 / args.steps}
 
     roof = roofline(kstats, info, R, w.name)
-    # complex64 RHS-matvecs per traced step: 2 per BiCGstab iteration of every RHS
-    mv_roof = matvec_roofline(kstats, info, "c64", rhs_matvecs=len(per_tr) * sum(2 * r["iters"] for r in res)) \
+    # complex64 RHS-matvecs per traced step: 2 per BiCGstab (4 per BiCGstab(2)) iteration of every RHS
+    per_iter = 4 if args.solver == "bicgstab2" else 2
+    mv_roof = matvec_roofline(kstats, info, "c64",
+                              rhs_matvecs=len(per_tr) * sum(per_iter * r["iters"] for r in res)) \
         if kstats else None
     launches = int(sum(s["launches"] for s in kstats.values()) / args.steps) * args.steps if kstats else 0
 
@@ -382,7 +387,8 @@ def run_gb300(args):
             "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64 matvec / f64 refinement", "data": "synthetic",
             "config": {"workload": f"{w.name}: lattice {info['nx']}x{info['ny']}x{info['nz']}, N={N} dipoles, "
-                                   f"{materials_note(w, args.aniso)}, x={w.x}, {R} RHS, tol 1e-5",
+                                   f"{materials_note(w, args.aniso)}, x={w.x}, {R} RHS, tol 1e-5, "
+                                   f"{'BiCGstab(2)' if args.solver == 'bicgstab2' else 'BiCGstab'}",
                        "global_batch": R * world, "padded_grid": [info["Lx"], info["Ly"], info["Lz"]],
                        "parallelism": f"rhs-sharded x{world}", "l2": "256 MB buffer written between steps"},
             "time_to_solution_ms": ms_per_step,

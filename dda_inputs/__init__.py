@@ -18,7 +18,10 @@ example targets (ELLIPSOID, RCTGLPRSM; the guide's ``examples_exp`` files
 are not available): a 16^3 sphere, a 64^3 sphere, a 3:2:1 ellipsoid on a
 96x64x32 lattice with 64 seeded directions x 2 polarizations, a 48x48x24
 two-material block with a seeded Bernoulli composition, and a 256^3 sphere
-with 8 seeded directions x 2 polarizations.
+with 8 seeded directions x 2 polarizations.  Two more: ``aubrick32x64x64``,
+the guide's FROM_FILE sample (a full 32x64x64 Au block), and
+``spheroid64x64x256``, a small target with the 256^3 sphere's 512-point z
+transform.
 """
 from __future__ import annotations
 
@@ -148,6 +151,13 @@ def workload(name: str) -> Workload:
     if name == "sphere256":
         k, e = _sweep(8)
         return Workload(name, sphere_grid(256), [1.33 + 0.01j], 20.0, k, e, "fp32_refined")
+    if name == "aubrick32x64x64":
+        # the guide's FROM_FILE sample: a 0.5 x 1 x 1 micron Au block as a
+        # 32 x 64 x 64 array, m = 0.9656 + 1.8628i, lambda = 0.5 micron,
+        # aeff = 0.49237 micron (x = 2 pi aeff / lambda), k along the short axis
+        k, e = _k_along_x_two_pols()
+        return Workload(name, np.ones((64, 64, 32), np.uint8), [0.9656 + 1.8628j], 2 * np.pi * 0.49237 / 0.5, k, e,
+                        "fp32_refined")
     if name == "spheroid64x64x256":
         # profiler-capture stand-in for sphere256: its 128x128x512 padded grid
         # has the same 512-point z transform at 1/16 of the memory

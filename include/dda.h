@@ -78,7 +78,7 @@ typedef enum {
 
 typedef struct {
     double tol;        /* relative residual |E - A P| / |E| to reach (guide: TOL = 1e-5)     */
-    int maxit;         /* max BiCGstab iterations per RHS, summed over refinement steps     */
+    int maxit;         /* max Krylov iterations per RHS, summed over refinement steps       */
     int use_graph;     /* 1: replay the iteration block as a captured CUDA graph            */
     double inner_tol;  /* FP32_REFINED: floor of the inner (FP32) relative tolerance        */
     int max_outer;     /* max refinement (outer) steps; <= 0 selects 8                       */
@@ -87,7 +87,12 @@ typedef struct {
     int residual_fp64; /* complex64 modes: 1 = true residuals E - A P with native FP64
                           arithmetic; 0 (default) = double-float arithmetic (FP32 pipes,
                           ~1e-12 relative accuracy, 6-8x faster on GB300)                  */
+    int solver;        /* DDA_SOLVER_BICGSTAB (0, default): BiCGstab, 2 matvecs an iteration;
+                          DDA_SOLVER_BICGSTAB2 (1): BiCGstab(2) (guide: PBCGS2, "Choice of
+                          Iterative Algorithm"), 4 matvecs an iteration                     */
 } dda_opts;
+
+enum { DDA_SOLVER_BICGSTAB = 0, DDA_SOLVER_BICGSTAB2 = 1 };
 
 typedef struct {
     double qext, qabs, qsca;  /* efficiency factors                                         */

@@ -50,7 +50,7 @@ class DdaError(RuntimeError):
 class dda_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("normal_eq", ctypes.c_int),
-                ("x0", ctypes.POINTER(ctypes.c_double)), ("residual_fp64", ctypes.c_int)]
+                ("x0", ctypes.POINTER(ctypes.c_double)), ("residual_fp64", ctypes.c_int), ("solver", ctypes.c_int)]
 
 
 class dda_result(ctypes.Structure):
@@ -149,8 +149,11 @@ def _rhs(khat, e):
     return k, ev.view(np.float64).reshape(k.shape[0], 6).copy(), k.shape[0]
 
 
+SOLVERS = {"bicgstab": 0, "bicgstab2": 1}
+
+
 def _opts(tol=1e-5, maxit=1000, use_graph=True, inner_tol=0.0, max_outer=0, normal_eq=False, x0=None,
-          residual_fp64=False):
+          residual_fp64=False, solver="bicgstab"):
     o = dda_opts()
     o.tol = tol
     o.maxit = maxit
@@ -159,6 +162,9 @@ def _opts(tol=1e-5, maxit=1000, use_graph=True, inner_tol=0.0, max_outer=0, norm
     o.max_outer = max_outer
     o.normal_eq = 1 if normal_eq else 0
     o.residual_fp64 = 1 if residual_fp64 else 0
+    if solver not in SOLVERS:
+        raise ValueError(f"solver must be one of {sorted(SOLVERS)}")
+    o.solver = SOLVERS[solver]
     keep = None
     if x0 is not None:
         keep = np.ascontiguousarray(x0, dtype=np.complex128).view(np.float64)

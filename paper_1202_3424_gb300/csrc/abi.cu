@@ -35,9 +35,11 @@ struct DevMem {
     size_t bytes = 0;
 };
 
+// Inner-solve vectors.  BiCGstab: b, x, r, rhat, p, v, s, t.  BiCGstab(2)
+// keeps r0, r1, r2 in r, s, t and u0, u1, u2 in p, v, u2 (shadow residual rhat).
 template <typename T> struct Inner {
     cx<T>*b = nullptr, *x = nullptr, *r = nullptr, *rhat = nullptr, *p = nullptr, *v = nullptr, *s = nullptr,
-    *t = nullptr;
+    *t = nullptr, *u2 = nullptr;
 };
 
 struct GraphEntry {
@@ -46,6 +48,7 @@ struct GraphEntry {
     int R = 0;
     int prec = -1;
     int K = 0;
+    int solver = 0;
     cudaStream_t stream = nullptr;
 };
 
@@ -143,7 +146,7 @@ enum Slot {
     S_PART, S_CNT, S_QSUM, S_COUNT,
     S_BETA64, S_BETA32, S_W, S_KHAT, S_EPOL,
     S_MV_X32, S_MV_Y32, S_GRAD, S_DBETA,
-    S_BETADF, S_XDF, S_YDF, S_TUNE,
+    S_BETADF, S_XDF, S_YDF, S_TUNE, S_IN_U2,
     S_NSLOTS
 };
 
@@ -500,6 +503,7 @@ template <typename T> struct InnerSlots {
         in.v = slot<cx<T>>(ctx, S_IN_V);
         in.s = slot<cx<T>>(ctx, S_IN_S);
         in.t = slot<cx<T>>(ctx, S_IN_T);
+        in.u2 = slot<cx<T>>(ctx, S_IN_U2);
         return in;
     }
 };
@@ -508,7 +512,7 @@ template <typename T> struct InnerSlots {
 // reduction kernels (<= kMaxReduceBlocks blocks, 2 sums) and for the fused
 // x-inverse scatter (one partial per block of that pass, 2 sums).
 int partial_stride(const dda_ctx* ctx) {
-    return 2 * std::max(kMaxReduceBlocks, xinv_blocks_per_rhs(ctx->g));
+    return std::max(5 * kMaxReduceBlocks, 2 * xinv_blocks_per_rhs(ctx->g));  // 5 sums: BiCGstab(2) Gram step
 }
 
 // Matvec over R RHS in chunks with the BiCGstab updates of `mode` fused into
@@ -562,10 +566,46 @@ template <typename T> dda_status inner_iteration(dda_ctx* ctx, int R) {
     return DDA_OK;
 }
 
-template <typename T> dda_status inner_block(dda_ctx* ctx, int R, int K) {
+// One BiCGstab(2) iteration for every active RHS (bicgstab2.cu): two BiCG
+// steps and the degree-2 minimal-residual step, 4 plain matvecs.
+template <typename T> dda_status inner_iteration_b2(dda_ctx* ctx, int R) {
+    using Ops = KrylovOps<cx<T>>;
+    using B2 = BiCGstab2Ops<cx<T>>;
+    const int64_t n = 3 * ctx->g.N;
+    Inner<T> in = InnerSlots<T>::get(ctx);
+    cx<T>*r0 = in.r, *r1 = in.s, *r2 = in.t, *u0 = in.p, *u1 = in.v, *u2 = in.u2;
+    KState* st = slot<KState>(ctx, S_STATE);
+    int* act = slot<int>(ctx, S_ACTIVE);
+    double2* part = slot<double2>(ctx, S_PART);
+    unsigned* cnt = slot<unsigned>(ctx, S_CNT);
+    cudaStream_t s = ctx->stream;
     dda_status rs;
-    for (int k = 0; k < K; ++k)
-        if ((rs = inner_iteration<T>(ctx, R)) != DDA_OK) return rs;
+    CU(B2::u0(R, n, u0, r0, st, act, s));
+    if ((rs = run_matvec<T>(ctx, R, u0, u1, act)) != DDA_OK) return rs;
+    CU(Ops::alpha(R, n, in.rhat, u1, st, act, part, cnt, s));
+    CU(B2::r0(R, n, r0, u1, in.x, u0, st, act, s));
+    if ((rs = run_matvec<T>(ctx, R, r0, r1, act)) != DDA_OK) return rs;
+    CU(B2::rho(R, n, in.rhat, r1, st, act, part, cnt, s));
+    CU(B2::u1(R, n, u0, u1, r0, r1, st, act, s));
+    if ((rs = run_matvec<T>(ctx, R, u1, u2, act)) != DDA_OK) return rs;
+    CU(Ops::alpha(R, n, in.rhat, u2, st, act, part, cnt, s));
+    CU(B2::r1(R, n, r0, r1, u0, u1, u2, in.x, st, act, s));
+    if ((rs = run_matvec<T>(ctx, R, r1, r2, act)) != DDA_OK) return rs;
+    CU(B2::gram(R, n, r0, r1, r2, st, act, part, cnt, s));
+    CU(B2::mr(R, n, in.x, r0, r1, r2, u0, u1, u2, in.rhat, st, act, part, cnt, s));
+    return DDA_OK;
+}
+
+// Iterations per captured block: 8 matvecs per RHS for either solver.
+int block_iterations(int solver) { return solver == DDA_SOLVER_BICGSTAB2 ? 2 : 4; }
+int matvecs_per_iteration(int solver) { return solver == DDA_SOLVER_BICGSTAB2 ? 4 : 2; }
+
+template <typename T> dda_status inner_block(dda_ctx* ctx, int R, int K, int solver) {
+    dda_status rs;
+    for (int k = 0; k < K; ++k) {
+        rs = solver == DDA_SOLVER_BICGSTAB2 ? inner_iteration_b2<T>(ctx, R) : inner_iteration<T>(ctx, R);
+        if (rs != DDA_OK) return rs;
+    }
     CU(launch_count_active(slot<int>(ctx, S_ACTIVE), R, slot<int>(ctx, S_COUNT), ctx->stream));
     CU(cudaMemcpyAsync(ctx->h_count, ctx->pool[S_COUNT].p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     return DDA_OK;
@@ -574,18 +614,19 @@ template <typename T> dda_status inner_block(dda_ctx* ctx, int R, int K) {
 // Iterate until no RHS is active (the device decides convergence and maxit).
 // The first block of K iterations runs eagerly; with use_graph the block is
 // then captured once and replayed.
-template <typename T> dda_status inner_solve(dda_ctx* ctx, int R, int maxit, bool use_graph) {
-    const int K = 4;
+template <typename T> dda_status inner_solve(dda_ctx* ctx, int R, int maxit, bool use_graph, int solver) {
+    const int K = block_iterations(solver);
     const int prec = sizeof(T) == 4 ? 1 : 0;
     const int max_blocks = maxit / K + 2;
     dda_status rs;
     bool have_graph = ctx->graph.exec && ctx->graph.R == R && ctx->graph.prec == prec && ctx->graph.K == K &&
-                      ctx->graph.stream == ctx->stream && ctx->graph.traced == ctx->prof.on;
+                      ctx->graph.solver == solver && ctx->graph.stream == ctx->stream &&
+                      ctx->graph.traced == ctx->prof.on;
     for (int b = 0; b < max_blocks; ++b) {
         if (use_graph && have_graph) {
             CU(cudaGraphLaunch(ctx->graph.exec, ctx->stream));
             if (ctx->prof.on) ctx->prof.graph_launched();
-        } else if ((rs = inner_block<T>(ctx, R, K)) != DDA_OK) {
+        } else if ((rs = inner_block<T>(ctx, R, K, solver)) != DDA_OK) {
             return rs;
         }
         CU(sync_collect(ctx));
@@ -598,7 +639,7 @@ template <typename T> dda_status inner_solve(dda_ctx* ctx, int R, int maxit, boo
             cudaGraph_t graph = nullptr;
             ctx->prof.capture_begin();
             CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-            rs = inner_block<T>(ctx, R, K);
+            rs = inner_block<T>(ctx, R, K, solver);
             cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
             ctx->prof.capture_end();
             if (rs != DDA_OK) {
@@ -612,6 +653,7 @@ template <typename T> dda_status inner_solve(dda_ctx* ctx, int R, int maxit, boo
             ctx->graph.R = R;
             ctx->graph.prec = prec;
             ctx->graph.K = K;
+            ctx->graph.solver = solver;
             ctx->graph.stream = ctx->stream;
             ctx->graph.traced = ctx->prof.on;
             have_graph = true;
@@ -644,11 +686,12 @@ dda_status ensure_common(dda_ctx* ctx, int R) {
     return DDA_OK;
 }
 
-template <typename T> dda_status ensure_inner(dda_ctx* ctx, int R) {
+template <typename T> dda_status ensure_inner(dda_ctx* ctx, int R, int solver) {
     const size_t vb = (size_t)R * 3 * ctx->g.N * sizeof(cx<T>);
     dda_status s;
     for (int sl = S_IN_B; sl <= S_IN_T; ++sl)
         if ((s = ensure(ctx, ctx->pool[sl], vb)) != DDA_OK) return s;
+    if (solver == DDA_SOLVER_BICGSTAB2 && (s = ensure(ctx, ctx->pool[S_IN_U2], vb)) != DDA_OK) return s;
     return ensure_pad<T>(ctx, R);
 }
 
@@ -663,7 +706,7 @@ dda_status solve_core(dda_ctx* ctx, int R, const dda_opts& o, bool refine, bool 
     // refinement residuals of the complex64 modes in double-float unless FP64 is asked for
     const bool df_resid = (sizeof(T) == 4) && !o.residual_fp64 && ctx->m_ghdf.p != nullptr;
     if ((rs = ensure_common(ctx, R)) != DDA_OK) return rs;
-    if ((rs = ensure_inner<T>(ctx, R)) != DDA_OK) return rs;
+    if ((rs = ensure_inner<T>(ctx, R, o.solver)) != DDA_OK) return rs;
     if ((rs = ensure_pad<double>(ctx, R)) != DDA_OK) return rs;
     const size_t vb64 = (size_t)R * n * sizeof(double2);
     for (int sl : {S_X64, S_R64, S_Y64})
@@ -737,7 +780,7 @@ dda_status solve_core(dda_ctx* ctx, int R, const dda_opts& o, bool refine, bool 
         CU(KrylovOps<cx<T>>::to_inner(R, n, Rr, in.b, slot<double>(ctx, S_SCALE), outer, s));
         CU(KrylovOps<cx<T>>::init(R, n, in.b, in.x, in.r, in.rhat, in.p, in.v, slot<KState>(ctx, S_STATE),
                                   slot<double>(ctx, S_TOLREL), outer, slot<int>(ctx, S_ACTIVE), part, cnt, s));
-        if ((rs = inner_solve<T>(ctx, R, o.maxit, o.use_graph != 0)) != DDA_OK) return rs;
+        if ((rs = inner_solve<T>(ctx, R, o.maxit, o.use_graph != 0, o.solver)) != DDA_OK) return rs;
         CU(cudaMemcpyAsync(hst.data(), ctx->pool[S_STATE].p, R * sizeof(KState), cudaMemcpyDeviceToHost, s));
         CU(KrylovOps<cx<T>>::accumulate(R, n, X, in.x, slot<double>(ctx, S_COEF), outer, s));
         if ((rs = matvec64(ctx, R, X, Y, outer, df_resid)) != DDA_OK) return rs;
@@ -748,7 +791,7 @@ dda_status solve_core(dda_ctx* ctx, int R, const dda_opts& o, bool refine, bool 
             if (!hact[r]) continue;
             RhsTrack& t = tr[r];
             t.iters += hst[r].iter;
-            t.mv += 2 * hst[r].iter + 1;
+            t.mv += matvecs_per_iteration(o.solver) * hst[r].iter + 1;
             t.outer += 1;
             const double prev = t.rn;
             t.rn = std::sqrt(hr[r]);
@@ -807,6 +850,7 @@ dda_opts default_opts() {
     o.normal_eq = 0;
     o.x0 = nullptr;
     o.residual_fp64 = 0;
+    o.solver = DDA_SOLVER_BICGSTAB;
     return o;
 }
 
@@ -818,6 +862,8 @@ dda_status forward_solve(dda_ctx* ctx, dda_precision prec, int R, const double* 
     if (res == nullptr) return ctx->fail(DDA_ERR_ARG, "res must not be NULL");
     dda_opts o = opts_in ? *opts_in : default_opts();
     if (!(o.tol > 0.0) || o.maxit <= 0) return ctx->fail(DDA_ERR_ARG, "tol must be > 0 and maxit > 0");
+    if (o.solver != DDA_SOLVER_BICGSTAB && o.solver != DDA_SOLVER_BICGSTAB2)
+        return ctx->fail(DDA_ERR_ARG, "unknown solver %d", o.solver);
     std::vector<double> k;
     std::vector<cd> ev;
     if ((rs = check_rhs(ctx, R, khat, e, k, ev)) != DDA_OK) return rs;

@@ -14,6 +14,7 @@ struct KState {
     double2 alpha;
     double2 omega;
     double2 beta;   // coefficient of the next search-direction update
+    double2 gamma1; // BiCGstab(2): first minimal-residual coefficient (the second is omega)
     double bnorm;   // |b|
     double rnorm;   // recurrence residual |r|
     double tol_abs; // stop when rnorm <= tol_abs
@@ -44,6 +45,23 @@ template <typename C> struct KrylovOps {
                                 cudaStream_t s);
     static cudaError_t accumulate(int R, int64_t n, double2* x64, const C* xin, const double* coef,
                                   const int* active, cudaStream_t s);
+};
+
+// BiCGstab(2) steps (bicgstab2.cu); the alpha reductions reuse KrylovOps::alpha.
+template <typename C> struct BiCGstab2Ops {
+    static cudaError_t u0(int R, int64_t n, C* u0, const C* r0, const KState* st, const int* active, cudaStream_t s);
+    static cudaError_t r0(int R, int64_t n, C* r0, const C* u1, C* x, const C* u0, const KState* st,
+                          const int* active, cudaStream_t s);
+    static cudaError_t rho(int R, int64_t n, const C* rt, const C* r1, KState* st, int* active, double2* part,
+                           unsigned* cnt, cudaStream_t s);
+    static cudaError_t u1(int R, int64_t n, C* u0, C* u1, const C* r0, const C* r1, const KState* st,
+                          const int* active, cudaStream_t s);
+    static cudaError_t r1(int R, int64_t n, C* r0, C* r1, const C* u0, const C* u1, const C* u2, C* x,
+                          const KState* st, const int* active, cudaStream_t s);
+    static cudaError_t gram(int R, int64_t n, const C* r0, const C* r1, const C* r2, KState* st, int* active,
+                            double2* part, unsigned* cnt, cudaStream_t s);
+    static cudaError_t mr(int R, int64_t n, C* x, C* r0, const C* r1, const C* r2, C* u0, const C* u1, const C* u2,
+                          const C* rt, KState* st, int* active, double2* part, unsigned* cnt, cudaStream_t s);
 };
 
 cudaError_t launch_count_active(const int* active, int R, int* out, cudaStream_t s);

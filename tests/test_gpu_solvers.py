@@ -1,0 +1,134 @@
+"""BiCGstab(2) (the guide's PBCGS2) on the GPU vs the oracle.
+
+The GPU runs BiCGstab(2) per RHS with FP64 scalars and plain matvecs
+(bicgstab2.cu); the oracle's bicgstab_l states Sleijpen & Fokkema's
+algorithm in numpy.  Iterates are compared after a fixed number of
+iterations (FP64), and converged solutions against dense LU.
+"""
+import numpy as np
+import pytest
+
+from dda_inputs import block_bernoulli_grid, ellipsoid_grid, polarization_pair, uniform_directions, workload
+from oracle import dda as odda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1202_3424_gb300 as dda
+    dda.load_library()
+    return dda
+
+
+def _ctx(dda, grid, m, x, prec=1):
+    ctx = dda.Context(0)
+    ctx.set_target(grid)
+    ctx.set_materials(m)
+    ctx.prepare_size_parameter(x, prec)
+    return ctx
+
+
+def _rhs_set(R, seed=5):
+    k = uniform_directions(R, seed)
+    e1, _ = polarization_pair(k)
+    return k, e1.astype(complex)
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def _oracle_system(grid, m, kd, khat, ehat):
+    r, comp = odda.site_positions(grid)
+    beta = odda.ldr_inverse_polarizability((np.asarray(m, dtype=complex) ** 2)[comp - 1], kd, khat, ehat)
+    A = odda.dense_matrix(r, kd, beta)
+    E = odda.incident_field(r, kd, khat, ehat)
+    return r, beta, A, E
+
+
+@pytest.mark.parametrize("k_iters", [1, 3, 6])
+def test_bicgstab2_iterates_match_oracle(lib, k_iters):
+    """FP64 BiCGstab(2) stopped after k iterations: the GPU iterate equals the
+    oracle's (same x0 = 0, shadow residual = b), and 4k + 1 matvecs are counted."""
+    grid = block_bernoulli_grid(6, 5, 4, seed=3)
+    m = [1.7 + 0.3j, 1.3 + 0.02j]
+    ctx = _ctx(lib, grid, m, 1.4, 0)
+    kd = ctx.info()["kd"]
+    k, e = _rhs_set(2)
+    res, P, _ = ctx.solve(0, k, e, tol=1e-14, maxit=k_iters, solver="bicgstab2", max_outer=1)
+    for i in range(2):
+        _, _, A, E = _oracle_system(grid, m, kd, k[i], e[i])
+        x, it, nmv, _ = odda.bicgstab_l(lambda v: A @ v, E.ravel(), 0.0, k_iters, ell=2)
+        assert it == k_iters and res[i]["iters"] == k_iters
+        assert res[i]["matvecs"] == 4 * k_iters + 1
+        assert _rel(P[i].T.ravel(), x) < 1e-10, (k_iters, i)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol,qtol", [(0, 1e-12, 1e-10), (1, 1e-8, 1e-7), (2, 1e-5, 1e-4)],
+                         ids=["fp64", "fp32_refined", "fp32"])
+def test_bicgstab2_solve_matches_dense_lu(lib, prec, tol, qtol):
+    grid = block_bernoulli_grid(7, 6, 5, seed=20120514)
+    m = [1.7 + 0.3j, 1.2 + 0.01j]
+    ctx = _ctx(lib, grid, m, 1.6)
+    kd = ctx.info()["kd"]
+    k, e = _rhs_set(3, 8)
+    res, P, st = ctx.solve(prec, k, e, tol=tol, maxit=2000, solver="bicgstab2")
+    assert st == 0, res
+    aeff = odda.aeff_lattice(int(np.count_nonzero(grid)))
+    for i in range(3):
+        _, beta, A, E = _oracle_system(grid, m, kd, k[i], e[i])
+        Po = np.linalg.solve(A, E.ravel()).reshape(-1, 3)
+        assert res[i]["resid_rel"] <= tol
+        assert _rel(P[i].T, Po) < max(30 * tol, 1e-10)
+        qo = odda.efficiencies(odda.cross_sections(kd, E, Po, beta), aeff)
+        for a, b in zip((res[i]["qext"], res[i]["qabs"], res[i]["qsca"]), qo):
+            assert abs(a - b) <= qtol * abs(b), (i, a, b)
+    ctx.close()
+
+
+def test_bicgstab2_batched_rhs_with_masks_agree_with_bicgstab(lib):
+    """Nine RHS in one batch (different directions converge at different
+    iterations and drop out by their masks), with the captured graph: every
+    solution equals the BiCGstab one to the tolerance."""
+    grid = ellipsoid_grid(14, 10, 8, 14, 10, 8)
+    m = [1.5 + 0.1j]
+    ctx = _ctx(lib, grid, m, 2.5)
+    k, e = _rhs_set(9, 17)
+    r2, P2, st2 = ctx.solve(1, k, e, tol=1e-7, solver="bicgstab2")
+    r1, P1, st1 = ctx.solve(1, k, e, tol=1e-7, solver="bicgstab")
+    assert st1 == 0 and st2 == 0
+    assert len({r["iters"] for r in r2}) > 1          # the masks did work
+    for i in range(9):
+        assert _rel(P2[i], P1[i]) < 1e-6, i
+        assert abs(r2[i]["qext"] - r1[i]["qext"]) < 1e-6 * abs(r1[i]["qext"])
+    ctx.close()
+
+
+def test_au_brick_pbcgs2_iterations(lib):
+    """The guide's FROM_FILE sample (32x64x64 Au block, m = 0.9656 + 1.8628i,
+    x = 6.19, TOL = 1e-5), where PBCGS2 takes 29 and 30 iterations for the two
+    polarizations with GKDLDR polarizabilities.  With LATTDR both solvers
+    converge, BiCGstab(2) within a factor of two of the printed counts."""
+    w = workload("aubrick32x64x64")
+    ctx = _ctx(lib, w.grid, w.m, w.x)
+    res2, _, st2 = ctx.solve(1, w.khat, w.ehat, tol=1e-5, want_P=False, solver="bicgstab2")
+    res1, _, st1 = ctx.solve(1, w.khat, w.ehat, tol=1e-5, want_P=False, solver="bicgstab")
+    assert st1 == 0 and st2 == 0
+    for r in res2:
+        assert 15 <= r["iters"] <= 60, r["iters"]
+    for a, b in zip(res2, res1):
+        assert abs(a["qext"] - b["qext"]) < 1e-4 * abs(b["qext"])
+    ctx.close()
+
+
+def test_unknown_solver_rejected(lib):
+    ctx = _ctx(lib, np.ones((2, 2, 2), np.uint8), [1.5 + 0.1j], 0.5)
+    k, e = _rhs_set(1)
+    with pytest.raises(ValueError):
+        ctx.solve(1, k, e, solver="qmr")
+    ctx.close()

@@ -518,7 +518,8 @@ int partial_stride(const dda_ctx* ctx) {
 // Matvec over R RHS in chunks with the BiCGstab updates of `mode` fused into
 // its x passes (see FusedKrylov).
 template <typename T>
-dda_status run_matvec_fused(dda_ctx* ctx, int R, int mode, cx<T>* x, cx<T>* y, const Inner<T>& in) {
+dda_status run_matvec_fused(dda_ctx* ctx, int R, int mode, cx<T>* x, cx<T>* y, const cx<T>* r, const cx<T>* v,
+                            const cx<T>* rhat) {
     const int rc = matvec_chunk<T>(ctx, R);
     const int64_t n = 3 * ctx->g.N;
     PadWork<T> w{slot<cx<T>>(ctx, PadSlots<T>::a), slot<cx<T>>(ctx, PadSlots<T>::b)};
@@ -533,9 +534,9 @@ dda_status run_matvec_fused(dda_ctx* ctx, int R, int mode, cx<T>* x, cx<T>* y, c
         if ((zs = pick_schedule<T>(ctx, rn, true, &w.zvar, &w.slices)) != DDA_OK) return zs;
         FusedKrylov<T> fk;
         fk.mode = mode;
-        fk.r = in.r + o;
-        fk.v = in.v + o;
-        fk.rhat = in.rhat + o;
+        fk.r = r + o;
+        fk.v = v + o;
+        fk.rhat = rhat + o;
         fk.st = slot<KState>(ctx, S_STATE) + r0;
         fk.part = slot<double2>(ctx, S_PART) + (int64_t)r0 * ps;
         fk.cnt = slot<unsigned>(ctx, S_CNT) + r0;
@@ -560,16 +561,18 @@ template <typename T> dda_status inner_iteration(dda_ctx* ctx, int R) {
     unsigned* cnt = slot<unsigned>(ctx, S_CNT);
     cudaStream_t s = ctx->stream;
     dda_status rs;
-    if ((rs = run_matvec_fused<T>(ctx, R, 1, in.p, in.v, in)) != DDA_OK) return rs;
-    if ((rs = run_matvec_fused<T>(ctx, R, 2, in.s, in.t, in)) != DDA_OK) return rs;
+    if ((rs = run_matvec_fused<T>(ctx, R, 1, in.p, in.v, in.r, in.v, in.rhat)) != DDA_OK) return rs;
+    if ((rs = run_matvec_fused<T>(ctx, R, 2, in.s, in.t, in.r, in.v, in.rhat)) != DDA_OK) return rs;
     CU(Ops::update_xr(R, n, in.x, in.p, in.s, in.t, in.r, in.rhat, st, act, part, cnt, s));
     return DDA_OK;
 }
 
 // One BiCGstab(2) iteration for every active RHS (bicgstab2.cu): two BiCG
-// steps and the degree-2 minimal-residual step, 4 plain matvecs.
+// steps and the degree-2 minimal-residual step, 4 matvecs.  The matvecs of
+// u1 = A u0 and u2 = A u1 take the update u <- r - beta u in their gather
+// and alpha = rho / <rt, A u> in their scatter (the BiCGstab mode-1 fusion,
+// fed beta -> -beta and omega = 0 by the BiCGstab(2) kernels).
 template <typename T> dda_status inner_iteration_b2(dda_ctx* ctx, int R) {
-    using Ops = KrylovOps<cx<T>>;
     using B2 = BiCGstab2Ops<cx<T>>;
     const int64_t n = 3 * ctx->g.N;
     Inner<T> in = InnerSlots<T>::get(ctx);
@@ -580,15 +583,11 @@ template <typename T> dda_status inner_iteration_b2(dda_ctx* ctx, int R) {
     unsigned* cnt = slot<unsigned>(ctx, S_CNT);
     cudaStream_t s = ctx->stream;
     dda_status rs;
-    CU(B2::u0(R, n, u0, r0, st, act, s));
-    if ((rs = run_matvec<T>(ctx, R, u0, u1, act)) != DDA_OK) return rs;
-    CU(Ops::alpha(R, n, in.rhat, u1, st, act, part, cnt, s));
+    if ((rs = run_matvec_fused<T>(ctx, R, 1, u0, u1, r0, r0, in.rhat)) != DDA_OK) return rs;
     CU(B2::r0(R, n, r0, u1, in.x, u0, st, act, s));
     if ((rs = run_matvec<T>(ctx, R, r0, r1, act)) != DDA_OK) return rs;
     CU(B2::rho(R, n, in.rhat, r1, st, act, part, cnt, s));
-    CU(B2::u1(R, n, u0, u1, r0, r1, st, act, s));
-    if ((rs = run_matvec<T>(ctx, R, u1, u2, act)) != DDA_OK) return rs;
-    CU(Ops::alpha(R, n, in.rhat, u2, st, act, part, cnt, s));
+    if ((rs = run_matvec_fused<T>(ctx, R, 1, u1, u2, r1, r1, in.rhat)) != DDA_OK) return rs;
     CU(B2::r1(R, n, r0, r1, u0, u1, u2, in.x, st, act, s));
     if ((rs = run_matvec<T>(ctx, R, r1, r2, act)) != DDA_OK) return rs;
     CU(B2::gram(R, n, r0, r1, r2, st, act, part, cnt, s));

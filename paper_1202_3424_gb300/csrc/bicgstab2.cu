@@ -10,6 +10,10 @@
 //   j = 1:  rho' = <rt, r1>;  beta = alpha rho' / rho;  rho = rho';
 //           u0 = r0 - beta u0;  u1 = r1 - beta u1;  u2 = A u1;  alpha = rho / <rt, u2>;
 //           r0 -= alpha u1;  r1 -= alpha u2;  x += alpha u0;  r2 = A r1
+// The u1 and u2 matvecs are the fused BiCGstab matvec (internal.h,
+// FusedKrylov mode 1), whose gather forms p <- r + beta (p - omega v) and
+// whose scatter forms alpha = rho / <rhat, A p>: between the BiCG steps the
+// state holds -beta in `beta` and 0 in `omega`, so that gather is u <- r - beta u.
 //   MR:     tau = <r1, r2>/s1, r2' = r2 - tau r1, s_j = |r_j'|^2, g'_j = <r_j', r0>/s_j,
 //           g2 = g'2 = omega, g1 = g'1 - tau g2;
 //           x += g1 r0 + g2 r1;  r0 -= g'1 r1 + g'2 r2';  u0 -= g1 u1 + g2 u2
@@ -43,16 +47,6 @@ __device__ __forceinline__ void stop(KState& s, int* active, int r, int status) 
     active[r] = 0;
 }
 
-// u0 = r0 - beta u0
-template <typename C>
-__global__ void __launch_bounds__(kThreads)
-    k_b2_u0(int64_t n, C* __restrict__ u0, const C* __restrict__ r0, const KState* __restrict__ st,
-            const int* __restrict__ active) {
-    RHS_LOOP_SETUP(active)
-    const C beta = from2<C>(st[r].beta);
-    for (int64_t i = i0; i < n; i += stride) u0[off + i] = csub(r0[off + i], cmul(beta, u0[off + i]));
-}
-
 // r0 -= alpha u1;  x += alpha u0
 template <typename C>
 __global__ void __launch_bounds__(kThreads)
@@ -66,7 +60,7 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// rho' = <rt, r1>;  beta = alpha rho' / rho;  rho = rho'
+// rho' = <rt, r1>;  beta = alpha rho' / rho (stored as -beta);  rho = rho'
 template <typename C>
 __global__ void __launch_bounds__(kThreads)
     k_b2_rho(int64_t n, const C* __restrict__ rt, const C* __restrict__ r1, KState* __restrict__ st,
@@ -81,38 +75,30 @@ __global__ void __launch_bounds__(kThreads)
         if (!finite2(acc[0])) stop(s, active, r, KS_NONFINITE);
         else if (s.rho.x == 0.0 && s.rho.y == 0.0) stop(s, active, r, KS_BREAKDOWN);
         else {
-            s.beta = cmul(s.alpha, zdiv(acc[0], s.rho));
+            const double2 b = cmul(s.alpha, zdiv(acc[0], s.rho));
+            s.beta = make_double2(-b.x, -b.y);
+            s.omega = make_double2(0.0, 0.0);  // (the solve's first iteration starts with omega = 1)
             s.rho = acc[0];
         }
         st[r] = s;
     }
 }
 
-// u0 = r0 - beta u0;  u1 = r1 - beta u1
+// u0 = r0 - beta u0 (the state holds -beta);  r0 -= alpha u1;  r1 -= alpha u2;  x += alpha u0
 template <typename C>
 __global__ void __launch_bounds__(kThreads)
-    k_b2_u1(int64_t n, C* __restrict__ u0, C* __restrict__ u1, const C* __restrict__ r0, const C* __restrict__ r1,
-            const KState* __restrict__ st, const int* __restrict__ active) {
-    RHS_LOOP_SETUP(active)
-    const C beta = from2<C>(st[r].beta);
-    for (int64_t i = i0; i < n; i += stride) {
-        u0[off + i] = csub(r0[off + i], cmul(beta, u0[off + i]));
-        u1[off + i] = csub(r1[off + i], cmul(beta, u1[off + i]));
-    }
-}
-
-// r0 -= alpha u1;  r1 -= alpha u2;  x += alpha u0
-template <typename C>
-__global__ void __launch_bounds__(kThreads)
-    k_b2_r1(int64_t n, C* __restrict__ r0, C* __restrict__ r1, const C* __restrict__ u0, const C* __restrict__ u1,
+    k_b2_r1(int64_t n, C* __restrict__ r0, C* __restrict__ r1, C* __restrict__ u0, const C* __restrict__ u1,
             const C* __restrict__ u2, C* __restrict__ x, const KState* __restrict__ st,
             const int* __restrict__ active) {
     RHS_LOOP_SETUP(active)
-    const C alpha = from2<C>(st[r].alpha);
+    const C alpha = from2<C>(st[r].alpha), mbeta = from2<C>(st[r].beta);
     for (int64_t i = i0; i < n; i += stride) {
-        r0[off + i] = csub(r0[off + i], cmul(alpha, u1[off + i]));
+        const C a = r0[off + i];
+        const C u = cadd(a, cmul(mbeta, u0[off + i]));
+        u0[off + i] = u;
+        r0[off + i] = csub(a, cmul(alpha, u1[off + i]));
         r1[off + i] = csub(r1[off + i], cmul(alpha, u2[off + i]));
-        x[off + i] = cadd(x[off + i], cmul(alpha, u0[off + i]));
+        x[off + i] = cadd(x[off + i], cmul(alpha, u));
     }
 }
 
@@ -163,7 +149,8 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // x += g1 r0 + g2 r1;  r0 -= g1 r1 + g2 r2;  u0 -= g1 u1 + g2 u2  (g2 = omega);
-// rho' = <rt, r0>, |r0|^2; convergence; beta of the next iteration.
+// rho' = <rt, r0>, |r0|^2; convergence; beta of the next iteration (stored
+// as -beta, with omega = 0, for the next u0 gather).
 template <typename C>
 __global__ void __launch_bounds__(kThreads)
     k_b2_mr(int64_t n, C* __restrict__ x, C* __restrict__ r0, const C* __restrict__ r1, const C* __restrict__ r2,
@@ -199,9 +186,9 @@ __global__ void __launch_bounds__(kThreads)
                    (s.rho.x == 0.0 && s.rho.y == 0.0)) {
             stop(s, active, r, KS_BREAKDOWN);
         } else {
-            const double2 mwr = make_double2(-(s.omega.x * s.rho.x - s.omega.y * s.rho.y),
-                                             -(s.omega.x * s.rho.y + s.omega.y * s.rho.x));  // -omega rho
-            s.beta = cmul(s.alpha, zdiv(acc[0], mwr));
+            // beta = alpha rho' / (-omega rho), stored negated
+            s.beta = cmul(s.alpha, zdiv(acc[0], cmul(s.omega, s.rho)));
+            s.omega = make_double2(0.0, 0.0);
             s.rho = acc[0];
         }
         st[r] = s;
@@ -213,15 +200,6 @@ __global__ void __launch_bounds__(kThreads)
 constexpr KernelKind kind_of(int bytes) { return bytes == 8 ? KK_KRYLOV_C64 : KK_KRYLOV_C128; }
 
 }  // namespace
-
-template <typename C>
-cudaError_t BiCGstab2Ops<C>::u0(int R, int64_t n, C* u0_, const C* r0, const KState* st, const int* active,
-                                cudaStream_t s) {
-    PROF_BEGIN(s);
-    k_b2_u0<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, u0_, r0, st, active);
-    PROF_END(kind_of(sizeof(C)), R, s);
-    return cudaGetLastError();
-}
 
 template <typename C>
 cudaError_t BiCGstab2Ops<C>::r0(int R, int64_t n, C* r0_, const C* u1, C* x, const C* u0_, const KState* st,
@@ -242,16 +220,7 @@ cudaError_t BiCGstab2Ops<C>::rho(int R, int64_t n, const C* rt, const C* r1, KSt
 }
 
 template <typename C>
-cudaError_t BiCGstab2Ops<C>::u1(int R, int64_t n, C* u0_, C* u1_, const C* r0_, const C* r1, const KState* st,
-                                const int* active, cudaStream_t s) {
-    PROF_BEGIN(s);
-    k_b2_u1<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, u0_, u1_, r0_, r1, st, active);
-    PROF_END(kind_of(sizeof(C)), R, s);
-    return cudaGetLastError();
-}
-
-template <typename C>
-cudaError_t BiCGstab2Ops<C>::r1(int R, int64_t n, C* r0_, C* r1_, const C* u0_, const C* u1_, const C* u2,
+cudaError_t BiCGstab2Ops<C>::r1(int R, int64_t n, C* r0_, C* r1_, C* u0_, const C* u1_, const C* u2,
                                 C* x, const KState* st, const int* active, cudaStream_t s) {
     PROF_BEGIN(s);
     k_b2_r1<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, r0_, r1_, u0_, u1_, u2, x, st, active);

@@ -47,16 +47,14 @@ template <typename C> struct KrylovOps {
                                   const int* active, cudaStream_t s);
 };
 
-// BiCGstab(2) steps (bicgstab2.cu); the alpha reductions reuse KrylovOps::alpha.
+// BiCGstab(2) steps (bicgstab2.cu); the u updates and alpha reductions run
+// inside the fused matvecs.
 template <typename C> struct BiCGstab2Ops {
-    static cudaError_t u0(int R, int64_t n, C* u0, const C* r0, const KState* st, const int* active, cudaStream_t s);
     static cudaError_t r0(int R, int64_t n, C* r0, const C* u1, C* x, const C* u0, const KState* st,
                           const int* active, cudaStream_t s);
     static cudaError_t rho(int R, int64_t n, const C* rt, const C* r1, KState* st, int* active, double2* part,
                            unsigned* cnt, cudaStream_t s);
-    static cudaError_t u1(int R, int64_t n, C* u0, C* u1, const C* r0, const C* r1, const KState* st,
-                          const int* active, cudaStream_t s);
-    static cudaError_t r1(int R, int64_t n, C* r0, C* r1, const C* u0, const C* u1, const C* u2, C* x,
+    static cudaError_t r1(int R, int64_t n, C* r0, C* r1, C* u0, const C* u1, const C* u2, C* x,
                           const KState* st, const int* active, cudaStream_t s);
     static cudaError_t gram(int R, int64_t n, const C* r0, const C* r1, const C* r2, KState* st, int* active,
                             double2* part, unsigned* cnt, cudaStream_t s);

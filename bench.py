@@ -66,9 +66,10 @@ def parse():
                          "m x (1, 1.05, 0.95), dielectric frame rotated by (0.4, 1.1, -0.6) rad)")
     ap.add_argument("--solver", default="bicgstab", choices=["bicgstab", "bicgstab2"],
                     help="solve mode: BiCGstab (default) or BiCGstab(2), the guide's PBCGS2")
-    ap.add_argument("--zpass", type=int, default=-1, choices=[-1, 0, 1],
+    ap.add_argument("--zpass", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="complex64 z-pass schedule: -1 autotuned (default), 0 component groups, "
-                         "1 register-resident (forcing one makes profiler runs reproduce the tuned choice)")
+                         "1 register-resident, 2 register-resident with octant columns "
+                         "(forcing one makes profiler runs reproduce the tuned choice)")
     return ap.parse_args()
 
 

@@ -290,6 +290,9 @@ dda_status dda_grad_qabs(dda_ctx* ctx, dda_precision precision, const double* kh
  *      1  register-resident: one thread holds all three components of its
  *         points, and the loads of the next RHS are issued before the current
  *         one is transformed;
+ *      2  as 1, with each block owning columns of the Green octant and
+ *         transforming the four columns (+-kx, +-ky) that share them (a
+ *         quarter of the Green staging; faster for few RHS);
  *  - the fused x+y slice passes: where the half-y spectrum of one z-slice,
  *    Lx x (Ly/2) points, fits in shared memory (Lx, Ly in 64..192 for
  *    complex64, 64 or 96 for complex128 and double-float), one block can
@@ -300,8 +303,8 @@ dda_status dda_grad_qabs(dda_ctx* ctx, dda_precision precision, const double* kh
  * matvecs on its own workspace the first time a matvec of a given type and
  * RHS count runs outside a stream capture, and keeps the fastest (inside a
  * capture an untimed choice is used until then).
- * dda_set_schedule: zpass -1 automatic (the default), 0 or 1 forces that z
- *   schedule wherever it exists (1 falls back to 0 elsewhere).
+ * dda_set_schedule: zpass -1 automatic (the default), 0, 1 or 2 forces that
+ *   z schedule wherever it exists (1 and 2 fall back to 0 elsewhere).
  * dda_set_slice_passes: on -1 automatic, 0 always the separate passes (the
  *   default: measured on GB300 the slice passes are faster only for small
  *   grids outside a solve), 1 the slice passes wherever they are built.

@@ -400,7 +400,7 @@ def dda_angular_averages(ctx, precision, khat, P, eta=0.5):
 
 
 def dda_set_schedule(ctx, zpass: int):
-    """Force the complex64 z-pass schedule (0 or 1) or restore autotuning (-1)."""
+    """Force the complex64 z-pass schedule (0, 1 or 2) or restore autotuning (-1)."""
     _check(ctx, load_library().dda_set_schedule(ctx, int(zpass)))
 
 

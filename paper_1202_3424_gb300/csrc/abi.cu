@@ -375,14 +375,14 @@ template <typename T> dda_status ensure_pad(dda_ctx* ctx, int R) {
 // vectors, and the fastest is kept.  The workspace must hold R RHS
 // (ensure_pad<T>).  Inside a stream capture, or with may_time false, an
 // untimed choice is returned: the cached one, else the register-resident z
-// schedule for R >= 4 and the slice passes where built.
+// schedule (octant mapping below 8 RHS) and the slice passes where built.
 template <typename T> dda_status pick_schedule(dda_ctx* ctx, int R, bool may_time, int* zvar, int* slices) {
     const int nv = zconv_schedules<T>(ctx->g);
     const bool sl = slice_passes<T>(ctx->g) && !ctx->aniso;
     std::vector<int> zs, ss;
     if (nv <= 1) zs = {0};
     else if (ctx->force_z >= 0) zs = {std::min(ctx->force_z, nv - 1)};
-    else zs = {0, 1};
+    else for (int z = 0; z < nv; ++z) zs.push_back(z);
     if (!sl) ss = {0};
     else if (ctx->force_slices >= 0) ss = {ctx->force_slices};
     else ss = {1, 0};
@@ -399,7 +399,7 @@ template <typename T> dda_status pick_schedule(dda_ctx* ctx, int R, bool may_tim
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CU(cudaStreamIsCapturing(ctx->stream, &cs));
     if (!may_time || cs != cudaStreamCaptureStatusNone) {
-        if (zs.size() > 1) *zvar = R >= 4 ? 1 : 0;
+        if (zs.size() > 1) *zvar = R >= 8 ? 1 : 2;
         return DDA_OK;
     }
     // zero-filled x, y and 1/alpha table (their values do not change the timing)
@@ -1959,7 +1959,8 @@ dda_status dda_grad_qabs(dda_ctx* ctx, dda_precision precision, const double* kh
 
 dda_status dda_set_schedule(dda_ctx* ctx, int zpass) {
     if (!ctx) return DDA_ERR_ARG;
-    if (zpass < -1 || zpass > 1) return ctx->fail(DDA_ERR_ARG, "z-pass schedule must be -1, 0 or 1 (got %d)", zpass);
+    if (zpass < -1 || zpass > 2)
+        return ctx->fail(DDA_ERR_ARG, "z-pass schedule must be -1, 0, 1 or 2 (got %d)", zpass);
     ctx->force_z = zpass;
     ctx->zsched.clear();
     if (ctx->graph.exec) {

@@ -85,10 +85,12 @@ int xinv_blocks_per_rhs(const Geom& g);
 
 // Number of z-pass schedules for this grid and arithmetic type: schedule 0
 // (three component groups per column, spectra exchanged through shared
-// memory) always; schedule 1 (register-resident, one thread holds all three
-// components of its points) for complex64 when the z plan keeps at most 8
-// points per thread.  Both compute the same product; the context times them
-// per RHS count and keeps the faster (dda_set_schedule can force one).
+// memory) always; for complex64 when the z plan keeps at most 8 points per
+// thread, schedule 1 (register-resident, one thread holds all three
+// components of its points) and schedule 2 (the same with the octant column
+// mapping: one staged Green tile serves the four columns +-kx, +-ky).  All
+// compute the same product; the context times them per RHS count and keeps
+// the fastest (dda_set_schedule can force one).
 template <typename T> int zconv_schedules(const Geom& g);
 
 // Fused x+y passes over whole z-slices (slice_impl.cuh): built for this

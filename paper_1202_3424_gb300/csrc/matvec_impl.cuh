@@ -450,6 +450,9 @@ __global__ void __launch_bounds__(3 * tp_z<LZ, T>() * ZPlan<LZ>::NT, zconv_min_b
 // flight while computing.  Shared traffic per point is about half that of
 // k_zconv; the price is ~128 registers per thread, so the plan must keep
 // L/NT <= 8 points per thread.
+// Column mapping: a block takes TP adjacent columns kx at one ky and stages
+// their Green entries with the signs of the odd components (xy in x and y,
+// xz in x, yz in y) folded in; k_zconv_oct below maps octant columns instead.
 template <int L> __host__ __device__ constexpr bool zreg_ok() { return Plan<L>::E <= 8; }
 template <int L> __host__ __device__ constexpr int tp_zr() {
     int tp = 128 / Plan<L>::NT;
@@ -574,6 +577,134 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
             });
         }
         r = rn;
+    }
+}
+
+// ---- z pass, register-resident schedule over octant columns (complex64) --------
+// As k_zconv_reg, but a block owns TP columns (kxo, kyo) of the Green octant,
+// kxo < Lx/2, and transforms all (up to four) columns (+-kx, +-ky) that share
+// them, so each staged Green tile serves 4 columns per RHS and the x and y
+// signs of the odd components are applied at use; the self-mirrored column
+// kx = Lx/2 is left to one extra block column in x, whose threads take TP
+// consecutive kyo.  It stages a quarter of the Green tiles, but its mirrored
+// columns are loaded one element off the 128-byte alignment: it wins for few
+// RHS, k_zconv_reg for many.
+template <typename T, int LZ, int RB>
+__global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
+    k_zconv_oct(cx<T>* __restrict__ U2, const cx<T>* __restrict__ gh, int R, int Lx, int Ly,
+                const cx<T>* __restrict__ tw, const int* __restrict__ active) {
+    using C = cx<T>;
+    using PL = Plan<LZ>;
+    constexpr int TP = tp_zr<LZ>(), NT = PL::NT, NZ = LZ / 2, HZ = LZ / 2 + 1, E = PL::E;
+    constexpr int R0 = stage_radix<PL, -1>(0), NB0 = E / R0, JN = R0 / 2;  // half-zero first stage
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);  // exchange planes [3][ROWS][TP]
+    constexpr int ROWS = zreg_rows<LZ, T>();  // padded rows of an exchange plane
+    C* gs = buf + 3 * ROWS * TP;              // Green tensor [6][HZ][TP]
+    C* tws = gs + 6 * HZ * TP;                // twiddle table [LZ]
+    const int hx = Lx / 2 + 1, hy = Ly / 2 + 1;
+    const int64_t cs = (int64_t)HZ * hy * hx;
+    const int t = threadIdx.x % TP, u = threadIdx.x / TP;
+    const bool nyq = (int)blockIdx.x * TP >= Lx / 2;  // the kx = Lx/2 block column
+    if (nyq && (int)blockIdx.y * TP >= hy) return;   // (uniform: before any barrier)
+    // sign variants v = fx + 2 fy of the octant column (kxo, kyo):
+    // kx = fx ? Lx - kxo : kxo, ky likewise.  kyo = 0 and Ly/2 have no
+    // distinct -ky (uniform in the regular blocks, per thread in the kx = Lx/2
+    // ones, which run fx = 0 only); kxo = 0 has no distinct -kx (that thread
+    // idles in variants 1, 3).
+    const int kxo = nyq ? Lx / 2 : blockIdx.x * TP + t;
+    const int kyo = nyq ? blockIdx.y * TP + t : blockIdx.y;
+    const int r0 = blockIdx.z * RB;
+    const int vstep = nyq ? 2 : 1;
+    const int nv = (!nyq && (kyo == 0 || 2 * kyo == Ly)) ? 2 : 4;
+    auto col_valid = [&](int v) {
+        if (nyq) return kyo < hy && ((v >> 1) == 0 || (kyo != 0 && 2 * kyo != Ly));
+        return kxo < Lx / 2 && ((v & 1) == 0 || kxo != 0);
+    };
+    const int64_t plane = (int64_t)Ly * Lx;
+    C* bt = buf + t;
+    const C* gt = gs + t;
+    auto ld = [&](int p, int pos) { return bt[(p * ROWS + exchange_row<LZ, NT, TP, sizeof(C)>(pos)) * TP]; };
+    auto st = [&](int p, int pos, C val) { bt[(p * ROWS + exchange_row<LZ, NT, TP, sizeof(C)>(pos)) * TP] = val; };
+    const int rend = min(R, r0 + RB);
+    auto next_active = [&](int r) {  // uniform across the block
+        while (r < rend && active != nullptr && active[r] == 0) ++r;
+        return r;
+    };
+    auto column = [&](int r, int c, int v) {
+        const int kx = (v & 1) ? Lx - kxo : kxo, ky = (v >> 1) ? Ly - kyo : kyo;
+        return U2 + ((int64_t)r * 3 + c) * NZ * plane + (int64_t)ky * Lx + (col_valid(v) ? kx : 0);
+    };
+    C nxt[3][NB0 * JN];  // first-stage inputs of the next column
+    auto prefetch = [&](int r, int v) {
+        const bool valid = col_valid(v);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const C* bc = column(r, c, v);
+#pragma unroll
+            for (int q = 0; q < NB0; ++q)
+#pragma unroll
+                for (int j = 0; j < JN; ++j)
+                    nxt[c][q * JN + j] = valid ? __ldcs(bc + (int64_t)(u + q * NT + j * (LZ / R0)) * plane) : czero<C>();
+        }
+    };
+    // the first column's loads are in flight while the Green tensor is staged
+    int r = next_active(r0), v = 0;
+    if (r < rend) prefetch(r, v);
+    {
+        for (int e = threadIdx.x; e < 6 * HZ * TP; e += blockDim.x) {
+            const int tt = e % TP, kz = (e / TP) % HZ, cc = e / (TP * HZ);
+            const int gx = nyq ? Lx / 2 : blockIdx.x * TP + tt, gy = nyq ? blockIdx.y * TP + tt : blockIdx.y;
+            gs[(cc * HZ + kz) * TP + tt] =
+                (gx < hx && gy < hy) ? gh[cc * cs + ((int64_t)kz * hy + gy) * hx + gx] : czero<C>();
+        }
+        // twiddles from shared memory: the per-stage loads of the six
+        // transforms per RHS then wait on shared, not L1, latency
+        for (int e = threadIdx.x; e < LZ; e += blockDim.x) tws[e] = tw[e];
+    }
+#pragma unroll 1
+    while (r < rend) {
+        C vc[3][E];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int q = 0; q < NB0; ++q)
+#pragma unroll
+                for (int j = 0; j < JN; ++j) vc[c][q * R0 + j] = nxt[c][q * JN + j];
+        int rn = r, vn = v + vstep;
+        if (vn >= nv) {
+            rn = next_active(r + 1);
+            vn = 0;
+        }
+        if (rn < rend) prefetch(rn, vn);
+        const bool fx = v & 1, fy = v >> 1, valid = col_valid(v);
+        // (each transform's first exchange opens with a barrier, which also
+        // orders it after the previous transform's last reads of the planes)
+        fft_stages_np<C, PL, -1, 0, 3>(vc, u, tws, ld, st, true);
+        for_each_out<PL, -1, false>(u, [&](int idx, int kz) {
+            const bool fz = kz > LZ / 2;
+            const int kzo = fz ? LZ - kz : kz;
+            const C* g = gt + kzo * TP;
+            const C gxx = g[0], gyy = g[3 * HZ * TP], gzz = g[5 * HZ * TP];
+            C gxy = g[HZ * TP], gxz = g[2 * HZ * TP], gyz = g[4 * HZ * TP];
+            if (fx != fy) gxy = cscale(gxy, T(-1));
+            if (fx != fz) gxz = cscale(gxz, T(-1));
+            if (fy != fz) gyz = cscale(gyz, T(-1));
+            const C px = vc[0][idx], py = vc[1][idx], pz = vc[2][idx];
+            vc[0][idx] = cadd(cadd(cmul(gxx, px), cmul(gxy, py)), cmul(gxz, pz));
+            vc[1][idx] = cadd(cadd(cmul(gxy, px), cmul(gyy, py)), cmul(gyz, pz));
+            vc[2][idx] = cadd(cadd(cmul(gxz, px), cmul(gyz, py)), cmul(gzz, pz));
+        });
+        fft_stages_np<C, PL, +1, 0, 3>(vc, u, tws, ld, st, false);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            C* bc = column(r, c, v);
+            for_each_out<PL, +1, true>(u, [&](int idx, int pos) {
+                if (valid) __stcs(bc + (int64_t)pos * plane, vc[c][idx]);
+            });
+        }
+        r = rn;
+        v = vn;
     }
 }
 
@@ -751,22 +882,26 @@ template <typename T> struct LaunchX {
         const int rb = multi ? RB : 1;
         cudaError_t e;
         if constexpr (sizeof(T) == 4 && zreg_ok<LZ>()) {
-            if (zvar == 1) {
-                // (long columns: a staged Green tile is ~2 RHS of loads, so
-                // it serves 16 RHS)
-                constexpr int TP = tp_zr<LZ>(), RBZ = LZ >= 256 ? 16 : 8;
+            if (zvar == 1 || zvar == 2) {
+                // a staged Green tile serves RB column-RHS: RBZ RHS of one
+                // column, or of the (up to) 4 columns of an octant column
+                // (long columns: the tile is ~2 RHS of loads, so it serves 16)
+                constexpr int TP = tp_zr<LZ>(), RBZ = LZ >= 256 ? 16 : 8, RBO = RBZ / 4;
                 constexpr size_t sm = zreg_smem<LZ, T>();
-                e = multi ? allow_smem(k_zconv_reg<T, LZ, RBZ>, sm) : allow_smem(k_zconv_reg<T, LZ, 1>, sm);
-                if (e != cudaSuccess) return e;
-                const int rbz = multi ? RBZ : 1;
-                dim3 grid((g.Lx + TP - 1) / TP, g.Ly, (R + rbz - 1) / rbz);
-                PROF_BEGIN(st);
-                if (multi)
-                    k_zconv_reg<T, LZ, RBZ><<<grid, zreg_threads<LZ>(), sm, st>>>(u2, gh, R, g.Lx, g.Ly, tw, active);
-                else
-                    k_zconv_reg<T, LZ, 1><<<grid, zreg_threads<LZ>(), sm, st>>>(u2, gh, R, g.Lx, g.Ly, tw, active);
-                PROF_END(KK_ZCONV_C64 + koff, R, st);
-                return cudaGetLastError();
+                const bool oct = zvar == 2;
+                const int rbz = !multi ? 1 : (oct ? RBO : RBZ);
+                dim3 grid(oct ? (g.Lx / 2 + TP - 1) / TP + 1 : (g.Lx + TP - 1) / TP, oct ? g.Ly / 2 + 1 : g.Ly,
+                          (R + rbz - 1) / rbz);
+                auto go = [&](auto kern) -> cudaError_t {
+                    cudaError_t ke = allow_smem(kern, sm);
+                    if (ke != cudaSuccess) return ke;
+                    PROF_BEGIN(st);
+                    kern<<<grid, zreg_threads<LZ>(), sm, st>>>(u2, gh, R, g.Lx, g.Ly, tw, active);
+                    PROF_END(KK_ZCONV_C64 + koff, R, st);
+                    return cudaGetLastError();
+                };
+                if (!multi) return oct ? go(k_zconv_oct<T, LZ, 1>) : go(k_zconv_reg<T, LZ, 1>);
+                return oct ? go(k_zconv_oct<T, LZ, RBO>) : go(k_zconv_reg<T, LZ, RBZ>);
             }
         }
         constexpr int TP = tp_z<LZ, T>(), NTH = 3 * TP * ZPlan<LZ>::NT;
@@ -782,7 +917,7 @@ template <typename T> struct LaunchX {
         PROF_END(KK_ZCONV_C64 + koff, R, st);
         return cudaGetLastError();
     }
-    template <int LZ> static int zvariants() { return (sizeof(T) == 4 && zreg_ok<LZ>()) ? 2 : 1; }
+    template <int LZ> static int zvariants() { return (sizeof(T) == 4 && zreg_ok<LZ>()) ? 3 : 1; }
 };
 
 // The lattice seen by the kernels is padded with vacuum to exactly L/2 sites

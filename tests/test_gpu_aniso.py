@@ -92,7 +92,7 @@ def test_aniso_matvec_matches_oracle(lib, name, gridf, m3, angles, x, prec, tol)
     ctx.close()
 
 
-@pytest.mark.parametrize("zpass", [0, 1], ids=["zgroups", "zregs"])
+@pytest.mark.parametrize("zpass", [0, 1, 2], ids=["zgroups", "zregs", "zregs_octant"])
 def test_aniso_matvec_z_schedules_nine_rhs(lib, zpass):
     grid = block_bernoulli_grid(9, 8, 7, seed=12)
     ctx = _ctx(lib, grid, M3, ANGLES, 1.8)
@@ -187,7 +187,7 @@ def test_aniso_full_size_row_samples(lib, prec, tol):
     X = random_complex((R, 3, N), 14)
     rows = np.random.default_rng(10).choice(N, 48, replace=False)
     rows[:2] = [0, N - 1]
-    for zpass in (0, 1):
+    for zpass in (0, 1, 2):
         ctx.set_schedule(zpass)
         Y = ctx.matvec(prec, w.khat[:R], w.ehat[:R], X)
         for r in range(R):

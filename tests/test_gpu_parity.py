@@ -88,11 +88,11 @@ REG_Z_LENGTHS = (16, 32, 64, 128, 256, 512)  # z plans with at most 8 points per
 
 
 @pytest.mark.parametrize("name,gridf,m,x", MATVEC_CASES, ids=[c[0] for c in MATVEC_CASES])
-@pytest.mark.parametrize("zpass", [0, 1], ids=["zgroups", "zregs"])
+@pytest.mark.parametrize("zpass", [0, 1, 2], ids=["zgroups", "zregs", "zregs_octant"])
 def test_matvec_z_schedules_match_oracle(lib, name, gridf, m, x, zpass):
-    """Both complex64 z-pass schedules against the pairwise oracle.  Nine RHS
-    span one full block of eight RHS and a ragged one; a grid whose z plan has
-    no register-resident schedule must fall back to schedule 0."""
+    """The complex64 z-pass schedules against the pairwise oracle.  Nine RHS
+    span full blocks of RHS and a ragged one; a grid whose z plan has no
+    register-resident schedule must fall back to schedule 0."""
     grid = gridf()
     ctx = _ctx(lib, grid, m, x, lib.Precision.FP32_REFINED)
     info = ctx.info()
@@ -110,11 +110,11 @@ def test_matvec_z_schedules_match_oracle(lib, name, gridf, m, x, zpass):
     ctx.close()
 
 
-@pytest.mark.parametrize("zpass", [0, 1], ids=["zgroups", "zregs"])
+@pytest.mark.parametrize("zpass", [0, 1, 2], ids=["zgroups", "zregs", "zregs_octant"])
 def test_matvec_long_z_columns_many_rhs(lib, zpass):
-    """A 4x5x100 rod (256-point z transform, where the register schedule
-    takes 16 RHS per block) with 18 RHS: one full block of RHS and a ragged
-    one, against the pairwise oracle."""
+    """A 4x5x100 rod (256-point z transform, where the register schedules
+    take 16 or, with octant columns, 4 RHS per block) with 18 RHS: full blocks
+    of RHS and a ragged one, against the pairwise oracle."""
     grid = np.ones((100, 5, 4), np.uint8)
     m = [1.4 + 0.05j]
     ctx = _ctx(lib, grid, m, 2.0, lib.Precision.FP32_REFINED)
@@ -141,7 +141,7 @@ def test_autotuned_schedule_reproduces_forced_one(lib):
     ctx.set_schedule(-1)
     ctx.set_slice_passes(-1)
     zpick, spick = ctx.get_schedule(R, with_slices=True)
-    assert zpick in (0, 1) and spick in (0, 1)
+    assert zpick in (0, 1, 2) and spick in (0, 1)
     X = random_complex((R, 3, ctx.info()["ndipoles"]), 4).astype(np.complex64)
     k, e = np.resize(w.khat, (R, 3)), np.resize(w.ehat, (R, 3))
     y_auto = ctx.matvec(2, k, e, X)
@@ -150,7 +150,7 @@ def test_autotuned_schedule_reproduces_forced_one(lib):
     y_forced = ctx.matvec(2, k, e, X)
     assert np.array_equal(y_auto, y_forced)
     with pytest.raises(lib.DdaError):
-        ctx.set_schedule(2)
+        ctx.set_schedule(3)
     ctx.close()
 
 
@@ -184,7 +184,7 @@ def test_matvec_row_samples_full_size(lib, name):
         rr, beta = _site_beta(w.grid, w.m, kd, w.khat[r], w.ehat[r])
         want.append(pairwise.matvec(rr, kd, beta, X[r].T, rows=rows)[0])
     for prec, tol, zpass, slices in ((0, F64_TOL, -1, 1), (0, F64_TOL, -1, 0), (3, F64_TOL, -1, 1),
-                                     (2, F32_TOL, 0, 1), (2, F32_TOL, 1, 1), (2, F32_TOL, 1, 0)):
+                                     (2, F32_TOL, 0, 1), (2, F32_TOL, 1, 1), (2, F32_TOL, 1, 0), (2, F32_TOL, 2, 0)):
         ctx.set_schedule(zpass)
         ctx.set_slice_passes(slices)
         Y = ctx.matvec(prec, w.khat[:R], w.ehat[:R], X)
@@ -216,9 +216,9 @@ def test_solve_with_and_without_slice_passes(lib, prec):
     ctx.close()
 
 
-@pytest.mark.parametrize("zpass", [0, 1], ids=["zgroups", "zregs"])
+@pytest.mark.parametrize("zpass", [0, 1, 2], ids=["zgroups", "zregs", "zregs_octant"])
 def test_matvec_row_samples_sphere256(lib, zpass):
-    """The 256^3 sphere (512^3 padded grid), complex64, both z schedules:
+    """The 256^3 sphere (512^3 padded grid), complex64, every z schedule:
     32 seeded rows recomputed by the pairwise oracle, over 3 RHS."""
     w = workload("sphere256")
     ctx = _ctx(lib, w.grid, w.m, w.x, lib.Precision.FP32_REFINED)

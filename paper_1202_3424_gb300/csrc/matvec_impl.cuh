@@ -469,6 +469,10 @@ template <int L, typename T> __host__ __device__ constexpr int zreg_rows() {
 template <int L, typename T> __host__ __device__ constexpr size_t zreg_smem() {
     return (((size_t)3 * zreg_rows<L, T>() + (size_t)6 * (L / 2 + 1)) * tp_zr<L>() + L) * sizeof(cx<T>);
 }
+// k_zconv_oct: one more Green column per tile
+template <int L, typename T> __host__ __device__ constexpr size_t zoct_smem() {
+    return zreg_smem<L, T>() + (size_t)6 * (L / 2 + 1) * sizeof(cx<T>);
+}
 
 template <typename T, int LZ, int RB>
 __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
@@ -581,14 +585,14 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
 }
 
 // ---- z pass, register-resident schedule over octant columns (complex64) --------
-// As k_zconv_reg, but a block owns TP columns (kxo, kyo) of the Green octant,
-// kxo < Lx/2, and transforms all (up to four) columns (+-kx, +-ky) that share
-// them, so each staged Green tile serves 4 columns per RHS and the x and y
-// signs of the odd components are applied at use; the self-mirrored column
-// kx = Lx/2 is left to one extra block column in x, whose threads take TP
-// consecutive kyo.  It stages a quarter of the Green tiles, but its mirrored
-// columns are loaded one element off the 128-byte alignment: it wins for few
-// RHS, k_zconv_reg for many.
+// As k_zconv_reg, but a block owns TP columns of the Green octant at one kyo
+// and transforms the (up to four) columns (+-kx, +-ky) that share them, so a
+// staged Green tile serves 4 columns per RHS; the x and y signs of the odd
+// components are applied at use.  Block a covers kx in [a, a+TP) directly and
+// the mirrored columns Lx - kxo, kxo in (a, a+TP], in ascending order (thread
+// t takes kxo = a + TP - t), so both loads are aligned rows of TP columns and
+// every column 0..Lx-1 has one owner (the self-mirrored Lx/2 is a mirrored
+// one of the last block); the tile therefore holds TP + 1 Green columns.
 template <typename T, int LZ, int RB>
 __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
     k_zconv_oct(cx<T>* __restrict__ U2, const cx<T>* __restrict__ gh, int R, int Lx, int Ly,
@@ -600,30 +604,26 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);  // exchange planes [3][ROWS][TP]
     constexpr int ROWS = zreg_rows<LZ, T>();  // padded rows of an exchange plane
-    C* gs = buf + 3 * ROWS * TP;              // Green tensor [6][HZ][TP]
-    C* tws = gs + 6 * HZ * TP;                // twiddle table [LZ]
+    constexpr int TG = TP + 1;                // Green columns a .. a+TP
+    C* gs = buf + 3 * ROWS * TP;              // Green tensor [6][HZ][TG]
+    C* tws = gs + 6 * HZ * TG;                // twiddle table [LZ]
     const int hx = Lx / 2 + 1, hy = Ly / 2 + 1;
     const int64_t cs = (int64_t)HZ * hy * hx;
     const int t = threadIdx.x % TP, u = threadIdx.x / TP;
-    const bool nyq = (int)blockIdx.x * TP >= Lx / 2;  // the kx = Lx/2 block column
-    if (nyq && (int)blockIdx.y * TP >= hy) return;   // (uniform: before any barrier)
-    // sign variants v = fx + 2 fy of the octant column (kxo, kyo):
-    // kx = fx ? Lx - kxo : kxo, ky likewise.  kyo = 0 and Ly/2 have no
-    // distinct -ky (uniform in the regular blocks, per thread in the kx = Lx/2
-    // ones, which run fx = 0 only); kxo = 0 has no distinct -kx (that thread
-    // idles in variants 1, 3).
-    const int kxo = nyq ? Lx / 2 : blockIdx.x * TP + t;
-    const int kyo = nyq ? blockIdx.y * TP + t : blockIdx.y;
+    const int a = blockIdx.x * TP, kyo = blockIdx.y;
     const int r0 = blockIdx.z * RB;
-    const int vstep = nyq ? 2 : 1;
-    const int nv = (!nyq && (kyo == 0 || 2 * kyo == Ly)) ? 2 : 4;
+    // sign variants v = fx + 2 fy: octant column kxo = fx ? a + TP - t : a + t,
+    // kx = fx ? Lx - kxo : kxo, ky = fy ? Ly - kyo : kyo.  kyo = 0 and Ly/2
+    // have no distinct -ky (uniform per block).  (The odd components vanish
+    // at kx = Lx/2, so its sign does not matter.)
+    const int nv = (kyo == 0 || 2 * kyo == Ly) ? 2 : 4;
+    auto octx = [&](int v) { return (v & 1) ? a + TP - t : a + t; };
     auto col_valid = [&](int v) {
-        if (nyq) return kyo < hy && ((v >> 1) == 0 || (kyo != 0 && 2 * kyo != Ly));
-        return kxo < Lx / 2 && ((v & 1) == 0 || kxo != 0);
+        const int kxo = octx(v);
+        return (v & 1) ? kxo <= Lx / 2 : kxo < Lx / 2;
     };
     const int64_t plane = (int64_t)Ly * Lx;
     C* bt = buf + t;
-    const C* gt = gs + t;
     auto ld = [&](int p, int pos) { return bt[(p * ROWS + exchange_row<LZ, NT, TP, sizeof(C)>(pos)) * TP]; };
     auto st = [&](int p, int pos, C val) { bt[(p * ROWS + exchange_row<LZ, NT, TP, sizeof(C)>(pos)) * TP] = val; };
     const int rend = min(R, r0 + RB);
@@ -632,7 +632,7 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
         return r;
     };
     auto column = [&](int r, int c, int v) {
-        const int kx = (v & 1) ? Lx - kxo : kxo, ky = (v >> 1) ? Ly - kyo : kyo;
+        const int kx = (v & 1) ? Lx - octx(v) : octx(v), ky = (v >> 1) ? Ly - kyo : kyo;
         return U2 + ((int64_t)r * 3 + c) * NZ * plane + (int64_t)ky * Lx + (col_valid(v) ? kx : 0);
     };
     C nxt[3][NB0 * JN];  // first-stage inputs of the next column
@@ -652,11 +652,10 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
     int r = next_active(r0), v = 0;
     if (r < rend) prefetch(r, v);
     {
-        for (int e = threadIdx.x; e < 6 * HZ * TP; e += blockDim.x) {
-            const int tt = e % TP, kz = (e / TP) % HZ, cc = e / (TP * HZ);
-            const int gx = nyq ? Lx / 2 : blockIdx.x * TP + tt, gy = nyq ? blockIdx.y * TP + tt : blockIdx.y;
-            gs[(cc * HZ + kz) * TP + tt] =
-                (gx < hx && gy < hy) ? gh[cc * cs + ((int64_t)kz * hy + gy) * hx + gx] : czero<C>();
+        for (int e = threadIdx.x; e < 6 * HZ * TG; e += blockDim.x) {
+            const int tt = e % TG, kz = (e / TG) % HZ, cc = e / (TG * HZ);
+            const int gx = a + tt;
+            gs[(cc * HZ + kz) * TG + tt] = gx < hx ? gh[cc * cs + ((int64_t)kz * hy + kyo) * hx + gx] : czero<C>();
         }
         // twiddles from shared memory: the per-stage loads of the six
         // transforms per RHS then wait on shared, not L1, latency
@@ -671,7 +670,7 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
             for (int q = 0; q < NB0; ++q)
 #pragma unroll
                 for (int j = 0; j < JN; ++j) vc[c][q * R0 + j] = nxt[c][q * JN + j];
-        int rn = r, vn = v + vstep;
+        int rn = r, vn = v + 1;
         if (vn >= nv) {
             rn = next_active(r + 1);
             vn = 0;
@@ -684,9 +683,9 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
         for_each_out<PL, -1, false>(u, [&](int idx, int kz) {
             const bool fz = kz > LZ / 2;
             const int kzo = fz ? LZ - kz : kz;
-            const C* g = gt + kzo * TP;
-            const C gxx = g[0], gyy = g[3 * HZ * TP], gzz = g[5 * HZ * TP];
-            C gxy = g[HZ * TP], gxz = g[2 * HZ * TP], gyz = g[4 * HZ * TP];
+            const C* g = gs + (fx ? TP - t : t) + kzo * TG;
+            const C gxx = g[0], gyy = g[3 * HZ * TG], gzz = g[5 * HZ * TG];
+            C gxy = g[HZ * TG], gxz = g[2 * HZ * TG], gyz = g[4 * HZ * TG];
             if (fx != fy) gxy = cscale(gxy, T(-1));
             if (fx != fz) gxz = cscale(gxz, T(-1));
             if (fy != fz) gyz = cscale(gyz, T(-1));
@@ -887,10 +886,10 @@ template <typename T> struct LaunchX {
                 // column, or of the (up to) 4 columns of an octant column
                 // (long columns: the tile is ~2 RHS of loads, so it serves 16)
                 constexpr int TP = tp_zr<LZ>(), RBZ = LZ >= 256 ? 16 : 8, RBO = RBZ / 4;
-                constexpr size_t sm = zreg_smem<LZ, T>();
                 const bool oct = zvar == 2;
+                const size_t sm = oct ? zoct_smem<LZ, T>() : zreg_smem<LZ, T>();
                 const int rbz = !multi ? 1 : (oct ? RBO : RBZ);
-                dim3 grid(oct ? (g.Lx / 2 + TP - 1) / TP + 1 : (g.Lx + TP - 1) / TP, oct ? g.Ly / 2 + 1 : g.Ly,
+                dim3 grid(oct ? (g.Lx / 2 + TP - 1) / TP : (g.Lx + TP - 1) / TP, oct ? g.Ly / 2 + 1 : g.Ly,
                           (R + rbz - 1) / rbz);
                 auto go = [&](auto kern) -> cudaError_t {
                     cudaError_t ke = allow_smem(kern, sm);

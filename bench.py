@@ -204,7 +204,7 @@ KERNEL_SOURCES = ["paper_1202_3424_gb300/csrc/matvec_impl.cuh", "paper_1202_3424
                   "paper_1202_3424_gb300/csrc/fft.cuh", "paper_1202_3424_gb300/csrc/krylov_dev.cuh",
                   "paper_1202_3424_gb300/csrc/common.cuh"]
 # (pass, workload, RHS per launch) -> (summary file, kernel heading in it)
-CAPTURES = {("z_conv_c64", "sphere64", 2): ("profiles/zconv_f32_sphere64.md", "k_zconv<float, 128, 8>"),
+CAPTURES = {("z_conv_c64", "sphere64", 2): ("profiles/zoct_f32_sphere64.md", "k_zconv_oct<float, 128, 2>"),
             ("z_conv_c64", "ellipsoid96x64x32", 32): ("profiles/passes_f32_ellipsoid96x64x32.md",
                                                       "k_zconv_reg<float, 64, 8>")}
 

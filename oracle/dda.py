@@ -300,6 +300,75 @@ def bicgstab_l(matvec, b: np.ndarray, tol: float, maxit: int, ell: int = 2, x0=N
     return x, it, nmv, relres
 
 
+def qmr_sym(matvec, b: np.ndarray, tol: float, maxit: int, x0=None, trace=None):
+    """Quasi-minimal residual method for complex symmetric A = A^T (Freund
+    1992; the guide's QMRCCG option, "Choice of Iterative Algorithm"), one
+    matvec per iteration, without look-ahead.
+
+    Lanczos with the bilinear form v^T w (no conjugate): v_1 = r_0/|r_0|,
+    delta_n = v_n^T v_n, alpha_n = v_n^T A v_n / delta_n,
+    gamma_n = beta_n delta_n / delta_{n-1},
+    v~_{n+1} = A v_n - alpha_n v_n - gamma_n v_{n-1}, beta_{n+1} = |v~_{n+1}|,
+    so that A V_n = V_{n+1} H_n with H_n tridiagonal ((n+1) x n).  The iterate
+    x_n = x_0 + V_n z_n minimizes |beta_1 e_1 - H_n z| (the quasi-residual),
+    by complex Givens rotations of H_n updated one column at a time; the
+    residual is updated alongside (r_n = r_{n-1} - t_n A p_n).  Stops when
+    |r_n| <= tol |b|.  With a list as `trace`, each iteration appends
+    (v_n, the quasi-residual |t~_{n+1}|).  Returns (x, iterations, matvecs, relres).
+    """
+    b = np.asarray(b, dtype=np.complex128).ravel()
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.complex128).ravel()
+    r = b - matvec(x) if x0 is not None else b.copy()
+    nmv = 1 if x0 is not None else 0
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return x, 0, nmv, 0.0
+    beta = np.linalg.norm(r)
+    v_prev, v = np.zeros_like(b), r / beta
+    delta_prev, delta = 1.0 + 0j, v @ v
+    gamma = 0.0 + 0j
+    p1, p2, ap1, ap2 = (np.zeros_like(b) for _ in range(4))   # p_{n-1}, p_{n-2}, A p_{n-1}, A p_{n-2}
+    c1, s1, c2, s2 = 1.0, 0j, 1.0, 0j                          # rotations G_{n-1}, G_{n-2}
+    tt = beta + 0j                                             # t~_n
+    relres = beta / bnorm
+    it = 0
+    while relres > tol and it < maxit:
+        w = matvec(v)
+        nmv += 1
+        alpha = (v @ w) / delta
+        vt = w - alpha * v - gamma * v_prev
+        beta_next = np.linalg.norm(vt)
+        # new column of H: gamma (row n-1), alpha (row n), beta_next (row n+1)
+        eps = s2 * gamma                                       # G_{n-2} on rows n-2, n-1
+        h1 = c2 * gamma
+        dlt = c1 * h1 + s1 * alpha                             # G_{n-1} on rows n-1, n
+        tau = -np.conj(s1) * h1 + c1 * alpha
+        if abs(tau) == 0.0:
+            c, s = 0.0, 1.0 + 0j
+        else:
+            c = abs(tau) / np.hypot(abs(tau), beta_next)
+            s = c * beta_next / np.conj(tau)
+        rho = c * tau + s * beta_next
+        t = c * tt                                             # x_n = x_{n-1} + t p_n
+        tt = -np.conj(s) * tt
+        p = (v - dlt * p1 - eps * p2) / rho
+        ap = (w - dlt * ap1 - eps * ap2) / rho
+        x = x + t * p
+        r = r - t * ap
+        p2, p1, ap2, ap1 = p1, p, ap1, ap
+        c2, s2, c1, s1 = c1, s1, c, s
+        it += 1
+        relres = np.linalg.norm(r) / bnorm
+        if trace is not None:
+            trace.append((v.copy(), abs(tt)))
+        if beta_next == 0.0:
+            break
+        v_prev, v = v, vt / beta_next
+        delta_prev, delta = delta, v @ v
+        gamma = beta_next * delta / delta_prev
+    return x, it, nmv, relres
+
+
 def normal_equation_error(matvec, P: np.ndarray, E: np.ndarray) -> float:
     """|A^H A P - A^H E| / |A^H E| (eq. err_tol).  Uses A^H x = conj(A conj(x)),
     valid because A = A^T."""

@@ -175,6 +175,14 @@ MUTATIONS = [
      [pins.bicgstab_l1_vs_bicgstab_error, pins.bicgstab_l2_mr_error]),
     ("bicgstab_l", _mutant(dda.bicgstab_l, "x = x + gpp[j] * r[j]", "x = x - gpp[j] * r[j]"),
      [pins.bicgstab_l2_mr_error]),
+    ("qmr_sym", _mutant(dda.qmr_sym, "alpha = (v @ w) / delta", "alpha = np.vdot(v, w) / delta"),
+     [pins.qmr_complex_symmetric_error]),
+    ("qmr_sym", _mutant(dda.qmr_sym, "gamma = beta_next * delta / delta_prev", "gamma = beta_next"),
+     [pins.qmr_complex_symmetric_error]),
+    ("qmr_sym", _mutant(dda.qmr_sym, "tau = -np.conj(s1) * h1 + c1 * alpha", "tau = -s1 * h1 + c1 * alpha"),
+     [pins.qmr_complex_symmetric_error]),
+    ("qmr_sym", _mutant(dda.qmr_sym, "eps = s2 * gamma", "eps = 0.0 * gamma"),
+     [pins.qmr_minres_error, pins.qmr_complex_symmetric_error]),
 ]
 
 

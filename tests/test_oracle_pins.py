@@ -362,6 +362,49 @@ def bicgstab_l2_mr_error():
     return max(err, float(np.abs(x - xs).max() / np.abs(xs).max()), abs(nmv - 4 * it))
 
 
+def qmr_minres_error(seed=2):
+    """For a real symmetric A the complex symmetric Lanczos process is the
+    symmetric one and QMR is MINRES: the k-th iterate minimizes |b - A x| over
+    the Krylov space K_k(A, b), which brute force recomputes by least squares
+    on an orthonormalized Krylov basis."""
+    rng = np.random.default_rng(seed)
+    n = 50
+    M = rng.normal(size=(n, n))
+    M = M + M.T + 0.5 * np.eye(n)           # indefinite
+    b = rng.normal(size=n)
+    err = 0.0
+    for k in (2, 5, 9):
+        xk, it, nmv, _ = dda.qmr_sym(lambda v: M @ v, b, 0.0, k)
+        K = np.array([np.linalg.matrix_power(M, j) @ b for j in range(k)]).T
+        Q, _ = np.linalg.qr(K)
+        y, *_ = np.linalg.lstsq(M @ Q, b, rcond=None)
+        best = np.linalg.norm(b - M @ (Q @ y))
+        err = max(err, abs(np.linalg.norm(b - M @ xk) - best) / best, abs(nmv - k))
+    return err
+
+
+def qmr_complex_symmetric_error():
+    """Complex symmetric A: the Lanczos vectors are orthogonal in the bilinear
+    form v_i^T v_j, the quasi-residual never grows, and the iteration reaches
+    the LU solution of a DDA system."""
+    A, b = _random_complex_symmetric()
+    tr = []
+    dda.qmr_sym(lambda v: A @ v, b, 1e-12, 300, trace=tr)
+    V = np.array([t[0] for t in tr[:10]])
+    G = V @ V.T
+    err = float(np.abs(G - np.diag(np.diag(G))).max() / np.abs(np.diag(G)).max())
+    q = [t[1] for t in tr]
+    err = max(err, max(0.0, max((q[i + 1] - q[i]) / q[i] for i in range(len(q) - 1))))
+    r = _small_cluster(6, 40)
+    kd = 0.7
+    beta = dda.ldr_inverse_polarizability(np.full(len(r), 2.4 + 0.6j), kd, [1, 0, 0], [0, 1, 0])
+    M = dda.dense_matrix(r, kd, beta)
+    E = dda.incident_field(r, kd, [1, 0, 0], [0, 1, 0]).ravel()
+    x, it, nmv, rel = dda.qmr_sym(lambda v: M @ v, E, 1e-13, 400)
+    xs = np.linalg.solve(M, E)
+    return max(err, float(np.abs(x - xs).max() / np.abs(xs).max()), float(np.linalg.norm(E - M @ x) / np.linalg.norm(E)) / 1e-3)
+
+
 # ------------------------------------------------------------------- tests --
 def test_pseudosphere_counts_match_guide(golden_dir):
     for box, diam, count, *_ in _golden_rows(os.path.join(golden_dir, "pseudosphere_counts.txt")):
@@ -721,3 +764,11 @@ def test_bicgstab_l1_reproduces_bicgstab():
 
 def test_bicgstab_l2_minimal_residual_and_solution():
     assert bicgstab_l2_mr_error() < 1e-11
+
+
+def test_qmr_is_minres_for_real_symmetric():
+    assert qmr_minres_error() < 1e-10
+
+
+def test_qmr_complex_symmetric_lanczos_and_solution():
+    assert qmr_complex_symmetric_error() < 1e-9

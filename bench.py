@@ -64,8 +64,9 @@ def parse():
     ap.add_argument("--aniso", action="store_true",
                     help="solve/matvec modes: anisotropic version of the workload's materials (principal indices "
                          "m x (1, 1.05, 0.95), dielectric frame rotated by (0.4, 1.1, -0.6) rad)")
-    ap.add_argument("--solver", default="bicgstab", choices=["bicgstab", "bicgstab2"],
-                    help="solve mode: BiCGstab (default) or BiCGstab(2), the guide's PBCGS2")
+    ap.add_argument("--solver", default="bicgstab", choices=["bicgstab", "bicgstab2", "qmr"],
+                    help="solve mode: BiCGstab (default), BiCGstab(2) (the guide's PBCGS2) or QMR for complex "
+                         "symmetric A (the guide's QMRCCG)")
     ap.add_argument("--zpass", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="complex64 z-pass schedule: -1 autotuned (default), 0 component groups, "
                          "1 register-resident, 2 register-resident with octant columns "
@@ -372,7 +373,7 @@ def run_gb300(args):
 
     roof = roofline(kstats, info, R, w.name)
     # complex64 RHS-matvecs per traced step: 2 per BiCGstab (4 per BiCGstab(2)) iteration of every RHS
-    per_iter = 4 if args.solver == "bicgstab2" else 2
+    per_iter = {"bicgstab": 2, "bicgstab2": 4, "qmr": 1}[args.solver]
     mv_roof = matvec_roofline(kstats, info, "c64",
                               rhs_matvecs=len(per_tr) * sum(per_iter * r["iters"] for r in res)) \
         if kstats else None
@@ -389,7 +390,7 @@ def run_gb300(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "c64 matvec / f64 refinement", "data": "synthetic",
             "config": {"workload": f"{w.name}: lattice {info['nx']}x{info['ny']}x{info['nz']}, N={N} dipoles, "
                                    f"{materials_note(w, args.aniso)}, x={w.x}, {R} RHS, tol 1e-5, "
-                                   f"{'BiCGstab(2)' if args.solver == 'bicgstab2' else 'BiCGstab'}",
+                                   f"{ {'bicgstab': 'BiCGstab', 'bicgstab2': 'BiCGstab(2)', 'qmr': 'QMR'}[args.solver]}",
                        "global_batch": R * world, "padded_grid": [info["Lx"], info["Ly"], info["Lz"]],
                        "parallelism": f"rhs-sharded x{world}", "l2": "256 MB buffer written between steps"},
             "time_to_solution_ms": ms_per_step,

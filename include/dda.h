@@ -89,10 +89,12 @@ typedef struct {
                           ~1e-12 relative accuracy, 6-8x faster on GB300)                  */
     int solver;        /* DDA_SOLVER_BICGSTAB (0, default): BiCGstab, 2 matvecs an iteration;
                           DDA_SOLVER_BICGSTAB2 (1): BiCGstab(2) (guide: PBCGS2, "Choice of
-                          Iterative Algorithm"), 4 matvecs an iteration                     */
+                          Iterative Algorithm"), 4 matvecs an iteration;
+                          DDA_SOLVER_QMR (2): QMR for complex symmetric A (guide: QMRCCG;
+                          Freund 1992), 1 matvec an iteration, no look-ahead             */
 } dda_opts;
 
-enum { DDA_SOLVER_BICGSTAB = 0, DDA_SOLVER_BICGSTAB2 = 1 };
+enum { DDA_SOLVER_BICGSTAB = 0, DDA_SOLVER_BICGSTAB2 = 1, DDA_SOLVER_QMR = 2 };
 
 typedef struct {
     double qext, qabs, qsca;  /* efficiency factors                                         */

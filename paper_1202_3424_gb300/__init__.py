@@ -149,7 +149,7 @@ def _rhs(khat, e):
     return k, ev.view(np.float64).reshape(k.shape[0], 6).copy(), k.shape[0]
 
 
-SOLVERS = {"bicgstab": 0, "bicgstab2": 1}
+SOLVERS = {"bicgstab": 0, "bicgstab2": 1, "qmr": 2}
 
 
 def _opts(tol=1e-5, maxit=1000, use_graph=True, inner_tol=0.0, max_outer=0, normal_eq=False, x0=None,

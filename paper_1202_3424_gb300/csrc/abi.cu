@@ -595,14 +595,48 @@ template <typename T> dda_status inner_iteration_b2(dda_ctx* ctx, int R) {
     return DDA_OK;
 }
 
-// Iterations per captured block: 8 matvecs per RHS for either solver.
-int block_iterations(int solver) { return solver == DDA_SOLVER_BICGSTAB2 ? 2 : 4; }
-int matvecs_per_iteration(int solver) { return solver == DDA_SOLVER_BICGSTAB2 ? 4 : 2; }
+// One QMR iteration for every active RHS (qmr.cu): w = A v, alpha, the
+// Lanczos vector with the rotations, the updates.  v, p and A p each rotate
+// through two slots; `odd` selects the assignment of this iteration.
+//   slots: x, r, w = t; v / v_prev = s / rhat; p1 / p2 = p / v; Ap1 / Ap2 = u2 / b
+template <typename T> dda_status inner_iteration_qmr(dda_ctx* ctx, int R, bool odd) {
+    using Q = QmrOps<cx<T>>;
+    const int64_t n = 3 * ctx->g.N;
+    Inner<T> in = InnerSlots<T>::get(ctx);
+    cx<T>*v = in.s, *vp = in.rhat, *p1 = in.p, *p2 = in.v, *ap1 = in.u2, *ap2 = in.b;
+    if (odd) {
+        std::swap(v, vp);
+        std::swap(p1, p2);
+        std::swap(ap1, ap2);
+    }
+    KState* st = slot<KState>(ctx, S_STATE);
+    int* act = slot<int>(ctx, S_ACTIVE);
+    double2* part = slot<double2>(ctx, S_PART);
+    unsigned* cnt = slot<unsigned>(ctx, S_CNT);
+    cudaStream_t s = ctx->stream;
+    dda_status rs;
+    if ((rs = run_matvec<T>(ctx, R, v, in.t, act)) != DDA_OK) return rs;
+    CU(Q::alpha(R, n, v, in.t, st, act, part, cnt, s));
+    CU(Q::lanczos(R, n, in.t, v, vp, st, act, part, cnt, s));
+    CU(Q::update(R, n, v, vp, in.t, p1, p2, ap1, ap2, in.x, in.r, st, act, part, cnt, s));
+    return DDA_OK;
+}
+
+// Iterations per captured block: 8 matvecs per RHS for every solver (an even
+// count, so the QMR slot rotation is the same at every block start).
+int block_iterations(int solver) {
+    return solver == DDA_SOLVER_BICGSTAB2 ? 2 : (solver == DDA_SOLVER_QMR ? 8 : 4);
+}
+int matvecs_per_iteration(int solver) {
+    return solver == DDA_SOLVER_BICGSTAB2 ? 4 : (solver == DDA_SOLVER_QMR ? 1 : 2);
+}
 
 template <typename T> dda_status inner_block(dda_ctx* ctx, int R, int K, int solver) {
     dda_status rs;
     for (int k = 0; k < K; ++k) {
-        rs = solver == DDA_SOLVER_BICGSTAB2 ? inner_iteration_b2<T>(ctx, R) : inner_iteration<T>(ctx, R);
+        if (solver == DDA_SOLVER_BICGSTAB2) rs = inner_iteration_b2<T>(ctx, R);
+        else if (solver == DDA_SOLVER_QMR) rs = inner_iteration_qmr<T>(ctx, R, (k & 1) != 0);
+        else rs = inner_iteration<T>(ctx, R);
         if (rs != DDA_OK) return rs;
     }
     CU(launch_count_active(slot<int>(ctx, S_ACTIVE), R, slot<int>(ctx, S_COUNT), ctx->stream));
@@ -690,7 +724,7 @@ template <typename T> dda_status ensure_inner(dda_ctx* ctx, int R, int solver) {
     dda_status s;
     for (int sl = S_IN_B; sl <= S_IN_T; ++sl)
         if ((s = ensure(ctx, ctx->pool[sl], vb)) != DDA_OK) return s;
-    if (solver == DDA_SOLVER_BICGSTAB2 && (s = ensure(ctx, ctx->pool[S_IN_U2], vb)) != DDA_OK) return s;
+    if (solver != DDA_SOLVER_BICGSTAB && (s = ensure(ctx, ctx->pool[S_IN_U2], vb)) != DDA_OK) return s;
     return ensure_pad<T>(ctx, R);
 }
 
@@ -779,6 +813,9 @@ dda_status solve_core(dda_ctx* ctx, int R, const dda_opts& o, bool refine, bool 
         CU(KrylovOps<cx<T>>::to_inner(R, n, Rr, in.b, slot<double>(ctx, S_SCALE), outer, s));
         CU(KrylovOps<cx<T>>::init(R, n, in.b, in.x, in.r, in.rhat, in.p, in.v, slot<KState>(ctx, S_STATE),
                                   slot<double>(ctx, S_TOLREL), outer, slot<int>(ctx, S_ACTIVE), part, cnt, s));
+        if (o.solver == DDA_SOLVER_QMR)
+            CU(QmrOps<cx<T>>::init(R, n, in.r, in.s, in.rhat, in.u2, in.b, slot<KState>(ctx, S_STATE),
+                                   slot<int>(ctx, S_ACTIVE), part, cnt, s));
         if ((rs = inner_solve<T>(ctx, R, o.maxit, o.use_graph != 0, o.solver)) != DDA_OK) return rs;
         CU(cudaMemcpyAsync(hst.data(), ctx->pool[S_STATE].p, R * sizeof(KState), cudaMemcpyDeviceToHost, s));
         CU(KrylovOps<cx<T>>::accumulate(R, n, X, in.x, slot<double>(ctx, S_COEF), outer, s));
@@ -861,7 +898,7 @@ dda_status forward_solve(dda_ctx* ctx, dda_precision prec, int R, const double* 
     if (res == nullptr) return ctx->fail(DDA_ERR_ARG, "res must not be NULL");
     dda_opts o = opts_in ? *opts_in : default_opts();
     if (!(o.tol > 0.0) || o.maxit <= 0) return ctx->fail(DDA_ERR_ARG, "tol must be > 0 and maxit > 0");
-    if (o.solver != DDA_SOLVER_BICGSTAB && o.solver != DDA_SOLVER_BICGSTAB2)
+    if (o.solver != DDA_SOLVER_BICGSTAB && o.solver != DDA_SOLVER_BICGSTAB2 && o.solver != DDA_SOLVER_QMR)
         return ctx->fail(DDA_ERR_ARG, "unknown solver %d", o.solver);
     std::vector<double> k;
     std::vector<cd> ev;

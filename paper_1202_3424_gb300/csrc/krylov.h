@@ -8,7 +8,22 @@ namespace dda {
 
 enum KStatus : int { KS_RUNNING = 0, KS_CONVERGED = 1, KS_BREAKDOWN = 2, KS_MAXIT = 3, KS_NONFINITE = 4, KS_IDLE = 5 };
 
-// Per-RHS scalars of one BiCGstab solve, all FP64, kept on the device.
+// QMR scalars of one RHS (qmr.cu): Lanczos coefficients, the last two
+// Givens rotations, the rotated right-hand side and this step's update.
+struct QmrScalars {
+    double2 delta, delta_prev;  // v_n^T v_n, v_{n-1}^T v_{n-1}
+    double2 gamma, alpha;       // H(n-1, n), H(n, n)
+    double2 s1, s2;             // rotations G_{n-1}, G_{n-2}: sines
+    double c1, c2;              // ... and cosines
+    double2 tt;                 // t~_n, the unrotated last entry of the right-hand side
+    double2 t, rho, dlt, eps;   // x += t p_n,  p_n = (v_n - dlt p_{n-1} - eps p_{n-2}) / rho
+    double inv_beta;            // 1 / |v~_{n+1}| (0: invariant subspace)
+    int lanczos_breakdown;      // v_{n+1}^T v_{n+1} = 0
+    double best;                // smallest |r| so far and its iteration (stagnation test)
+    int best_iter;
+};
+
+// Per-RHS scalars of one Krylov solve, all FP64, kept on the device.
 struct KState {
     double2 rho;    // <rhat, r> of the current residual
     double2 alpha;
@@ -22,6 +37,7 @@ struct KState {
     int maxit;
     int status;     // KStatus
     int pad;
+    QmrScalars q;   // QMR only
 };
 
 static constexpr int kMaxReduceBlocks = 1024;
@@ -60,6 +76,21 @@ template <typename C> struct BiCGstab2Ops {
                             double2* part, unsigned* cnt, cudaStream_t s);
     static cudaError_t mr(int R, int64_t n, C* x, C* r0, const C* r1, const C* r2, C* u0, const C* u1, const C* u2,
                           const C* rt, KState* st, int* active, double2* part, unsigned* cnt, cudaStream_t s);
+};
+
+// QMR steps for complex symmetric A (qmr.cu): init after KrylovOps::init,
+// then per iteration w = A v, alpha, the Lanczos step with the rotations,
+// and the update of p, A p, x, r and v.
+template <typename C> struct QmrOps {
+    static cudaError_t init(int R, int64_t n, const C* r, C* v, C* v_prev, C* ap1, C* ap2, KState* st,
+                            int* active, double2* part, unsigned* cnt, cudaStream_t s);
+    static cudaError_t alpha(int R, int64_t n, const C* v, const C* w, KState* st, int* active, double2* part,
+                             unsigned* cnt, cudaStream_t s);
+    static cudaError_t lanczos(int R, int64_t n, const C* w, const C* v, C* v_prev, KState* st, int* active,
+                               double2* part, unsigned* cnt, cudaStream_t s);
+    static cudaError_t update(int R, int64_t n, const C* v, C* vt, const C* w, const C* p1, C* p2, const C* ap1,
+                              C* ap2, C* x, C* r, KState* st, int* active, double2* part, unsigned* cnt,
+                              cudaStream_t s);
 };
 
 cudaError_t launch_count_active(const int* active, int R, int* out, cudaStream_t s);

@@ -1,8 +1,9 @@
-"""BiCGstab(2) (the guide's PBCGS2) on the GPU vs the oracle.
+"""The BiCGstab(2) (the guide's PBCGS2) and QMR (the guide's QMRCCG) solvers
+on the GPU vs the oracle.
 
-The GPU runs BiCGstab(2) per RHS with FP64 scalars and plain matvecs
-(bicgstab2.cu); the oracle's bicgstab_l states Sleijpen & Fokkema's
-algorithm in numpy.  Iterates are compared after a fixed number of
+The GPU runs them per RHS with FP64 scalars (bicgstab2.cu, qmr.cu); the
+oracle's bicgstab_l and qmr_sym state Sleijpen & Fokkema's and Freund's
+algorithms in numpy.  Iterates are compared after a fixed number of
 iterations (FP64), and converged solutions against dense LU.
 """
 import numpy as np
@@ -50,6 +51,26 @@ def _oracle_system(grid, m, kd, khat, ehat):
     return r, beta, A, E
 
 
+@pytest.mark.parametrize("k_iters", [1, 2, 5, 9, 17])
+def test_qmr_iterates_match_oracle(lib, k_iters):
+    """FP64 QMR stopped after k iterations (odd and even counts cross the
+    slot rotation and the 8-iteration graph blocks): the GPU iterate equals
+    the oracle's, with k + 1 matvecs counted."""
+    grid = block_bernoulli_grid(6, 5, 4, seed=3)
+    m = [1.7 + 0.3j, 1.3 + 0.02j]
+    ctx = _ctx(lib, grid, m, 1.4, 0)
+    kd = ctx.info()["kd"]
+    k, e = _rhs_set(2)
+    res, P, _ = ctx.solve(0, k, e, tol=1e-14, maxit=k_iters, solver="qmr", max_outer=1)
+    for i in range(2):
+        _, _, A, E = _oracle_system(grid, m, kd, k[i], e[i])
+        x, it, nmv, _ = odda.qmr_sym(lambda v: A @ v, E.ravel(), 0.0, k_iters)
+        assert it == k_iters and res[i]["iters"] == k_iters
+        assert res[i]["matvecs"] == k_iters + 1
+        assert _rel(P[i].T.ravel(), x) < 1e-10, (k_iters, i)
+    ctx.close()
+
+
 @pytest.mark.parametrize("k_iters", [1, 3, 6])
 def test_bicgstab2_iterates_match_oracle(lib, k_iters):
     """FP64 BiCGstab(2) stopped after k iterations: the GPU iterate equals the
@@ -69,15 +90,16 @@ def test_bicgstab2_iterates_match_oracle(lib, k_iters):
     ctx.close()
 
 
+@pytest.mark.parametrize("solver", ["bicgstab2", "qmr"])
 @pytest.mark.parametrize("prec,tol,qtol", [(0, 1e-12, 1e-10), (1, 1e-8, 1e-7), (2, 1e-5, 1e-4)],
                          ids=["fp64", "fp32_refined", "fp32"])
-def test_bicgstab2_solve_matches_dense_lu(lib, prec, tol, qtol):
+def test_solver_matches_dense_lu(lib, prec, tol, qtol, solver):
     grid = block_bernoulli_grid(7, 6, 5, seed=20120514)
     m = [1.7 + 0.3j, 1.2 + 0.01j]
     ctx = _ctx(lib, grid, m, 1.6)
     kd = ctx.info()["kd"]
     k, e = _rhs_set(3, 8)
-    res, P, st = ctx.solve(prec, k, e, tol=tol, maxit=2000, solver="bicgstab2")
+    res, P, st = ctx.solve(prec, k, e, tol=tol, maxit=2000, solver=solver)
     assert st == 0, res
     aeff = odda.aeff_lattice(int(np.count_nonzero(grid)))
     for i in range(3):
@@ -91,7 +113,8 @@ def test_bicgstab2_solve_matches_dense_lu(lib, prec, tol, qtol):
     ctx.close()
 
 
-def test_bicgstab2_batched_rhs_with_masks_agree_with_bicgstab(lib):
+@pytest.mark.parametrize("solver", ["bicgstab2", "qmr"])
+def test_batched_rhs_with_masks_agree_with_bicgstab(lib, solver):
     """Nine RHS in one batch (different directions converge at different
     iterations and drop out by their masks), with the captured graph: every
     solution equals the BiCGstab one to the tolerance."""
@@ -99,7 +122,7 @@ def test_bicgstab2_batched_rhs_with_masks_agree_with_bicgstab(lib):
     m = [1.5 + 0.1j]
     ctx = _ctx(lib, grid, m, 2.5)
     k, e = _rhs_set(9, 17)
-    r2, P2, st2 = ctx.solve(1, k, e, tol=1e-7, solver="bicgstab2")
+    r2, P2, st2 = ctx.solve(1, k, e, tol=1e-7, solver=solver)
     r1, P1, st1 = ctx.solve(1, k, e, tol=1e-7, solver="bicgstab")
     assert st1 == 0 and st2 == 0
     assert len({r["iters"] for r in r2}) > 1          # the masks did work
@@ -112,8 +135,10 @@ def test_bicgstab2_batched_rhs_with_masks_agree_with_bicgstab(lib):
 def test_au_brick_pbcgs2_iterations(lib):
     """The guide's FROM_FILE sample (32x64x64 Au block, m = 0.9656 + 1.8628i,
     x = 6.19, TOL = 1e-5), where PBCGS2 takes 29 and 30 iterations for the two
-    polarizations with GKDLDR polarizabilities.  With LATTDR both solvers
-    converge, BiCGstab(2) within a factor of two of the printed counts."""
+    polarizations with GKDLDR polarizabilities.  With LATTDR the solvers
+    converge (QMR, without look-ahead, in FP64: its complex64 Lanczos process
+    stalls on this metallic target), BiCGstab(2) within a factor of two of the
+    printed counts, all to the same efficiencies."""
     w = workload("aubrick32x64x64")
     ctx = _ctx(lib, w.grid, w.m, w.x)
     res2, _, st2 = ctx.solve(1, w.khat, w.ehat, tol=1e-5, want_P=False, solver="bicgstab2")
@@ -121,8 +146,11 @@ def test_au_brick_pbcgs2_iterations(lib):
     assert st1 == 0 and st2 == 0
     for r in res2:
         assert 15 <= r["iters"] <= 60, r["iters"]
-    for a, b in zip(res2, res1):
+    resq, _, stq = ctx.solve(0, w.khat, w.ehat, tol=1e-5, want_P=False, solver="qmr", maxit=3000)
+    assert stq == 0
+    for a, b, q in zip(res2, res1, resq):
         assert abs(a["qext"] - b["qext"]) < 1e-4 * abs(b["qext"])
+        assert abs(q["qext"] - b["qext"]) < 1e-4 * abs(b["qext"])
     ctx.close()
 
 
@@ -130,5 +158,5 @@ def test_unknown_solver_rejected(lib):
     ctx = _ctx(lib, np.ones((2, 2, 2), np.uint8), [1.5 + 0.1j], 0.5)
     k, e = _rhs_set(1)
     with pytest.raises(ValueError):
-        ctx.solve(1, k, e, solver="qmr")
+        ctx.solve(1, k, e, solver="cg")
     ctx.close()

@@ -100,7 +100,8 @@ typedef struct {
     double qext, qabs, qsca;  /* efficiency factors                                         */
     double resid_rel;         /* true relative residual |E - A P|/|E|, FP64 matvec           */
     double resid_normal_eq;   /* eq. err_tol form, or -1 if not requested                    */
-    int iters;                /* BiCGstab iterations (2 matvecs each), all refinement steps */
+    int iters;                /* Krylov iterations, all refinement steps (BiCGstab: 2 matvecs
+                                 each, BiCGstab(2): 4, QMR: 1)                              */
     int outer_iters;          /* refinement steps (1 for a converged plain solve)           */
     int matvecs;              /* A.x products applied to this RHS, all precisions           */
     dda_status status;        /* DDA_OK, DDA_ERR_NOT_CONVERGED, DDA_ERR_BREAKDOWN, ...      */

@@ -88,3 +88,21 @@ def test_scattering_directions_host_code_matches_oracle():
         assert t.size == t2.size
         assert np.abs(t - t2).max() < 1e-13 and np.abs(p - p2).max() < 1e-13 and np.abs(w - w2).max() < 1e-13
     assert dda.dda_scattering_directions(3.093665, 0.5)[0].size == 962
+
+
+def _header_struct_fields(name):
+    """Field names of `typedef struct { ... } name;` in include/dda.h, in order."""
+    text = open(os.path.join(ROOT, "include", "dda.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    m = re.search(r"typedef struct\s*\{([^{}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    return re.findall(r"(\w+)\s*(?=[,;])", m.group(1))
+
+
+@pytest.mark.parametrize("struct", ["dda_opts", "dda_result", "dda_info"])
+def test_binding_structs_match_header(struct):
+    """The ctypes mirrors of the ABI structs list the header's fields in order
+    (a field added on one side only would shift every later one)."""
+    import paper_1202_3424_gb300 as dda
+    ours = [name for name, _ in getattr(dda, struct)._fields_]
+    assert ours == _header_struct_fields(struct)

@@ -61,6 +61,8 @@ def parse():
                     help="matvec: only time dda_matvec_device (for profiler captures)")
     ap.add_argument("--rhs", type=int, default=0, help="matvec mode: RHS per product (0 = workload's)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="matvec mode precision")
+    ap.add_argument("--cufft", action="store_true",
+                    help="matvec mode: also time the same-size FFT convolution written with torch.fft (cuFFT)")
     ap.add_argument("--aniso", action="store_true",
                     help="solve/matvec modes: anisotropic version of the workload's materials (principal indices "
                          "m x (1, 1.05, 0.95), dielectric frame rotated by (0.4, 1.1, -0.6) rad)")
@@ -610,10 +612,62 @@ def run_matvec_only(args):
         kern[name] = {"avg_ms": avg, "gbs": (b / (avg / 1e3) / 1e9) if b else None}
     mv_roof = matvec_roofline(kst, info, "c64" if args.precision == "fp32" else "c128")
     zpass = ctx.get_schedule(R) if args.precision == "fp32" else 0
-    print(json.dumps({"mode": "matvec", "workload": w.name, "rhs": R, "precision": args.precision, "zpass": zpass,
-                      "ms_per_matvec": ms, "rhs_matvecs_per_s": R / (ms / 1e3), "kernels": kern,
-                      "matvec_roofline": mv_roof}), flush=True)
+    line = {"mode": "matvec", "workload": w.name, "rhs": R, "precision": args.precision, "zpass": zpass,
+            "ms_per_matvec": ms, "rhs_matvecs_per_s": R / (ms / 1e3), "kernels": kern, "matvec_roofline": mv_roof}
+    if args.cufft:
+        line["cufft_comparison"] = cufft_matvec_timing(w, info, R, dt, x, args.steps)
+        line["cufft_comparison"]["speedup_of_library"] = line["cufft_comparison"]["ms_per_matvec"] / ms
+    print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def cufft_matvec_timing(w, info, R, dt, x, steps, chunk_bytes=4 << 30):
+    """Timed comparison only: the same-size FFT-convolution matvec written with
+    torch.fft (cuFFT) -- scatter of the compact vectors into the zero-padded
+    grid, 3-D FFTs of the three components, the symmetric 3x3 product with a
+    full-grid Fourier-space tensor, inverse FFTs, gather at the occupied sites
+    and the diagonal term.  The tensor and the diagonal are random (their
+    values do not change the timing), so the result is not the DDA product."""
+    import torch
+    Lx, Ly, Lz = info["Lx"], info["Ly"], info["Lz"]
+    nz, ny, nx = w.grid.shape
+    dev = x.device
+    sites = torch.as_tensor(np.flatnonzero(w.grid.reshape(-1) != 0), device=dev)
+    iz, rem = sites // (ny * nx), sites % (ny * nx)
+    iy, ix = rem // nx, rem % nx
+    flat = (iz * Ly + iy) * Lx + ix                      # site -> padded-grid index
+    g = torch.Generator(device="cuda").manual_seed(2)
+    G = torch.randn((6, Lz, Ly, Lx), dtype=dt, device=dev, generator=g)
+    beta = torch.randn((R, 1, x.shape[2]), dtype=dt, device=dev, generator=g)
+    per_rhs = 3 * Lz * Ly * Lx * x.element_size()
+    rc = max(1, min(R, chunk_bytes // per_rhs))
+    y = torch.empty_like(x)
+
+    def matvec():
+        for r0 in range(0, R, rc):
+            xs = x[r0:r0 + rc]
+            n = xs.shape[0]
+            pad = torch.zeros((n, 3, Lz * Ly * Lx), dtype=dt, device=dev)
+            pad[:, :, flat] = xs
+            f = torch.fft.fftn(pad.view(n, 3, Lz, Ly, Lx), dim=(-3, -2, -1))
+            px, py, pz = f[:, 0], f[:, 1], f[:, 2]
+            f = torch.stack((G[0] * px + G[1] * py + G[2] * pz, G[1] * px + G[3] * py + G[4] * pz,
+                             G[2] * px + G[4] * py + G[5] * pz), dim=1)
+            out = torch.fft.ifftn(f, dim=(-3, -2, -1)).view(n, 3, -1)
+            y[r0:r0 + n] = out[:, :, flat] + beta[r0:r0 + n] * xs
+
+    for _ in range(3):
+        matvec()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        matvec()
+    e1.record()
+    e1.synchronize()
+    return {"ms_per_matvec": e0.elapsed_time(e1) / steps, "rhs_per_chunk": rc,
+            "what": "torch.fft (cuFFT) convolution of the same padded size, random full-grid tensor"}
 
 
 def run_grad(args):

@@ -652,10 +652,20 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
     int r = next_active(r0), v = 0;
     if (r < rend) prefetch(r, v);
     {
-        for (int e = threadIdx.x; e < 6 * HZ * TG; e += blockDim.x) {
-            const int tt = e % TG, kz = (e / TG) % HZ, cc = e / (TG * HZ);
-            const int gx = a + tt;
-            gs[(cc * HZ + kz) * TG + tt] = gx < hx ? gh[cc * cs + ((int64_t)kz * hy + kyo) * hx + gx] : czero<C>();
+        // (8 independent loads per thread in flight: the tile is read once
+        // per block, so its latency is the fixed cost of a launch)
+        constexpr int NS = 6 * HZ * TG, UN = 8;
+        for (int e0 = threadIdx.x; e0 < NS; e0 += UN * blockDim.x) {
+            C gv[UN];
+#pragma unroll
+            for (int q = 0; q < UN; ++q) {
+                const int e = e0 + q * blockDim.x;
+                const int tt = e % TG, kz = (e / TG) % HZ, cc = e / (TG * HZ);
+                gv[q] = (e < NS && a + tt < hx) ? gh[cc * cs + ((int64_t)kz * hy + kyo) * hx + a + tt] : czero<C>();
+            }
+#pragma unroll
+            for (int q = 0; q < UN; ++q)
+                if (e0 + q * blockDim.x < NS) gs[e0 + q * blockDim.x] = gv[q];
         }
         // twiddles from shared memory: the per-stage loads of the six
         // transforms per RHS then wait on shared, not L1, latency

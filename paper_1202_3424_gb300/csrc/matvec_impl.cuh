@@ -525,19 +525,46 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
     {
         const int kyo = ky <= Ly / 2 ? ky : Ly - ky;
         const bool fy = ky > Ly / 2;
-        for (int e = threadIdx.x; e < 6 * HZ * TP; e += blockDim.x) {
-            const int tt = e % TP, kz = (e / TP) % HZ, cc = e / (TP * HZ);
-            const int kxs = blockIdx.x * TP + tt;
-            C g = czero<C>();
-            if (kxs < Lx) {
-                const bool fx = kxs > Lx / 2;
-                const int kxo = fx ? Lx - kxs : kxs;
-                g = gh[cc * cs + ((int64_t)kz * hy + kyo) * hx + kxo];
-                // xy is odd in x and y, xz odd in x, yz odd in y (z handled at use)
-                const bool flip = (cc == 1 && fx != fy) || (cc == 2 && fx) || (cc == 4 && fy);
-                if (flip) g = cscale(g, T(-1));
+        if constexpr (LZ >= 512) {  // (the 512-point plan has no registers to spare)
+            for (int e = threadIdx.x; e < 6 * HZ * TP; e += blockDim.x) {
+                const int tt = e % TP, kz = (e / TP) % HZ, cc = e / (TP * HZ);
+                const int kxs = blockIdx.x * TP + tt;
+                C g = czero<C>();
+                if (kxs < Lx) {
+                    const bool fx = kxs > Lx / 2;
+                    const int kxo = fx ? Lx - kxs : kxs;
+                    g = gh[cc * cs + ((int64_t)kz * hy + kyo) * hx + kxo];
+                    // xy is odd in x and y, xz odd in x, yz odd in y (z handled at use)
+                    const bool flip = (cc == 1 && fx != fy) || (cc == 2 && fx) || (cc == 4 && fy);
+                    if (flip) g = cscale(g, T(-1));
+                }
+                gs[(cc * HZ + kz) * TP + tt] = g;
             }
-            gs[(cc * HZ + kz) * TP + tt] = g;
+        } else {
+            // 4 independent loads per thread in flight: the tile's latency is
+            // a fixed cost of every block
+            constexpr int NS = 6 * HZ * TP, UN = 4;
+            for (int e0 = threadIdx.x; e0 < NS; e0 += UN * blockDim.x) {
+                C gv[UN];
+#pragma unroll
+                for (int q = 0; q < UN; ++q) {
+                    const int e = e0 + q * blockDim.x;
+                    const int tt = e % TP, kz = (e / TP) % HZ, cc = e / (TP * HZ);
+                    const int kxs = blockIdx.x * TP + tt;
+                    const int kxo = kxs > Lx / 2 ? Lx - kxs : kxs;
+                    gv[q] = (e < NS && kxs < Lx) ? gh[cc * cs + ((int64_t)kz * hy + kyo) * hx + kxo] : czero<C>();
+                }
+#pragma unroll
+                for (int q = 0; q < UN; ++q) {
+                    const int e = e0 + q * blockDim.x;
+                    if (e >= NS) continue;
+                    const int tt = e % TP, cc = e / (TP * HZ);
+                    const bool fx = blockIdx.x * TP + tt > Lx / 2;
+                    // xy is odd in x and y, xz odd in x, yz odd in y (z handled at use)
+                    const bool flip = (cc == 1 && fx != fy) || (cc == 2 && fx) || (cc == 4 && fy);
+                    gs[e] = flip ? cscale(gv[q], T(-1)) : gv[q];
+                }
+            }
         }
         // twiddles from shared memory: the per-stage loads of the six
         // transforms per RHS then wait on shared, not L1, latency

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kThreads)
     double2 acc[1];
     block_totals<C, 1>(d, acc);
     if (last_block_total_reduced<1>(acc, part + (int64_t)r * gridDim.x, cnt + r) && threadIdx.x == 0) {
-        KState s = st[r];
+        KState& s = st[r];
         if (!finite2(acc[0])) stop(s, active, r, KS_NONFINITE);
         else if (s.rho.x == 0.0 && s.rho.y == 0.0) stop(s, active, r, KS_BREAKDOWN);
         else {
@@ -80,7 +80,6 @@ __global__ void __launch_bounds__(kThreads)
             s.omega = make_double2(0.0, 0.0);  // (the solve's first iteration starts with omega = 1)
             s.rho = acc[0];
         }
-        st[r] = s;
     }
 }
 
@@ -121,7 +120,7 @@ __global__ void __launch_bounds__(kThreads)
     double2 acc[5];
     block_totals<C, 5>(d, acc);
     if (last_block_total_reduced<5>(acc, part + (int64_t)r * gridDim.x * 5, cnt + r) && threadIdx.x == 0) {
-        KState s = st[r];
+        KState& s = st[r];
         const double s1 = acc[0].x;
         bool ok = true;
         for (int k = 0; k < 5; ++k) ok = ok && finite2(acc[k]);
@@ -144,7 +143,6 @@ __global__ void __launch_bounds__(kThreads)
                 s.gamma1 = csub(g1p, cmul(tau, g2p));  // gamma_1
             }
         }
-        st[r] = s;
     }
 }
 
@@ -172,7 +170,7 @@ __global__ void __launch_bounds__(kThreads)
     double2 acc[2];
     block_totals<C, 2>(d, acc);
     if (last_block_total_reduced<2>(acc, part + (int64_t)r * gridDim.x * 2, cnt + r) && threadIdx.x == 0) {
-        KState s = st[r];
+        KState& s = st[r];
         const double rn = sqrt(acc[1].x);
         s.rnorm = rn;
         s.iter += 1;
@@ -191,7 +189,6 @@ __global__ void __launch_bounds__(kThreads)
             s.omega = make_double2(0.0, 0.0);
             s.rho = acc[0];
         }
-        st[r] = s;
     }
 }
 

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kThreads)
     double2 acc[1];
     block_totals<C, 1>(d, acc);
     if (last_block_total_reduced<1>(acc, part + (int64_t)r * gridDim.x, cnt + r) && threadIdx.x == 0) {
-        KState s = st[r];
+        KState& s = st[r];  // (in place: a copy of the whole state costs registers)
         const double bn = sqrt(acc[0].x);
         s.bnorm = bn;
         s.rnorm = bn;
@@ -74,7 +74,6 @@ __global__ void __launch_bounds__(kThreads)
         } else {
             s.status = run ? KS_RUNNING : KS_IDLE;
         }
-        st[r] = s;
         active[r] = run;
     }
 }
@@ -159,7 +158,7 @@ __global__ void __launch_bounds__(kThreads)
     double2 acc[2];
     block_totals<C, 2>(d, acc);
     if (last_block_total_reduced<2>(acc, part + (int64_t)r * gridDim.x * 2, cnt + r) && threadIdx.x == 0) {
-        KState s = st[r];
+        KState& s = st[r];  // (in place: a copy of the whole state costs registers)
         const double rn = sqrt(acc[1].x);
         s.rnorm = rn;
         s.iter += 1;
@@ -179,7 +178,6 @@ __global__ void __launch_bounds__(kThreads)
             s.beta = cmul(zdiv(acc[0], s.rho), zdiv(s.alpha, s.omega));
             s.rho = acc[0];
         }
-        st[r] = s;
     }
 }
 

@@ -142,9 +142,12 @@ template <typename C> __device__ __forceinline__ C from2(double2 a) {
     return r;
 }
 
+// The finalizers update the fields they own in place: a copy of the whole
+// per-RHS state would take its registers in every kernel that inlines them.
+
 // sigma = <rhat, v>  ->  alpha = rho / sigma (breakdown if sigma == 0)
 __device__ __forceinline__ void finalize_alpha(KState* st, int* active, int r, double2 sig) {
-    KState s = st[r];
+    KState& s = st[r];
     if (!finite2(sig)) {
         s.status = KS_NONFINITE;
         active[r] = 0;
@@ -154,19 +157,17 @@ __device__ __forceinline__ void finalize_alpha(KState* st, int* active, int r, d
     } else {
         s.alpha = zdiv(s.rho, sig);
     }
-    st[r] = s;
 }
 
 // omega = <t, s> / <t, t>  (0 when t = 0: then s = 0 and the update converges)
 __device__ __forceinline__ void finalize_omega(KState* st, int* active, int r, double2 ts, double tt) {
-    KState s = st[r];
+    KState& s = st[r];
     if (!finite2(ts) || !isfinite(tt)) {
         s.status = KS_NONFINITE;
         active[r] = 0;
     } else {
         s.omega = tt > 0.0 ? make_double2(ts.x / tt, ts.y / tt) : make_double2(0.0, 0.0);
     }
-    st[r] = s;
 }
 
 }  // namespace dda

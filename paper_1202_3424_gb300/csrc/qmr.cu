@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kThreads)
     double2 acc[1];
     block_totals<C, 1>(d, acc);
     if (last_block_total_reduced<1>(acc, part + (int64_t)r * gridDim.x, cnt + r) && threadIdx.x == 0) {
-        KState s = st[r];
+        KState& s = st[r];
         QmrScalars& q = s.q;
         q.delta = acc[0];
         q.delta_prev = make_double2(1.0, 0.0);
@@ -94,7 +94,6 @@ __global__ void __launch_bounds__(kThreads)
         q.best_iter = 0;
         if (!finite2(acc[0])) stop(s, active, r, KS_NONFINITE);
         else if (dzero(acc[0])) stop(s, active, r, KS_BREAKDOWN);
-        st[r] = s;
     }
 }
 
@@ -109,10 +108,9 @@ __global__ void __launch_bounds__(kThreads)
     double2 acc[1];
     block_totals<C, 1>(d, acc);
     if (last_block_total_reduced<1>(acc, part + (int64_t)r * gridDim.x, cnt + r) && threadIdx.x == 0) {
-        KState s = st[r];
+        KState& s = st[r];
         if (!finite2(acc[0])) stop(s, active, r, KS_NONFINITE);
         else s.q.alpha = zdiv(acc[0], s.q.delta);
-        st[r] = s;
     }
 }
 
@@ -135,11 +133,10 @@ __global__ void __launch_bounds__(kThreads)
     double2 acc[2];
     block_totals<C, 2>(d, acc);
     if (last_block_total_reduced<2>(acc, part + (int64_t)r * gridDim.x * 2, cnt + r) && threadIdx.x == 0) {
-        KState s = st[r];
+        KState& s = st[r];
         QmrScalars& q = s.q;
         if (!finite2(acc[0]) || !finite2(acc[1])) {
             stop(s, active, r, KS_NONFINITE);
-            st[r] = s;
             return;
         }
         const double bn = sqrt(acc[0].x);
@@ -179,7 +176,6 @@ __global__ void __launch_bounds__(kThreads)
         } else {
             q.inv_beta = 0.0;  // invariant subspace: this step's iterate is exact
         }
-        st[r] = s;
     }
 }
 
@@ -212,7 +208,7 @@ __global__ void __launch_bounds__(kThreads)
     double2 acc[1];
     block_totals<C, 1>(d, acc);
     if (last_block_total_reduced<1>(acc, part + (int64_t)r * gridDim.x, cnt + r) && threadIdx.x == 0) {
-        KState s = st[r];
+        KState& s = st[r];
         const double rn = sqrt(acc[0].x);
         s.rnorm = rn;
         s.iter += 1;
@@ -224,7 +220,6 @@ __global__ void __launch_bounds__(kThreads)
         else if (rn <= s.tol_abs) stop(s, active, r, KS_CONVERGED);
         else if (s.iter >= s.maxit || s.iter - s.q.best_iter >= kQmrStall) stop(s, active, r, KS_MAXIT);
         else if (s.q.inv_beta == 0.0 || s.q.lanczos_breakdown) stop(s, active, r, KS_BREAKDOWN);
-        st[r] = s;
     }
 }
 

@@ -15,7 +15,10 @@
  * is silent (LATTDR polarizability of Draine & Goodman 1993, Draine 1988
  * interaction tensor and cross sections):
  *   1/alpha = (4pi/3)(eps+2)/(eps-1) + (b1 + b2 eps + b3 eps S)(kd)^2 - (2/3) i (kd)^3,
- *   b1 = -1.8915316, b2 = 0.1648469, b3 = -1.7700004, S = sum_a (khat_a e_a)^2,
+ *   b1 = -1.8915316, b2 = 0.1648469, b3 = -1.7700004, S = sum_a khat_a^2 |e_a|^2
+ *   (= sum_a (khat_a e_a)^2 for a real e; for a complex e the |e_a|^2 form is the
+ *   one that keeps the lattice dispersion relation exact on the cube's 3-fold
+ *   axes, where circular polarizations are lattice modes too),
  *   A_jl = e^{ik rho}/rho [k^2 (rr - I) + (ik rho - 1)/rho^2 (3 rr - I)]  (j != l),
  *   A_jj = (1/alpha_j) I  (anisotropic materials: the 1/alpha tensor of site j),
  *   C_ext = 4 pi k sum Im(E_inc^* . P),  C_abs = 4 pi k sum (-Im(1/alpha) - 2k^3/3)|P|^2

@@ -13,11 +13,11 @@ Contents
                pairwise matvec, cross sections, pair-sum and quadrature C_sca,
                adjoint dQ_abs/d(eps).
   mie       -- Mie-series efficiencies for a homogeneous sphere.
+  lattice   -- Ewald evaluation of the dipole lattice sum that defines the
+               LATTDR polarizability (pins its constants and the form of S).
   pairwise  -- the same pairwise matvec in plain C with OpenMP (for sizes where
                numpy is too slow: row samples of large targets, timed baseline).
 
 Parity status per function is stated in each docstring ("pinned by ...").
-Functions whose constants could not be pinned from the guide say
-"parity unpinned" for that part.
 """
-from . import dda, mie  # noqa: F401
+from . import dda, lattice, mie  # noqa: F401

@@ -19,8 +19,10 @@ import numpy as np
 
 # LATTDR coefficients of the lattice dispersion relation (Draine & Goodman
 # 1993), cited by the guide in "Dipole Polarizabilities".  The guide does not
-# print them: parity unpinned for these three numbers (they are pinned only
-# indirectly, through convergence to the Mie series as N grows).
+# print them.  Pinned by the relation's defining property: the second-order
+# coefficient of the lattice sum of oracle.lattice, extrapolated to kd -> 0
+# over several refractive indices and directions, is b1 + b2 eps + b3 eps S
+# with these values to 1e-6.
 LDR_B1 = -1.8915316
 LDR_B2 = 0.1648469
 LDR_B3 = -1.7700004
@@ -60,17 +62,24 @@ def ldr_inverse_polarizability(eps, kd: float, khat, ehat) -> np.ndarray:
 
     alpha_CM = (3/4pi) (eps-1)/(eps+2)          (Clausius-Mossotti, d = 1)
     1/alpha  = 1/alpha_CM + (b1 + b2 eps + b3 eps S) (kd)^2 - (2/3) i (kd)^3
-    S        = sum_a (khat_a ehat_a)^2            (ehat as given, unconjugated)
+    S        = sum_a khat_a^2 |ehat_a|^2         (ehat a unit vector)
 
-    eps may be an array (one value per composition or per dipole).  The
-    -(2/3) i k^3 term is the radiative-reaction correction; pinned by the
-    N = 1 closed forms and the lossless invariant (C_abs = 0 for real eps).
-    The b_i are parity unpinned (see module constants).
+    eps may be an array (one value per composition or per dipole).  Pinned by
+    the defining property of the lattice dispersion relation: this 1/alpha
+    equals e^* T(m k khat) e, the lattice sum of oracle.lattice, up to
+    O((kd)^4), for every direction and polarization, real and complex.  For a
+    real ehat, S = sum_a (khat_a ehat_a)^2, Draine & Goodman's form; for a
+    complex one the lattice sum decides between the candidate extensions: on
+    a 3-fold axis of the cube every transverse ehat (circular too) is a mode
+    of the lattice with one eigenvalue, which the |ehat_a|^2 form reproduces
+    and the unconjugated square (zero for circular ehat there) does not.  The
+    -(2/3) i k^3 term is the radiative-reaction correction, also pinned by
+    the N = 1 closed forms and the lossless invariant.
     """
     eps = np.asarray(eps, dtype=np.complex128)
     khat = np.asarray(khat, dtype=np.float64)
     ehat = np.asarray(ehat, dtype=np.complex128)
-    S = np.sum((khat * ehat) ** 2)
+    S = np.sum(khat ** 2 * np.abs(ehat) ** 2)
     inv_acm = (4.0 * math.pi / 3.0) * (eps + 2.0) / (eps - 1.0)
     return inv_acm + (LDR_B1 + LDR_B2 * eps + LDR_B3 * eps * S) * kd ** 2 - (2.0 / 3.0) * 1j * kd ** 3
 
@@ -105,7 +114,7 @@ def ldr_inverse_tensor(eps3, angles, kd: float, khat, ehat) -> np.ndarray:
 def ldr_inverse_polarizability_derivative(eps, kd: float, khat, ehat) -> np.ndarray:
     """d(1/alpha)/d(eps) of the LATTDR form above: -4pi/(eps-1)^2 + (b2 + b3 S) k^2."""
     eps = np.asarray(eps, dtype=np.complex128)
-    S = np.sum((np.asarray(khat, float) * np.asarray(ehat, complex)) ** 2)
+    S = np.sum(np.asarray(khat, float) ** 2 * np.abs(np.asarray(ehat, complex)) ** 2)
     return -4.0 * math.pi / (eps - 1.0) ** 2 + (LDR_B2 + LDR_B3 * S) * kd ** 2
 
 

@@ -179,16 +179,24 @@ void free_mem(DevMem& m) {
     m.bytes = 0;
 }
 
+// S = sum_a khat_a^2 |e_a|^2 for a unit e: for a real e this is Draine &
+// Goodman's sum_a (khat_a e_a)^2; for a complex e it is the form that keeps
+// the lattice dispersion relation exact on the cube's 3-fold axes, where every
+// transverse polarization (circular ones too) is a lattice mode.
+double ldr_s(const double* khat, const cd* e) {
+    double S = 0.0;
+    for (int a = 0; a < 3; ++a) S += khat[a] * khat[a] * std::norm(e[a]);
+    return S;
+}
+
 cd ldr_inverse_alpha(cd eps, double kd, const double* khat, const cd* e) {
-    cd S = 0.0;
-    for (int a = 0; a < 3; ++a) S += (khat[a] * e[a]) * (khat[a] * e[a]);
+    const double S = ldr_s(khat, e);
     const cd inv_acm = (4.0 * kPi / 3.0) * (eps + 2.0) / (eps - 1.0);
     return inv_acm + (kB1 + kB2 * eps + kB3 * eps * S) * (kd * kd) - cd(0.0, 2.0 / 3.0) * (kd * kd * kd);
 }
 
 cd ldr_inverse_alpha_deps(cd eps, double kd, const double* khat, const cd* e) {
-    cd S = 0.0;
-    for (int a = 0; a < 3; ++a) S += (khat[a] * e[a]) * (khat[a] * e[a]);
+    const double S = ldr_s(khat, e);
     return -4.0 * kPi / ((eps - 1.0) * (eps - 1.0)) + (kB2 + kB3 * S) * (kd * kd);
 }
 

@@ -175,6 +175,28 @@ MUTATIONS = [
      [pins.bicgstab_l1_vs_bicgstab_error, pins.bicgstab_l2_mr_error]),
     ("bicgstab_l", _mutant(dda.bicgstab_l, "x = x + gpp[j] * r[j]", "x = x - gpp[j] * r[j]"),
      [pins.bicgstab_l2_mr_error]),
+    ("ldr_inverse_polarizability", _mutant(dda.ldr_inverse_polarizability, "(LDR_B1 + LDR_B2", "(-LDR_B1 + LDR_B2"),
+     [pins.ldr_dispersion_error]),
+    ("ldr_inverse_polarizability", _mutant(dda.ldr_inverse_polarizability, "+ LDR_B2 * eps +", "- LDR_B2 * eps +"),
+     [pins.ldr_dispersion_error]),
+    ("ldr_inverse_polarizability", _mutant(dda.ldr_inverse_polarizability, "LDR_B2 * eps +", "LDR_B2 +"),
+     [pins.ldr_dispersion_error]),
+    ("ldr_inverse_polarizability", _mutant(dda.ldr_inverse_polarizability, "+ LDR_B3 * eps * S)", "- LDR_B3 * eps * S)"),
+     [pins.ldr_dispersion_error]),
+    ("ldr_inverse_polarizability", _mutant(dda.ldr_inverse_polarizability, "LDR_B3 * eps * S)", "LDR_B3 * eps)"),
+     [pins.ldr_dispersion_error]),
+    ("ldr_inverse_polarizability", _mutant(dda.ldr_inverse_polarizability, "LDR_B3 * eps * S)", "LDR_B3 * S)"),
+     [pins.ldr_dispersion_error]),
+    ("ldr_inverse_polarizability", _mutant(dda.ldr_inverse_polarizability, "S = np.sum(khat ** 2 * np.abs(ehat) ** 2)",
+                                           "S = np.sum((khat * ehat) ** 2)"), [pins.ldr_dispersion_error]),
+    ("ldr_inverse_polarizability", _mutant(dda.ldr_inverse_polarizability, "S = np.sum(khat ** 2 * np.abs(ehat) ** 2)",
+                                           "S = np.sum((khat * np.conj(ehat)) ** 2)"), [pins.ldr_dispersion_error]),
+    ("ldr_inverse_polarizability", _mutant(dda.ldr_inverse_polarizability, "S = np.sum(khat ** 2 * np.abs(ehat) ** 2)",
+                                           "S = np.sum(np.abs(khat * ehat))"), [pins.ldr_dispersion_error]),
+    ("ldr_inverse_polarizability", _mutant(dda.ldr_inverse_polarizability, "* kd ** 2 -", "* kd ** 3 -"),
+     [pins.ldr_dispersion_error]),
+    ("ldr_inverse_polarizability", _mutant(dda.ldr_inverse_polarizability, "(eps + 2.0) / (eps - 1.0)",
+                                           "(eps + 2.0) / (eps + 1.0)"), [pins.ldr_dispersion_error]),
     ("qmr_sym", _mutant(dda.qmr_sym, "alpha = (v @ w) / delta", "alpha = np.vdot(v, w) / delta"),
      [pins.qmr_complex_symmetric_error]),
     ("qmr_sym", _mutant(dda.qmr_sym, "gamma = beta_next * delta / delta_prev", "gamma = beta_next"),
@@ -191,6 +213,15 @@ def test_planted_mistake_is_caught(monkeypatch, name, fn, checks):
     monkeypatch.setattr(dda, name, fn)
     worst = max(check() for check in checks)
     assert worst > 1e-6, f"mutation {fn.__name__} of {name} not caught (error {worst})"
+
+
+@pytest.mark.parametrize("name,delta", [("LDR_B1", 1e-4), ("LDR_B2", -1e-4), ("LDR_B3", 1e-4)])
+def test_ldr_constant_drift_is_caught(monkeypatch, name, delta):
+    """A constant off in its fifth significant digit no longer matches the
+    coefficients that the lattice sum gives."""
+    monkeypatch.setattr(dda, name, getattr(dda, name) + delta)
+    b = pins.ldr_coefficients_from_lattice()
+    assert np.abs(b - [dda.LDR_B1, dda.LDR_B2, dda.LDR_B3]).max() > 5e-5
 
 
 def test_mie_planted_mistake_is_caught(monkeypatch, golden_dir):

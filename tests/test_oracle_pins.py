@@ -12,7 +12,7 @@ import pytest
 
 from dda_inputs import (block_bernoulli_grid, ellipsoid_grid, random_complex, sphere_grid,
                         uniform_directions, polarization_pair, workload)
-from oracle import dda, mie, pairwise
+from oracle import dda, lattice, mie, pairwise
 
 
 # ----------------------------------------------------------------- helpers --
@@ -490,6 +490,132 @@ def test_ldr_reduces_to_clausius_mossotti_at_zero_frequency():
     eps = np.array([2.0 + 0.5j, 5.0 + 1.0j])
     b = dda.ldr_inverse_polarizability(eps, 0.0, [1, 0, 0], [0, 1, 0])
     assert np.allclose(1.0 / b, (3 / (4 * math.pi)) * (eps - 1) / (eps + 2), rtol=1e-15)
+
+
+# ------------------------------------------- lattice dispersion relation --
+def _unit(v):
+    v = np.asarray(v, dtype=np.complex128)
+    return v / np.sqrt(np.vdot(v, v).real)
+
+
+def _transverse_pair(khat):
+    """Two real unit vectors perpendicular to khat and to each other."""
+    k = np.asarray(khat, float) / np.linalg.norm(khat)
+    a = np.cross([0.0, 0.0, 1.0], k) if abs(k[2]) < 0.9 else np.cross([1.0, 0.0, 0.0], k)
+    a /= np.linalg.norm(a)
+    return k, a, np.cross(k, a)
+
+
+# Directions and polarizations of the LDR pins: lattice axes, face and body
+# diagonals, a generic direction; linear, circular and elliptical states.
+_LDR_CASES = []
+for _kv in ((1, 0, 0), (1, 1, 0), (1, 1, 1), (1, 2, 3), (-2, 1, 4)):
+    _k, _a, _b = _transverse_pair(_kv)
+    for _ev in (_a, 0.6 * _a + 0.8 * _b, _a + 1j * _b, _a + 0.4j * _b):
+        _LDR_CASES.append((_k, _unit(_ev)))
+
+
+def brute_force_lattice_sum(kd, q, nmax):
+    """sum_{0 < |l_a| <= nmax} G(r_l) exp(i q.l) with G the textbook dipole
+    field tensor (Jackson eq. 9.18 as a matrix), written out here; converges
+    absolutely when Im kd > |Im q|."""
+    g = np.arange(-nmax, nmax + 1, dtype=float)
+    L = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    L = L[np.any(L != 0, axis=1)]
+    r = np.linalg.norm(L, axis=1)
+    n = L / r[:, None]
+    nn = n[:, :, None] * n[:, None, :]
+    eye = np.eye(3)
+    e = np.exp(1j * kd * r) / r
+    G = (kd * kd * e)[:, None, None] * (eye - nn) + (e * (1 - 1j * kd * r) / r ** 2)[:, None, None] * (3 * nn - eye)
+    return np.einsum("l,lab->ab", np.exp(1j * (L @ np.asarray(q, complex))), G)
+
+
+def ewald_consistency_error():
+    """The Ewald sum against itself at three splitting parameters, and against
+    the brute-force site sum at a damped wavenumber (Im kd = 0.9: terms fall
+    as e^{-0.9 r}, so |l_a| <= 36 reaches 1e-13)."""
+    q = np.array([0.31, -0.17, 0.22])
+    errs = []
+    for kd in (0.37, 0.05 + 0.0j):
+        Ts = [lattice.dipole_lattice_sum(kd, 1.4 * q, eta=eta) for eta in (0.9, 1.3, 1.8)]
+        errs += [np.abs(T - Ts[0]).max() / np.abs(Ts[0]).max() for T in Ts[1:]]
+    kd = 0.6 + 0.9j
+    ref = brute_force_lattice_sum(kd, q, 36)
+    errs.append(np.abs(lattice.dipole_lattice_sum(kd, q) - ref).max() / np.abs(ref).max())
+    return max(errs)
+
+
+def _ldr_residuals(m, kd):
+    """|e^* T(m kd khat) e - 1/alpha_oracle| over the direction/polarization cases."""
+    eps = m * m
+    return np.array([abs(lattice.lattice_mode_inverse_polarizability(eps, kd, k, e)
+                         - dda.ldr_inverse_polarizability(eps, kd, k, e)) for k, e in _LDR_CASES])
+
+
+def ldr_dispersion_error():
+    """The LATTDR 1/alpha meets its defining property to O((kd)^4): the
+    residual against the lattice sum, divided by (kd)^4, stays below 2 at
+    kd = 0.02 and 0.01 (measured 0.10-0.62) for three refractive indices,
+    real ehat and complex ehat.  A wrong b_i, a wrong S or a wrong power of kd
+    leaves an O((kd)^2) residual, 10^4 times larger.  Returns the excess over
+    the bound (0 when met)."""
+    worst = 0.0
+    for m in (1.3, 1.7, 2.4):
+        for kd in (0.02, 0.01):
+            worst = max(worst, float(_ldr_residuals(m, kd).max()) / kd ** 4)
+    return max(0.0, worst - 2.0)
+
+
+def ldr_coefficients_from_lattice():
+    """b1, b2, b3 extracted from the lattice sum alone: for real m and real
+    ehat, c(kd) = [e.T.e - (4pi/3)(eps+2)/(eps-1) + (2/3) i kd^3] / kd^2 =
+    b1 + b2 eps + b3 eps S + O(kd^2); Richardson's step (4 c(h/2) - c(h))/3
+    removes the O(kd^2) term, and a least-squares fit over several eps and S
+    gives the three constants."""
+    rows, rhs = [], []
+    for m in (1.2, 1.6, 2.1):
+        eps = m * m
+        inv_cm = (4 * math.pi / 3) * (eps + 2) / (eps - 1)
+        for kv in ((1, 0, 0), (1, 1, 0), (1, 1, 1), (1, 2, 3)):
+            k, a, _ = _transverse_pair(kv)
+            S = float(np.sum((k * a) ** 2))
+            c = [(lattice.lattice_mode_inverse_polarizability(eps, h, k, a) - inv_cm
+                  + (2.0 / 3.0) * 1j * h ** 3).real / h ** 2 for h in (0.02, 0.01)]
+            rows.append([1.0, eps, eps * S])
+            rhs.append((4 * c[1] - c[0]) / 3)
+    b, *_ = np.linalg.lstsq(np.array(rows), np.array(rhs), rcond=None)
+    return b
+
+
+def test_ewald_lattice_sum_is_consistent():
+    assert ewald_consistency_error() < 1e-11
+
+
+def test_ldr_meets_the_lattice_dispersion_relation():
+    assert ldr_dispersion_error() == 0.0
+
+
+def test_ldr_constants_follow_from_the_lattice_sum():
+    b = ldr_coefficients_from_lattice()
+    assert np.abs(b - [dda.LDR_B1, dda.LDR_B2, dda.LDR_B3]).max() < 1e-6, b
+
+
+def test_circular_polarization_is_a_lattice_mode_on_the_body_diagonal():
+    """On the 3-fold axis every transverse e is an eigenvector of T with one
+    eigenvalue, so the LDR 1/alpha must not depend on the polarization
+    state there (this is what fixes S for complex e)."""
+    k, a, b = _transverse_pair((1, 1, 1))
+    m, kd = 1.5, 0.01
+    T = lattice.dipole_lattice_sum(kd, m * kd * k)
+    inv = []
+    for e in (_unit(a), _unit(a + 1j * b), _unit(b - 0.3j * a)):
+        Te = T @ e
+        lam = np.vdot(e, Te)
+        assert np.linalg.norm(Te - lam * e) < 1e-9
+        inv.append(dda.ldr_inverse_polarizability(m * m, kd, k, e))
+        assert abs(inv[-1] - lam) < kd ** 4
+    assert max(abs(v - inv[0]) for v in inv) < 1e-14
 
 
 def test_ldr_derivative_matches_finite_difference():

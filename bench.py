@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--fp64-sequential", action="store_true",
                     help="FP64 leg solves the RHS one at a time (orientation-sweep comparison)")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the 128-RHS ellipsoid sweep block of the default solve run")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the FP64 reference solve (tol 1e-10) behind q_relerr_vs_fp64")
     ap.add_argument("--ext", type=float, default=0.5, help="nearfield mode: extension fraction on every side")
     ap.add_argument("--eta", type=float, default=0.5, help="farfield mode: ETASCA of the scattering directions")
     ap.add_argument("--mode", default="solve", choices=["solve", "matvec", "grad", "nearfield", "farfield"],
@@ -332,7 +336,8 @@ def run_gb300(args):
         step(dda.Precision.FP64)
         per64, mv64, res64, _ = timed(dda.Precision.FP64, args.fp64_steps)
         fp64 = {"time_to_solution_ms": sum(per64) / len(per64), "matvecs_per_s": mv64 / (sum(per64) / 1e3),
-                "iters": [r["iters"] for r in res64], "resid_rel": [r["resid_rel"] for r in res64]}
+                "iters": [r["iters"] for r in res64], "resid_rel": [r["resid_rel"] for r in res64],
+                "q": [[r["qext"], r["qabs"], r["qsca"]] for r in res64]}
     elif args.fp64_steps > 0:
         # orientation sweep as a plain FP64 single-RHS loop: one solve per RHS
         P1 = torch.empty((1, 3, N), dtype=torch.complex128, device=dev)
@@ -381,9 +386,21 @@ def run_gb300(args):
         if kstats else None
     launches = int(sum(s["launches"] for s in kstats.values()) / args.steps) * args.steps if kstats else 0
 
+    # error of the production mode per result, against an FP64 solve to 1e-10
+    accuracy = None
+    if not args.no_accuracy:
+        accuracy = accuracy_vs_fp64(dda, ctx, w, P_dev, res, fp64["q"] if fp64 and "q" in fp64 else None)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, info, budget_s=12.0)
+
+    sweep = None
+    if args.mode == "solve" and args.workload == "sphere64" and not args.no_sweep and not args.aniso \
+            and args.solver == "bicgstab":
+        ctx.close()
+        ctx = None
+        sweep = ellipsoid_sweep(dda, dev, stream, flush, dist)
 
     if rank == 0:
         line = {
@@ -404,12 +421,135 @@ def run_gb300(args):
             "traced_ms_per_step": sum(per_tr) / len(per_tr),
             "kernels": {k_: {"launches": v["launches"], "ms": v["ms"], "share": v["share"]} for k_, v in kstats.items()},
             "roofline": roof, "matvec_roofline": mv_roof,
+            "q_relerr_vs_fp64": accuracy,
+            "ellipsoid_sweep_128rhs": sweep,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
-    ctx.close()
+    if ctx is not None:
+        ctx.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _q_relerr(q, qref):
+    """Per RHS: |Q - Q_ref| / |Q_ref| for Q_ext, Q_abs, Q_sca."""
+    return [[abs(a - b) / abs(b) for a, b in zip(qi, qr)] for qi, qr in zip(q, qref)]
+
+
+def accuracy_vs_fp64(dda, ctx, w, P_dev, res, q_fp64_tol5=None, tol_ref=1e-10):
+    """Error of the FP32-refined results (tol 1e-5) per RHS and per
+    efficiency factor, against a plain FP64 solve of the same RHS to
+    tol_ref on the same GPU (the FP64 path matches the CPU oracle to 1e-10).
+    The FP64 solve to 1e-5 is shown beside it: both stop at the same
+    residual, so their distance from the tight solution is of one size."""
+    import torch
+    Pref = torch.empty_like(P_dev)
+    rref, st = dda.dda_solve_device(ctx.handle, dda.Precision.FP64, w.khat, w.ehat, Pref, tol=tol_ref, maxit=4000)
+    if st != 0:
+        return {"error": f"FP64 reference solve status {st}"}
+    qref = [[r["qext"], r["qabs"], r["qsca"]] for r in rref]
+    q = [[r["qext"], r["qabs"], r["qsca"]] for r in res]
+    err = _q_relerr(q, qref)
+    out = {"what": "per RHS [Q_ext, Q_abs, Q_sca] relative error of the FP32-refined solve (tol 1e-5) vs a "
+                   f"plain FP64 solve to tol {tol_ref:g}",
+           "fp32_refined": err, "max": max(max(e) for e in err), "q_ref": qref,
+           "ref_resid_rel": [r["resid_rel"] for r in rref]}
+    if q_fp64_tol5 is not None:
+        e64 = _q_relerr(q_fp64_tol5, qref)
+        out["fp64_tol1e-5"] = e64
+        out["fp64_tol1e-5_max"] = max(max(e) for e in e64)
+    return out
+
+
+def ellipsoid_sweep(dda, dev, stream, flush, dist, steps=3, warmup=2):
+    """The 128-RHS orientation sweep of the 3:2:1 ellipsoid (96x64x32, 64
+    seeded directions x 2 polarizations): one batched FP32-refined solve of
+    all RHS (shared Green tensor, per-RHS masks, graph replay) against 128
+    sequential single-RHS plain FP64 solves, the whole matvec alone and
+    inside the solve against HBM, and the per-result error on 16 RHS."""
+    import torch
+    w = workload("ellipsoid96x64x32")
+    R = w.nrhs
+    ctx = dda.Context(dev.index)
+    dda.dda_set_stream(ctx.handle, stream.cuda_stream)
+    ctx.set_target(w.grid)
+    ctx.set_materials(w.m)
+    ctx.prepare_size_parameter(w.x, dda.Precision.FP32_REFINED)
+    info = ctx.info()
+    N = info["ndipoles"]
+    P = torch.empty((R, 3, N), dtype=torch.complex128, device=dev)
+
+    def solve(prec, k, e, out, tol=1e-5):
+        rr, st = dda.dda_solve_device(ctx.handle, prec, k, e, out, tol=tol, maxit=3000)
+        if st != 0:
+            raise RuntimeError(f"sweep solve failed: {[r['status_name'] for r in rr]}")
+        return rr
+
+    def event_ms(fn):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), out
+
+    for _ in range(warmup):
+        solve(dda.Precision.FP32_REFINED, w.khat, w.ehat, P)
+    torch.cuda.synchronize()
+    per, res = [], None
+    for _ in range(steps):
+        ms, res = event_ms(lambda: solve(dda.Precision.FP32_REFINED, w.khat, w.ehat, P))
+        per.append(ms)
+    t_b = statistics.median(per)
+    mv = sum(r["matvecs"] for r in res)
+    # traced solve: the five passes inside the solve against HBM
+    L = dda.load_library()
+    L.dda_profile_enable(ctx.handle, 1)
+    solve(dda.Precision.FP32_REFINED, w.khat, w.ehat, P)
+    kin = read_profile(dda, ctx)
+    L.dda_profile_enable(ctx.handle, 0)
+    mv_in = matvec_roofline(kin, info, "c64", rhs_matvecs=sum(2 * r["iters"] for r in res))
+    # the matvec alone (128 RHS per product)
+    x = torch.randn((R, 3, N), dtype=torch.complex64, device=dev, generator=torch.Generator(device=dev).manual_seed(1))
+    y = torch.empty_like(x)
+    for _ in range(3):
+        dda.dda_matvec_device(ctx.handle, 2, w.khat, w.ehat, x, y)
+    ms_mv, _ = event_ms(lambda: [dda.dda_matvec_device(ctx.handle, 2, w.khat, w.ehat, x, y) for _ in range(10)])
+    L.dda_profile_enable(ctx.handle, 1)
+    for _ in range(10):
+        dda.dda_matvec_device(ctx.handle, 2, w.khat, w.ehat, x, y)
+    kmv = read_profile(dda, ctx)
+    L.dda_profile_enable(ctx.handle, 0)
+    mv_alone = matvec_roofline(kmv, info, "c64")
+    del x, y
+    # 128 sequential single-RHS plain FP64 solves (the orientation loop without batching)
+    P1 = torch.empty((1, 3, N), dtype=torch.complex128, device=dev)
+    solve(dda.Precision.FP64, w.khat[:1], w.ehat[:1], P1)
+    torch.cuda.synchronize()
+    t_64, seq = event_ms(lambda: [solve(dda.Precision.FP64, w.khat[i:i + 1], w.ehat[i:i + 1], P1)[0]
+                                  for i in range(R)])
+    # per-result error on the first 16 RHS against FP64 to 1e-10
+    n_acc = 16
+    P16 = torch.empty((n_acc, 3, N), dtype=torch.complex128, device=dev)
+    rref = solve(dda.Precision.FP64, w.khat[:n_acc], w.ehat[:n_acc], P16, tol=1e-10)
+    err = _q_relerr([[r["qext"], r["qabs"], r["qsca"]] for r in res[:n_acc]],
+                    [[r["qext"], r["qabs"], r["qsca"]] for r in rref])
+    err64 = _q_relerr([[r["qext"], r["qabs"], r["qsca"]] for r in seq[:n_acc]],
+                      [[r["qext"], r["qabs"], r["qsca"]] for r in rref])
+    ctx.close()
+    return {"workload": f"{w.name}: lattice {info['nx']}x{info['ny']}x{info['nz']}, N={N}, m={w.m}, x={w.x}, "
+                        f"{R} RHS (64 seeded directions x 2 polarizations), tol 1e-5",
+            "batched_fp32_refined_ms": t_b, "batched_rhs_matvecs_per_s": mv / (t_b / 1e3),
+            "iters_min_max": [min(r["iters"] for r in res), max(r["iters"] for r in res)],
+            "max_resid_rel": max(r["resid_rel"] for r in res),
+            "sequential_fp64_single_rhs_ms": t_64, "speedup_vs_sequential_fp64": t_64 / t_b,
+            "matvec_alone_ms": ms_mv / 10, "matvec_alone_roofline": mv_alone, "matvec_in_solve_roofline": mv_in,
+            "q_relerr_vs_fp64_first16": {"fp32_refined": err, "max": max(max(e) for e in err),
+                                         "fp64_tol1e-5_max": max(max(e) for e in err64),
+                                         "ref": "plain FP64 solve to tol 1e-10"},
+            "steps": steps, "warmup": warmup, "l2": "256 MB buffer written before each timed solve"}
 
 
 def read_profile(dda, ctx):

@@ -101,7 +101,10 @@ enum { DDA_SOLVER_BICGSTAB = 0, DDA_SOLVER_BICGSTAB2 = 1, DDA_SOLVER_QMR = 2 };
 
 typedef struct {
     double qext, qabs, qsca;  /* efficiency factors                                         */
-    double resid_rel;         /* true relative residual |E - A P|/|E|, FP64 matvec           */
+    double resid_rel;         /* true relative residual |E - A P|/|E| on FP64 vectors; its   *
+                               * matvec is native FP64 for DDA_FP64, and for the complex64    *
+                               * modes double-float (FP32 pairs, ~44 bits, within 1e-10 of   *
+                               * FP64) unless dda_opts.residual_fp64 = 1 selects native FP64 */
     double resid_normal_eq;   /* eq. err_tol form, or -1 if not requested                    */
     int iters;                /* Krylov iterations, all refinement steps (BiCGstab: 2 matvecs
                                  each, BiCGstab(2): 4, QMR: 1)                              */
@@ -190,7 +193,9 @@ dda_status dda_matvec_device(dda_ctx* ctx, dda_precision precision, int R, const
  * could fail or fragment that pool), and latency-critical loops that cannot
  * afford the implicit synchronization an allocation may cause.  There is no
  * counterpart in the paper; this is a deployment convenience.
- * Same arguments, layout and result as dda_matvec_device; the context must
+ * Same arguments, layout and result as dda_matvec_device, for the
+ * precisions DDA_FP64 and DDA_FP32 (DDA_DF64 and DDA_FP32_REFINED are
+ * rejected with DDA_ERR_ARG); the context must
  * already be prepared (dda_prepare allocates; this call does not).  The
  * padded FFT work buffers and the 1/alpha table live in one fixed scratch
  * array of 64 MiB (67108864 bytes) that the library declares in device
@@ -199,9 +204,10 @@ dda_status dda_matvec_device(dda_ctx* ctx, dda_precision precision, int R, const
  * DDA_ERR_SIZE (about 144 bytes per RHS for every site of the lattice
  * rounded up to half the padded FFT lengths, (Lx/2)(Ly/2)(Lz/2), for
  * complex64, twice that for complex128: the 64^3 lattice fits one complex64
- * RHS).  The first call on a device
- * looks up the array's device address: make that first call before any
- * stream capture.  All calls, from every context of the process, share the
+ * RHS).  The first call on a device looks up the array's device address,
+ * and so does the first call after that device's context was destroyed and
+ * re-created (cudaDeviceReset): make that first call before any stream
+ * capture.  All calls, from every context of the process, share the
  * one array and leave their data in it; no part of it needs to start at zero
  * (every buffer is written before it is read), but calls that overlap on the
  * GPU race on it, so do not run two of them concurrently on one device.

@@ -1,6 +1,8 @@
 // C ABI of the DDA hot path: context, target/material/wavelength set-up,
 // matvec, the BiCGstab solve with FP64 iterative refinement, Q reductions and
 // the adjoint gradient.  Declarations and conventions: include/dda.h.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -1005,17 +1007,46 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kMaxDevices] = {};
+unsigned long long g_noalloc_ctx[kMaxDevices] = {};
 
-// Device address of the scratch array on `device` (which must be current),
-// looked up on the first call for that device.
+// Unique id of the calling thread's current CUDA context, through the driver
+// entry points that the runtime hands out (the library does not link the
+// driver library itself).  0 if the driver does not offer them.
+unsigned long long current_context_id() {
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void* f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(f);
+    });
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&c) == CUDA_SUCCESS && c && get_id(c, &id) == CUDA_SUCCESS) return id;
+    return 0;
+}
+
+// Device address of the scratch array on `device` (which must be current).
+// It is looked up on the first call for that device, and again when the
+// device's context has been destroyed and re-created since (cudaDeviceReset
+// reloads the library's module, and the array may then sit elsewhere).
 cudaError_t noalloc_scratch(int device, unsigned char** out) {
     if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (g_noalloc_ptr[device] == nullptr) {
+    const unsigned long long ctx_id = current_context_id();
+    if (g_noalloc_ptr[device] == nullptr || (ctx_id != 0 && ctx_id != g_noalloc_ctx[device])) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         g_noalloc_ptr[device] = p;
+        g_noalloc_ctx[device] = ctx_id;
     }
     *out = static_cast<unsigned char*>(g_noalloc_ptr[device]);
     return cudaSuccess;
@@ -1392,7 +1423,10 @@ dda_status dda_matvec_device_noalloc(dda_ctx* ctx, dda_precision precision, int 
                                      const double* e, const void* x_dev, void* y_dev) {
     if (!ctx) return DDA_ERR_ARG;
     if (!x_dev || !y_dev) return ctx->fail(DDA_ERR_ARG, "NULL vector");
-    if (precision == DDA_FP32_REFINED) return ctx->fail(DDA_ERR_ARG, "matvec precision must be DDA_FP64 or DDA_FP32");
+    if (precision != DDA_FP64 && precision != DDA_FP32)
+        return ctx->fail(DDA_ERR_ARG,
+                         "dda_matvec_device_noalloc takes DDA_FP64 or DDA_FP32 (got %d); the double-float "
+                         "DDA_DF64 matvec is available through dda_matvec_device only", (int)precision);
     dda_status rs;
     if ((rs = check_ready(ctx, precision)) != DDA_OK) return rs;
     CU(cudaSetDevice(ctx->device));

@@ -7,6 +7,11 @@ oracle can evaluate at any size (needs a GB300).
 - two-material block, adjoint gradient vs central finite differences on 16
   seeded dipoles.
 - 256^3 sphere, 16 RHS: Q vs the Mie series within the guide's "few percent".
+- 64^3 sphere (both polarizations) and 16 RHS of the ellipsoid sweep: the
+  production mode (complex64 matvec, FP64 refinement, tol 1e-5) against a
+  plain FP64 solve to 1e-10, Q_ext, Q_abs and Q_sca per RHS to 1e-5
+  relative.  (The FP64 path itself matches the oracle to 1e-10 in
+  test_gpu_parity.py.)
 """
 import math
 
@@ -66,10 +71,10 @@ def test_block_gradient_matches_finite_differences(lib):
     rng = np.random.default_rng(SEED_COMPOSITION)
     picks = rng.choice(N, 16, replace=False)
     flat = np.flatnonzero(grid.ravel())          # site j -> flat grid index (x-fastest scan)
-    for j in picks[:8]:                             # 8 dipoles x (Re, Im) x 2 sides = 32 extra solves
+    for j in picks:                                 # 16 dipoles x (Re, Im) x 2 sides = 64 extra solves
         eps = complex(m[comp[j] - 1]) ** 2
         for part, g in ((1.0, gre[j]), (1j, gim[j])):
-            h = 2e-3 * abs(eps)
+            h = 1e-4 * abs(eps)
             q = []
             for sgn in (+1, -1):
                 g3 = grid.copy().ravel()
@@ -98,3 +103,34 @@ def test_sphere256_matches_mie(lib):
     # a sphere: every direction and polarization sees the same Q up to lattice anisotropy
     assert qe.max() - qe.min() < 0.01 * qm[0]
     ctx.close()
+
+
+Q_RTOL = 1e-5
+
+
+def _q(res):
+    return np.array([[r["qext"], r["qabs"], r["qsca"]] for r in res])
+
+
+def _refined_vs_fp64(lib, w, nrhs):
+    ctx = _ctx(lib, w.grid, w.m, w.x, lib.Precision.FP32_REFINED)
+    k, e = w.khat[:nrhs], w.ehat[:nrhs]
+    r32, _, st = ctx.solve(lib.Precision.FP32_REFINED, k, e, want_P=False, tol=1e-5, maxit=3000)
+    assert st == 0 and max(r["resid_rel"] for r in r32) <= 1e-5
+    r64, _, st = ctx.solve(lib.Precision.FP64, k, e, want_P=False, tol=1e-10, maxit=4000)
+    assert st == 0 and max(r["resid_rel"] for r in r64) <= 1e-10
+    ctx.close()
+    q32, q64 = _q(r32), _q(r64)
+    return np.abs(q32 - q64) / np.abs(q64)
+
+
+def test_sphere64_refined_q_matches_fp64(lib):
+    """The bench workload: both polarizations, every factor within 1e-5."""
+    err = _refined_vs_fp64(lib, workload("sphere64"), 2)
+    assert err.max() <= Q_RTOL, err
+
+
+def test_ellipsoid_sweep_refined_q_matches_fp64(lib):
+    """16 RHS of the 128-RHS sweep (seeded directions, both polarizations)."""
+    err = _refined_vs_fp64(lib, workload("ellipsoid96x64x32"), 16)
+    assert err.max() <= Q_RTOL, err

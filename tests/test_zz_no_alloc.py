@@ -50,6 +50,48 @@ def test_noalloc_matches_matvec_on_two_calls(env, prec, tol):
     ctx.close()
 
 
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (2, 1e-5)], ids=["fp64", "fp32"])
+def test_noalloc_matches_matvec_with_tensor_polarizabilities(env, prec, tol):
+    """Anisotropic materials: the scratch then holds the per-RHS 1/alpha
+    tensors (six entries per composition) instead of scalars."""
+    dda, torch = env
+    ctx = dda.Context(0)
+    ctx.set_target(sphere_grid(12))
+    ctx.set_anisotropic_materials([[1.4 + 0.02j, 1.5 + 0.05j, 1.3 + 0.01j]], [(0.4, 1.1, -0.6)])
+    ctx.prepare_size_parameter(1.2, dda.Precision.FP32_REFINED)
+    N = ctx.info()["ndipoles"]
+    k = uniform_directions(3, 7)
+    e = polarization_pair(k)[1].astype(complex)
+    dt = torch.complex128 if prec == 0 else torch.complex64
+    for call in range(2):
+        x = torch.from_numpy(random_complex((3, 3, N), 200 + call)).to(dt).cuda()
+        y_ref = torch.empty_like(x)
+        y_na = torch.full_like(x, float("nan"))
+        dda.dda_matvec_device(ctx.handle, prec, k, e, x, y_ref)
+        dda.dda_matvec_device_noalloc(ctx.handle, prec, k, e, x, y_na)
+        torch.cuda.synchronize()
+        assert torch.isfinite(y_na).all()
+        assert _rel(y_na, y_ref) < tol, (call, _rel(y_na, y_ref))
+    ctx.close()
+
+
+def test_noalloc_rejects_the_double_float_precision(env):
+    dda, torch = env
+    ctx = dda.Context(0)
+    ctx.set_target(sphere_grid(8))
+    ctx.set_materials([1.33 + 0.01j])
+    ctx.prepare_size_parameter(0.5, dda.Precision.FP32_REFINED)
+    N = ctx.info()["ndipoles"]
+    k = uniform_directions(1, 3)
+    e = polarization_pair(k)[0].astype(complex)
+    x = torch.zeros((1, 3, N), dtype=torch.complex128, device="cuda")
+    y = torch.zeros_like(x)
+    with pytest.raises(dda.DdaError) as ei:
+        dda.dda_matvec_device_noalloc(ctx.handle, 3, k, e, x, y)
+    assert ei.value.status_name == "DDA_ERR_ARG" and "DDA_DF64" in str(ei.value)
+    ctx.close()
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(env):
     dda, torch = env
     w = workload("sphere64")

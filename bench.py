@@ -13,9 +13,10 @@ FP32-refined vs plain FP64 on the same GPU.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
-Multi-GPU (torchrun, one rank per GPU): every rank solves its own copy of the
-workload's right-hand sides (orientation sweeps shard over RHS with no
-exchange), so scaling is weak and the value is the sum over ranks.
+Multi-GPU (torchrun, one rank per GPU): the orientation sweep holds the
+workload's right-hand sides once per rank and is sharded into contiguous RHS
+blocks (paper_1202_3424_gb300.sweep), one per rank, solved with no exchange;
+scaling is weak and the value is the sum over ranks.
 The reference arm (--impl reference) times the CPU oracle's pairwise
 O(N^2) FP64 matvec on the host cores on a bounded row sample of the same
 workload.
@@ -73,9 +74,13 @@ def parse():
     ap.add_argument("--solver", default="bicgstab", choices=["bicgstab", "bicgstab2", "qmr"],
                     help="solve mode: BiCGstab (default), BiCGstab(2) (the guide's PBCGS2) or QMR for complex "
                          "symmetric A (the guide's QMRCCG)")
-    ap.add_argument("--zpass", type=int, default=-1, choices=[-1, 0, 1, 2],
+    ap.add_argument("--xpass", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="complex64 x-pass schedule: -1 autotuned (default), 0 rows staged through shared memory, "
+                         "1 + V warp-local rows with radix plan V")
+    ap.add_argument("--zpass", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4],
                     help="complex64 z-pass schedule: -1 autotuned (default), 0 component groups, "
-                         "1 register-resident, 2 register-resident with octant columns "
+                         "1 register-resident, 2 register-resident with octant columns, 3 and 4 as 1 and 2 "
+                         "with the radix-16 plan "
                          "(forcing one makes profiler runs reproduce the tuned choice)")
     return ap.parse_args()
 
@@ -266,7 +271,14 @@ def run_gb300(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = workload(args.workload)
-    R = w.nrhs
+    # weak scaling: the orientation sweep holds the workload's RHS once per
+    # rank, and each rank solves its contiguous block (sweep.shard_rhs) with no
+    # exchange; the per-RHS results are gathered once after the timed region
+    from paper_1202_3424_gb300 import sweep
+    k_all, e_all = np.tile(w.khat, (world, 1)), np.tile(w.ehat, (world, 1))
+    mine = sweep.shard_rhs(len(k_all), rank, world)
+    k_loc, e_loc = k_all[mine.start:mine.stop], e_all[mine.start:mine.stop]
+    R = len(k_loc)
     ctx = dda.Context(local)
     stream = torch.cuda.current_stream(dev)
     dda.dda_set_stream(ctx.handle, stream.cuda_stream)
@@ -276,13 +288,14 @@ def run_gb300(args):
     ctx.prepare_size_parameter(w.x, dda.Precision.FP32_REFINED)
     prepare_ms = (time.perf_counter() - t0) * 1e3
     ctx.set_schedule(args.zpass)
+    ctx.set_xpass(args.xpass)
     info = ctx.info()
     N = info["ndipoles"]
     P_dev = torch.empty((R, 3, N), dtype=torch.complex128, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
     def step(prec, tol=1e-5):
-        res, st = dda.dda_solve_device(ctx.handle, prec, w.khat, w.ehat, P_dev, tol=tol, maxit=2000,
+        res, st = dda.dda_solve_device(ctx.handle, prec, k_loc, e_loc, P_dev, tol=tol, maxit=2000,
                                        solver=args.solver)
         if st != 0:
             raise RuntimeError(f"solve failed: {[r['status_name'] for r in res]}")
@@ -341,7 +354,7 @@ def run_gb300(args):
     elif args.fp64_steps > 0:
         # orientation sweep as a plain FP64 single-RHS loop: one solve per RHS
         P1 = torch.empty((1, 3, N), dtype=torch.complex128, device=dev)
-        dda.dda_solve_device(ctx.handle, dda.Precision.FP64, w.khat[:1], w.ehat[:1], P1, tol=1e-5, maxit=2000)
+        dda.dda_solve_device(ctx.handle, dda.Precision.FP64, k_loc[:1], e_loc[:1], P1, tol=1e-5, maxit=2000)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -350,7 +363,7 @@ def run_gb300(args):
         mv64 = 0
         it64 = []
         for r_ in range(R):
-            rr, st = dda.dda_solve_device(ctx.handle, dda.Precision.FP64, w.khat[r_:r_ + 1], w.ehat[r_:r_ + 1], P1,
+            rr, st = dda.dda_solve_device(ctx.handle, dda.Precision.FP64, k_loc[r_:r_ + 1], e_loc[r_:r_ + 1], P1,
                                           tol=1e-5, maxit=2000)
             mv64 += rr[0]["matvecs"]
             it64.append(rr[0]["iters"])
@@ -363,8 +376,8 @@ def run_gb300(args):
     # end to end through the host-buffer C-ABI call (P copied back every step)
     e2e = None
     if not args.no_e2e:
-        k = np.ascontiguousarray(w.khat)
-        e = np.ascontiguousarray(w.ehat)
+        k = np.ascontiguousarray(k_loc)
+        e = np.ascontiguousarray(e_loc)
         ctx.solve(dda.Precision.FP32_REFINED, k, e, tol=1e-5, maxit=2000, solver=args.solver)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -378,6 +391,9 @@ def run_gb300(args):
                "h2d_bytes_per_step": int(k.nbytes + e.nbytes), "d2h_bytes_per_step": int(P_host.nbytes + 72 * R),
                "time_to_solution_ms": t_e2e * 1e3 / args.steps}
 
+    # the matvec schedules the autotuner chose for this RHS count (cached by now)
+    schedule = {"solve": ctx.get_solve_schedule(R),
+                "plain_matvec": {"zpass": ctx.get_schedule(R), "xpass_fwd_inv": list(ctx.get_xpass(R))}}
     roof = roofline(kstats, info, R, w.name)
     # complex64 RHS-matvecs per traced step: 2 per BiCGstab (4 per BiCGstab(2)) iteration of every RHS
     per_iter = {"bicgstab": 2, "bicgstab2": 4, "qmr": 1}[args.solver]
@@ -386,21 +402,28 @@ def run_gb300(args):
         if kstats else None
     launches = int(sum(s["launches"] for s in kstats.values()) / args.steps) * args.steps if kstats else 0
 
+    # every rank's per-RHS results, in sweep order (the sweep's one collective)
+    def solve_block(kb, eb):
+        rr, _ = dda.dda_solve_device(ctx.handle, dda.Precision.FP32_REFINED, kb, eb, P_dev[:len(kb)], tol=1e-5,
+                                     maxit=2000, solver=args.solver)
+        return [[r["qext"], r["qabs"], r["qsca"], r["resid_rel"]] for r in rr]
+    swept = sweep.solve_sweep(solve_block, k_all, e_all, dist)
+
     # error of the production mode per result, against an FP64 solve to 1e-10
     accuracy = None
     if not args.no_accuracy:
-        accuracy = accuracy_vs_fp64(dda, ctx, w, P_dev, res, fp64["q"] if fp64 and "q" in fp64 else None)
+        accuracy = accuracy_vs_fp64(dda, ctx, k_loc, e_loc, P_dev, res, fp64["q"] if fp64 and "q" in fp64 else None)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, info, budget_s=12.0)
 
-    sweep = None
+    ell_sweep = None
     if args.mode == "solve" and args.workload == "sphere64" and not args.no_sweep and not args.aniso \
-            and args.solver == "bicgstab":
+            and args.solver == "bicgstab" and world == 1:
         ctx.close()
         ctx = None
-        sweep = ellipsoid_sweep(dda, dev, stream, flush, dist)
+        ell_sweep = ellipsoid_sweep(dda, dev, stream, flush, dist)
 
     if rank == 0:
         line = {
@@ -410,19 +433,20 @@ def run_gb300(args):
             "config": {"workload": f"{w.name}: lattice {info['nx']}x{info['ny']}x{info['nz']}, N={N} dipoles, "
                                    f"{materials_note(w, args.aniso)}, x={w.x}, {R} RHS, tol 1e-5, "
                                    f"{ {'bicgstab': 'BiCGstab', 'bicgstab2': 'BiCGstab(2)', 'qmr': 'QMR'}[args.solver]}",
-                       "global_batch": R * world, "padded_grid": [info["Lx"], info["Ly"], info["Lz"]],
-                       "parallelism": f"rhs-sharded x{world}", "l2": "256 MB buffer written between steps"},
+                       "global_batch": len(k_all), "padded_grid": [info["Lx"], info["Ly"], info["Lz"]],
+                       "parallelism": f"rhs-sharded x{world} (sweep.shard_rhs blocks, no exchange; results "
+                                      f"gathered after timing)", "l2": "256 MB buffer written between steps"},
             "time_to_solution_ms": ms_per_step,
             "iters": [r["iters"] for r in res], "outer_iters": [r["outer_iters"] for r in res],
             "matvecs_per_step": mv / args.steps, "resid_rel": [r["resid_rel"] for r in res],
-            "q": [[r["qext"], r["qabs"], r["qsca"]] for r in res],
+            "q": [r[:3] for r in swept], "sweep_rhs": len(swept),
             "fp64_plain": fp64, "speedup_vs_fp64": fp64["time_to_solution_ms"] / ms_per_step if fp64 else None,
             "prepare_ms": prepare_ms,
             "traced_ms_per_step": sum(per_tr) / len(per_tr),
             "kernels": {k_: {"launches": v["launches"], "ms": v["ms"], "share": v["share"]} for k_, v in kstats.items()},
-            "roofline": roof, "matvec_roofline": mv_roof,
+            "roofline": roof, "matvec_roofline": mv_roof, "schedule": schedule,
             "q_relerr_vs_fp64": accuracy,
-            "ellipsoid_sweep_128rhs": sweep,
+            "ellipsoid_sweep_128rhs": ell_sweep,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
@@ -437,7 +461,7 @@ def _q_relerr(q, qref):
     return [[abs(a - b) / abs(b) for a, b in zip(qi, qr)] for qi, qr in zip(q, qref)]
 
 
-def accuracy_vs_fp64(dda, ctx, w, P_dev, res, q_fp64_tol5=None, tol_ref=1e-10):
+def accuracy_vs_fp64(dda, ctx, khat, ehat, P_dev, res, q_fp64_tol5=None, tol_ref=1e-10):
     """Error of the FP32-refined results (tol 1e-5) per RHS and per
     efficiency factor, against a plain FP64 solve of the same RHS to
     tol_ref on the same GPU (the FP64 path matches the CPU oracle to 1e-10).
@@ -445,7 +469,7 @@ def accuracy_vs_fp64(dda, ctx, w, P_dev, res, q_fp64_tol5=None, tol_ref=1e-10):
     residual, so their distance from the tight solution is of one size."""
     import torch
     Pref = torch.empty_like(P_dev)
-    rref, st = dda.dda_solve_device(ctx.handle, dda.Precision.FP64, w.khat, w.ehat, Pref, tol=tol_ref, maxit=4000)
+    rref, st = dda.dda_solve_device(ctx.handle, dda.Precision.FP64, khat, ehat, Pref, tol=tol_ref, maxit=4000)
     if st != 0:
         return {"error": f"FP64 reference solve status {st}"}
     qref = [[r["qext"], r["qabs"], r["qsca"]] for r in rref]
@@ -720,6 +744,7 @@ def run_matvec_only(args):
     set_materials(ctx, w, args.aniso)
     ctx.prepare_size_parameter(w.x, dda.Precision.FP32_REFINED)
     ctx.set_schedule(args.zpass)
+    ctx.set_xpass(args.xpass)
     N = ctx.info()["ndipoles"]
     k = np.resize(w.khat, (R, 3))
     e = np.resize(w.ehat, (R, 3))
@@ -752,7 +777,9 @@ def run_matvec_only(args):
         kern[name] = {"avg_ms": avg, "gbs": (b / (avg / 1e3) / 1e9) if b else None}
     mv_roof = matvec_roofline(kst, info, "c64" if args.precision == "fp32" else "c128")
     zpass = ctx.get_schedule(R) if args.precision == "fp32" else 0
+    xpass = list(ctx.get_xpass(R)) if args.precision == "fp32" else 0
     line = {"mode": "matvec", "workload": w.name, "rhs": R, "precision": args.precision, "zpass": zpass,
+            "xpass": xpass,
             "ms_per_matvec": ms, "rhs_matvecs_per_s": R / (ms / 1e3), "kernels": kern, "matvec_roofline": mv_roof}
     if args.cufft:
         line["cufft_comparison"] = cufft_matvec_timing(w, info, R, dt, x, args.steps)

@@ -159,6 +159,17 @@ dda_status dda_set_materials(dda_ctx* ctx, int ncomp, const double* m_complex, d
  * Errors as for dda_set_materials; DDA_ERR_NONFINITE for a non-finite angle. */
 dda_status dda_set_anisotropic_materials(dda_ctx* ctx, int ncomp, const double* m_principal,
                                          const double* df_angles, double m_ambient);
+/* Per-site materials (the guide's ICOMP per dipole, without the 255-code
+ * limit): one complex refractive index for every occupied site of the
+ * current target, m_site[2j], m_site[2j+1] for site j in the order of
+ * dda_set_target (x fastest), and the ambient index.  Each site's 1/alpha is
+ * the LATTDR value of its own (m_j/m_ambient)^2; the grid's composition
+ * codes then only mark occupancy.  Solves, matvecs, Q, the gradient and the
+ * field calls all apply; the fused slice passes are skipped.  Needs
+ * dda_set_target (DDA_ERR_ARG otherwise); a later dda_set_target,
+ * dda_set_materials or dda_set_anisotropic_materials ends the mode.  Errors
+ * as for dda_set_materials, per site.                                          */
+dda_status dda_set_site_materials(dda_ctx* ctx, const double* m_site, double m_ambient);
 /* Wavelength and size (guide: WAVINI / AEFFINI, same physical units): sets
  * d = aeff/(3N/4pi)^(1/3), k = 2 pi m_ambient / lambda_vac, and builds the
  * transformed Green tensor for `precision` (FP64 tensor always; FP32 copy for
@@ -305,29 +316,52 @@ dda_status dda_grad_qabs(dda_ctx* ctx, dda_precision precision, const double* kh
  *      2  as 1, with each block owning columns of the Green octant and
  *         transforming the four columns (+-kx, +-ky) that share them (a
  *         quarter of the Green staging; faster for few RHS);
+ *      3, 4  as 1 and 2 with a radix-16 plan of the z transform (Lz = 128:
+ *         8 x 16, Lz = 256: 16 x 16): one exchange per transform instead of
+ *         two, 16 points per thread, no register prefetch of the next RHS;
  *  - the fused x+y slice passes: where the half-y spectrum of one z-slice,
  *    Lx x (Ly/2) points, fits in shared memory (Lx, Ly in 64..192 for
  *    complex64, 64 or 96 for complex128 and double-float), one block can
  *    transform a whole slice along x and y, so the x-transformed rows never
- *    go through HBM (3 kernels per matvec instead of 5).
+ *    go through HBM (3 kernels per matvec instead of 5);
+ *  - the x passes (complex64 only): 0 stages each block's rows through
+ *    shared memory around the transform; 1 + V holds each row in one warp
+ *    (up to 32 lanes, read and scattered straight from and to global memory,
+ *    warp barriers between the radix stages) with radix plan V: V = 0 is the
+ *    staged plan, V = 1 (Lx = 128, 192, 256) a plan with fewer exchanges
+ *    (radix 16, or more points per lane).
  * All choices compute the same product; results agree to rounding.  In
- * automatic mode the context times every available combination inside whole
+ * automatic mode the context times the available choices inside whole
  * matvecs on its own workspace the first time a matvec of a given type and
- * RHS count runs outside a stream capture, and keeps the fastest (inside a
- * capture an untimed choice is used until then).
- * dda_set_schedule: zpass -1 automatic (the default), 0, 1 or 2 forces that
- *   z schedule wherever it exists (1 and 2 fall back to 0 elsewhere).
+ * RHS count runs outside a stream capture (the z schedule with the slice
+ * passes, then the x-forward, then the x-inverse schedule, each keeping the
+ * fastest so far), and keeps the result (inside a capture an untimed choice
+ * is used until then).
+ * dda_set_schedule: zpass -1 automatic (the default), 0..4 forces that z
+ *   schedule wherever it exists (3 and 4 fall back to 1 and 2 where the
+ *   length has one plan, 1..4 to 0 where the register schedules do not exist).
  * dda_set_slice_passes: on -1 automatic, 0 always the separate passes (the
  *   default: measured on GB300 the slice passes are faster only for small
  *   grids outside a solve), 1 the slice passes wherever they are built.
- * Both clear the timings; any other value: DDA_ERR_ARG.
+ * dda_set_xpass: xfwd, xinv -1 automatic (the default), 0, 1 or 2 forces
+ *   that x-forward / x-inverse schedule where it exists (2 falls back to 1
+ *   where Lx has one plan).
+ * All three clear the timings; any other value: DDA_ERR_ARG.
  * dda_get_schedule: the z schedule (and, if slices is not NULL, whether the
  *   slice passes run) of complex64 matvecs of R RHS on the current target,
  *   timing the candidates now if needed (this sizes the workspace for R).
- *   Needs dda_prepare with DDA_FP32_REFINED or DDA_FP32.                      */
+ *   Needs dda_prepare with DDA_FP32_REFINED or DDA_FP32.
+ * dda_get_xpass: likewise, the x-forward and x-inverse schedules of those
+ *   matvecs.
+ * dda_get_solve_schedule: the z, x-forward and x-inverse schedules of the
+ *   complex64 matvecs inside a solve of R RHS (those carry the fused BiCGstab
+ *   updates and are tuned apart from plain matvecs, with the same candidates). */
 dda_status dda_set_schedule(dda_ctx* ctx, int zpass);
 dda_status dda_set_slice_passes(dda_ctx* ctx, int on);
+dda_status dda_set_xpass(dda_ctx* ctx, int xfwd, int xinv);
 dda_status dda_get_schedule(dda_ctx* ctx, int R, int* zpass, int* slices);
+dda_status dda_get_xpass(dda_ctx* ctx, int R, int* xfwd, int* xinv);
+dda_status dda_get_solve_schedule(dda_ctx* ctx, int R, int* zpass, int* xfwd, int* xinv);
 
 /* Launch tracing (the guide's TIMEIT timing switch, per kernel kind rather than
  * per run): when on, every hot-path kernel launch is bracketed by CUDA events

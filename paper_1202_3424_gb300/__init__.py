@@ -26,7 +26,8 @@ __all__ = [
     "dda_prepare", "dda_get_info", "dda_solve", "dda_solve_device", "dda_matvec", "dda_matvec_device",
     "dda_incident_field", "dda_grad_qabs", "dda_matvec_device_noalloc", "dda_set_schedule", "dda_get_schedule",
     "dda_nearfield", "dda_nearfield_dims", "dda_set_slice_passes", "dda_scattering_directions", "dda_farfield",
-    "dda_angular_averages", "dda_mueller", "dda_set_anisotropic_materials",
+    "dda_angular_averages", "dda_mueller", "dda_set_anisotropic_materials", "dda_set_xpass", "dda_get_xpass",
+    "dda_set_site_materials", "dda_get_solve_schedule",
 ]
 
 STATUS = {0: "DDA_OK", 1: "DDA_ERR_ARG", 2: "DDA_ERR_CUDA", 3: "DDA_ERR_OOM", 4: "DDA_ERR_SIZE",
@@ -122,6 +123,11 @@ def load_library(build_if_missing: bool = True):
         "dda_nearfield": ([vp, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D, _D], ctypes.c_int),
         "dda_get_schedule": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
                              ctypes.c_int),
+        "dda_set_xpass": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "dda_set_site_materials": ([vp, _D, ctypes.c_double], ctypes.c_int),
+        "dda_get_solve_schedule": ([vp, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 3, ctypes.c_int),
+        "dda_get_xpass": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+                          ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -218,6 +224,16 @@ def dda_set_anisotropic_materials(ctx, m_principal, df_angles, m_ambient: float 
         raise ValueError("one (theta_DF, phi_DF, beta_DF) per composition")
     _check(ctx, load_library().dda_set_anisotropic_materials(ctx, mm.shape[0], _dptr(mm.view(np.float64)),
                                                               _dptr(aa), float(m_ambient)))
+
+
+def dda_set_site_materials(ctx, m_site, m_ambient: float = 1.0):
+    """One complex refractive index per occupied site (site order of
+    dda_set_target); no limit on the number of distinct values."""
+    mm = np.ascontiguousarray(np.asarray(m_site, dtype=np.complex128).ravel())
+    N = dda_get_info(ctx)["ndipoles"]
+    if mm.size != N:
+        raise ValueError(f"{mm.size} indices for {N} occupied sites")
+    _check(ctx, load_library().dda_set_site_materials(ctx, _dptr(mm.view(np.float64)), float(m_ambient)))
 
 
 def dda_prepare(ctx, lambda_vac: float, aeff: float, precision: int = Precision.FP64):
@@ -418,6 +434,31 @@ def dda_get_schedule(ctx, R: int, with_slices: bool = False):
     return (out.value, sl.value) if with_slices else out.value
 
 
+def dda_set_xpass(ctx, xpass):
+    """Force the complex64 x-pass schedules (0 staged rows, 1 + V warp-local
+    rows with radix plan V) or restore autotuning (-1): one value for both
+    x passes, or an (x-forward, x-inverse) pair."""
+    f, i = (xpass, xpass) if np.ndim(xpass) == 0 else xpass
+    _check(ctx, load_library().dda_set_xpass(ctx, int(f), int(i)))
+
+
+def dda_get_xpass(ctx, R: int):
+    """(x-forward, x-inverse) schedules complex64 matvecs of R RHS use
+    (timed now if needed)."""
+    f, i = ctypes.c_int(-1), ctypes.c_int(-1)
+    _check(ctx, load_library().dda_get_xpass(ctx, int(R), ctypes.byref(f), ctypes.byref(i)))
+    return f.value, i.value
+
+
+def dda_get_solve_schedule(ctx, R: int):
+    """{"zpass", "xfwd", "xinv"}: the schedules of the complex64 matvecs in a
+    solve of R RHS (timed now if needed)."""
+    z, f, i = ctypes.c_int(-1), ctypes.c_int(-1), ctypes.c_int(-1)
+    _check(ctx, load_library().dda_get_solve_schedule(ctx, int(R), ctypes.byref(z), ctypes.byref(f),
+                                                      ctypes.byref(i)))
+    return {"zpass": z.value, "xfwd": f.value, "xinv": i.value}
+
+
 class Context:
     """Owns one dda_ctx (one GPU)."""
 
@@ -449,6 +490,9 @@ class Context:
 
     def set_anisotropic_materials(self, m_principal, df_angles, m_ambient=1.0):
         dda_set_anisotropic_materials(self.handle, m_principal, df_angles, m_ambient)
+
+    def set_site_materials(self, m_site, m_ambient=1.0):
+        dda_set_site_materials(self.handle, m_site, m_ambient)
 
     def prepare(self, lambda_vac, aeff, precision=Precision.FP64):
         dda_prepare(self.handle, lambda_vac, aeff, precision)
@@ -486,6 +530,15 @@ class Context:
 
     def set_schedule(self, zpass):
         dda_set_schedule(self.handle, zpass)
+
+    def set_xpass(self, xpass):
+        dda_set_xpass(self.handle, xpass)
+
+    def get_xpass(self, R):
+        return dda_get_xpass(self.handle, R)
+
+    def get_solve_schedule(self, R):
+        return dda_get_solve_schedule(self.handle, R)
 
     def set_slice_passes(self, on):
         dda_set_slice_passes(self.handle, on)

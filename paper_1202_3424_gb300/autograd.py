@@ -1,13 +1,15 @@
 """torch.autograd.Function for the absorption efficiency Q_abs.
 
 The forward pass is a DDA solve on the GPU for one incident plane wave,
-with the dielectric function given per dipole; the backward pass returns
-dQ_abs/d(eps_j) for every dipole from one adjoint solve through the same
-FFT matvec (the interaction matrix is complex symmetric, so A^T nu = W P^*
-is solved with A itself).  All of it runs in the CUDA library (dda_grad_qabs).
+with the dielectric function given per dipole (every dipole its own value:
+the C ABI's per-site materials, no limit on distinct values).  The backward
+pass returns dQ_abs/d(eps_j) for every dipole from one adjoint solve through
+the same FFT matvec (the interaction matrix is complex symmetric, so
+A^T nu = W P^* is solved with A itself); it runs only when a gradient is
+asked for, and its forward solve starts from the saved polarization, so it
+takes no iterations.  All of it runs in the CUDA library (dda_solve,
+dda_grad_qabs).
 
-Dipoles with equal eps share one composition of the C ABI (at most 255
-distinct values per call); each dipole's gradient is still its own.
 Gradient convention (PyTorch, real loss of a complex input):
     eps.grad = dQ/dRe(eps) + i dQ/dIm(eps).
 """
@@ -23,7 +25,8 @@ class DipoleTarget:
     """Geometry, size parameter and incident wave of the Q_abs objective.
 
     occupancy: bool/uint8 grid [nz, ny, nx]; x: size parameter 2 pi a_eff/lambda
-    (a_eff from the number of dipoles); khat (3,), ehat (3,) complex.
+    (a_eff from the number of dipoles); khat (3,), ehat (3,) complex.  The
+    dipoles are the occupied sites in x-fastest scan order.
     """
 
     def __init__(self, occupancy, x: float, khat, ehat, precision: int = Precision.FP64, device: int = 0,
@@ -36,24 +39,41 @@ class DipoleTarget:
         self.tol = tol
         self.maxit = maxit
         self.ctx = Context(device)
+        self.ctx.set_target(self.occ.astype(np.uint8))
         self.N = int(self.occ.sum())
+        self._eps = None
 
-    def qabs_and_grad(self, eps: np.ndarray):
+    def _set_eps(self, eps: np.ndarray):
         eps = np.asarray(eps, dtype=np.complex128).ravel()
         if eps.size != self.N:
             raise ValueError(f"eps has {eps.size} entries, the target has {self.N} dipoles")
-        vals, inv = np.unique(eps, return_inverse=True)
-        if vals.size > 255:
-            raise ValueError("at most 255 distinct dielectric functions per call")
-        grid = np.zeros(self.occ.shape, dtype=np.uint8)
-        grid[self.occ] = (inv + 1).astype(np.uint8)        # x-fastest scan order == site order
-        self.ctx.set_target(grid)
-        self.ctx.set_materials(np.sqrt(vals))
+        if self._eps is not None and np.array_equal(eps, self._eps):
+            return
+        # the library squares the index again, so either square root will do
+        self.ctx.set_site_materials(np.sqrt(eps))
         prep = Precision.FP32_REFINED if self.precision != Precision.FP64 else Precision.FP64
         self.ctx.prepare_size_parameter(self.x, prep)
-        g_re, g_im, P, (rf, ra) = self.ctx.grad_qabs(self.precision, self.khat, self.ehat, tol=self.tol,
-                                                     maxit=self.maxit)
-        return rf["qabs"], g_re + 1j * g_im
+        self._eps = eps.copy()
+
+    def qabs(self, eps: np.ndarray):
+        """(Q_abs, P [3, N]) from one forward solve."""
+        self._set_eps(eps)
+        res, P, st = self.ctx.solve(self.precision, self.khat, self.ehat, tol=self.tol, maxit=self.maxit)
+        if st != 0:
+            raise RuntimeError(f"forward solve failed: {res[0]['status_name']}")
+        return res[0]["qabs"], P[0]
+
+    def grad(self, eps: np.ndarray, P=None):
+        """dQ_abs/dRe(eps) + i dQ_abs/dIm(eps) per dipole; P (from qabs) warm-starts the forward solve."""
+        self._set_eps(eps)
+        opts = {} if P is None else {"x0": np.asarray(P, dtype=np.complex128).reshape(1, 3, self.N)}
+        g_re, g_im, _, (rf, ra) = self.ctx.grad_qabs(self.precision, self.khat, self.ehat, tol=self.tol,
+                                                     maxit=self.maxit, **opts)
+        return g_re + 1j * g_im
+
+    def qabs_and_grad(self, eps: np.ndarray):
+        q, P = self.qabs(eps)
+        return q, self.grad(eps, P)
 
     def close(self):
         self.ctx.close()
@@ -64,11 +84,14 @@ class QabsFn(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, eps: torch.Tensor, target: DipoleTarget):
-        q, g = target.qabs_and_grad(eps.detach().cpu().numpy())
-        ctx.save_for_backward(torch.from_numpy(g).to(eps.device))
+        e = eps.detach().cpu().numpy()
+        q, P = target.qabs(e)
+        ctx.target = target
+        if ctx.needs_input_grad[0]:
+            ctx.eps, ctx.P = e, P
         return torch.tensor(q, dtype=torch.float64, device=eps.device)
 
     @staticmethod
     def backward(ctx, grad_out):
-        (g,) = ctx.saved_tensors
-        return grad_out * g, None
+        g = ctx.target.grad(ctx.eps, ctx.P)
+        return grad_out * torch.from_numpy(g).to(grad_out.device), None

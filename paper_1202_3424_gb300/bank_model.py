@@ -186,8 +186,143 @@ def table(plans=None):
     return out
 
 
+# ---- warp-local pencils (x passes) ------------------------------------------
+# The warp-local x passes (csrc/xwarp.cuh) hold each pencil in NT <= 32
+# consecutive lanes and give it its own exchange plane of L + pad elements;
+# the exchange after stage S of direction DIR stores and loads position pos
+# at pos ^ ((pos >> K) & 15), with K chosen here per exchange.
+XWARP_HEADER = os.path.join(HERE, "csrc", "xwarp.cuh")
+
+
+def read_warp_plans(path: str = XWARP_HEADER):
+    """{(L, V): (NT, radices)} from the XwPlan table of xwarp.cuh."""
+    text = open(path).read()
+    out = {}
+    for L, V, L2, NT, rad in re.findall(r"struct XwPlan<(\d+), (\d+)> : PlanDef<(\d+), (\d+), ([\d, ]+)>", text):
+        out[(int(L), int(V))] = (int(NT), [int(r) for r in rad.split(",")])
+    return out
+
+
+def read_warp_table(path: str = XWARP_HEADER):
+    """({(L, NT, DIR, S): K}, {NT: pad}) as tabulated in xwarp.cuh."""
+    text = open(path).read()
+    pat = r"if \(L == (\d+) && NT == (\d+) && DIR == (-?\d+) && S == (\d+)\) return (\d+);"
+    keys = {(int(a), int(b), int(c), int(d)): int(e) for a, b, c, d, e in re.findall(pat, text)}
+    pads = {int(a): int(b) for a, b in re.findall(r"if \(NT == (\d+)\) return (\d+);", text)}
+    return keys, pads
+
+
+def warp_exchange_instrs(L, NT, rad, direction, S):
+    """(store instructions, load instructions) of the exchange after stage S;
+    each instruction lists the position of every pencil thread u."""
+    stores = [p for i, p in enumerate(_stage_instrs(L, NT, rad, direction, S, stores=True))]
+    loads = [p for p in _stage_instrs(L, NT, rad, direction, S, stores=False)]
+    return stores, loads
+
+
+def _stage_instrs(L, NT, rad, direction, S, stores):
+    E = L // NT
+    if stores:
+        R, P = stage_radix(rad, direction, S), stage_p(rad, direction, S)
+        for q in range(E // R):
+            for m in range(R):
+                pos = []
+                for u in range(NT):
+                    if NT % P == 0:
+                        pos.append((u // P) * (P * R) + (u % P) + q * NT * R + m * P)
+                    elif P % NT == 0:
+                        pos.append(u + (q - q % (P // NT)) * NT * R + (q % (P // NT)) * NT + m * P)
+                    else:
+                        i = u + q * NT
+                        k = i % P
+                        pos.append((i - k) * R + k + m * P)
+                yield pos
+    else:
+        R2 = stage_radix(rad, direction, S + 1)
+        for q in range(E // R2):
+            for j in range(R2):
+                yield [u + q * NT + j * (L // R2) for u in range(NT)]
+
+
+def warp_swizzle(pos, key):
+    return pos ^ ((pos >> key) & 15) if key else pos
+
+
+def warp_exchange_cost(L, NT, rad, direction, S, key, plane):
+    """(wavefronts, ideal) of one exchange for one warp (32 // NT pencils)."""
+    act = ideal = 0
+    st, ld = warp_exchange_instrs(L, NT, rad, direction, S)
+    for instr in st + ld:
+        addrs = [((lane // NT) * plane + warp_swizzle(instr[lane % NT], key)) * 8 for lane in range(32)]
+        act += wavefronts(addrs)
+        ideal += 2
+    return act, ideal
+
+
+WARP_PADS = (0, 8, 16, 24)
+
+
+def warp_table(plans=None):
+    """({(L, NT, DIR, S): K}, {NT: pad}, {(L, NT): (cost, plain cost)}): per
+    exchange the key K (0: none) with the fewest wavefronts, ties to the
+    smaller K; per pencil width NT the plane padding that is cheapest summed
+    over every plan of that width."""
+    plans = plans or read_warp_plans()
+    by_nt = {}
+    for (L, V), (NT, rad) in plans.items():
+        by_nt.setdefault(NT, []).append((L, rad))
+    keys, pads, costs = {}, {}, {}
+    for NT, lst in sorted(by_nt.items()):
+        best = None
+        for pad in WARP_PADS:
+            tot, ks, cs = 0, {}, {}
+            for L, rad in lst:
+                a_sum = i_sum = p_sum = 0
+                for direction in (-1, +1):
+                    for S in range(len(rad) - 1):
+                        cands = []
+                        for key in range(0, 7):
+                            a, i = warp_exchange_cost(L, NT, rad, direction, S, key, L + pad)
+                            cands.append((a, key, i))
+                        a, key, i = min(cands)
+                        ks[(L, NT, direction, S)] = key
+                        a_sum += a
+                        i_sum += i
+                        p_sum += cands[0][0]
+                cs[(L, NT)] = (a_sum / i_sum if i_sum else 1.0, p_sum / i_sum if i_sum else 1.0)
+                tot += a_sum
+            if best is None or tot < best[0]:
+                best = (tot, pad, ks, cs)
+        _, pad, ks, cs = best
+        pads[NT] = pad
+        keys.update(ks)
+        costs.update(cs)
+    return keys, pads, costs
+
+
 def main(argv):
     t = table()
+    if "--check-warp" in argv:
+        keys, pads, costs = warp_table()
+        want = {k: v for k, v in keys.items() if v}
+        have, have_pads = read_warp_table()
+        if want != have or pads != have_pads:
+            print("warp_swizzle_key / warp_plane_pad in xwarp.cuh differ from the model:")
+            print("  model:", sorted(want.items()), pads)
+            print("  header:", sorted(have.items()), have_pads)
+            return 1
+        print("xwarp.cuh tables match the model (%d swizzled exchanges)" % len(want))
+        return 0
+    if "--warp" in argv:
+        keys, pads, costs = warp_table()
+        for (L, NT), (c, p) in sorted(costs.items()):
+            print(f"L={L:4d} NT={NT:3d} pad {pads[NT]:2d}  cost {c:.3f} of ideal (unswizzled {p:.3f})")
+        for k, v in sorted(keys.items()):
+            if v:
+                print(f"    if (L == {k[0]} && NT == {k[1]} && DIR == {k[2]} && S == {k[3]}) return {v};")
+        for nt, pad in sorted(pads.items()):
+            print(f"    if (NT == {nt}) return {pad};")
+        return 0
     if "--check" in argv:
         want = {k: v[0] for k, v in t.items() if v[0] != 0}
         have = read_table()

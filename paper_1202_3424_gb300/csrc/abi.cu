@@ -79,6 +79,9 @@ struct dda_ctx {
     bool aniso = false;
     std::vector<std::array<cd, 3>> m3;
     std::vector<std::array<double, 3>> df_angles;
+    // per-site materials (dda_set_site_materials): m holds one index per
+    // occupied site, and site j takes table entry j + 1 (tg.comp_of is null)
+    bool site_mode = false;
 
     // prepared wavelength
     bool prepared = false, has32 = false;
@@ -92,8 +95,9 @@ struct dda_ctx {
     GraphEntry graph;
     // z-pass schedule per (element bytes, RHS count), timed on first use;
     // force_z >= 0 overrides (dda_set_schedule)
-    std::map<std::pair<int, int>, std::pair<int, int>> zsched;  // -> (z variant, slice passes)
+    std::map<std::pair<int, int>, std::array<int, 4>> zsched;  // -> (z, slice passes, x-fwd, x-inv)
     int force_z = -1;
+    int force_xf = -1, force_xi = -1;  // x-pass schedules: -1 timed, else forced (dda_set_xpass)
     // -1 timed, 0 separate passes (default), 1 slice passes where built.
     // Measured on GB300 the slice passes win only on small grids outside a
     // solve (64^3 sphere, 2 RHS: 0.163 vs 0.175 ms per matvec) and lose inside
@@ -174,6 +178,8 @@ dda_status ensure(dda_ctx* ctx, DevMem& m, size_t bytes, bool zero = false) {
 }
 
 template <typename P> P* slot(dda_ctx* ctx, int s) { return reinterpret_cast<P*>(ctx->pool[s].p); }
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 void free_mem(DevMem& m) {
     if (m.p) cudaFree(m.p);
@@ -378,93 +384,177 @@ template <typename T> dda_status ensure_pad(dda_ctx* ctx, int R) {
 }
 
 // Schedule of the matvec passes for R right-hand sides: the z-pass variant
-// (zconv_schedules) and whether the fused x+y slice passes run
-// (slice_passes).  Where more than one combination exists, each is timed
-// once inside a whole plain matvec of R RHS (the passes decide what their
-// neighbours find in L2) on the context's workspace plus a transient pair of
-// vectors, and the fastest is kept.  The workspace must hold R RHS
-// (ensure_pad<T>).  Inside a stream capture, or with may_time false, an
-// untimed choice is returned: the cached one, else the register-resident z
-// schedule (octant mapping below 8 RHS) and the slice passes where built.
-template <typename T> dda_status pick_schedule(dda_ctx* ctx, int R, bool may_time, int* zvar, int* slices) {
+// (zconv_schedules), whether the fused x+y slice passes run (slice_passes),
+// and the x-forward and x-inverse schedules (xpass_schedules).  Where more
+// than one choice exists they are timed inside whole plain matvecs of R RHS
+// (the passes decide what their neighbours find in L2) on the context's
+// workspace plus a transient pair of vectors, one coordinate at a time (z
+// and slices, then x-forward, then x-inverse), and the fastest is kept.  The
+// workspace must hold R RHS (ensure_pad<T>).  Inside a stream capture, or
+// with may_time false, an untimed choice is returned: the cached one, else
+// the register-resident z schedule (octant mapping below 8 RHS), the slice
+// passes where built and forced, and the warp-local x passes with plan 0.
+int partial_stride(const dda_ctx* ctx);
+
+template <typename T>
+dda_status pick_schedule(dda_ctx* ctx, int R, bool may_time, PadWork<T>* out, bool fused = false) {
     const int nv = zconv_schedules<T>(ctx->g);
-    const bool sl = slice_passes<T>(ctx->g) && !ctx->aniso;
+    const int nx = xpass_schedules<T>(ctx->g);
+    const bool sl = slice_passes<T>(ctx->g) && !ctx->aniso && !ctx->site_mode;
     std::vector<int> zs, ss;
     if (nv <= 1) zs = {0};
-    else if (ctx->force_z >= 0) zs = {std::min(ctx->force_z, nv - 1)};
+    else if (ctx->force_z >= 0) {
+        // a plan-variant schedule (3, 4) falls back to its plan-0 schedule
+        // (1, 2) where the length has one plan, and anything to 0 where the
+        // register schedules do not exist
+        int fz = ctx->force_z;
+        if (fz >= nv) fz = (nv >= 3 && fz >= 3) ? fz - 2 : nv - 1;
+        zs = {fz};
+    }
     else for (int z = 0; z < nv; ++z) zs.push_back(z);
     if (!sl) ss = {0};
     else if (ctx->force_slices >= 0) ss = {ctx->force_slices};
     else ss = {1, 0};
-    *zvar = zs[0];
-    *slices = ss[0];
-    if (zs.size() * ss.size() == 1) return DDA_OK;
-    const std::pair<int, int> key((int)sizeof(cx<T>), R);
+    auto xlist = [&](int force) {
+        std::vector<int> xs;
+        if (nx <= 1) {
+            xs = {0};
+        } else if (force >= 0) {
+            xs = {std::min(force, nx - 1)};
+        } else {
+            for (int x = 1; x < nx; ++x) xs.push_back(x);
+            xs.push_back(0);
+        }
+        return xs;
+    };
+    const std::vector<int> xfs = xlist(ctx->force_xf), xis = xlist(ctx->force_xi);
+    // untimed choice: the first of each list (warp-local x passes, plan 0)
+    auto apply = [&](const std::array<int, 4>& c) {
+        out->zvar = c[0];
+        out->slices = c[1];
+        out->xfwd = c[2];
+        out->xinv = c[3];
+    };
+    std::array<int, 4> cur = {zs[0], ss[0], xfs[0], xis[0]};
+    apply(cur);
+    if (zs.size() * ss.size() == 1 && xfs.size() == 1 && xis.size() == 1) return DDA_OK;
+    // plain matvecs and the BiCGstab matvecs with fused updates (the solves)
+    // are tuned apart: the fused gather and scatter change what is fastest
+    const std::pair<int, int> key((int)sizeof(cx<T>) * (fused ? -1 : 1), R);
     auto it = ctx->zsched.find(key);
     if (it != ctx->zsched.end()) {
-        *zvar = it->second.first;
-        *slices = it->second.second;
+        apply(it->second);
         return DDA_OK;
     }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CU(cudaStreamIsCapturing(ctx->stream, &cs));
     if (!may_time || cs != cudaStreamCaptureStatusNone) {
-        if (zs.size() > 1) *zvar = R >= 8 ? 1 : 2;
+        if (zs.size() > 1) out->zvar = R >= 8 ? 1 : 2;
         return DDA_OK;
     }
-    // zero-filled x, y and 1/alpha table (their values do not change the timing)
+    // x, y and 1/alpha table filled with one byte pattern (finite, nonzero
+    // values; they do not change the timing), and for the fused matvecs a
+    // scratch Krylov state, partial sums, tickets and active flags
     const int BS = beta_rhs_stride(ctx);
-    const size_t vec = (size_t)R * 3 * ctx->g.N * sizeof(cx<T>);
+    const size_t vec = align256((size_t)R * 3 * ctx->g.N * sizeof(cx<T>));
+    const size_t tab = align256((size_t)R * BS * sizeof(cx<T>));
+    const int ps = partial_stride(ctx);
+    const size_t stb = align256((size_t)R * sizeof(KState)), pb = align256((size_t)R * ps * sizeof(double2));
+    const size_t cb = align256((size_t)R * sizeof(unsigned)), ab = align256((size_t)R * sizeof(int));
     dda_status s;
-    if ((s = ensure(ctx, ctx->pool[S_TUNE], 2 * vec + (size_t)R * BS * sizeof(cx<T>), true)) != DDA_OK) return s;
+    if ((s = ensure(ctx, ctx->pool[S_TUNE], 2 * vec + tab + (fused ? stb + pb + cb + ab : 0), true)) != DDA_OK)
+        return s;
     char* base = static_cast<char*>(ctx->pool[S_TUNE].p);
-    const cx<T>* x = reinterpret_cast<const cx<T>*>(base);
+    cx<T>* x = reinterpret_cast<cx<T>*>(base);
     cx<T>* y = reinterpret_cast<cx<T>*>(base + vec);
     const cx<T>* beta = reinterpret_cast<const cx<T>*>(base + 2 * vec);
+    KState* kst = reinterpret_cast<KState*>(base + 2 * vec + tab);
+    double2* part = reinterpret_cast<double2*>(base + 2 * vec + tab + stb);
+    unsigned* cnt = reinterpret_cast<unsigned*>(base + 2 * vec + tab + stb + pb);
+    int* act = reinterpret_cast<int*>(base + 2 * vec + tab + stb + pb + cb);
+    CU(cudaMemsetAsync(base, 0x3c, 2 * vec + tab, ctx->stream));
     PadWork<T> w{slot<cx<T>>(ctx, PadSlots<T>::a), slot<cx<T>>(ctx, PadSlots<T>::b)};
     w.beta_tensor = ctx->aniso;
-    std::vector<std::pair<int, int>> combos;
-    for (int zv : zs)
-        for (int sv : ss) combos.emplace_back(zv, sv);
-    auto run = [&](size_t i) {
-        w.zvar = combos[i].first;
-        w.slices = combos[i].second;
-        return launch_matvec<T>(ctx->g, R, x, y, w, ctx->tg, beta, BS, ghat_of<T>(ctx), tw_of<T>(ctx), nullptr,
-                                ctx->stream);
+    auto run = [&](const std::array<int, 4>& c) -> cudaError_t {
+        w.zvar = c[0];
+        w.slices = c[1];
+        w.xfwd = c[2];
+        w.xinv = c[3];
+        if (!fused)
+            return launch_matvec<T>(ctx->g, R, x, y, w, ctx->tg, beta, BS, ghat_of<T>(ctx), tw_of<T>(ctx), nullptr,
+                                    ctx->stream);
+        // the two matvecs of a BiCGstab iteration, on a fresh scratch state
+        // (the fused scatters write alpha and omega, and clear the flag of a
+        // RHS that breaks down)
+        cudaError_t e = cudaMemsetAsync(kst, 0x3c, R * sizeof(KState), ctx->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(act, 0x01, R * sizeof(int), ctx->stream);
+        for (int mode = 1; mode <= 2 && e == cudaSuccess; ++mode) {
+            FusedKrylov<T> fk;
+            fk.mode = mode;
+            fk.r = x;
+            fk.v = y;
+            fk.rhat = x;
+            fk.st = kst;
+            fk.part = part;
+            fk.cnt = cnt;
+            fk.part_stride = ps;
+            e = launch_matvec_fused<T>(ctx->g, R, x, y, w, ctx->tg, beta, BS, ghat_of<T>(ctx), tw_of<T>(ctx), act,
+                                       fk, ctx->stream);
+        }
+        return e;
     };
     const bool was_on = ctx->prof.on;
     ctx->prof.on = false;  // tuning launches are not part of the traced work
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t ce = cudaEventCreate(&e0);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
-    // one warm-up matvec each, then rounds that alternate the combinations
-    // (so a clock ramp or a neighbour's burst does not favour one); keep
-    // each one's best round
-    constexpr int kRounds = 3, kReps = 2;
-    std::vector<float> best(combos.size(), 0.f);
-    for (size_t i = 0; i < combos.size() && ce == cudaSuccess; ++i) ce = run(i);
-    for (int round = 0; round < kRounds && ce == cudaSuccess; ++round) {
-        for (size_t i = 0; i < combos.size() && ce == cudaSuccess; ++i) {
-            ce = cudaEventRecord(e0, ctx->stream);
-            for (int k = 0; k < kReps && ce == cudaSuccess; ++k) ce = run(i);
-            if (ce == cudaSuccess) ce = cudaEventRecord(e1, ctx->stream);
-            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
-            if (ce == cudaSuccess && (round == 0 || ms < best[i])) best[i] = ms;
+    // The fastest of a set of candidates: one warm-up matvec each, then
+    // rounds that alternate the candidates (so a clock ramp or a neighbour's
+    // burst does not favour one); each keeps its best round.
+    auto fastest = [&](const std::vector<std::array<int, 4>>& combos) -> size_t {
+        constexpr int kRounds = 3, kReps = 2;
+        std::vector<float> best(combos.size(), 0.f);
+        for (size_t i = 0; i < combos.size() && ce == cudaSuccess; ++i) ce = run(combos[i]);
+        for (int round = 0; round < kRounds && ce == cudaSuccess; ++round) {
+            for (size_t i = 0; i < combos.size() && ce == cudaSuccess; ++i) {
+                ce = cudaEventRecord(e0, ctx->stream);
+                for (int k = 0; k < kReps && ce == cudaSuccess; ++k) ce = run(combos[i]);
+                if (ce == cudaSuccess) ce = cudaEventRecord(e1, ctx->stream);
+                if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+                if (ce == cudaSuccess && (round == 0 || ms < best[i])) best[i] = ms;
+            }
         }
+        size_t pick = 0;
+        for (size_t i = 1; i < combos.size(); ++i)
+            if (best[i] < best[pick]) pick = i;
+        return pick;
+    };
+    // One coordinate at a time (the passes are separate kernels): the z
+    // schedule and slice passes with the default x passes, then the x-forward
+    // schedule, then the x-inverse schedule.
+    std::vector<std::array<int, 4>> combos;
+    for (int zv : zs)
+        for (int sv : ss) combos.push_back({zv, sv, cur[2], cur[3]});
+    if (combos.size() > 1) cur = combos[fastest(combos)];
+    if (!cur[1] && xfs.size() > 1 && ce == cudaSuccess) {
+        combos.clear();
+        for (int xv : xfs) combos.push_back({cur[0], 0, xv, cur[3]});
+        cur = combos[fastest(combos)];
+    }
+    if (!cur[1] && xis.size() > 1 && ce == cudaSuccess) {
+        combos.clear();
+        for (int xv : xis) combos.push_back({cur[0], 0, cur[2], xv});
+        cur = combos[fastest(combos)];
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     ctx->prof.on = was_on;
     free_mem(ctx->pool[S_TUNE]);
     if (ce != cudaSuccess) return ctx->cuda_fail(ce, "matvec schedule timing");
-    size_t pick = 0;
-    for (size_t i = 1; i < combos.size(); ++i)
-        if (best[i] < best[pick]) pick = i;
-    ctx->zsched[key] = combos[pick];
-    *zvar = combos[pick].first;
-    *slices = combos[pick].second;
+    ctx->zsched[key] = cur;
+    apply(cur);
     return DDA_OK;
 }
 
@@ -479,7 +569,7 @@ dda_status run_matvec(dda_ctx* ctx, int R, const cx<T>* x, cx<T>* y, const int* 
     dda_status zs;
     for (int r0 = 0; r0 < R; r0 += rc) {
         const int rn = std::min(rc, R - r0);
-        if ((zs = pick_schedule<T>(ctx, rn, true, &w.zvar, &w.slices)) != DDA_OK) return zs;
+        if ((zs = pick_schedule<T>(ctx, rn, true, &w)) != DDA_OK) return zs;
         CU(launch_matvec<T>(ctx->g, rn, x + (int64_t)r0 * n, y + (int64_t)r0 * n, w, ctx->tg,
                             beta_of<T>(ctx) + (int64_t)r0 * BS, BS, ghat_of<T>(ctx), tw_of<T>(ctx),
                             active ? active + r0 : nullptr, ctx->stream));
@@ -541,7 +631,7 @@ dda_status run_matvec_fused(dda_ctx* ctx, int R, int mode, cx<T>* x, cx<T>* y, c
     for (int r0 = 0; r0 < R; r0 += rc) {
         const int rn = std::min(rc, R - r0);
         const int64_t o = (int64_t)r0 * n;
-        if ((zs = pick_schedule<T>(ctx, rn, true, &w.zvar, &w.slices)) != DDA_OK) return zs;
+        if ((zs = pick_schedule<T>(ctx, rn, true, &w, true)) != DDA_OK) return zs;
         FusedKrylov<T> fk;
         fk.mode = mode;
         fk.r = r + o;
@@ -1052,8 +1142,6 @@ cudaError_t noalloc_scratch(int device, unsigned char** out) {
     return cudaSuccess;
 }
 
-size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
-
 template <typename T>
 dda_status matvec_noalloc(dda_ctx* ctx, int R, const std::vector<double>& k, const std::vector<cd>& ev,
                           const void* x_dev, void* y_dev) {
@@ -1080,7 +1168,7 @@ dda_status matvec_noalloc(dda_ctx* ctx, int R, const std::vector<double>& k, con
     w.beta_tensor = ctx->aniso;
     CU(cudaMemcpyAsync(d_beta, beta.data(), beta.size() * sizeof(C), cudaMemcpyHostToDevice, ctx->stream));
     dda_status zs;
-    if ((zs = pick_schedule<T>(ctx, R, false, &w.zvar, &w.slices)) != DDA_OK) return zs;  // no timing here
+    if ((zs = pick_schedule<T>(ctx, R, false, &w)) != DDA_OK) return zs;  // no timing here
     CU(launch_matvec<T>(ctx->g, R, static_cast<const C*>(x_dev), static_cast<C*>(y_dev), w, ctx->tg, d_beta, BS,
                         ghat_of<T>(ctx), tw_of<T>(ctx), nullptr, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
@@ -1089,6 +1177,19 @@ dda_status matvec_noalloc(dda_ctx* ctx, int R, const std::vector<double>& k, con
 }  // namespace
 
 namespace {
+// Back to composition codes after per-site materials: the device composition
+// array of the target serves the tables again.
+void leave_site_mode(dda_ctx* ctx) {
+    if (!ctx->site_mode) return;
+    ctx->site_mode = false;
+    ctx->tg.comp_of = (uint8_t*)ctx->m_comp_of.p;
+    ctx->zsched.clear();
+    if (ctx->graph.exec) {
+        cudaGraphExecDestroy(ctx->graph.exec);
+        ctx->graph.exec = nullptr;
+    }
+}
+
 // Switch between the scalar and the tensor 1/alpha tables: the cached
 // schedules (slice passes) and the captured solve graph depend on it.
 void set_isotropy(dda_ctx* ctx, bool aniso) {
@@ -1215,6 +1316,11 @@ dda_status dda_set_target(dda_ctx* ctx, int nx, int ny, int nz, const uint8_t* c
     ctx->zsched.clear();
     ctx->max_code = maxc;
     ctx->has_target = true;
+    if (ctx->site_mode) {  // per-site materials belong to the previous target
+        ctx->site_mode = false;
+        ctx->has_materials = false;
+        ctx->m.clear();
+    }
     if (ctx->graph.exec) {
         cudaGraphExecDestroy(ctx->graph.exec);
         ctx->graph.exec = nullptr;
@@ -1235,9 +1341,41 @@ dda_status dda_set_materials(dda_ctx* ctx, int ncomp, const double* m_complex, d
         if (std::abs(mr * mr - 1.0) == 0.0)
             return ctx->fail(DDA_ERR_ARG, "composition %d matches the ambient medium (zero polarizability)", c + 1);
     }
+    leave_site_mode(ctx);
     ctx->m = m;
     ctx->m_amb = m_ambient;
     set_isotropy(ctx, false);
+    ctx->has_materials = true;
+    ctx->prepared = false;
+    ctx->has32 = false;
+    return DDA_OK;
+}
+
+dda_status dda_set_site_materials(dda_ctx* ctx, const double* m_site, double m_ambient) {
+    if (!ctx) return DDA_ERR_ARG;
+    if (!ctx->has_target) return ctx->fail(DDA_ERR_ARG, "dda_set_target first (one index per occupied site)");
+    if (m_site == nullptr) return ctx->fail(DDA_ERR_ARG, "NULL indices");
+    if (!(m_ambient > 0.0) || !std::isfinite(m_ambient)) return ctx->fail(DDA_ERR_ARG, "ambient index must be > 0");
+    const int64_t N = ctx->g.N;
+    std::vector<cd> m((size_t)N);
+    for (int64_t j = 0; j < N; ++j) {
+        m[j] = cd(m_site[2 * j], m_site[2 * j + 1]);
+        if (!std::isfinite(m[j].real()) || !std::isfinite(m[j].imag()))
+            return ctx->fail(DDA_ERR_NONFINITE, "refractive index of site %lld is not finite", (long long)j);
+        const cd mr = m[j] / m_ambient;
+        if (std::abs(mr * mr - 1.0) == 0.0)
+            return ctx->fail(DDA_ERR_ARG, "site %lld matches the ambient medium (zero polarizability)", (long long)j);
+    }
+    set_isotropy(ctx, false);
+    ctx->m = std::move(m);
+    ctx->m_amb = m_ambient;
+    ctx->site_mode = true;
+    ctx->tg.comp_of = nullptr;
+    ctx->zsched.clear();
+    if (ctx->graph.exec) {
+        cudaGraphExecDestroy(ctx->graph.exec);
+        ctx->graph.exec = nullptr;
+    }
     ctx->has_materials = true;
     ctx->prepared = false;
     ctx->has32 = false;
@@ -1267,6 +1405,7 @@ dda_status dda_set_anisotropic_materials(dda_ctx* ctx, int ncomp, const double* 
                 return ctx->fail(DDA_ERR_NONFINITE, "dielectric-frame angle of composition %d is not finite", c + 1);
         }
     }
+    leave_site_mode(ctx);
     ctx->m.resize(ncomp);
     for (int c = 0; c < ncomp; ++c) ctx->m[c] = m3[c][0];
     ctx->m3 = m3;
@@ -1283,7 +1422,7 @@ dda_status dda_prepare(dda_ctx* ctx, double lambda_vac, double aeff, dda_precisi
     if (!ctx) return DDA_ERR_ARG;
     ProfScope prof_scope(ctx);
     if (!ctx->has_target || !ctx->has_materials) return ctx->fail(DDA_ERR_ARG, "set target and materials first");
-    if ((int)ctx->m.size() < ctx->max_code)
+    if (!ctx->site_mode && (int)ctx->m.size() < ctx->max_code)
         return ctx->fail(DDA_ERR_ARG, "grid uses composition %d but only %d indices given", ctx->max_code, (int)ctx->m.size());
     if (!(lambda_vac > 0.0) || !(aeff > 0.0) || !std::isfinite(lambda_vac) || !std::isfinite(aeff))
         return ctx->fail(DDA_ERR_ARG, "wavelength and aeff must be positive and finite");
@@ -2038,8 +2177,8 @@ dda_status dda_grad_qabs(dda_ctx* ctx, dda_precision precision, const double* kh
 
 dda_status dda_set_schedule(dda_ctx* ctx, int zpass) {
     if (!ctx) return DDA_ERR_ARG;
-    if (zpass < -1 || zpass > 2)
-        return ctx->fail(DDA_ERR_ARG, "z-pass schedule must be -1, 0, 1 or 2 (got %d)", zpass);
+    if (zpass < -1 || zpass > 4)
+        return ctx->fail(DDA_ERR_ARG, "z-pass schedule must be -1 or 0..4 (got %d)", zpass);
     ctx->force_z = zpass;
     ctx->zsched.clear();
     if (ctx->graph.exec) {
@@ -2070,9 +2209,57 @@ dda_status dda_get_schedule(dda_ctx* ctx, int R, int* zpass, int* slices) {
     cudaSetDevice(ctx->device);
     dda_status s;
     if ((s = ensure_pad<float>(ctx, R)) != DDA_OK) return s;
-    int sl = 0;
-    s = pick_schedule<float>(ctx, matvec_chunk<float>(ctx, R), true, zpass, &sl);
-    if (slices) *slices = sl;
+    PadWork<float> w;
+    s = pick_schedule<float>(ctx, matvec_chunk<float>(ctx, R), true, &w);
+    *zpass = w.zvar;
+    if (slices) *slices = w.slices;
+    return s;
+}
+
+dda_status dda_get_solve_schedule(dda_ctx* ctx, int R, int* zpass, int* xfwd, int* xinv) {
+    if (!ctx || !zpass || !xfwd || !xinv) return DDA_ERR_ARG;
+    if (R <= 0) return ctx->fail(DDA_ERR_ARG, "R must be > 0");
+    if (!ctx->prepared || !ctx->has32)
+        return ctx->fail(DDA_ERR_ARG, "dda_prepare with a complex64-capable precision has not been called");
+    ProfScope prof_scope(ctx);
+    cudaSetDevice(ctx->device);
+    dda_status s;
+    if ((s = ensure_pad<float>(ctx, R)) != DDA_OK) return s;
+    PadWork<float> w;
+    s = pick_schedule<float>(ctx, matvec_chunk<float>(ctx, R), true, &w, true);
+    *zpass = w.zvar;
+    *xfwd = w.xfwd;
+    *xinv = w.xinv;
+    return s;
+}
+
+dda_status dda_set_xpass(dda_ctx* ctx, int xfwd, int xinv) {
+    if (!ctx) return DDA_ERR_ARG;
+    if (xfwd < -1 || xfwd > 2 || xinv < -1 || xinv > 2)
+        return ctx->fail(DDA_ERR_ARG, "x-pass schedules must be -1, 0, 1 or 2 (got %d, %d)", xfwd, xinv);
+    ctx->force_xf = xfwd;
+    ctx->force_xi = xinv;
+    ctx->zsched.clear();
+    if (ctx->graph.exec) {
+        cudaGraphExecDestroy(ctx->graph.exec);
+        ctx->graph.exec = nullptr;
+    }
+    return DDA_OK;
+}
+
+dda_status dda_get_xpass(dda_ctx* ctx, int R, int* xfwd, int* xinv) {
+    if (!ctx || !xfwd || !xinv) return DDA_ERR_ARG;
+    if (R <= 0) return ctx->fail(DDA_ERR_ARG, "R must be > 0");
+    if (!ctx->prepared || !ctx->has32)
+        return ctx->fail(DDA_ERR_ARG, "dda_prepare with a complex64-capable precision has not been called");
+    ProfScope prof_scope(ctx);
+    cudaSetDevice(ctx->device);
+    dda_status s;
+    if ((s = ensure_pad<float>(ctx, R)) != DDA_OK) return s;
+    PadWork<float> w;
+    s = pick_schedule<float>(ctx, matvec_chunk<float>(ctx, R), true, &w);
+    *xfwd = w.xfwd;
+    *xinv = w.xinv;
     return s;
 }
 

@@ -97,4 +97,10 @@ template <typename D, typename S> __host__ __device__ __forceinline__ D ccast(S 
     return r;
 }
 
+// Index of site s in the per-RHS 1/alpha and weight tables: its composition
+// code, or, with per-site materials (no composition array), s + 1.
+__device__ __forceinline__ int table_index(const uint8_t* __restrict__ comp_of, int64_t s) {
+    return comp_of != nullptr ? (int)comp_of[s] : (int)(s + 1);
+}
+
 }  // namespace dda

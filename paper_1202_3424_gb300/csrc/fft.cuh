@@ -189,6 +189,70 @@ template <int SGN, typename C> struct Dft<8, SGN, C> {
     }
 };
 
+// Radix 16 as 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2; four length-4 DFTs over
+// n1, the twiddles W16^(n2 k1), four length-4 DFTs over n2.
+template <int SGN, typename C> struct Dft<16, SGN, C> {
+    template <int J> __device__ __forceinline__ static C w16(C a) {
+        using T = typename real_of<C>::type;
+        const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173);  // cos, sin(pi/8)
+        const T r2 = T(0.70710678118654752440);
+        auto w = [](T re, T im) { C r; r.x = re; r.y = im; return r; };
+        if constexpr (J == 1) return cmul(a, w(c1, SGN > 0 ? s1 : -s1));
+        else if constexpr (J == 2) return cscale(cadd(a, cmul_i<SGN>(a)), r2);
+        else if constexpr (J == 3) return cmul(a, w(s1, SGN > 0 ? c1 : -c1));
+        else if constexpr (J == 4) return cmul_i<SGN>(a);
+        else if constexpr (J == 6) return cscale(csub(cmul_i<SGN>(a), a), r2);
+        else return cmul(a, w(-c1, SGN > 0 ? -s1 : s1));  // J == 9
+    }
+    __device__ __forceinline__ static void finish(C* v, C (&y)[4][4]) {
+        y[1][1] = w16<1>(y[1][1]);
+        y[1][2] = w16<2>(y[1][2]);
+        y[1][3] = w16<3>(y[1][3]);
+        y[2][1] = w16<2>(y[2][1]);
+        y[2][2] = w16<4>(y[2][2]);
+        y[2][3] = w16<6>(y[2][3]);
+        y[3][1] = w16<3>(y[3][1]);
+        y[3][2] = w16<6>(y[3][2]);
+        y[3][3] = w16<9>(y[3][3]);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            C z[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+            Dft<4, SGN, C>::run(z);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = z[k2];
+        }
+    }
+    __device__ __forceinline__ static void run(C* v) {
+        C y[4][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) {
+#pragma unroll
+            for (int n1 = 0; n1 < 4; ++n1) y[n2][n1] = v[4 * n1 + n2];
+            Dft<4, SGN, C>::run(y[n2]);
+        }
+        finish(v, y);
+    }
+    // inputs 8..15 are zero
+    __device__ __forceinline__ static void run_half(C* v) {
+        C y[4][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) {
+            y[n2][0] = v[n2];
+            y[n2][1] = v[4 + n2];
+            Dft<4, SGN, C>::run_half(y[n2]);
+        }
+        finish(v, y);
+    }
+};
+
+// ---- exchange-plane address maps -------------------------------------------
+// Kernels whose pencils lie within one warp give each pencil its own plane
+// and map position pos of the exchange after stage S to a swizzled slot;
+// the default keeps the position.
+struct NoSwizzle {
+    template <int DIR, int S> __device__ __forceinline__ static int map(int pos) { return pos; }
+};
+
 // ---- stage recursion -----------------------------------------------------
 // v: E registers; u: thread index within the pencil (0..NT-1);
 // tw: forward twiddle table of L entries exp(-2 pi i m/L);
@@ -199,7 +263,7 @@ template <bool WARP> __device__ __forceinline__ void stage_sync() {
     else __syncthreads();
 }
 
-template <typename C, class PL, int DIR, int S, class Ld, class St, bool WARP = false>
+template <typename C, class PL, int DIR, int S, class Ld, class St, bool WARP = false, class SWZ = NoSwizzle>
 __device__ __forceinline__ void fft_stages(C (&v)[PL::E], int u, const C* __restrict__ tw, Ld& ld, St& st,
                                            bool half_first) {
     constexpr int L = PL::L, NT = PL::NT, E = PL::E, NS = PL::NS;
@@ -252,19 +316,20 @@ __device__ __forceinline__ void fft_stages(C (&v)[PL::E], int u, const C* __rest
 #pragma unroll
             for (int q = 0; q < NB; ++q)
 #pragma unroll
-                for (int m = 0; m < R; ++m) st(base + q * NT * R + m * P, v[q * R + m]);
+                for (int m = 0; m < R; ++m) st(SWZ::template map<DIR, S>(base + q * NT * R + m * P), v[q * R + m]);
         } else if constexpr (P % NT == 0) {
 #pragma unroll
             for (int q = 0; q < NB; ++q)
 #pragma unroll
                 for (int m = 0; m < R; ++m)
-                    st(u + (q - q % (P / NT)) * NT * R + (q % (P / NT)) * NT + m * P, v[q * R + m]);
+                    st(SWZ::template map<DIR, S>(u + (q - q % (P / NT)) * NT * R + (q % (P / NT)) * NT + m * P),
+                       v[q * R + m]);
         } else {
 #pragma unroll
             for (int q = 0; q < NB; ++q) {
                 const int i = u + q * NT, k = i % P;
 #pragma unroll
-                for (int m = 0; m < R; ++m) st((i - k) * R + k + m * P, v[q * R + m]);
+                for (int m = 0; m < R; ++m) st(SWZ::template map<DIR, S>((i - k) * R + k + m * P), v[q * R + m]);
             }
         }
         stage_sync<WARP>();
@@ -273,8 +338,8 @@ __device__ __forceinline__ void fft_stages(C (&v)[PL::E], int u, const C* __rest
 #pragma unroll
         for (int q = 0; q < NB2; ++q)
 #pragma unroll
-            for (int j = 0; j < R2; ++j) v[q * R2 + j] = ld(u + q * NT + j * (L / R2));
-        fft_stages<C, PL, DIR, S + 1, Ld, St, WARP>(v, u, tw, ld, st, false);
+            for (int j = 0; j < R2; ++j) v[q * R2 + j] = ld(SWZ::template map<DIR, S>(u + q * NT + j * (L / R2)));
+        fft_stages<C, PL, DIR, S + 1, Ld, St, WARP, SWZ>(v, u, tw, ld, st, false);
     }
 }
 

@@ -52,6 +52,8 @@ template <typename T> struct PadWork {
     cx<T>* u1 = nullptr;  // [R][3][nz][ny][Lx] (unused when the slice passes run)
     cx<T>* u2 = nullptr;  // [R][3][nz][Ly][Lx]
     int zvar = 0;         // z-pass schedule, see zconv_schedules
+    int xfwd = 0;         // x-forward schedule, see xpass_schedules
+    int xinv = 0;         // x-inverse schedule, likewise
     int slices = 1;       // fused x+y slice passes where built (see slice_passes)
     // The 1/alpha table holds 3x3 tensors (anisotropic materials): per RHS
     // [3 rows c][comp][3 columns], so row c of composition comp's tensor is at
@@ -92,6 +94,12 @@ int xinv_blocks_per_rhs(const Geom& g);
 // compute the same product; the context times them per RHS count and keeps
 // the fastest (dda_set_schedule can force one).
 template <typename T> int zconv_schedules(const Geom& g);
+
+// Number of x-pass schedules for this grid and arithmetic type: 0, the rows
+// staged through shared memory (k_xfwd, k_xinv), always; for complex64 also
+// 1 + V for the warp-local passes with radix plan variant V (xwarp.cuh).
+// Timed by the context like the z schedules.
+template <typename T> int xpass_schedules(const Geom& g);
 
 // Fused x+y passes over whole z-slices (slice_impl.cuh): built for this
 // grid and element type?  Then the matvec runs xy-fwd, z, yx-inv instead of

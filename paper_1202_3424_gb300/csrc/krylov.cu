@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(kThreads)
         }
         acc[0].x += im;
         if (tensor) {
-            const double* wt = wr + comp_of[j] * 6;
+            const double* wt = wr + table_index(comp_of, j) * 6;
             double q = 0.0;
 #pragma unroll
             for (int c = 0; c < 3; ++c) q += wt[c] * (pv[c].x * pv[c].x + pv[c].y * pv[c].y);
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kThreads)
                  wt[5] * (pv[1].x * pv[2].x + pv[1].y * pv[2].y);
             acc[0].y += q;
         } else {
-            acc[0].y += wr[comp_of[j]] * p2;
+            acc[0].y += wr[table_index(comp_of, j)] * p2;
         }
     }
     if (last_block_total<1>(acc, part + (int64_t)r * gridDim.x, cnt + r) && threadIdx.x == 0) sums[r] = acc[0];
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(kThreads)
     k_adjoint_rhs(int64_t N, const double2* __restrict__ P, const uint8_t* __restrict__ comp_of,
                   const double* __restrict__ w, double2* __restrict__ b) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
-        const double wj = w[comp_of[j]];
+        const double wj = w[table_index(comp_of, j)];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const double2 pv = P[c * N + j];
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(kThreads)
             p2 += pv.x * pv.x + pv.y * pv.y;
             nup = cadd(nup, cmul(nv, pv));
         }
-        const double2 bp = dbeta[comp_of[j]];
+        const double2 bp = dbeta[table_index(comp_of, j)];
         const double2 q = cmul(bp, nup);
         g_re[j] = K * (-p2 * bp.y - 2.0 * q.x);
         g_im[j] = K * (-p2 * bp.x + 2.0 * q.y);

@@ -37,6 +37,7 @@
 #include "internal.h"
 #include "krylov_dev.cuh"
 #include "profiler.h"
+#include "xwarp.cuh"
 
 namespace dda {
 
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
             if constexpr (MODE == 1) kh[i] = czero<C>();
             if (s >= 0) {
                 xv[i] = xs[s];
-                bv[i] = TENSOR ? br[comp_of[s] * 3 + c] : br[comp_of[s]];
+                bv[i] = TENSOR ? br[table_index(comp_of, s) * 3 + c] : br[table_index(comp_of, s)];
                 if constexpr (MODE == 1) kh[i] = krhat[off + s];
             }
         }
@@ -280,7 +281,7 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
         if (s >= 0) {
             C yv = cadd(buf[ix * SP + t2], cmul(bv[i], xv[i]));
             if constexpr (TENSOR) {  // the two off-diagonal entries of row c
-                const C* bb = br + comp_of[s] * 3;
+                const C* bb = br + table_index(comp_of, s) * 3;
                 const int c1 = c == 0 ? 1 : 0, c2 = c == 2 ? 1 : 2;
                 const C* xr = X + (int64_t)r * 3 * N;
                 yv = cadd(yv, cadd(cmul(bb[c1], xr[c1 * N + s]), cmul(bb[c2], xr[c2 * N + s])));
@@ -449,42 +450,53 @@ __global__ void __launch_bounds__(3 * tp_z<LZ, T>() * ZPlan<LZ>::NT, zconv_min_b
 // the current one is transformed, so one block keeps its column's loads in
 // flight while computing.  Shared traffic per point is about half that of
 // k_zconv; the price is ~128 registers per thread, so the plan must keep
-// L/NT <= 8 points per thread.
+// L/NT <= 8 points per thread -- or, with radix-16 plan variants (one
+// exchange per transform where the plain plan needs two), 16 points per
+// thread and no register prefetch of the next RHS.
 // Column mapping: a block takes TP adjacent columns kx at one ky and stages
 // their Green entries with the signs of the odd components (xy in x and y,
 // xz in x, yz in y) folded in; k_zconv_oct below maps octant columns instead.
+template <int L, int V> struct ZrPlan : Plan<L> {};
+template <> struct ZrPlan<128, 1> : PlanDef<128, 8, 8, 16> {};
+template <> struct ZrPlan<256, 1> : PlanDef<256, 16, 16, 16> {};
+__host__ __device__ constexpr int zr_variants(int L) { return (L == 128 || L == 256) ? 2 : 1; }
 template <int L> __host__ __device__ constexpr bool zreg_ok() { return Plan<L>::E <= 8; }
-template <int L> __host__ __device__ constexpr int tp_zr() {
-    int tp = 128 / Plan<L>::NT;
+template <class PL> __host__ __device__ constexpr int tp_zr() {
+    int tp = 128 / PL::NT;
     return tp > 32 ? 32 : (tp < 4 ? 4 : tp);
 }
-template <int L> __host__ __device__ constexpr int zreg_threads() { return tp_zr<L>() * Plan<L>::NT; }
-// 128 registers per thread: 512 / threads blocks per SM
-template <int L> __host__ __device__ constexpr int zreg_min_blocks() {
-    return 512 / zreg_threads<L>() < 1 ? 1 : 512 / zreg_threads<L>();
+template <class PL> __host__ __device__ constexpr int zreg_threads() { return tp_zr<PL>() * PL::NT; }
+// 128 registers per thread: 512 / threads blocks per SM; the 16-point
+// variants (whose ~100 KB of shared memory allows 2 blocks per SM anyway)
+// take the registers of 2 blocks
+template <class PL> __host__ __device__ constexpr int zreg_min_blocks() {
+    return PL::E > 8 ? 2 : (512 / zreg_threads<PL>() < 1 ? 1 : 512 / zreg_threads<PL>());
 }
-template <int L, typename T> __host__ __device__ constexpr int zreg_rows() {
-    return exchange_rows<L, Plan<L>::NT, tp_zr<L>(), sizeof(cx<T>)>();
+template <class PL, typename T> __host__ __device__ constexpr int zreg_rows() {
+    return exchange_rows<PL::L, PL::NT, tp_zr<PL>(), sizeof(cx<T>)>();
 }
-template <int L, typename T> __host__ __device__ constexpr size_t zreg_smem() {
-    return (((size_t)3 * zreg_rows<L, T>() + (size_t)6 * (L / 2 + 1)) * tp_zr<L>() + L) * sizeof(cx<T>);
+template <class PL, typename T> __host__ __device__ constexpr size_t zreg_smem() {
+    return (((size_t)3 * zreg_rows<PL, T>() + (size_t)6 * (PL::L / 2 + 1)) * tp_zr<PL>() + PL::L) * sizeof(cx<T>);
 }
 // k_zconv_oct: one more Green column per tile
-template <int L, typename T> __host__ __device__ constexpr size_t zoct_smem() {
-    return zreg_smem<L, T>() + (size_t)6 * (L / 2 + 1) * sizeof(cx<T>);
+template <class PL, typename T> __host__ __device__ constexpr size_t zoct_smem() {
+    return zreg_smem<PL, T>() + (size_t)6 * (PL::L / 2 + 1) * sizeof(cx<T>);
 }
+// the loads of the next RHS are prefetched into registers up to 8 points per thread
+template <class PL> __host__ __device__ constexpr bool zreg_prefetch() { return PL::E <= 8; }
 
-template <typename T, int LZ, int RB>
-__global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
+template <typename T, int LZ, int RB, int V = 0>
+__global__ void __launch_bounds__(zreg_threads<ZrPlan<LZ, V>>(), zreg_min_blocks<ZrPlan<LZ, V>>())
     k_zconv_reg(cx<T>* __restrict__ U2, const cx<T>* __restrict__ gh, int R, int Lx, int Ly,
                 const cx<T>* __restrict__ tw, const int* __restrict__ active) {
     using C = cx<T>;
-    using PL = Plan<LZ>;
-    constexpr int TP = tp_zr<LZ>(), NT = PL::NT, NZ = LZ / 2, HZ = LZ / 2 + 1, E = PL::E;
+    using PL = ZrPlan<LZ, V>;
+    constexpr int TP = tp_zr<PL>(), NT = PL::NT, NZ = LZ / 2, HZ = LZ / 2 + 1, E = PL::E;
     constexpr int R0 = stage_radix<PL, -1>(0), NB0 = E / R0, JN = R0 / 2;  // half-zero first stage
+    constexpr bool PF = zreg_prefetch<PL>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);  // exchange planes [3][ROWS][TP]
-    constexpr int ROWS = zreg_rows<LZ, T>();  // padded rows of an exchange plane
+    constexpr int ROWS = zreg_rows<PL, T>();  // padded rows of an exchange plane
     C* gs = buf + 3 * ROWS * TP;              // Green tensor [6][HZ][TP]
     C* tws = gs + 6 * HZ * TP;                // twiddle table [LZ]
     const int ky = blockIdx.y;
@@ -507,8 +519,8 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
     auto column = [&](int r, int c) {
         return U2 + ((int64_t)r * 3 + c) * NZ * plane + (int64_t)ky * Lx + (valid ? kx : 0);
     };
-    C nxt[3][NB0 * JN];  // first-stage inputs of the next RHS
-    auto prefetch = [&](int r) {
+    C nxt[3][PF ? NB0 * JN : 1];  // first-stage inputs of the next RHS
+    auto load_first = [&](int r, auto&& put) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const C* bc = column(r, c);
@@ -516,8 +528,11 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
             for (int q = 0; q < NB0; ++q)
 #pragma unroll
                 for (int j = 0; j < JN; ++j)
-                    nxt[c][q * JN + j] = valid ? __ldcs(bc + (int64_t)(u + q * NT + j * (LZ / R0)) * plane) : czero<C>();
+                    put(c, q, j, valid ? __ldcs(bc + (int64_t)(u + q * NT + j * (LZ / R0)) * plane) : czero<C>());
         }
+    };
+    auto prefetch = [&](int r) {
+        if constexpr (PF) load_first(r, [&](int c, int q, int j, C x) { nxt[c][q * JN + j] = x; });
     };
     // the first RHS's loads are in flight while the Green tensor is staged
     int r = next_active(r0);
@@ -573,12 +588,16 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
 #pragma unroll 1
     while (r < rend) {
         C vc[3][E];
+        if constexpr (PF) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
+            for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int q = 0; q < NB0; ++q)
+                for (int q = 0; q < NB0; ++q)
 #pragma unroll
-                for (int j = 0; j < JN; ++j) vc[c][q * R0 + j] = nxt[c][q * JN + j];
+                    for (int j = 0; j < JN; ++j) vc[c][q * R0 + j] = nxt[c][q * JN + j];
+        } else {
+            load_first(r, [&](int c, int q, int j, C x) { vc[c][q * R0 + j] = x; });
+        }
         const int rn = next_active(r + 1);
         if (rn < rend) prefetch(rn);
         // (each transform's first exchange opens with a barrier, which also
@@ -620,17 +639,18 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
 // t takes kxo = a + TP - t), so both loads are aligned rows of TP columns and
 // every column 0..Lx-1 has one owner (the self-mirrored Lx/2 is a mirrored
 // one of the last block); the tile therefore holds TP + 1 Green columns.
-template <typename T, int LZ, int RB>
-__global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
+template <typename T, int LZ, int RB, int V = 0>
+__global__ void __launch_bounds__(zreg_threads<ZrPlan<LZ, V>>(), zreg_min_blocks<ZrPlan<LZ, V>>())
     k_zconv_oct(cx<T>* __restrict__ U2, const cx<T>* __restrict__ gh, int R, int Lx, int Ly,
                 const cx<T>* __restrict__ tw, const int* __restrict__ active) {
     using C = cx<T>;
-    using PL = Plan<LZ>;
-    constexpr int TP = tp_zr<LZ>(), NT = PL::NT, NZ = LZ / 2, HZ = LZ / 2 + 1, E = PL::E;
+    using PL = ZrPlan<LZ, V>;
+    constexpr int TP = tp_zr<PL>(), NT = PL::NT, NZ = LZ / 2, HZ = LZ / 2 + 1, E = PL::E;
     constexpr int R0 = stage_radix<PL, -1>(0), NB0 = E / R0, JN = R0 / 2;  // half-zero first stage
+    constexpr bool PF = zreg_prefetch<PL>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);  // exchange planes [3][ROWS][TP]
-    constexpr int ROWS = zreg_rows<LZ, T>();  // padded rows of an exchange plane
+    constexpr int ROWS = zreg_rows<PL, T>();  // padded rows of an exchange plane
     constexpr int TG = TP + 1;                // Green columns a .. a+TP
     C* gs = buf + 3 * ROWS * TP;              // Green tensor [6][HZ][TG]
     C* tws = gs + 6 * HZ * TG;                // twiddle table [LZ]
@@ -662,8 +682,8 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
         const int kx = (v & 1) ? Lx - octx(v) : octx(v), ky = (v >> 1) ? Ly - kyo : kyo;
         return U2 + ((int64_t)r * 3 + c) * NZ * plane + (int64_t)ky * Lx + (col_valid(v) ? kx : 0);
     };
-    C nxt[3][NB0 * JN];  // first-stage inputs of the next column
-    auto prefetch = [&](int r, int v) {
+    C nxt[3][PF ? NB0 * JN : 1];  // first-stage inputs of the next column
+    auto load_first = [&](int r, int v, auto&& put) {
         const bool valid = col_valid(v);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -672,8 +692,11 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
             for (int q = 0; q < NB0; ++q)
 #pragma unroll
                 for (int j = 0; j < JN; ++j)
-                    nxt[c][q * JN + j] = valid ? __ldcs(bc + (int64_t)(u + q * NT + j * (LZ / R0)) * plane) : czero<C>();
+                    put(c, q, j, valid ? __ldcs(bc + (int64_t)(u + q * NT + j * (LZ / R0)) * plane) : czero<C>());
         }
+    };
+    auto prefetch = [&](int r, int v) {
+        if constexpr (PF) load_first(r, v, [&](int c, int q, int j, C x) { nxt[c][q * JN + j] = x; });
     };
     // the first column's loads are in flight while the Green tensor is staged
     int r = next_active(r0), v = 0;
@@ -701,12 +724,16 @@ __global__ void __launch_bounds__(zreg_threads<LZ>(), zreg_min_blocks<LZ>())
 #pragma unroll 1
     while (r < rend) {
         C vc[3][E];
+        if constexpr (PF) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
+            for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int q = 0; q < NB0; ++q)
+                for (int q = 0; q < NB0; ++q)
 #pragma unroll
-                for (int j = 0; j < JN; ++j) vc[c][q * R0 + j] = nxt[c][q * JN + j];
+                    for (int j = 0; j < JN; ++j) vc[c][q * R0 + j] = nxt[c][q * JN + j];
+        } else {
+            load_first(r, v, [&](int c, int q, int j, C x) { vc[c][q * R0 + j] = x; });
+        }
         int rn = r, vn = v + 1;
         if (vn >= nv) {
             rn = next_active(r + 1);
@@ -821,9 +848,64 @@ template <typename T> struct LaunchX {
     // double-float matvecs run only the plain passes (no fused Krylov modes)
     static constexpr bool kDouble = std::is_same<T, dfl>::value;
     static constexpr int koff = sizeof(T) == 4 ? 0 : (kDouble ? (KK_XFWD_DF - KK_XFWD_C64) : (KK_XFWD_C128 - KK_XFWD_C64));
+    // warp-local x passes (xwarp.cuh, complex64): xvar = 1 + plan variant
+    static constexpr bool kWarpX = sizeof(T) == 4 && !kDouble;
+    template <int LX, int V>
+    static cudaError_t fwd_w(const Geom& g, int R, cx<T>* x, cx<T>* u1, const int* site_of, const cx<T>* tw,
+                             const int* active, const FusedKrylov<T>& fk, cudaStream_t st) {
+        if constexpr (kWarpX) {
+            using PL = XwPlan<LX, V>;
+            const size_t sm = xw_smem<PL>();
+            const int nrows = g.ny * g.nz;
+            dim3 grid((nrows + xw_rows<PL>() - 1) / xw_rows<PL>(), 3, R);
+            auto go = [&](auto kern, const cx<T>* kr, const cx<T>* kv, const KState* ks) -> cudaError_t {
+                cudaError_t e = allow_smem(kern, sm);
+                if (e != cudaSuccess) return e;
+                PROF_BEGIN(st);
+                kern<<<grid, kXwThreads, sm, st>>>(x, u1, site_of, nrows, g.N, tw, active, kr, kv, ks);
+                PROF_END(KK_XFWD_C64, R, st);
+                return cudaGetLastError();
+            };
+            if (fk.mode == 1) return go(k_xfwd_w<LX, V, 1>, fk.r, fk.v, fk.st);
+            if (fk.mode == 2) return go(k_xfwd_w<LX, V, 2>, fk.r, fk.v, fk.st);
+            return go(k_xfwd_w<LX, V, 0>, nullptr, nullptr, nullptr);
+        }
+        return cudaErrorInvalidValue;
+    }
+    template <int LX, int V, bool TENSOR>
+    static cudaError_t inv_w(const Geom& g, int R, const cx<T>* u1, cx<T>* y, const cx<T>* x, const DevTarget& tg,
+                             const cx<T>* beta, int beta_stride, const cx<T>* tw, int* active,
+                             const FusedKrylov<T>& fk, cudaStream_t st) {
+        if constexpr (kWarpX) {
+            using PL = XwPlan<LX, V>;
+            const size_t sm = xw_smem<PL>();
+            const int nrows = g.ny * g.nz;
+            dim3 grid((nrows + xw_rows<PL>() - 1) / xw_rows<PL>(), 3, R);
+            auto go = [&](auto kern) -> cudaError_t {
+                cudaError_t e = allow_smem(kern, sm);
+                if (e != cudaSuccess) return e;
+                PROF_BEGIN(st);
+                kern<<<grid, kXwThreads, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride, nrows, g.N,
+                                                   tw, active, fk.rhat, fk.st, fk.part, fk.cnt, fk.part_stride);
+                PROF_END(KK_XINV_C64, R, st);
+                return cudaGetLastError();
+            };
+            if (fk.mode == 1) return go(k_xinv_w<LX, V, 1, TENSOR>);
+            if (fk.mode == 2) return go(k_xinv_w<LX, V, 2, TENSOR>);
+            return go(k_xinv_w<LX, V, 0, TENSOR>);
+        }
+        return cudaErrorInvalidValue;
+    }
+    template <int LX> static int xvariants() { return kWarpX ? 1 + xw_variants(LX) : 1; }
     template <int LX>
     static cudaError_t fwd(const Geom& g, int R, cx<T>* x, cx<T>* u1, const int* site_of, const cx<T>* tw,
-                           const int* active, const FusedKrylov<T>& fk, cudaStream_t st) {
+                           const int* active, const FusedKrylov<T>& fk, int xvar, cudaStream_t st) {
+        if constexpr (kWarpX) {
+            if (xvar == 2 && xw_variants(LX) > 1) {
+                if constexpr (xw_variants(LX) > 1) return fwd_w<LX, 1>(g, R, x, u1, site_of, tw, active, fk, st);
+            }
+            if (xvar >= 1) return fwd_w<LX, 0>(g, R, x, u1, site_of, tw, active, fk, st);
+        }
         constexpr int TP = tp_x<LX, sizeof(cx<T>)>(), NTH = TP * XPlan<LX, sizeof(cx<T>)>::NT;
         const size_t sm = (size_t)LX * (TP + 1) * sizeof(cx<T>);
         const int nrows = g.ny * g.nz;
@@ -868,7 +950,17 @@ template <typename T> struct LaunchX {
     template <int LX>
     static cudaError_t inv(const Geom& g, int R, const cx<T>* u1, cx<T>* y, const cx<T>* x, const DevTarget& tg,
                            const cx<T>* beta, int beta_stride, bool tensor, const cx<T>* tw, int* active,
-                           const FusedKrylov<T>& fk, cudaStream_t st) {
+                           const FusedKrylov<T>& fk, int xvar, cudaStream_t st) {
+        if constexpr (kWarpX) {
+            if (xvar == 2 && xw_variants(LX) > 1) {
+                if constexpr (xw_variants(LX) > 1)
+                    return tensor ? inv_w<LX, 1, true>(g, R, u1, y, x, tg, beta, beta_stride, tw, active, fk, st)
+                                  : inv_w<LX, 1, false>(g, R, u1, y, x, tg, beta, beta_stride, tw, active, fk, st);
+            }
+            if (xvar >= 1)
+                return tensor ? inv_w<LX, 0, true>(g, R, u1, y, x, tg, beta, beta_stride, tw, active, fk, st)
+                              : inv_w<LX, 0, false>(g, R, u1, y, x, tg, beta, beta_stride, tw, active, fk, st);
+        }
         auto run = [&](auto mode) {
             constexpr int M = decltype(mode)::value;
             return tensor ? inv_mode<LX, M, true>(g, R, u1, y, x, tg, beta, beta_stride, tw, active, fk, st)
@@ -918,26 +1010,37 @@ template <typename T> struct LaunchX {
         const int rb = multi ? RB : 1;
         cudaError_t e;
         if constexpr (sizeof(T) == 4 && zreg_ok<LZ>()) {
-            if (zvar == 1 || zvar == 2) {
-                // a staged Green tile serves RB column-RHS: RBZ RHS of one
-                // column, or of the (up to) 4 columns of an octant column
-                // (long columns: the tile is ~2 RHS of loads, so it serves 16)
-                constexpr int TP = tp_zr<LZ>(), RBZ = LZ >= 256 ? 16 : 8, RBO = RBZ / 4;
-                const bool oct = zvar == 2;
-                const size_t sm = oct ? zoct_smem<LZ, T>() : zreg_smem<LZ, T>();
-                const int rbz = !multi ? 1 : (oct ? RBO : RBZ);
-                dim3 grid(oct ? (g.Lx / 2 + TP - 1) / TP : (g.Lx + TP - 1) / TP, oct ? g.Ly / 2 + 1 : g.Ly,
-                          (R + rbz - 1) / rbz);
-                auto go = [&](auto kern) -> cudaError_t {
-                    cudaError_t ke = allow_smem(kern, sm);
-                    if (ke != cudaSuccess) return ke;
-                    PROF_BEGIN(st);
-                    kern<<<grid, zreg_threads<LZ>(), sm, st>>>(u2, gh, R, g.Lx, g.Ly, tw, active);
-                    PROF_END(KK_ZCONV_C64 + koff, R, st);
-                    return cudaGetLastError();
+            // 1, 2: register-resident, by columns or octant columns, plan 0;
+            // 3, 4: the same with radix plan variant 1 (zr_variants)
+            if (zvar >= 1 && zvar <= 4) {
+                auto sched = [&](auto var) -> cudaError_t {
+                    constexpr int V = decltype(var)::value;
+                    using PL = ZrPlan<LZ, V>;
+                    // a staged Green tile serves RB column-RHS: RBZ RHS of one
+                    // column, or of the (up to) 4 columns of an octant column
+                    // (long columns: the tile is ~2 RHS of loads, so it serves 16)
+                    constexpr int TP = tp_zr<PL>(), RBZ = LZ >= 256 ? 16 : 8, RBO = RBZ / 4;
+                    const bool oct = zvar == 2 || zvar == 4;
+                    const size_t sm = oct ? zoct_smem<PL, T>() : zreg_smem<PL, T>();
+                    const int rbz = !multi ? 1 : (oct ? RBO : RBZ);
+                    dim3 grid(oct ? (g.Lx / 2 + TP - 1) / TP : (g.Lx + TP - 1) / TP, oct ? g.Ly / 2 + 1 : g.Ly,
+                              (R + rbz - 1) / rbz);
+                    auto go = [&](auto kern) -> cudaError_t {
+                        cudaError_t ke = allow_smem(kern, sm);
+                        if (ke != cudaSuccess) return ke;
+                        PROF_BEGIN(st);
+                        kern<<<grid, zreg_threads<PL>(), sm, st>>>(u2, gh, R, g.Lx, g.Ly, tw, active);
+                        PROF_END(KK_ZCONV_C64 + koff, R, st);
+                        return cudaGetLastError();
+                    };
+                    if (!multi) return oct ? go(k_zconv_oct<T, LZ, 1, V>) : go(k_zconv_reg<T, LZ, 1, V>);
+                    return oct ? go(k_zconv_oct<T, LZ, RBO, V>) : go(k_zconv_reg<T, LZ, RBZ, V>);
                 };
-                if (!multi) return oct ? go(k_zconv_oct<T, LZ, 1>) : go(k_zconv_reg<T, LZ, 1>);
-                return oct ? go(k_zconv_oct<T, LZ, RBO>) : go(k_zconv_reg<T, LZ, RBZ>);
+                if (zvar >= 3) {
+                    if constexpr (zr_variants(LZ) > 1) return sched(std::integral_constant<int, 1>{});
+                    return cudaErrorInvalidValue;
+                }
+                return sched(std::integral_constant<int, 0>{});
             }
         }
         constexpr int TP = tp_z<LZ, T>(), NTH = 3 * TP * ZPlan<LZ>::NT;
@@ -953,7 +1056,9 @@ template <typename T> struct LaunchX {
         PROF_END(KK_ZCONV_C64 + koff, R, st);
         return cudaGetLastError();
     }
-    template <int LZ> static int zvariants() { return (sizeof(T) == 4 && zreg_ok<LZ>()) ? 3 : 1; }
+    template <int LZ> static int zvariants() {
+        return (sizeof(T) == 4 && zreg_ok<LZ>()) ? 1 + 2 * zr_variants(LZ) : 1;
+    }
 };
 
 // The lattice seen by the kernels is padded with vacuum to exactly L/2 sites
@@ -967,7 +1072,7 @@ cudaError_t launch_matvec_fused(const Geom& g, int R, cx<T>* x, cx<T>* y, const 
     if (g.nx * 2 != g.Lx || g.ny * 2 != g.Ly || g.nz * 2 != g.Lz) return cudaErrorInvalidValue;
     cudaError_t e;
     auto fwdx = [&]() -> cudaError_t {
-        DDA_DISPATCH_L(g.Lx, LX::template fwd, g, R, x, w.u1, tg.site_of, tw.x, active, fk, st);
+        DDA_DISPATCH_L(g.Lx, LX::template fwd, g, R, x, w.u1, tg.site_of, tw.x, active, fk, w.xfwd, st);
     };
     auto ys = [&](int mode, const cx<T>* s, cx<T>* d, int64_t sb, int64_t db) -> cudaError_t {
         DDA_DISPATCH_L(g.Ly, LX::template strided, mode, s, d, (int64_t)g.Lx, g.Lx, sb, db, R * 3 * g.nz, 3 * g.nz,
@@ -978,7 +1083,7 @@ cudaError_t launch_matvec_fused(const Geom& g, int R, cx<T>* x, cx<T>* y, const 
     };
     auto invx = [&]() -> cudaError_t {
         DDA_DISPATCH_L(g.Lx, LX::template inv, g, R, w.u1, y, x, tg, beta, beta_stride, w.beta_tensor, tw.x, active,
-                       fk, st);
+                       fk, w.xinv, st);
     };
     if (w.slices && !w.beta_tensor && slice_passes<T>(g)) {
         if ((e = launch_slice_fwd<T>(g, R, x, w.u2, tg.site_of, tw, active, fk, st)) != cudaSuccess) return e;
@@ -1005,6 +1110,24 @@ template <typename T> int zconv_schedules(const Geom& g) {
         case 384: return LaunchX<T>::template zvariants<384>();
         case 512: return LaunchX<T>::template zvariants<512>();
         default: return 0;
+    }
+}
+
+// Number of x-pass schedules: 0 staged rows (k_xfwd, k_xinv); for complex64
+// also 1 + V, the warp-local passes with radix plan variant V (xwarp.cuh).
+template <typename T> int xpass_schedules(const Geom& g) {
+    switch (g.Lx) {
+        case 16: return LaunchX<T>::template xvariants<16>();
+        case 32: return LaunchX<T>::template xvariants<32>();
+        case 48: return LaunchX<T>::template xvariants<48>();
+        case 64: return LaunchX<T>::template xvariants<64>();
+        case 96: return LaunchX<T>::template xvariants<96>();
+        case 128: return LaunchX<T>::template xvariants<128>();
+        case 192: return LaunchX<T>::template xvariants<192>();
+        case 256: return LaunchX<T>::template xvariants<256>();
+        case 384: return LaunchX<T>::template xvariants<384>();
+        case 512: return LaunchX<T>::template xvariants<512>();
+        default: return 1;
     }
 }
 

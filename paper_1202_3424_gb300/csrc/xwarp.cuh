@@ -1,0 +1,303 @@
+// x passes of the FFT-convolution matvec with warp-local pencils (complex64).
+//
+// The x passes transform rows of the padded lattice, which are contiguous in
+// both of their buffers: U1 rows [nz][ny][Lx], and the compact site vectors,
+// where the occupied sites of one lattice row have consecutive indices.  So a
+// row can be held by NT <= 32 consecutive lanes of one warp and read and
+// written straight from and to global memory in the layout of the first and
+// last radix stage (lane u holds positions u + q NT + j L/R, which are
+// consecutive across the lanes): the loads and the scatter coalesce without
+// staging the rows in shared memory, and the exchanges between radix stages
+// need only warp barriers.  Each pencil has its own exchange plane; the
+// exchange after stage S stores and loads position pos at the slot
+// pos ^ ((pos >> K) & 15), with K chosen per exchange by the shared-memory
+// bank model (paper_1202_3424_gb300/bank_model.py, --warp) so that both the
+// stride patterns of the stores and the consecutive loads keep every bank to
+// one word per wavefront.
+//
+// Radix plans: variant 0 is the plan of the staged x passes; variant 1, where
+// it exists, trades registers for fewer exchanges (radix 16 or radix 8 with
+// more points per lane).  The context times the variants inside whole
+// matvecs and keeps the fastest (see pick_schedule in abi.cu).
+#pragma once
+
+#include "fft.cuh"
+#include "krylov_dev.cuh"
+
+namespace dda {
+
+template <int L, int V> struct XwPlan;
+template <> struct XwPlan<16, 0> : PlanDef<16, 4, 4, 4> {};
+template <> struct XwPlan<32, 0> : PlanDef<32, 4, 4, 8> {};
+template <> struct XwPlan<48, 0> : PlanDef<48, 4, 4, 4, 3> {};
+template <> struct XwPlan<64, 0> : PlanDef<64, 8, 8, 8> {};
+template <> struct XwPlan<96, 0> : PlanDef<96, 8, 4, 4, 3, 2> {};
+template <> struct XwPlan<128, 0> : PlanDef<128, 16, 4, 4, 8> {};
+template <> struct XwPlan<128, 1> : PlanDef<128, 8, 8, 16> {};
+template <> struct XwPlan<192, 0> : PlanDef<192, 16, 4, 4, 4, 3> {};
+template <> struct XwPlan<192, 1> : PlanDef<192, 8, 8, 8, 3> {};
+template <> struct XwPlan<256, 0> : PlanDef<256, 32, 4, 8, 8> {};
+template <> struct XwPlan<256, 1> : PlanDef<256, 16, 16, 16> {};
+template <> struct XwPlan<384, 0> : PlanDef<384, 32, 4, 4, 4, 3, 2> {};
+template <> struct XwPlan<512, 0> : PlanDef<512, 32, 8, 8, 8> {};
+
+// Number of plan variants per length.
+__host__ __device__ constexpr int xw_variants(int L) { return (L == 128 || L == 192 || L == 256) ? 2 : 1; }
+
+// Exchange-plane swizzle key K of the exchange after stage S (0: none).
+__host__ __device__ constexpr int warp_swizzle_key(int L, int NT, int DIR, int S) {
+    // (table of bank_model.py --warp)
+    if (L == 16 && NT == 4 && DIR == -1 && S == 0) return 1;
+    if (L == 16 && NT == 4 && DIR == 1 && S == 0) return 1;
+    if (L == 32 && NT == 4 && DIR == -1 && S == 0) return 1;
+    if (L == 32 && NT == 4 && DIR == 1 && S == 0) return 2;
+    if (L == 48 && NT == 4 && DIR == -1 && S == 0) return 1;
+    if (L == 64 && NT == 8 && DIR == -1 && S == 0) return 3;
+    if (L == 64 && NT == 8 && DIR == 1 && S == 0) return 3;
+    if (L == 96 && NT == 8 && DIR == -1 && S == 0) return 2;
+    if (L == 96 && NT == 8 && DIR == -1 && S == 1) return 2;
+    if (L == 96 && NT == 8 && DIR == 1 && S == 0) return 1;
+    if (L == 96 && NT == 8 && DIR == 1 && S == 2) return 3;
+    if (L == 128 && NT == 8 && DIR == -1 && S == 0) return 3;
+    if (L == 128 && NT == 8 && DIR == 1 && S == 0) return 4;
+    if (L == 128 && NT == 16 && DIR == -1 && S == 0) return 2;
+    if (L == 128 && NT == 16 && DIR == -1 && S == 1) return 2;
+    if (L == 128 && NT == 16 && DIR == 1 && S == 0) return 3;
+    if (L == 128 && NT == 16 && DIR == 1 && S == 1) return 2;
+    if (L == 192 && NT == 8 && DIR == -1 && S == 0) return 3;
+    if (L == 192 && NT == 8 && DIR == 1 && S == 1) return 2;
+    if (L == 192 && NT == 16 && DIR == -1 && S == 0) return 2;
+    if (L == 192 && NT == 16 && DIR == -1 && S == 1) return 2;
+    if (L == 192 && NT == 16 && DIR == 1 && S == 2) return 3;
+    if (L == 256 && NT == 16 && DIR == -1 && S == 0) return 4;
+    if (L == 256 && NT == 16 && DIR == 1 && S == 0) return 4;
+    if (L == 256 && NT == 32 && DIR == -1 && S == 0) return 2;
+    if (L == 256 && NT == 32 && DIR == -1 && S == 1) return 3;
+    if (L == 256 && NT == 32 && DIR == 1 && S == 0) return 3;
+    if (L == 256 && NT == 32 && DIR == 1 && S == 1) return 3;
+    if (L == 384 && NT == 32 && DIR == -1 && S == 0) return 2;
+    if (L == 384 && NT == 32 && DIR == -1 && S == 1) return 2;
+    if (L == 384 && NT == 32 && DIR == 1 && S == 0) return 1;
+    if (L == 384 && NT == 32 && DIR == 1 && S == 3) return 3;
+    if (L == 512 && NT == 32 && DIR == -1 && S == 0) return 3;
+    if (L == 512 && NT == 32 && DIR == -1 && S == 1) return 3;
+    if (L == 512 && NT == 32 && DIR == 1 && S == 0) return 3;
+    if (L == 512 && NT == 32 && DIR == 1 && S == 1) return 3;
+    return 0;
+}
+// Plane padding (elements) per pencil width: with NT < 16 several pencils
+// share a half-warp, and the padding puts their planes on different banks.
+__host__ __device__ constexpr int warp_plane_pad(int NT) {
+    // (table of bank_model.py --warp)
+    if (NT == 4) return 8;
+    if (NT == 8) return 8;
+    if (NT == 16) return 0;
+    if (NT == 32) return 0;
+    return 0;
+}
+
+template <class PL> struct WarpSwz {
+    template <int DIR, int S> __device__ __forceinline__ static int map(int pos) {
+        constexpr int K = warp_swizzle_key(PL::L, PL::NT, DIR, S);
+        if constexpr (K == 0) return pos;
+        else return pos ^ ((pos >> K) & 15);
+    }
+};
+
+constexpr int kXwThreads = 256;
+template <class PL> __host__ __device__ constexpr int xw_rows() { return kXwThreads / PL::NT; }
+template <class PL> __host__ __device__ constexpr int xw_plane() { return PL::L + warp_plane_pad(PL::NT); }
+// exchange planes of the block's rows, then the twiddle table
+template <class PL> __host__ __device__ constexpr size_t xw_smem() {
+    return ((size_t)xw_rows<PL>() * xw_plane<PL>() + (PL::L <= 256 ? PL::L : 0)) * sizeof(float2);
+}
+// register budgets (blocks per SM): 64 per thread up to 8 points per lane,
+// then 85, then 128; the inverse keeps its diagonal operands in registers and
+// takes the larger budget above 12 points per lane
+template <class PL> __host__ __device__ constexpr int xwf_min_blocks() { return PL::E <= 8 ? 4 : (PL::E <= 16 ? 3 : 2); }
+template <class PL> __host__ __device__ constexpr int xwi_min_blocks() { return PL::E <= 8 ? 4 : (PL::E <= 12 ? 3 : 2); }
+
+// Up to 256 points the block copies the twiddle table to shared memory
+// (after its global loads are issued): the stage twiddles of different lanes
+// then cost shared wavefronts, not one L1 request per cache line they touch
+// (measured: 192-point rows 2-5 % faster).  The 512-point rows read the
+// table from global memory: there the block barrier of the copy cost 15 %.
+template <int L> __host__ __device__ constexpr bool xw_shared_twiddles() { return L <= 256; }
+template <int L> __device__ __forceinline__ const float2* stage_twiddles(float2* tws, const float2* __restrict__ tw) {
+    if constexpr (!xw_shared_twiddles<L>()) return tw;
+    for (int e = threadIdx.x; e < L; e += kXwThreads) tws[e] = tw[e];
+    __syncthreads();
+    return tws;
+}
+
+// ---- x-forward: gather + row FFT, warp-local pencils -------------------------------
+// Same result as k_xfwd: rows (iy, iz) of the padded-to-LX/2 lattice, sites
+// x < LX/2 gathered through the lattice -> site map; MODE 1 and 2 form the
+// BiCGstab update in the gather and write it back to X.
+template <int LX, int V, int MODE>
+__global__ void __launch_bounds__(kXwThreads, xwf_min_blocks<XwPlan<LX, V>>())
+    k_xfwd_w(float2* __restrict__ X, float2* __restrict__ U1, const int* __restrict__ site_of, int nrows, int64_t N,
+             const float2* __restrict__ tw, const int* __restrict__ active, const float2* __restrict__ kr,
+             const float2* __restrict__ kv, const KState* __restrict__ st) {
+    using C = float2;
+    using PL = XwPlan<LX, V>;
+    constexpr int NT = PL::NT, E = PL::E, NX = LX / 2, RPB = xw_rows<PL>(), PS = xw_plane<PL>();
+    constexpr int R0 = stage_radix<PL, -1>(0), NB0 = E / R0, JN = R0 / 2;  // half-zero first stage
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int c = blockIdx.y, r = blockIdx.z;
+    if (active != nullptr && active[r] == 0) return;
+    const int p = threadIdx.x / NT, u = threadIdx.x % NT;
+    const int row = blockIdx.x * RPB + p;
+    const bool ok = row < nrows;
+    C* plane = reinterpret_cast<C*>(smem_raw) + p * PS;
+    const int64_t off = ((int64_t)r * 3 + c) * N;
+    C* xs = X + off;
+    C ka = czero<C>(), kb = czero<C>();
+    if constexpr (MODE == 1) {
+        ka = from2<C>(st[r].beta);
+        kb = from2<C>(st[r].omega);
+    } else if constexpr (MODE == 2) {
+        ka = from2<C>(st[r].alpha);
+    }
+    // site indices of the first stage's inputs (positions < LX/2), then the
+    // values: all loads of the lane are in flight before the first is used
+    int sidx[NB0 * JN];
+#pragma unroll
+    for (int q = 0; q < NB0; ++q)
+#pragma unroll
+        for (int j = 0; j < JN; ++j)
+            sidx[q * JN + j] = ok ? site_of[(int64_t)row * NX + u + q * NT + j * (LX / R0)] : -1;
+    C v[E];
+#pragma unroll
+    for (int q = 0; q < NB0; ++q)
+#pragma unroll
+        for (int j = 0; j < JN; ++j) {
+            const int s = sidx[q * JN + j];
+            C val = czero<C>();
+            if (s >= 0) {
+                if constexpr (MODE == 0) val = xs[s];
+                else if constexpr (MODE == 1) val = cadd(kr[off + s], cmul(ka, csub(xs[s], cmul(kb, kv[off + s]))));
+                else val = csub(kr[off + s], cmul(ka, kv[off + s]));
+            }
+            v[q * R0 + j] = val;
+        }
+    if constexpr (MODE != 0) {
+#pragma unroll
+        for (int q = 0; q < NB0; ++q)
+#pragma unroll
+            for (int j = 0; j < JN; ++j)
+                if (sidx[q * JN + j] >= 0) xs[sidx[q * JN + j]] = v[q * R0 + j];
+    }
+    const C* tws = stage_twiddles<LX>(reinterpret_cast<C*>(smem_raw) + RPB * PS, tw);
+    auto ld = [&](int pos) { return plane[pos]; };
+    auto stf = [&](int pos, C val) { plane[pos] = val; };
+    fft_stages<C, PL, -1, 0, decltype(ld), decltype(stf), true, WarpSwz<PL>>(v, u, tws, ld, stf, true);
+    C* out = U1 + ((int64_t)r * 3 + c) * (int64_t)nrows * LX + (int64_t)row * LX;
+    for_each_out<PL, -1, false>(u, [&](int idx, int pos) {
+        if (ok) out[pos] = v[idx];
+    });
+}
+
+// ---- x-inverse: row IFFT + diagonal + scatter, warp-local pencils --------------
+// Same result as k_xinv (Y = conv + (1/alpha) X at the occupied sites, the
+// TENSOR form, and the fused BiCGstab reductions of MODE 1 and 2).
+template <int LX, int V, int MODE, bool TENSOR>
+__global__ void __launch_bounds__(kXwThreads, xwi_min_blocks<XwPlan<LX, V>>())
+    k_xinv_w(const float2* __restrict__ U1, float2* __restrict__ Y, const float2* __restrict__ X,
+             const int* __restrict__ site_of, const uint8_t* __restrict__ comp_of, const float2* __restrict__ beta,
+             int beta_stride, int nrows, int64_t N, const float2* __restrict__ tw, int* __restrict__ active,
+             const float2* __restrict__ krhat, KState* __restrict__ st, double2* __restrict__ part,
+             unsigned* __restrict__ cnt, int part_stride) {
+    using C = float2;
+    using PL = XwPlan<LX, V>;
+    constexpr int NT = PL::NT, E = PL::E, NX = LX / 2, RPB = xw_rows<PL>(), PS = xw_plane<PL>();
+    constexpr int R0 = stage_radix<PL, +1>(0), NB0 = E / R0;
+    constexpr int RL = stage_radix<PL, +1>(PL::NS - 1), NBL = E / RL, MN = RL / 2, NO = NBL * MN;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int c = blockIdx.y, r = blockIdx.z;
+    if (active != nullptr && active[r] == 0) return;
+    const int p = threadIdx.x / NT, u = threadIdx.x % NT;
+    const int row = blockIdx.x * RPB + p;
+    const bool ok = row < nrows;
+    C* plane = reinterpret_cast<C*>(smem_raw) + p * PS;
+    const int64_t off = ((int64_t)r * 3 + c) * N;
+    const C* xs = X + off;
+    C* ys = Y + off;
+    const C* br = beta + (int64_t)r * beta_stride + (TENSOR ? c * (beta_stride / 3) : 0);
+    const C* in = U1 + ((int64_t)r * 3 + c) * (int64_t)nrows * LX + (int64_t)row * LX;
+    // the row in the first stage's layout, then the site indices of the
+    // lattice-half outputs and (up to 12 points per lane) the diagonal
+    // operands: their latency is hidden by the transform
+    C v[E];
+#pragma unroll
+    for (int q = 0; q < NB0; ++q)
+#pragma unroll
+        for (int j = 0; j < R0; ++j) v[q * R0 + j] = ok ? in[u + q * NT + j * (LX / R0)] : czero<C>();
+    int sidx[NO];
+#pragma unroll
+    for (int q = 0; q < NBL; ++q)
+#pragma unroll
+        for (int m = 0; m < MN; ++m)
+            sidx[q * MN + m] = ok ? site_of[(int64_t)row * NX + u + q * NT + m * (LX / RL)] : -1;
+    // (with 16 or more points per lane the transform needs those registers:
+    // the operands are then loaded after it)
+    constexpr bool kHoist = E <= 12;
+    C xv[NO], bv[NO];
+    C kh[MODE == 1 ? NO : 1];
+    auto load_operands = [&]() {
+#pragma unroll
+        for (int k = 0; k < NO; ++k) {
+            const int s = sidx[k];
+            xv[k] = czero<C>();
+            bv[k] = czero<C>();
+            if constexpr (MODE == 1) kh[k] = czero<C>();
+            if (s >= 0) {
+                xv[k] = xs[s];
+                bv[k] = TENSOR ? br[table_index(comp_of, s) * 3 + c] : br[table_index(comp_of, s)];
+                if constexpr (MODE == 1) kh[k] = krhat[off + s];
+            }
+        }
+    };
+    if constexpr (kHoist) load_operands();
+    auto ld = [&](int pos) { return plane[pos]; };
+    auto stf = [&](int pos, C val) { plane[pos] = val; };
+    fft_stages<C, PL, +1, 0, decltype(ld), decltype(stf), true, WarpSwz<PL>>(v, u, tw, ld, stf, false);
+    if constexpr (!kHoist) load_operands();
+    DotAcc<C> d[2];
+#pragma unroll
+    for (int q = 0; q < NBL; ++q)
+#pragma unroll
+        for (int m = 0; m < MN; ++m) {
+            const int k = q * MN + m, s = sidx[k];
+            if (s >= 0) {
+                C yv = cadd(v[q * RL + m], cmul(bv[k], xv[k]));
+                if constexpr (TENSOR) {  // the two off-diagonal entries of row c
+                    const C* bb = br + table_index(comp_of, s) * 3;
+                    const int c1 = c == 0 ? 1 : 0, c2 = c == 2 ? 1 : 2;
+                    const C* xr = X + (int64_t)r * 3 * N;
+                    yv = cadd(yv, cadd(cmul(bb[c1], xr[c1 * N + s]), cmul(bb[c2], xr[c2 * N + s])));
+                }
+                ys[s] = yv;
+                if constexpr (MODE == 1) d[0].add_cdot(kh[k], yv);
+                if constexpr (MODE == 2) {
+                    d[0].add_cdot(yv, xv[k]);
+                    d[1].add_norm2(yv);
+                }
+            }
+        }
+    if constexpr (MODE != 0) {
+        constexpr int ND = MODE == 1 ? 1 : 2;
+        DotAcc<C> dd[ND];
+#pragma unroll
+        for (int k = 0; k < ND; ++k) dd[k] = d[k];
+        double2 acc[ND];
+        block_totals<C, ND>(dd, acc);
+        const int nb = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
+        if (last_block_combine<ND>(acc, part + (int64_t)r * part_stride, cnt + r, bid, nb) && threadIdx.x == 0) {
+            if constexpr (MODE == 1) finalize_alpha(st, active, r, acc[0]);
+            else finalize_omega(st, active, r, acc[0], acc[1].x);
+        }
+    }
+}
+
+}  // namespace dda

@@ -46,3 +46,34 @@ def test_padding_removes_the_narrow_tile_conflicts():
     assert a / i > 1.5
     a, i = bm.cost(512, NT, rad, 4, 3)
     assert a == i
+
+
+def test_warp_plans_are_valid_stockham_schedules():
+    """Every warp-local plan fits a warp, and every radix divides the points
+    per lane with NT dividing L/R (the stage layout's requirements)."""
+    for (L, V), (NT, rad) in bm.read_warp_plans().items():
+        E = L // NT
+        assert NT <= 32 and 32 % NT == 0 and L % NT == 0, (L, V)
+        prod = 1
+        for R in rad:
+            prod *= R
+            assert E % R == 0 and (L // R) % NT == 0, (L, V, R)
+        assert prod == L and rad[0] % 2 == 0, (L, V)
+
+
+def test_warp_swizzle_is_a_permutation_within_the_plane():
+    for key in range(1, 7):
+        for L in (64, 96, 128, 192, 256, 384, 512):
+            slots = {bm.warp_swizzle(p, key) for p in range(L)}
+            assert slots == set(range(L)), (L, key)
+
+
+def test_warp_header_tables_are_the_models_choice():
+    keys, pads, costs = bm.warp_table()
+    have, have_pads = bm.read_warp_table()
+    assert have == {k: v for k, v in keys.items() if v}
+    assert have_pads == pads
+    # the hot lengths reach the ideal wavefront count within 15 %
+    for (L, NT), (c, plain) in costs.items():
+        if L >= 64:
+            assert c <= 1.15, (L, NT, c)

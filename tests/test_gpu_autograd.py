@@ -98,3 +98,85 @@ def test_warm_start_and_normal_equation_error(env):
     assert st4 == 0 and res4[0]["iters"] < res[0]["iters"]
     assert np.abs(P4 - P).max() < 1e-8 * np.abs(P).max()
     ctx.close()
+
+
+def test_qabsfn_runs_the_adjoint_only_in_backward(env):
+    """The forward pass is one solve; the adjoint solve (target.grad) runs
+    when, and only when, the gradient is asked for."""
+    dda, torch, DipoleTarget, QabsFn = env
+    occ = ellipsoid_grid(6, 5, 4, 6, 5, 4).astype(bool)
+    N = int(occ.sum())
+    eps = np.full(N, 2.2 + 0.3j)
+    tgt = DipoleTarget(occ, 1.1, [1.0, 0.0, 0.0], np.array([0.0, 0.0, 1.0], complex), tol=1e-12)
+    calls = []
+    grad = tgt.grad
+    tgt.grad = lambda *a, **k: calls.append(1) or grad(*a, **k)
+    q0 = QabsFn.apply(torch.tensor(eps), tgt)                      # no gradient wanted
+    t = torch.tensor(eps, requires_grad=True)
+    q1 = QabsFn.apply(t, tgt)
+    assert calls == [] and abs(q0.item() - q1.item()) < 1e-12 * abs(q0.item())
+    q1.backward()
+    assert calls == [1] and torch.isfinite(t.grad).all()
+    tgt.close()
+
+
+def test_qabsfn_on_the_block_with_every_dipole_distinct(env):
+    """The 48x48x24 two-material block with a seeded perturbation of every
+    dipole's eps (55,296 distinct values, beyond any composition-code table):
+    QabsFn's gradient against central finite differences on 16 seeded dipoles
+    (h = 1e-4 |eps|, FP64 solves to 1e-12)."""
+    dda, torch, DipoleTarget, QabsFn = env
+    from dda_inputs import SEED_COMPOSITION, workload
+    w = workload("block48x48x24")
+    occ = w.grid > 0
+    N = int(occ.sum())
+    base = (np.asarray(w.m) ** 2)[w.grid[occ] - 1]
+    rng = np.random.default_rng(SEED_COMPOSITION + 1)
+    eps = base * (1.0 + 0.02 * (rng.random(N) - 0.5)) + 0.01j * rng.random(N)
+    assert np.unique(eps).size == N
+    tgt = DipoleTarget(occ, w.x, w.khat[0], w.ehat[0], tol=1e-12, maxit=3000)
+    t = torch.tensor(eps, requires_grad=True)
+    q = QabsFn.apply(t, tgt)
+    q.backward()
+    g = t.grad.numpy()
+    picks = np.random.default_rng(SEED_COMPOSITION).choice(N, 16, replace=False)
+    for j in picks:
+        for d in (1.0, 1j):
+            h = 1e-4 * abs(eps[j])
+            ep, em = eps.copy(), eps.copy()
+            ep[j] += d * h
+            em[j] -= d * h
+            fd = (tgt.qabs(ep)[0] - tgt.qabs(em)[0]) / (2 * h)
+            want = g[j].real if d == 1.0 else g[j].imag
+            assert abs(fd - want) <= 1e-3 * abs(want) + 1e-10 * abs(q.item()), (j, d, fd, want)
+    tgt.close()
+
+
+def test_site_materials_match_composition_codes(env):
+    """Per-site materials given the values of a composition table reproduce
+    the composition-code solve (same tables, other indexing)."""
+    dda, torch, DipoleTarget, QabsFn = env
+    grid = block_bernoulli_grid(9, 7, 5, seed=31)
+    m = [1.7 + 0.3j, 1.2 + 0.01j]
+    ctx = dda.Context(0)
+    ctx.set_target(grid)
+    ctx.set_materials(m)
+    ctx.prepare_size_parameter(1.5, dda.Precision.FP32_REFINED)
+    k = uniform_directions(3, 11)
+    e = polarization_pair(k)[1].astype(complex)
+    out = []
+    for site in (False, True):
+        if site:
+            ctx.set_site_materials(np.asarray(m)[grid[grid > 0] - 1])
+            ctx.prepare_size_parameter(1.5, dda.Precision.FP32_REFINED)
+        for prec in (0, 1):
+            res, P, st = ctx.solve(prec, k, e, tol=1e-9 if prec == 0 else 1e-6)
+            assert st == 0
+            out.append(np.array([[r["qext"], r["qabs"], r["qsca"]] for r in res]))
+    assert np.abs(out[0] - out[2]).max() < 1e-12 * np.abs(out[0]).max()
+    assert np.abs(out[1] - out[3]).max() < 1e-5 * np.abs(out[1]).max()
+    # a new target ends the per-site mode: materials must be given again
+    ctx.set_target(grid)
+    with pytest.raises(dda.DdaError):
+        ctx.prepare_size_parameter(1.5, dda.Precision.FP64)
+    ctx.close()

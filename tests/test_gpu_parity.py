@@ -85,20 +85,35 @@ def test_matvec_matches_pairwise_oracle(lib, name, gridf, m, x, prec, tol):
 
 
 REG_Z_LENGTHS = (16, 32, 64, 128, 256, 512)  # z plans with at most 8 points per thread
+Z_PLAN_VARIANTS = (128, 256)                  # lengths with a radix-16 plan (schedules 3, 4)
+Z_IDS = ["zgroups", "zregs", "zregs_octant", "zregs_radix16", "zregs_octant_radix16"]
 
 
-@pytest.mark.parametrize("name,gridf,m,x", MATVEC_CASES, ids=[c[0] for c in MATVEC_CASES])
-@pytest.mark.parametrize("zpass", [0, 1, 2], ids=["zgroups", "zregs", "zregs_octant"])
+def _z_expected(zpass, Lz):
+    if Lz not in REG_Z_LENGTHS:
+        return 0
+    return zpass if (zpass < 3 or Lz in Z_PLAN_VARIANTS) else zpass - 2
+
+
+Z_CASES = MATVEC_CASES + [
+    ("rod_z128_block_3x4x60", lambda: block_bernoulli_grid(3, 4, 60, seed=24), [1.5 + 0.1j, 1.25 + 0.02j], 2.0),
+    ("rod_z256_ellipsoid_6x5x110", lambda: ellipsoid_grid(6, 5, 110, 6, 5, 110), [1.4 + 0.05j], 2.5),
+]
+
+
+@pytest.mark.parametrize("name,gridf,m,x", Z_CASES, ids=[c[0] for c in Z_CASES])
+@pytest.mark.parametrize("zpass", [0, 1, 2, 3, 4], ids=Z_IDS)
 def test_matvec_z_schedules_match_oracle(lib, name, gridf, m, x, zpass):
     """The complex64 z-pass schedules against the pairwise oracle.  Nine RHS
     span full blocks of RHS and a ragged one; a grid whose z plan has no
-    register-resident schedule must fall back to schedule 0."""
+    register-resident schedule must fall back to schedule 0, and one with a
+    single radix plan from 3, 4 to 1, 2."""
     grid = gridf()
     ctx = _ctx(lib, grid, m, x, lib.Precision.FP32_REFINED)
     info = ctx.info()
     ctx.set_schedule(zpass)
     R = 9
-    assert ctx.get_schedule(R) == (zpass if info["Lz"] in REG_Z_LENGTHS else 0)
+    assert ctx.get_schedule(R) == _z_expected(zpass, info["Lz"])
     kd = info["kd"]
     khat, ehat = _rhs_set(R)
     X = random_complex((R, 3, info["ndipoles"]), 12)
@@ -110,7 +125,7 @@ def test_matvec_z_schedules_match_oracle(lib, name, gridf, m, x, zpass):
     ctx.close()
 
 
-@pytest.mark.parametrize("zpass", [0, 1, 2], ids=["zgroups", "zregs", "zregs_octant"])
+@pytest.mark.parametrize("zpass", [0, 1, 2, 3, 4], ids=Z_IDS)
 def test_matvec_long_z_columns_many_rhs(lib, zpass):
     """A 4x5x100 rod (256-point z transform, where the register schedules
     take 16 or, with octant columns, 4 RHS per block) with 18 RHS: full blocks
@@ -132,6 +147,99 @@ def test_matvec_long_z_columns_many_rhs(lib, zpass):
     ctx.close()
 
 
+# Rows of the hot x lengths (Lx = 128, 192, 256, 512): full, ragged and
+# two-material rows, every x-pass schedule (0 staged rows, 1 and 2 the
+# warp-local rows with radix plan variants 0 and 1).
+X_CASES = [
+    ("rows128_block_64x6x4", lambda: block_bernoulli_grid(64, 6, 4, seed=21), [1.6 + 0.1j, 1.3 + 0.02j], 2.0),
+    ("rows192_ellipsoid_90x7x5", lambda: ellipsoid_grid(90, 7, 5, 90, 7, 5), [1.5 + 0.05j], 3.0),
+    ("rows256_block_120x3x3", lambda: block_bernoulli_grid(120, 3, 3, seed=22), [1.4 + 0.2j, 2.0 + 0.5j], 2.5),
+    ("rows512_rod_200x2x2", lambda: np.ones((2, 2, 200), np.uint8), [1.33 + 0.01j], 2.0),
+    ("rows64_plate_25x25x3", MATVEC_CASES[5][1], MATVEC_CASES[5][2], MATVEC_CASES[5][3]),
+    ("rows32_ellipsoid_ragged", MATVEC_CASES[2][1], MATVEC_CASES[2][2], MATVEC_CASES[2][3]),
+]
+X_VARIANTS = {128: 2, 192: 2, 256: 2}   # radix plan variants of the warp-local rows
+
+
+@pytest.mark.parametrize("name,gridf,m,x", X_CASES, ids=[c[0] for c in X_CASES])
+@pytest.mark.parametrize("xpass", [0, 1, 2], ids=["xstaged", "xwarp_plan0", "xwarp_plan1"])
+def test_matvec_x_schedules_match_oracle(lib, name, gridf, m, x, xpass):
+    """The complex64 x-pass schedules against the pairwise oracle, isotropic
+    and with tilted biaxial materials (the tensor 1/alpha of the x-inverse)."""
+    grid = gridf()
+    ctx = _ctx(lib, grid, m, x, lib.Precision.FP32_REFINED)
+    info = ctx.info()
+    ctx.set_xpass(xpass)
+    R = 5
+    nvar = X_VARIANTS.get(info["Lx"], 1)
+    assert ctx.get_xpass(R) == (min(xpass, nvar),) * 2
+    kd = info["kd"]
+    khat, ehat = _rhs_set(R)
+    X = random_complex((R, 3, info["ndipoles"]), 14)
+    Y = ctx.matvec(2, khat, ehat, X)
+    for r in range(R):
+        rr, beta = _site_beta(grid, m, kd, khat[r], ehat[r])
+        want, _ = pairwise.matvec(rr, kd, beta, X[r].T)
+        assert _rel(Y[r].T, want) < F32_TOL, (name, xpass, r)
+    # tensor polarizabilities: same schedule, against the oracle's tensor matvec
+    m3 = [[mm * f for f in (1.0, 1.06, 0.94)] for mm in m]
+    ang = [(0.3 + 0.2 * i, 1.0, -0.5) for i in range(len(m))]
+    ctx.set_anisotropic_materials(m3, ang)
+    ctx.prepare_size_parameter(x, lib.Precision.FP32_REFINED)
+    ctx.set_xpass(xpass)
+    Y = ctx.matvec(2, khat, ehat, X)
+    rr, comp = odda.site_positions(grid)
+    for r in (0, R - 1):
+        bt = np.stack([odda.ldr_inverse_tensor(np.asarray(m3[c - 1]) ** 2, ang[c - 1], kd, khat[r], ehat[r])
+                       for c in comp])
+        # the C oracle sums the interaction part (scalar diagonal 0); the tensor diagonal is added here
+        off, _ = pairwise.matvec(rr, kd, np.zeros(len(rr), complex), X[r].T)
+        want = off + np.einsum("nab,nb->na", bt, X[r].T)
+        assert _rel(Y[r].T, want) < F32_TOL, (name, xpass, "tensor", r)
+    ctx.close()
+
+
+@pytest.mark.parametrize("xpass", [0, 1, 2], ids=["xstaged", "xwarp_plan0", "xwarp_plan1"])
+def test_refined_solve_through_each_x_schedule(lib, xpass):
+    """The BiCGstab updates fused into the x passes (gather and scatter modes
+    1 and 2, with their reductions) under each x schedule: a FP32-refined
+    solve of a 64x6x4 two-material block (128-point rows) reaches the FP64
+    solution's efficiencies."""
+    grid = block_bernoulli_grid(64, 6, 4, seed=23)
+    m = [1.6 + 0.1j, 1.3 + 0.02j]
+    ctx = _ctx(lib, grid, m, 2.0, lib.Precision.FP32_REFINED)
+    k, e = _rhs_set(3)
+    ref, _, st = ctx.solve(lib.Precision.FP64, k, e, want_P=False, tol=1e-10, maxit=2000)
+    assert st == 0
+    ctx.set_xpass(xpass)
+    res, _, st = ctx.solve(lib.Precision.FP32_REFINED, k, e, want_P=False, tol=1e-6, maxit=2000)
+    assert st == 0 and max(r["resid_rel"] for r in res) <= 1e-6
+    q = np.array([[r["qext"], r["qabs"], r["qsca"]] for r in res])
+    q0 = np.array([[r["qext"], r["qabs"], r["qsca"]] for r in ref])
+    assert np.abs(q - q0).max() < 1e-5 * np.abs(q0).max(), (xpass, q, q0)
+    ctx.close()
+
+
+@pytest.mark.parametrize("zpass", [1, 2, 3, 4], ids=Z_IDS[1:])
+def test_refined_solve_through_each_z_schedule(lib, zpass):
+    """A FP32-refined solve of a 5x4x60 two-material rod (128-point z
+    transform) under each register z schedule reaches the FP64 solution's
+    efficiencies (the solve's matvecs carry the fused BiCGstab updates)."""
+    grid = block_bernoulli_grid(5, 4, 60, seed=25)
+    m = [1.6 + 0.1j, 1.3 + 0.02j]
+    ctx = _ctx(lib, grid, m, 2.5, lib.Precision.FP32_REFINED)
+    k, e = _rhs_set(3)
+    ref, _, st = ctx.solve(lib.Precision.FP64, k, e, want_P=False, tol=1e-10, maxit=2000)
+    assert st == 0
+    ctx.set_schedule(zpass)
+    res, _, st = ctx.solve(lib.Precision.FP32_REFINED, k, e, want_P=False, tol=1e-6, maxit=2000)
+    assert st == 0 and max(r["resid_rel"] for r in res) <= 1e-6
+    q = np.array([[r["qext"], r["qabs"], r["qsca"]] for r in res])
+    q0 = np.array([[r["qext"], r["qabs"], r["qsca"]] for r in ref])
+    assert np.abs(q - q0).max() < 1e-5 * np.abs(q0).max(), (zpass, q, q0)
+    ctx.close()
+
+
 def test_autotuned_schedule_reproduces_forced_one(lib):
     """The autotuner picks a z schedule and a slice-pass setting; the matvec
     it runs is bit-identical to forcing that choice."""
@@ -141,16 +249,21 @@ def test_autotuned_schedule_reproduces_forced_one(lib):
     ctx.set_schedule(-1)
     ctx.set_slice_passes(-1)
     zpick, spick = ctx.get_schedule(R, with_slices=True)
-    assert zpick in (0, 1, 2) and spick in (0, 1)
+    xpick = ctx.get_xpass(R)
+    assert zpick in (0, 1, 2, 3, 4) and spick in (0, 1) and all(v in (0, 1, 2) for v in xpick)
     X = random_complex((R, 3, ctx.info()["ndipoles"]), 4).astype(np.complex64)
     k, e = np.resize(w.khat, (R, 3)), np.resize(w.ehat, (R, 3))
     y_auto = ctx.matvec(2, k, e, X)
     ctx.set_schedule(zpick)
     ctx.set_slice_passes(spick)
+    ctx.set_xpass(xpick)
+    assert ctx.get_xpass(R) == xpick
     y_forced = ctx.matvec(2, k, e, X)
     assert np.array_equal(y_auto, y_forced)
     with pytest.raises(lib.DdaError):
-        ctx.set_schedule(3)
+        ctx.set_schedule(5)
+    with pytest.raises(lib.DdaError):
+        ctx.set_xpass(3)
     ctx.close()
 
 
@@ -183,13 +296,16 @@ def test_matvec_row_samples_full_size(lib, name):
     for r in range(R):
         rr, beta = _site_beta(w.grid, w.m, kd, w.khat[r], w.ehat[r])
         want.append(pairwise.matvec(rr, kd, beta, X[r].T, rows=rows)[0])
-    for prec, tol, zpass, slices in ((0, F64_TOL, -1, 1), (0, F64_TOL, -1, 0), (3, F64_TOL, -1, 1),
-                                     (2, F32_TOL, 0, 1), (2, F32_TOL, 1, 1), (2, F32_TOL, 1, 0), (2, F32_TOL, 2, 0)):
+    for prec, tol, zpass, slices, xpass in ((0, F64_TOL, -1, 1, -1), (0, F64_TOL, -1, 0, -1), (3, F64_TOL, -1, 1, -1),
+                                            (2, F32_TOL, 0, 1, 0), (2, F32_TOL, 1, 1, 0), (2, F32_TOL, 1, 0, 0),
+                                            (2, F32_TOL, 2, 0, 0), (2, F32_TOL, 2, 0, 1), (2, F32_TOL, 1, 0, 2),
+                                            (2, F32_TOL, 3, 0, 1), (2, F32_TOL, 4, 0, 2)):
         ctx.set_schedule(zpass)
         ctx.set_slice_passes(slices)
+        ctx.set_xpass(xpass)
         Y = ctx.matvec(prec, w.khat[:R], w.ehat[:R], X)
         for r in range(R):
-            assert _rel(Y[r].T[rows], want[r]) < tol, (name, prec, zpass, slices, r)
+            assert _rel(Y[r].T[rows], want[r]) < tol, (name, prec, zpass, slices, xpass, r)
     ctx.close()
 
 
@@ -223,6 +339,7 @@ def test_matvec_row_samples_sphere256(lib, zpass):
     w = workload("sphere256")
     ctx = _ctx(lib, w.grid, w.m, w.x, lib.Precision.FP32_REFINED)
     ctx.set_schedule(zpass)
+    ctx.set_xpass(zpass % 2)   # the 512-point rows: staged and warp-local
     kd = ctx.info()["kd"]
     N = ctx.info()["ndipoles"]
     R = 3

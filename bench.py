@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--xpass", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="complex64 x-pass schedule: -1 autotuned (default), 0 rows staged through shared memory, "
                          "1 + V warp-local rows with radix plan V")
+    ap.add_argument("--xinv", type=int, default=None, choices=[-1, 0, 1, 2],
+                    help="x-inverse schedule (overrides --xpass for the inverse pass only)")
     ap.add_argument("--zpass", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4],
                     help="complex64 z-pass schedule: -1 autotuned (default), 0 component groups, "
                          "1 register-resident, 2 register-resident with octant columns, 3 and 4 as 1 and 2 "
@@ -214,11 +216,11 @@ def pass_flops(kind, info, R):
 
 KERNEL_SOURCES = ["paper_1202_3424_gb300/csrc/matvec_impl.cuh", "paper_1202_3424_gb300/csrc/matvec_f32.cu",
                   "paper_1202_3424_gb300/csrc/fft.cuh", "paper_1202_3424_gb300/csrc/krylov_dev.cuh",
-                  "paper_1202_3424_gb300/csrc/common.cuh"]
+                  "paper_1202_3424_gb300/csrc/common.cuh", "paper_1202_3424_gb300/csrc/xwarp.cuh"]
 # (pass, workload, RHS per launch) -> (summary file, kernel heading in it)
-CAPTURES = {("z_conv_c64", "sphere64", 2): ("profiles/zoct_f32_sphere64.md", "k_zconv_oct<float, 128, 2>"),
+CAPTURES = {("z_conv_c64", "sphere64", 2): ("profiles/zoct16_f32_sphere64.md", "k_zconv_oct<float, 128, 2, 1>"),
             ("z_conv_c64", "ellipsoid96x64x32", 32): ("profiles/passes_f32_ellipsoid96x64x32.md",
-                                                      "k_zconv_reg<float, 64, 8>")}
+                                                      "k_zconv_reg<float, 64, 8, 0>")}
 
 
 def captured_traffic(kernel, workload_name, rhs_per_launch):
@@ -288,7 +290,7 @@ def run_gb300(args):
     ctx.prepare_size_parameter(w.x, dda.Precision.FP32_REFINED)
     prepare_ms = (time.perf_counter() - t0) * 1e3
     ctx.set_schedule(args.zpass)
-    ctx.set_xpass(args.xpass)
+    ctx.set_xpass((args.xpass, args.xpass if args.xinv is None else args.xinv))
     info = ctx.info()
     N = info["ndipoles"]
     P_dev = torch.empty((R, 3, N), dtype=torch.complex128, device=dev)
@@ -744,7 +746,7 @@ def run_matvec_only(args):
     set_materials(ctx, w, args.aniso)
     ctx.prepare_size_parameter(w.x, dda.Precision.FP32_REFINED)
     ctx.set_schedule(args.zpass)
-    ctx.set_xpass(args.xpass)
+    ctx.set_xpass((args.xpass, args.xpass if args.xinv is None else args.xinv))
     N = ctx.info()["ndipoles"]
     k = np.resize(w.khat, (R, 3))
     e = np.resize(w.ehat, (R, 3))

@@ -103,4 +103,16 @@ __device__ __forceinline__ int table_index(const uint8_t* __restrict__ comp_of, 
     return comp_of != nullptr ? (int)comp_of[s] : (int)(s + 1);
 }
 
+// How the x-inverse pass finds a site's 1/alpha (a template parameter of its
+// kernels): the scalar of the site's composition, row c of its composition's
+// tensor, or the scalar of the site itself (per-site materials).
+enum { kDiagComp = 0, kDiagTensor = 1, kDiagSite = 2 };
+template <int DIAG, typename C>
+__device__ __forceinline__ C diag_entry(const C* __restrict__ br, const uint8_t* __restrict__ comp_of, int64_t s,
+                                        int c) {
+    if constexpr (DIAG == kDiagTensor) return br[comp_of[s] * 3 + c];
+    else if constexpr (DIAG == kDiagSite) return br[s + 1];
+    else return br[comp_of[s]];
+}
+
 }  // namespace dda

@@ -21,9 +21,13 @@ int pick_fft_length(int n) {
 }
 
 // Blocks of one RHS in the x-inverse pass (partial-sum slots per RHS): the
-// larger of the complex64 and 16-byte element tilings.
+// most among the staged tilings of complex64 and 16-byte elements and the
+// warp-local blocks of every plan variant.
 template <int L> static int min_tp_x() {
-    return tp_x<L, 8>() < tp_x<L, 16>() ? tp_x<L, 8>() : tp_x<L, 16>();
+    int tp = tp_x<L, 8>() < tp_x<L, 16>() ? tp_x<L, 8>() : tp_x<L, 16>();
+    tp = xwi_rows<XwPlan<L, 0>>() < tp ? xwi_rows<XwPlan<L, 0>>() : tp;
+    if constexpr (xw_variants(L) > 1) tp = xwi_rows<XwPlan<L, 1>>() < tp ? xwi_rows<XwPlan<L, 1>>() : tp;
+    return tp;
 }
 int xinv_blocks_per_rhs(const Geom& g) {
     const int nrows = g.ny * g.nz;

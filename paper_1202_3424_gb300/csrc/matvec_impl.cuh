@@ -190,14 +190,17 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
 }
 
 // ---- x-inverse: row IFFT + diagonal + scatter -----------------------------------
-// Y = conv + (1/alpha) X at the occupied sites.  With TENSOR the block of
-// component c adds row c of the site's 1/alpha tensor times all three
-// components of X (layout in PadWork::beta_tensor); a separate instantiation
-// so that the isotropic kernel keeps its registers.  Fused BiCGstab reductions
+// Y = conv + (1/alpha) X at the occupied sites.  DIAG says how a site finds
+// its 1/alpha (each kind its own instantiation, so that the common one keeps
+// its registers and its load chain):
+//   kDiagComp    the scalar of its composition code;
+//   kDiagTensor  row c of its composition's tensor, times all three
+//                components of X (layout in PadWork::beta_tensor);
+//   kDiagSite    the scalar of site s itself, entry s + 1 (per-site materials).  Fused BiCGstab reductions
 // (FP64 totals per RHS over all blocks of that RHS, finalized by the last one):
 //   MODE 1  Y = v:  sigma = <rhat, v>          ->  alpha = rho / sigma
 //   MODE 2  Y = t:  <t, s>, <t, t> with X = s  ->  omega
-template <typename T, int LX, int MODE, bool TENSOR>
+template <typename T, int LX, int MODE, int DIAG>
 __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(cx<T>)>::NT,
                                    xinv_min_blocks<LX, sizeof(cx<T>)>())
     k_xinv(const cx<T>* __restrict__ U1, cx<T>* __restrict__ Y, const cx<T>* __restrict__ X,
@@ -217,6 +220,7 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
     const int64_t off = ((int64_t)r * 3 + c) * N;
     const C* xs = X + off;
     C* ys = Y + off;
+    constexpr bool TENSOR = DIAG == kDiagTensor;
     const C* br = beta + (int64_t)r * beta_stride + (TENSOR ? c * (beta_stride / 3) : 0);
     // All global loads are issued up front: the rows to transform, then the
     // site indices and, behind them, the operands of the diagonal term, whose
@@ -255,7 +259,7 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
             if constexpr (MODE == 1) kh[i] = czero<C>();
             if (s >= 0) {
                 xv[i] = xs[s];
-                bv[i] = TENSOR ? br[table_index(comp_of, s) * 3 + c] : br[table_index(comp_of, s)];
+                bv[i] = diag_entry<DIAG>(br, comp_of, s, c);
                 if constexpr (MODE == 1) kh[i] = krhat[off + s];
             }
         }
@@ -281,7 +285,7 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
         if (s >= 0) {
             C yv = cadd(buf[ix * SP + t2], cmul(bv[i], xv[i]));
             if constexpr (TENSOR) {  // the two off-diagonal entries of row c
-                const C* bb = br + table_index(comp_of, s) * 3;
+                const C* bb = br + comp_of[s] * 3;
                 const int c1 = c == 0 ? 1 : 0, c2 = c == 2 ? 1 : 2;
                 const C* xr = X + (int64_t)r * 3 * N;
                 yv = cadd(yv, cadd(cmul(bb[c1], xr[c1 * N + s]), cmul(bb[c2], xr[c2 * N + s])));
@@ -872,27 +876,27 @@ template <typename T> struct LaunchX {
         }
         return cudaErrorInvalidValue;
     }
-    template <int LX, int V, bool TENSOR>
+    template <int LX, int V, int DIAG>
     static cudaError_t inv_w(const Geom& g, int R, const cx<T>* u1, cx<T>* y, const cx<T>* x, const DevTarget& tg,
                              const cx<T>* beta, int beta_stride, const cx<T>* tw, int* active,
                              const FusedKrylov<T>& fk, cudaStream_t st) {
         if constexpr (kWarpX) {
             using PL = XwPlan<LX, V>;
-            const size_t sm = xw_smem<PL>();
+            const size_t sm = (size_t)xwi_rows<PL>() * xw_plane<PL>() * sizeof(float2);
             const int nrows = g.ny * g.nz;
-            dim3 grid((nrows + xw_rows<PL>() - 1) / xw_rows<PL>(), 3, R);
+            dim3 grid((nrows + xwi_rows<PL>() - 1) / xwi_rows<PL>(), 3, R);
             auto go = [&](auto kern) -> cudaError_t {
                 cudaError_t e = allow_smem(kern, sm);
                 if (e != cudaSuccess) return e;
                 PROF_BEGIN(st);
-                kern<<<grid, kXwThreads, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride, nrows, g.N,
+                kern<<<grid, kXwiThreads, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride, nrows, g.N,
                                                    tw, active, fk.rhat, fk.st, fk.part, fk.cnt, fk.part_stride);
                 PROF_END(KK_XINV_C64, R, st);
                 return cudaGetLastError();
             };
-            if (fk.mode == 1) return go(k_xinv_w<LX, V, 1, TENSOR>);
-            if (fk.mode == 2) return go(k_xinv_w<LX, V, 2, TENSOR>);
-            return go(k_xinv_w<LX, V, 0, TENSOR>);
+            if (fk.mode == 1) return go(k_xinv_w<LX, V, 1, DIAG>);
+            if (fk.mode == 2) return go(k_xinv_w<LX, V, 2, DIAG>);
+            return go(k_xinv_w<LX, V, 0, DIAG>);
         }
         return cudaErrorInvalidValue;
     }
@@ -927,7 +931,7 @@ template <typename T> struct LaunchX {
         PROF_END(KK_XFWD_C64 + koff, R, st);
         return cudaGetLastError();
     }
-    template <int LX, int MODE, bool TENSOR>
+    template <int LX, int MODE, int DIAG>
     static cudaError_t inv_mode(const Geom& g, int R, const cx<T>* u1, cx<T>* y, const cx<T>* x, const DevTarget& tg,
                                 const cx<T>* beta, int beta_stride, const cx<T>* tw, int* active,
                                 const FusedKrylov<T>& fk, cudaStream_t st) {
@@ -936,13 +940,13 @@ template <typename T> struct LaunchX {
         const int nrows = g.ny * g.nz;
         dim3 grid((nrows + TP - 1) / TP, 3, R);
         cudaError_t e;
-        if ((e = allow_smem(k_xinv<T, LX, MODE, TENSOR>, sm)) != cudaSuccess) return e;
+        if ((e = allow_smem(k_xinv<T, LX, MODE, DIAG>, sm)) != cudaSuccess) return e;
         if constexpr (MODE == 0)
-            k_xinv<T, LX, 0, TENSOR><<<grid, NTH, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride,
+            k_xinv<T, LX, 0, DIAG><<<grid, NTH, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride,
                                                            nrows, g.N, tw, active, nullptr, nullptr, nullptr,
                                                            nullptr, 0);
         else
-            k_xinv<T, LX, MODE, TENSOR><<<grid, NTH, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride,
+            k_xinv<T, LX, MODE, DIAG><<<grid, NTH, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride,
                                                               nrows, g.N, tw, active, fk.rhat, fk.st, fk.part,
                                                               fk.cnt, fk.part_stride);
         return cudaGetLastError();
@@ -951,20 +955,32 @@ template <typename T> struct LaunchX {
     static cudaError_t inv(const Geom& g, int R, const cx<T>* u1, cx<T>* y, const cx<T>* x, const DevTarget& tg,
                            const cx<T>* beta, int beta_stride, bool tensor, const cx<T>* tw, int* active,
                            const FusedKrylov<T>& fk, int xvar, cudaStream_t st) {
+        // the kind of diagonal: tensor table, composition codes, or per-site
+        // materials (no composition array)
+        const int diag = tensor ? kDiagTensor : (tg.comp_of ? kDiagComp : kDiagSite);
+        auto by_diag = [&](auto launch) -> cudaError_t {
+            if (diag == kDiagTensor) return launch(std::integral_constant<int, kDiagTensor>{});
+            if (diag == kDiagSite) return launch(std::integral_constant<int, kDiagSite>{});
+            return launch(std::integral_constant<int, kDiagComp>{});
+        };
         if constexpr (kWarpX) {
             if (xvar == 2 && xw_variants(LX) > 1) {
                 if constexpr (xw_variants(LX) > 1)
-                    return tensor ? inv_w<LX, 1, true>(g, R, u1, y, x, tg, beta, beta_stride, tw, active, fk, st)
-                                  : inv_w<LX, 1, false>(g, R, u1, y, x, tg, beta, beta_stride, tw, active, fk, st);
+                    return by_diag([&](auto d) {
+                        return inv_w<LX, 1, decltype(d)::value>(g, R, u1, y, x, tg, beta, beta_stride, tw, active,
+                                                                fk, st);
+                    });
             }
             if (xvar >= 1)
-                return tensor ? inv_w<LX, 0, true>(g, R, u1, y, x, tg, beta, beta_stride, tw, active, fk, st)
-                              : inv_w<LX, 0, false>(g, R, u1, y, x, tg, beta, beta_stride, tw, active, fk, st);
+                return by_diag([&](auto d) {
+                    return inv_w<LX, 0, decltype(d)::value>(g, R, u1, y, x, tg, beta, beta_stride, tw, active, fk, st);
+                });
         }
         auto run = [&](auto mode) {
             constexpr int M = decltype(mode)::value;
-            return tensor ? inv_mode<LX, M, true>(g, R, u1, y, x, tg, beta, beta_stride, tw, active, fk, st)
-                          : inv_mode<LX, M, false>(g, R, u1, y, x, tg, beta, beta_stride, tw, active, fk, st);
+            return by_diag([&](auto d) {
+                return inv_mode<LX, M, decltype(d)::value>(g, R, u1, y, x, tg, beta, beta_stride, tw, active, fk, st);
+            });
         };
         cudaError_t e = cudaSuccess;
         PROF_BEGIN(st);
@@ -1019,6 +1035,9 @@ template <typename T> struct LaunchX {
                     // a staged Green tile serves RB column-RHS: RBZ RHS of one
                     // column, or of the (up to) 4 columns of an octant column
                     // (long columns: the tile is ~2 RHS of loads, so it serves 16)
+                    // (one RHS per octant block for the radix-16 variant -- twice
+                    // the blocks at 2 RHS -- was measured slower: the staging of
+                    // the Green tile then costs more than the warps gain)
                     constexpr int TP = tp_zr<PL>(), RBZ = LZ >= 256 ? 16 : 8, RBO = RBZ / 4;
                     const bool oct = zvar == 2 || zvar == 4;
                     const size_t sm = oct ? zoct_smem<PL, T>() : zreg_smem<PL, T>();

@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(SliceCfg<LX, LY, sizeof(cx<T>)>::NTH)
         const int e = threadIdx.x + i * NTH, s = sidx[i];
         if constexpr (!kHoistX) xv[i] = s >= 0 ? xs[s] : czero<C>();
         if (s >= 0) {
-            const C yv = cadd(plane[(e % NX) * SPY + e / NX], cmul(br[table_index(comp_of, s)], xv[i]));
+            const C yv = cadd(plane[(e % NX) * SPY + e / NX], cmul(br[comp_of[s]], xv[i]));
             ys[s] = yv;
             if constexpr (MODE == 1) d[0].add_cdot(krhat[off + s], yv);
             if constexpr (MODE == 2) {

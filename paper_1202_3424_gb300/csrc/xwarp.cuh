@@ -104,8 +104,13 @@ template <class PL> struct WarpSwz {
     }
 };
 
+// Block sizes: the x-forward runs 256 threads; the x-inverse 128, so that
+// the block reduction of its fused BiCGstab dot products waits for 4 warps,
+// not 8 (the barrier stall of the 256-thread blocks was the second largest).
 constexpr int kXwThreads = 256;
+constexpr int kXwiThreads = 128;
 template <class PL> __host__ __device__ constexpr int xw_rows() { return kXwThreads / PL::NT; }
+template <class PL> __host__ __device__ constexpr int xwi_rows() { return kXwiThreads / PL::NT; }
 template <class PL> __host__ __device__ constexpr int xw_plane() { return PL::L + warp_plane_pad(PL::NT); }
 // exchange planes of the block's rows, then the twiddle table
 template <class PL> __host__ __device__ constexpr size_t xw_smem() {
@@ -115,7 +120,7 @@ template <class PL> __host__ __device__ constexpr size_t xw_smem() {
 // then 85, then 128; the inverse keeps its diagonal operands in registers and
 // takes the larger budget above 12 points per lane
 template <class PL> __host__ __device__ constexpr int xwf_min_blocks() { return PL::E <= 8 ? 4 : (PL::E <= 16 ? 3 : 2); }
-template <class PL> __host__ __device__ constexpr int xwi_min_blocks() { return PL::E <= 8 ? 4 : (PL::E <= 12 ? 3 : 2); }
+template <class PL> __host__ __device__ constexpr int xwi_min_blocks() { return PL::E <= 8 ? 8 : (PL::E <= 12 ? 6 : 4); }
 
 // Up to 256 points the block copies the twiddle table to shared memory
 // (after its global loads are issued): the stage twiddles of different lanes
@@ -200,9 +205,9 @@ __global__ void __launch_bounds__(kXwThreads, xwf_min_blocks<XwPlan<LX, V>>())
 
 // ---- x-inverse: row IFFT + diagonal + scatter, warp-local pencils --------------
 // Same result as k_xinv (Y = conv + (1/alpha) X at the occupied sites, the
-// TENSOR form, and the fused BiCGstab reductions of MODE 1 and 2).
-template <int LX, int V, int MODE, bool TENSOR>
-__global__ void __launch_bounds__(kXwThreads, xwi_min_blocks<XwPlan<LX, V>>())
+// DIAG kinds, and the fused BiCGstab reductions of MODE 1 and 2).
+template <int LX, int V, int MODE, int DIAG>
+__global__ void __launch_bounds__(kXwiThreads, xwi_min_blocks<XwPlan<LX, V>>())
     k_xinv_w(const float2* __restrict__ U1, float2* __restrict__ Y, const float2* __restrict__ X,
              const int* __restrict__ site_of, const uint8_t* __restrict__ comp_of, const float2* __restrict__ beta,
              int beta_stride, int nrows, int64_t N, const float2* __restrict__ tw, int* __restrict__ active,
@@ -210,7 +215,7 @@ __global__ void __launch_bounds__(kXwThreads, xwi_min_blocks<XwPlan<LX, V>>())
              unsigned* __restrict__ cnt, int part_stride) {
     using C = float2;
     using PL = XwPlan<LX, V>;
-    constexpr int NT = PL::NT, E = PL::E, NX = LX / 2, RPB = xw_rows<PL>(), PS = xw_plane<PL>();
+    constexpr int NT = PL::NT, E = PL::E, NX = LX / 2, RPB = xwi_rows<PL>(), PS = xw_plane<PL>();
     constexpr int R0 = stage_radix<PL, +1>(0), NB0 = E / R0;
     constexpr int RL = stage_radix<PL, +1>(PL::NS - 1), NBL = E / RL, MN = RL / 2, NO = NBL * MN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -223,6 +228,7 @@ __global__ void __launch_bounds__(kXwThreads, xwi_min_blocks<XwPlan<LX, V>>())
     const int64_t off = ((int64_t)r * 3 + c) * N;
     const C* xs = X + off;
     C* ys = Y + off;
+    constexpr bool TENSOR = DIAG == kDiagTensor;
     const C* br = beta + (int64_t)r * beta_stride + (TENSOR ? c * (beta_stride / 3) : 0);
     const C* in = U1 + ((int64_t)r * 3 + c) * (int64_t)nrows * LX + (int64_t)row * LX;
     // the row in the first stage's layout, then the site indices of the
@@ -253,7 +259,7 @@ __global__ void __launch_bounds__(kXwThreads, xwi_min_blocks<XwPlan<LX, V>>())
             if constexpr (MODE == 1) kh[k] = czero<C>();
             if (s >= 0) {
                 xv[k] = xs[s];
-                bv[k] = TENSOR ? br[table_index(comp_of, s) * 3 + c] : br[table_index(comp_of, s)];
+                bv[k] = diag_entry<DIAG>(br, comp_of, s, c);
                 if constexpr (MODE == 1) kh[k] = krhat[off + s];
             }
         }
@@ -272,7 +278,7 @@ __global__ void __launch_bounds__(kXwThreads, xwi_min_blocks<XwPlan<LX, V>>())
             if (s >= 0) {
                 C yv = cadd(v[q * RL + m], cmul(bv[k], xv[k]));
                 if constexpr (TENSOR) {  // the two off-diagonal entries of row c
-                    const C* bb = br + table_index(comp_of, s) * 3;
+                    const C* bb = br + comp_of[s] * 3;
                     const int c1 = c == 0 ? 1 : 0, c2 = c == 2 ? 1 : 2;
                     const C* xr = X + (int64_t)r * 3 * N;
                     yv = cadd(yv, cadd(cmul(bb[c1], xr[c1 * N + s]), cmul(bb[c2], xr[c2 * N + s])));

@@ -79,6 +79,8 @@ def parse():
                          "1 + V warp-local rows with radix plan V")
     ap.add_argument("--xinv", type=int, default=None, choices=[-1, 0, 1, 2],
                     help="x-inverse schedule (overrides --xpass for the inverse pass only)")
+    ap.add_argument("--ypass", type=int, default=-1, choices=[-1, 0, 1],
+                    help="complex64 y-pass radix plan: -1 autotuned (default), 0 or 1")
     ap.add_argument("--zpass", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4],
                     help="complex64 z-pass schedule: -1 autotuned (default), 0 component groups, "
                          "1 register-resident, 2 register-resident with octant columns, 3 and 4 as 1 and 2 "
@@ -291,6 +293,7 @@ def run_gb300(args):
     prepare_ms = (time.perf_counter() - t0) * 1e3
     ctx.set_schedule(args.zpass)
     ctx.set_xpass((args.xpass, args.xpass if args.xinv is None else args.xinv))
+    ctx.set_ypass(args.ypass)
     info = ctx.info()
     N = info["ndipoles"]
     P_dev = torch.empty((R, 3, N), dtype=torch.complex128, device=dev)
@@ -395,7 +398,8 @@ def run_gb300(args):
 
     # the matvec schedules the autotuner chose for this RHS count (cached by now)
     schedule = {"solve": ctx.get_solve_schedule(R),
-                "plain_matvec": {"zpass": ctx.get_schedule(R), "xpass_fwd_inv": list(ctx.get_xpass(R))}}
+                "plain_matvec": {"zpass": ctx.get_schedule(R), "xpass_fwd_inv": list(ctx.get_xpass(R)),
+                                 "ypass": ctx.get_ypass(R)}}
     roof = roofline(kstats, info, R, w.name)
     # complex64 RHS-matvecs per traced step: 2 per BiCGstab (4 per BiCGstab(2)) iteration of every RHS
     per_iter = {"bicgstab": 2, "bicgstab2": 4, "qmr": 1}[args.solver]
@@ -747,6 +751,7 @@ def run_matvec_only(args):
     ctx.prepare_size_parameter(w.x, dda.Precision.FP32_REFINED)
     ctx.set_schedule(args.zpass)
     ctx.set_xpass((args.xpass, args.xpass if args.xinv is None else args.xinv))
+    ctx.set_ypass(args.ypass)
     N = ctx.info()["ndipoles"]
     k = np.resize(w.khat, (R, 3))
     e = np.resize(w.ehat, (R, 3))
@@ -780,8 +785,9 @@ def run_matvec_only(args):
     mv_roof = matvec_roofline(kst, info, "c64" if args.precision == "fp32" else "c128")
     zpass = ctx.get_schedule(R) if args.precision == "fp32" else 0
     xpass = list(ctx.get_xpass(R)) if args.precision == "fp32" else 0
+    ypass = ctx.get_ypass(R) if args.precision == "fp32" else 0
     line = {"mode": "matvec", "workload": w.name, "rhs": R, "precision": args.precision, "zpass": zpass,
-            "xpass": xpass,
+            "xpass": xpass, "ypass": ypass,
             "ms_per_matvec": ms, "rhs_matvecs_per_s": R / (ms / 1e3), "kernels": kern, "matvec_roofline": mv_roof}
     if args.cufft:
         line["cufft_comparison"] = cufft_matvec_timing(w, info, R, dt, x, args.steps)

@@ -329,7 +329,10 @@ dda_status dda_grad_qabs(dda_ctx* ctx, dda_precision precision, const double* kh
  *    (up to 32 lanes, read and scattered straight from and to global memory,
  *    warp barriers between the radix stages) with radix plan V: V = 0 is the
  *    staged plan, V = 1 (Lx = 128, 192, 256) a plan with fewer exchanges
- *    (radix 16, or more points per lane).
+ *    (radix 16, or more points per lane);
+ *  - the y passes (complex64 only, Ly = 128, 192, 256): 0 the plan of the
+ *    staged passes, 1 a radix plan with one exchange fewer (8 x 16,
+ *    8 x 8 x 3, 16 x 16).
  * All choices compute the same product; results agree to rounding.  In
  * automatic mode the context times the available choices inside whole
  * matvecs on its own workspace the first time a matvec of a given type and
@@ -346,14 +349,16 @@ dda_status dda_grad_qabs(dda_ctx* ctx, dda_precision precision, const double* kh
  * dda_set_xpass: xfwd, xinv -1 automatic (the default), 0, 1 or 2 forces
  *   that x-forward / x-inverse schedule where it exists (2 falls back to 1
  *   where Lx has one plan).
- * All three clear the timings; any other value: DDA_ERR_ARG.
+ * The setters clear the timings; any other value: DDA_ERR_ARG.
  * dda_get_schedule: the z schedule (and, if slices is not NULL, whether the
  *   slice passes run) of complex64 matvecs of R RHS on the current target,
  *   timing the candidates now if needed (this sizes the workspace for R).
  *   Needs dda_prepare with DDA_FP32_REFINED or DDA_FP32.
  * dda_get_xpass: likewise, the x-forward and x-inverse schedules of those
  *   matvecs.
- * dda_get_solve_schedule: the z, x-forward and x-inverse schedules of the
+ * dda_set_ypass: ypass -1 automatic (the default), 0 or 1 forces that y
+ *   plan where it exists.  dda_get_ypass: the y plan of plain matvecs.
+ * dda_get_solve_schedule: the z, x-forward, x-inverse and y schedules of the
  *   complex64 matvecs inside a solve of R RHS (those carry the fused BiCGstab
  *   updates and are tuned apart from plain matvecs, with the same candidates). */
 dda_status dda_set_schedule(dda_ctx* ctx, int zpass);
@@ -361,7 +366,9 @@ dda_status dda_set_slice_passes(dda_ctx* ctx, int on);
 dda_status dda_set_xpass(dda_ctx* ctx, int xfwd, int xinv);
 dda_status dda_get_schedule(dda_ctx* ctx, int R, int* zpass, int* slices);
 dda_status dda_get_xpass(dda_ctx* ctx, int R, int* xfwd, int* xinv);
-dda_status dda_get_solve_schedule(dda_ctx* ctx, int R, int* zpass, int* xfwd, int* xinv);
+dda_status dda_set_ypass(dda_ctx* ctx, int ypass);
+dda_status dda_get_ypass(dda_ctx* ctx, int R, int* ypass);
+dda_status dda_get_solve_schedule(dda_ctx* ctx, int R, int* zpass, int* xfwd, int* xinv, int* ypass);
 
 /* Launch tracing (the guide's TIMEIT timing switch, per kernel kind rather than
  * per run): when on, every hot-path kernel launch is bracketed by CUDA events

@@ -27,7 +27,7 @@ __all__ = [
     "dda_incident_field", "dda_grad_qabs", "dda_matvec_device_noalloc", "dda_set_schedule", "dda_get_schedule",
     "dda_nearfield", "dda_nearfield_dims", "dda_set_slice_passes", "dda_scattering_directions", "dda_farfield",
     "dda_angular_averages", "dda_mueller", "dda_set_anisotropic_materials", "dda_set_xpass", "dda_get_xpass",
-    "dda_set_site_materials", "dda_get_solve_schedule",
+    "dda_set_site_materials", "dda_get_solve_schedule", "dda_set_ypass", "dda_get_ypass",
 ]
 
 STATUS = {0: "DDA_OK", 1: "DDA_ERR_ARG", 2: "DDA_ERR_CUDA", 3: "DDA_ERR_OOM", 4: "DDA_ERR_SIZE",
@@ -125,7 +125,9 @@ def load_library(build_if_missing: bool = True):
                              ctypes.c_int),
         "dda_set_xpass": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "dda_set_site_materials": ([vp, _D, ctypes.c_double], ctypes.c_int),
-        "dda_get_solve_schedule": ([vp, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 3, ctypes.c_int),
+        "dda_get_solve_schedule": ([vp, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 4, ctypes.c_int),
+        "dda_set_ypass": ([vp, ctypes.c_int], ctypes.c_int),
+        "dda_get_ypass": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "dda_get_xpass": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
                           ctypes.c_int),
     }
@@ -451,12 +453,24 @@ def dda_get_xpass(ctx, R: int):
 
 
 def dda_get_solve_schedule(ctx, R: int):
-    """{"zpass", "xfwd", "xinv"}: the schedules of the complex64 matvecs in a
-    solve of R RHS (timed now if needed)."""
-    z, f, i = ctypes.c_int(-1), ctypes.c_int(-1), ctypes.c_int(-1)
+    """{"zpass", "xfwd", "xinv", "ypass"}: the schedules of the complex64
+    matvecs in a solve of R RHS (timed now if needed)."""
+    z, f, i, y = ctypes.c_int(-1), ctypes.c_int(-1), ctypes.c_int(-1), ctypes.c_int(-1)
     _check(ctx, load_library().dda_get_solve_schedule(ctx, int(R), ctypes.byref(z), ctypes.byref(f),
-                                                      ctypes.byref(i)))
-    return {"zpass": z.value, "xfwd": f.value, "xinv": i.value}
+                                                      ctypes.byref(i), ctypes.byref(y)))
+    return {"zpass": z.value, "xfwd": f.value, "xinv": i.value, "ypass": y.value}
+
+
+def dda_set_ypass(ctx, ypass: int):
+    """Force the complex64 y-pass radix plan (0 or 1) or restore autotuning (-1)."""
+    _check(ctx, load_library().dda_set_ypass(ctx, int(ypass)))
+
+
+def dda_get_ypass(ctx, R: int):
+    """The y-pass radix plan complex64 matvecs of R RHS use (timed now if needed)."""
+    y = ctypes.c_int(-1)
+    _check(ctx, load_library().dda_get_ypass(ctx, int(R), ctypes.byref(y)))
+    return y.value
 
 
 class Context:
@@ -539,6 +553,12 @@ class Context:
 
     def get_solve_schedule(self, R):
         return dda_get_solve_schedule(self.handle, R)
+
+    def set_ypass(self, ypass):
+        dda_set_ypass(self.handle, ypass)
+
+    def get_ypass(self, R):
+        return dda_get_ypass(self.handle, R)
 
     def set_slice_passes(self, on):
         dda_set_slice_passes(self.handle, on)

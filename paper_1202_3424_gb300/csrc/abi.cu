@@ -95,9 +95,10 @@ struct dda_ctx {
     GraphEntry graph;
     // z-pass schedule per (element bytes, RHS count), timed on first use;
     // force_z >= 0 overrides (dda_set_schedule)
-    std::map<std::pair<int, int>, std::array<int, 4>> zsched;  // -> (z, slice passes, x-fwd, x-inv)
+    std::map<std::pair<int, int>, std::array<int, 5>> zsched;  // -> (z, slice passes, x-fwd, x-inv, y)
     int force_z = -1;
     int force_xf = -1, force_xi = -1;  // x-pass schedules: -1 timed, else forced (dda_set_xpass)
+    int force_y = -1;                   // y-pass radix plan: -1 timed, else forced (dda_set_ypass)
     // -1 timed, 0 separate passes (default), 1 slice passes where built.
     // Measured on GB300 the slice passes win only on small grids outside a
     // solve (64^3 sphere, 2 RHS: 0.163 vs 0.175 ms per matvec) and lose inside
@@ -428,16 +429,23 @@ dda_status pick_schedule(dda_ctx* ctx, int R, bool may_time, PadWork<T>* out, bo
         return xs;
     };
     const std::vector<int> xfs = xlist(ctx->force_xf), xis = xlist(ctx->force_xi);
-    // untimed choice: the first of each list (warp-local x passes, plan 0)
-    auto apply = [&](const std::array<int, 4>& c) {
+    const int ny = ypass_schedules<T>(ctx->g);
+    std::vector<int> ys;
+    if (ny <= 1) ys = {0};
+    else if (ctx->force_y >= 0) ys = {std::min(ctx->force_y, ny - 1)};
+    else ys = {0, 1};
+    // untimed choice: the first of each list (warp-local x passes, plan 0;
+    // y passes plan 0)
+    auto apply = [&](const std::array<int, 5>& c) {
         out->zvar = c[0];
         out->slices = c[1];
         out->xfwd = c[2];
         out->xinv = c[3];
+        out->yvar = c[4];
     };
-    std::array<int, 4> cur = {zs[0], ss[0], xfs[0], xis[0]};
+    std::array<int, 5> cur = {zs[0], ss[0], xfs[0], xis[0], ys[0]};
     apply(cur);
-    if (zs.size() * ss.size() == 1 && xfs.size() == 1 && xis.size() == 1) return DDA_OK;
+    if (zs.size() * ss.size() == 1 && xfs.size() == 1 && xis.size() == 1 && ys.size() == 1) return DDA_OK;
     // plain matvecs and the BiCGstab matvecs with fused updates (the solves)
     // are tuned apart: the fused gather and scatter change what is fastest
     const std::pair<int, int> key((int)sizeof(cx<T>) * (fused ? -1 : 1), R);
@@ -475,11 +483,12 @@ dda_status pick_schedule(dda_ctx* ctx, int R, bool may_time, PadWork<T>* out, bo
     CU(cudaMemsetAsync(base, 0x3c, 2 * vec + tab, ctx->stream));
     PadWork<T> w{slot<cx<T>>(ctx, PadSlots<T>::a), slot<cx<T>>(ctx, PadSlots<T>::b)};
     w.beta_tensor = ctx->aniso;
-    auto run = [&](const std::array<int, 4>& c) -> cudaError_t {
+    auto run = [&](const std::array<int, 5>& c) -> cudaError_t {
         w.zvar = c[0];
         w.slices = c[1];
         w.xfwd = c[2];
         w.xinv = c[3];
+        w.yvar = c[4];
         if (!fused)
             return launch_matvec<T>(ctx->g, R, x, y, w, ctx->tg, beta, BS, ghat_of<T>(ctx), tw_of<T>(ctx), nullptr,
                                     ctx->stream);
@@ -511,7 +520,7 @@ dda_status pick_schedule(dda_ctx* ctx, int R, bool may_time, PadWork<T>* out, bo
     // The fastest of a set of candidates: one warm-up matvec each, then
     // rounds that alternate the candidates (so a clock ramp or a neighbour's
     // burst does not favour one); each keeps its best round.
-    auto fastest = [&](const std::vector<std::array<int, 4>>& combos) -> size_t {
+    auto fastest = [&](const std::vector<std::array<int, 5>>& combos) -> size_t {
         constexpr int kRounds = 3, kReps = 2;
         std::vector<float> best(combos.size(), 0.f);
         for (size_t i = 0; i < combos.size() && ce == cudaSuccess; ++i) ce = run(combos[i]);
@@ -532,20 +541,25 @@ dda_status pick_schedule(dda_ctx* ctx, int R, bool may_time, PadWork<T>* out, bo
         return pick;
     };
     // One coordinate at a time (the passes are separate kernels): the z
-    // schedule and slice passes with the default x passes, then the x-forward
-    // schedule, then the x-inverse schedule.
-    std::vector<std::array<int, 4>> combos;
+    // schedule and slice passes with the default x and y passes, then the
+    // x-forward schedule, the x-inverse schedule and the y-pass plan.
+    std::vector<std::array<int, 5>> combos;
     for (int zv : zs)
-        for (int sv : ss) combos.push_back({zv, sv, cur[2], cur[3]});
+        for (int sv : ss) combos.push_back({zv, sv, cur[2], cur[3], cur[4]});
     if (combos.size() > 1) cur = combos[fastest(combos)];
     if (!cur[1] && xfs.size() > 1 && ce == cudaSuccess) {
         combos.clear();
-        for (int xv : xfs) combos.push_back({cur[0], 0, xv, cur[3]});
+        for (int xv : xfs) combos.push_back({cur[0], 0, xv, cur[3], cur[4]});
         cur = combos[fastest(combos)];
     }
     if (!cur[1] && xis.size() > 1 && ce == cudaSuccess) {
         combos.clear();
-        for (int xv : xis) combos.push_back({cur[0], 0, cur[2], xv});
+        for (int xv : xis) combos.push_back({cur[0], 0, cur[2], xv, cur[4]});
+        cur = combos[fastest(combos)];
+    }
+    if (!cur[1] && ys.size() > 1 && ce == cudaSuccess) {
+        combos.clear();
+        for (int yv : ys) combos.push_back({cur[0], 0, cur[2], cur[3], yv});
         cur = combos[fastest(combos)];
     }
     if (e0) cudaEventDestroy(e0);
@@ -2216,8 +2230,8 @@ dda_status dda_get_schedule(dda_ctx* ctx, int R, int* zpass, int* slices) {
     return s;
 }
 
-dda_status dda_get_solve_schedule(dda_ctx* ctx, int R, int* zpass, int* xfwd, int* xinv) {
-    if (!ctx || !zpass || !xfwd || !xinv) return DDA_ERR_ARG;
+dda_status dda_get_solve_schedule(dda_ctx* ctx, int R, int* zpass, int* xfwd, int* xinv, int* ypass) {
+    if (!ctx || !zpass || !xfwd || !xinv || !ypass) return DDA_ERR_ARG;
     if (R <= 0) return ctx->fail(DDA_ERR_ARG, "R must be > 0");
     if (!ctx->prepared || !ctx->has32)
         return ctx->fail(DDA_ERR_ARG, "dda_prepare with a complex64-capable precision has not been called");
@@ -2230,6 +2244,34 @@ dda_status dda_get_solve_schedule(dda_ctx* ctx, int R, int* zpass, int* xfwd, in
     *zpass = w.zvar;
     *xfwd = w.xfwd;
     *xinv = w.xinv;
+    *ypass = w.yvar;
+    return s;
+}
+
+dda_status dda_set_ypass(dda_ctx* ctx, int ypass) {
+    if (!ctx) return DDA_ERR_ARG;
+    if (ypass < -1 || ypass > 1) return ctx->fail(DDA_ERR_ARG, "y-pass schedule must be -1, 0 or 1 (got %d)", ypass);
+    ctx->force_y = ypass;
+    ctx->zsched.clear();
+    if (ctx->graph.exec) {
+        cudaGraphExecDestroy(ctx->graph.exec);
+        ctx->graph.exec = nullptr;
+    }
+    return DDA_OK;
+}
+
+dda_status dda_get_ypass(dda_ctx* ctx, int R, int* ypass) {
+    if (!ctx || !ypass) return DDA_ERR_ARG;
+    if (R <= 0) return ctx->fail(DDA_ERR_ARG, "R must be > 0");
+    if (!ctx->prepared || !ctx->has32)
+        return ctx->fail(DDA_ERR_ARG, "dda_prepare with a complex64-capable precision has not been called");
+    ProfScope prof_scope(ctx);
+    cudaSetDevice(ctx->device);
+    dda_status s;
+    if ((s = ensure_pad<float>(ctx, R)) != DDA_OK) return s;
+    PadWork<float> w;
+    s = pick_schedule<float>(ctx, matvec_chunk<float>(ctx, R), true, &w);
+    *ypass = w.yvar;
     return s;
 }
 

@@ -54,6 +54,7 @@ template <typename T> struct PadWork {
     int zvar = 0;         // z-pass schedule, see zconv_schedules
     int xfwd = 0;         // x-forward schedule, see xpass_schedules
     int xinv = 0;         // x-inverse schedule, likewise
+    int yvar = 0;         // y-pass radix plan variant, see ypass_schedules
     int slices = 1;       // fused x+y slice passes where built (see slice_passes)
     // The 1/alpha table holds 3x3 tensors (anisotropic materials): per RHS
     // [3 rows c][comp][3 columns], so row c of composition comp's tensor is at
@@ -100,6 +101,10 @@ template <typename T> int zconv_schedules(const Geom& g);
 // 1 + V for the warp-local passes with radix plan variant V (xwarp.cuh).
 // Timed by the context like the z schedules.
 template <typename T> int xpass_schedules(const Geom& g);
+
+// Number of y-pass schedules (radix plan variants of the strided y passes,
+// complex64 only), timed like the others.
+template <typename T> int ypass_schedules(const Geom& g);
 
 // Fused x+y passes over whole z-slices (slice_impl.cuh): built for this
 // grid and element type?  Then the matvec runs xy-fwd, z, yx-inv instead of

@@ -5,6 +5,7 @@ namespace dda {
 
 template int zconv_schedules<double>(const Geom&);
 template int xpass_schedules<double>(const Geom&);
+template int ypass_schedules<double>(const Geom&);
 template cudaError_t launch_zconv<double>(const Geom&, int, double2*, const double2*, const double2*, const int*, int, cudaStream_t);
 template cudaError_t launch_matvec<double>(const Geom&, int, const double2*, double2*, const PadWork<double>&,
                                            const DevTarget&, const double2*, int, const double2*,

@@ -65,11 +65,6 @@ template <int L, int ES> __host__ __device__ constexpr int xinv_min_blocks() {
     constexpr int threads = tp_x<L, ES>() * XPlan<L, ES>::NT;
     return threads >= 1024 ? 1 : 1024 / threads;
 }
-template <int L, int ES> __host__ __device__ constexpr int tp_s() {
-    constexpr int nt = Plan<L>::NT;
-    const int tp = (256 / nt) > 32 ? 32 : ((256 / nt) < 8 ? 8 : (256 / nt));
-    return (ES == 8 && tp < 16) ? 16 : tp;
-}
 // z pass: 3*TP*NT threads per block, TP adjacent columns, and enough blocks
 // per SM (registers capped by the launch bound) to hide the latency of the
 // strided column loads: measured on GB300, three 384-thread blocks per SM
@@ -318,13 +313,27 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
 // to dst likewise.  MODE 0: forward with input positions >= L/2 zero;
 // MODE 1: inverse keeping positions < L/2; MODE 2: full forward transform.
 // TP pencils adjacent in w per block, so loads and stores coalesce across w.
-template <typename T, int L, int MODE>
-__global__ void __launch_bounds__(tp_s<L, sizeof(cx<T>)>() * Plan<L>::NT)
+// Radix plan variant V = 1 (complex64 y passes, tuned like the other passes):
+// 128 = 8 x 16, 192 = 8 x 8 x 3, 256 = 16 x 16, one exchange fewer than
+// the plan of V = 0 at twice the points per thread.  A half-warp always
+// covers 16 adjacent pencils at one position, so any position pattern of
+// the exchanges is free of bank conflicts.
+template <int L, int V> struct SPlan : Plan<L> {};
+template <> struct SPlan<128, 1> : PlanDef<128, 8, 8, 16> {};
+template <> struct SPlan<192, 1> : PlanDef<192, 8, 8, 8, 3> {};
+template <> struct SPlan<256, 1> : PlanDef<256, 16, 16, 16> {};
+__host__ __device__ constexpr int s_variants(int L) { return (L == 128 || L == 192 || L == 256) ? 2 : 1; }
+template <class PL, int ES> __host__ __device__ constexpr int tp_sp() {
+    const int tp = (256 / PL::NT) > 32 ? 32 : ((256 / PL::NT) < 8 ? 8 : (256 / PL::NT));
+    return (ES == 8 && tp < 16) ? 16 : tp;
+}
+template <typename T, int L, int MODE, int V = 0>
+__global__ void __launch_bounds__(tp_sp<SPlan<L, V>, sizeof(cx<T>)>() * SPlan<L, V>::NT)
     k_strided(const cx<T>* src, cx<T>* dst, int64_t pt_stride, int width, int64_t src_bstride, int64_t dst_bstride,
               int batches_per_rhs, const cx<T>* __restrict__ tw, const int* __restrict__ active) {
     using C = cx<T>;
-    using PL = Plan<L>;
-    constexpr int TP = tp_s<L, sizeof(cx<T>)>();
+    using PL = SPlan<L, V>;
+    constexpr int TP = tp_sp<PL, sizeof(cx<T>)>();
     constexpr int DIR = MODE == 1 ? +1 : -1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
@@ -993,24 +1002,35 @@ template <typename T> struct LaunchX {
         PROF_END(KK_XINV_C64 + koff, R, st);
         return cudaSuccess;
     }
-    template <int MODE, int L>
+    template <int MODE, int L, int V = 0>
     static cudaError_t strided_mode(const cx<T>* src, cx<T>* dst, int64_t pt_stride, int width, int64_t sb,
                                     int64_t db, int batches, int per_rhs, const cx<T>* tw, const int* active,
                                     cudaStream_t st, int kind, double units) {
-        constexpr int TP = tp_s<L, sizeof(cx<T>)>(), NTH = TP * Plan<L>::NT;
-        const size_t sm = (size_t)exchange_rows<L, Plan<L>::NT, TP, sizeof(cx<T>)>() * TP * sizeof(cx<T>);
-        cudaError_t e = allow_smem(k_strided<T, L, MODE>, sm);
+        using PL = SPlan<L, V>;
+        constexpr int TP = tp_sp<PL, sizeof(cx<T>)>(), NTH = TP * PL::NT;
+        const size_t sm = (size_t)exchange_rows<L, PL::NT, TP, sizeof(cx<T>)>() * TP * sizeof(cx<T>);
+        cudaError_t e = allow_smem(k_strided<T, L, MODE, V>, sm);
         if (e != cudaSuccess) return e;
         dim3 grid((width + TP - 1) / TP, batches, 1);
         PROF_BEGIN(st);
-        k_strided<T, L, MODE><<<grid, NTH, sm, st>>>(src, dst, pt_stride, width, sb, db, per_rhs, tw, active);
+        k_strided<T, L, MODE, V><<<grid, NTH, sm, st>>>(src, dst, pt_stride, width, sb, db, per_rhs, tw, active);
         PROF_END(kind, units, st);
         return cudaGetLastError();
     }
+    // yvar 1: radix plan variant 1 where it exists (complex64 y passes only)
+    template <int L> static int yvariants() { return (sizeof(T) == 4 && !kDouble) ? s_variants(L) : 1; }
     template <int L>
     static cudaError_t strided(int mode, const cx<T>* src, cx<T>* dst, int64_t pt_stride, int width, int64_t sb,
                                int64_t db, int batches, int per_rhs, const cx<T>* tw, const int* active,
-                               cudaStream_t st, int kind, double units) {
+                               cudaStream_t st, int kind, double units, int yvar = 0) {
+        if constexpr (sizeof(T) == 4 && !kDouble && s_variants(L) > 1) {
+            if (yvar == 1 && mode == 0)
+                return strided_mode<0, L, 1>(src, dst, pt_stride, width, sb, db, batches, per_rhs, tw, active, st, kind,
+                                             units);
+            if (yvar == 1 && mode == 1)
+                return strided_mode<1, L, 1>(src, dst, pt_stride, width, sb, db, batches, per_rhs, tw, active, st, kind,
+                                             units);
+        }
         if (mode == 0)
             return strided_mode<0, L>(src, dst, pt_stride, width, sb, db, batches, per_rhs, tw, active, st, kind, units);
         if (mode == 1)
@@ -1095,7 +1115,7 @@ cudaError_t launch_matvec_fused(const Geom& g, int R, cx<T>* x, cx<T>* y, const 
     };
     auto ys = [&](int mode, const cx<T>* s, cx<T>* d, int64_t sb, int64_t db) -> cudaError_t {
         DDA_DISPATCH_L(g.Ly, LX::template strided, mode, s, d, (int64_t)g.Lx, g.Lx, sb, db, R * 3 * g.nz, 3 * g.nz,
-                       tw.y, active, st, (mode == 0 ? KK_YFWD_C64 : KK_YINV_C64) + LX::koff, (double)R);
+                       tw.y, active, st, (mode == 0 ? KK_YFWD_C64 : KK_YINV_C64) + LX::koff, (double)R, w.yvar);
     };
     auto zc = [&]() -> cudaError_t {
         DDA_DISPATCH_L(g.Lz, LX::template zconv, g, R, w.u2, ghat, tw.z, active, w.zvar, st);
@@ -1146,6 +1166,17 @@ template <typename T> int xpass_schedules(const Geom& g) {
         case 256: return LaunchX<T>::template xvariants<256>();
         case 384: return LaunchX<T>::template xvariants<384>();
         case 512: return LaunchX<T>::template xvariants<512>();
+        default: return 1;
+    }
+}
+
+// Number of y-pass schedules: radix plan variants of the strided y passes
+// (complex64: 2 for Ly = 128, 192, 256; else 1).
+template <typename T> int ypass_schedules(const Geom& g) {
+    switch (g.Ly) {
+        case 128: return LaunchX<T>::template yvariants<128>();
+        case 192: return LaunchX<T>::template yvariants<192>();
+        case 256: return LaunchX<T>::template yvariants<256>();
         default: return 1;
     }
 }

@@ -220,6 +220,56 @@ def test_refined_solve_through_each_x_schedule(lib, xpass):
     ctx.close()
 
 
+# Columns of the y lengths with two radix plans (Ly = 128, 192, 256)
+Y_CASES = [
+    ("cols128_block_5x64x3", lambda: block_bernoulli_grid(5, 64, 3, seed=26), [1.5 + 0.1j, 1.25 + 0.02j], 2.0),
+    ("cols192_ellipsoid_7x90x5", lambda: ellipsoid_grid(7, 90, 5, 7, 90, 5), [1.45 + 0.05j], 3.0),
+    ("cols256_block_3x120x3", lambda: block_bernoulli_grid(3, 120, 3, seed=27), [1.4 + 0.2j, 2.0 + 0.5j], 2.5),
+]
+
+
+@pytest.mark.parametrize("name,gridf,m,x", Y_CASES, ids=[c[0] for c in Y_CASES])
+@pytest.mark.parametrize("ypass", [0, 1], ids=["yplan0", "yplan1"])
+def test_matvec_y_plans_match_oracle(lib, name, gridf, m, x, ypass):
+    """Both radix plans of the complex64 y passes against the pairwise oracle
+    (full, ragged and two-material columns)."""
+    grid = gridf()
+    ctx = _ctx(lib, grid, m, x, lib.Precision.FP32_REFINED)
+    info = ctx.info()
+    ctx.set_ypass(ypass)
+    R = 5
+    assert ctx.get_ypass(R) == ypass
+    kd = info["kd"]
+    khat, ehat = _rhs_set(R)
+    X = random_complex((R, 3, info["ndipoles"]), 15)
+    Y = ctx.matvec(2, khat, ehat, X)
+    for r in range(R):
+        rr, beta = _site_beta(grid, m, kd, khat[r], ehat[r])
+        want, _ = pairwise.matvec(rr, kd, beta, X[r].T)
+        assert _rel(Y[r].T, want) < F32_TOL, (name, ypass, r)
+    with pytest.raises(lib.DdaError):
+        ctx.set_ypass(2)
+    ctx.close()
+
+
+def test_refined_solve_through_the_second_y_plan(lib):
+    """The solve's matvecs (fused BiCGstab updates) with the y plan 8 x 16."""
+    grid = block_bernoulli_grid(5, 64, 3, seed=28)
+    m = [1.6 + 0.1j, 1.3 + 0.02j]
+    ctx = _ctx(lib, grid, m, 2.5, lib.Precision.FP32_REFINED)
+    k, e = _rhs_set(3)
+    ref, _, st = ctx.solve(lib.Precision.FP64, k, e, want_P=False, tol=1e-10, maxit=2000)
+    assert st == 0
+    ctx.set_ypass(1)
+    res, _, st = ctx.solve(lib.Precision.FP32_REFINED, k, e, want_P=False, tol=1e-6, maxit=2000)
+    assert st == 0 and max(r["resid_rel"] for r in res) <= 1e-6
+    assert ctx.get_solve_schedule(3)["ypass"] == 1
+    q = np.array([[r["qext"], r["qabs"], r["qsca"]] for r in res])
+    q0 = np.array([[r["qext"], r["qabs"], r["qsca"]] for r in ref])
+    assert np.abs(q - q0).max() < 1e-5 * np.abs(q0).max()
+    ctx.close()
+
+
 @pytest.mark.parametrize("zpass", [1, 2, 3, 4], ids=Z_IDS[1:])
 def test_refined_solve_through_each_z_schedule(lib, zpass):
     """A FP32-refined solve of a 5x4x60 two-material rod (128-point z
@@ -250,13 +300,15 @@ def test_autotuned_schedule_reproduces_forced_one(lib):
     ctx.set_slice_passes(-1)
     zpick, spick = ctx.get_schedule(R, with_slices=True)
     xpick = ctx.get_xpass(R)
-    assert zpick in (0, 1, 2, 3, 4) and spick in (0, 1) and all(v in (0, 1, 2) for v in xpick)
+    ypick = ctx.get_ypass(R)
+    assert zpick in (0, 1, 2, 3, 4) and spick in (0, 1) and all(v in (0, 1, 2) for v in xpick) and ypick in (0, 1)
     X = random_complex((R, 3, ctx.info()["ndipoles"]), 4).astype(np.complex64)
     k, e = np.resize(w.khat, (R, 3)), np.resize(w.ehat, (R, 3))
     y_auto = ctx.matvec(2, k, e, X)
     ctx.set_schedule(zpick)
     ctx.set_slice_passes(spick)
     ctx.set_xpass(xpick)
+    ctx.set_ypass(ypick)
     assert ctx.get_xpass(R) == xpick
     y_forced = ctx.matvec(2, k, e, X)
     assert np.array_equal(y_auto, y_forced)

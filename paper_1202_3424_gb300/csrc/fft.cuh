@@ -245,6 +245,71 @@ template <int SGN, typename C> struct Dft<16, SGN, C> {
     }
 };
 
+// Radix 32 as 4 x 8: n = 8 n1 + n2, k = k1 + 4 k2; eight length-4 DFTs over
+// n1, the twiddles W32^(n2 k1) (n2 k1 <= 21), four length-8 DFTs over n2.
+struct W32Table {
+    // cos and sin of pi j / 16, j = 0..21
+    static constexpr double c[22] = {1, 0.98078528040323043, 0.92387953251128674, 0.83146961230254524, 0.70710678118654757, 0.55557023301960229, 0.38268343236508984, 0.19509032201612833, 6.123233995736766e-17, -0.19509032201612819, -0.38268343236508973, -0.55557023301960196, -0.70710678118654746, -0.83146961230254535, -0.92387953251128674, -0.98078528040323043, -1, -0.98078528040323043, -0.92387953251128685, -0.83146961230254546, -0.70710678118654768, -0.55557023301960218};
+    static constexpr double s[22] = {0, 0.19509032201612825, 0.38268343236508978, 0.55557023301960218, 0.70710678118654746, 0.83146961230254524, 0.92387953251128674, 0.98078528040323043, 1, 0.98078528040323043, 0.92387953251128674, 0.83146961230254546, 0.70710678118654757, 0.55557023301960218, 0.38268343236508989, 0.19509032201612861, 1.2246467991473532e-16, -0.19509032201612836, -0.38268343236508967, -0.55557023301960196, -0.70710678118654746, -0.83146961230254524};
+};
+template <int SGN, typename C> struct Dft<32, SGN, C> {
+    template <int J> __device__ __forceinline__ static C w32(C a) {
+        using T = typename real_of<C>::type;
+        if constexpr (J == 0) return a;
+        else if constexpr (J == 8) return cmul_i<SGN>(a);
+        else if constexpr (J == 16) return cscale(a, T(-1));
+        else {
+            constexpr double cj = W32Table::c[J], sj = SGN > 0 ? W32Table::s[J] : -W32Table::s[J];
+            C w;
+            w.x = T(cj);
+            w.y = T(sj);
+            return cmul(a, w);
+        }
+    }
+    template <int N2> __device__ __forceinline__ static void twiddle_row(C (&y)[8][4]) {
+        y[N2][1] = w32<N2>(y[N2][1]);
+        y[N2][2] = w32<2 * N2>(y[N2][2]);
+        y[N2][3] = w32<3 * N2>(y[N2][3]);
+    }
+    __device__ __forceinline__ static void finish(C* v, C (&y)[8][4]) {
+        twiddle_row<1>(y);
+        twiddle_row<2>(y);
+        twiddle_row<3>(y);
+        twiddle_row<4>(y);
+        twiddle_row<5>(y);
+        twiddle_row<6>(y);
+        twiddle_row<7>(y);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            C z[8] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1], y[4][k1], y[5][k1], y[6][k1], y[7][k1]};
+            Dft<8, SGN, C>::run(z);
+#pragma unroll
+            for (int k2 = 0; k2 < 8; ++k2) v[k1 + 4 * k2] = z[k2];
+        }
+    }
+    __device__ __forceinline__ static void run(C* v) {
+        C y[8][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 8; ++n2) {
+#pragma unroll
+            for (int n1 = 0; n1 < 4; ++n1) y[n2][n1] = v[8 * n1 + n2];
+            Dft<4, SGN, C>::run(y[n2]);
+        }
+        finish(v, y);
+    }
+    // inputs 16..31 are zero
+    __device__ __forceinline__ static void run_half(C* v) {
+        C y[8][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 8; ++n2) {
+            y[n2][0] = v[n2];
+            y[n2][1] = v[8 + n2];
+            Dft<4, SGN, C>::run_half(y[n2]);
+        }
+        finish(v, y);
+    }
+};
+
 // ---- exchange-plane address maps -------------------------------------------
 // Kernels whose pencils lie within one warp give each pencil its own plane
 // and map position pos of the exchange after stage S to a swizzled slot;

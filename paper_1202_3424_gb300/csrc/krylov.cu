@@ -147,13 +147,34 @@ __global__ void __launch_bounds__(kThreads)
     const C alpha = from2<C>(st[r].alpha), omega = from2<C>(st[r].omega);
     const int64_t off = (int64_t)r * n;
     DotAcc<C> d[2];
-    for (int64_t i = i0; i < n; i += stride) {
-        const C si = s_[off + i];
-        x[off + i] = cadd(x[off + i], cadd(cmul(alpha, p[off + i]), cmul(omega, si)));
-        const C ri = csub(si, cmul(omega, t[off + i]));
-        r_[off + i] = ri;
-        d[0].add_cdot(rhat[off + i], ri);
-        d[1].add_norm2(ri);
+    // The grid gives a thread about U elements (reduce_blocks): all their
+    // loads are issued before the first is used, so the pass waits on one
+    // memory latency instead of U in a row.
+    constexpr int U = 4;
+    for (int64_t b = i0; b < n; b += U * stride) {
+        C si[U], xi[U], pi[U], ti[U], hi[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int64_t i = b + k * stride;
+            if (i < n) {
+                si[k] = s_[off + i];
+                xi[k] = x[off + i];
+                pi[k] = p[off + i];
+                ti[k] = t[off + i];
+                hi[k] = rhat[off + i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int64_t i = b + k * stride;
+            if (i < n) {
+                x[off + i] = cadd(xi[k], cadd(cmul(alpha, pi[k]), cmul(omega, si[k])));
+                const C ri = csub(si[k], cmul(omega, ti[k]));
+                r_[off + i] = ri;
+                d[0].add_cdot(hi[k], ri);
+                d[1].add_norm2(ri);
+            }
+        }
     }
     double2 acc[2];
     block_totals<C, 2>(d, acc);

@@ -314,15 +314,18 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
 // MODE 1: inverse keeping positions < L/2; MODE 2: full forward transform.
 // TP pencils adjacent in w per block, so loads and stores coalesce across w.
 // Radix plan variant V = 1 (complex64 y passes, tuned like the other passes):
-// 128 = 8 x 16, 192 = 8 x 8 x 3, 256 = 16 x 16, one exchange fewer than
-// the plan of V = 0 at twice the points per thread.  A half-warp always
+// 128 = 8 x 16, 192 = 8 x 8 x 3, 256 = 16 x 16, 512 = 32 x 16, one exchange
+// fewer than the plan of V = 0 at twice (512: four times) the points per thread.  A half-warp always
 // covers 16 adjacent pencils at one position, so any position pattern of
 // the exchanges is free of bank conflicts.
 template <int L, int V> struct SPlan : Plan<L> {};
 template <> struct SPlan<128, 1> : PlanDef<128, 8, 8, 16> {};
 template <> struct SPlan<192, 1> : PlanDef<192, 8, 8, 8, 3> {};
 template <> struct SPlan<256, 1> : PlanDef<256, 16, 16, 16> {};
-__host__ __device__ constexpr int s_variants(int L) { return (L == 128 || L == 192 || L == 256) ? 2 : 1; }
+template <> struct SPlan<512, 1> : PlanDef<512, 16, 32, 16> {};
+__host__ __device__ constexpr int s_variants(int L) {
+    return (L == 128 || L == 192 || L == 256 || L == 512) ? 2 : 1;
+}
 template <class PL, int ES> __host__ __device__ constexpr int tp_sp() {
     const int tp = (256 / PL::NT) > 32 ? 32 : ((256 / PL::NT) < 8 ? 8 : (256 / PL::NT));
     return (ES == 8 && tp < 16) ? 16 : tp;
@@ -1177,6 +1180,7 @@ template <typename T> int ypass_schedules(const Geom& g) {
         case 128: return LaunchX<T>::template yvariants<128>();
         case 192: return LaunchX<T>::template yvariants<192>();
         case 256: return LaunchX<T>::template yvariants<256>();
+        case 512: return LaunchX<T>::template yvariants<512>();
         default: return 1;
     }
 }

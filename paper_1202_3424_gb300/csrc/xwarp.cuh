@@ -16,8 +16,8 @@
 // one word per wavefront.
 //
 // Radix plans: variant 0 is the plan of the staged x passes; variant 1, where
-// it exists, trades registers for fewer exchanges (radix 16 or radix 8 with
-// more points per lane).  The context times the variants inside whole
+// it exists, trades registers for fewer exchanges (radix 16 or 32, or radix 8
+// with more points per lane).  The context times the variants inside whole
 // matvecs and keeps the fastest (see pick_schedule in abi.cu).
 #pragma once
 
@@ -40,9 +40,12 @@ template <> struct XwPlan<256, 0> : PlanDef<256, 32, 4, 8, 8> {};
 template <> struct XwPlan<256, 1> : PlanDef<256, 16, 16, 16> {};
 template <> struct XwPlan<384, 0> : PlanDef<384, 32, 4, 4, 4, 3, 2> {};
 template <> struct XwPlan<512, 0> : PlanDef<512, 32, 8, 8, 8> {};
+template <> struct XwPlan<512, 1> : PlanDef<512, 16, 32, 16> {};
 
 // Number of plan variants per length.
-__host__ __device__ constexpr int xw_variants(int L) { return (L == 128 || L == 192 || L == 256) ? 2 : 1; }
+__host__ __device__ constexpr int xw_variants(int L) {
+    return (L == 128 || L == 192 || L == 256 || L == 512) ? 2 : 1;
+}
 
 // Exchange-plane swizzle key K of the exchange after stage S (0: none).
 __host__ __device__ constexpr int warp_swizzle_key(int L, int NT, int DIR, int S) {
@@ -79,6 +82,8 @@ __host__ __device__ constexpr int warp_swizzle_key(int L, int NT, int DIR, int S
     if (L == 384 && NT == 32 && DIR == -1 && S == 1) return 2;
     if (L == 384 && NT == 32 && DIR == 1 && S == 0) return 1;
     if (L == 384 && NT == 32 && DIR == 1 && S == 3) return 3;
+    if (L == 512 && NT == 16 && DIR == -1 && S == 0) return 5;
+    if (L == 512 && NT == 16 && DIR == 1 && S == 0) return 4;
     if (L == 512 && NT == 32 && DIR == -1 && S == 0) return 3;
     if (L == 512 && NT == 32 && DIR == -1 && S == 1) return 3;
     if (L == 512 && NT == 32 && DIR == 1 && S == 0) return 3;
@@ -120,7 +125,9 @@ template <class PL> __host__ __device__ constexpr size_t xw_smem() {
 // then 85, then 128; the inverse keeps its diagonal operands in registers and
 // takes the larger budget above 12 points per lane
 template <class PL> __host__ __device__ constexpr int xwf_min_blocks() { return PL::E <= 8 ? 4 : (PL::E <= 16 ? 3 : 2); }
-template <class PL> __host__ __device__ constexpr int xwi_min_blocks() { return PL::E <= 8 ? 8 : (PL::E <= 12 ? 6 : 4); }
+template <class PL> __host__ __device__ constexpr int xwi_min_blocks() {
+    return PL::E <= 8 ? 8 : (PL::E <= 12 ? 6 : (PL::E <= 16 ? 4 : 2));
+}
 
 // Up to 256 points the block copies the twiddle table to shared memory
 // (after its global loads are issued): the stage twiddles of different lanes
@@ -129,10 +136,13 @@ template <class PL> __host__ __device__ constexpr int xwi_min_blocks() { return 
 // table from global memory: there the block barrier of the copy cost 15 %.
 template <int L> __host__ __device__ constexpr bool xw_shared_twiddles() { return L <= 256; }
 template <int L> __device__ __forceinline__ const float2* stage_twiddles(float2* tws, const float2* __restrict__ tw) {
-    if constexpr (!xw_shared_twiddles<L>()) return tw;
-    for (int e = threadIdx.x; e < L; e += kXwThreads) tws[e] = tw[e];
-    __syncthreads();
-    return tws;
+    if constexpr (!xw_shared_twiddles<L>()) {
+        return tw;
+    } else {
+        for (int e = threadIdx.x; e < L; e += kXwThreads) tws[e] = tw[e];
+        __syncthreads();
+        return tws;
+    }
 }
 
 // ---- x-forward: gather + row FFT, warp-local pencils -------------------------------

@@ -158,7 +158,7 @@ X_CASES = [
     ("rows64_plate_25x25x3", MATVEC_CASES[5][1], MATVEC_CASES[5][2], MATVEC_CASES[5][3]),
     ("rows32_ellipsoid_ragged", MATVEC_CASES[2][1], MATVEC_CASES[2][2], MATVEC_CASES[2][3]),
 ]
-X_VARIANTS = {128: 2, 192: 2, 256: 2}   # radix plan variants of the warp-local rows
+X_VARIANTS = {128: 2, 192: 2, 256: 2, 512: 2}   # radix plan variants of the warp-local rows
 
 
 @pytest.mark.parametrize("name,gridf,m,x", X_CASES, ids=[c[0] for c in X_CASES])
@@ -225,6 +225,7 @@ Y_CASES = [
     ("cols128_block_5x64x3", lambda: block_bernoulli_grid(5, 64, 3, seed=26), [1.5 + 0.1j, 1.25 + 0.02j], 2.0),
     ("cols192_ellipsoid_7x90x5", lambda: ellipsoid_grid(7, 90, 5, 7, 90, 5), [1.45 + 0.05j], 3.0),
     ("cols256_block_3x120x3", lambda: block_bernoulli_grid(3, 120, 3, seed=27), [1.4 + 0.2j, 2.0 + 0.5j], 2.5),
+    ("cols512_ellipsoid_2x230x2", lambda: ellipsoid_grid(2, 230, 2, 2, 230, 2), [1.33 + 0.01j], 2.0),
 ]
 
 

@@ -212,9 +212,9 @@ dda_status dda_matvec_device(dda_ctx* ctx, dda_precision precision, int R, const
  * array of 64 MiB (67108864 bytes) that the library declares in device
  * memory: every GPU that loads the library holds it until the process exits.
  * Lattices or RHS counts whose scratch would exceed it are rejected with
- * DDA_ERR_SIZE (about 144 bytes per RHS for every site of the lattice
+ * DDA_ERR_SIZE (about 96 bytes per RHS for every site of the lattice
  * rounded up to half the padded FFT lengths, (Lx/2)(Ly/2)(Lz/2), for
- * complex64, twice that for complex128: the 64^3 lattice fits one complex64
+ * complex64, twice that for complex128: the 64^3 lattice fits two complex64
  * RHS).  The first call on a device looks up the array's device address,
  * and so does the first call after that device's context was destroyed and
  * re-created (cudaDeviceReset): make that first call before any stream

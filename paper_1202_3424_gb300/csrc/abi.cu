@@ -148,7 +148,7 @@ struct ProfScope {
 enum Slot {
     S_E64, S_X64, S_R64, S_Y64,
     S_IN_B, S_IN_X, S_IN_R, S_IN_RHAT, S_IN_P, S_IN_V, S_IN_S, S_IN_T,
-    S_PAD1_32, S_PAD2_32, S_PAD1_64, S_PAD2_64,
+    S_PAD2_32, S_PAD2_64,
     S_STATE, S_ACTIVE, S_WANT, S_OUTER, S_TOLREL, S_SCALE, S_COEF, S_NORM_B, S_NORM_R,
     S_PART, S_CNT, S_QSUM, S_COUNT,
     S_BETA64, S_BETA32, S_W, S_KHAT, S_EPOL,
@@ -343,19 +343,20 @@ dda_status upload_tables(dda_ctx* ctx, int R, const std::vector<double>& k, cons
     return DDA_OK;
 }
 
-// Chunk of RHS whose padded work fits the budget.
+// Chunk of RHS whose padded work (one [3][nz][Ly][Lx] buffer per RHS: the x
+// passes use its rows, see RowMap) fits the budget.
 template <typename T> int matvec_chunk(const dda_ctx* ctx, int R) {
-    const size_t per = (size_t)3 * (ctx->g.u1_per_comp() + ctx->g.u2_per_comp()) * sizeof(cx<T>);
+    const size_t per = (size_t)3 * ctx->g.u2_per_comp() * sizeof(cx<T>);
     const size_t budget = (size_t)48 << 30;
     int c = (int)std::max<size_t>(1, budget / per);
     return std::min(c, R);
 }
 
 template <typename T> struct PadSlots;
-template <> struct PadSlots<float> { static constexpr int a = S_PAD1_32, b = S_PAD2_32; };
-template <> struct PadSlots<double> { static constexpr int a = S_PAD1_64, b = S_PAD2_64; };
+template <> struct PadSlots<float> { static constexpr int b = S_PAD2_32; };
+template <> struct PadSlots<double> { static constexpr int b = S_PAD2_64; };
 // double-float elements are 16 bytes like complex128: share its work buffers
-template <> struct PadSlots<dfl> { static constexpr int a = S_PAD1_64, b = S_PAD2_64; };
+template <> struct PadSlots<dfl> { static constexpr int b = S_PAD2_64; };
 
 template <typename T> const cx<T>* ghat_of(const dda_ctx* ctx);
 template <> const float2* ghat_of<float>(const dda_ctx* ctx) { return (const float2*)ctx->m_gh32.p; }
@@ -378,9 +379,6 @@ template <> const cdfl* beta_of<dfl>(dda_ctx* ctx) { return slot<cdfl>(ctx, S_BE
 
 template <typename T> dda_status ensure_pad(dda_ctx* ctx, int R) {
     const int rc = matvec_chunk<T>(ctx, R);
-    dda_status s;
-    if ((s = ensure(ctx, ctx->pool[PadSlots<T>::a], (size_t)rc * 3 * ctx->g.u1_per_comp() * sizeof(cx<T>))) != DDA_OK)
-        return s;
     return ensure(ctx, ctx->pool[PadSlots<T>::b], (size_t)rc * 3 * ctx->g.u2_per_comp() * sizeof(cx<T>));
 }
 
@@ -481,7 +479,7 @@ dda_status pick_schedule(dda_ctx* ctx, int R, bool may_time, PadWork<T>* out, bo
     unsigned* cnt = reinterpret_cast<unsigned*>(base + 2 * vec + tab + stb + pb);
     int* act = reinterpret_cast<int*>(base + 2 * vec + tab + stb + pb + cb);
     CU(cudaMemsetAsync(base, 0x3c, 2 * vec + tab, ctx->stream));
-    PadWork<T> w{slot<cx<T>>(ctx, PadSlots<T>::a), slot<cx<T>>(ctx, PadSlots<T>::b)};
+    PadWork<T> w{nullptr, slot<cx<T>>(ctx, PadSlots<T>::b)};
     w.beta_tensor = ctx->aniso;
     auto run = [&](const std::array<int, 5>& c) -> cudaError_t {
         w.zvar = c[0];
@@ -577,7 +575,7 @@ template <typename T>
 dda_status run_matvec(dda_ctx* ctx, int R, const cx<T>* x, cx<T>* y, const int* active) {
     const int rc = matvec_chunk<T>(ctx, R);
     const int64_t n = 3 * ctx->g.N;
-    PadWork<T> w{slot<cx<T>>(ctx, PadSlots<T>::a), slot<cx<T>>(ctx, PadSlots<T>::b)};
+    PadWork<T> w{nullptr, slot<cx<T>>(ctx, PadSlots<T>::b)};
     w.beta_tensor = ctx->aniso;
     const int BS = beta_rhs_stride(ctx);
     dda_status zs;
@@ -636,7 +634,7 @@ dda_status run_matvec_fused(dda_ctx* ctx, int R, int mode, cx<T>* x, cx<T>* y, c
                             const cx<T>* rhat) {
     const int rc = matvec_chunk<T>(ctx, R);
     const int64_t n = 3 * ctx->g.N;
-    PadWork<T> w{slot<cx<T>>(ctx, PadSlots<T>::a), slot<cx<T>>(ctx, PadSlots<T>::b)};
+    PadWork<T> w{nullptr, slot<cx<T>>(ctx, PadSlots<T>::b)};
     w.beta_tensor = ctx->aniso;
     const int BS = beta_rhs_stride(ctx);
     const int ps = partial_stride(ctx);
@@ -1162,9 +1160,8 @@ dda_status matvec_noalloc(dda_ctx* ctx, int R, const std::vector<double>& k, con
     using C = cx<T>;
     const int BS = beta_rhs_stride(ctx);
     const size_t beta_bytes = align256((size_t)R * BS * sizeof(C));
-    const size_t u1_bytes = align256((size_t)R * 3 * ctx->g.u1_per_comp() * sizeof(C));
     const size_t u2_bytes = (size_t)R * 3 * ctx->g.u2_per_comp() * sizeof(C);
-    const size_t need = beta_bytes + u1_bytes + u2_bytes;
+    const size_t need = beta_bytes + u2_bytes;
     if (need > kNoAllocScratchBytes)
         return ctx->fail(DDA_ERR_SIZE,
                          "dda_matvec_device_noalloc needs %zu bytes of scratch for R=%d on this lattice; "
@@ -1178,7 +1175,7 @@ dda_status matvec_noalloc(dda_ctx* ctx, int R, const std::vector<double>& k, con
     std::vector<C> beta(bt.size());
     for (size_t i = 0; i < bt.size(); ++i) beta[i] = ccast<C>(make_double2(bt[i].real(), bt[i].imag()));
     C* d_beta = reinterpret_cast<C*>(base);
-    PadWork<T> w{reinterpret_cast<C*>(base + beta_bytes), reinterpret_cast<C*>(base + beta_bytes + u1_bytes)};
+    PadWork<T> w{nullptr, reinterpret_cast<C*>(base + beta_bytes)};
     w.beta_tensor = ctx->aniso;
     CU(cudaMemcpyAsync(d_beta, beta.data(), beta.size() * sizeof(C), cudaMemcpyHostToDevice, ctx->stream));
     dda_status zs;
@@ -1734,7 +1731,6 @@ dda_status nearfield_run(dda_ctx* ctx, int R, const double* P_host, const int di
     const int rc = std::max(1, std::min(R, 8));  // RHS per pass over the box
     C* Pbox = (C*)alloc((size_t)rc * 3 * Ne * sizeof(C));
     C* Ybox = (C*)alloc((size_t)rc * 3 * Ne * sizeof(C));
-    C* u1 = (C*)alloc((size_t)rc * 3 * g.u1_per_comp() * sizeof(C));
     C* u2 = (C*)alloc((size_t)rc * 3 * g.u2_per_comp() * sizeof(C));
     C* beta0 = (C*)alloc((size_t)rc * 2 * sizeof(C));
     double2* d_P = (double2*)alloc((size_t)rc * 3 * N * sizeof(double2));
@@ -1774,7 +1770,7 @@ dda_status nearfield_run(dda_ctx* ctx, int R, const double* P_host, const int di
     tg.lat_of = d_lat;
     tg.comp_of = d_comp;
     Twiddles<T> tw{(const C*)twT[0], (const C*)twT[1], (const C*)twT[2]};
-    PadWork<T> pw{u1, u2};
+    PadWork<T> pw{nullptr, u2};
     pw.slices = ctx->force_slices != 0;
     // phase origin: the target's own centre, in box index space
     const double cx = off[0] + 0.5 * (ctx->g.ox - 1), cy = off[1] + 0.5 * (ctx->g.oy - 1),

@@ -47,9 +47,23 @@ template <typename T> struct Twiddles {
     const cx<T>* z = nullptr;
 };
 
+// The x passes write and read the rows (iz, iy < ny) of one buffer
+// U [R][3][nz][Ly][Lx], row (iz, iy) at ky = iy of z-plane iz.  So the y
+// passes run in place (a block reads all positions of its pencils before it
+// writes any), the z pass works in place on the same buffer, and no
+// separate [nz][ny][Lx] buffer occupies L2 or HBM.
+struct RowMap {
+    int ny;               // lattice rows per z-plane
+    int pitch;            // rows per z-plane in the buffer (Ly)
+    int64_t comp_stride;  // elements per (RHS, component) slab: nz Ly Lx
+    __device__ __forceinline__ int64_t at(int r, int c, int row, int lx) const {
+        return ((int64_t)r * 3 + c) * comp_stride + ((int64_t)(row / ny) * pitch + row % ny) * lx;
+    }
+};
+
 // Workspace for the padded passes of one matvec of R right-hand sides.
 template <typename T> struct PadWork {
-    cx<T>* u1 = nullptr;  // [R][3][nz][ny][Lx] (unused when the slice passes run)
+    cx<T>* u1 = nullptr;  // unused (the x passes use the rows of u2, RowMap)
     cx<T>* u2 = nullptr;  // [R][3][nz][Ly][Lx]
     int zvar = 0;         // z-pass schedule, see zconv_schedules
     int xfwd = 0;         // x-forward schedule, see xpass_schedules

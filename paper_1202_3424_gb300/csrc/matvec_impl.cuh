@@ -10,12 +10,12 @@
 //
 // Pass structure (one kernel each, per RHS and component unless noted):
 //   x-fwd   gather P from the compact site vector, FFT rows along x (input
-//           half zero)                                  -> U1 [nz][ny][Lx]
-//   y-fwd   FFT along y (input half zero)               -> U2 [nz][Ly][Lx]
+//           half zero)           -> rows (z, y < ny) of U [nz][Ly][Lx]
+//   y-fwd   FFT along y (input half zero), in place     -> U [nz][Ly][Lx]
 //   z-conv  for each (kx,ky) column, all three components: FFT along z
 //           (input half zero), multiply by the symmetric 3x3 Ghat in
 //           registers, inverse FFT along z, keep z < nz  -> U2 in place
-//   y-inv   inverse FFT along y, keep y < ny            -> U1
+//   y-inv   inverse FFT along y, keep y < ny, in place  -> rows (z, y < ny) of U
 //   x-inv   inverse FFT along x, keep x < nx, add (1/alpha) P, scatter to
 //           the compact site vector
 // Ghat is stored as one octant (k <= L/2 on each axis) of the transformed
@@ -111,8 +111,8 @@ template <int L, typename T> __host__ __device__ constexpr size_t zconv_smem() {
 //                      MODE 2  X = s <- r - alpha v.
 template <typename T, int LX, int MODE>
 __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(cx<T>)>::NT)
-    k_xfwd(cx<T>* __restrict__ X, cx<T>* __restrict__ U1, const int* __restrict__ site_of, int nrows, int64_t N,
-           const cx<T>* __restrict__ tw, const int* __restrict__ active, const cx<T>* __restrict__ kr,
+    k_xfwd(cx<T>* __restrict__ X, cx<T>* __restrict__ U, RowMap rm, const int* __restrict__ site_of, int nrows,
+           int64_t N, const cx<T>* __restrict__ tw, const int* __restrict__ active, const cx<T>* __restrict__ kr,
            const cx<T>* __restrict__ kv, const KState* __restrict__ st) {
     using C = cx<T>;
     using PL = XPlan<LX, sizeof(cx<T>)>;
@@ -175,12 +175,11 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
     __syncthreads();
     for_each_out<PL, -1, false>(u, [&](int idx, int pos) { bt[pos * SP] = v[idx]; });
     __syncthreads();
-    C* out = U1 + ((int64_t)r * 3 + c) * (int64_t)nrows * LX;
     constexpr int NO = (TP * LX + NTH - 1) / NTH;
 #pragma unroll
     for (int i = 0; i < NO; ++i) {
         const int e = threadIdx.x + i * NTH, t2 = e / LX, x = e - t2 * LX, row = row0 + t2;
-        if (e < TP * LX && row < nrows) out[(int64_t)row * LX + x] = buf[x * SP + t2];
+        if (e < TP * LX && row < nrows) U[rm.at(r, c, row, LX) + x] = buf[x * SP + t2];
     }
 }
 
@@ -198,7 +197,7 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
 template <typename T, int LX, int MODE, int DIAG>
 __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(cx<T>)>::NT,
                                    xinv_min_blocks<LX, sizeof(cx<T>)>())
-    k_xinv(const cx<T>* __restrict__ U1, cx<T>* __restrict__ Y, const cx<T>* __restrict__ X,
+    k_xinv(const cx<T>* __restrict__ U, RowMap rm, cx<T>* __restrict__ Y, const cx<T>* __restrict__ X,
            const int* __restrict__ site_of, const uint8_t* __restrict__ comp_of, const cx<T>* __restrict__ beta,
            int beta_stride, int nrows, int64_t N, const cx<T>* __restrict__ tw, int* __restrict__ active,
            const cx<T>* __restrict__ krhat, KState* __restrict__ st, double2* __restrict__ part,
@@ -211,7 +210,6 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
     const int c = blockIdx.y, r = blockIdx.z;
     if (active != nullptr && active[r] == 0) return;
     const int row0 = blockIdx.x * TP;
-    const C* in = U1 + ((int64_t)r * 3 + c) * (int64_t)nrows * LX;
     const int64_t off = ((int64_t)r * 3 + c) * N;
     const C* xs = X + off;
     C* ys = Y + off;
@@ -227,7 +225,7 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
 #pragma unroll
         for (int i = 0; i < NI; ++i) {
             const int e = threadIdx.x + i * NTH, t2 = e / LX, x = e - t2 * LX, row = row0 + t2;
-            rin[i] = (e < TP * LX && row < nrows) ? in[(int64_t)row * LX + x] : czero<C>();
+            rin[i] = (e < TP * LX && row < nrows) ? U[rm.at(r, c, row, LX) + x] : czero<C>();
         }
 #pragma unroll
         for (int i = 0; i < NG; ++i) {
@@ -860,6 +858,11 @@ static inline unsigned grid1d(int64_t n, int threads) {
         default: return cudaErrorInvalidValue;              \
     }
 
+// The x passes' rows inside the y-transformed buffer (see RowMap).
+static inline RowMap row_map(const Geom& g) {
+    return RowMap{g.ny, g.Ly, (int64_t)g.nz * g.Ly * g.Lx};
+}
+
 template <typename T> struct LaunchX {
     // double-float matvecs run only the plain passes (no fused Krylov modes)
     static constexpr bool kDouble = std::is_same<T, dfl>::value;
@@ -878,7 +881,7 @@ template <typename T> struct LaunchX {
                 cudaError_t e = allow_smem(kern, sm);
                 if (e != cudaSuccess) return e;
                 PROF_BEGIN(st);
-                kern<<<grid, kXwThreads, sm, st>>>(x, u1, site_of, nrows, g.N, tw, active, kr, kv, ks);
+                kern<<<grid, kXwThreads, sm, st>>>(x, u1, row_map(g), site_of, nrows, g.N, tw, active, kr, kv, ks);
                 PROF_END(KK_XFWD_C64, R, st);
                 return cudaGetLastError();
             };
@@ -901,7 +904,8 @@ template <typename T> struct LaunchX {
                 cudaError_t e = allow_smem(kern, sm);
                 if (e != cudaSuccess) return e;
                 PROF_BEGIN(st);
-                kern<<<grid, kXwiThreads, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride, nrows, g.N,
+                kern<<<grid, kXwiThreads, sm, st>>>(u1, row_map(g), y, x, tg.site_of, tg.comp_of, beta, beta_stride,
+                                                    nrows, g.N,
                                                    tw, active, fk.rhat, fk.st, fk.part, fk.cnt, fk.part_stride);
                 PROF_END(KK_XINV_C64, R, st);
                 return cudaGetLastError();
@@ -930,14 +934,17 @@ template <typename T> struct LaunchX {
         PROF_BEGIN(st);
         if (fk.mode == 0 || kDouble) {
             if ((e = allow_smem(k_xfwd<T, LX, 0>, sm)) != cudaSuccess) return e;
-            k_xfwd<T, LX, 0><<<grid, NTH, sm, st>>>(x, u1, site_of, nrows, g.N, tw, active, nullptr, nullptr, nullptr);
+            k_xfwd<T, LX, 0><<<grid, NTH, sm, st>>>(x, u1, row_map(g), site_of, nrows, g.N, tw, active, nullptr,
+                                                    nullptr, nullptr);
         } else if constexpr (!kDouble) {
             if (fk.mode == 1) {
                 if ((e = allow_smem(k_xfwd<T, LX, 1>, sm)) != cudaSuccess) return e;
-                k_xfwd<T, LX, 1><<<grid, NTH, sm, st>>>(x, u1, site_of, nrows, g.N, tw, active, fk.r, fk.v, fk.st);
+                k_xfwd<T, LX, 1><<<grid, NTH, sm, st>>>(x, u1, row_map(g), site_of, nrows, g.N, tw, active, fk.r,
+                                                        fk.v, fk.st);
             } else {
                 if ((e = allow_smem(k_xfwd<T, LX, 2>, sm)) != cudaSuccess) return e;
-                k_xfwd<T, LX, 2><<<grid, NTH, sm, st>>>(x, u1, site_of, nrows, g.N, tw, active, fk.r, fk.v, fk.st);
+                k_xfwd<T, LX, 2><<<grid, NTH, sm, st>>>(x, u1, row_map(g), site_of, nrows, g.N, tw, active, fk.r,
+                                                        fk.v, fk.st);
             }
         }
         PROF_END(KK_XFWD_C64 + koff, R, st);
@@ -954,11 +961,13 @@ template <typename T> struct LaunchX {
         cudaError_t e;
         if ((e = allow_smem(k_xinv<T, LX, MODE, DIAG>, sm)) != cudaSuccess) return e;
         if constexpr (MODE == 0)
-            k_xinv<T, LX, 0, DIAG><<<grid, NTH, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride,
+            k_xinv<T, LX, 0, DIAG><<<grid, NTH, sm, st>>>(u1, row_map(g), y, x, tg.site_of, tg.comp_of, beta,
+                                                         beta_stride,
                                                            nrows, g.N, tw, active, nullptr, nullptr, nullptr,
                                                            nullptr, 0);
         else
-            k_xinv<T, LX, MODE, DIAG><<<grid, NTH, sm, st>>>(u1, y, x, tg.site_of, tg.comp_of, beta, beta_stride,
+            k_xinv<T, LX, MODE, DIAG><<<grid, NTH, sm, st>>>(u1, row_map(g), y, x, tg.site_of, tg.comp_of, beta,
+                                                            beta_stride,
                                                               nrows, g.N, tw, active, fk.rhat, fk.st, fk.part,
                                                               fk.cnt, fk.part_stride);
         return cudaGetLastError();
@@ -1114,7 +1123,7 @@ cudaError_t launch_matvec_fused(const Geom& g, int R, cx<T>* x, cx<T>* y, const 
     if (g.nx * 2 != g.Lx || g.ny * 2 != g.Ly || g.nz * 2 != g.Lz) return cudaErrorInvalidValue;
     cudaError_t e;
     auto fwdx = [&]() -> cudaError_t {
-        DDA_DISPATCH_L(g.Lx, LX::template fwd, g, R, x, w.u1, tg.site_of, tw.x, active, fk, w.xfwd, st);
+        DDA_DISPATCH_L(g.Lx, LX::template fwd, g, R, x, w.u2, tg.site_of, tw.x, active, fk, w.xfwd, st);
     };
     auto ys = [&](int mode, const cx<T>* s, cx<T>* d, int64_t sb, int64_t db) -> cudaError_t {
         DDA_DISPATCH_L(g.Ly, LX::template strided, mode, s, d, (int64_t)g.Lx, g.Lx, sb, db, R * 3 * g.nz, 3 * g.nz,
@@ -1124,7 +1133,7 @@ cudaError_t launch_matvec_fused(const Geom& g, int R, cx<T>* x, cx<T>* y, const 
         DDA_DISPATCH_L(g.Lz, LX::template zconv, g, R, w.u2, ghat, tw.z, active, w.zvar, st);
     };
     auto invx = [&]() -> cudaError_t {
-        DDA_DISPATCH_L(g.Lx, LX::template inv, g, R, w.u1, y, x, tg, beta, beta_stride, w.beta_tensor, tw.x, active,
+        DDA_DISPATCH_L(g.Lx, LX::template inv, g, R, w.u2, y, x, tg, beta, beta_stride, w.beta_tensor, tw.x, active,
                        fk, w.xinv, st);
     };
     if (w.slices && !w.beta_tensor && slice_passes<T>(g)) {
@@ -1132,10 +1141,12 @@ cudaError_t launch_matvec_fused(const Geom& g, int R, cx<T>* x, cx<T>* y, const 
         if ((e = zc()) != cudaSuccess) return e;
         return launch_slice_inv<T>(g, R, w.u2, y, x, tg, beta, beta_stride, tw, active, fk, st);
     }
+    // (both y passes in place on u2: see RowMap)
+    const int64_t plane = (int64_t)g.Ly * g.Lx;
     if ((e = fwdx()) != cudaSuccess) return e;
-    if ((e = ys(0, w.u1, w.u2, (int64_t)g.ny * g.Lx, (int64_t)g.Ly * g.Lx)) != cudaSuccess) return e;
+    if ((e = ys(0, w.u2, w.u2, plane, plane)) != cudaSuccess) return e;
     if ((e = zc()) != cudaSuccess) return e;
-    if ((e = ys(1, w.u2, w.u1, (int64_t)g.Ly * g.Lx, (int64_t)g.ny * g.Lx)) != cudaSuccess) return e;
+    if ((e = ys(1, w.u2, w.u2, plane, plane)) != cudaSuccess) return e;
     return invx();
 }
 

@@ -1,7 +1,8 @@
 // x passes of the FFT-convolution matvec with warp-local pencils (complex64).
 //
 // The x passes transform rows of the padded lattice, which are contiguous in
-// both of their buffers: U1 rows [nz][ny][Lx], and the compact site vectors,
+// both of their buffers: the rows (z, y < ny) of U [nz][Ly][Lx] (RowMap in
+// matvec_impl.cuh), and the compact site vectors,
 // where the occupied sites of one lattice row have consecutive indices.  So a
 // row can be held by NT <= 32 consecutive lanes of one warp and read and
 // written straight from and to global memory in the layout of the first and
@@ -151,7 +152,8 @@ template <int L> __device__ __forceinline__ const float2* stage_twiddles(float2*
 // BiCGstab update in the gather and write it back to X.
 template <int LX, int V, int MODE>
 __global__ void __launch_bounds__(kXwThreads, xwf_min_blocks<XwPlan<LX, V>>())
-    k_xfwd_w(float2* __restrict__ X, float2* __restrict__ U1, const int* __restrict__ site_of, int nrows, int64_t N,
+    k_xfwd_w(float2* __restrict__ X, float2* __restrict__ U, RowMap rm, const int* __restrict__ site_of, int nrows,
+             int64_t N,
              const float2* __restrict__ tw, const int* __restrict__ active, const float2* __restrict__ kr,
              const float2* __restrict__ kv, const KState* __restrict__ st) {
     using C = float2;
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(kXwThreads, xwf_min_blocks<XwPlan<LX, V>>())
     auto ld = [&](int pos) { return plane[pos]; };
     auto stf = [&](int pos, C val) { plane[pos] = val; };
     fft_stages<C, PL, -1, 0, decltype(ld), decltype(stf), true, WarpSwz<PL>>(v, u, tws, ld, stf, true);
-    C* out = U1 + ((int64_t)r * 3 + c) * (int64_t)nrows * LX + (int64_t)row * LX;
+    C* out = U + rm.at(r, c, ok ? row : 0, LX);
     for_each_out<PL, -1, false>(u, [&](int idx, int pos) {
         if (ok) out[pos] = v[idx];
     });
@@ -218,7 +220,7 @@ __global__ void __launch_bounds__(kXwThreads, xwf_min_blocks<XwPlan<LX, V>>())
 // DIAG kinds, and the fused BiCGstab reductions of MODE 1 and 2).
 template <int LX, int V, int MODE, int DIAG>
 __global__ void __launch_bounds__(kXwiThreads, xwi_min_blocks<XwPlan<LX, V>>())
-    k_xinv_w(const float2* __restrict__ U1, float2* __restrict__ Y, const float2* __restrict__ X,
+    k_xinv_w(const float2* __restrict__ U, RowMap rm, float2* __restrict__ Y, const float2* __restrict__ X,
              const int* __restrict__ site_of, const uint8_t* __restrict__ comp_of, const float2* __restrict__ beta,
              int beta_stride, int nrows, int64_t N, const float2* __restrict__ tw, int* __restrict__ active,
              const float2* __restrict__ krhat, KState* __restrict__ st, double2* __restrict__ part,
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(kXwiThreads, xwi_min_blocks<XwPlan<LX, V>>())
     C* ys = Y + off;
     constexpr bool TENSOR = DIAG == kDiagTensor;
     const C* br = beta + (int64_t)r * beta_stride + (TENSOR ? c * (beta_stride / 3) : 0);
-    const C* in = U1 + ((int64_t)r * 3 + c) * (int64_t)nrows * LX + (int64_t)row * LX;
+    const C* in = U + rm.at(r, c, ok ? row : 0, LX);
     // the row in the first stage's layout, then the site indices of the
     // lattice-half outputs and (up to 12 points per lane) the diagonal
     // operands: their latency is hidden by the transform

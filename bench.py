@@ -404,7 +404,8 @@ def run_gb300(args):
     # complex64 RHS-matvecs per traced step: 2 per BiCGstab (4 per BiCGstab(2)) iteration of every RHS
     per_iter = {"bicgstab": 2, "bicgstab2": 4, "qmr": 1}[args.solver]
     mv_roof = matvec_roofline(kstats, info, "c64",
-                              rhs_matvecs=len(per_tr) * sum(per_iter * r["iters"] for r in res)) \
+                              rhs_matvecs=len(per_tr) * sum(per_iter * r["iters"] for r in res),
+                              fused_vectors=FUSED_VECTORS_PER_MATVEC.get(args.solver, 0.0)) \
         if kstats else None
     launches = int(sum(s["launches"] for s in kstats.values()) / args.steps) * args.steps if kstats else 0
 
@@ -540,7 +541,8 @@ def ellipsoid_sweep(dda, dev, stream, flush, dist, steps=3, warmup=2):
     solve(dda.Precision.FP32_REFINED, w.khat, w.ehat, P)
     kin = read_profile(dda, ctx)
     L.dda_profile_enable(ctx.handle, 0)
-    mv_in = matvec_roofline(kin, info, "c64", rhs_matvecs=sum(2 * r["iters"] for r in res))
+    mv_in = matvec_roofline(kin, info, "c64", rhs_matvecs=sum(2 * r["iters"] for r in res),
+                            fused_vectors=FUSED_VECTORS_PER_MATVEC["bicgstab"])
     # the matvec alone (128 RHS per product)
     x = torch.randn((R, 3, N), dtype=torch.complex64, device=dev, generator=torch.Generator(device=dev).manual_seed(1))
     y = torch.empty_like(x)
@@ -627,7 +629,16 @@ def roofline(kstats, info, R, workload_name=None):
             "rhs_per_launch": units_per_launch, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
 
 
-def matvec_roofline(kstats, info, suffix="c64", rhs_matvecs=None):
+# Vector traffic the BiCGstab updates fused into the x passes add per
+# RHS-matvec, in units of one compact vector (3N complex): over the two
+# matvecs of an iteration, the mode-1 gather reads r, p, v and writes p (3
+# more than a plain gather of p), the mode-2 gather reads r, v and writes s (2
+# more), and the mode-1 scatter reads rhat (1 more): 6 per iteration, 3 per
+# matvec.
+FUSED_VECTORS_PER_MATVEC = {"bicgstab": 3.0}
+
+
+def matvec_roofline(kstats, info, suffix="c64", rhs_matvecs=None, fused_vectors=0.0):
     """The whole FFT-convolution matvec (its five passes together) against
     HBM: algorithmic bytes of all launches of the passes / their total time.
 
@@ -635,7 +646,9 @@ def matvec_roofline(kstats, info, suffix="c64", rhs_matvecs=None):
     intermediates, index maps, Green octant).  The profiler's units count
     the RHS a launch was given; inside a solve RHS that have converged are
     skipped, so rhs_matvecs (the RHS-matvecs actually done, from the solver's
-    iteration counts) replaces them there.  `survey_model` also gives the
+    iteration counts) replaces them there, and fused_vectors (compact
+    vectors per RHS-matvec that the fused Krylov updates read or write in
+    the x passes) adds that traffic.  `survey_model` also gives the
     lattice-wide model (81 R + 6) M s per matvec of R RHS (M = lattice
     sites, P read and written on the whole lattice)."""
     hbm, src = load_peaks()
@@ -649,15 +662,18 @@ def matvec_roofline(kstats, info, suffix="c64", rhs_matvecs=None):
         per_rhs = pass_bytes(k, info, 1) - fixed
         units = kstats[k]["units"] if rhs_matvecs is None else rhs_matvecs
         b += per_rhs * units + fixed * kstats[k]["launches"]
-    ach = b / (ms / 1e3) / 1e9
     s = 8 if suffix == "c64" else 16
+    fused_bytes = fused_vectors * 3 * info["ndipoles"] * s * (rhs_matvecs or 0)
+    b += fused_bytes
+    ach = b / (ms / 1e3) / 1e9
     M = (info["Lx"] // 2) * (info["Ly"] // 2) * (info["Lz"] // 2)
     zk = [k for k in kinds if k.startswith("z_conv")][0]
     units = kstats[zk]["units"] if rhs_matvecs is None else rhs_matvecs
     sb = (81 * units + 6 * kstats[zk]["launches"]) * M * s
     sach = sb / (ms / 1e3) / 1e9
     return {"passes": sorted(kinds), "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-            "frac": ach / hbm, "ms": ms, "algorithmic_bytes": b, "rhs_matvecs": units,
+            "frac": ach / hbm, "ms": ms, "algorithmic_bytes": b, "fused_update_bytes": fused_bytes,
+            "rhs_matvecs": units,
             "survey_model": {"bytes": sb, "achieved": sach, "frac": sach / hbm},
             "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
 

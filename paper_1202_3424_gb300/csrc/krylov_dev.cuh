@@ -54,6 +54,17 @@ __device__ __forceinline__ void block_reduce(double2 (&v)[ND]) {
     block_reduce<double, ND>(vx, vy, v);
 }
 
+// Ticket of the last-block reduction: an acquire-release add at GPU scope.
+// The release publishes the partials this thread stored before it; the
+// acquire (of the block that draws the last ticket) makes every block's
+// partials visible to that block, whose other threads read them after a
+// barrier, so no sequentially consistent fence (__threadfence) is needed.
+__device__ __forceinline__ unsigned ticket_acq_rel(unsigned* counter) {
+    unsigned t;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(t) : "l"(counter) : "memory");
+    return t;
+}
+
 // Store this block's partial sums (block totals already in thread 0's v[])
 // as partial `bid` of `nblocks`; the last block to arrive gets the grand
 // totals in thread 0's v[] and returns true (in every thread of that block).
@@ -64,23 +75,34 @@ __device__ __forceinline__ bool last_block_combine(double2 (&v)[ND], double2* pa
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int d = 0; d < ND; ++d) partials[bid * ND + d] = v[d];
-        __threadfence();
-        const unsigned ticket = atomicAdd(counter, 1u);
-        is_last = (ticket == (unsigned)nblocks - 1);
+        is_last = (ticket_acq_rel(counter) == (unsigned)nblocks - 1);
     }
     __syncthreads();
     if (!is_last) return false;
-    __threadfence();
+    // the partials are read UN per thread at a time, all loads issued before
+    // the first add: this block's combine is the launch's serial tail, and a
+    // loop with one load per trip waits one L2 latency per trip (the sums
+    // keep their order: partial b0 + k * blockDim.x is added k-th)
+    constexpr int UN = ND <= 2 ? 8 : 2;
     double2 s[ND];
 #pragma unroll
     for (int d = 0; d < ND; ++d) s[d] = make_double2(0.0, 0.0);
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+    for (int b0 = threadIdx.x; b0 < nblocks; b0 += UN * blockDim.x) {
+        double2 q[UN][ND];
 #pragma unroll
-        for (int d = 0; d < ND; ++d) {
-            const double2 q = __ldcg(&partials[b * ND + d]);
-            s[d].x += q.x;
-            s[d].y += q.y;
+        for (int k = 0; k < UN; ++k) {
+            const int b = b0 + k * blockDim.x;
+#pragma unroll
+            for (int d = 0; d < ND; ++d) q[k][d] = b < nblocks ? __ldcg(&partials[b * ND + d]) : make_double2(0.0, 0.0);
         }
+#pragma unroll
+        for (int k = 0; k < UN; ++k)
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                s[d].x += q[k][d].x;
+                s[d].y += q[k][d].y;
+            }
+    }
     block_reduce<ND>(s);
 #pragma unroll
     for (int d = 0; d < ND; ++d) v[d] = s[d];

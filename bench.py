@@ -631,11 +631,11 @@ def roofline(kstats, info, R, workload_name=None):
 
 # Vector traffic the BiCGstab updates fused into the x passes add per
 # RHS-matvec, in units of one compact vector (3N complex): over the two
-# matvecs of an iteration, the mode-1 gather reads r, p, v and writes p (3
-# more than a plain gather of p), the mode-2 gather reads r, v and writes s (2
-# more), and the mode-1 scatter reads rhat (1 more): 6 per iteration, 3 per
-# matvec.
-FUSED_VECTORS_PER_MATVEC = {"bicgstab": 3.0}
+# matvecs of an iteration, the first gather reads s, t, p, v, x and writes r,
+# x, p (7 more than a plain gather of p), the second gather reads r, v and
+# writes s (2 more), and each scatter reads rhat (2 more): 11 per iteration,
+# 5.5 per matvec.  (The iteration has no other kernel.)
+FUSED_VECTORS_PER_MATVEC = {"bicgstab": 5.5}
 
 
 def matvec_roofline(kstats, info, suffix="c64", rhs_matvecs=None, fused_vectors=0.0):

@@ -495,12 +495,18 @@ dda_status pick_schedule(dda_ctx* ctx, int R, bool may_time, PadWork<T>* out, bo
         // RHS that breaks down)
         cudaError_t e = cudaMemsetAsync(kst, 0x3c, R * sizeof(KState), ctx->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(act, 0x01, R * sizeof(int), ctx->stream);
-        for (int mode = 1; mode <= 2 && e == cudaSuccess; ++mode) {
+        // (BiCGstab's modes 3 and 2; the scratch vectors stand in for all of
+        // the Krylov vectors, whose values do not matter here)
+        for (int mode : {3, 2}) {
+            if (e != cudaSuccess) break;
             FusedKrylov<T> fk;
             fk.mode = mode;
             fk.r = x;
             fk.v = y;
             fk.rhat = x;
+            fk.s = x;
+            fk.t = y;
+            fk.x = y;
             fk.st = kst;
             fk.part = part;
             fk.cnt = cnt;
@@ -624,14 +630,16 @@ template <typename T> struct InnerSlots {
 // reduction kernels (<= kMaxReduceBlocks blocks, 2 sums) and for the fused
 // x-inverse scatter (one partial per block of that pass, 2 sums).
 int partial_stride(const dda_ctx* ctx) {
-    return std::max(5 * kMaxReduceBlocks, 2 * xinv_blocks_per_rhs(ctx->g));  // 5 sums: BiCGstab(2) Gram step
+    // 5 sums: the BiCGstab(2) Gram step; 4 per block: the BiCGstab t = A s scatter
+    return std::max(5 * kMaxReduceBlocks, 4 * xinv_blocks_per_rhs(ctx->g));
 }
 
 // Matvec over R RHS in chunks with the BiCGstab updates of `mode` fused into
 // its x passes (see FusedKrylov).
 template <typename T>
-dda_status run_matvec_fused(dda_ctx* ctx, int R, int mode, cx<T>* x, cx<T>* y, const cx<T>* r, const cx<T>* v,
-                            const cx<T>* rhat) {
+dda_status run_matvec_fused(dda_ctx* ctx, int R, int mode, cx<T>* x, cx<T>* y, cx<T>* r, const cx<T>* v,
+                            const cx<T>* rhat, const cx<T>* s_ = nullptr, const cx<T>* t = nullptr,
+                            cx<T>* xsol = nullptr) {
     const int rc = matvec_chunk<T>(ctx, R);
     const int64_t n = 3 * ctx->g.N;
     PadWork<T> w{nullptr, slot<cx<T>>(ctx, PadSlots<T>::b)};
@@ -649,6 +657,11 @@ dda_status run_matvec_fused(dda_ctx* ctx, int R, int mode, cx<T>* x, cx<T>* y, c
         fk.r = r + o;
         fk.v = v + o;
         fk.rhat = rhat + o;
+        if (mode == 3) {
+            fk.s = s_ + o;
+            fk.t = t + o;
+            fk.x = xsol + o;
+        }
         fk.st = slot<KState>(ctx, S_STATE) + r0;
         fk.part = slot<double2>(ctx, S_PART) + (int64_t)r0 * ps;
         fk.cnt = slot<unsigned>(ctx, S_CNT) + r0;
@@ -659,24 +672,17 @@ dda_status run_matvec_fused(dda_ctx* ctx, int R, int mode, cx<T>* x, cx<T>* y, c
     return DDA_OK;
 }
 
-// One BiCGstab iteration for every active RHS: 5 passes with p <- r + beta(p -
-// omega v) fused into the gather and alpha into the scatter, 5 passes with
-// s <- r - alpha v and omega fused likewise, then the x/r update with the
-// convergence test.
+// One BiCGstab iteration for every active RHS, two matvecs and no other
+// kernel: the first one's gather applies the previous iteration's end
+// (r <- s - omega t, x += alpha p + omega s) and forms p <- r + beta (p -
+// omega v), its scatter alpha; the second one's gather forms s <- r -
+// alpha v, its scatter omega, |r|, rho', beta and the stopping tests
+// (FusedKrylov modes 3 and 2).
 template <typename T> dda_status inner_iteration(dda_ctx* ctx, int R) {
-    using Ops = KrylovOps<cx<T>>;
-    const int64_t n = 3 * ctx->g.N;
     Inner<T> in = InnerSlots<T>::get(ctx);
-    KState* st = slot<KState>(ctx, S_STATE);
-    int* act = slot<int>(ctx, S_ACTIVE);
-    double2* part = slot<double2>(ctx, S_PART);
-    unsigned* cnt = slot<unsigned>(ctx, S_CNT);
-    cudaStream_t s = ctx->stream;
     dda_status rs;
-    if ((rs = run_matvec_fused<T>(ctx, R, 1, in.p, in.v, in.r, in.v, in.rhat)) != DDA_OK) return rs;
-    if ((rs = run_matvec_fused<T>(ctx, R, 2, in.s, in.t, in.r, in.v, in.rhat)) != DDA_OK) return rs;
-    CU(Ops::update_xr(R, n, in.x, in.p, in.s, in.t, in.r, in.rhat, st, act, part, cnt, s));
-    return DDA_OK;
+    if ((rs = run_matvec_fused<T>(ctx, R, 3, in.p, in.v, in.r, in.v, in.rhat, in.s, in.t, in.x)) != DDA_OK) return rs;
+    return run_matvec_fused<T>(ctx, R, 2, in.s, in.t, in.r, in.v, in.rhat);
 }
 
 // One BiCGstab(2) iteration for every active RHS (bicgstab2.cu): two BiCG
@@ -804,6 +810,12 @@ template <typename T> dda_status inner_solve(dda_ctx* ctx, int R, int maxit, boo
             have_graph = true;
         }
     }
+    // BiCGstab: the last x update of a RHS that stopped in the second matvec's
+    // scatter is still to be applied
+    if (solver == DDA_SOLVER_BICGSTAB) {
+        Inner<T> in = InnerSlots<T>::get(ctx);
+        CU(KrylovOps<cx<T>>::finish_x(R, 3 * ctx->g.N, in.x, in.p, in.s, slot<KState>(ctx, S_STATE), ctx->stream));
+    }
     return DDA_OK;
 }
 
@@ -923,7 +935,8 @@ dda_status solve_core(dda_ctx* ctx, int R, const dda_opts& o, bool refine, bool 
         }
         CU(cudaMemcpyAsync(ctx->pool[S_STATE].p, hst.data(), R * sizeof(KState), cudaMemcpyHostToDevice, s));
         CU(KrylovOps<cx<T>>::to_inner(R, n, Rr, in.b, slot<double>(ctx, S_SCALE), outer, s));
-        CU(KrylovOps<cx<T>>::init(R, n, in.b, in.x, in.r, in.rhat, in.p, in.v, slot<KState>(ctx, S_STATE),
+        CU(KrylovOps<cx<T>>::init(R, n, in.b, in.x, in.r, in.rhat, in.p, in.v,
+                                  o.solver == DDA_SOLVER_BICGSTAB ? in.s : nullptr, slot<KState>(ctx, S_STATE),
                                   slot<double>(ctx, S_TOLREL), outer, slot<int>(ctx, S_ACTIVE), part, cnt, s));
         if (o.solver == DDA_SOLVER_QMR)
             CU(QmrOps<cx<T>>::init(R, n, in.r, in.s, in.rhat, in.u2, in.b, slot<KState>(ctx, S_STATE),

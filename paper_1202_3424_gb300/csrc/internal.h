@@ -85,13 +85,21 @@ struct KState;
 //   mode 1: gather p <- r + beta (p - omega v) (written back to x);
 //           scatter v = A p and sigma = <rhat, v> -> alpha
 //   mode 2: gather s <- r - alpha v (written back to x);
-//           scatter t = A s and <t, s>, <t, t> -> omega
+//           scatter t = A s and <t, s>, <t, t>, <s, s>, <rhat, s>,
+//           <rhat, t> -> omega, |r'|, rho', beta and the stopping tests
+//   mode 3: gather of the BiCGstab iteration's first matvec: the previous
+//           iteration's r' = s - omega t and x += alpha p + omega s, then
+//           p <- r' + beta (p - omega v) (written back to x); scatter as mode 1
+// (BiCGstab runs modes 3 and 2; BiCGstab(2) uses mode 1.)
 // part/cnt: per-RHS partial sums (part_stride double2 per RHS) and tickets.
 template <typename T> struct FusedKrylov {
     int mode = 0;
-    const cx<T>* r = nullptr;
+    cx<T>* r = nullptr;  // read by modes 1 and 2, written by mode 3
     const cx<T>* v = nullptr;
     const cx<T>* rhat = nullptr;
+    const cx<T>* s = nullptr;  // mode 3: the previous iteration's s and t = A s
+    const cx<T>* t = nullptr;
+    cx<T>* x = nullptr;  // mode 3: the solution, updated in the gather
     KState* st = nullptr;
     double2* part = nullptr;
     unsigned* cnt = nullptr;

@@ -8,6 +8,13 @@
 //   s = r - alpha v;  t = A s;  omega = <t, s> / <t, t>;
 //   x += alpha p + omega s;  r = s - omega t;  rho' = <rhat, r>;
 //   beta = (rho'/rho)(alpha/omega).
+// In the solve these updates ride in the matvec passes (internal.h,
+// FusedKrylov): the gather of the first matvec forms the previous
+// iteration's r and x and the new p, the second matvec's scatter sums
+// <t, s>, <t, t>, <s, s>, <rhat, s>, <rhat, t>, from which |r'|^2 =
+// <s, s> - |<t, s>|^2 / <t, t> and rho' = <rhat, s> - omega <rhat, t>
+// (krylov_dev.cuh: finalize_omega_rho); k_finish_x applies the last x
+// update of a RHS that stopped.
 // Vectors are complex64 or complex128; every scalar (rho, alpha, omega,
 // beta, norms) is FP64.  Reductions write one FP64 partial per block; the
 // last block of a reduction (atomic ticket) sums the partials and updates the
@@ -32,13 +39,13 @@ static constexpr int kThreads = 256;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
 
 // ---- inner-solve kernels ---------------------------------------------------------
-// x = 0, r = rhat = b, p = v = 0;  |b|^2 -> scalars.
+// x = 0, r = rhat = b (and s = b when given), p = v = 0;  |b|^2 -> scalars.
 template <typename C>
 __global__ void __launch_bounds__(kThreads)
     k_init(int64_t n, const C* __restrict__ b, C* __restrict__ x, C* __restrict__ r_, C* __restrict__ rhat,
-           C* __restrict__ p, C* __restrict__ v, KState* __restrict__ st, const double* __restrict__ tol_rel,
-           const int* __restrict__ want, int* __restrict__ active, double2* __restrict__ part,
-           unsigned* __restrict__ cnt) {
+           C* __restrict__ p, C* __restrict__ v, C* __restrict__ s_, KState* __restrict__ st,
+           const double* __restrict__ tol_rel, const int* __restrict__ want, int* __restrict__ active,
+           double2* __restrict__ part, unsigned* __restrict__ cnt) {
     const int r = blockIdx.y;
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t off = (int64_t)r * n;
@@ -50,6 +57,7 @@ __global__ void __launch_bounds__(kThreads)
         rhat[off + i] = bi;
         p[off + i] = czero<C>();
         v[off + i] = czero<C>();
+        if (s_ != nullptr) s_[off + i] = bi;
         d[0].add_norm2(bi);
     }
     double2 acc[1];
@@ -78,128 +86,18 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// p = r + beta (p - omega v)
+// x += alpha p + omega s for each RHS whose BiCGstab iteration stopped with
+// that update pending (finalize_omega_rho); the others are left alone.
 template <typename C>
 __global__ void __launch_bounds__(kThreads)
-    k_update_p(int64_t n, C* __restrict__ p, const C* __restrict__ r_, const C* __restrict__ v,
-               const KState* __restrict__ st, const int* __restrict__ active) {
-    RHS_PROLOGUE(active)
-    const C beta = from2<C>(st[r].beta), omega = from2<C>(st[r].omega);
-    const int64_t off = (int64_t)r * n;
-    for (int64_t i = i0; i < n; i += stride) {
-        const C pv = csub(p[off + i], cmul(omega, v[off + i]));
-        p[off + i] = cadd(r_[off + i], cmul(beta, pv));
-    }
-}
-
-// sigma = <rhat, v>;  alpha = rho / sigma
-template <typename C>
-__global__ void __launch_bounds__(kThreads)
-    k_alpha(int64_t n, const C* __restrict__ rhat, const C* __restrict__ v, KState* __restrict__ st,
-            int* __restrict__ active, double2* __restrict__ part, unsigned* __restrict__ cnt) {
-    RHS_PROLOGUE(active)
-    const int64_t off = (int64_t)r * n;
-    DotAcc<C> d[1];
-    for (int64_t i = i0; i < n; i += stride) d[0].add_cdot(rhat[off + i], v[off + i]);
-    double2 acc[1];
-    block_totals<C, 1>(d, acc);
-    if (last_block_total_reduced<1>(acc, part + (int64_t)r * gridDim.x, cnt + r) && threadIdx.x == 0)
-        finalize_alpha(st, active, r, acc[0]);
-}
-
-// s = r - alpha v
-template <typename C>
-__global__ void __launch_bounds__(kThreads)
-    k_update_s(int64_t n, C* __restrict__ s_, const C* __restrict__ r_, const C* __restrict__ v,
-               const KState* __restrict__ st, const int* __restrict__ active) {
-    RHS_PROLOGUE(active)
-    const C alpha = from2<C>(st[r].alpha);
-    const int64_t off = (int64_t)r * n;
-    for (int64_t i = i0; i < n; i += stride) s_[off + i] = csub(r_[off + i], cmul(alpha, v[off + i]));
-}
-
-// omega = <t, s> / <t, t>
-template <typename C>
-__global__ void __launch_bounds__(kThreads)
-    k_omega(int64_t n, const C* __restrict__ t, const C* __restrict__ s_, KState* __restrict__ st,
-            int* __restrict__ active, double2* __restrict__ part, unsigned* __restrict__ cnt) {
-    RHS_PROLOGUE(active)
-    const int64_t off = (int64_t)r * n;
-    DotAcc<C> d[2];
-    for (int64_t i = i0; i < n; i += stride) {
-        const C ti = t[off + i];
-        d[0].add_cdot(ti, s_[off + i]);
-        d[1].add_norm2(ti);
-    }
-    double2 acc[2];
-    block_totals<C, 2>(d, acc);
-    if (last_block_total_reduced<2>(acc, part + (int64_t)r * gridDim.x * 2, cnt + r) && threadIdx.x == 0)
-        finalize_omega(st, active, r, acc[0], acc[1].x);
-}
-
-// x += alpha p + omega s;  r = s - omega t;  rho' = <rhat, r>, |r|^2; convergence.
-template <typename C>
-__global__ void __launch_bounds__(kThreads)
-    k_update_xr(int64_t n, C* __restrict__ x, const C* __restrict__ p, const C* __restrict__ s_,
-                const C* __restrict__ t, C* __restrict__ r_, const C* __restrict__ rhat, KState* __restrict__ st,
-                int* __restrict__ active, double2* __restrict__ part, unsigned* __restrict__ cnt) {
-    RHS_PROLOGUE(active)
+    k_finish_x(int64_t n, C* __restrict__ x, const C* __restrict__ p, const C* __restrict__ s_,
+               const KState* __restrict__ st) {
+    const int r = blockIdx.y;
+    if (!st[r].pending) return;
     const C alpha = from2<C>(st[r].alpha), omega = from2<C>(st[r].omega);
     const int64_t off = (int64_t)r * n;
-    DotAcc<C> d[2];
-    // The grid gives a thread about U elements (reduce_blocks): all their
-    // loads are issued before the first is used, so the pass waits on one
-    // memory latency instead of U in a row.
-    constexpr int U = 4;
-    for (int64_t b = i0; b < n; b += U * stride) {
-        C si[U], xi[U], pi[U], ti[U], hi[U];
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-            const int64_t i = b + k * stride;
-            if (i < n) {
-                si[k] = s_[off + i];
-                xi[k] = x[off + i];
-                pi[k] = p[off + i];
-                ti[k] = t[off + i];
-                hi[k] = rhat[off + i];
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-            const int64_t i = b + k * stride;
-            if (i < n) {
-                x[off + i] = cadd(xi[k], cadd(cmul(alpha, pi[k]), cmul(omega, si[k])));
-                const C ri = csub(si[k], cmul(omega, ti[k]));
-                r_[off + i] = ri;
-                d[0].add_cdot(hi[k], ri);
-                d[1].add_norm2(ri);
-            }
-        }
-    }
-    double2 acc[2];
-    block_totals<C, 2>(d, acc);
-    if (last_block_total_reduced<2>(acc, part + (int64_t)r * gridDim.x * 2, cnt + r) && threadIdx.x == 0) {
-        KState& s = st[r];  // (in place: a copy of the whole state costs registers)
-        const double rn = sqrt(acc[1].x);
-        s.rnorm = rn;
-        s.iter += 1;
-        if (!isfinite(rn) || !finite2(acc[0])) {
-            s.status = KS_NONFINITE;
-            active[r] = 0;
-        } else if (rn <= s.tol_abs) {
-            s.status = KS_CONVERGED;
-            active[r] = 0;
-        } else if (s.iter >= s.maxit) {
-            s.status = KS_MAXIT;
-            active[r] = 0;
-        } else if ((acc[0].x == 0.0 && acc[0].y == 0.0) || (s.omega.x == 0.0 && s.omega.y == 0.0)) {
-            s.status = KS_BREAKDOWN;
-            active[r] = 0;
-        } else {
-            s.beta = cmul(zdiv(acc[0], s.rho), zdiv(s.alpha, s.omega));
-            s.rho = acc[0];
-        }
-    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[off + i] = cadd(x[off + i], cadd(cmul(alpha, p[off + i]), cmul(omega, s_[off + i])));
 }
 
 __global__ void k_count_active(const int* __restrict__ active, int R, int* __restrict__ out) {
@@ -378,53 +276,20 @@ int reduce_blocks(int64_t n) {
 }
 
 template <typename C>
-cudaError_t KrylovOps<C>::init(int R, int64_t n, const C* b, C* x, C* r, C* rhat, C* p, C* v, KState* st,
+cudaError_t KrylovOps<C>::init(int R, int64_t n, const C* b, C* x, C* r, C* rhat, C* p, C* v, C* s_, KState* st,
                                const double* tol_rel, const int* want, int* active, double2* part, unsigned* cnt,
                                cudaStream_t s) {
     PROF_BEGIN(s);
-    k_init<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, b, x, r, rhat, p, v, st, tol_rel, want, active, part,
-                                                              cnt);
+    k_init<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, b, x, r, rhat, p, v, s_, st, tol_rel, want, active,
+                                                              part, cnt);
     PROF_END((sizeof(C) == 8 ? KK_KRYLOV_C64 : KK_KRYLOV_C128), R, s);
     return cudaGetLastError();
 }
 template <typename C>
-cudaError_t KrylovOps<C>::update_p(int R, int64_t n, C* p, const C* r, const C* v, const KState* st,
-                                   const int* active, cudaStream_t s) {
+cudaError_t KrylovOps<C>::finish_x(int R, int64_t n, C* x, const C* p, const C* s_, const KState* st,
+                                   cudaStream_t s) {
     PROF_BEGIN(s);
-    k_update_p<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, p, r, v, st, active);
-    PROF_END((sizeof(C) == 8 ? KK_KRYLOV_C64 : KK_KRYLOV_C128), R, s);
-    return cudaGetLastError();
-}
-template <typename C>
-cudaError_t KrylovOps<C>::alpha(int R, int64_t n, const C* rhat, const C* v, KState* st, int* active, double2* part,
-                                unsigned* cnt, cudaStream_t s) {
-    PROF_BEGIN(s);
-    k_alpha<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, rhat, v, st, active, part, cnt);
-    PROF_END((sizeof(C) == 8 ? KK_KRYLOV_C64 : KK_KRYLOV_C128), R, s);
-    return cudaGetLastError();
-}
-template <typename C>
-cudaError_t KrylovOps<C>::update_s(int R, int64_t n, C* s_, const C* r, const C* v, const KState* st,
-                                   const int* active, cudaStream_t s) {
-    PROF_BEGIN(s);
-    k_update_s<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, s_, r, v, st, active);
-    PROF_END((sizeof(C) == 8 ? KK_KRYLOV_C64 : KK_KRYLOV_C128), R, s);
-    return cudaGetLastError();
-}
-template <typename C>
-cudaError_t KrylovOps<C>::omega(int R, int64_t n, const C* t, const C* s_, KState* st, int* active, double2* part,
-                                unsigned* cnt, cudaStream_t s) {
-    PROF_BEGIN(s);
-    k_omega<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, t, s_, st, active, part, cnt);
-    PROF_END((sizeof(C) == 8 ? KK_KRYLOV_C64 : KK_KRYLOV_C128), R, s);
-    return cudaGetLastError();
-}
-template <typename C>
-cudaError_t KrylovOps<C>::update_xr(int R, int64_t n, C* x, const C* p, const C* s_, const C* t, C* r,
-                                    const C* rhat, KState* st, int* active, double2* part, unsigned* cnt,
-                                    cudaStream_t s) {
-    PROF_BEGIN(s);
-    k_update_xr<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, x, p, s_, t, r, rhat, st, active, part, cnt);
+    k_finish_x<C><<<dim3(reduce_blocks(n), R), kThreads, 0, s>>>(n, x, p, s_, st);
     PROF_END((sizeof(C) == 8 ? KK_KRYLOV_C64 : KK_KRYLOV_C128), R, s);
     return cudaGetLastError();
 }

@@ -36,7 +36,7 @@ struct KState {
     int iter;       // iterations completed in this solve
     int maxit;
     int status;     // KStatus
-    int pad;
+    int pending;    // BiCGstab: stopped with the last x update still to apply (KrylovOps::finish_x)
     QmrScalars q;   // QMR only
 };
 
@@ -44,19 +44,12 @@ static constexpr int kMaxReduceBlocks = 1024;
 int reduce_blocks(int64_t n);
 
 template <typename C> struct KrylovOps {
-    static cudaError_t init(int R, int64_t n, const C* b, C* x, C* r, C* rhat, C* p, C* v, KState* st,
+    // (s_ may be null; BiCGstab passes its s vector, which starts as b)
+    static cudaError_t init(int R, int64_t n, const C* b, C* x, C* r, C* rhat, C* p, C* v, C* s_, KState* st,
                             const double* tol_rel, const int* want, int* active, double2* part, unsigned* cnt,
                             cudaStream_t s);
-    static cudaError_t update_p(int R, int64_t n, C* p, const C* r, const C* v, const KState* st, const int* active,
-                                cudaStream_t s);
-    static cudaError_t alpha(int R, int64_t n, const C* rhat, const C* v, KState* st, int* active, double2* part,
-                             unsigned* cnt, cudaStream_t s);
-    static cudaError_t update_s(int R, int64_t n, C* s_, const C* r, const C* v, const KState* st, const int* active,
-                                cudaStream_t s);
-    static cudaError_t omega(int R, int64_t n, const C* t, const C* s_, KState* st, int* active, double2* part,
-                             unsigned* cnt, cudaStream_t s);
-    static cudaError_t update_xr(int R, int64_t n, C* x, const C* p, const C* s_, const C* t, C* r, const C* rhat,
-                                 KState* st, int* active, double2* part, unsigned* cnt, cudaStream_t s);
+    // x += alpha p + omega s for the RHS that stopped with that update pending
+    static cudaError_t finish_x(int R, int64_t n, C* x, const C* p, const C* s_, const KState* st, cudaStream_t s);
     static cudaError_t to_inner(int R, int64_t n, const double2* r64, C* bin, const double* scale, const int* active,
                                 cudaStream_t s);
     static cudaError_t accumulate(int R, int64_t n, double2* x64, const C* xin, const double* coef,

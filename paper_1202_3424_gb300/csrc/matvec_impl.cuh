@@ -108,12 +108,14 @@ template <int L, typename T> __host__ __device__ constexpr size_t zconv_smem() {
 // MODE 0 gathers X.  With the BiCGstab updates fused into the gather
 // (per-RHS scalars from st), the gathered vector is formed on the fly and
 // written back to X:  MODE 1  X = p <- r + beta (p - omega v);
-//                      MODE 2  X = s <- r - alpha v.
+//                      MODE 2  X = s <- r - alpha v;
+//                      MODE 3  X = p <- r' + beta (p - omega v) with
+//                              r' = s - omega t and x += alpha p + omega s
+//                              (fused_gather in krylov_dev.cuh).
 template <typename T, int LX, int MODE>
 __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(cx<T>)>::NT)
     k_xfwd(cx<T>* __restrict__ X, cx<T>* __restrict__ U, RowMap rm, const int* __restrict__ site_of, int nrows,
-           int64_t N, const cx<T>* __restrict__ tw, const int* __restrict__ active, const cx<T>* __restrict__ kr,
-           const cx<T>* __restrict__ kv, const KState* __restrict__ st) {
+           int64_t N, const cx<T>* __restrict__ tw, const int* __restrict__ active, FwdVecs<cx<T>> fv) {
     using C = cx<T>;
     using PL = XPlan<LX, sizeof(cx<T>)>;
     constexpr int TP = tp_x<LX, sizeof(cx<T>)>(), SP = TP + 1, NX = LX / 2;
@@ -124,13 +126,7 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
     const int row0 = blockIdx.x * TP;
     const int64_t off = ((int64_t)r * 3 + c) * N;
     C* xs = X + off;
-    C ka = czero<C>(), kb = czero<C>();
-    if constexpr (MODE == 1) {
-        ka = from2<C>(st[r].beta);
-        kb = from2<C>(st[r].omega);
-    } else if constexpr (MODE == 2) {
-        ka = from2<C>(st[r].alpha);
-    }
+    const GatherScalars<C> gs = gather_scalars<MODE, C>(fv.st, r);
     // The gather runs in three unrolled phases (site indices, then values,
     // then shared-memory stores) so that every load of a thread is in flight
     // at once: the site -> value chain is two dependent memory latencies.
@@ -141,28 +137,18 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
         const int e = threadIdx.x + i * NTH, t = e / NX, ix = e - t * NX, row = row0 + t;
         sidx[i] = (e < TP * NX && row < nrows) ? site_of[(int64_t)row * NX + ix] : -1;
     }
-    C val[NG];
+    Gathered<C> val[NG];
 #pragma unroll
     for (int i = 0; i < NG; ++i) {
         const int s = sidx[i];
-        val[i] = czero<C>();
-        if (s >= 0) {
-            if constexpr (MODE == 0) {
-                val[i] = xs[s];
-            } else if constexpr (MODE == 1) {
-                val[i] = cadd(kr[off + s], cmul(ka, csub(xs[s], cmul(kb, kv[off + s]))));
-            } else {
-                val[i] = csub(kr[off + s], cmul(ka, kv[off + s]));
-            }
-        }
+        val[i].val = czero<C>();
+        if (s >= 0) val[i] = fused_gather<MODE>(xs, fv, off, s, gs);
     }
 #pragma unroll
     for (int i = 0; i < NG; ++i) {
         const int e = threadIdx.x + i * NTH, t = e / NX, ix = e - t * NX;
-        if (e < TP * NX) buf[ix * SP + t] = val[i];
-        if constexpr (MODE != 0) {
-            if (sidx[i] >= 0) xs[sidx[i]] = val[i];
-        }
+        if (e < TP * NX) buf[ix * SP + t] = val[i].val;
+        if (sidx[i] >= 0) fused_store<MODE>(xs, fv, off, sidx[i], val[i]);
     }
     __syncthreads();
     const int t = threadIdx.x % TP, u = threadIdx.x / TP;
@@ -192,8 +178,9 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
 //                components of X (layout in PadWork::beta_tensor);
 //   kDiagSite    the scalar of site s itself, entry s + 1 (per-site materials).  Fused BiCGstab reductions
 // (FP64 totals per RHS over all blocks of that RHS, finalized by the last one):
-//   MODE 1  Y = v:  sigma = <rhat, v>          ->  alpha = rho / sigma
-//   MODE 2  Y = t:  <t, s>, <t, t> with X = s  ->  omega
+//   MODE 1  Y = v:  sigma = <rhat, v>                    ->  alpha = rho / sigma
+//   MODE 2  Y = t:  <t, s>, <t, t>, <s, s>, <rhat, s>,
+//                   <rhat, t> with X = s                 ->  finalize_omega_rho
 template <typename T, int LX, int MODE, int DIAG>
 __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(cx<T>)>::NT,
                                    xinv_min_blocks<LX, sizeof(cx<T>)>())
@@ -242,18 +229,18 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
     // operands are then loaded after it)
     constexpr bool kHoist = PL::E <= 12;
     C xv[NG], bv[NG];
-    C kh[MODE == 1 ? NG : 1];
+    C kh[MODE != 0 ? NG : 1];
     auto load_operands = [&]() {
 #pragma unroll
         for (int i = 0; i < NG; ++i) {
             const int s = sidx[i];
             xv[i] = czero<C>();
             bv[i] = czero<C>();
-            if constexpr (MODE == 1) kh[i] = czero<C>();
+            if constexpr (MODE != 0) kh[i] = czero<C>();
             if (s >= 0) {
                 xv[i] = xs[s];
                 bv[i] = diag_entry<DIAG>(br, comp_of, s, c);
-                if constexpr (MODE == 1) kh[i] = krhat[off + s];
+                if constexpr (MODE != 0) kh[i] = krhat[off + s];
             }
         }
     };
@@ -270,7 +257,7 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
     for_each_out<PL, +1, true>(u, [&](int idx, int pos) { bt[pos * SP] = v[idx]; });
     if constexpr (!kHoist) load_operands();
     __syncthreads();
-    DotAcc<C> d[2];
+    DotAcc<C> d[4];
 #pragma unroll
     for (int i = 0; i < NG; ++i) {
         const int e = threadIdx.x + i * NTH, t2 = e / NX, ix = e - t2 * NX;
@@ -285,25 +272,10 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
             }
             ys[s] = yv;
             if constexpr (MODE == 1) d[0].add_cdot(kh[i], yv);
-            if constexpr (MODE == 2) {
-                d[0].add_cdot(yv, xv[i]);
-                d[1].add_norm2(yv);
-            }
+            if constexpr (MODE == 2) fused_dots_t(d, yv, xv[i], kh[i]);
         }
     }
-    if constexpr (MODE != 0) {
-        constexpr int ND = MODE == 1 ? 1 : 2;
-        DotAcc<C> dd[ND];
-#pragma unroll
-        for (int k = 0; k < ND; ++k) dd[k] = d[k];
-        double2 acc[ND];
-        block_totals<C, ND>(dd, acc);
-        const int nb = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
-        if (last_block_combine<ND>(acc, part + (int64_t)r * part_stride, cnt + r, bid, nb) && threadIdx.x == 0) {
-            if constexpr (MODE == 1) finalize_alpha(st, active, r, acc[0]);
-            else finalize_omega(st, active, r, acc[0], acc[1].x);
-        }
-    }
+    if constexpr (MODE != 0) fused_partials<C, MODE>(d, part, r, part_stride);
 }
 
 // ---- strided pencils (y passes; y and z passes of the Green tensor) -----------
@@ -863,6 +835,27 @@ static inline RowMap row_map(const Geom& g) {
     return RowMap{g.ny, g.Ly, (int64_t)g.nz * g.Ly * g.Lx};
 }
 
+// The x-forward gathers' vectors of a fused matvec.
+template <typename T> static inline FwdVecs<cx<T>> fwd_vecs(const FusedKrylov<T>& fk) {
+    return FwdVecs<cx<T>>{fk.r, fk.v, fk.s, fk.t, fk.x, fk.st};
+}
+// The x-inverse scatter of mode 3 is that of mode 1 (v = A p, sigma).
+static inline int inverse_mode(int mode) { return mode == 3 ? 1 : mode; }
+
+// After a fused x-inverse pass of nb blocks per RHS: sum its partials and
+// update the scalars (k_fused_finalize; traced as Krylov work).
+template <typename T>
+static inline cudaError_t fused_finalize(int mode, int R, int nb, const FusedKrylov<T>& fk, int* active,
+                                         cudaStream_t st) {
+    mode = inverse_mode(mode);
+    if (mode == 0) return cudaSuccess;
+    PROF_BEGIN(st);
+    if (mode == 1) k_fused_finalize<cx<T>, 1><<<R, kFinThreads, 0, st>>>(fk.part, fk.part_stride, nb, fk.st, active);
+    else k_fused_finalize<cx<T>, 2><<<R, kFinThreads, 0, st>>>(fk.part, fk.part_stride, nb, fk.st, active);
+    PROF_END(sizeof(T) == 4 ? KK_KRYLOV_C64 : KK_KRYLOV_C128, R, st);
+    return cudaGetLastError();
+}
+
 template <typename T> struct LaunchX {
     // double-float matvecs run only the plain passes (no fused Krylov modes)
     static constexpr bool kDouble = std::is_same<T, dfl>::value;
@@ -877,17 +870,18 @@ template <typename T> struct LaunchX {
             const size_t sm = xw_smem<PL>();
             const int nrows = g.ny * g.nz;
             dim3 grid((nrows + xw_rows<PL>() - 1) / xw_rows<PL>(), 3, R);
-            auto go = [&](auto kern, const cx<T>* kr, const cx<T>* kv, const KState* ks) -> cudaError_t {
+            auto go = [&](auto kern) -> cudaError_t {
                 cudaError_t e = allow_smem(kern, sm);
                 if (e != cudaSuccess) return e;
                 PROF_BEGIN(st);
-                kern<<<grid, kXwThreads, sm, st>>>(x, u1, row_map(g), site_of, nrows, g.N, tw, active, kr, kv, ks);
+                kern<<<grid, kXwThreads, sm, st>>>(x, u1, row_map(g), site_of, nrows, g.N, tw, active, fwd_vecs(fk));
                 PROF_END(KK_XFWD_C64, R, st);
                 return cudaGetLastError();
             };
-            if (fk.mode == 1) return go(k_xfwd_w<LX, V, 1>, fk.r, fk.v, fk.st);
-            if (fk.mode == 2) return go(k_xfwd_w<LX, V, 2>, fk.r, fk.v, fk.st);
-            return go(k_xfwd_w<LX, V, 0>, nullptr, nullptr, nullptr);
+            if (fk.mode == 1) return go(k_xfwd_w<LX, V, 1>);
+            if (fk.mode == 2) return go(k_xfwd_w<LX, V, 2>);
+            if (fk.mode == 3) return go(k_xfwd_w<LX, V, 3>);
+            return go(k_xfwd_w<LX, V, 0>);
         }
         return cudaErrorInvalidValue;
     }
@@ -908,10 +902,12 @@ template <typename T> struct LaunchX {
                                                     nrows, g.N,
                                                    tw, active, fk.rhat, fk.st, fk.part, fk.cnt, fk.part_stride);
                 PROF_END(KK_XINV_C64, R, st);
-                return cudaGetLastError();
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                return fused_finalize<T>(fk.mode, R, (int)(grid.x * grid.y), fk, active, st);
             };
-            if (fk.mode == 1) return go(k_xinv_w<LX, V, 1, DIAG>);
-            if (fk.mode == 2) return go(k_xinv_w<LX, V, 2, DIAG>);
+            const int mode = inverse_mode(fk.mode);
+            if (mode == 1) return go(k_xinv_w<LX, V, 1, DIAG>);
+            if (mode == 2) return go(k_xinv_w<LX, V, 2, DIAG>);
             return go(k_xinv_w<LX, V, 0, DIAG>);
         }
         return cudaErrorInvalidValue;
@@ -930,23 +926,22 @@ template <typename T> struct LaunchX {
         const size_t sm = (size_t)LX * (TP + 1) * sizeof(cx<T>);
         const int nrows = g.ny * g.nz;
         dim3 grid((nrows + TP - 1) / TP, 3, R);
-        cudaError_t e;
+        cudaError_t e = cudaSuccess;
         PROF_BEGIN(st);
+        auto go = [&](auto kern) -> cudaError_t {
+            cudaError_t ke = allow_smem(kern, sm);
+            if (ke == cudaSuccess) kern<<<grid, NTH, sm, st>>>(x, u1, row_map(g), site_of, nrows, g.N, tw, active,
+                                                               fwd_vecs(fk));
+            return ke;
+        };
         if (fk.mode == 0 || kDouble) {
-            if ((e = allow_smem(k_xfwd<T, LX, 0>, sm)) != cudaSuccess) return e;
-            k_xfwd<T, LX, 0><<<grid, NTH, sm, st>>>(x, u1, row_map(g), site_of, nrows, g.N, tw, active, nullptr,
-                                                    nullptr, nullptr);
+            e = go(k_xfwd<T, LX, 0>);
         } else if constexpr (!kDouble) {
-            if (fk.mode == 1) {
-                if ((e = allow_smem(k_xfwd<T, LX, 1>, sm)) != cudaSuccess) return e;
-                k_xfwd<T, LX, 1><<<grid, NTH, sm, st>>>(x, u1, row_map(g), site_of, nrows, g.N, tw, active, fk.r,
-                                                        fk.v, fk.st);
-            } else {
-                if ((e = allow_smem(k_xfwd<T, LX, 2>, sm)) != cudaSuccess) return e;
-                k_xfwd<T, LX, 2><<<grid, NTH, sm, st>>>(x, u1, row_map(g), site_of, nrows, g.N, tw, active, fk.r,
-                                                        fk.v, fk.st);
-            }
+            if (fk.mode == 1) e = go(k_xfwd<T, LX, 1>);
+            else if (fk.mode == 2) e = go(k_xfwd<T, LX, 2>);
+            else e = go(k_xfwd<T, LX, 3>);
         }
+        if (e != cudaSuccess) return e;
         PROF_END(KK_XFWD_C64 + koff, R, st);
         return cudaGetLastError();
     }
@@ -971,6 +966,11 @@ template <typename T> struct LaunchX {
                                                               nrows, g.N, tw, active, fk.rhat, fk.st, fk.part,
                                                               fk.cnt, fk.part_stride);
         return cudaGetLastError();
+    }
+    // blocks per RHS of the staged x-inverse pass (the partials of its fused sums)
+    template <int LX> static int inv_blocks(const Geom& g) {
+        constexpr int TP = tp_x<LX, sizeof(cx<T>)>();
+        return (g.ny * g.nz + TP - 1) / TP * 3;
     }
     template <int LX>
     static cudaError_t inv(const Geom& g, int R, const cx<T>* u1, cx<T>* y, const cx<T>* x, const DevTarget& tg,
@@ -1008,11 +1008,13 @@ template <typename T> struct LaunchX {
         if (fk.mode == 0 || kDouble) {
             e = run(std::integral_constant<int, 0>{});
         } else if constexpr (!kDouble) {
-            e = fk.mode == 1 ? run(std::integral_constant<int, 1>{}) : run(std::integral_constant<int, 2>{});
+            e = inverse_mode(fk.mode) == 1 ? run(std::integral_constant<int, 1>{})
+                                            : run(std::integral_constant<int, 2>{});
         }
         if (e != cudaSuccess) return e;
         PROF_END(KK_XINV_C64 + koff, R, st);
-        return cudaSuccess;
+        if (fk.mode == 0 || kDouble) return cudaSuccess;
+        return fused_finalize<T>(fk.mode, R, inv_blocks<LX>(g), fk, active, st);
     }
     template <int MODE, int L, int V = 0>
     static cudaError_t strided_mode(const cx<T>* src, cx<T>* dst, int64_t pt_stride, int width, int64_t sb,

@@ -52,7 +52,7 @@ template <typename T, int LX, int LY, int MODE>
 __global__ void __launch_bounds__(SliceCfg<LX, LY, sizeof(cx<T>)>::NTH)
     k_xyfwd(cx<T>* __restrict__ X, cx<T>* __restrict__ U2, const int* __restrict__ site_of, int64_t N,
             const cx<T>* __restrict__ twx, const cx<T>* __restrict__ twy, const int* __restrict__ active,
-            const cx<T>* __restrict__ kr, const cx<T>* __restrict__ kv, const KState* __restrict__ st) {
+            FwdVecs<cx<T>> fv) {
     using C = cx<T>;
     using CF = SliceCfg<LX, LY, sizeof(C)>;
     using PX = typename CF::PX;
@@ -65,13 +65,7 @@ __global__ void __launch_bounds__(SliceCfg<LX, LY, sizeof(cx<T>)>::NTH)
     if (active != nullptr && active[r] == 0) return;
     const int64_t off = ((int64_t)r * 3 + c) * N;
     C* xs = X + off;
-    C ka = czero<C>(), kb = czero<C>();
-    if constexpr (MODE == 1) {
-        ka = from2<C>(st[r].beta);
-        kb = from2<C>(st[r].omega);
-    } else if constexpr (MODE == 2) {
-        ka = from2<C>(st[r].alpha);
-    }
+    const GatherScalars<C> gs = gather_scalars<MODE, C>(fv.st, r);
     // gather the slice's sites: site indices first, then values (two
     // dependent latencies, every load of a thread in flight at once)
     constexpr int NG = (NY * NX + NTH - 1) / NTH;
@@ -83,28 +77,18 @@ __global__ void __launch_bounds__(SliceCfg<LX, LY, sizeof(cx<T>)>::NTH)
             const int e = threadIdx.x + i * NTH;
             sidx[i] = e < NY * NX ? so[e] : -1;
         }
-        C val[NG];
+        Gathered<C> val[NG];
 #pragma unroll
         for (int i = 0; i < NG; ++i) {
             const int s = sidx[i];
-            val[i] = czero<C>();
-            if (s >= 0) {
-                if constexpr (MODE == 0) {
-                    val[i] = xs[s];
-                } else if constexpr (MODE == 1) {
-                    val[i] = cadd(kr[off + s], cmul(ka, csub(xs[s], cmul(kb, kv[off + s]))));
-                } else {
-                    val[i] = csub(kr[off + s], cmul(ka, kv[off + s]));
-                }
-            }
+            val[i].val = czero<C>();
+            if (s >= 0) val[i] = fused_gather<MODE>(xs, fv, off, s, gs);
         }
 #pragma unroll
         for (int i = 0; i < NG; ++i) {
             const int e = threadIdx.x + i * NTH;
-            if (e < NY * NX) plane[(e % NX) * SPY + e / NX] = val[i];
-            if constexpr (MODE != 0) {
-                if (sidx[i] >= 0) xs[sidx[i]] = val[i];
-            }
+            if (e < NY * NX) plane[(e % NX) * SPY + e / NX] = val[i].val;
+            if (sidx[i] >= 0) fused_store<MODE>(xs, fv, off, sidx[i], val[i]);
         }
     }
     __syncthreads();
@@ -236,7 +220,7 @@ __global__ void __launch_bounds__(SliceCfg<LX, LY, sizeof(cx<T>)>::NTH)
         }
     }
     // diagonal term, scatter, fused Krylov dot products
-    DotAcc<C> d[2];
+    DotAcc<C> d[4];
 #pragma unroll
     for (int i = 0; i < NG; ++i) {
         const int e = threadIdx.x + i * NTH, s = sidx[i];
@@ -245,25 +229,10 @@ __global__ void __launch_bounds__(SliceCfg<LX, LY, sizeof(cx<T>)>::NTH)
             const C yv = cadd(plane[(e % NX) * SPY + e / NX], cmul(br[comp_of[s]], xv[i]));
             ys[s] = yv;
             if constexpr (MODE == 1) d[0].add_cdot(krhat[off + s], yv);
-            if constexpr (MODE == 2) {
-                d[0].add_cdot(yv, xv[i]);
-                d[1].add_norm2(yv);
-            }
+            if constexpr (MODE == 2) fused_dots_t(d, yv, xv[i], krhat[off + s]);
         }
     }
-    if constexpr (MODE != 0) {
-        constexpr int ND = MODE == 1 ? 1 : 2;
-        DotAcc<C> dd[ND];
-#pragma unroll
-        for (int k = 0; k < ND; ++k) dd[k] = d[k];
-        double2 acc[ND];
-        block_totals<C, ND>(dd, acc);
-        const int nb = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
-        if (last_block_combine<ND>(acc, part + (int64_t)r * part_stride, cnt + r, bid, nb) && threadIdx.x == 0) {
-            if constexpr (MODE == 1) finalize_alpha(st, active, r, acc[0]);
-            else finalize_omega(st, active, r, acc[0], acc[1].x);
-        }
-    }
+    if constexpr (MODE != 0) fused_partials<C, MODE>(d, part, r, part_stride);
 }
 
 // ---- launchers ---------------------------------------------------------------------
@@ -279,21 +248,21 @@ template <typename T> struct LaunchSlice {
             dim3 grid(g.nz, 3, R);
             cudaError_t e;
             PROF_BEGIN(st);
+            auto go = [&](auto kern) -> cudaError_t {
+                cudaError_t ke = allow_smem(kern, CF::smem);
+                if (ke == cudaSuccess)
+                    kern<<<grid, CF::NTH, CF::smem, st>>>(x, u2, site_of, g.N, twx, twy, active, fwd_vecs(fk));
+                return ke;
+            };
+            e = cudaSuccess;
             if (fk.mode == 0 || kDouble) {
-                if ((e = allow_smem(k_xyfwd<T, LX, LY, 0>, CF::smem)) != cudaSuccess) return e;
-                k_xyfwd<T, LX, LY, 0><<<grid, CF::NTH, CF::smem, st>>>(x, u2, site_of, g.N, twx, twy, active, nullptr,
-                                                                      nullptr, nullptr);
+                e = go(k_xyfwd<T, LX, LY, 0>);
             } else if constexpr (!kDouble) {
-                if (fk.mode == 1) {
-                    if ((e = allow_smem(k_xyfwd<T, LX, LY, 1>, CF::smem)) != cudaSuccess) return e;
-                    k_xyfwd<T, LX, LY, 1><<<grid, CF::NTH, CF::smem, st>>>(x, u2, site_of, g.N, twx, twy, active,
-                                                                          fk.r, fk.v, fk.st);
-                } else {
-                    if ((e = allow_smem(k_xyfwd<T, LX, LY, 2>, CF::smem)) != cudaSuccess) return e;
-                    k_xyfwd<T, LX, LY, 2><<<grid, CF::NTH, CF::smem, st>>>(x, u2, site_of, g.N, twx, twy, active,
-                                                                          fk.r, fk.v, fk.st);
-                }
+                if (fk.mode == 1) e = go(k_xyfwd<T, LX, LY, 1>);
+                else if (fk.mode == 2) e = go(k_xyfwd<T, LX, LY, 2>);
+                else e = go(k_xyfwd<T, LX, LY, 3>);
             }
+            if (e != cudaSuccess) return e;
             PROF_END(kind, R, st);
             return cudaGetLastError();
         }
@@ -315,7 +284,7 @@ template <typename T> struct LaunchSlice {
                                                                       beta_stride, g.N, twx, twy, active, nullptr,
                                                                       nullptr, nullptr, nullptr, 0);
             } else if constexpr (!kDouble) {
-                if (fk.mode == 1) {
+                if (inverse_mode(fk.mode) == 1) {
                     if ((e = allow_smem(k_yxinv<T, LX, LY, 1>, CF::smem)) != cudaSuccess) return e;
                     k_yxinv<T, LX, LY, 1><<<grid, CF::NTH, CF::smem, st>>>(u2, y, x, tg.site_of, tg.comp_of, beta,
                                                                           beta_stride, g.N, twx, twy, active,
@@ -330,7 +299,9 @@ template <typename T> struct LaunchSlice {
                 }
             }
             PROF_END(kind, R, st);
-            return cudaGetLastError();
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if (fk.mode == 0 || kDouble) return cudaSuccess;
+            return fused_finalize<T>(fk.mode, R, (int)(grid.x * grid.y), fk, active, st);
         }
     }
 };

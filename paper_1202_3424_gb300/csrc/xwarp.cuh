@@ -129,6 +129,11 @@ template <class PL> __host__ __device__ constexpr int xwf_min_blocks() { return 
 template <class PL> __host__ __device__ constexpr int xwi_min_blocks() {
     return PL::E <= 8 ? 8 : (PL::E <= 12 ? 6 : (PL::E <= 16 ? 4 : 2));
 }
+// the second BiCGstab scatter (MODE 2) keeps rhat and five sums besides: the
+// next larger budget (85 registers at 8 points per lane, 102 at 12)
+template <class PL, int MODE> __host__ __device__ constexpr int xwi_mode_min_blocks() {
+    return MODE != 2 ? xwi_min_blocks<PL>() : (PL::E <= 8 ? 6 : (PL::E <= 12 ? 5 : xwi_min_blocks<PL>()));
+}
 
 // Up to 256 points the block copies the twiddle table to shared memory
 // (after its global loads are issued): the stage twiddles of different lanes
@@ -148,14 +153,12 @@ template <int L> __device__ __forceinline__ const float2* stage_twiddles(float2*
 
 // ---- x-forward: gather + row FFT, warp-local pencils -------------------------------
 // Same result as k_xfwd: rows (iy, iz) of the padded-to-LX/2 lattice, sites
-// x < LX/2 gathered through the lattice -> site map; MODE 1 and 2 form the
-// BiCGstab update in the gather and write it back to X.
+// x < LX/2 gathered through the lattice -> site map; MODE 1-3 form the
+// BiCGstab update in the gather and write it back (fused_gather).
 template <int LX, int V, int MODE>
 __global__ void __launch_bounds__(kXwThreads, xwf_min_blocks<XwPlan<LX, V>>())
     k_xfwd_w(float2* __restrict__ X, float2* __restrict__ U, RowMap rm, const int* __restrict__ site_of, int nrows,
-             int64_t N,
-             const float2* __restrict__ tw, const int* __restrict__ active, const float2* __restrict__ kr,
-             const float2* __restrict__ kv, const KState* __restrict__ st) {
+             int64_t N, const float2* __restrict__ tw, const int* __restrict__ active, FwdVecs<float2> fv) {
     using C = float2;
     using PL = XwPlan<LX, V>;
     constexpr int NT = PL::NT, E = PL::E, NX = LX / 2, RPB = xw_rows<PL>(), PS = xw_plane<PL>();
@@ -169,13 +172,7 @@ __global__ void __launch_bounds__(kXwThreads, xwf_min_blocks<XwPlan<LX, V>>())
     C* plane = reinterpret_cast<C*>(smem_raw) + p * PS;
     const int64_t off = ((int64_t)r * 3 + c) * N;
     C* xs = X + off;
-    C ka = czero<C>(), kb = czero<C>();
-    if constexpr (MODE == 1) {
-        ka = from2<C>(st[r].beta);
-        kb = from2<C>(st[r].omega);
-    } else if constexpr (MODE == 2) {
-        ka = from2<C>(st[r].alpha);
-    }
+    const GatherScalars<C> gs = gather_scalars<MODE, C>(fv.st, r);
     // site indices of the first stage's inputs (positions < LX/2), then the
     // values: all loads of the lane are in flight before the first is used
     int sidx[NB0 * JN];
@@ -185,25 +182,30 @@ __global__ void __launch_bounds__(kXwThreads, xwf_min_blocks<XwPlan<LX, V>>())
         for (int j = 0; j < JN; ++j)
             sidx[q * JN + j] = ok ? site_of[(int64_t)row * NX + u + q * NT + j * (LX / R0)] : -1;
     C v[E];
+    Gathered<C> gv[MODE == 3 ? NB0 * JN : 1];  // (MODE 3 keeps r and x for the stores)
 #pragma unroll
     for (int q = 0; q < NB0; ++q)
 #pragma unroll
         for (int j = 0; j < JN; ++j) {
             const int s = sidx[q * JN + j];
-            C val = czero<C>();
-            if (s >= 0) {
-                if constexpr (MODE == 0) val = xs[s];
-                else if constexpr (MODE == 1) val = cadd(kr[off + s], cmul(ka, csub(xs[s], cmul(kb, kv[off + s]))));
-                else val = csub(kr[off + s], cmul(ka, kv[off + s]));
-            }
-            v[q * R0 + j] = val;
+            Gathered<C> o;
+            o.val = czero<C>();
+            if (s >= 0) o = fused_gather<MODE>(xs, fv, off, s, gs);
+            v[q * R0 + j] = o.val;
+            if constexpr (MODE == 3) gv[q * JN + j] = o;
         }
     if constexpr (MODE != 0) {
 #pragma unroll
         for (int q = 0; q < NB0; ++q)
 #pragma unroll
-            for (int j = 0; j < JN; ++j)
-                if (sidx[q * JN + j] >= 0) xs[sidx[q * JN + j]] = v[q * R0 + j];
+            for (int j = 0; j < JN; ++j) {
+                const int s = sidx[q * JN + j];
+                if (s < 0) continue;
+                Gathered<C> o;
+                if constexpr (MODE == 3) o = gv[q * JN + j];
+                else o.val = v[q * R0 + j];
+                fused_store<MODE>(xs, fv, off, s, o);
+            }
     }
     const C* tws = stage_twiddles<LX>(reinterpret_cast<C*>(smem_raw) + RPB * PS, tw);
     auto ld = [&](int pos) { return plane[pos]; };
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(kXwThreads, xwf_min_blocks<XwPlan<LX, V>>())
 // Same result as k_xinv (Y = conv + (1/alpha) X at the occupied sites, the
 // DIAG kinds, and the fused BiCGstab reductions of MODE 1 and 2).
 template <int LX, int V, int MODE, int DIAG>
-__global__ void __launch_bounds__(kXwiThreads, xwi_min_blocks<XwPlan<LX, V>>())
+__global__ void __launch_bounds__(kXwiThreads, (xwi_mode_min_blocks<XwPlan<LX, V>, MODE>()))
     k_xinv_w(const float2* __restrict__ U, RowMap rm, float2* __restrict__ Y, const float2* __restrict__ X,
              const int* __restrict__ site_of, const uint8_t* __restrict__ comp_of, const float2* __restrict__ beta,
              int beta_stride, int nrows, int64_t N, const float2* __restrict__ tw, int* __restrict__ active,
@@ -261,18 +263,18 @@ __global__ void __launch_bounds__(kXwiThreads, xwi_min_blocks<XwPlan<LX, V>>())
     // the operands are then loaded after it)
     constexpr bool kHoist = E <= 12;
     C xv[NO], bv[NO];
-    C kh[MODE == 1 ? NO : 1];
+    C kh[MODE != 0 ? NO : 1];
     auto load_operands = [&]() {
 #pragma unroll
         for (int k = 0; k < NO; ++k) {
             const int s = sidx[k];
             xv[k] = czero<C>();
             bv[k] = czero<C>();
-            if constexpr (MODE == 1) kh[k] = czero<C>();
+            if constexpr (MODE != 0) kh[k] = czero<C>();
             if (s >= 0) {
                 xv[k] = xs[s];
                 bv[k] = diag_entry<DIAG>(br, comp_of, s, c);
-                if constexpr (MODE == 1) kh[k] = krhat[off + s];
+                if constexpr (MODE != 0) kh[k] = krhat[off + s];
             }
         }
     };
@@ -281,7 +283,7 @@ __global__ void __launch_bounds__(kXwiThreads, xwi_min_blocks<XwPlan<LX, V>>())
     auto stf = [&](int pos, C val) { plane[pos] = val; };
     fft_stages<C, PL, +1, 0, decltype(ld), decltype(stf), true, WarpSwz<PL>>(v, u, tw, ld, stf, false);
     if constexpr (!kHoist) load_operands();
-    DotAcc<C> d[2];
+    DotAcc<C> d[4];
 #pragma unroll
     for (int q = 0; q < NBL; ++q)
 #pragma unroll
@@ -297,25 +299,10 @@ __global__ void __launch_bounds__(kXwiThreads, xwi_min_blocks<XwPlan<LX, V>>())
                 }
                 ys[s] = yv;
                 if constexpr (MODE == 1) d[0].add_cdot(kh[k], yv);
-                if constexpr (MODE == 2) {
-                    d[0].add_cdot(yv, xv[k]);
-                    d[1].add_norm2(yv);
-                }
+                if constexpr (MODE == 2) fused_dots_t(d, yv, xv[k], kh[k]);
             }
         }
-    if constexpr (MODE != 0) {
-        constexpr int ND = MODE == 1 ? 1 : 2;
-        DotAcc<C> dd[ND];
-#pragma unroll
-        for (int k = 0; k < ND; ++k) dd[k] = d[k];
-        double2 acc[ND];
-        block_totals<C, ND>(dd, acc);
-        const int nb = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
-        if (last_block_combine<ND>(acc, part + (int64_t)r * part_stride, cnt + r, bid, nb) && threadIdx.x == 0) {
-            if constexpr (MODE == 1) finalize_alpha(st, active, r, acc[0]);
-            else finalize_omega(st, active, r, acc[0], acc[1].x);
-        }
-    }
+    if constexpr (MODE != 0) fused_partials<C, MODE>(d, part, r, part_stride);
 }
 
 }  // namespace dda

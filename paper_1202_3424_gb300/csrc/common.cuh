@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <cstdio>
+#include <type_traits>
 #include <string>
 
 namespace dda {
@@ -72,6 +73,24 @@ template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
     C r;
     r.x = a.x * b.x - a.y * b.y;
     r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+// g0 p0 + g1 p1 + g2 p2 (a row of the 3x3 product in Fourier space) as one
+// FMA chain per part: 12 instructions for complex64 instead of the 16 of
+// three products and two sums (IEEE rules forbid the compiler this
+// reassociation)
+template <typename C> __host__ __device__ __forceinline__ C cdot3(C g0, C p0, C g1, C p1, C g2, C p2) {
+    C r;
+    if constexpr (std::is_same<C, float2>::value) {
+        r.x = fmaf(g0.x, p0.x, fmaf(-g0.y, p0.y, fmaf(g1.x, p1.x, fmaf(-g1.y, p1.y, fmaf(g2.x, p2.x, -g2.y * p2.y)))));
+        r.y = fmaf(g0.x, p0.y, fmaf(g0.y, p0.x, fmaf(g1.x, p1.y, fmaf(g1.y, p1.x, fmaf(g2.x, p2.y, g2.y * p2.x)))));
+    } else if constexpr (std::is_same<C, double2>::value) {
+        r.x = fma(g0.x, p0.x, fma(-g0.y, p0.y, fma(g1.x, p1.x, fma(-g1.y, p1.y, fma(g2.x, p2.x, -g2.y * p2.y)))));
+        r.y = fma(g0.x, p0.y, fma(g0.y, p0.x, fma(g1.x, p1.y, fma(g1.y, p1.x, fma(g2.x, p2.y, g2.y * p2.x)))));
+    } else {
+        r.x = g0.x * p0.x - g0.y * p0.y + (g1.x * p1.x - g1.y * p1.y) + (g2.x * p2.x - g2.y * p2.y);
+        r.y = g0.x * p0.y + g0.y * p0.x + (g1.x * p1.y + g1.y * p1.x) + (g2.x * p2.y + g2.y * p2.x);
+    }
     return r;
 }
 // a * conj(b)

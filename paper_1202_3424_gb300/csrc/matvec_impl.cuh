@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(3 * tp_z<LZ, T>() * ZPlan<LZ>::NT, zconv_min_b
             }
             const int kr = row(kz);
             const C pa = pb[kr * SP], pbv = pb[(ROWS + kr) * SP], pc = pb[(2 * ROWS + kr) * SP];
-            v[idx] = cadd(cadd(cmul(a0, pa), cmul(a1, pbv)), cmul(a2, pc));
+            v[idx] = cdot3(a0, pa, a1, pbv, a2, pc);
         });
         pencil_fft_regs<C, PL, +1>(v, u, tws, ld, st);
         for_each_out<PL, +1, true>(u, [&](int idx, int pos) {
@@ -600,9 +600,9 @@ __global__ void __launch_bounds__(zreg_threads<ZrPlan<LZ, V>>(), zreg_min_blocks
                 gyz = cscale(gyz, T(-1));
             }
             const C px = vc[0][idx], py = vc[1][idx], pz = vc[2][idx];
-            vc[0][idx] = cadd(cadd(cmul(gxx, px), cmul(gxy, py)), cmul(gxz, pz));
-            vc[1][idx] = cadd(cadd(cmul(gxy, px), cmul(gyy, py)), cmul(gyz, pz));
-            vc[2][idx] = cadd(cadd(cmul(gxz, px), cmul(gyz, py)), cmul(gzz, pz));
+            vc[0][idx] = cdot3(gxx, px, gxy, py, gxz, pz);
+            vc[1][idx] = cdot3(gxy, px, gyy, py, gyz, pz);
+            vc[2][idx] = cdot3(gxz, px, gyz, py, gzz, pz);
         });
         fft_stages_np<C, PL, +1, 0, 3>(vc, u, tws, ld, st, false);
 #pragma unroll
@@ -740,9 +740,9 @@ __global__ void __launch_bounds__(zreg_threads<ZrPlan<LZ, V>>(), zreg_min_blocks
             if (fx != fz) gxz = cscale(gxz, T(-1));
             if (fy != fz) gyz = cscale(gyz, T(-1));
             const C px = vc[0][idx], py = vc[1][idx], pz = vc[2][idx];
-            vc[0][idx] = cadd(cadd(cmul(gxx, px), cmul(gxy, py)), cmul(gxz, pz));
-            vc[1][idx] = cadd(cadd(cmul(gxy, px), cmul(gyy, py)), cmul(gyz, pz));
-            vc[2][idx] = cadd(cadd(cmul(gxz, px), cmul(gyz, py)), cmul(gzz, pz));
+            vc[0][idx] = cdot3(gxx, px, gxy, py, gxz, pz);
+            vc[1][idx] = cdot3(gxy, px, gyy, py, gyz, pz);
+            vc[2][idx] = cdot3(gxz, px, gyz, py, gzz, pz);
         });
         fft_stages_np<C, PL, +1, 0, 3>(vc, u, tws, ld, st, false);
 #pragma unroll

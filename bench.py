@@ -172,6 +172,14 @@ class ClockSampler:
 
 
 # --------------------------------------------------- algorithmic traffic ----
+def target_info(ctx, w):
+    """The context's target description plus the number of x rows (z, y)
+    that hold at least one site."""
+    info = dict(ctx.info())
+    info["xrows"] = int(np.count_nonzero(np.asarray(w.grid).any(axis=2)))
+    return info
+
+
 def pass_bytes(kind, info, R, ncomp_tables=1):
     """Algorithmic bytes of one launch of a matvec pass over R right-hand sides:
     the data the pass must read and write once (compact vectors, padded
@@ -195,7 +203,10 @@ def pass_bytes(kind, info, R, ncomp_tables=1):
     if kind.startswith("z_conv"):
         return R * 2 * u2 + oct_
     if kind.startswith("x_inv"):
-        return R * (u1 + 2 * vec) + 4 * M + N
+        # only the x rows holding sites are read and transformed (a row
+        # without sites has no output)
+        rows = info.get("xrows", ny * nz)
+        return R * (3 * rows * Lx * s + 2 * vec) + 4 * rows * nx + N
     return None
 
 
@@ -294,7 +305,7 @@ def run_gb300(args):
     ctx.set_schedule(args.zpass)
     ctx.set_xpass((args.xpass, args.xpass if args.xinv is None else args.xinv))
     ctx.set_ypass(args.ypass)
-    info = ctx.info()
+    info = target_info(ctx, w)
     N = info["ndipoles"]
     P_dev = torch.empty((R, 3, N), dtype=torch.complex128, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
@@ -507,7 +518,7 @@ def ellipsoid_sweep(dda, dev, stream, flush, dist, steps=3, warmup=2):
     ctx.set_target(w.grid)
     ctx.set_materials(w.m)
     ctx.prepare_size_parameter(w.x, dda.Precision.FP32_REFINED)
-    info = ctx.info()
+    info = target_info(ctx, w)
     N = info["ndipoles"]
     P = torch.empty((R, 3, N), dtype=torch.complex128, device=dev)
 
@@ -792,7 +803,7 @@ def run_matvec_only(args):
         dda.dda_matvec_device(ctx.handle, prec, k, e, x, y)
     kst = read_profile(dda, ctx)
     L.dda_profile_enable(ctx.handle, 0)
-    info = ctx.info()
+    info = target_info(ctx, w)
     kern = {}
     for name, v in kst.items():
         avg = v["ms"] / v["launches"]

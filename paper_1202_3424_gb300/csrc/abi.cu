@@ -67,7 +67,7 @@ struct dda_ctx {
     bool has_target = false;
     int max_code = 0;
     DevTarget tg;
-    DevMem m_site_of, m_lat_of, m_comp_of;
+    DevMem m_site_of, m_lat_of, m_comp_of, m_rows;
 
     // materials
     std::vector<cd> m;
@@ -1263,6 +1263,7 @@ dda_status dda_destroy(dda_ctx* ctx) {
     if (ctx->graph.exec) cudaGraphExecDestroy(ctx->graph.exec);
     for (auto& m : ctx->pool) free_mem(m);
     free_mem(ctx->m_site_of);
+    free_mem(ctx->m_rows);
     free_mem(ctx->m_lat_of);
     free_mem(ctx->m_comp_of);
     free_mem(ctx->m_gh64);
@@ -1323,6 +1324,17 @@ dda_status dda_set_target(dda_ctx* ctx, int nx, int ny, int nz, const uint8_t* c
             }
     if (lat_of.empty()) return ctx->fail(DDA_ERR_ARG, "target has no occupied site");
     g.N = (int64_t)lat_of.size();
+    // the x rows with at least one site (the x-inverse pass transforms only these)
+    std::vector<int> rows;
+    for (int iz = 0; iz < g.nz; ++iz)
+        for (int iy = 0; iy < g.ny; ++iy) {
+            const int64_t r0 = ((int64_t)iz * g.ny + iy) * g.nx;
+            for (int ix = 0; ix < g.nx; ++ix)
+                if (site_of[r0 + ix] >= 0) {
+                    rows.push_back(iz * g.ny + iy);
+                    break;
+                }
+        }
     cudaSetDevice(ctx->device);
     ctx->prepared = false;
     ctx->has32 = false;
@@ -1333,9 +1345,13 @@ dda_status dda_set_target(dda_ctx* ctx, int nx, int ny, int nz, const uint8_t* c
     CU(cudaMemcpy(ctx->m_site_of.p, site_of.data(), M * sizeof(int), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(ctx->m_lat_of.p, lat_of.data(), g.N * sizeof(int), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(ctx->m_comp_of.p, comp_of.data(), g.N, cudaMemcpyHostToDevice));
+    if ((s = ensure(ctx, ctx->m_rows, rows.size() * sizeof(int))) != DDA_OK) return s;
+    CU(cudaMemcpy(ctx->m_rows.p, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice));
     ctx->tg.site_of = (int*)ctx->m_site_of.p;
     ctx->tg.lat_of = (int*)ctx->m_lat_of.p;
     ctx->tg.comp_of = (uint8_t*)ctx->m_comp_of.p;
+    ctx->tg.rows = (const int*)ctx->m_rows.p;
+    ctx->tg.nrows = (int)rows.size();
     ctx->g = g;
     ctx->zsched.clear();
     ctx->max_code = maxc;

@@ -38,6 +38,11 @@ struct DevTarget {
     int* site_of = nullptr;        // [M] lattice -> site index, -1 for vacuum
     int* lat_of = nullptr;         // [N] site -> lattice index
     uint8_t* comp_of = nullptr;    // [N] composition code 1..ncomp
+    // the x rows (iz * ny + iy of the extended lattice) holding at least one
+    // site, ascending: the x-inverse pass reads and transforms only these
+    // (a row without sites has no output); null: every row
+    const int* rows = nullptr;
+    int nrows = 0;
 };
 
 // Twiddle tables, one per padded axis: exp(-2 pi i m/L), m < L.

@@ -186,7 +186,8 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
                                    xinv_min_blocks<LX, sizeof(cx<T>)>())
     k_xinv(const cx<T>* __restrict__ U, RowMap rm, cx<T>* __restrict__ Y, const cx<T>* __restrict__ X,
            const int* __restrict__ site_of, const uint8_t* __restrict__ comp_of, const cx<T>* __restrict__ beta,
-           int beta_stride, int nrows, int64_t N, const cx<T>* __restrict__ tw, int* __restrict__ active,
+           int beta_stride, const int* __restrict__ rows, int nrows, int64_t N, const cx<T>* __restrict__ tw,
+           int* __restrict__ active,
            const cx<T>* __restrict__ krhat, KState* __restrict__ st, double2* __restrict__ part,
            unsigned* __restrict__ cnt, int part_stride) {
     using C = cx<T>;
@@ -196,7 +197,12 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
     C* buf = reinterpret_cast<C*>(smem_raw);
     const int c = blockIdx.y, r = blockIdx.z;
     if (active != nullptr && active[r] == 0) return;
+    // list entries row0 .. row0 + TP - 1 (rows: the rows with sites, else all)
     const int row0 = blockIdx.x * TP;
+    auto row_of = [&](int t2) {
+        const int li = row0 + t2;
+        return li < nrows ? (rows != nullptr ? rows[li] : li) : -1;
+    };
     const int64_t off = ((int64_t)r * 3 + c) * N;
     const C* xs = X + off;
     C* ys = Y + off;
@@ -211,13 +217,13 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
         C rin[NI];
 #pragma unroll
         for (int i = 0; i < NI; ++i) {
-            const int e = threadIdx.x + i * NTH, t2 = e / LX, x = e - t2 * LX, row = row0 + t2;
-            rin[i] = (e < TP * LX && row < nrows) ? U[rm.at(r, c, row, LX) + x] : czero<C>();
+            const int e = threadIdx.x + i * NTH, t2 = e / LX, x = e - t2 * LX, row = e < TP * LX ? row_of(t2) : -1;
+            rin[i] = row >= 0 ? U[rm.at(r, c, row, LX) + x] : czero<C>();
         }
 #pragma unroll
         for (int i = 0; i < NG; ++i) {
-            const int e = threadIdx.x + i * NTH, t2 = e / NX, ix = e - t2 * NX, row = row0 + t2;
-            sidx[i] = (e < TP * NX && row < nrows) ? site_of[(int64_t)row * NX + ix] : -1;
+            const int e = threadIdx.x + i * NTH, t2 = e / NX, ix = e - t2 * NX, row = e < TP * NX ? row_of(t2) : -1;
+            sidx[i] = row >= 0 ? site_of[(int64_t)row * NX + ix] : -1;
         }
 #pragma unroll
         for (int i = 0; i < NI; ++i) {
@@ -892,15 +898,15 @@ template <typename T> struct LaunchX {
         if constexpr (kWarpX) {
             using PL = XwPlan<LX, V>;
             const size_t sm = (size_t)xwi_rows<PL>() * xw_plane<PL>() * sizeof(float2);
-            const int nrows = g.ny * g.nz;
+            const int nrows = tg.rows != nullptr ? tg.nrows : g.ny * g.nz;
             dim3 grid((nrows + xwi_rows<PL>() - 1) / xwi_rows<PL>(), 3, R);
             auto go = [&](auto kern) -> cudaError_t {
                 cudaError_t e = allow_smem(kern, sm);
                 if (e != cudaSuccess) return e;
                 PROF_BEGIN(st);
                 kern<<<grid, kXwiThreads, sm, st>>>(u1, row_map(g), y, x, tg.site_of, tg.comp_of, beta, beta_stride,
-                                                    nrows, g.N,
-                                                   tw, active, fk.rhat, fk.st, fk.part, fk.cnt, fk.part_stride);
+                                                    tg.rows, nrows, g.N, tw, active, fk.rhat, fk.st, fk.part, fk.cnt,
+                                                    fk.part_stride);
                 PROF_END(KK_XINV_C64, R, st);
                 if ((e = cudaGetLastError()) != cudaSuccess) return e;
                 return fused_finalize<T>(fk.mode, R, (int)(grid.x * grid.y), fk, active, st);
@@ -951,26 +957,25 @@ template <typename T> struct LaunchX {
                                 const FusedKrylov<T>& fk, cudaStream_t st) {
         constexpr int TP = tp_x<LX, sizeof(cx<T>)>(), NTH = TP * XPlan<LX, sizeof(cx<T>)>::NT;
         const size_t sm = (size_t)LX * (TP + 1) * sizeof(cx<T>);
-        const int nrows = g.ny * g.nz;
+        const int nrows = tg.rows != nullptr ? tg.nrows : g.ny * g.nz;
         dim3 grid((nrows + TP - 1) / TP, 3, R);
         cudaError_t e;
         if ((e = allow_smem(k_xinv<T, LX, MODE, DIAG>, sm)) != cudaSuccess) return e;
         if constexpr (MODE == 0)
             k_xinv<T, LX, 0, DIAG><<<grid, NTH, sm, st>>>(u1, row_map(g), y, x, tg.site_of, tg.comp_of, beta,
-                                                         beta_stride,
-                                                           nrows, g.N, tw, active, nullptr, nullptr, nullptr,
-                                                           nullptr, 0);
+                                                         beta_stride, tg.rows, nrows, g.N, tw, active, nullptr,
+                                                         nullptr, nullptr, nullptr, 0);
         else
             k_xinv<T, LX, MODE, DIAG><<<grid, NTH, sm, st>>>(u1, row_map(g), y, x, tg.site_of, tg.comp_of, beta,
-                                                            beta_stride,
-                                                              nrows, g.N, tw, active, fk.rhat, fk.st, fk.part,
-                                                              fk.cnt, fk.part_stride);
+                                                            beta_stride, tg.rows, nrows, g.N, tw, active, fk.rhat,
+                                                            fk.st, fk.part, fk.cnt, fk.part_stride);
         return cudaGetLastError();
     }
     // blocks per RHS of the staged x-inverse pass (the partials of its fused sums)
-    template <int LX> static int inv_blocks(const Geom& g) {
+    template <int LX> static int inv_blocks(const Geom& g, const DevTarget& tg) {
         constexpr int TP = tp_x<LX, sizeof(cx<T>)>();
-        return (g.ny * g.nz + TP - 1) / TP * 3;
+        const int nrows = tg.rows != nullptr ? tg.nrows : g.ny * g.nz;
+        return (nrows + TP - 1) / TP * 3;
     }
     template <int LX>
     static cudaError_t inv(const Geom& g, int R, const cx<T>* u1, cx<T>* y, const cx<T>* x, const DevTarget& tg,
@@ -1014,7 +1019,7 @@ template <typename T> struct LaunchX {
         if (e != cudaSuccess) return e;
         PROF_END(KK_XINV_C64 + koff, R, st);
         if (fk.mode == 0 || kDouble) return cudaSuccess;
-        return fused_finalize<T>(fk.mode, R, inv_blocks<LX>(g), fk, active, st);
+        return fused_finalize<T>(fk.mode, R, inv_blocks<LX>(g, tg), fk, active, st);
     }
     template <int MODE, int L, int V = 0>
     static cudaError_t strided_mode(const cx<T>* src, cx<T>* dst, int64_t pt_stride, int width, int64_t sb,

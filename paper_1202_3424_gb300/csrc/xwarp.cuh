@@ -224,7 +224,8 @@ template <int LX, int V, int MODE, int DIAG>
 __global__ void __launch_bounds__(kXwiThreads, (xwi_mode_min_blocks<XwPlan<LX, V>, MODE>()))
     k_xinv_w(const float2* __restrict__ U, RowMap rm, float2* __restrict__ Y, const float2* __restrict__ X,
              const int* __restrict__ site_of, const uint8_t* __restrict__ comp_of, const float2* __restrict__ beta,
-             int beta_stride, int nrows, int64_t N, const float2* __restrict__ tw, int* __restrict__ active,
+             int beta_stride, const int* __restrict__ rows, int nrows, int64_t N, const float2* __restrict__ tw,
+             int* __restrict__ active,
              const float2* __restrict__ krhat, KState* __restrict__ st, double2* __restrict__ part,
              unsigned* __restrict__ cnt, int part_stride) {
     using C = float2;
@@ -236,8 +237,10 @@ __global__ void __launch_bounds__(kXwiThreads, (xwi_mode_min_blocks<XwPlan<LX, V
     const int c = blockIdx.y, r = blockIdx.z;
     if (active != nullptr && active[r] == 0) return;
     const int p = threadIdx.x / NT, u = threadIdx.x % NT;
-    const int row = blockIdx.x * RPB + p;
-    const bool ok = row < nrows;
+    // row list entry blockIdx.x * RPB + p (rows: the rows with sites, else all)
+    const int li = blockIdx.x * RPB + p;
+    const bool ok = li < nrows;
+    const int row = ok ? (rows != nullptr ? rows[li] : li) : 0;
     C* plane = reinterpret_cast<C*>(smem_raw) + p * PS;
     const int64_t off = ((int64_t)r * 3 + c) * N;
     const C* xs = X + off;

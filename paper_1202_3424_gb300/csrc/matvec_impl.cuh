@@ -84,9 +84,12 @@ template <int L, typename T> __host__ __device__ constexpr int tp_z() {
     }
     return tp;
 }
-// (complex128 z passes are FP64-ALU-bound and keep their registers)
+// (complex128 z passes are FP64-ALU-bound and keep their registers; the
+// double-float ones take two 384-thread blocks per SM where their registers
+// fit 85 without spilling: the power-of-two lengths up to 128)
 template <int L, typename T> __host__ __device__ constexpr int zconv_min_blocks() {
     constexpr int threads = 3 * tp_z<L, T>() * ZPlan<L>::NT;
+    if constexpr (std::is_same<T, dfl>::value) return (threads == 384 && (L == 64 || L == 128)) ? 2 : 1;
     return (sizeof(T) == 4 && 2048 / threads >= 3) ? 3 : 1;
 }
 // Row stride (complex elements) of the z pass's shared-memory planes.

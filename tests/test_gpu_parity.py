@@ -471,6 +471,28 @@ def test_sphere16_solve_matches_oracle_bicgstab(lib):
     ctx.close()
 
 
+@pytest.mark.parametrize("k", [1, 3, 7])
+def test_iteration_limit_returns_the_kth_bicgstab_iterate(lib, k):
+    """A solve stopped by its iteration limit returns the oracle BiCGstab's
+    k-th iterate: the update x += alpha p + omega s of the last iteration,
+    which the GPU solve applies in the next iteration's first gather, is
+    applied after the loop for a RHS that stops (c1 workload, FP64)."""
+    w = workload("sphere16")
+    ctx = _ctx(lib, w.grid, w.m, w.x, lib.Precision.FP64)
+    kd = ctx.info()["kd"]
+    res, P, st = ctx.solve(0, w.khat[:1], w.ehat[:1], tol=1e-14, maxit=k)
+    assert res[0]["iters"] == k
+    assert res[0]["status_name"] == "DDA_ERR_NOT_CONVERGED"
+    r, _ = odda.site_positions(w.grid)
+    _, beta = _site_beta(w.grid, w.m, kd, w.khat[0], w.ehat[0])
+    E = odda.incident_field(r, kd, w.khat[0], w.ehat[0])
+    mv = lambda v: pairwise.matvec(r, kd, beta, v.reshape(-1, 3))[0].ravel()  # noqa: E731
+    Po, it, _, _ = odda.bicgstab(mv, E.ravel(), 1e-14, k)
+    assert it == k
+    assert _rel(P[0].T, Po.reshape(-1, 3)) < 1e-10
+    ctx.close()
+
+
 def test_batched_masked_solve_equals_single_solves(lib):
     grid = ellipsoid_grid(12, 10, 8, 12, 10, 8)
     m = [1.33 + 0.05j]

@@ -309,10 +309,10 @@ template <class PL, int ES> __host__ __device__ constexpr int tp_sp() {
     const int tp = (256 / PL::NT) > 32 ? 32 : ((256 / PL::NT) < 8 ? 8 : (256 / PL::NT));
     return (ES == 8 && tp < 16) ? 16 : tp;
 }
-template <typename T, int L, int MODE, int V = 0>
-__global__ void __launch_bounds__(tp_sp<SPlan<L, V>, sizeof(cx<T>)>() * SPlan<L, V>::NT)
-    k_strided(const cx<T>* src, cx<T>* dst, int64_t pt_stride, int width, int64_t src_bstride, int64_t dst_bstride,
-              int batches_per_rhs, const cx<T>* __restrict__ tw, const int* __restrict__ active) {
+template <typename T, int L, int MODE, int V>
+__device__ __forceinline__ void strided_body(const cx<T>* src, cx<T>* dst, int64_t pt_stride, int width,
+                                             int64_t src_bstride, int64_t dst_bstride, int batches_per_rhs,
+                                             const cx<T>* __restrict__ tw, const int* __restrict__ active) {
     using C = cx<T>;
     using PL = SPlan<L, V>;
     constexpr int TP = tp_sp<PL, sizeof(cx<T>)>();
@@ -335,6 +335,25 @@ __global__ void __launch_bounds__(tp_sp<SPlan<L, V>, sizeof(cx<T>)>() * SPlan<L,
     for_each_out<PL, DIR, MODE == 1>(u, [&](int idx, int pos) {
         if (valid) d[pos * pt_stride] = v[idx];
     });
+}
+template <typename T, int L, int MODE, int V = 0>
+__global__ void __launch_bounds__(tp_sp<SPlan<L, V>, sizeof(cx<T>)>() * SPlan<L, V>::NT)
+    k_strided(const cx<T>* src, cx<T>* dst, int64_t pt_stride, int width, int64_t src_bstride, int64_t dst_bstride,
+              int batches_per_rhs, const cx<T>* __restrict__ tw, const int* __restrict__ active) {
+    strided_body<T, L, MODE, V>(src, dst, pt_stride, width, src_bstride, dst_bstride, batches_per_rhs, tw, active);
+}
+// The complex64 512-point y passes with the 32 x 16 plan, capped at 80
+// registers for three 256-thread blocks per SM (the inverse took 90 and ran
+// two: 8.98 -> 8.39 ms on the 256^3 sphere).  The same cap slowed the 128- and
+// 192-point passes by 11-14 %, so they keep k_strided.
+template <typename T, int L, int MODE, int V = 0>
+__global__ void __launch_bounds__(tp_sp<SPlan<L, V>, sizeof(cx<T>)>() * SPlan<L, V>::NT, 3)
+    k_strided3(const cx<T>* src, cx<T>* dst, int64_t pt_stride, int width, int64_t src_bstride,
+               int64_t dst_bstride, int batches_per_rhs, const cx<T>* __restrict__ tw, const int* __restrict__ active) {
+    strided_body<T, L, MODE, V>(src, dst, pt_stride, width, src_bstride, dst_bstride, batches_per_rhs, tw, active);
+}
+template <typename T, int L, int V> __host__ __device__ constexpr bool strided_capped() {
+    return sizeof(cx<T>) == 8 && L == 512 && V == 1;
 }
 
 // ---- z pass with the Fourier-space product ------------------------------------
@@ -1031,11 +1050,15 @@ template <typename T> struct LaunchX {
         using PL = SPlan<L, V>;
         constexpr int TP = tp_sp<PL, sizeof(cx<T>)>(), NTH = TP * PL::NT;
         const size_t sm = (size_t)exchange_rows<L, PL::NT, TP, sizeof(cx<T>)>() * TP * sizeof(cx<T>);
-        cudaError_t e = allow_smem(k_strided<T, L, MODE, V>, sm);
+        auto kern = [] {
+            if constexpr (strided_capped<T, L, V>()) return k_strided3<T, L, MODE, V>;
+            else return k_strided<T, L, MODE, V>;
+        }();
+        cudaError_t e = allow_smem(kern, sm);
         if (e != cudaSuccess) return e;
         dim3 grid((width + TP - 1) / TP, batches, 1);
         PROF_BEGIN(st);
-        k_strided<T, L, MODE, V><<<grid, NTH, sm, st>>>(src, dst, pt_stride, width, sb, db, per_rhs, tw, active);
+        kern<<<grid, NTH, sm, st>>>(src, dst, pt_stride, width, sb, db, per_rhs, tw, active);
         PROF_END(kind, units, st);
         return cudaGetLastError();
     }

@@ -74,10 +74,11 @@ def parse():
     ap.add_argument("--solver", default="bicgstab", choices=["bicgstab", "bicgstab2", "qmr"],
                     help="solve mode: BiCGstab (default), BiCGstab(2) (the guide's PBCGS2) or QMR for complex "
                          "symmetric A (the guide's QMRCCG)")
-    ap.add_argument("--xpass", type=int, default=-1, choices=[-1, 0, 1, 2],
+    ap.add_argument("--xpass", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
                     help="complex64 x-pass schedule: -1 autotuned (default), 0 rows staged through shared memory, "
-                         "1 + V warp-local rows with radix plan V")
-    ap.add_argument("--xinv", type=int, default=None, choices=[-1, 0, 1, 2],
+                         "1 + V warp-local rows with radix plan V (the last V of 64, 128, 256 and 512 points "
+                         "exchanges by warp shuffles)")
+    ap.add_argument("--xinv", type=int, default=None, choices=[-1, 0, 1, 2, 3],
                     help="x-inverse schedule (overrides --xpass for the inverse pass only)")
     ap.add_argument("--ypass", type=int, default=-1, choices=[-1, 0, 1],
                     help="complex64 y-pass radix plan: -1 autotuned (default), 0 or 1")

@@ -346,9 +346,12 @@ dda_status dda_grad_qabs(dda_ctx* ctx, dda_precision precision, const double* kh
  * dda_set_slice_passes: on -1 automatic, 0 always the separate passes (the
  *   default: measured on GB300 the slice passes are faster only for small
  *   grids outside a solve), 1 the slice passes wherever they are built.
- * dda_set_xpass: xfwd, xinv -1 automatic (the default), 0, 1 or 2 forces
- *   that x-forward / x-inverse schedule where it exists (2 falls back to 1
- *   where Lx has one plan).
+ * dda_set_xpass: xfwd, xinv -1 automatic (the default), 0..3 forces that
+ *   x-forward / x-inverse schedule: 0 rows staged through shared memory,
+ *   1 + V the warp-local rows with radix plan variant V (Lx = 128, 256, 512:
+ *   V = 0, 1, 2; Lx = 64, 192: V = 0, 1; else V = 0; the last variant of 64,
+ *   128, 256 and 512 points exchanges by warp shuffles); a V beyond the
+ *   length's variants falls back to its last one.
  * The setters clear the timings; any other value: DDA_ERR_ARG.
  * dda_get_schedule: the z schedule (and, if slices is not NULL, whether the
  *   slice passes run) of complex64 matvecs of R RHS on the current target,

@@ -2302,8 +2302,8 @@ dda_status dda_get_ypass(dda_ctx* ctx, int R, int* ypass) {
 
 dda_status dda_set_xpass(dda_ctx* ctx, int xfwd, int xinv) {
     if (!ctx) return DDA_ERR_ARG;
-    if (xfwd < -1 || xfwd > 2 || xinv < -1 || xinv > 2)
-        return ctx->fail(DDA_ERR_ARG, "x-pass schedules must be -1, 0, 1 or 2 (got %d, %d)", xfwd, xinv);
+    if (xfwd < -1 || xfwd > 3 || xinv < -1 || xinv > 3)
+        return ctx->fail(DDA_ERR_ARG, "x-pass schedules must be -1, 0, 1, 2 or 3 (got %d, %d)", xfwd, xinv);
     ctx->force_xf = xfwd;
     ctx->force_xi = xinv;
     ctx->zsched.clear();

@@ -25,6 +25,8 @@
 // exchange through shared memory with two barriers each -- block barriers,
 // or warp barriers when every pencil lies within one warp (WARP) -- so every
 // thread of the block must run these routines the same number of times.
+// Two-stage plans whose pencil lies in consecutive lanes can exchange by
+// warp shuffles instead (ShflExchange), with no shared memory and no barrier.
 #pragma once
 
 #include "common.cuh"
@@ -315,6 +317,61 @@ template <int SGN, typename C> struct Dft<32, SGN, C> {
 // and map position pos of the exchange after stage S to a swizzled slot;
 // the default keeps the position.
 struct NoSwizzle {
+    static constexpr bool kShuffle = false;
+    template <int DIR, int S> __device__ __forceinline__ static int map(int pos) { return pos; }
+};
+
+// ---- exchange by warp shuffles ---------------------------------------------
+// For a two-stage plan whose first radix R is a multiple of NT and whose
+// pencil lies in NT consecutive lanes, the exchange is a set of NT x NT
+// transposes: the first stage leaves output position (u + q NT) R + m in
+// register q R + m of lane u (P = 1), and the second stage wants position
+// u' + NT c (c = q2 + j E/R2) in register q2 R2 + j of lane u'.  Writing the
+// register as h NT + l, lane u's register h NT + l goes to lane l, register
+// h NT + u.  shfl_exchange_ok checks that for every lane and register.
+template <class PL, int DIR> __host__ __device__ constexpr bool shfl_exchange_ok() {
+    constexpr int L = PL::L, NT = PL::NT, E = PL::E;
+    if (PL::NS != 2 || E % NT != 0 || NT > 32 || (NT & (NT - 1)) != 0) return false;
+    constexpr int R = stage_radix<PL, DIR>(0), R2 = stage_radix<PL, DIR>(1);
+    constexpr int NB = E / R, NB2 = E / R2;
+    if (L / R2 != NT * NB2) return false;
+    for (int u = 0; u < NT; ++u)
+        for (int q = 0; q < NB; ++q)
+            for (int m = 0; m < R; ++m) {
+                const int pos = (u + q * NT) * R + m, reg = q * R + m;
+                const int h = reg / NT, l = reg % NT;
+                const int c = pos / NT, want = (c % NB2) * R2 + c / NB2;
+                if (pos % NT != l || want != h * NT + u) return false;
+            }
+    return true;
+}
+
+// In-register transpose of the NT x NT blocks v[h NT + i] across NT
+// consecutive lanes (u = lane within the group), in log2(NT) rounds: round b
+// swaps the entries whose lane bit b and register bit b differ with lane
+// u ^ b, so after all rounds lane u holds register u of every lane.
+template <int NT, int E, typename C> __device__ __forceinline__ void shfl_transpose(C (&v)[E], int u) {
+#pragma unroll
+    for (int b = 1; b < NT; b <<= 1) {
+        const bool hi = (u & b) != 0;
+#pragma unroll
+        for (int h = 0; h < E / NT; ++h)
+#pragma unroll
+            for (int i = 0; i < NT; ++i) {
+                if (i & b) continue;
+                C& lo_reg = v[h * NT + i];
+                C& hi_reg = v[h * NT + (i | b)];
+                const C send = hi ? lo_reg : hi_reg;
+                C recv;
+                recv.x = __shfl_xor_sync(0xffffffffu, send.x, b);
+                recv.y = __shfl_xor_sync(0xffffffffu, send.y, b);
+                if (hi) lo_reg = recv;
+                else hi_reg = recv;
+            }
+    }
+}
+struct ShflExchange {
+    static constexpr bool kShuffle = true;
     template <int DIR, int S> __device__ __forceinline__ static int map(int pos) { return pos; }
 };
 
@@ -374,7 +431,11 @@ __device__ __forceinline__ void fft_stages(C (&v)[PL::E], int u, const C* __rest
             Dft<R, DIR, C>::run(&v[q * R]);
         }
     }
-    if constexpr (S < NS - 1) {
+    if constexpr (S < NS - 1 && SWZ::kShuffle) {
+        static_assert(S == 0 && shfl_exchange_ok<PL, DIR>(), "the shuffle exchange needs a two-stage transpose plan");
+        shfl_transpose<NT>(v, u);
+        fft_stages<C, PL, DIR, S + 1, Ld, St, WARP, SWZ>(v, u, tw, ld, st, false);
+    } else if constexpr (S < NS - 1) {
         stage_sync<WARP>();
         if constexpr (NT % P == 0) {
             const int base = (u / P) * (P * R) + (u % P);

@@ -24,11 +24,17 @@ int pick_fft_length(int n) {
 // Blocks of one RHS in the x-inverse pass (partial-sum slots per RHS): the
 // most among the staged tilings of complex64 and 16-byte elements and the
 // warp-local blocks of every plan variant.
+template <int L, int V = 0> static int min_xwi_rows() {
+    int tp = xwi_rows<XwPlan<L, V>>();
+    if constexpr (V + 1 < xw_variants(L)) {
+        const int rest = min_xwi_rows<L, V + 1>();
+        tp = rest < tp ? rest : tp;
+    }
+    return tp;
+}
 template <int L> static int min_tp_x() {
     int tp = tp_x<L, 8>() < tp_x<L, 16>() ? tp_x<L, 8>() : tp_x<L, 16>();
-    tp = xwi_rows<XwPlan<L, 0>>() < tp ? xwi_rows<XwPlan<L, 0>>() : tp;
-    if constexpr (xw_variants(L) > 1) tp = xwi_rows<XwPlan<L, 1>>() < tp ? xwi_rows<XwPlan<L, 1>>() : tp;
-    return tp;
+    return min_xwi_rows<L>() < tp ? min_xwi_rows<L>() : tp;
 }
 int xinv_blocks_per_rhs(const Geom& g) {
     const int nrows = g.ny * g.nz;

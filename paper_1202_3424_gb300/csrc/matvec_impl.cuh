@@ -941,14 +941,22 @@ template <typename T> struct LaunchX {
         return cudaErrorInvalidValue;
     }
     template <int LX> static int xvariants() { return kWarpX ? 1 + xw_variants(LX) : 1; }
+    // f(integral_constant<V>) for plan variant v of the warp-local rows (the
+    // last variant where v is larger)
+    template <int LX, int V = 0, class F> static cudaError_t by_xvariant(int v, F&& f) {
+        if constexpr (V + 1 < xw_variants(LX)) {
+            if (v > V) return by_xvariant<LX, V + 1>(v, f);
+        }
+        return f(std::integral_constant<int, V>{});
+    }
     template <int LX>
     static cudaError_t fwd(const Geom& g, int R, cx<T>* x, cx<T>* u1, const int* site_of, const cx<T>* tw,
                            const int* active, const FusedKrylov<T>& fk, int xvar, cudaStream_t st) {
         if constexpr (kWarpX) {
-            if (xvar == 2 && xw_variants(LX) > 1) {
-                if constexpr (xw_variants(LX) > 1) return fwd_w<LX, 1>(g, R, x, u1, site_of, tw, active, fk, st);
-            }
-            if (xvar >= 1) return fwd_w<LX, 0>(g, R, x, u1, site_of, tw, active, fk, st);
+            if (xvar >= 1)
+                return by_xvariant<LX>(xvar - 1, [&](auto v) {
+                    return fwd_w<LX, decltype(v)::value>(g, R, x, u1, site_of, tw, active, fk, st);
+                });
         }
         constexpr int TP = tp_x<LX, sizeof(cx<T>)>(), NTH = TP * XPlan<LX, sizeof(cx<T>)>::NT;
         const size_t sm = (size_t)LX * (TP + 1) * sizeof(cx<T>);
@@ -1012,16 +1020,12 @@ template <typename T> struct LaunchX {
             return launch(std::integral_constant<int, kDiagComp>{});
         };
         if constexpr (kWarpX) {
-            if (xvar == 2 && xw_variants(LX) > 1) {
-                if constexpr (xw_variants(LX) > 1)
-                    return by_diag([&](auto d) {
-                        return inv_w<LX, 1, decltype(d)::value>(g, R, u1, y, x, tg, beta, beta_stride, tw, active,
-                                                                fk, st);
-                    });
-            }
             if (xvar >= 1)
-                return by_diag([&](auto d) {
-                    return inv_w<LX, 0, decltype(d)::value>(g, R, u1, y, x, tg, beta, beta_stride, tw, active, fk, st);
+                return by_xvariant<LX>(xvar - 1, [&](auto v) {
+                    return by_diag([&](auto d) {
+                        return inv_w<LX, decltype(v)::value, decltype(d)::value>(g, R, u1, y, x, tg, beta,
+                                                                                 beta_stride, tw, active, fk, st);
+                    });
                 });
         }
         auto run = [&](auto mode) {

@@ -18,8 +18,10 @@
 //
 // Radix plans: variant 0 is the plan of the staged x passes; variant 1, where
 // it exists, trades registers for fewer exchanges (radix 16 or 32, or radix 8
-// with more points per lane).  The context times the variants inside whole
-// matvecs and keeps the fastest (see pick_schedule in abi.cu).
+// with more points per lane); the last variant of 64, 128, 256 and 512 points
+// is a two-stage plan whose exchange runs by warp shuffles.  The context
+// times the variants inside whole matvecs and keeps the fastest (see
+// pick_schedule in abi.cu).
 #pragma once
 
 #include "fft.cuh"
@@ -42,10 +44,23 @@ template <> struct XwPlan<256, 1> : PlanDef<256, 16, 16, 16> {};
 template <> struct XwPlan<384, 0> : PlanDef<384, 32, 4, 4, 4, 3, 2> {};
 template <> struct XwPlan<512, 0> : PlanDef<512, 32, 8, 8, 8> {};
 template <> struct XwPlan<512, 1> : PlanDef<512, 16, 32, 16> {};
+// Warp-shuffle variants: the two-stage plans (8 x 8, 8 x 16, 16 x 16,
+// 32 x 16) with their one exchange done by shuffles between the pencil's
+// lanes (shfl_transpose in fft.cuh) instead of the shared-memory plane.
+template <class B> struct ShflPlan : B {
+    static constexpr bool kShuffle = true;
+};
+template <> struct XwPlan<64, 1> : ShflPlan<PlanDef<64, 8, 8, 8>> {};
+template <> struct XwPlan<128, 2> : ShflPlan<PlanDef<128, 8, 8, 16>> {};
+template <> struct XwPlan<256, 2> : ShflPlan<PlanDef<256, 16, 16, 16>> {};
+template <> struct XwPlan<512, 2> : ShflPlan<PlanDef<512, 16, 32, 16>> {};
+
+template <class PL, class = void> struct xw_shfl : std::false_type {};
+template <class PL> struct xw_shfl<PL, std::void_t<decltype(PL::kShuffle)>> : std::bool_constant<PL::kShuffle> {};
 
 // Number of plan variants per length.
 __host__ __device__ constexpr int xw_variants(int L) {
-    return (L == 128 || L == 192 || L == 256 || L == 512) ? 2 : 1;
+    return (L == 128 || L == 256 || L == 512) ? 3 : ((L == 64 || L == 192) ? 2 : 1);
 }
 
 // Exchange-plane swizzle key K of the exchange after stage S (0: none).
@@ -103,6 +118,7 @@ __host__ __device__ constexpr int warp_plane_pad(int NT) {
 }
 
 template <class PL> struct WarpSwz {
+    static constexpr bool kShuffle = false;
     template <int DIR, int S> __device__ __forceinline__ static int map(int pos) {
         constexpr int K = warp_swizzle_key(PL::L, PL::NT, DIR, S);
         if constexpr (K == 0) return pos;
@@ -117,7 +133,11 @@ constexpr int kXwThreads = 256;
 constexpr int kXwiThreads = 128;
 template <class PL> __host__ __device__ constexpr int xw_rows() { return kXwThreads / PL::NT; }
 template <class PL> __host__ __device__ constexpr int xwi_rows() { return kXwiThreads / PL::NT; }
-template <class PL> __host__ __device__ constexpr int xw_plane() { return PL::L + warp_plane_pad(PL::NT); }
+// (the shuffle variants need no exchange plane)
+template <class PL> __host__ __device__ constexpr int xw_plane() {
+    return xw_shfl<PL>::value ? 0 : PL::L + warp_plane_pad(PL::NT);
+}
+template <class PL> using XwExchange = std::conditional_t<xw_shfl<PL>::value, ShflExchange, WarpSwz<PL>>;
 // exchange planes of the block's rows, then the twiddle table
 template <class PL> __host__ __device__ constexpr size_t xw_smem() {
     return ((size_t)xw_rows<PL>() * xw_plane<PL>() + (PL::L <= 256 ? PL::L : 0)) * sizeof(float2);
@@ -210,7 +230,7 @@ __global__ void __launch_bounds__(kXwThreads, xwf_min_blocks<XwPlan<LX, V>>())
     const C* tws = stage_twiddles<LX>(reinterpret_cast<C*>(smem_raw) + RPB * PS, tw);
     auto ld = [&](int pos) { return plane[pos]; };
     auto stf = [&](int pos, C val) { plane[pos] = val; };
-    fft_stages<C, PL, -1, 0, decltype(ld), decltype(stf), true, WarpSwz<PL>>(v, u, tws, ld, stf, true);
+    fft_stages<C, PL, -1, 0, decltype(ld), decltype(stf), true, XwExchange<PL>>(v, u, tws, ld, stf, true);
     C* out = U + rm.at(r, c, ok ? row : 0, LX);
     for_each_out<PL, -1, false>(u, [&](int idx, int pos) {
         if (ok) out[pos] = v[idx];
@@ -284,7 +304,7 @@ __global__ void __launch_bounds__(kXwiThreads, (xwi_mode_min_blocks<XwPlan<LX, V
     if constexpr (kHoist) load_operands();
     auto ld = [&](int pos) { return plane[pos]; };
     auto stf = [&](int pos, C val) { plane[pos] = val; };
-    fft_stages<C, PL, +1, 0, decltype(ld), decltype(stf), true, WarpSwz<PL>>(v, u, tw, ld, stf, false);
+    fft_stages<C, PL, +1, 0, decltype(ld), decltype(stf), true, XwExchange<PL>>(v, u, tw, ld, stf, false);
     if constexpr (!kHoist) load_operands();
     DotAcc<C> d[4];
 #pragma unroll

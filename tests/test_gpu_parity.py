@@ -148,8 +148,9 @@ def test_matvec_long_z_columns_many_rhs(lib, zpass):
 
 
 # Rows of the hot x lengths (Lx = 128, 192, 256, 512): full, ragged and
-# two-material rows, every x-pass schedule (0 staged rows, 1 and 2 the
-# warp-local rows with radix plan variants 0 and 1).
+# two-material rows, every x-pass schedule (0 staged rows, 1 + V the
+# warp-local rows with radix plan variant V; the last variant of 64, 128, 256
+# and 512 points exchanges by warp shuffles).
 X_CASES = [
     ("rows128_block_64x6x4", lambda: block_bernoulli_grid(64, 6, 4, seed=21), [1.6 + 0.1j, 1.3 + 0.02j], 2.0),
     ("rows192_ellipsoid_90x7x5", lambda: ellipsoid_grid(90, 7, 5, 90, 7, 5), [1.5 + 0.05j], 3.0),
@@ -158,11 +159,11 @@ X_CASES = [
     ("rows64_plate_25x25x3", MATVEC_CASES[5][1], MATVEC_CASES[5][2], MATVEC_CASES[5][3]),
     ("rows32_ellipsoid_ragged", MATVEC_CASES[2][1], MATVEC_CASES[2][2], MATVEC_CASES[2][3]),
 ]
-X_VARIANTS = {128: 2, 192: 2, 256: 2, 512: 2}   # radix plan variants of the warp-local rows
+X_VARIANTS = {64: 2, 128: 3, 192: 2, 256: 3, 512: 3}   # radix plan variants of the warp-local rows
 
 
 @pytest.mark.parametrize("name,gridf,m,x", X_CASES, ids=[c[0] for c in X_CASES])
-@pytest.mark.parametrize("xpass", [0, 1, 2], ids=["xstaged", "xwarp_plan0", "xwarp_plan1"])
+@pytest.mark.parametrize("xpass", [0, 1, 2, 3], ids=["xstaged", "xwarp_plan0", "xwarp_plan1", "xwarp_plan2"])
 def test_matvec_x_schedules_match_oracle(lib, name, gridf, m, x, xpass):
     """The complex64 x-pass schedules against the pairwise oracle, isotropic
     and with tilted biaxial materials (the tensor 1/alpha of the x-inverse)."""
@@ -199,7 +200,7 @@ def test_matvec_x_schedules_match_oracle(lib, name, gridf, m, x, xpass):
     ctx.close()
 
 
-@pytest.mark.parametrize("xpass", [0, 1, 2], ids=["xstaged", "xwarp_plan0", "xwarp_plan1"])
+@pytest.mark.parametrize("xpass", [0, 1, 2, 3], ids=["xstaged", "xwarp_plan0", "xwarp_plan1", "xwarp_plan2"])
 def test_refined_solve_through_each_x_schedule(lib, xpass):
     """The BiCGstab updates fused into the x passes (gather and scatter modes
     1 and 2, with their reductions) under each x schedule: a FP32-refined
@@ -302,7 +303,7 @@ def test_autotuned_schedule_reproduces_forced_one(lib):
     zpick, spick = ctx.get_schedule(R, with_slices=True)
     xpick = ctx.get_xpass(R)
     ypick = ctx.get_ypass(R)
-    assert zpick in (0, 1, 2, 3, 4) and spick in (0, 1) and all(v in (0, 1, 2) for v in xpick) and ypick in (0, 1)
+    assert zpick in (0, 1, 2, 3, 4) and spick in (0, 1) and all(v in (0, 1, 2, 3) for v in xpick) and ypick in (0, 1)
     X = random_complex((R, 3, ctx.info()["ndipoles"]), 4).astype(np.complex64)
     k, e = np.resize(w.khat, (R, 3)), np.resize(w.ehat, (R, 3))
     y_auto = ctx.matvec(2, k, e, X)
@@ -316,7 +317,7 @@ def test_autotuned_schedule_reproduces_forced_one(lib):
     with pytest.raises(lib.DdaError):
         ctx.set_schedule(5)
     with pytest.raises(lib.DdaError):
-        ctx.set_xpass(3)
+        ctx.set_xpass(4)
     ctx.close()
 
 

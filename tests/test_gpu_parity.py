@@ -147,6 +147,28 @@ def test_matvec_long_z_columns_many_rhs(lib, zpass):
     ctx.close()
 
 
+@pytest.mark.parametrize("zpass", [0, 1, 2, 3, 4], ids=Z_IDS)
+def test_matvec_512_point_z_columns(lib, zpass):
+    """A 3x2x200 rod (512-point z transform, one radix plan: schedules 3
+    and 4 fall back to 1 and 2) with 18 RHS: a full block of 16 RHS and a
+    ragged one, against the pairwise oracle."""
+    grid = np.ones((200, 2, 3), np.uint8)
+    m = [1.5 + 0.02j]
+    ctx = _ctx(lib, grid, m, 2.5, lib.Precision.FP32_REFINED)
+    info = ctx.info()
+    assert info["Lz"] == 512
+    ctx.set_schedule(zpass)
+    R = 18
+    khat, ehat = _rhs_set(R)
+    X = random_complex((R, 3, info["ndipoles"]), 15)
+    Y = ctx.matvec(2, khat, ehat, X)
+    for r in range(R):
+        rr, beta = _site_beta(grid, m, info["kd"], khat[r], ehat[r])
+        want, _ = pairwise.matvec(rr, info["kd"], beta, X[r].T)
+        assert _rel(Y[r].T, want) < F32_TOL, (zpass, r)
+    ctx.close()
+
+
 # Rows of the hot x lengths (Lx = 128, 192, 256, 512): full, ragged and
 # two-material rows, every x-pass schedule (0 staged rows, 1 + V the
 # warp-local rows with radix plan variant V; the last variant of 64, 128, 256

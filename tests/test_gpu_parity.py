@@ -49,6 +49,15 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / np.abs(b).max())
 
 
+def _rel_elem(a, b, floor):
+    """Largest error of any single element, relative to that element's own
+    magnitude plus floor * max|b|.  An FFT convolution spreads its rounding
+    error evenly over the output (about eps * log2(L) * max|b| per element),
+    so elements far below floor * max|b| cannot be matched to the relative
+    tolerance; every element above it is held to it on its own."""
+    return float((np.abs(a - b) / (np.abs(b) + floor * np.abs(b).max())).max())
+
+
 def _rhs_set(R, seed=20120214):
     k = uniform_directions(R, seed)
     e1, _ = polarization_pair(k)
@@ -81,6 +90,8 @@ def test_matvec_matches_pairwise_oracle(lib, name, gridf, m, x, prec, tol):
         rr, beta = _site_beta(grid, m, kd, khat[r], ehat[r])
         want, _ = pairwise.matvec(rr, kd, beta, X[r].T)
         assert _rel(Y[r].T, want) < tol, (name, r)
+        if prec != 2:   # FP64 and double-float: element by element above 1 % of the largest
+            assert _rel_elem(Y[r].T, want, 1e-2) < tol, (name, r)
     ctx.close()
 
 

@@ -16,11 +16,14 @@
 // (krylov_dev.cuh: finalize_omega_rho); k_finish_x applies the last x
 // update of a RHS that stopped.
 // Vectors are complex64 or complex128; every scalar (rho, alpha, omega,
-// beta, norms) is FP64.  Reductions write one FP64 partial per block; the
-// last block of a reduction (atomic ticket) sums the partials and updates the
-// per-RHS scalars on the device, so an iteration needs no host round trip and
-// can be replayed as a CUDA graph.  A RHS whose `active` flag is 0 is skipped
-// by every kernel (per-RHS convergence masking).
+// beta, norms) is FP64.  The iteration's sums are written as partials by the
+// x-inverse blocks and summed per RHS, in a fixed order, by k_fused_finalize
+// (krylov_dev.cuh), which also updates the scalars; the reductions of this
+// file (initial rho, norms, Q sums) write one FP64 partial per block and the
+// last block of each (atomic ticket) sums them.  Either way the scalars stay
+// on the device, so an iteration needs no host round trip and can be
+// replayed as a CUDA graph.  A RHS whose `active` flag is 0 is skipped by
+// every kernel (per-RHS convergence masking).
 #include <math.h>
 
 #include "internal.h"

@@ -2,7 +2,9 @@
 // the matvec passes that fuse Krylov updates into their gather/scatter:
 // dot-product accumulators, block and last-block reductions (FP64 totals
 // per right-hand side, with an atomic ticket so that the last block to
-// finish updates the per-RHS scalars on the device), and the scalar updates.
+// finish updates the per-RHS scalars on the device), the partial sums of the
+// fused passes and the per-RHS kernel that sums them (k_fused_finalize), and
+// the scalar updates.
 #pragma once
 
 #include <math.h>

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(tp_x<LX, sizeof(cx<T>)>() * XPlan<LX, sizeof(c
 //   kDiagTensor  row c of its composition's tensor, times all three
 //                components of X (layout in PadWork::beta_tensor);
 //   kDiagSite    the scalar of site s itself, entry s + 1 (per-site materials).  Fused BiCGstab reductions
-// (FP64 totals per RHS over all blocks of that RHS, finalized by the last one):
+// (partial sums per block, summed per RHS by k_fused_finalize):
 //   MODE 1  Y = v:  sigma = <rhat, v>                    ->  alpha = rho / sigma
 //   MODE 2  Y = t:  <t, s>, <t, t>, <s, s>, <rhat, s>,
 //                   <rhat, t> with X = s                 ->  finalize_omega_rho

@@ -201,6 +201,13 @@ __global__ void __launch_bounds__(kXwThreads, xwf_min_blocks<XwPlan<LX, V>>())
 #pragma unroll
         for (int j = 0; j < JN; ++j)
             sidx[q * JN + j] = ok ? site_of[(int64_t)row * NX + u + q * NT + j * (LX / R0)] : -1;
+    // the twiddle table goes to shared memory while loads are in flight: in
+    // the fused modes, which use their gathered values at once (the update is
+    // stored), behind the site-index loads, so that the copy's block barrier
+    // does not wait for the slowest warp's gathers; in MODE 0 behind the
+    // gathers themselves
+    const C* tws = tw;
+    if constexpr (MODE != 0) tws = stage_twiddles<LX>(reinterpret_cast<C*>(smem_raw) + RPB * PS, tw);
     C v[E];
     Gathered<C> gv[MODE == 3 ? NB0 * JN : 1];  // (MODE 3 keeps r and x for the stores)
 #pragma unroll
@@ -227,7 +234,7 @@ __global__ void __launch_bounds__(kXwThreads, xwf_min_blocks<XwPlan<LX, V>>())
                 fused_store<MODE>(xs, fv, off, s, o);
             }
     }
-    const C* tws = stage_twiddles<LX>(reinterpret_cast<C*>(smem_raw) + RPB * PS, tw);
+    if constexpr (MODE == 0) tws = stage_twiddles<LX>(reinterpret_cast<C*>(smem_raw) + RPB * PS, tw);
     auto ld = [&](int pos) { return plane[pos]; };
     auto stf = [&](int pos, C val) { plane[pos] = val; };
     fft_stages<C, PL, -1, 0, decltype(ld), decltype(stf), true, XwExchange<PL>>(v, u, tws, ld, stf, true);

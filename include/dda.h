@@ -222,7 +222,9 @@ dda_status dda_matvec_device(dda_ctx* ctx, dda_precision precision, int R, const
  * one array and leave their data in it; no part of it needs to start at zero
  * (every buffer is written before it is read), but calls that overlap on the
  * GPU race on it, so do not run two of them concurrently on one device.
- * Synchronizes the context stream before returning.                            */
+ * Synchronizes the context stream before returning, so it cannot be part of
+ * a CUDA graph: called while the context stream is being captured it returns
+ * DDA_ERR_ARG and leaves the capture untouched.                               */
 dda_status dda_matvec_device_noalloc(dda_ctx* ctx, dda_precision precision, int R, const double* khat,
                                      const double* e, const void* x_dev, void* y_dev);
 

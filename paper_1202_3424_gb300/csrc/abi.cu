@@ -1606,6 +1606,13 @@ dda_status dda_matvec_device_noalloc(dda_ctx* ctx, dda_precision precision, int 
         return ctx->fail(DDA_ERR_ARG,
                          "dda_matvec_device_noalloc takes DDA_FP64 or DDA_FP32 (got %d); the double-float "
                          "DDA_DF64 matvec is available through dda_matvec_device only", (int)precision);
+    // (it copies its 1/alpha table from host memory and synchronizes the
+    // stream: neither may happen inside a stream capture)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing(ctx->stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+        return ctx->fail(DDA_ERR_ARG, "dda_matvec_device_noalloc cannot run inside a stream capture (it synchronizes "
+                                      "the context stream)");
     dda_status rs;
     if ((rs = check_ready(ctx, precision)) != DDA_OK) return rs;
     CU(cudaSetDevice(ctx->device));

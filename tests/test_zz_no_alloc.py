@@ -107,3 +107,38 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(env):
         dda.dda_matvec_device_noalloc(ctx.handle, 2, np.repeat(w.khat[:1], R, 0), np.repeat(w.ehat[:1], R, 0), x, y)
     assert ei.value.status_name == "DDA_ERR_SIZE"
     ctx.close()
+
+
+def test_noalloc_refuses_a_stream_capture(env):
+    """The call synchronizes its stream, so inside a capture of the context
+    stream it returns DDA_ERR_ARG before touching the stream; the capture
+    stays valid and the next uncaptured call works."""
+    dda, torch = env
+    ctx = dda.Context(0)
+    ctx.set_target(sphere_grid(8))
+    ctx.set_materials([1.33 + 0.01j])
+    ctx.prepare_size_parameter(0.6, dda.Precision.FP32_REFINED)
+    N = ctx.info()["ndipoles"]
+    k = uniform_directions(1, 3)
+    e = polarization_pair(k)[0].astype(complex)
+    s = torch.cuda.Stream()
+    dda.dda_set_stream(ctx.handle, s.cuda_stream)
+    x = torch.from_numpy(random_complex((1, 3, N), 300)).to(torch.complex64).cuda()
+    y = torch.empty_like(x)
+    torch.cuda.synchronize()   # (x and y were made on the default stream)
+    with torch.cuda.stream(s):
+        dda.dda_matvec_device_noalloc(ctx.handle, 2, k, e, x, y)   # outside any capture: fine
+    torch.cuda.synchronize()
+    y0 = y.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        x.mul_(1)
+        with pytest.raises(dda.DdaError, match="capture"):
+            dda.dda_matvec_device_noalloc(ctx.handle, 2, k, e, x, y)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        dda.dda_matvec_device_noalloc(ctx.handle, 2, k, e, x, y)
+    torch.cuda.synchronize()
+    assert torch.equal(y, y0)
+    dda.dda_set_stream(ctx.handle, None)
+    ctx.close()
